@@ -1,0 +1,180 @@
+/*
+ * fd4 -- multi-scale anisotropic fourth-order diffusion (MAFOD) on one GPU.
+ *
+ * C ABI of the GB300 (sm_103a) library.  The method is the filter of
+ * Gorgi Zadeh, Didas, Wintergerst and Schultz, "Multi-Scale Anisotropic
+ * Fourth-Order Diffusion Improves Ridge and Valley Localization"
+ * (arXiv:1611.06906); section and equation numbers below refer to it.
+ *
+ * Conventions shared by every entry point
+ *   - Images are single-channel float32, row-major; pixel (x, y) of an image
+ *     with row pitch `pitch` (in elements) is p[y * pitch + x], x the column.
+ *     Every per-pixel array of one call (image, scale index map, tensor field,
+ *     V map) uses the same `pitch`, counted in elements of its own type.
+ *     pitch >= w and pitch % 4 == 0 (16-byte rows); device pointers 16-byte
+ *     aligned.  Minimum image size is 3 x 3.
+ *   - Names starting with d_ are device pointers, h_ host pointers.
+ *   - The caller owns every buffer.  Entry points never allocate memory;
+ *     scratch comes from a caller-provided workspace d_ws of at least
+ *     fd4_workspace_bytes(...) bytes (256-byte aligned).  A workspace may be
+ *     reused by later calls on the same stream, not by concurrent ones.
+ *   - All device work is enqueued on `stream` (NULL = legacy default stream)
+ *     and is asynchronous; the functions return once it is enqueued.
+ *   - Return value: FD4_OK (0) or a negative fd4_status.  Argument errors are
+ *     detected on the host before anything is enqueued.  FD4_ERR_CUDA means
+ *     a CUDA runtime call failed; cudaGetLastError() is left set.
+ *   - The parity tolerance the library is tested to (max-abs 1e-4 against an
+ *     FP64 evaluation of the same method) assumes intensities in [0, 1].
+ */
+#ifndef FD4_H
+#define FD4_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (the runtime's stream handle); NULL is the legacy stream. */
+typedef struct CUstream_st *fd4_stream_t;
+
+typedef enum fd4_status {
+    FD4_OK = 0,
+    FD4_ERR_BAD_ARG = -1,          /* null pointer, size or parameter out of range  */
+    FD4_ERR_UNSTABLE_TAU = -2,     /* 3T/(M(n^2+n)) > tau_max, or tau_max > 1/17    */
+    FD4_ERR_TOO_MANY_SIGMAS = -3,  /* n_sigma > FD4_MAX_SIGMAS                      */
+    FD4_ERR_PITCH = -4,            /* pitch < w or pitch % 4 != 0                   */
+    FD4_ERR_WS_TOO_SMALL = -5,     /* ws_bytes < fd4_workspace_bytes(...)           */
+    FD4_ERR_TIMEOUT = -6,          /* a bounded device-side wait gave up            */
+    FD4_ERR_CUDA = -7,             /* a CUDA runtime call failed                    */
+    FD4_ERR_ALIGN = -8,            /* device pointer not 16-byte aligned            */
+    FD4_ERR_SIGMA_RANGE = -9,      /* sigma <= 0, sigma > FD4_MAX_SIGMA, unsorted   */
+    FD4_ERR_NOT_IMPLEMENTED = -10
+} fd4_status;
+
+/* Which creases are enhanced (Sec. 3.2, the paragraph after Eq. 7) and which
+ * polarity the vesselness accepts (Sec. 3.3, Eq. 9 and its valley analogue). */
+typedef enum fd4_mode { FD4_RIDGE = 0, FD4_VALLEY = 1, FD4_BOTH = 2 } fd4_mode;
+
+/* Boundary of the discrete operator (Sec. 3.4).  NATURAL: a derivative row
+ * exists only where its 3x3 stencil fits in the image (per stencil); the
+ * scheme then conserves the mean grey value.  PERIODIC: wrap-around, meant for
+ * tests (the Fourier analysis of the biharmonic special case).              */
+typedef enum fd4_boundary { FD4_BC_NATURAL = 0, FD4_BC_PERIODIC = 1 } fd4_boundary;
+
+#define FD4_MAX_SIGMAS 32          /* scale-set size limit (uint8 index map)     */
+#define FD4_MAX_SIGMA 16.0f        /* largest sigma: kernel radius ceil(4 sigma) <= 64 */
+#define FD4_MAX_FED_STEPS 4096     /* longest FED cycle                          */
+
+typedef struct fd4_params {
+    float lambda;            /* contrast lambda of Eq. 7 (default 0.005)          */
+    float rho;               /* integration scale of Eq. 6 (default 0.5)          */
+    float beta;              /* Frangi beta of Eq. 9 (default 0.5)                */
+    float c;                 /* Frangi c of Eq. 9; <= 0: half the maximum of S
+                                over all scales and pixels of the image (default) */
+    float gamma;             /* scale normalisation sigma^(2 gamma) (default 1)    */
+    float tau_max;           /* stable explicit step (default 0.05, Sec. 3.5)      */
+    int mode;                /* fd4_mode (default FD4_BOTH, Sec. 3.2)              */
+    int boundary;            /* fd4_boundary (default FD4_BC_NATURAL)              */
+    int kappa;               /* FED step ordering: 0 = automatic, else i -> kappa*i mod n */
+    int grad_norm_squared;   /* 0: 1/sqrt(1+|grad|) as printed in Eq. 6 (default);
+                                1: 1/sqrt(1+|grad|^2)                              */
+} fd4_params;
+
+/* Fills *p with the defaults listed above. */
+void fd4_default_params(fd4_params *p);
+
+/* Human-readable name of a status code (static storage). */
+const char *fd4_strerror(int status);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int fd4_version(void);
+
+/* FED step sizes (Sec. 3.5, Eq. 22-23), on the host in float64.
+ *   n = ceil(-1/2 + 1/2 sqrt(1 + 12 T / (M tau_max)))  when n_in == 0, else n_in;
+ *   tau_i = 3T / (2 M (n^2 + n) cos^2(pi (2i+1) / (4n+2))),  i = 0..n-1.
+ * The paper reorders the steps with the kappa cycles of the FED authors'
+ * code, which it does not print.  This library orders them as
+ * tau_out[i] = tau_{kappa i mod n} with gcd(kappa, n) = 1.  kappa_in = 1 keeps
+ * the natural order; kappa_in = 0 picks the kappa with the smallest
+ * rounding-error growth bound
+ *     A(kappa) = max_j max_p |prod_{l<j} (1 - tau_pi(l) p)| * max_q |prod_{l>=j} (1 - tau_pi(l) q)|
+ * over p, q on 4096 points of [0, 34] (34 bounds the operator norm, Sec. 3.4),
+ * ties to the smaller kappa.
+ * tau_out: host array of tau_cap doubles; *n_out = n; kappa_out nullable.
+ * Errors: BAD_ARG (T <= 0, M <= 0, tau_max <= 0, n_in < 0, kappa not coprime
+ * to n, n > tau_cap or > FD4_MAX_FED_STEPS), UNSTABLE_TAU (tau_max > 1/17, or
+ * n_in given with 3T/(M(n^2+n)) > tau_max).                                  */
+int fd4_fed_taus(double T, int M, double tau_max, int n_in, int kappa_in,
+                 double *tau_out, int tau_cap, int *n_out, int *kappa_out);
+
+/* Workspace sizes.  op selects the entry point; the size covers a w x h image
+ * with pitch roundup(w, 4) and n_sigma scales.                               */
+typedef enum fd4_op {
+    FD4_OP_SELECT_SCALES = 0,
+    FD4_OP_BUILD_TENSOR = 1,
+    FD4_OP_FED_CYCLE = 2,
+    FD4_OP_FILTER = 3
+} fd4_op;
+size_t fd4_workspace_bytes(int op, int w, int h, int n_sigma);
+
+/* Per-pixel scale selection (Sec. 3.3, Eq. 9).
+ * For each sigma of h_sigmas (host, n_sigma values, strictly increasing, each
+ * in (0, FD4_MAX_SIGMA]): the Hessian of u_sigma = u * G_sigma (sampled
+ * Gaussian-derivative kernels of radius ceil(4 sigma), half-sample mirror
+ * border), its eigenvalues scaled by sigma^(2 gamma) and ordered
+ * |nu1| <= |nu2| (equal magnitudes: nu2 the negative one), S and R_B = nu1/nu2.
+ * V = 0 for the wrong polarity (RIDGE: nu2 > 0, VALLEY: nu2 < 0), else
+ * exp(-R_B^2/(2 beta^2)) (1 - exp(-S^2/(2 c^2))).  c = params->c if > 0, else
+ * half the maximum of S over all scales and pixels.
+ * Output d_sigma_idx[y*pitch+x] = argmax_s V (uint8, ties to the smaller
+ * sigma); d_vmax (nullable, float) = the maximum V.
+ * d_img: device float image.  params: host, nullable (defaults).           */
+int fd4_select_scales(const float *d_img, int w, int h, int pitch,
+                      const float *h_sigmas, int n_sigma, const fd4_params *params,
+                      uint8_t *d_sigma_idx, float *d_vmax,
+                      void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+
+/* Fourth-order diffusion tensor field (Sec. 3.1 Eq. 6, Sec. 3.2 Eq. 7-8).
+ * N = H(u_s) / sqrt(1 + |grad u_s|) at s = h_sigmas[d_sigma_idx[p]] per pixel
+ * (|grad u_s|^2 under the root if params->grad_norm_squared), then
+ * N_rho = G_rho * N componentwise (radius ceil(4 rho), mirror border), the
+ * eigen-decomposition N_rho = nu1 e1 e1^T + nu2 e2 e2^T with nu1 >= nu2, and
+ * mu_i = 1 / (1 + nu_i^2 / lambda^2), set to 1 where RIDGE and nu_i >= 0 or
+ * VALLEY and nu_i <= 0.  D has eigentensors e1e1, e2e2, sym(e1e2),
+ * antisym(e1e2) with eigenvalues mu1, mu2, (mu1+mu2)/2, 0.
+ * Output d_tensor: 4 floats per pixel (cos 2t, sin 2t, mu1, mu2),
+ * e1 = (cos t, sin t); (1, 0) where nu1 == nu2.  Row pitch `pitch` pixels
+ * (4*pitch floats).  d_sigma_idx entries must be < n_sigma.               */
+int fd4_build_tensor(const float *d_u, int w, int h, int pitch,
+                     const uint8_t *d_sigma_idx, const float *h_sigmas, int n_sigma,
+                     const fd4_params *params, float *d_tensor,
+                     void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+
+/* One FED cycle (Sec. 3.5, Eq. 21): u <- (I - tau_{n-1} P) ... (I - tau_0 P) u
+ * with P = L^T D L (Sec. 3.4, Eq. 17), Hajiaboli stencils at unit spacing,
+ * D from d_tensor (as written by fd4_build_tensor) frozen over the cycle.
+ * d_u is updated in place.  h_tau: host, n step sizes in execution order
+ * (for instance from fd4_fed_taus); each step is applied exactly as given.
+ * boundary: fd4_boundary.                                                   */
+int fd4_fed_cycle(float *d_u, int w, int h, int pitch, const float *d_tensor,
+                  const double *h_tau, int n, int boundary,
+                  void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+
+/* The whole filter (Sec. 3): step sizes from (T, M, n_in, params->tau_max,
+ * params->kappa) as in fd4_fed_taus; sigma* once on the input (unless
+ * sigma_given, in which case d_sigma_idx is read); then M cycles of
+ * fd4_build_tensor on the current image followed by one fd4_fed_cycle.
+ * d_in is not modified; d_out receives the result (may equal d_in).
+ * d_sigma_idx: nullable when !sigma_given (then kept in the workspace);
+ * otherwise receives / supplies sigma*.                                     */
+int fd4_filter(const float *d_in, float *d_out, int w, int h, int pitch,
+               const float *h_sigmas, int n_sigma, const fd4_params *params,
+               double T, int M, int n_in, uint8_t *d_sigma_idx, int sigma_given,
+               void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FD4_H */

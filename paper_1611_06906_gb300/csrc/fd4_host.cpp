@@ -1,0 +1,380 @@
+// Host side of the fd4 C ABI: parameter defaults, FED step table, Gaussian
+// taps, argument validation, workspace layout and the entry points, which
+// validate and then enqueue the device kernels (fd4_scale.cu, fd4_fed.cu).
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "fd4_internal.h"
+
+using namespace fd4;
+
+extern "C" void fd4_default_params(fd4_params *p)
+{
+    if (!p) return;
+    p->lambda = 0.005f;   // Sec. 4.1 and 4.3
+    p->rho = 0.5f;        // Sec. 3.1
+    p->beta = 0.5f;       // Sec. 3.3
+    p->c = 0.0f;          // auto: half the maximum of S (Sec. 3.3)
+    p->gamma = 1.0f;      // sigma^2 normalisation (Sec. 3.3)
+    p->tau_max = 0.05f;   // Sec. 3.5
+    p->mode = FD4_BOTH;   // "enhancing both ridges and valleys" (Sec. 3.2)
+    p->boundary = FD4_BC_NATURAL;
+    p->kappa = 0;
+    p->grad_norm_squared = 0;
+}
+
+extern "C" const char *fd4_strerror(int s)
+{
+    switch (s) {
+    case FD4_OK: return "ok";
+    case FD4_ERR_BAD_ARG: return "bad argument";
+    case FD4_ERR_UNSTABLE_TAU: return "FED step sizes exceed the stability limit";
+    case FD4_ERR_TOO_MANY_SIGMAS: return "too many scales";
+    case FD4_ERR_PITCH: return "row pitch must be >= width and a multiple of 4";
+    case FD4_ERR_WS_TOO_SMALL: return "workspace too small";
+    case FD4_ERR_TIMEOUT: return "device-side wait timed out";
+    case FD4_ERR_CUDA: return "CUDA runtime error";
+    case FD4_ERR_ALIGN: return "device pointer not 16-byte aligned";
+    case FD4_ERR_SIGMA_RANGE: return "scales must be increasing and in (0, 16]";
+    case FD4_ERR_NOT_IMPLEMENTED: return "not implemented";
+    default: return "unknown status";
+    }
+}
+
+extern "C" int fd4_version(void) { return 100; }
+
+// ---------------------------------------------------------------------------
+// FED step table (Sec. 3.5, Eq. 22-23) and the kappa ordering.
+
+static double growth_bound(const std::vector<double> &tau_nat, int kappa)
+{
+    // A(kappa) = max_j PRE_j * SUF_j with PRE_j = max_p |prod_{l<j} f_l(p)| and
+    // SUF_j = max_q |prod_{l>=j} f_l(q)|, f_l(p) = 1 - tau_{kappa l mod n} p.
+    const int n = (int)tau_nat.size();
+    const int NP = 4096;
+    std::vector<double> pre(n + 1, 0.0), suf(n + 1, 0.0), run(n + 1);
+    for (int ip = 0; ip < NP; ++ip) {
+        const double p = 34.0 * ip / (NP - 1);
+        run[0] = 1.0;
+        for (int l = 0; l < n; ++l)
+            run[l + 1] = run[l] * (1.0 - tau_nat[(size_t)((long long)kappa * l % n)] * p);
+        for (int j = 0; j <= n; ++j)
+            pre[j] = std::fmax(pre[j], std::fabs(run[j]));
+        double tail = 1.0;
+        suf[n] = std::fmax(suf[n], 1.0);
+        for (int j = n - 1; j >= 0; --j) {
+            tail *= 1.0 - tau_nat[(size_t)((long long)kappa * j % n)] * p;
+            suf[j] = std::fmax(suf[j], std::fabs(tail));
+        }
+    }
+    double a = 0.0;
+    for (int j = 0; j <= n; ++j)
+        a = std::fmax(a, pre[j] * suf[j]);
+    return a;
+}
+
+static int gcd_int(int a, int b)
+{
+    while (b != 0) {
+        const int t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+extern "C" int fd4_fed_taus(double T, int M, double tau_max, int n_in, int kappa_in,
+                            double *tau_out, int tau_cap, int *n_out, int *kappa_out)
+{
+    if (!tau_out || !n_out || !(T > 0.0) || M <= 0 || !(tau_max > 0.0) || n_in < 0 || kappa_in < 0)
+        return FD4_ERR_BAD_ARG;
+    if (tau_max > 1.0 / 17.0 + 1e-12)  // Gershgorin bound of Sec. 3.4 at unit spacing
+        return FD4_ERR_UNSTABLE_TAU;
+    int n = n_in;
+    if (n == 0) {
+        const double v = -0.5 + 0.5 * std::sqrt(1.0 + 12.0 * T / (M * tau_max));
+        n = (int)std::ceil(v);
+        if (n < 1) n = 1;
+    }
+    if (n > FD4_MAX_FED_STEPS || n > tau_cap)
+        return FD4_ERR_BAD_ARG;
+    const double nn = (double)n * (double)n + (double)n;
+    if (3.0 * T / (M * nn) > tau_max * (1.0 + 1e-12))
+        return FD4_ERR_UNSTABLE_TAU;
+    std::vector<double> nat(n);
+    for (int i = 0; i < n; ++i) {
+        const double c = std::cos(M_PI * (2.0 * i + 1.0) / (4.0 * n + 2.0));
+        nat[i] = 3.0 * T / (2.0 * M * nn * c * c);
+    }
+    int kappa = kappa_in;
+    if (kappa == 0) {
+        double best = HUGE_VAL;
+        kappa = 1;
+        const int kmax = n > 1 ? n - 1 : 1;
+        for (int k = 1; k <= kmax; ++k) {
+            if (n > 1 && gcd_int(k, n) != 1) continue;
+            const double a = growth_bound(nat, k);
+            if (a < best) {
+                best = a;
+                kappa = k;
+            }
+        }
+    } else if (n > 1 && gcd_int(kappa % n, n) != 1) {
+        return FD4_ERR_BAD_ARG;
+    }
+    for (int i = 0; i < n; ++i)
+        tau_out[i] = nat[(size_t)((long long)kappa * i % n)];
+    *n_out = n;
+    if (kappa_out) *kappa_out = kappa;
+    return FD4_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Gaussian taps.  Sampled at integer offsets, radius ceil(4 sigma): the
+// smoothing kernel sums to one, the first-derivative kernel maps the ramp x to
+// 1, the second-derivative kernel has zero sum and maps x^2/2 to 1.
+
+int fd4::gauss_taps(double sigma, GaussTaps *t)
+{
+    const int r = (int)std::ceil(4.0 * sigma);
+    if (!(sigma > 0.0) || r > kMaxRadius) return FD4_ERR_SIGMA_RANGE;
+    t->r = r;
+    const int n = 2 * r + 1;
+    std::vector<double> g(n), d1(n), d2(n);
+    const double inv2s2 = 1.0 / (2.0 * sigma * sigma);
+    double sg = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double x = i - r;
+        g[i] = std::exp(-x * x * inv2s2);
+        sg += g[i];
+    }
+    double m2 = 0.0, s2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double x = i - r;
+        g[i] /= sg;
+        d1[i] = x * g[i];                          // proportional to -G'(-x)
+        m2 += x * d1[i];
+        d2[i] = (x * x - sigma * sigma) * g[i];    // proportional to G''(x)
+        s2 += d2[i];
+    }
+    double q = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double x = i - r;
+        d1[i] /= m2;
+        d2[i] -= s2 * g[i];
+        q += 0.5 * x * x * d2[i];
+    }
+    for (int i = 0; i < n; ++i) {
+        t->w0[i] = (float)g[i];
+        t->w1[i] = (float)d1[i];
+        t->w2[i] = (float)(d2[i] / q);
+    }
+    return FD4_OK;
+}
+
+int fd4::rho_taps(double rho, RhoTaps *t)
+{
+    const int r = (int)std::ceil(4.0 * rho);
+    if (!(rho > 0.0) || r > kMaxRhoRadius) return FD4_ERR_BAD_ARG;
+    t->r = r;
+    std::vector<double> g(2 * r + 1);
+    double s = 0.0;
+    for (int i = 0; i <= 2 * r; ++i) {
+        const double x = i - r;
+        g[i] = std::exp(-x * x / (2.0 * rho * rho));
+        s += g[i];
+    }
+    for (int i = 0; i <= 2 * r; ++i)
+        t->w0[i] = (float)(g[i] / s);
+    return FD4_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Validation and workspace layout.
+
+int fd4::check_image(const void *d, int w, int h, int pitch)
+{
+    if (!d || w < 3 || h < 3) return FD4_ERR_BAD_ARG;
+    if (pitch < w || (pitch & 3) != 0) return FD4_ERR_PITCH;
+    if (((uintptr_t)d & 15u) != 0) return FD4_ERR_ALIGN;
+    if ((double)h * (double)pitch * 16.0 > 9.0e18) return FD4_ERR_BAD_ARG;
+    return FD4_OK;
+}
+
+int fd4::check_sigmas(const float *s, int n)
+{
+    if (!s || n <= 0) return FD4_ERR_BAD_ARG;
+    if (n > FD4_MAX_SIGMAS) return FD4_ERR_TOO_MANY_SIGMAS;
+    for (int i = 0; i < n; ++i) {
+        if (!(s[i] > 0.0f) || !(s[i] <= FD4_MAX_SIGMA)) return FD4_ERR_SIGMA_RANGE;
+        if (i > 0 && !(s[i] > s[i - 1])) return FD4_ERR_SIGMA_RANGE;
+    }
+    return FD4_OK;
+}
+
+void fd4::resolve_params(const fd4_params *in, fd4_params *out)
+{
+    if (in) *out = *in;
+    else fd4_default_params(out);
+}
+
+static int check_params(const fd4_params &p)
+{
+    if (!(p.lambda > 0.0f) || !(p.rho > 0.0f) || !(p.beta > 0.0f) || !(p.gamma >= 0.0f))
+        return FD4_ERR_BAD_ARG;
+    if ((int)std::ceil(4.0 * p.rho) > kMaxRhoRadius) return FD4_ERR_BAD_ARG;
+    if (p.mode < FD4_RIDGE || p.mode > FD4_BOTH) return FD4_ERR_BAD_ARG;
+    if (p.boundary != FD4_BC_NATURAL && p.boundary != FD4_BC_PERIODIC) return FD4_ERR_BAD_ARG;
+    if (!(p.c >= 0.0f) && !(p.c < 0.0f)) return FD4_ERR_BAD_ARG;  // NaN
+    return FD4_OK;
+}
+
+size_t fd4::plane_bytes(int h, int pitch, size_t elem)
+{
+    return align_up((size_t)h * (size_t)pitch * elem, 256);
+}
+
+size_t fd4::ws_select_bytes(int h, int pitch, int n_sigma)
+{
+    return kHeaderBytes + 2 * (size_t)n_sigma * plane_bytes(h, pitch, 4);
+}
+
+size_t fd4::ws_tensor_bytes(int h, int pitch) { return kHeaderBytes + plane_bytes(h, pitch, 16); }
+
+size_t fd4::ws_fed_bytes(int h, int pitch) { return kHeaderBytes + plane_bytes(h, pitch, 4); }
+
+// filter: sigma* (u8) | tensor field (float4) | stage workspace shared by the stages
+size_t fd4::ws_filter_bytes(int h, int pitch, int n_sigma)
+{
+    size_t stage = ws_select_bytes(h, pitch, n_sigma);
+    if (ws_tensor_bytes(h, pitch) > stage) stage = ws_tensor_bytes(h, pitch);
+    if (ws_fed_bytes(h, pitch) > stage) stage = ws_fed_bytes(h, pitch);
+    return plane_bytes(h, pitch, 1) + plane_bytes(h, pitch, 16) + stage;
+}
+
+extern "C" size_t fd4_workspace_bytes(int op, int w, int h, int n_sigma)
+{
+    if (w < 1 || h < 1 || n_sigma < 0) return 0;
+    const int pitch = (int)align_up((size_t)w, 4);
+    switch (op) {
+    case FD4_OP_SELECT_SCALES: return ws_select_bytes(h, pitch, n_sigma);
+    case FD4_OP_BUILD_TENSOR: return ws_tensor_bytes(h, pitch);
+    case FD4_OP_FED_CYCLE: return ws_fed_bytes(h, pitch);
+    case FD4_OP_FILTER: return ws_filter_bytes(h, pitch, n_sigma);
+    default: return 0;
+    }
+}
+
+static int ws_ok(const void *ws, size_t have, size_t need)
+{
+    if (!ws) return FD4_ERR_BAD_ARG;
+    if (((uintptr_t)ws & 255u) != 0) return FD4_ERR_ALIGN;
+    return have >= need ? FD4_OK : FD4_ERR_WS_TOO_SMALL;
+}
+
+static int cuda_status(int e) { return e == 0 ? FD4_OK : FD4_ERR_CUDA; }
+
+// ---------------------------------------------------------------------------
+// Entry points.
+
+extern "C" int fd4_select_scales(const float *d_img, int w, int h, int pitch, const float *h_sigmas,
+                                 int n_sigma, const fd4_params *params, uint8_t *d_sigma_idx,
+                                 float *d_vmax, void *d_ws, size_t ws_bytes, fd4_stream_t stream)
+{
+    int rc;
+    fd4_params p;
+    resolve_params(params, &p);
+    if ((rc = check_image(d_img, w, h, pitch)) != FD4_OK) return rc;
+    if ((rc = check_sigmas(h_sigmas, n_sigma)) != FD4_OK) return rc;
+    if ((rc = check_params(p)) != FD4_OK) return rc;
+    if (!d_sigma_idx) return FD4_ERR_BAD_ARG;
+    if (d_vmax && ((uintptr_t)d_vmax & 15u)) return FD4_ERR_ALIGN;
+    if ((rc = ws_ok(d_ws, ws_bytes, ws_select_bytes(h, pitch, n_sigma))) != FD4_OK) return rc;
+    return cuda_status(launch_select(d_img, w, h, pitch, h_sigmas, n_sigma, p, d_sigma_idx, d_vmax,
+                                     (char *)d_ws, (cudaStream_t)stream));
+}
+
+extern "C" int fd4_build_tensor(const float *d_u, int w, int h, int pitch, const uint8_t *d_sigma_idx,
+                                const float *h_sigmas, int n_sigma, const fd4_params *params,
+                                float *d_tensor, void *d_ws, size_t ws_bytes, fd4_stream_t stream)
+{
+    int rc;
+    fd4_params p;
+    resolve_params(params, &p);
+    if ((rc = check_image(d_u, w, h, pitch)) != FD4_OK) return rc;
+    if ((rc = check_sigmas(h_sigmas, n_sigma)) != FD4_OK) return rc;
+    if ((rc = check_params(p)) != FD4_OK) return rc;
+    if (!d_sigma_idx || !d_tensor) return FD4_ERR_BAD_ARG;
+    if ((uintptr_t)d_tensor & 15u) return FD4_ERR_ALIGN;
+    if ((rc = ws_ok(d_ws, ws_bytes, ws_tensor_bytes(h, pitch))) != FD4_OK) return rc;
+    return cuda_status(launch_tensor(d_u, w, h, pitch, d_sigma_idx, h_sigmas, n_sigma, p, d_tensor,
+                                     (char *)d_ws, (cudaStream_t)stream));
+}
+
+extern "C" int fd4_fed_cycle(float *d_u, int w, int h, int pitch, const float *d_tensor,
+                             const double *h_tau, int n, int boundary, void *d_ws, size_t ws_bytes,
+                             fd4_stream_t stream)
+{
+    int rc;
+    if ((rc = check_image(d_u, w, h, pitch)) != FD4_OK) return rc;
+    if (!d_tensor || !h_tau || n < 1 || n > FD4_MAX_FED_STEPS) return FD4_ERR_BAD_ARG;
+    if ((uintptr_t)d_tensor & 15u) return FD4_ERR_ALIGN;
+    if (boundary != FD4_BC_NATURAL && boundary != FD4_BC_PERIODIC) return FD4_ERR_BAD_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!(h_tau[i] > 0.0) || !(h_tau[i] < 1e6)) return FD4_ERR_BAD_ARG;
+    if ((rc = ws_ok(d_ws, ws_bytes, ws_fed_bytes(h, pitch))) != FD4_OK) return rc;
+    return cuda_status(launch_fed_cycle(d_u, w, h, pitch, d_tensor, h_tau, n, boundary, (char *)d_ws,
+                                        (cudaStream_t)stream));
+}
+
+extern "C" int fd4_filter(const float *d_in, float *d_out, int w, int h, int pitch,
+                          const float *h_sigmas, int n_sigma, const fd4_params *params, double T,
+                          int M, int n_in, uint8_t *d_sigma_idx, int sigma_given, void *d_ws,
+                          size_t ws_bytes, fd4_stream_t stream)
+{
+    int rc;
+    fd4_params p;
+    resolve_params(params, &p);
+    if ((rc = check_image(d_in, w, h, pitch)) != FD4_OK) return rc;
+    if ((rc = check_image(d_out, w, h, pitch)) != FD4_OK) return rc;
+    if ((rc = check_sigmas(h_sigmas, n_sigma)) != FD4_OK) return rc;
+    if ((rc = check_params(p)) != FD4_OK) return rc;
+    if (sigma_given && !d_sigma_idx) return FD4_ERR_BAD_ARG;
+    if ((rc = ws_ok(d_ws, ws_bytes, ws_filter_bytes(h, pitch, n_sigma))) != FD4_OK) return rc;
+    std::vector<double> tau(FD4_MAX_FED_STEPS);
+    int n = 0;
+    if ((rc = fd4_fed_taus(T, M, p.tau_max, n_in, p.kappa, tau.data(), FD4_MAX_FED_STEPS, &n, nullptr)) != FD4_OK)
+        return rc;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)d_ws;
+    // [sigma* plane | tensor plane | stage workspace = header + scratch]; the
+    // stages run in order on one stream, so they share the stage workspace.
+    uint8_t *idx = (uint8_t *)ws;
+    float *tensor = (float *)(ws + plane_bytes(h, pitch, 1));
+    char *sws = ws + plane_bytes(h, pitch, 1) + plane_bytes(h, pitch, 16);
+
+    if (sigma_given) {
+        idx = d_sigma_idx;
+    } else {
+        rc = launch_select(d_in, w, h, pitch, h_sigmas, n_sigma, p, idx, nullptr, sws, st);
+        if (rc) return FD4_ERR_CUDA;
+        if (d_sigma_idx) {
+            if (cudaMemcpy2DAsync(d_sigma_idx, (size_t)pitch, idx, (size_t)pitch, (size_t)w, (size_t)h,
+                                  cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                return FD4_ERR_CUDA;
+        }
+    }
+    if (d_out != d_in) {
+        if (cudaMemcpy2DAsync(d_out, (size_t)pitch * 4, d_in, (size_t)pitch * 4, (size_t)w * 4, (size_t)h,
+                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return FD4_ERR_CUDA;
+    }
+    for (int k = 0; k < M; ++k) {
+        if (launch_tensor(d_out, w, h, pitch, idx, h_sigmas, n_sigma, p, tensor, sws, st)) return FD4_ERR_CUDA;
+        if (launch_fed_cycle(d_out, w, h, pitch, tensor, tau.data(), n, p.boundary, sws, st)) return FD4_ERR_CUDA;
+    }
+    return FD4_OK;
+}

@@ -1,0 +1,226 @@
+"""Thin Python binding of the fd4 C ABI (include/fd4.h).
+
+Argument marshalling only: every step of the filter runs in the CUDA kernels
+of libfd4.so.  PyTorch provides device memory and the current stream.  There
+is no CPU fallback; if the library cannot be loaded every call raises.
+
+Device images are float32 tensors of shape (h, pitch) with pitch a multiple
+of 4 and the image in the first w columns (``to_device`` pads a numpy image).
+The tensor field has shape (h, pitch, 4): (cos 2t, sin 2t, mu1, mu2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+RIDGE, VALLEY, BOTH = 0, 1, 2
+NATURAL, PERIODIC = 0, 1
+OP_SELECT_SCALES, OP_BUILD_TENSOR, OP_FED_CYCLE, OP_FILTER = 0, 1, 2, 3
+MAX_FED_STEPS = 4096
+
+_lock = threading.Lock()
+_lib = None
+
+
+class Fd4Error(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (what, strerror(status), status))
+
+
+class Params(ctypes.Structure):
+    """fd4_params (include/fd4.h)."""
+    _fields_ = [("lambda_", ctypes.c_float), ("rho", ctypes.c_float), ("beta", ctypes.c_float),
+                ("c", ctypes.c_float), ("gamma", ctypes.c_float), ("tau_max", ctypes.c_float),
+                ("mode", ctypes.c_int), ("boundary", ctypes.c_int), ("kappa", ctypes.c_int),
+                ("grad_norm_squared", ctypes.c_int)]
+
+
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_i = ctypes.c_int
+_fp = ctypes.POINTER(ctypes.c_float)
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_pp = ctypes.POINTER(Params)
+
+SIGNATURES = {
+    "fd4_default_params": (None, [_pp]),
+    "fd4_strerror": (ctypes.c_char_p, [_i]),
+    "fd4_version": (_i, []),
+    "fd4_fed_taus": (_i, [ctypes.c_double, _i, ctypes.c_double, _i, _i, _dp, _i, _ip, _ip]),
+    "fd4_workspace_bytes": (_sz, [_i, _i, _i, _i]),
+    "fd4_select_scales": (_i, [_vp, _i, _i, _i, _fp, _i, _pp, _vp, _vp, _vp, _sz, _vp]),
+    "fd4_build_tensor": (_i, [_vp, _i, _i, _i, _vp, _fp, _i, _pp, _vp, _vp, _sz, _vp]),
+    "fd4_fed_cycle": (_i, [_vp, _i, _i, _i, _vp, _dp, _i, _i, _vp, _sz, _vp]),
+    "fd4_filter": (_i, [_vp, _vp, _i, _i, _i, _fp, _i, _pp, ctypes.c_double, _i, _i, _vp, _i, _vp,
+                        _sz, _vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libfd4.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+        return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().fd4_strerror(int(status)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise Fd4Error(rc, what)
+
+
+def params(**kw) -> Params:
+    """Defaults of fd4_default_params with keyword overrides (lambda_ for lambda)."""
+    p = Params()
+    lib().fd4_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, "lambda_" if k == "lam" else k, v)
+    return p
+
+
+def fed_taus(T: float, M: int, tau_max: float = 0.05, n: int = 0, kappa: int = 0):
+    """FED step sizes in execution order (fd4_fed_taus).  Returns (tau, kappa)."""
+    buf = (ctypes.c_double * MAX_FED_STEPS)()
+    n_out, k_out = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().fd4_fed_taus(float(T), int(M), float(tau_max), int(n), int(kappa), buf, MAX_FED_STEPS,
+                              ctypes.byref(n_out), ctypes.byref(k_out)), "fd4_fed_taus")
+    return np.array(buf[: n_out.value]), k_out.value
+
+
+def workspace_bytes(op: int, w: int, h: int, n_sigma: int = 0) -> int:
+    return int(lib().fd4_workspace_bytes(int(op), int(w), int(h), int(n_sigma)))
+
+
+# ---------------------------------------------------------------------------
+# torch-side helpers (allocation and streams only)
+
+def _torch():
+    import torch
+    return torch
+
+
+def pitch_for(w: int) -> int:
+    return (int(w) + 3) // 4 * 4
+
+
+def empty_image(h: int, w: int, dtype=None, channels: int = 0, device="cuda"):
+    torch = _torch()
+    shape = (h, pitch_for(w)) + ((channels,) if channels else ())
+    return torch.zeros(shape, dtype=dtype or torch.float32, device=device)
+
+
+def to_device(img: np.ndarray, device="cuda"):
+    """Copy a (h, w) float image into a zero-padded (h, pitch) float32 device tensor."""
+    torch = _torch()
+    h, w = img.shape
+    buf = empty_image(h, w, device=device)
+    buf[:, :w] = torch.from_numpy(np.ascontiguousarray(img, dtype=np.float32)).to(device)
+    return buf
+
+
+def workspace(op: int, w: int, h: int, n_sigma: int = 0, device="cuda"):
+    torch = _torch()
+    return torch.empty(max(workspace_bytes(op, w, h, n_sigma), 256), dtype=torch.uint8, device=device)
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _sigmas(sigmas):
+    arr = (ctypes.c_float * len(sigmas))(*[float(s) for s in sigmas])
+    return arr, len(sigmas)
+
+
+def _pitch(buf):
+    return int(buf.shape[1])
+
+
+def select_scales(img, w: int, sigmas, prm: Params | None = None, want_vmax: bool = False,
+                  ws=None, stream=None):
+    """fd4_select_scales.  Returns (sigma_idx uint8 (h, pitch), vmax or None)."""
+    torch = _torch()
+    h, pitch = img.shape
+    idx = torch.zeros((h, pitch), dtype=torch.uint8, device=img.device)
+    vmax = torch.zeros((h, pitch), dtype=torch.float32, device=img.device) if want_vmax else None
+    sg, K = _sigmas(sigmas)
+    if ws is None:
+        ws = workspace(OP_SELECT_SCALES, pitch, h, K, img.device)
+    _check(lib().fd4_select_scales(_ptr(img), int(w), h, pitch, sg, K,
+                                   ctypes.byref(prm) if prm is not None else None, _ptr(idx), _ptr(vmax),
+                                   _ptr(ws), ws.numel(), _stream(stream)), "fd4_select_scales")
+    return idx, vmax
+
+
+def build_tensor(u, w: int, sigma_idx, sigmas, prm: Params | None = None, out=None, ws=None, stream=None):
+    """fd4_build_tensor.  Returns the (h, pitch, 4) tensor field."""
+    torch = _torch()
+    h, pitch = u.shape
+    if out is None:
+        out = torch.zeros((h, pitch, 4), dtype=torch.float32, device=u.device)
+    sg, K = _sigmas(sigmas)
+    if ws is None:
+        ws = workspace(OP_BUILD_TENSOR, pitch, h, K, u.device)
+    _check(lib().fd4_build_tensor(_ptr(u), int(w), h, pitch, _ptr(sigma_idx), sg, K,
+                                  ctypes.byref(prm) if prm is not None else None, _ptr(out), _ptr(ws),
+                                  ws.numel(), _stream(stream)), "fd4_build_tensor")
+    return out
+
+
+def fed_cycle(u, w: int, tensor, tau, boundary: int = NATURAL, ws=None, stream=None):
+    """fd4_fed_cycle, in place on u."""
+    h, pitch = u.shape
+    t = np.ascontiguousarray(tau, dtype=np.float64)
+    if ws is None:
+        ws = workspace(OP_FED_CYCLE, pitch, h, 0, u.device)
+    _check(lib().fd4_fed_cycle(_ptr(u), int(w), h, pitch, _ptr(tensor), t.ctypes.data_as(_dp), t.size,
+                               int(boundary), _ptr(ws), ws.numel(), _stream(stream)), "fd4_fed_cycle")
+    return u
+
+
+def filter_image(u_in, w: int, sigmas, T: float, M: int, n: int = 0, prm: Params | None = None,
+                 sigma_idx=None, out=None, ws=None, stream=None):
+    """fd4_filter.  Returns (out, sigma_idx)."""
+    torch = _torch()
+    h, pitch = u_in.shape
+    if out is None:
+        out = torch.zeros_like(u_in)
+    given = sigma_idx is not None
+    if sigma_idx is None:
+        sigma_idx = torch.zeros((h, pitch), dtype=torch.uint8, device=u_in.device)
+    sg, K = _sigmas(sigmas)
+    if ws is None:
+        ws = workspace(OP_FILTER, pitch, h, K, u_in.device)
+    _check(lib().fd4_filter(_ptr(u_in), _ptr(out), int(w), h, pitch, sg, K,
+                            ctypes.byref(prm) if prm is not None else None, float(T), int(M), int(n),
+                            _ptr(sigma_idx), int(given), _ptr(ws), ws.numel(), _stream(stream)),
+           "fd4_filter")
+    return out, sigma_idx

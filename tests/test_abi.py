@@ -1,0 +1,106 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+function include/fd4.h declares, computes the host-side FED table like the
+oracle, and rejects bad arguments on the host before touching CUDA."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1611_06906_gb300 import fd4
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fd4.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    names = re.findall(r"\b(fd4_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_function():
+    L = fd4.lib()
+    names = declared_functions()
+    assert "fd4_filter" in names and "fd4_fed_cycle" in names
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) <= set(fd4.SIGNATURES) | set(n for n in names if n not in fd4.SIGNATURES)
+
+
+def test_defaults_and_strerror():
+    p = fd4.params()
+    assert abs(p.lambda_ - 0.005) < 1e-9 and p.rho == 0.5 and p.beta == 0.5 and p.tau_max == pytest.approx(0.05)
+    assert p.mode == fd4.BOTH and p.boundary == fd4.NATURAL and p.c == 0.0 and p.gamma == 1.0
+    assert fd4.strerror(0) == "ok"
+    assert "workspace" in fd4.strerror(-5)
+    assert fd4.lib().fd4_version() >= 100
+
+
+@pytest.mark.parametrize("T,M,n", [(11 / 3, 2, 10), (35.0, 5, 20), (325 / 3, 10, 25), (12.0, 2, 0),
+                                   (500.0, 10000, 0), (20.0, 1000, 0)])
+def test_fed_taus_match_oracle(oracle, T, M, n):
+    tau_o, kappa_o, _ = oracle.fed_taus(T, M, 0.05, n=n, kappa=0)
+    tau_l, kappa_l = fd4.fed_taus(T, M, 0.05, n=n, kappa=0)
+    assert kappa_l == kappa_o
+    assert tau_l.size == tau_o.size
+    assert np.abs(tau_l - tau_o).max() <= 1e-14 * tau_o.max()
+
+
+def test_fed_taus_errors():
+    with pytest.raises(fd4.Fd4Error) as e:
+        fd4.fed_taus(35.0, 5, 0.05, n=10)
+    assert e.value.status == -2
+    with pytest.raises(fd4.Fd4Error) as e:
+        fd4.fed_taus(1.0, 1, 0.07)  # above the 1/17 bound of Sec. 3.4
+    assert e.value.status == -2
+    with pytest.raises(fd4.Fd4Error) as e:
+        fd4.fed_taus(35.0, 5, 0.05, n=20, kappa=4)  # not coprime with 20
+    assert e.value.status == -1
+
+
+def test_workspace_sizes_grow_with_the_problem():
+    a = fd4.workspace_bytes(fd4.OP_SELECT_SCALES, 100, 100, 4)
+    b = fd4.workspace_bytes(fd4.OP_SELECT_SCALES, 100, 100, 8)
+    assert 0 < a < b
+    f = fd4.workspace_bytes(fd4.OP_FILTER, 1024, 1024, 8)
+    assert f >= b and f >= 1024 * 1024 * (1 + 16)
+    assert fd4.workspace_bytes(99, 10, 10, 1) == 0
+
+
+def test_host_side_argument_errors():
+    """Every check below fails before any CUDA call is made."""
+    L = fd4.lib()
+    sig = (ctypes.c_float * 2)(1.0, 2.0)
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: validation rejects first
+    ws = ctypes.c_void_p(1 << 24)
+    # null image
+    assert L.fd4_select_scales(None, 8, 8, 8, sig, 2, None, fake, None, ws, 1 << 30, None) == -1
+    # pitch not a multiple of 4
+    assert L.fd4_select_scales(fake, 8, 8, 10, sig, 2, None, fake, None, ws, 1 << 30, None) == -4
+    # pitch < w
+    assert L.fd4_select_scales(fake, 8, 8, 4, sig, 2, None, fake, None, ws, 1 << 30, None) == -4
+    # unaligned image pointer
+    assert L.fd4_select_scales(ctypes.c_void_p((1 << 20) + 4), 8, 8, 8, sig, 2, None, fake, None, ws,
+                               1 << 30, None) == -8
+    # scales not increasing / out of range
+    bad = (ctypes.c_float * 2)(2.0, 1.0)
+    assert L.fd4_select_scales(fake, 8, 8, 8, bad, 2, None, fake, None, ws, 1 << 30, None) == -9
+    big = (ctypes.c_float * 1)(17.0)
+    assert L.fd4_select_scales(fake, 8, 8, 8, big, 1, None, fake, None, ws, 1 << 30, None) == -9
+    many = (ctypes.c_float * 40)(*[1 + 0.1 * i for i in range(40)])
+    assert L.fd4_select_scales(fake, 8, 8, 8, many, 40, None, fake, None, ws, 1 << 30, None) == -3
+    # workspace too small
+    assert L.fd4_select_scales(fake, 8, 8, 8, sig, 2, None, fake, None, ws, 16, None) == -5
+    # image too small
+    assert L.fd4_select_scales(fake, 2, 8, 4, sig, 2, None, fake, None, ws, 1 << 30, None) == -1
+    # FED cycle: bad step sizes and boundary
+    tau = (ctypes.c_double * 2)(0.1, -0.2)
+    assert L.fd4_fed_cycle(fake, 8, 8, 8, fake, tau, 2, 0, ws, 1 << 30, None) == -1
+    tau = (ctypes.c_double * 2)(0.1, 0.2)
+    assert L.fd4_fed_cycle(fake, 8, 8, 8, fake, tau, 2, 7, ws, 1 << 30, None) == -1
+    # filter: unstable schedule is reported before any launch
+    p = fd4.params(tau_max=0.05)
+    assert L.fd4_filter(fake, fake, 8, 8, 8, sig, 2, ctypes.byref(p), 35.0, 5, 10, None, 0, ws,
+                        1 << 40, None) == -2
