@@ -165,11 +165,12 @@ def _pitch(buf):
 
 
 def select_scales(img, w: int, sigmas, prm: Params | None = None, want_vmax: bool = False,
-                  ws=None, stream=None):
+                  ws=None, stream=None, idx=None):
     """fd4_select_scales.  Returns (sigma_idx uint8 (h, pitch), vmax or None)."""
     torch = _torch()
     h, pitch = img.shape
-    idx = torch.zeros((h, pitch), dtype=torch.uint8, device=img.device)
+    if idx is None:
+        idx = torch.zeros((h, pitch), dtype=torch.uint8, device=img.device)
     vmax = torch.zeros((h, pitch), dtype=torch.float32, device=img.device) if want_vmax else None
     sg, K = _sigmas(sigmas)
     if ws is None:
@@ -207,14 +208,14 @@ def fed_cycle(u, w: int, tensor, tau, boundary: int = NATURAL, ws=None, stream=N
 
 
 def filter_image(u_in, w: int, sigmas, T: float, M: int, n: int = 0, prm: Params | None = None,
-                 sigma_idx=None, out=None, ws=None, stream=None):
-    """fd4_filter.  Returns (out, sigma_idx)."""
+                 sigma_idx=None, out=None, ws=None, stream=None, keep_idx: bool = True):
+    """fd4_filter.  Returns (out, sigma_idx); sigma_idx is None if not kept."""
     torch = _torch()
     h, pitch = u_in.shape
     if out is None:
         out = torch.zeros_like(u_in)
     given = sigma_idx is not None
-    if sigma_idx is None:
+    if sigma_idx is None and keep_idx:
         sigma_idx = torch.zeros((h, pitch), dtype=torch.uint8, device=u_in.device)
     sg, K = _sigmas(sigmas)
     if ws is None:

@@ -62,13 +62,22 @@ def _tensor_to_device(t, w):
     return buf
 
 
-@pytest.mark.parametrize("shape,boundary", [((128, 128), 0), ((53, 37), 0), ((61, 130), 0), ((32, 40), 1)])
-def test_fed_cycle_random_tensor(oracle, shape, boundary):
+@pytest.fixture(params=[0, 2, 3, 4], ids=["step", "fuse2", "fuse3", "fuse4"])
+def fed_variant(request, monkeypatch):
+    """FED kernel variant: one launch per step, or 2..4 steps fused per launch."""
+    monkeypatch.setenv("FD4_FED_FUSE", str(request.param))
+    return request.param
+
+
+@pytest.mark.parametrize("shape,boundary,n", [((128, 128), 0, 20), ((53, 37), 0, 20), ((61, 130), 0, 19),
+                                              ((32, 40), 1, 20), ((3, 3), 0, 5), ((5, 7), 1, 7),
+                                              ((260, 97), 0, 25)])
+def test_fed_cycle_random_tensor(oracle, fed_variant, shape, boundary, n):
     rng = np.random.default_rng(shape[0] * 7 + shape[1])
     h, w = shape
     u0 = rng.random((h, w)).astype(np.float32)
     t = _random_tensor(rng, h, w)
-    tau, _, _ = oracle.fed_taus(35.0, 5, 0.05, n=20)
+    tau, _, _ = oracle.fed_taus(n * (n + 1) * 0.05 / 3, 1, 0.05, n=n)
     ref = oracle.fed_cycle(u0, t, tau, boundary)
     u = fd4.to_device(u0)
     fd4.fed_cycle(u, w, _tensor_to_device(t, w), tau, boundary)
@@ -78,7 +87,7 @@ def test_fed_cycle_random_tensor(oracle, shape, boundary):
     assert float(u[:, w:].abs().max()) == 0.0 if u.shape[1] > w else True
 
 
-def test_fed_single_step_equals_oracle_operator(oracle):
+def test_fed_single_step_equals_oracle_operator(oracle, fed_variant):
     rng = np.random.default_rng(1)
     h, w = 70, 90
     u0 = rng.random((h, w)).astype(np.float32)
@@ -89,7 +98,7 @@ def test_fed_single_step_equals_oracle_operator(oracle):
     assert np.abs(_np(u, w) - ref).max() <= 2e-6
 
 
-def test_biharmonic_mode_periodic(oracle):
+def test_biharmonic_mode_periodic(oracle, fed_variant):
     h, w = 32, 40
     y, x = np.mgrid[0:h, 0:w].astype(np.float64)
     kx, ky = 2 * math.pi * 3 / w, 2 * math.pi * 2 / h
@@ -103,7 +112,7 @@ def test_biharmonic_mode_periodic(oracle):
     assert np.abs(_np(u, w) - expect).max() <= 1e-5
 
 
-def test_mean_is_conserved_natural_boundary():
+def test_mean_is_conserved_natural_boundary(fed_variant):
     import torch
     rng = np.random.default_rng(2)
     h, w = 300, 257
