@@ -174,6 +174,29 @@ int fd4_filter(const float *d_in, float *d_out, int w, int h, int pitch,
                double T, int M, int n_in, uint8_t *d_sigma_idx, int sigma_given,
                void *d_ws, size_t ws_bytes, fd4_stream_t stream);
 
+/* Allocation-free FED cycle.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- host applications
+ * that own all device memory and pass a library only the buffers it works on,
+ * and programs that must not call cudaMalloc after start-up (it can
+ * synchronise the device, and some run under a no-allocation policy).  It
+ * computes exactly what fd4_fed_cycle computes, with the same arguments minus
+ * the workspace: its scratch plane is a static array inside the library,
+ * FD4_NOALLOC_MAX_PIXELS floats (16 MiB) per GPU, held by every GPU that loads
+ * the library until the process exits.
+ *   - h * pitch must not exceed FD4_NOALLOC_MAX_PIXELS, else
+ *     FD4_ERR_WS_TOO_SMALL (the built-in scratch is too small for the image).
+ *   - The first call on a device looks up the scratch array's device address
+ *     (once per device, with that device current); make that first call before
+ *     any stream capture.
+ *   - All calls share the one scratch array, which keeps the last call's
+ *     contents; nothing in it has to start at zero.  Calls whose work overlaps
+ *     on the GPU (different streams, or different host threads on one device)
+ *     race on it and must be serialised by the caller.
+ *   - It calls no cudaMalloc, cudaFree or allocating library routine.        */
+#define FD4_NOALLOC_MAX_PIXELS (4 * 1024 * 1024)
+int fd4_fed_cycle_noalloc(float *d_u, int w, int h, int pitch, const float *d_tensor,
+                          const double *h_tau, int n, int boundary, fd4_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -60,7 +60,9 @@ SIGNATURES = {
     "fd4_fed_cycle": (_i, [_vp, _i, _i, _i, _vp, _dp, _i, _i, _vp, _sz, _vp]),
     "fd4_filter": (_i, [_vp, _vp, _i, _i, _i, _fp, _i, _pp, ctypes.c_double, _i, _i, _vp, _i, _vp,
                         _sz, _vp]),
+    "fd4_fed_cycle_noalloc": (_i, [_vp, _i, _i, _i, _vp, _dp, _i, _i, _vp]),
 }
+NOALLOC_MAX_PIXELS = 4 * 1024 * 1024
 
 
 def library_path() -> str:
@@ -225,3 +227,14 @@ def filter_image(u_in, w: int, sigmas, T: float, M: int, n: int = 0, prm: Params
                             _ptr(sigma_idx), int(given), _ptr(ws), ws.numel(), _stream(stream)),
            "fd4_filter")
     return out, sigma_idx
+
+
+def fed_cycle_noalloc(u, w: int, tensor, tau, boundary: int = NATURAL, stream=None):
+    """fd4_fed_cycle_noalloc, in place on u: the FED cycle without a workspace,
+    for callers that cannot allocate device memory (scratch is built into the
+    library; see include/fd4.h)."""
+    h, pitch = u.shape
+    t = np.ascontiguousarray(tau, dtype=np.float64)
+    _check(lib().fd4_fed_cycle_noalloc(_ptr(u), int(w), h, pitch, _ptr(tensor), t.ctypes.data_as(_dp),
+                                       t.size, int(boundary), _stream(stream)), "fd4_fed_cycle_noalloc")
+    return u
