@@ -158,6 +158,17 @@ def oracle_sample(imgs, wl, mode, max_images=2):
     return res, secs, O.num_threads(), pxsteps
 
 
+def _timed(fn, steps, stream, torch):
+    """CUDA-event time (ms) of `steps` calls of fn on `stream`."""
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    z.record(stream)
+    z.synchronize()
+    return a.elapsed_time(z)
+
+
 def run_fd4(args, rank, world, local_rank):
     imgs, wl = make_workload(args.workload, rank, args.limit)  # before CUDA init (spawn pool)
     import torch
@@ -170,116 +181,117 @@ def run_fd4(args, rank, world, local_rank):
     sig, M, n, T = wl["sigmas"], wl["M"], wl["n"], wl["T"]
     K = len(sig)
     mode = MODES[wl["mode"]]
-    prm = fd4.params(mode=mode)
-    tau, kappa = fd4.fed_taus(T, M, 0.05, n=n)
     ims = [Image(im, dev, fd4, torch) for im in imgs]
-    big = max(ims, key=lambda b: b.h * b.pitch)
-    ws = fd4.workspace(fd4.OP_FILTER, big.pitch, max(b.h for b in ims), K, dev)
+    npx = sum(b.npx for b in ims)
+    px_steps = npx * M * n
     stream = torch.cuda.current_stream()
-    px_steps = sum(b.npx for b in ims) * M * n
-    launches_per_step = sum((K + 1) + M * (K + 1 + n) for _ in ims)
-
-    def step(ev=None):
-        for b in ims:
-            if ev is not None:
-                e = [torch.cuda.Event(enable_timing=True) for _ in range(2 + 2 * M)]
-                e[0].record(stream)
-            fd4.select_scales(b.u_in, b.w, sig, prm, ws=ws, idx=b.idx)
-            b.out.copy_(b.u_in)
-            if ev is not None:
-                e[1].record(stream)
-            for k in range(M):
-                fd4.build_tensor(b.out, b.w, b.idx, sig, prm, out=b.ten, ws=ws)
-                if ev is not None:
-                    e[2 + 2 * k].record(stream)
-                fd4.fed_cycle(b.out, b.w, b.ten, tau, ws=ws)
-                if ev is not None:
-                    e[3 + 2 * k].record(stream)
-            if ev is not None:
-                ev.append((b, e))
 
     def barrier():
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        step()
-    barrier()
-    evs = []
-    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local_rank) as clk:
-        t_start.record(stream)
-        for _ in range(args.steps):
-            step(evs)
-        t_end.record(stream)
-        barrier()
-    ms = t_start.elapsed_time(t_end)
-    fed_ms = sel_ms = ten_ms = 0.0
-    fed_bytes = 0
-    for b, e in evs:
-        sel_ms += e[0].elapsed_time(e[1])
-        prev = e[1]
-        for k in range(M):
-            ten_ms += prev.elapsed_time(e[2 + 2 * k])
-            fed_ms += e[2 + 2 * k].elapsed_time(e[3 + 2 * k])
-            prev = e[3 + 2 * k]
-        fed_bytes += 24 * b.npx * n * M
-    if dist is not None:
+    def max_over_ranks(ms):
+        if dist is None:
+            return ms
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * px_steps * args.steps / (ms * 1e-3) / 1e6
+        return float(t.item())
 
-    # end to end through the public entry point, host buffers, copies inside the timed region
+    # batched path: one launch per stage across the batch, replayed as a CUDA graph
+    lst = fd4.image_list([b.u_in for b in ims], [b.w for b in ims], [b.out for b in ims], [b.idx for b in ims])
+    ws = fd4.batch_workspace(lst, K, dev)
+    best, tune_ms = fd4.autotune_batched(lst, sig, T, M, n, fd4.params(mode=mode), ws=ws)
+    prm = fd4.params(mode=mode, fed_steps_per_launch=best)
+    g_all = fd4.Graph(lst, sig, T, M, n, prm, ws=ws)
+    g_sel = fd4.Graph(lst, sig, T, M, n, prm, ws=ws, stages=fd4.STAGE_SELECT)
+    g_ten = fd4.Graph(lst, sig, T, M, n, prm, ws=ws, stages=fd4.STAGE_TENSOR)
+    g_fed = fd4.Graph(lst, sig, T, M, n, prm, ws=ws, stages=fd4.STAGE_FED)
+    L = -(-n // best) if best > 1 else n          # FED launches per cycle
+    fed_launches = M * L
+    sweeps = -(-K // 16)                          # sweep launches per stage (16 scales each)
+    launches_per_step = (-(-len(ims) // 128)      # descriptor upload
+                         + sweeps + 1 + 1         # selection sweep, argmax, input copy
+                         + M * (sweeps + 1 + L + (L % 2)))  # tensor sweep, finish, FED (+ copy-back)
+
+    for _ in range(args.warmup):
+        g_all.launch()
+    barrier()
+    with ClockSampler(local_rank) as clk:
+        ms = _timed(g_all.launch, args.steps, stream, torch)
+        barrier()
+    ms = max_over_ranks(ms)
+    value = world * px_steps * args.steps / (ms * 1e-3) / 1e6
+    # stage split and the FED kernel alone (each graph replays one stage of the same schedule)
+    sel_ms = _timed(g_sel.launch, args.steps, stream, torch) / args.steps
+    ten_ms = _timed(g_ten.launch, args.steps, stream, torch) / args.steps
+    fed_ms = _timed(g_fed.launch, args.steps, stream, torch) / args.steps
+    g_all.launch()  # leave the outputs of a complete filter pass in place
+    barrier()
+
+    # plain path: per-image calls, one launch per FED step
+    plain_prm = fd4.params(mode=mode, fed_steps_per_launch=1)
+    ws_plain = fd4.workspace(fd4.OP_FILTER, max(b.pitch for b in ims), max(b.h for b in ims), K, dev)
+    outs_plain = [torch.empty_like(b.u_in) for b in ims]
+
+    def plain_step():
+        for b, o in zip(ims, outs_plain):
+            fd4.filter_image(b.u_in, b.w, sig, T, M, n, plain_prm, out=o, ws=ws_plain, keep_idx=False)
+
+    plain_step()
+    barrier()
+    plain_ms = max_over_ranks(_timed(plain_step, max(1, min(args.steps, 3)), stream, torch) / max(1, min(args.steps, 3)))
+    plain_value = world * px_steps / (plain_ms * 1e-3) / 1e6
+    diff_plain = max(float((o[:, :b.w] - b.out[:, :b.w]).abs().max()) for o, b in zip(outs_plain, ims))
+
+    # end to end through the public API: pinned host buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
         hin = [b.u_in.cpu().pin_memory() for b in ims]
         hout = [torch.empty_like(h).pin_memory() for h in hin]
+
         def e2e_step():
-            for b, hi, ho in zip(ims, hin, hout):
+            for b, hi in zip(ims, hin):
                 b.u_in.copy_(hi, non_blocking=True)
-                fd4.filter_image(b.u_in, b.w, sig, T, M, n, prm, out=b.out, ws=ws, keep_idx=False)
+            g_all.launch()
+            for b, ho in zip(ims, hout):
                 ho.copy_(b.out, non_blocking=True)
-        for _ in range(max(1, min(args.warmup, 2))):
-            e2e_step()
+
+        e2e_step()
         barrier()
-        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
-        z.record(stream)
-        barrier()
-        ems = a.elapsed_time(z)
-        if dist is not None:
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(_timed(e2e_step, args.steps, stream, torch))
         nbytes = sum(h.numel() * 4 for h in hin)
         e2e = {"value": world * px_steps * args.steps / (ems * 1e-3) / 1e6, "unit": UNIT,
-               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "ms_per_step": ems / args.steps}
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": ems / args.steps,
+               "path": "pinned host images -> fd4_graph_launch (batched filter) -> pinned host results"}
 
     if rank != 0:
         return
     peak, peak_kind = load_peaks()
+    fed_bytes = 24 * npx * M * n  # algorithmic bytes of the FED steps of one pass
     achieved = fed_bytes / (fed_ms * 1e-3) / 1e9
+    kname = "k_fed_fused<%d>" % best if best > 1 else "k_fed_step"
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": args.traffic, "kernel": "k_fed_step",
+            "traffic": args.traffic, "kernel": kname,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind,
-            "bytes_per_px_step": 24, "avg_launch_us": fed_ms * 1e3 / (len(evs) * M * n)}
+            "bytes_per_px_step": 24, "steps_per_launch": best,
+            "avg_launch_us": fed_ms * 1e3 / fed_launches,
+            "algorithmic_bytes_per_launch": fed_bytes / fed_launches}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": args.workload, "images": len(ims),
-                      "mpixel": round(sum(b.npx for b in ims) / 1e6, 3), "sigmas": K, "mode": wl["mode"],
-                      "M": M, "n": n, "T": T, "kappa": kappa, "path": "plain",
+           "config": {"workload": args.workload, "images": len(ims), "mpixel": round(npx / 1e6, 3),
+                      "sigmas": K, "mode": wl["mode"], "M": M, "n": n, "T": T,
+                      "path": "batched (one persistent launch per stage) + CUDA graph",
+                      "fed_steps_per_launch": best, "autotune_ms": tune_ms,
                       "l2": "inputs larger than L2 (images %.2f GB, tensor field %.2f GB per pass)" % (
-                          sum(b.npx for b in ims) * 4e-9, sum(b.npx for b in ims) * 16e-9)},
+                          npx * 4e-9, npx * 16e-9)},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
            "clocks": clk.summary(),
-           "stages_ms_per_step": {"select": sel_ms / args.steps, "tensor": ten_ms / args.steps,
-                                  "fed": fed_ms / args.steps}}
+           "stages_ms_per_step": {"select": sel_ms, "tensor": ten_ms, "fed": fed_ms},
+           "plain": {"value": plain_value, "ms_per_step": plain_ms,
+                     "path": "per-image fd4_filter calls, one launch per FED step",
+                     "speedup_of_batched": value / plain_value, "max_abs_diff_to_batched": diff_plain}}
     if world == 1 and not args.no_cpu_baseline:
         res, secs, cores, pxs = oracle_sample(imgs, wl, mode)
         errs, agree, errs_inj = [], [], []
@@ -290,7 +302,7 @@ def run_fd4(args, rank, world, local_rank):
             agree.append(float((b.idx[:, :b.w].cpu().numpy() == idx_o).mean()))
             idx_in = torch.zeros_like(b.idx)
             idx_in[:, :b.w] = torch.from_numpy(idx_o).to(dev)
-            o2, _ = fd4.filter_image(b.u_in, b.w, sig, T, M, n, prm, sigma_idx=idx_in, ws=ws)
+            o2, _ = fd4.filter_image(b.u_in, b.w, sig, T, M, n, prm, sigma_idx=idx_in, ws=ws_plain)
             errs_inj.append(float(np.abs(o2[:, :b.w].cpu().numpy() - ref).max()))
         sample = "oracle full filter of the %d smallest batch images (%s px)" % (
             len(res), ", ".join("%dx%d" % imgs[i].shape[::-1] for i, _, _ in res))
@@ -299,6 +311,8 @@ def run_fd4(args, rank, world, local_rank):
         out["parity"] = {"vs": "FP64 oracle", "images": sample, "max_abs": max(errs),
                          "max_abs_oracle_sigma": max(errs_inj), "sigma_agreement": min(agree),
                          "tolerance": 1e-4}
+    for g in (g_all, g_sel, g_ten, g_fed):
+        g.close()
     print(json.dumps(out), flush=True)
 
 

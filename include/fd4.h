@@ -64,7 +64,7 @@ typedef enum fd4_mode { FD4_RIDGE = 0, FD4_VALLEY = 1, FD4_BOTH = 2 } fd4_mode;
 typedef enum fd4_boundary { FD4_BC_NATURAL = 0, FD4_BC_PERIODIC = 1 } fd4_boundary;
 
 #define FD4_MAX_SIGMAS 32          /* scale-set size limit (uint8 index map)     */
-#define FD4_MAX_SIGMA 16.0f        /* largest sigma: kernel radius ceil(4 sigma) <= 64 */
+#define FD4_MAX_SIGMA 12.0f        /* largest sigma: kernel radius ceil(4 sigma) <= 48 */
 #define FD4_MAX_FED_STEPS 4096     /* longest FED cycle                          */
 
 typedef struct fd4_params {
@@ -80,6 +80,10 @@ typedef struct fd4_params {
     int kappa;               /* FED step ordering: 0 = automatic, else i -> kappa*i mod n */
     int grad_norm_squared;   /* 0: 1/sqrt(1+|grad|) as printed in Eq. 6 (default);
                                 1: 1/sqrt(1+|grad|^2)                              */
+    int fed_steps_per_launch;/* FED kernel schedule (no effect on the result beyond
+                                FP32 rounding): 0 = library default (2),
+                                1 = one launch per explicit step, 2..4 = that many
+                                steps fused per launch (see fd4_autotune_batched) */
 } fd4_params;
 
 /* Fills *p with the defaults listed above. */
@@ -173,6 +177,60 @@ int fd4_filter(const float *d_in, float *d_out, int w, int h, int pitch,
                const float *h_sigmas, int n_sigma, const fd4_params *params,
                double T, int M, int n_in, uint8_t *d_sigma_idx, int sigma_given,
                void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batches: many images of uneven sizes, one persistent launch per stage.     */
+
+typedef struct fd4_image {
+    const float *d_in;       /* device input image (not modified unless == d_out) */
+    float *d_out;            /* device output image; may equal d_in                */
+    uint8_t *d_sigma_idx;    /* nullable unless sigma_given: receives / supplies sigma* */
+    int w, h, pitch;         /* as for the single-image calls                      */
+} fd4_image;
+
+#define FD4_MAX_BATCH 65536
+
+/* Workspace for fd4_filter_batched / fd4_graph_create on this list of images. */
+size_t fd4_batch_workspace_bytes(const fd4_image *h_imgs, int n_images, int n_sigma);
+
+/* fd4_filter on every image of the host array h_imgs (n_images entries), with
+ * one launch per stage covering all images: each stage kernel walks a flat
+ * list of tiles spanning the batch.  Results are those of fd4_filter on each
+ * image separately (identical arithmetic per pixel).  Errors as fd4_filter;
+ * every image is validated before anything is enqueued.                      */
+int fd4_filter_batched(const fd4_image *h_imgs, int n_images, const float *h_sigmas, int n_sigma,
+                       const fd4_params *params, double T, int M, int n_in, int sigma_given,
+                       void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+
+/* The schedule of fd4_filter_batched (descriptor upload, selection, input
+ * copy, M cycles of tensor build and FED cycle) captured once into a CUDA
+ * graph and replayed by fd4_graph_launch.  `stages` selects what is captured:
+ * FD4_STAGES_ALL for the filter; a subset replays only those stages on the
+ * current workspace contents (for timing one stage: FD4_STAGE_FED alone runs
+ * M FED cycles on the images with the tensor fields left by a previous run).
+ * The graph keeps the device pointers of h_imgs and d_ws: those buffers must
+ * stay allocated while the graph exists; their contents are read at each
+ * launch.  The host arrays may be freed after the call.                     */
+#define FD4_STAGE_SELECT 1
+#define FD4_STAGE_COPY 2
+#define FD4_STAGE_TENSOR 4
+#define FD4_STAGE_FED 8
+#define FD4_STAGES_ALL 15
+typedef struct fd4_graph_st *fd4_graph;
+int fd4_graph_create(const fd4_image *h_imgs, int n_images, const float *h_sigmas, int n_sigma,
+                     const fd4_params *params, double T, int M, int n_in, int sigma_given, int stages,
+                     void *d_ws, size_t ws_bytes, fd4_graph *out);
+int fd4_graph_launch(fd4_graph g, fd4_stream_t stream);
+int fd4_graph_destroy(fd4_graph g);
+
+/* Autotuner for the FED kernel schedule: runs the selection and one tensor
+ * build of the batch, then times one FED cycle with each schedule (1 to 4
+ * steps per launch) with CUDA events on `stream` (synchronising it) and
+ * writes the fastest to *best_steps_per_launch; times_ms (nullable, 4
+ * entries) receives the times.  The images' d_out buffers are overwritten.  */
+int fd4_autotune_batched(const fd4_image *h_imgs, int n_images, const float *h_sigmas, int n_sigma,
+                         const fd4_params *params, double T, int M, int n_in, void *d_ws, size_t ws_bytes,
+                         fd4_stream_t stream, int *best_steps_per_launch, float *times_ms);
 
 /* Allocation-free FED cycle.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory -- host applications

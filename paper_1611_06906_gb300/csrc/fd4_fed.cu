@@ -22,72 +22,128 @@ __device__ __forceinline__ int wrap(int i, int n)
     return i < 0 ? i + n : i;
 }
 
-__global__ void __launch_bounds__(BX *BY) k_fed_step(const float *__restrict__ uin, float *__restrict__ uout,
-                                                     const float4 *__restrict__ ten, int w, int h, int pitch,
-                                                     float tau, int periodic)
+__global__ void __launch_bounds__(BX *BY) k_fed_step(Imgs I, float tau, int parity, int periodic)
 {
     __shared__ float su[BY + 4][BX + 4];
     __shared__ float sxx[BY + 2][BX + 2], sxy[BY + 2][BX + 2], syy[BY + 2][BX + 2];
-    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    __shared__ ImgDesc sd;
+    __shared__ int s_local;
     const int tid = threadIdx.y * BX + threadIdx.x;
+    for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
+        __syncthreads();
+        if (tid == 0) find_tile(I, SHAPE_SMALL, t, sd, s_local);
+        __syncthreads();
+        const int w = sd.w, h = sd.h, pitch = sd.pitch;
+        const float *uin = parity ? sd.tmp : sd.u;
+        float *uout = parity ? sd.u : sd.tmp;
+        const float4 *ten = sd.tensor;
+        const int tiles_x = (w + BX - 1) / BX;
+        const int x0 = (s_local % tiles_x) * BX, y0 = (s_local / tiles_x) * BY;
 
-    for (int i = tid; i < (BY + 4) * (BX + 4); i += BX * BY) {
-        const int ry = i / (BX + 4), rx = i - ry * (BX + 4);
-        int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
-        float v = 0.0f;
-        if (periodic) {
-            v = uin[(size_t)wrap(gy, h) * pitch + wrap(gx, w)];
-        } else if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
-            v = uin[(size_t)gy * pitch + gx];
+        for (int i = tid; i < (BY + 4) * (BX + 4); i += BX * BY) {
+            const int ry = i / (BX + 4), rx = i - ry * (BX + 4);
+            int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
+            float v = 0.0f;
+            if (periodic) {
+                v = uin[(size_t)wrap(gy, h) * pitch + wrap(gx, w)];
+            } else if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
+                v = uin[(size_t)gy * pitch + gx];
+            }
+            su[ry][rx] = v;
         }
-        su[ry][rx] = v;
+        __syncthreads();
+
+        for (int i = tid; i < (BY + 2) * (BX + 2); i += BX * BY) {
+            const int ry = i / (BX + 2), rx = i - ry * (BX + 2);
+            int px = x0 - 1 + rx, py = y0 - 1 + ry;
+            float Txx = 0.0f, Txy = 0.0f, Tyy = 0.0f;
+            bool in = true, vx = true, vy = true;
+            if (periodic) {
+                px = wrap(px, w);
+                py = wrap(py, h);
+            } else {
+                in = px >= 0 && px < w && py >= 0 && py < h;
+                vx = px >= 1 && px <= w - 2;
+                vy = py >= 1 && py <= h - 2;
+            }
+            if (in && (vx || vy)) {
+                const float c = su[ry + 1][rx + 1];
+                const float hxx = vx ? su[ry + 1][rx] - 2.0f * c + su[ry + 1][rx + 2] : 0.0f;
+                const float hyy = vy ? su[ry][rx + 1] - 2.0f * c + su[ry + 2][rx + 1] : 0.0f;
+                const float hxy =
+                    (vx && vy) ? 0.25f * (su[ry][rx] + su[ry + 2][rx + 2] - su[ry + 2][rx] - su[ry][rx + 2]) : 0.0f;
+                const float4 tt = __ldg(ten + (size_t)py * pitch + px);  // (cos 2t, sin 2t, mu1, mu2)
+                // D : h in the eigenframe of e1 = (cos t, sin t), e2 = (-sin t, cos t)
+                const float sh = 0.5f * (hxx + hyy), dh = 0.5f * (hxx - hyy);
+                const float h11 = sh + tt.x * dh + tt.y * hxy;
+                const float h22 = sh - tt.x * dh - tt.y * hxy;
+                const float h12 = tt.x * hxy - tt.y * dh;
+                const float t11 = tt.z * h11, t22 = tt.w * h22, t12 = 0.5f * (tt.z + tt.w) * h12;
+                const float st = 0.5f * (t11 + t22), dt = 0.5f * (t11 - t22);
+                Txx = vx ? st + tt.x * dt - tt.y * t12 : 0.0f;
+                Tyy = vy ? st - tt.x * dt + tt.y * t12 : 0.0f;
+                Txy = (vx && vy) ? tt.y * dt + tt.x * t12 : 0.0f;
+            }
+            sxx[ry][rx] = Txx;
+            sxy[ry][rx] = Txy;
+            syy[ry][rx] = Tyy;
+        }
+        __syncthreads();
+
+        const int tx = threadIdx.x, ty = threadIdx.y;
+        const int gx = x0 + tx, gy = y0 + ty;
+        if (gx >= w || gy >= h) continue;
+        const float div = (sxx[ty + 1][tx] - 2.0f * sxx[ty + 1][tx + 1] + sxx[ty + 1][tx + 2]) +
+                          (syy[ty][tx + 1] - 2.0f * syy[ty + 1][tx + 1] + syy[ty + 2][tx + 1]) +
+                          0.5f * (sxy[ty + 2][tx + 2] + sxy[ty][tx] - sxy[ty][tx + 2] - sxy[ty + 2][tx]);
+        uout[(size_t)gy * pitch + gx] = su[ty + 2][tx + 2] - tau * div;
     }
-    __syncthreads();
+}
 
-    for (int i = tid; i < (BY + 2) * (BX + 2); i += BX * BY) {
-        const int ry = i / (BX + 2), rx = i - ry * (BX + 2);
-        int px = x0 - 1 + rx, py = y0 - 1 + ry;
-        float Txx = 0.0f, Txy = 0.0f, Tyy = 0.0f;
-        bool in = true, vx = true, vy = true;
-        if (periodic) {
-            px = wrap(px, w);
-            py = wrap(py, h);
-        } else {
-            in = px >= 0 && px < w && py >= 0 && py < h;
-            vx = px >= 1 && px <= w - 2;
-            vy = py >= 1 && py <= h - 2;
-        }
-        if (in && (vx || vy)) {
-            const float c = su[ry + 1][rx + 1];
-            const float hxx = vx ? su[ry + 1][rx] - 2.0f * c + su[ry + 1][rx + 2] : 0.0f;
-            const float hyy = vy ? su[ry][rx + 1] - 2.0f * c + su[ry + 2][rx + 1] : 0.0f;
-            const float hxy = (vx && vy) ? 0.25f * (su[ry][rx] + su[ry + 2][rx + 2] - su[ry + 2][rx] - su[ry][rx + 2])
-                                         : 0.0f;
-            const float4 t = __ldg(ten + (size_t)py * pitch + px);  // (cos 2t, sin 2t, mu1, mu2)
-            // D : h in the eigenframe of e1 = (cos t, sin t), e2 = (-sin t, cos t)
-            const float sh = 0.5f * (hxx + hyy), dh = 0.5f * (hxx - hyy);
-            const float h11 = sh + t.x * dh + t.y * hxy;
-            const float h22 = sh - t.x * dh - t.y * hxy;
-            const float h12 = t.x * hxy - t.y * dh;
-            const float t11 = t.z * h11, t22 = t.w * h22, t12 = 0.5f * (t.z + t.w) * h12;
-            const float st = 0.5f * (t11 + t22), dt = 0.5f * (t11 - t22);
-            Txx = vx ? st + t.x * dt - t.y * t12 : 0.0f;
-            Tyy = vy ? st - t.x * dt + t.y * t12 : 0.0f;
-            Txy = (vx && vy) ? t.y * dt + t.x * t12 : 0.0f;
-        }
-        sxx[ry][rx] = Txx;
-        sxy[ry][rx] = Txy;
-        syy[ry][rx] = Tyy;
+// Copies each image's input into its filter state (skipped where they coincide).
+__global__ void __launch_bounds__(256) k_copy_in(Imgs I)
+{
+    __shared__ ImgDesc sd;
+    __shared__ int s_local;
+    const int tid = threadIdx.x;
+    for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
+        __syncthreads();
+        if (tid == 0) find_tile(I, SHAPE_SMALL, t, sd, s_local);
+        __syncthreads();
+        if (sd.in == sd.u) continue;
+        const int tiles_x = (sd.w + 31) / 32;
+        const int x = (s_local % tiles_x) * 32 + (tid & 31), y = (s_local / tiles_x) * 8 + (tid >> 5);
+        if (x < sd.w && y < sd.h) sd.u[(size_t)y * sd.pitch + x] = sd.in[(size_t)y * sd.pitch + x];
     }
-    __syncthreads();
+}
 
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int gx = x0 + tx, gy = y0 + ty;
-    if (gx >= w || gy >= h) return;
-    const float div = (sxx[ty + 1][tx] - 2.0f * sxx[ty + 1][tx + 1] + sxx[ty + 1][tx + 2]) +
-                      (syy[ty][tx + 1] - 2.0f * syy[ty + 1][tx + 1] + syy[ty + 2][tx + 1]) +
-                      0.5f * (sxy[ty + 2][tx + 2] + sxy[ty][tx] - sxy[ty][tx + 2] - sxy[ty + 2][tx]);
-    uout[(size_t)gy * pitch + gx] = su[ty + 2][tx + 2] - tau * div;
+// Writes a chunk of batch descriptors (passed as kernel parameters) to the
+// device table, so the upload is an ordinary kernel node in a CUDA graph.
+constexpr int kDescChunk = 128;
+struct DescChunk {
+    int first, n;
+    ImgDesc d[kDescChunk];
+};
+__global__ void k_put_descs(DescChunk c, ImgDesc *table)
+{
+    const int i = threadIdx.x;
+    if (i < c.n) table[c.first + i] = c.d[i];
+}
+
+// Copies the FED ping-pong plane back into the image (odd number of launches).
+__global__ void __launch_bounds__(256) k_copy_back(Imgs I)
+{
+    __shared__ ImgDesc sd;
+    __shared__ int s_local;
+    const int tid = threadIdx.x;
+    for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
+        __syncthreads();
+        if (tid == 0) find_tile(I, SHAPE_SMALL, t, sd, s_local);
+        __syncthreads();
+        const int tiles_x = (sd.w + 31) / 32;
+        const int x = (s_local % tiles_x) * 32 + (tid & 31), y = (s_local / tiles_x) * 8 + (tid >> 5);
+        if (x < sd.w && y < sd.h) sd.u[(size_t)y * sd.pitch + x] = sd.tmp[(size_t)y * sd.pitch + x];
+    }
 }
 
 
@@ -112,9 +168,7 @@ struct StepTaus {
 };
 
 template <int S>
-__global__ void __launch_bounds__(FNT, 2) k_fed_fused(const float *__restrict__ uin, float *__restrict__ uout,
-                                                      const float4 *__restrict__ ten, int w, int h, int pitch,
-                                                      StepTaus taus, int periodic)
+__global__ void __launch_bounds__(FNT, 2) k_fed_fused(Imgs I, StepTaus taus, int parity, int periodic)
 {
     constexpr int H = 2 * S, TXo = FRX - 2 * H, TYo = FRY - 2 * H;
     extern __shared__ float fsm[];
@@ -122,23 +176,36 @@ __global__ void __launch_bounds__(FNT, 2) k_fed_fused(const float *__restrict__ 
     float (*sxx)[FRX] = reinterpret_cast<float (*)[FRX]>(fsm + FRX * FRY);
     float (*sxy)[FRX] = reinterpret_cast<float (*)[FRX]>(fsm + 2 * FRX * FRY);
     float (*syy)[FRX] = reinterpret_cast<float (*)[FRX]>(fsm + 3 * FRX * FRY);
-
     __shared__ float stau[8];
-    const int gx0 = blockIdx.x * TXo - H, gy0 = blockIdx.y * TYo - H;
+    __shared__ ImgDesc sd;
+    __shared__ int s_local;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < 8) stau[tid] = taus.t[tid];
+    // this thread's column segment of the staged region
+    const int rx = (warp % (FRX / 32)) * 32 + lane, ry0 = (warp / (FRX / 32)) * FV;
+    const int xl = rx > 0 ? rx - 1 : 0, xr = rx < FRX - 1 ? rx + 1 : FRX - 1;
+
+    for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
+    __syncthreads();
+    if (tid == 0) find_tile(I, S, t, sd, s_local);
+    __syncthreads();
+    const int w = sd.w, h = sd.h, pitch = sd.pitch;
+    const float *uin = parity ? sd.tmp : sd.u;
+    float *uout = parity ? sd.u : sd.tmp;
+    const float4 *ten = sd.tensor;
+    const int tiles_x = (w + TXo - 1) / TXo;
+    const int gx0 = (s_local % tiles_x) * TXo - H, gy0 = (s_local / tiles_x) * TYo - H;
 
     for (int i = tid; i < FRX * FRY; i += FNT) {
-        const int ry = i / FRX, rx = i - ry * FRX;
-        const int gx = gx0 + rx, gy = gy0 + ry;
+        const int ry = i / FRX, rxx = i - ry * FRX;
+        const int gx = gx0 + rxx, gy = gy0 + ry;
         float v = 0.0f;
         if (periodic) v = uin[(size_t)wrap(gy, h) * pitch + wrap(gx, w)];
         else if (gx >= 0 && gx < w && gy >= 0 && gy < h) v = uin[(size_t)gy * pitch + gx];
-        su[ry][rx] = v;
+        su[ry][rxx] = v;
     }
 
-    // this thread's column segment and its pixels' tensor values
-    const int rx = (warp % (FRX / 32)) * 32 + lane, ry0 = (warp / (FRX / 32)) * FV;
+    // the tensor values of this thread's pixels (D is frozen over the cycle)
     const int gx = gx0 + rx;
     const int pgx = periodic ? wrap(gx, w) : gx;
     const bool in_x = periodic || (gx >= 0 && gx < w);
@@ -152,7 +219,6 @@ __global__ void __launch_bounds__(FNT, 2) k_fed_fused(const float *__restrict__ 
     }
     __syncthreads();
 
-    const int xl = rx > 0 ? rx - 1 : 0, xr = rx < FRX - 1 ? rx + 1 : FRX - 1;
     for (int l = 0; l < taus.n; ++l) {
         // T = M D M L u where the region shrunk by 2l+1 holds valid data
         const int lo_t = 2 * l + 1;
@@ -175,16 +241,16 @@ __global__ void __launch_bounds__(FNT, 2) k_fed_fused(const float *__restrict__ 
                         const float hxx = vx ? bL - 2.0f * bC + bR : 0.0f;
                         const float hyy = vy ? aC - 2.0f * bC + cC : 0.0f;
                         const float hxy = (vx && vy) ? 0.25f * (aL + cR - cL - aR) : 0.0f;
-                        const float4 t = tv[j];
+                        const float4 tt = tv[j];
                         const float sh = 0.5f * (hxx + hyy), dh = 0.5f * (hxx - hyy);
-                        const float h11 = sh + t.x * dh + t.y * hxy;
-                        const float h22 = sh - t.x * dh - t.y * hxy;
-                        const float h12 = t.x * hxy - t.y * dh;
-                        const float t11 = t.z * h11, t22 = t.w * h22, t12 = 0.5f * (t.z + t.w) * h12;
+                        const float h11 = sh + tt.x * dh + tt.y * hxy;
+                        const float h22 = sh - tt.x * dh - tt.y * hxy;
+                        const float h12 = tt.x * hxy - tt.y * dh;
+                        const float t11 = tt.z * h11, t22 = tt.w * h22, t12 = 0.5f * (tt.z + tt.w) * h12;
                         const float st = 0.5f * (t11 + t22), dt = 0.5f * (t11 - t22);
-                        Txx = vx ? st + t.x * dt - t.y * t12 : 0.0f;
-                        Tyy = vy ? st - t.x * dt + t.y * t12 : 0.0f;
-                        Txy = (vx && vy) ? t.y * dt + t.x * t12 : 0.0f;
+                        Txx = vx ? st + tt.x * dt - tt.y * t12 : 0.0f;
+                        Tyy = vy ? st - tt.x * dt + tt.y * t12 : 0.0f;
+                        Txy = (vx && vy) ? tt.y * dt + tt.x * t12 : 0.0f;
                     }
                     sxx[ry][rx] = Txx;
                     sxy[ry][rx] = Txy;
@@ -230,23 +296,13 @@ __global__ void __launch_bounds__(FNT, 2) k_fed_fused(const float *__restrict__ 
         const int ox = gx0 + H + tx, oy = gy0 + H + ty;
         if (ox < w && oy < h) uout[(size_t)oy * pitch + ox] = su[H + ty][H + tx];
     }
+    }  // tile loop
 }
 
 }  // namespace
 
-// Steps fused per launch: FD4_FED_FUSE in the environment (0 = one launch per
-// step with k_fed_step, 2..4 = k_fed_fused<S>); default 2.
-static int fuse_steps()
-{
-    const char *e = getenv("FD4_FED_FUSE");
-    if (!e) return 2;
-    const int v = atoi(e);
-    return (v == 0 || (v >= 2 && v <= 4)) ? v : 2;
-}
-
 template <int S>
-static int launch_fused(const float *a, float *b, const float4 *ten, int w, int h, int pitch, const double *tau,
-                        int n, int periodic, cudaStream_t st)
+static int set_fused_smem()
 {
     static int attr_dev = -1;
     int dev = 0;
@@ -257,49 +313,102 @@ static int launch_fused(const float *a, float *b, const float4 *ten, int w, int 
             return 1;
         attr_dev = dev;
     }
-    constexpr int TXo = FRX - 4 * S, TYo = FRY - 4 * S;
-    const dim3 grid((w + TXo - 1) / TXo, (h + TYo - 1) / TYo);
+    return 0;
+}
+
+int prepare_fed_kernels() { return set_fused_smem<2>() || set_fused_smem<3>() || set_fused_smem<4>(); }
+
+template <int S>
+static int launch_fused(Imgs I, const double *tau, int n, int parity, int periodic, cudaStream_t st)
+{
+    if (set_fused_smem<S>()) return 1;
     StepTaus t{};
     t.n = n;
     for (int i = 0; i < n; ++i) t.t[i] = (float)tau[i];
-    k_fed_fused<S><<<grid, FNT, kFusedSmem, st>>>(a, b, ten, w, h, pitch, t, periodic);
+    const int grid = persistent_grid((const void *)k_fed_fused<S>, FNT, kFusedSmem, I.tiles);
+    k_fed_fused<S><<<grid, FNT, kFusedSmem, st>>>(I, t, parity, periodic);
     return 0;
+}
+
+int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundary, int steps_per_launch,
+                     cudaStream_t st)
+{
+    const int periodic = boundary == FD4_BC_PERIODIC;
+    int S = steps_per_launch;
+    if (S < 1 || S > 4) S = 2;
+    int parity = 0;
+    if (S == 1) {
+        Imgs I = B.I;
+        I.tiles = B.tiles[SHAPE_SMALL];
+        const int grid = persistent_grid((const void *)k_fed_step, BX * BY, 0, I.tiles);
+        for (int i = 0; i < n; ++i) {
+            k_fed_step<<<grid, dim3(BX, BY), 0, st>>>(I, (float)h_tau[i], parity, periodic);
+            parity ^= 1;
+        }
+    } else {
+        Imgs I = B.I;
+        I.tiles = B.tiles[S];
+        for (int i = 0; i < n; i += S) {
+            const int k = n - i < S ? n - i : S;
+            const int rc = S == 2 ? launch_fused<2>(I, h_tau + i, k, parity, periodic, st)
+                         : S == 3 ? launch_fused<3>(I, h_tau + i, k, parity, periodic, st)
+                                  : launch_fused<4>(I, h_tau + i, k, parity, periodic, st);
+            if (rc) return 1;
+            parity ^= 1;
+        }
+    }
+    if (parity) {  // the last launch wrote the ping-pong plane
+        Imgs I = B.I;
+        I.tiles = B.tiles[SHAPE_SMALL];
+        const int grid = persistent_grid((const void *)k_copy_back, 256, 0, I.tiles);
+        k_copy_back<<<grid, 256, 0, st>>>(I);
+    }
+    return cudaGetLastError() != cudaSuccess;
+}
+
+int launch_copy_in_batch(const HostBatch &B, cudaStream_t st)
+{
+    Imgs I = B.I;
+    I.tiles = B.tiles[SHAPE_SMALL];
+    const int grid = persistent_grid((const void *)k_copy_in, 256, 0, I.tiles);
+    k_copy_in<<<grid, 256, 0, st>>>(I);
+    return cudaGetLastError() != cudaSuccess;
+}
+
+int launch_put_descs(const ImgDesc *h_descs, int n, ImgDesc *d_table, cudaStream_t st)
+{
+    thread_local static DescChunk c;  // ~15 KB: kept off the stack
+    for (int first = 0; first < n; first += kDescChunk) {
+        c.first = first;
+        c.n = n - first < kDescChunk ? n - first : kDescChunk;
+        for (int i = 0; i < c.n; ++i) c.d[i] = h_descs[first + i];
+        k_put_descs<<<1, kDescChunk, 0, st>>>(c, d_table);
+    }
+    return cudaGetLastError() != cudaSuccess;
+}
+
+// Steps per launch for the single-image entry points: FD4_FED_FUSE in the
+// environment (1 = one launch per step, 2..4 fused); default 2.
+int default_steps_per_launch()
+{
+    const char *e = getenv("FD4_FED_FUSE");
+    if (!e) return 2;
+    const int v = atoi(e);
+    if (v == 0) return 1;
+    return (v >= 1 && v <= 4) ? v : 2;
 }
 
 int launch_fed_cycle(float *d_u, int w, int h, int pitch, const float *d_tensor, const double *h_tau, int n,
                      int boundary, char *ws, cudaStream_t st)
 {
-    float *tmp = (float *)(ws + kHeaderBytes);
-    const float4 *ten = (const float4 *)d_tensor;
-    const int periodic = boundary == FD4_BC_PERIODIC;
-    const int S = fuse_steps();
-    float *a = d_u, *b = tmp;
-    if (S == 0) {
-        const dim3 grid((w + BX - 1) / BX, (h + BY - 1) / BY), block(BX, BY);
-        for (int i = 0; i < n; ++i) {
-            k_fed_step<<<grid, block, 0, st>>>(a, b, ten, w, h, pitch, (float)h_tau[i], periodic);
-            float *t = a;
-            a = b;
-            b = t;
-        }
-    } else {
-        for (int i = 0; i < n; i += S) {
-            const int k = n - i < S ? n - i : S;
-            int rc = S == 2 ? launch_fused<2>(a, b, ten, w, h, pitch, h_tau + i, k, periodic, st)
-                   : S == 3 ? launch_fused<3>(a, b, ten, w, h, pitch, h_tau + i, k, periodic, st)
-                            : launch_fused<4>(a, b, ten, w, h, pitch, h_tau + i, k, periodic, st);
-            if (rc) return 1;
-            float *t = a;
-            a = b;
-            b = t;
-        }
-    }
-    if (a != d_u) {
-        if (cudaMemcpy2DAsync(d_u, (size_t)pitch * 4, a, (size_t)pitch * 4, (size_t)w * 4, (size_t)h,
-                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-            return 1;
-    }
-    return cudaGetLastError() != cudaSuccess;
+    ImgDesc d{};
+    d.u = d_u;
+    d.tmp = (float *)(ws + kHeaderBytes);
+    d.tensor = (float4 *)d_tensor;
+    d.w = w;
+    d.h = h;
+    d.pitch = pitch;
+    return launch_fed_batch(single_batch(d), h_tau, n, boundary, default_steps_per_launch(), st);
 }
 
 }  // namespace fd4

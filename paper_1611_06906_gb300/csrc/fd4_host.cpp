@@ -23,6 +23,7 @@ extern "C" void fd4_default_params(fd4_params *p)
     p->boundary = FD4_BC_NATURAL;
     p->kappa = 0;
     p->grad_norm_squared = 0;
+    p->fed_steps_per_launch = 0;
 }
 
 extern "C" const char *fd4_strerror(int s)
@@ -37,7 +38,7 @@ extern "C" const char *fd4_strerror(int s)
     case FD4_ERR_TIMEOUT: return "device-side wait timed out";
     case FD4_ERR_CUDA: return "CUDA runtime error";
     case FD4_ERR_ALIGN: return "device pointer not 16-byte aligned";
-    case FD4_ERR_SIGMA_RANGE: return "scales must be increasing and in (0, 16]";
+    case FD4_ERR_SIGMA_RANGE: return "scales must be increasing and in (0, 12]";
     case FD4_ERR_NOT_IMPLEMENTED: return "not implemented";
     default: return "unknown status";
     }
@@ -329,6 +330,28 @@ extern "C" int fd4_fed_cycle(float *d_u, int w, int h, int pitch, const float *d
                                         (cudaStream_t)stream));
 }
 
+// The filter schedule on a batch: selection (unless given), input copy, then M
+// cycles of tensor build and FED cycle.  Everything is enqueued on `st`.
+static int enqueue_filter(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
+                          const double *tau, int n, int M, int sigma_given, cudaStream_t st,
+                          int stages = FD4_STAGES_ALL)
+{
+    const int steps = p.fed_steps_per_launch > 0 ? p.fed_steps_per_launch : default_steps_per_launch();
+    if ((stages & FD4_STAGE_SELECT) && !sigma_given && launch_select_batch(B, h_sigmas, n_sigma, p, st))
+        return FD4_ERR_CUDA;
+    if ((stages & FD4_STAGE_COPY) && launch_copy_in_batch(B, st)) return FD4_ERR_CUDA;
+    for (int k = 0; k < M; ++k) {
+        if ((stages & FD4_STAGE_TENSOR) && launch_tensor_batch(B, h_sigmas, n_sigma, p, st)) return FD4_ERR_CUDA;
+        if ((stages & FD4_STAGE_FED) && launch_fed_batch(B, tau, n, p.boundary, steps, st)) return FD4_ERR_CUDA;
+    }
+    return FD4_OK;
+}
+
+static int check_steps(const fd4_params &p)
+{
+    return (p.fed_steps_per_launch < 0 || p.fed_steps_per_launch > 4) ? FD4_ERR_BAD_ARG : FD4_OK;
+}
+
 extern "C" int fd4_filter(const float *d_in, float *d_out, int w, int h, int pitch,
                           const float *h_sigmas, int n_sigma, const fd4_params *params, double T,
                           int M, int n_in, uint8_t *d_sigma_idx, int sigma_given, void *d_ws,
@@ -341,6 +364,7 @@ extern "C" int fd4_filter(const float *d_in, float *d_out, int w, int h, int pit
     if ((rc = check_image(d_out, w, h, pitch)) != FD4_OK) return rc;
     if ((rc = check_sigmas(h_sigmas, n_sigma)) != FD4_OK) return rc;
     if ((rc = check_params(p)) != FD4_OK) return rc;
+    if ((rc = check_steps(p)) != FD4_OK) return rc;
     if (sigma_given && !d_sigma_idx) return FD4_ERR_BAD_ARG;
     if ((rc = ws_ok(d_ws, ws_bytes, ws_filter_bytes(h, pitch, n_sigma))) != FD4_OK) return rc;
     std::vector<double> tau(FD4_MAX_FED_STEPS);
@@ -348,33 +372,249 @@ extern "C" int fd4_filter(const float *d_in, float *d_out, int w, int h, int pit
     if ((rc = fd4_fed_taus(T, M, p.tau_max, n_in, p.kappa, tau.data(), FD4_MAX_FED_STEPS, &n, nullptr)) != FD4_OK)
         return rc;
 
-    cudaStream_t st = (cudaStream_t)stream;
-    char *ws = (char *)d_ws;
     // [sigma* plane | tensor plane | stage workspace = header + scratch]; the
-    // stages run in order on one stream, so they share the stage workspace.
-    uint8_t *idx = (uint8_t *)ws;
-    float *tensor = (float *)(ws + plane_bytes(h, pitch, 1));
+    // stages run in order on one stream, so they share the scratch.
+    char *ws = (char *)d_ws;
     char *sws = ws + plane_bytes(h, pitch, 1) + plane_bytes(h, pitch, 16);
+    char *scratch = sws + kHeaderBytes;
+    const size_t pb = plane_bytes(h, pitch, 4);
+    ImgDesc d{};
+    d.in = d_in;
+    d.u = d_out;
+    d.tmp = (float *)scratch;
+    d.vp = (float *)scratch;
+    d.s2 = (float *)(scratch + (size_t)n_sigma * pb);
+    d.nfield = (float4 *)scratch;
+    d.tensor = (float4 *)(ws + plane_bytes(h, pitch, 1));
+    d.idx = d_sigma_idx ? d_sigma_idx : (uint8_t *)ws;
+    d.vmax = nullptr;
+    d.max_s2 = &((WsHeader *)sws)->max_s2;
+    d.plane = pb / 4;
+    d.w = w;
+    d.h = h;
+    d.pitch = pitch;
+    return enqueue_filter(single_batch(d), h_sigmas, n_sigma, p, tau.data(), n, M, sigma_given,
+                          (cudaStream_t)stream);
+}
 
-    if (sigma_given) {
-        idx = d_sigma_idx;
-    } else {
-        rc = launch_select(d_in, w, h, pitch, h_sigmas, n_sigma, p, idx, nullptr, sws, st);
-        if (rc) return FD4_ERR_CUDA;
-        if (d_sigma_idx) {
-            if (cudaMemcpy2DAsync(d_sigma_idx, (size_t)pitch, idx, (size_t)pitch, (size_t)w, (size_t)h,
-                                  cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-                return FD4_ERR_CUDA;
+// ---------------------------------------------------------------------------
+// Batches.  Workspace: [descriptor table | max S^2 words | per image:
+// sigma* plane, tensor plane, scratch (selection planes / N field / FED plane)].
+
+static size_t scratch_bytes(int h, int pitch, int n_sigma)
+{
+    size_t sc = 2 * (size_t)n_sigma * plane_bytes(h, pitch, 4);
+    if (plane_bytes(h, pitch, 16) > sc) sc = plane_bytes(h, pitch, 16);
+    return sc;
+}
+
+static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vector<ImgDesc> *descs, char *ws,
+                           HostBatch *B)
+{
+    size_t off = align_up(sizeof(ImgDesc) * (size_t)n, 256);
+    const size_t ms_off = off;
+    off += align_up(sizeof(unsigned) * (size_t)n, 256);
+    int t0[kShapes] = {0, 0, 0, 0, 0};
+    if (descs) descs->resize(n);
+    for (int i = 0; i < n; ++i) {
+        const fd4_image &im = imgs[i];
+        const size_t pb = plane_bytes(im.h, im.pitch, 4);
+        const size_t o_idx = off, o_ten = o_idx + plane_bytes(im.h, im.pitch, 1);
+        const size_t o_sc = o_ten + plane_bytes(im.h, im.pitch, 16);
+        off = o_sc + scratch_bytes(im.h, im.pitch, n_sigma);
+        if (!descs) continue;
+        ImgDesc &d = (*descs)[i];
+        d = ImgDesc{};
+        d.in = im.d_in;
+        d.u = im.d_out;
+        d.tmp = (float *)(ws + o_sc);
+        d.vp = (float *)(ws + o_sc);
+        d.s2 = (float *)(ws + o_sc + (size_t)n_sigma * pb);
+        d.nfield = (float4 *)(ws + o_sc);
+        d.tensor = (float4 *)(ws + o_ten);
+        d.idx = im.d_sigma_idx ? im.d_sigma_idx : (uint8_t *)(ws + o_idx);
+        d.vmax = nullptr;
+        d.max_s2 = (unsigned *)(ws + ms_off) + i;
+        d.plane = pb / 4;
+        d.w = im.w;
+        d.h = im.h;
+        d.pitch = im.pitch;
+        for (int s = 0; s < kShapes; ++s) {
+            d.t0[s] = t0[s];
+            t0[s] += tiles_of(im.w, im.h, s);
         }
     }
-    if (d_out != d_in) {
-        if (cudaMemcpy2DAsync(d_out, (size_t)pitch * 4, d_in, (size_t)pitch * 4, (size_t)w * 4, (size_t)h,
-                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-            return FD4_ERR_CUDA;
+    if (B) {
+        B->I.table = (const ImgDesc *)ws;
+        B->I.n = n;
+        B->I.tiles = 0;
+        B->I.one = ImgDesc{};
+        for (int s = 0; s < kShapes; ++s) B->tiles[s] = t0[s];
+        B->max_s2 = (unsigned *)(ws + ms_off);
+        B->n_max_s2 = n;
     }
-    for (int k = 0; k < M; ++k) {
-        if (launch_tensor(d_out, w, h, pitch, idx, h_sigmas, n_sigma, p, tensor, sws, st)) return FD4_ERR_CUDA;
-        if (launch_fed_cycle(d_out, w, h, pitch, tensor, tau.data(), n, p.boundary, sws, st)) return FD4_ERR_CUDA;
+    return off;
+}
+
+extern "C" size_t fd4_batch_workspace_bytes(const fd4_image *h_imgs, int n_images, int n_sigma)
+{
+    if (!h_imgs || n_images < 1 || n_images > FD4_MAX_BATCH || n_sigma < 0) return 0;
+    for (int i = 0; i < n_images; ++i)
+        if (h_imgs[i].w < 1 || h_imgs[i].h < 1 || h_imgs[i].pitch < h_imgs[i].w) return 0;
+    return batch_layout(h_imgs, n_images, n_sigma, nullptr, nullptr, nullptr);
+}
+
+// Validates a batch call and computes its step sizes.
+static int batch_prepare(const fd4_image *imgs, int n_images, const float *h_sigmas, int n_sigma,
+                         const fd4_params &p, double T, int M, int n_in, int sigma_given, const void *d_ws,
+                         size_t ws_bytes, std::vector<double> &tau, int &n)
+{
+    int rc;
+    if (!imgs || n_images < 1 || n_images > FD4_MAX_BATCH) return FD4_ERR_BAD_ARG;
+    for (int i = 0; i < n_images; ++i) {
+        const fd4_image &im = imgs[i];
+        if ((rc = check_image(im.d_in, im.w, im.h, im.pitch)) != FD4_OK) return rc;
+        if ((rc = check_image(im.d_out, im.w, im.h, im.pitch)) != FD4_OK) return rc;
+        if (sigma_given && !im.d_sigma_idx) return FD4_ERR_BAD_ARG;
     }
+    if ((rc = check_sigmas(h_sigmas, n_sigma)) != FD4_OK) return rc;
+    if ((rc = check_params(p)) != FD4_OK) return rc;
+    if ((rc = check_steps(p)) != FD4_OK) return rc;
+    if ((rc = ws_ok(d_ws, ws_bytes, fd4_batch_workspace_bytes(imgs, n_images, n_sigma))) != FD4_OK) return rc;
+    tau.assign(FD4_MAX_FED_STEPS, 0.0);
+    return fd4_fed_taus(T, M, p.tau_max, n_in, p.kappa, tau.data(), FD4_MAX_FED_STEPS, &n, nullptr);
+}
+
+static int enqueue_batch(const fd4_image *imgs, int n_images, const float *h_sigmas, int n_sigma,
+                         const fd4_params &p, const double *tau, int n, int M, int sigma_given, void *d_ws,
+                         cudaStream_t st, int stages = FD4_STAGES_ALL)
+{
+    std::vector<ImgDesc> descs;
+    HostBatch B;
+    batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B);
+    if (launch_put_descs(descs.data(), n_images, (ImgDesc *)d_ws, st)) return FD4_ERR_CUDA;
+    return enqueue_filter(B, h_sigmas, n_sigma, p, tau, n, M, sigma_given, st, stages);
+}
+
+extern "C" int fd4_filter_batched(const fd4_image *h_imgs, int n_images, const float *h_sigmas, int n_sigma,
+                                  const fd4_params *params, double T, int M, int n_in, int sigma_given,
+                                  void *d_ws, size_t ws_bytes, fd4_stream_t stream)
+{
+    fd4_params p;
+    resolve_params(params, &p);
+    std::vector<double> tau;
+    int n = 0;
+    int rc = batch_prepare(h_imgs, n_images, h_sigmas, n_sigma, p, T, M, n_in, sigma_given, d_ws, ws_bytes, tau, n);
+    if (rc != FD4_OK) return rc;
+    return enqueue_batch(h_imgs, n_images, h_sigmas, n_sigma, p, tau.data(), n, M, sigma_given, d_ws,
+                         (cudaStream_t)stream);
+}
+
+struct fd4_graph_st {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+extern "C" int fd4_graph_create(const fd4_image *h_imgs, int n_images, const float *h_sigmas, int n_sigma,
+                                const fd4_params *params, double T, int M, int n_in, int sigma_given,
+                                int stages, void *d_ws, size_t ws_bytes, fd4_graph *out)
+{
+    if (!out || stages <= 0 || stages > FD4_STAGES_ALL) return FD4_ERR_BAD_ARG;
+    *out = nullptr;
+    fd4_params p;
+    resolve_params(params, &p);
+    std::vector<double> tau;
+    int n = 0;
+    int rc = batch_prepare(h_imgs, n_images, h_sigmas, n_sigma, p, T, M, n_in, sigma_given, d_ws, ws_bytes, tau, n);
+    if (rc != FD4_OK) return rc;
+    // kernel attributes are set outside the capture
+    if (prepare_scale_kernels() || prepare_fed_kernels()) return FD4_ERR_CUDA;
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return FD4_ERR_CUDA;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaStreamDestroy(s);
+        return FD4_ERR_CUDA;
+    }
+    rc = enqueue_batch(h_imgs, n_images, h_sigmas, n_sigma, p, tau.data(), n, M, sigma_given, d_ws, s, stages);
+    const cudaError_t ec = cudaStreamEndCapture(s, &g);
+    cudaStreamDestroy(s);
+    if (rc != FD4_OK || ec != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        return rc != FD4_OK ? rc : FD4_ERR_CUDA;
+    }
+    cudaGraphExec_t e = nullptr;
+    if (cudaGraphInstantiate(&e, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return FD4_ERR_CUDA;
+    }
+    fd4_graph_st *gs = new fd4_graph_st{g, e};
+    *out = gs;
     return FD4_OK;
+}
+
+extern "C" int fd4_graph_launch(fd4_graph g, fd4_stream_t stream)
+{
+    if (!g) return FD4_ERR_BAD_ARG;
+    return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? FD4_OK : FD4_ERR_CUDA;
+}
+
+extern "C" int fd4_graph_destroy(fd4_graph g)
+{
+    if (!g) return FD4_ERR_BAD_ARG;
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
+    return FD4_OK;
+}
+
+extern "C" int fd4_autotune_batched(const fd4_image *h_imgs, int n_images, const float *h_sigmas, int n_sigma,
+                                    const fd4_params *params, double T, int M, int n_in, void *d_ws,
+                                    size_t ws_bytes, fd4_stream_t stream, int *best_steps_per_launch,
+                                    float *times_ms)
+{
+    if (!best_steps_per_launch) return FD4_ERR_BAD_ARG;
+    fd4_params p;
+    resolve_params(params, &p);
+    std::vector<double> tau;
+    int n = 0;
+    int rc = batch_prepare(h_imgs, n_images, h_sigmas, n_sigma, p, T, M, n_in, 0, d_ws, ws_bytes, tau, n);
+    if (rc != FD4_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<ImgDesc> descs;
+    HostBatch B;
+    batch_layout(h_imgs, n_images, n_sigma, &descs, (char *)d_ws, &B);
+    if (launch_put_descs(descs.data(), n_images, (ImgDesc *)d_ws, st)) return FD4_ERR_CUDA;
+    if (launch_select_batch(B, h_sigmas, n_sigma, p, st) || launch_copy_in_batch(B, st) ||
+        launch_tensor_batch(B, h_sigmas, n_sigma, p, st))
+        return FD4_ERR_CUDA;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return FD4_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return FD4_ERR_CUDA;
+    }
+    float best = 0.0f;
+    int arg = 2;
+    rc = FD4_OK;
+    for (int S = 1; S <= 4 && rc == FD4_OK; ++S) {
+        // one untimed pass, then the timed one
+        if (launch_fed_batch(B, tau.data(), n, p.boundary, S, st) || cudaEventRecord(e0, st) != cudaSuccess ||
+            launch_fed_batch(B, tau.data(), n, p.boundary, S, st) || cudaEventRecord(e1, st) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = FD4_ERR_CUDA;
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (times_ms) times_ms[S - 1] = ms;
+        if (S == 1 || ms < best) {
+            best = ms;
+            arg = S;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == FD4_OK) *best_steps_per_launch = arg;
+    return rc;
 }

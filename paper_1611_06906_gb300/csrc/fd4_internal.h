@@ -9,7 +9,7 @@
 
 namespace fd4 {
 
-constexpr int kMaxRadius = 64;              // ceil(4 * FD4_MAX_SIGMA)
+constexpr int kMaxRadius = 48;              // ceil(4 * FD4_MAX_SIGMA)
 constexpr int kMaxTaps = 2 * kMaxRadius + 1;
 constexpr int kMaxRhoRadius = 8;            // G_rho radius limit (rho <= 2)
 constexpr size_t kHeaderBytes = 256;        // status word, max S^2, spare
@@ -36,6 +36,80 @@ struct WsHeader {
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// ---------------------------------------------------------------------------
+// Batches.  Every stage kernel walks a flat list of tiles that spans all images
+// of a batch (a persistent grid striding over the list); the tile shape
+// depends on the kernel.
+enum TileShape { SHAPE_SWEEP = 0, SHAPE_SMALL = 1, SHAPE_FUSE2 = 2, SHAPE_FUSE3 = 3, SHAPE_FUSE4 = 4, kShapes = 5 };
+
+__host__ __device__ inline int shape_tx(int s) { return s == SHAPE_SWEEP ? 32 : s == SHAPE_SMALL ? 32 : 64 - 4 * s; }
+__host__ __device__ inline int shape_ty(int s) { return s == SHAPE_SWEEP ? 64 : s == SHAPE_SMALL ? 8 : 32 - 4 * s; }
+
+// Per-image pointers and sizes of one batch entry (planes laid out by the host).
+struct ImgDesc {
+    const float *in;     // image read by scale selection
+    float *u;            // image filtered in place (tensor build input, FED state)
+    float *tmp;          // FED ping-pong plane
+    float *vp, *s2;      // selection planes, n_sigma each, `plane` floats apart
+    float4 *nfield;      // normalised Hessian (Nxx, Nxy, Nyy, 0)
+    float4 *tensor;      // (cos 2t, sin 2t, mu1, mu2)
+    uint8_t *idx;        // selected scale index
+    float *vmax;         // nullable
+    unsigned *max_s2;    // max S^2 of the image (float bits)
+    size_t plane;
+    int w, h, pitch;
+    int t0[kShapes];     // first flat tile of this image, per tile shape
+};
+
+// A batch: a device table of n descriptors, or (table == nullptr) one inline.
+struct Imgs {
+    const ImgDesc *table;
+    int n;
+    int tiles;           // total tiles for the launched kernel's shape
+    ImgDesc one;
+};
+
+inline int tiles_of(int w, int h, int shape)
+{
+    return ((w + shape_tx(shape) - 1) / shape_tx(shape)) * ((h + shape_ty(shape) - 1) / shape_ty(shape));
+}
+
+// Fills d.t0 for a single image and returns the inline batch for `shape`.
+inline Imgs single(const ImgDesc &d0, int shape)
+{
+    Imgs I;
+    I.table = nullptr;
+    I.n = 1;
+    I.one = d0;
+    for (int s = 0; s < kShapes; ++s) I.one.t0[s] = 0;
+    I.tiles = tiles_of(d0.w, d0.h, shape);
+    return I;
+}
+
+#ifdef __CUDACC__
+// Thread 0 of a block: the descriptor of flat tile t (shape `shape`) and the
+// tile's index within its image.
+__device__ __forceinline__ void find_tile(const Imgs &I, int shape, int t, ImgDesc &out, int &local)
+{
+    if (I.table == nullptr) {
+        out = I.one;
+        local = t;
+        return;
+    }
+    int lo = 0, hi = I.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (I.table[mid].t0[shape] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    out = I.table[lo];
+    local = t - out.t0[shape];
+}
+#endif
+
+// Persistent grid size for a kernel: resident blocks per SM x SMs, capped by the tiles.
+int persistent_grid(const void *kernel, int threads, size_t smem, int tiles);
+
 // Host helpers (fd4_host.cpp).
 int gauss_taps(double sigma, GaussTaps *out);            // radius ceil(4 sigma)
 int rho_taps(double rho, RhoTaps *out);
@@ -50,7 +124,43 @@ size_t ws_tensor_bytes(int h, int pitch);
 size_t ws_fed_bytes(int h, int pitch);
 size_t ws_filter_bytes(int h, int pitch, int n_sigma);
 
-// Launch wrappers (fd4_scale.cu, fd4_fed.cu); they return cudaError_t as int.
+// Host view of a batch: the device-visible batch, the total tile count per
+// tile shape, and the images' max-S^2 words (contiguous) cleared before selection.
+struct HostBatch {
+    Imgs I;
+    int tiles[kShapes];
+    unsigned *max_s2;
+    int n_max_s2;
+};
+
+// One image: inline descriptor.
+inline HostBatch single_batch(const ImgDesc &d)
+{
+    HostBatch B;
+    B.I = single(d, SHAPE_SWEEP);
+    for (int s = 0; s < kShapes; ++s) B.tiles[s] = tiles_of(d.w, d.h, s);
+    B.max_s2 = d.max_s2;
+    B.n_max_s2 = 1;
+    return B;
+}
+
+// Stage launchers over a batch (fd4_scale.cu, fd4_fed.cu); nonzero on a CUDA error.
+int launch_select_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
+                        cudaStream_t st);
+int launch_tensor_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
+                        cudaStream_t st);
+// n FED steps on every image; the result ends in ImgDesc::u.  steps_per_launch:
+// 1 = one launch per step (k_fed_step), 2..4 = k_fed_fused<S>.
+int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundary, int steps_per_launch,
+                     cudaStream_t st);
+// Sets the shared-memory attributes of every kernel (call before stream capture).
+int prepare_scale_kernels();
+int prepare_fed_kernels();
+int default_steps_per_launch();
+int launch_copy_in_batch(const HostBatch &B, cudaStream_t st);
+int launch_put_descs(const ImgDesc *h_descs, int n, ImgDesc *d_table, cudaStream_t st);
+
+// Single-image launchers used by the per-image entry points.
 int launch_select(const float *d_img, int w, int h, int pitch, const float *h_sigmas,
                   int n_sigma, const fd4_params &p, uint8_t *d_idx, float *d_vmax,
                   char *ws, cudaStream_t st);

@@ -1,13 +1,16 @@
 // Gaussian scale space, vesselness scale selection and the diffusion-tensor
 // build (Sec. 3.1 Eq. 6, Sec. 3.2 Eq. 7-8, Sec. 3.3 Eq. 9).
 //
-// One tile kernel computes the derivatives of u_sigma = u * G_sigma for a
-// 32 x 64 output tile: the tile plus a mirror-extended halo of r = ceil(4 sigma)
-// pixels is staged in shared memory, a row pass applies the smoothing, first-
-// and second-derivative taps along x, and a column pass combines them into
-// u_x, u_y, u_xx, u_xy, u_yy.  Both passes keep a sliding register window so
-// that each shared-memory load feeds eight outputs.  The work is FP32 FMA
-// bound (about 2 (2r+1) (3 + 5) FMAs per pixel and scale).
+// k_scale_sweep computes the derivatives of u_sigma = u * G_sigma for every
+// scale of the set on a 32 x 64 output tile in one block: the tile plus a
+// mirror-extended halo of the largest radius is staged in shared memory once,
+// then for each scale a row pass applies the smoothing, first- and
+// second-derivative taps along x and a column pass combines them into
+// u_x, u_y, u_xx, u_xy, u_yy.  Both passes keep register windows that are
+// refilled four taps at a time (one 16-byte shared load in the row pass), so
+// the inner loops are almost pure FMA.  The work is FP32-FMA bound: about
+// 3 (2R+4)(1 + (2R+8)/64) + 5 (2R+4) FMAs per pixel and scale, R = ceil(4 sigma)
+// rounded up to a multiple of 4.
 #include <cstdint>
 
 #include "fd4_internal.h"
@@ -17,25 +20,47 @@ namespace {
 
 constexpr int TX = 32;        // output tile width
 constexpr int TY = 64;        // output tile height
-constexpr int VR = 8;         // row pass: outputs per thread along x
-constexpr int VC = 8;         // column pass: outputs per thread along y
+constexpr int V = 8;          // outputs per thread in both passes
 constexpr int NT = 256;       // threads per block
 constexpr int RS = TX + 1;    // row-pass output stride (conflict-free column reads)
+constexpr int kMaxSweep = 16; // scales per launch
+constexpr int kSweepFloats = kMaxSweep * 3 * (2 * kMaxRadius + 4);
 
-static_assert(TX / VR * 8 == 32, "row pass maps 8 rows x 4 segments to a warp");
-static_assert(TX * (TY / VC) == NT, "column pass: one unit per thread");
+static_assert(TX * (TY / V) == NT, "column pass: one unit per thread");
 
-__host__ __device__ inline int in_stride(int r)
+// Taps of up to kMaxSweep scales.  Scale s uses the padded radius R[s] (a
+// multiple of 4, >= ceil(4 sigma)); its three kernels w0, w1, w2 (smoothing,
+// first and second derivative, correlation weights) each hold L = 2R+4
+// entries at w[off[s] + k*L + i], entry i being the tap at offset i - R (zero
+// beyond the true radius).
+struct SweepTaps {
+    int K;                    // scales in this launch
+    int K_total;              // size of the whole scale set
+    int s0;                   // index of this launch's first scale in the set
+    int Rmax;                 // max R[s]
+    int R[kMaxSweep];
+    int off[kMaxSweep];
+    float scale4[kMaxSweep];  // sigma^(4 gamma)
+    int wfloats;              // used entries of w (multiple of 4)
+    float w[kSweepFloats];
+};
+
+__host__ __device__ inline int sweep_in_stride(int Rmax)
 {
-    // >= TX + 2r and == 1 mod 32: the 8 rows a warp touches in the row pass
-    // start in 8 different banks.
-    return ((TX + 2 * r - 1 + 31) / 32) * 32 + 1;
+    // >= TX + 2 Rmax + 4 (the row pass reads up to column 35 + 2 Rmax) and
+    // == 4 mod 8: 16-byte aligned rows, and the 16-byte loads of two adjacent
+    // rows (one quarter-warp phase) fall in different bank quads.
+    const int need = TX + 2 * Rmax + 4;
+    return ((need - 4 + 7) / 8) * 8 + 4;
 }
 
-__host__ __device__ inline size_t tile_smem_bytes(int r)
+// the column pass reads staged rows up to 67 + 2 Rmax
+__host__ __device__ inline int sweep_rows(int Rmax) { return TY + 2 * Rmax + 4; }
+
+__host__ __device__ inline size_t sweep_smem_bytes(int Rmax, int wfloats)
 {
-    const int rows = TY + 2 * r;
-    return sizeof(float) * ((size_t)3 * (2 * r + 1) + (size_t)rows * in_stride(r) + (size_t)3 * rows * RS);
+    const int rows = sweep_rows(Rmax);
+    return sizeof(float) * ((size_t)wfloats + (size_t)rows * sweep_in_stride(Rmax) + (size_t)3 * rows * RS);
 }
 
 __device__ __forceinline__ int mirror(int i, int n)
@@ -55,233 +80,255 @@ __device__ __forceinline__ float det2_sym(float a, float b, float d)
     return fmaf(a, d, -bb) + err;
 }
 
-struct SelectOut {
-    float *vp;          // K planes: exp(-R_B^2/(2 beta^2)), 0 for the wrong polarity
-    float *s2;          // K planes: S^2
-    size_t plane;       // elements per plane
-    int s;              // scale index
-    float scale4;       // sigma^(4 gamma)
-    float inv2b2;       // 1 / (2 beta^2)
-    int mode;
-    unsigned *max_s2;   // float bits
-};
-
-struct TensorOut {
-    const uint8_t *idx;
-    float4 *nfield;     // (Nxx, Nxy, Nyy, 0)
-    int s;
-    int grad_sq;
-};
-
 enum { OUT_SELECT = 0, OUT_TENSOR = 1 };
 
-template <int OUT>
-__global__ void __launch_bounds__(NT) k_gauss_tile(const float *__restrict__ img, int w, int h, int pitch,
-                                                   GaussTaps taps, SelectOut so, TensorOut to)
+// Column pass of one field over the 12-row register window: acc_a += wa * field
+// (and acc_b += wb * field when TWO), V outputs down one column.
+template <bool TWO>
+__device__ __forceinline__ void column_pass(const float *src, const float *wa, const float *wb, int nch,
+                                            float (&acc_a)[V], float (&acc_b)[V])
 {
-    extern __shared__ float smem[];
-    const int r = taps.r;
-    const int nt = 2 * r + 1;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-    if (OUT == OUT_TENSOR) {
-        // only tiles holding a pixel whose selected scale is this one do work
-        int any = 0;
-        for (int i = tid; i < TX * TY; i += NT) {
-            const int x = x0 + (i & (TX - 1)), y = y0 + i / TX;
-            if (x < w && y < h && to.idx[(size_t)y * pitch + x] == to.s) any = 1;
-        }
-        if (!__syncthreads_or(any)) return;
-    }
-
-    const int S = in_stride(r);
-    const int rows = TY + 2 * r;
-    float *wt = smem;                    // w0 | w1 | w2, nt each
-    float *tin = wt + 3 * nt;            // rows x S input with halo
-    float *trow = tin + rows * S;        // 3 fields x rows x RS
-    for (int i = tid; i < nt; i += NT) {
-        wt[i] = taps.w0[i];
-        wt[nt + i] = taps.w1[i];
-        wt[2 * nt + i] = taps.w2[i];
-    }
-    const int in_w = TX + 2 * r;
-    for (int ry = warp; ry < rows; ry += NT / 32) {
-        const float *src = img + (size_t)mirror(y0 - r + ry, h) * pitch;
-        for (int rx = lane; rx < in_w; rx += 32)
-            tin[ry * S + rx] = __ldg(src + mirror(x0 - r + rx, w));
-    }
-    __syncthreads();
-
-    // Row pass: three filtered fields along x for every staged row.
-    for (int u = tid; u < rows * (TX / VR); u += NT) {
-        const int ry = u >> 2, xo = (u & 3) * VR;
-        const float *src = tin + ry * S + xo;
-        float a0[VR], a1[VR], a2[VR], win[VR];
+    float win[V + 4];
 #pragma unroll
-        for (int j = 0; j < VR; ++j) {
-            a0[j] = a1[j] = a2[j] = 0.0f;
-            win[j] = src[j];
-        }
-        for (int k = 0; k < nt; ++k) {
-            const float c0 = wt[k], c1 = wt[nt + k], c2 = wt[2 * nt + k];
+    for (int q = 0; q < V + 4; ++q) win[q] = src[q * RS];
 #pragma unroll
-            for (int j = 0; j < VR; ++j) {
-                a0[j] = fmaf(c0, win[j], a0[j]);
-                a1[j] = fmaf(c1, win[j], a1[j]);
-                a2[j] = fmaf(c2, win[j], a2[j]);
+    for (int j = 0; j < V; ++j) {
+        acc_a[j] = 0.0f;
+        if (TWO) acc_b[j] = 0.0f;
+    }
+    for (int ch = 0; ch < nch; ++ch) {
+        const float4 A = *reinterpret_cast<const float4 *>(wa + 4 * ch);
+        float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (TWO) B = *reinterpret_cast<const float4 *>(wb + 4 * ch);
+        const float av[4] = {A.x, A.y, A.z, A.w};
+        const float bv[4] = {B.x, B.y, B.z, B.w};
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                acc_a[j] = fmaf(av[ii], win[j + ii], acc_a[j]);
+                if (TWO) acc_b[j] = fmaf(bv[ii], win[j + ii], acc_b[j]);
             }
-#pragma unroll
-            for (int j = 0; j < VR - 1; ++j) win[j] = win[j + 1];
-            if (k + 1 < nt) win[VR - 1] = src[VR + k];
         }
-        float *d0 = trow + ry * RS + xo;
+        if (ch + 1 < nch) {
 #pragma unroll
-        for (int j = 0; j < VR; ++j) {
-            d0[j] = a0[j];
-            d0[rows * RS + j] = a1[j];
-            d0[2 * rows * RS + j] = a2[j];
-        }
-    }
-    __syncthreads();
-
-    // Column pass: thread owns column ox, rows oy0 .. oy0+VC-1 of the tile.
-    const int ox = tid & 31, oy0 = (tid >> 5) * VC;
-    float uxx[VC], uxy[VC], uyy[VC], ux[VC], uy[VC];
-    {   // field 2 (second derivative along x) smoothed along y -> u_xx
-        const float *src = trow + 2 * rows * RS + oy0 * RS + ox;
-        float win[VC];
+            for (int q = 0; q < V; ++q) win[q] = win[q + 4];
 #pragma unroll
-        for (int j = 0; j < VC; ++j) {
-            uxx[j] = 0.0f;
-            win[j] = src[j * RS];
-        }
-        for (int k = 0; k < nt; ++k) {
-            const float c0 = wt[k];
-#pragma unroll
-            for (int j = 0; j < VC; ++j) uxx[j] = fmaf(c0, win[j], uxx[j]);
-#pragma unroll
-            for (int j = 0; j < VC - 1; ++j) win[j] = win[j + 1];
-            if (k + 1 < nt) win[VC - 1] = src[(VC + k) * RS];
-        }
-    }
-    {   // field 1 (first derivative along x): smoothed -> u_x, differentiated -> u_xy
-        const float *src = trow + rows * RS + oy0 * RS + ox;
-        float win[VC];
-#pragma unroll
-        for (int j = 0; j < VC; ++j) {
-            ux[j] = uxy[j] = 0.0f;
-            win[j] = src[j * RS];
-        }
-        for (int k = 0; k < nt; ++k) {
-            const float c0 = wt[k], c1 = wt[nt + k];
-#pragma unroll
-            for (int j = 0; j < VC; ++j) {
-                ux[j] = fmaf(c0, win[j], ux[j]);
-                uxy[j] = fmaf(c1, win[j], uxy[j]);
-            }
-#pragma unroll
-            for (int j = 0; j < VC - 1; ++j) win[j] = win[j + 1];
-            if (k + 1 < nt) win[VC - 1] = src[(VC + k) * RS];
-        }
-    }
-    {   // field 0 (smoothed along x): first derivative -> u_y, second -> u_yy
-        const float *src = trow + oy0 * RS + ox;
-        float win[VC];
-#pragma unroll
-        for (int j = 0; j < VC; ++j) {
-            uy[j] = uyy[j] = 0.0f;
-            win[j] = src[j * RS];
-        }
-        for (int k = 0; k < nt; ++k) {
-            const float c1 = wt[nt + k], c2 = wt[2 * nt + k];
-#pragma unroll
-            for (int j = 0; j < VC; ++j) {
-                uy[j] = fmaf(c1, win[j], uy[j]);
-                uyy[j] = fmaf(c2, win[j], uyy[j]);
-            }
-#pragma unroll
-            for (int j = 0; j < VC - 1; ++j) win[j] = win[j + 1];
-            if (k + 1 < nt) win[VC - 1] = src[(VC + k) * RS];
-        }
-    }
-
-    const int gx = x0 + ox;
-    float bmax = 0.0f;
-#pragma unroll
-    for (int j = 0; j < VC; ++j) {
-        const int gy = y0 + oy0 + j;
-        if (gx >= w || gy >= h) continue;
-        const size_t p = (size_t)gy * pitch + gx;
-        const float a = uxx[j], b = uxy[j], d = uyy[j];
-        if (OUT == OUT_SELECT) {
-            // eigenvalues of H (the sigma^(2 gamma) factor cancels in R_B and
-            // the sign test; S^2 picks it up as sigma^(4 gamma))
-            const float m = 0.5f * (a + d);
-            const float rr = hypotf(0.5f * (a - d), b);
-            const float far = m > 0.0f ? m + rr : m - rr;  // larger magnitude; ties -> negative
-            float vp = 0.0f;
-            const bool wrong = (so.mode == FD4_RIDGE && far > 0.0f) || (so.mode == FD4_VALLEY && far < 0.0f);
-            if (!wrong && far != 0.0f) {
-                const float near = det2_sym(a, b, d) / far;        // cancellation-free
-                const float rb = near / far;
-                vp = expf(-rb * rb * so.inv2b2);
-            }
-            const float s2 = so.scale4 * fmaf(a, a, fmaf(2.0f * b, b, d * d));
-            so.vp[so.s * so.plane + p] = vp;
-            so.s2[so.s * so.plane + p] = s2;
-            bmax = fmaxf(bmax, s2);
-        } else {
-            if (to.idx[p] != to.s) continue;
-            const float g2 = fmaf(ux[j], ux[j], uy[j] * uy[j]);
-            const float g = to.grad_sq ? g2 : sqrtf(g2);
-            const float f = 1.0f / sqrtf(1.0f + g);
-            to.nfield[p] = make_float4(f * a, f * b, f * d, 0.0f);
-        }
-    }
-    if (OUT == OUT_SELECT) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-        __shared__ float wmax[NT / 32];
-        if (lane == 0) wmax[warp] = bmax;
-        __syncthreads();
-        if (tid == 0) {
-            float m = wmax[0];
-            for (int i = 1; i < NT / 32; ++i) m = fmaxf(m, wmax[i]);
-            atomicMax(so.max_s2, __float_as_uint(m));
+            for (int q = 0; q < 4; ++q) win[V + q] = src[(4 * ch + V + 4 + q) * RS];
         }
     }
 }
 
-// Second selection pass: V = vp (1 - exp(-S^2 / (2 c^2))) per scale, argmax with
-// ties to the smaller scale (strict comparison in increasing sigma order).
-__global__ void k_select_argmax(const float *__restrict__ vp, const float *__restrict__ s2, size_t plane,
-                                int K, int w, int h, int pitch, const unsigned *max_s2, float c_user,
-                                uint8_t *idx, float *vmax)
+template <int OUT>
+__global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, float inv2b2, int mode, int grad_sq)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= w || y >= h) return;
-    float k2;  // 1 / (2 c^2)
-    if (c_user > 0.0f) {
-        k2 = 0.5f / (c_user * c_user);
-    } else {
-        const float m = __uint_as_float(*max_s2);  // max S^2 = (2c)^2
-        k2 = m > 0.0f ? 2.0f / m : 0.0f;
+    extern __shared__ __align__(16) float smem[];
+    __shared__ ImgDesc sd;
+    __shared__ int s_local;
+    __shared__ unsigned present;
+    const int Rmax = taps.Rmax;
+    const int S = sweep_in_stride(Rmax);
+    const int rows = sweep_rows(Rmax);
+    const int in_w = TX + 2 * Rmax + 4;
+    float *wt = smem;                        // taps
+    float *tin = wt + taps.wfloats;          // rows x S staged input
+    float *trow = tin + rows * S;            // 3 fields x rows x RS
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < taps.wfloats; i += NT) wt[i] = taps.w[i];
+
+    for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
+    __syncthreads();   // the previous tile is done with shared memory
+    if (tid == 0) {
+        find_tile(I, SHAPE_SWEEP, t, sd, s_local);
+        present = 0u;
     }
-    const size_t p = (size_t)y * pitch + x;
-    float best = -1.0f;
-    int arg = 0;
-    for (int s = 0; s < K; ++s) {
-        float v = __ldg(vp + s * plane + p);
-        v = (v > 0.0f && k2 > 0.0f) ? v * -expm1f(-__ldg(s2 + s * plane + p) * k2) : 0.0f;
-        if (v > best) {
-            best = v;
-            arg = s;
+    __syncthreads();
+    const int w = sd.w, h = sd.h, pitch = sd.pitch;
+    const int tiles_x = (w + TX - 1) / TX;
+    const int x0 = (s_local % tiles_x) * TX, y0 = (s_local / tiles_x) * TY;
+    const float *img = OUT == OUT_SELECT ? sd.in : sd.u;
+    for (int ry = warp; ry < rows; ry += NT / 32) {
+        const float *src = img + (size_t)mirror(y0 - Rmax + ry, h) * pitch;
+        for (int rx = lane; rx < in_w; rx += 32) tin[ry * S + rx] = __ldg(src + mirror(x0 - Rmax + rx, w));
+    }
+
+    const int ox = tid & 31, oy0 = (tid >> 5) * V;
+    const int gx = x0 + ox;
+    float nxx[V], nxy[V], nyy[V];
+    int my_idx[V];
+    if (OUT == OUT_TENSOR) {
+        unsigned bits = 0u;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            nxx[j] = nxy[j] = nyy[j] = 0.0f;
+            const int gy = y0 + oy0 + j;
+            my_idx[j] = (gx < w && gy < h) ? (int)sd.idx[(size_t)gy * pitch + gx] : 255;
+            const int local = my_idx[j] - taps.s0;
+            if (local >= 0 && local < taps.K) bits |= 1u << local;
+        }
+        if (bits) atomicOr(&present, bits);
+    }
+    __syncthreads();
+
+    float bmax = 0.0f;
+    for (int s = 0; s < taps.K; ++s) {
+        if (OUT == OUT_TENSOR && !((present >> s) & 1u)) continue;   // block-uniform
+        const int R = taps.R[s];
+        const int L = 2 * R + 4, nch = L / 4;
+        const int off = Rmax - R;
+        const float *w0 = wt + taps.off[s], *w1 = w0 + L, *w2 = w1 + L;
+
+        // Row pass on staged rows [off, off + TY + 2R + 4): three fields along x.
+        const int nrows = TY + 2 * R + 4;
+        for (int u = tid; u < nrows * (TX / V); u += NT) {
+            const int sy = off + (u >> 2), xo = (u & 3) * V;
+            const float *src = tin + sy * S + xo + off;
+            float win[V + 4];
+            {
+                const float4 a = *reinterpret_cast<const float4 *>(src);
+                const float4 b = *reinterpret_cast<const float4 *>(src + 4);
+                const float4 c = *reinterpret_cast<const float4 *>(src + 8);
+                win[0] = a.x; win[1] = a.y; win[2] = a.z; win[3] = a.w;
+                win[4] = b.x; win[5] = b.y; win[6] = b.z; win[7] = b.w;
+                win[8] = c.x; win[9] = c.y; win[10] = c.z; win[11] = c.w;
+            }
+            float a0[V], a1[V], a2[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) a0[j] = a1[j] = a2[j] = 0.0f;
+            for (int ch = 0; ch < nch; ++ch) {
+                const float4 W0 = *reinterpret_cast<const float4 *>(w0 + 4 * ch);
+                const float4 W1 = *reinterpret_cast<const float4 *>(w1 + 4 * ch);
+                const float4 W2 = *reinterpret_cast<const float4 *>(w2 + 4 * ch);
+                const float c0[4] = {W0.x, W0.y, W0.z, W0.w};
+                const float c1[4] = {W1.x, W1.y, W1.z, W1.w};
+                const float c2[4] = {W2.x, W2.y, W2.z, W2.w};
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii) {
+#pragma unroll
+                    for (int j = 0; j < V; ++j) {
+                        a0[j] = fmaf(c0[ii], win[j + ii], a0[j]);
+                        a1[j] = fmaf(c1[ii], win[j + ii], a1[j]);
+                        a2[j] = fmaf(c2[ii], win[j + ii], a2[j]);
+                    }
+                }
+                if (ch + 1 < nch) {
+#pragma unroll
+                    for (int q = 0; q < V; ++q) win[q] = win[q + 4];
+                    const float4 d = *reinterpret_cast<const float4 *>(src + 4 * ch + 12);
+                    win[8] = d.x; win[9] = d.y; win[10] = d.z; win[11] = d.w;
+                }
+            }
+            float *d0 = trow + sy * RS + xo;
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                d0[j] = a0[j];
+                d0[rows * RS + j] = a1[j];
+                d0[2 * rows * RS + j] = a2[j];
+            }
+        }
+        __syncthreads();
+
+        // Column pass: tile column ox, tile rows oy0 .. oy0 + V - 1.
+        const float *col = trow + (oy0 + off) * RS + ox;
+        float uxx[V], uxy[V], uyy[V], ux[V], uy[V];
+        column_pass<false>(col + 2 * rows * RS, w0, w0, nch, uxx, uxx);      // d2/dx2, smoothed in y
+        if (OUT == OUT_TENSOR) {
+            column_pass<true>(col + rows * RS, w0, w1, nch, ux, uxy);        // d/dx: smoothed / d/dy
+            column_pass<true>(col, w1, w2, nch, uy, uyy);                   // smoothed in x: d/dy, d2/dy2
+        } else {
+            column_pass<false>(col + rows * RS, w1, w1, nch, uxy, uxy);
+            column_pass<false>(col, w2, w2, nch, uyy, uyy);
+        }
+        __syncthreads();   // trow is rewritten by the next scale's row pass
+
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const int gy = y0 + oy0 + j;
+            if (gx >= w || gy >= h) continue;
+            const float a = uxx[j], b = uxy[j], d = uyy[j];
+            if (OUT == OUT_SELECT) {
+                // eigenvalues of H (sigma^(2 gamma) cancels in R_B and the sign
+                // test; S^2 picks it up as sigma^(4 gamma))
+                const float m = 0.5f * (a + d);
+                const float rr = hypotf(0.5f * (a - d), b);
+                const float far = m > 0.0f ? m + rr : m - rr;  // larger magnitude; ties -> negative
+                float vp = 0.0f;
+                const bool wrong = (mode == FD4_RIDGE && far > 0.0f) || (mode == FD4_VALLEY && far < 0.0f);
+                if (!wrong && far != 0.0f) {
+                    const float near = det2_sym(a, b, d) / far;  // cancellation-free
+                    const float rb = near / far;
+                    vp = expf(-rb * rb * inv2b2);
+                }
+                const float s2 = taps.scale4[s] * fmaf(a, a, fmaf(2.0f * b, b, d * d));
+                const size_t p = (size_t)gy * pitch + gx;
+                sd.vp[(size_t)(taps.s0 + s) * sd.plane + p] = vp;
+                sd.s2[(size_t)(taps.s0 + s) * sd.plane + p] = s2;
+                bmax = fmaxf(bmax, s2);
+            } else if (my_idx[j] == taps.s0 + s) {
+                const float g2 = fmaf(ux[j], ux[j], uy[j] * uy[j]);
+                const float g = grad_sq ? g2 : sqrtf(g2);
+                const float f = 1.0f / sqrtf(1.0f + g);
+                nxx[j] = f * a;
+                nxy[j] = f * b;
+                nyy[j] = f * d;
+            }
         }
     }
-    idx[p] = (uint8_t)arg;
-    if (vmax) vmax[p] = best;
+
+    if (OUT == OUT_SELECT) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+        if (lane == 0 && bmax > 0.0f) atomicMax(sd.max_s2, __float_as_uint(bmax));
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const int gy = y0 + oy0 + j;
+            if (gx >= w || gy >= h) continue;
+            const int local = my_idx[j] - taps.s0;
+            const bool mine = local >= 0 && local < taps.K;
+            const bool orphan = taps.s0 == 0 && my_idx[j] >= taps.K_total;   // out-of-range index: N = 0
+            if (mine || orphan) sd.nfield[(size_t)gy * pitch + gx] = make_float4(nxx[j], nxy[j], nyy[j], 0.0f);
+        }
+    }
+    }  // tile loop
+}
+
+// Second selection pass: V = vp (1 - exp(-S^2 / (2 c^2))) per scale, argmax with
+// ties to the smaller scale (strict comparison in increasing sigma order).
+// 32 x 8 tiles, one pixel per thread.
+__global__ void __launch_bounds__(256) k_select_argmax(Imgs I, int K, float c_user)
+{
+    __shared__ ImgDesc sd;
+    __shared__ int s_local;
+    const int tid = threadIdx.x;
+    for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
+        __syncthreads();
+        if (tid == 0) find_tile(I, SHAPE_SMALL, t, sd, s_local);
+        __syncthreads();
+        const int tiles_x = (sd.w + 31) / 32;
+        const int x = (s_local % tiles_x) * 32 + (tid & 31), y = (s_local / tiles_x) * 8 + (tid >> 5);
+        if (x >= sd.w || y >= sd.h) continue;
+        float k2;  // 1 / (2 c^2)
+        if (c_user > 0.0f) {
+            k2 = 0.5f / (c_user * c_user);
+        } else {
+            const float m = __uint_as_float(*sd.max_s2);  // max S^2 = (2c)^2
+            k2 = m > 0.0f ? 2.0f / m : 0.0f;
+        }
+        const size_t p = (size_t)y * sd.pitch + x;
+        float best = -1.0f;
+        int arg = 0;
+        for (int s = 0; s < K; ++s) {
+            float v = __ldg(sd.vp + s * sd.plane + p);
+            v = (v > 0.0f && k2 > 0.0f) ? v * -expm1f(-__ldg(sd.s2 + s * sd.plane + p) * k2) : 0.0f;
+            if (v > best) {
+                best = v;
+                arg = s;
+            }
+        }
+        sd.idx[p] = (uint8_t)arg;
+        if (sd.vmax) sd.vmax[p] = best;
+    }
 }
 
 __device__ __forceinline__ float pm_mu(float nu, float lambda, int mode)
@@ -291,144 +338,231 @@ __device__ __forceinline__ float pm_mu(float nu, float lambda, int mode)
     return 1.0f / fmaf(q, q, 1.0f);
 }
 
-constexpr int FX = 32, FY = 8;   // tensor-finish tile
+constexpr int FX = 32, FY = 8;   // tensor-finish tile (SHAPE_SMALL)
 
 // N_rho = G_rho * N (mirror border), closed-form eigen-decomposition and
 // Perona-Malik diffusivities -> (cos 2t, sin 2t, mu1, mu2), e1 for nu1 >= nu2.
-__global__ void __launch_bounds__(FX * FY) k_tensor_finish(const float4 *__restrict__ nf, int w, int h, int pitch,
-                                                            RhoTaps taps, float lambda, int mode, float4 *out)
+__global__ void __launch_bounds__(FX * FY) k_tensor_finish(Imgs I, RhoTaps taps, float lambda, int mode)
 {
     __shared__ float4 sin_[FY + 2 * kMaxRhoRadius][FX + 2 * kMaxRhoRadius];
     __shared__ float4 srow[FY + 2 * kMaxRhoRadius][FX];
+    __shared__ float wr[2 * kMaxRhoRadius + 1];
+    __shared__ ImgDesc sd;
+    __shared__ int s_local;
     const int r = taps.r;
-    const int x0 = blockIdx.x * FX, y0 = blockIdx.y * FY;
     const int tid = threadIdx.x;
+    if (tid <= 2 * r) wr[tid] = taps.w0[tid];
     const int rows = FY + 2 * r, cols = FX + 2 * r;
-    for (int i = tid; i < rows * cols; i += FX * FY) {
-        const int ry = i / cols, rx = i - ry * cols;
-        sin_[ry][rx] = nf[(size_t)mirror(y0 - r + ry, h) * pitch + mirror(x0 - r + rx, w)];
-    }
-    __syncthreads();
-    for (int i = tid; i < rows * FX; i += FX * FY) {
-        const int ry = i / FX, rx = i - ry * FX;
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int k = 0; k <= 2 * r; ++k) {
-            const float c = taps.w0[k];
-            const float4 v = sin_[ry][rx + k];
-            a.x = fmaf(c, v.x, a.x);
-            a.y = fmaf(c, v.y, a.y);
-            a.z = fmaf(c, v.z, a.z);
+    for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
+        __syncthreads();
+        if (tid == 0) find_tile(I, SHAPE_SMALL, t, sd, s_local);
+        __syncthreads();
+        const int w = sd.w, h = sd.h, pitch = sd.pitch;
+        const int tiles_x = (w + FX - 1) / FX;
+        const int x0 = (s_local % tiles_x) * FX, y0 = (s_local / tiles_x) * FY;
+        const float4 *nf = sd.nfield;
+        for (int i = tid; i < rows * cols; i += FX * FY) {
+            const int ry = i / cols, rx = i - ry * cols;
+            sin_[ry][rx] = nf[(size_t)mirror(y0 - r + ry, h) * pitch + mirror(x0 - r + rx, w)];
         }
-        srow[ry][rx] = a;
+        __syncthreads();
+        for (int i = tid; i < rows * FX; i += FX * FY) {
+            const int ry = i / FX, rx = i - ry * FX;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int k = 0; k <= 2 * r; ++k) {
+                const float c = wr[k];
+                const float4 v = sin_[ry][rx + k];
+                a.x = fmaf(c, v.x, a.x);
+                a.y = fmaf(c, v.y, a.y);
+                a.z = fmaf(c, v.z, a.z);
+            }
+            srow[ry][rx] = a;
+        }
+        __syncthreads();
+        const int tx = tid & (FX - 1), ty = tid / FX;
+        const int gx = x0 + tx, gy = y0 + ty;
+        if (gx >= w || gy >= h) continue;
+        float a = 0.f, b = 0.f, d = 0.f;
+        for (int k = 0; k <= 2 * r; ++k) {
+            const float c = wr[k];
+            const float4 v = srow[ty + k][tx];
+            a = fmaf(c, v.x, a);
+            b = fmaf(c, v.y, b);
+            d = fmaf(c, v.z, d);
+        }
+        const float m = 0.5f * (a + d), q = 0.5f * (a - d);
+        const float rr = hypotf(q, b);
+        const float det = det2_sym(a, b, d);
+        float nu1, nu2;
+        if (m > 0.0f) {
+            nu1 = m + rr;
+            nu2 = det / nu1;
+        } else if (m < 0.0f) {
+            nu2 = m - rr;
+            nu1 = det / nu2;
+        } else {
+            nu1 = rr;
+            nu2 = -rr;
+        }
+        float c2 = 1.0f, s2 = 0.0f;
+        if (rr > 0.0f) {
+            c2 = q / rr;
+            s2 = b / rr;
+        }
+        sd.tensor[(size_t)gy * pitch + gx] = make_float4(c2, s2, pm_mu(nu1, lambda, mode), pm_mu(nu2, lambda, mode));
     }
-    __syncthreads();
-    const int tx = tid & (FX - 1), ty = tid / FX;
-    const int gx = x0 + tx, gy = y0 + ty;
-    if (gx >= w || gy >= h) return;
-    float a = 0.f, b = 0.f, d = 0.f;
-    for (int k = 0; k <= 2 * r; ++k) {
-        const float c = taps.w0[k];
-        const float4 v = srow[ty + k][tx];
-        a = fmaf(c, v.x, a);
-        b = fmaf(c, v.y, b);
-        d = fmaf(c, v.z, d);
-    }
-    const float m = 0.5f * (a + d), q = 0.5f * (a - d);
-    const float rr = hypotf(q, b);
-    const float det = det2_sym(a, b, d);
-    float nu1, nu2;
-    if (m > 0.0f) {
-        nu1 = m + rr;
-        nu2 = det / nu1;
-    } else if (m < 0.0f) {
-        nu2 = m - rr;
-        nu1 = det / nu2;
-    } else {
-        nu1 = rr;
-        nu2 = -rr;
-    }
-    float c2 = 1.0f, s2 = 0.0f;
-    if (rr > 0.0f) {
-        c2 = q / rr;
-        s2 = b / rr;
-    }
-    out[(size_t)gy * pitch + gx] = make_float4(c2, s2, pm_mu(nu1, lambda, mode), pm_mu(nu2, lambda, mode));
 }
 
-int set_tile_smem()
+// Opts the sweep kernel into the dynamic shared memory a launch needs.
+int set_sweep_smem(size_t bytes)
 {
-    static int done = -1;
+    static size_t done = 0;
+    static int done_dev = -1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
-    if (done == dev) return 0;
-    const int bytes = (int)tile_smem_bytes(kMaxRadius);
-    if (cudaFuncSetAttribute(k_gauss_tile<OUT_SELECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+    if (done_dev != dev) {
+        done = 0;
+        done_dev = dev;
+    }
+    if (bytes <= done) return 0;
+    if (cudaFuncSetAttribute(k_scale_sweep<OUT_SELECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
         return 1;
-    if (cudaFuncSetAttribute(k_gauss_tile<OUT_TENSOR>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_scale_sweep<OUT_TENSOR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
         return 1;
-    done = dev;
+    done = bytes;
+    return 0;
+}
+
+// Packs the taps of scales [s0, s0 + K) of the set into *t.
+int pack_taps(const float *h_sigmas, int n_sigma, int s0, int K, double gamma, SweepTaps *t)
+{
+    t->K = K;
+    t->K_total = n_sigma;
+    t->s0 = s0;
+    t->Rmax = 0;
+    int off = 0;
+    for (int s = 0; s < K; ++s) {
+        GaussTaps g;
+        if (gauss_taps(h_sigmas[s0 + s], &g) != FD4_OK) return 1;
+        const int R = (g.r + 3) / 4 * 4, L = 2 * R + 4;
+        if (off + 3 * L > kSweepFloats) return 1;
+        t->R[s] = R;
+        t->off[s] = off;
+        t->scale4[s] = (float)pow((double)h_sigmas[s0 + s], 4.0 * gamma);
+        if (R > t->Rmax) t->Rmax = R;
+        const float *src[3] = {g.w0, g.w1, g.w2};
+        for (int k = 0; k < 3; ++k)
+            for (int i = 0; i < L; ++i) {
+                const int o = i - R;  // tap offset
+                t->w[off + k * L + i] = (o >= -g.r && o <= g.r) ? src[k][o + g.r] : 0.0f;
+            }
+        off += 3 * L;
+    }
+    t->wfloats = off;
     return 0;
 }
 
 }  // namespace
 
+int prepare_scale_kernels() { return set_sweep_smem(sweep_smem_bytes(kMaxRadius, kSweepFloats)); }
+
+static int sweep_launch(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p, bool tensor,
+                        cudaStream_t st)
+{
+    thread_local static SweepTaps taps;  // 25 KB: kept off the stack
+    Imgs I = B.I;
+    I.tiles = B.tiles[SHAPE_SWEEP];
+    const float inv2b2 = (float)(1.0 / (2.0 * (double)p.beta * p.beta));
+    for (int s0 = 0; s0 < n_sigma; s0 += kMaxSweep) {
+        const int K = n_sigma - s0 < kMaxSweep ? n_sigma - s0 : kMaxSweep;
+        if (pack_taps(h_sigmas, n_sigma, s0, K, p.gamma, &taps)) return 1;
+        const size_t smem = sweep_smem_bytes(taps.Rmax, taps.wfloats);
+        if (set_sweep_smem(smem)) return 1;
+        if (tensor) {
+            const int grid = persistent_grid((const void *)k_scale_sweep<OUT_TENSOR>, NT, smem, I.tiles);
+            k_scale_sweep<OUT_TENSOR><<<grid, NT, smem, st>>>(I, taps, inv2b2, p.mode, p.grad_norm_squared);
+        } else {
+            const int grid = persistent_grid((const void *)k_scale_sweep<OUT_SELECT>, NT, smem, I.tiles);
+            k_scale_sweep<OUT_SELECT><<<grid, NT, smem, st>>>(I, taps, inv2b2, p.mode, p.grad_norm_squared);
+        }
+    }
+    return cudaGetLastError() != cudaSuccess;
+}
+
+int launch_select_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
+                        cudaStream_t st)
+{
+    if (cudaMemsetAsync(B.max_s2, 0, sizeof(unsigned) * (size_t)B.n_max_s2, st) != cudaSuccess) return 1;
+    if (sweep_launch(B, h_sigmas, n_sigma, p, false, st)) return 1;
+    Imgs I = B.I;
+    I.tiles = B.tiles[SHAPE_SMALL];
+    const int grid = persistent_grid((const void *)k_select_argmax, 256, 0, I.tiles);
+    k_select_argmax<<<grid, 256, 0, st>>>(I, n_sigma, p.c);
+    return cudaGetLastError() != cudaSuccess;
+}
+
+int launch_tensor_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
+                        cudaStream_t st)
+{
+    if (sweep_launch(B, h_sigmas, n_sigma, p, true, st)) return 1;
+    RhoTaps rt;
+    if (rho_taps(p.rho, &rt) != FD4_OK) return 1;
+    Imgs I = B.I;
+    I.tiles = B.tiles[SHAPE_SMALL];
+    const int grid = persistent_grid((const void *)k_tensor_finish, FX * FY, 0, I.tiles);
+    k_tensor_finish<<<grid, FX * FY, 0, st>>>(I, rt, p.lambda, p.mode);
+    return cudaGetLastError() != cudaSuccess;
+}
+
+// Single-image stages: workspace [header | planes], descriptor passed inline.
 int launch_select(const float *d_img, int w, int h, int pitch, const float *h_sigmas, int n_sigma,
                   const fd4_params &p, uint8_t *d_idx, float *d_vmax, char *ws, cudaStream_t st)
 {
-    if (set_tile_smem()) return 1;
     WsHeader *hdr = (WsHeader *)ws;
-    const size_t plane = (size_t)h * pitch;
     const size_t pb = plane_bytes(h, pitch, 4);
-    float *vp = (float *)(ws + kHeaderBytes);
-    float *s2 = (float *)(ws + kHeaderBytes + (size_t)n_sigma * pb);
-    const size_t pstride = pb / 4;  // plane stride in floats (>= plane)
-    if (cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st) != cudaSuccess) return 1;
-    const dim3 grid((w + TX - 1) / TX, (h + TY - 1) / TY);
-    TensorOut to{};
-    for (int s = 0; s < n_sigma; ++s) {
-        GaussTaps taps;
-        if (gauss_taps(h_sigmas[s], &taps) != FD4_OK) return 1;
-        SelectOut so;
-        so.vp = vp;
-        so.s2 = s2;
-        so.plane = pstride;
-        so.s = s;
-        so.scale4 = (float)pow((double)h_sigmas[s], 4.0 * p.gamma);
-        so.inv2b2 = (float)(1.0 / (2.0 * (double)p.beta * p.beta));
-        so.mode = p.mode;
-        so.max_s2 = &hdr->max_s2;
-        k_gauss_tile<OUT_SELECT><<<grid, NT, tile_smem_bytes(taps.r), st>>>(d_img, w, h, pitch, taps, so, to);
-    }
-    (void)plane;
-    k_select_argmax<<<dim3((w + 127) / 128, h), 128, 0, st>>>(vp, s2, pstride, n_sigma, w, h, pitch,
-                                                             &hdr->max_s2, p.c, d_idx, d_vmax);
-    return cudaGetLastError() != cudaSuccess;
+    ImgDesc d{};
+    d.in = d_img;
+    d.vp = (float *)(ws + kHeaderBytes);
+    d.s2 = (float *)(ws + kHeaderBytes + (size_t)n_sigma * pb);
+    d.plane = pb / 4;
+    d.idx = d_idx;
+    d.vmax = d_vmax;
+    d.max_s2 = &hdr->max_s2;
+    d.w = w;
+    d.h = h;
+    d.pitch = pitch;
+    return launch_select_batch(single_batch(d), h_sigmas, n_sigma, p, st);
 }
 
 int launch_tensor(const float *d_u, int w, int h, int pitch, const uint8_t *d_idx, const float *h_sigmas,
                   int n_sigma, const fd4_params &p, float *d_tensor, char *ws, cudaStream_t st)
 {
-    if (set_tile_smem()) return 1;
-    float4 *nf = (float4 *)(ws + kHeaderBytes);
-    // pixels whose index is out of range keep N = 0 (isotropic, mu = 1)
-    if (cudaMemsetAsync(nf, 0, (size_t)h * pitch * sizeof(float4), st) != cudaSuccess) return 1;
-    const dim3 grid((w + TX - 1) / TX, (h + TY - 1) / TY);
-    SelectOut so{};
-    for (int s = 0; s < n_sigma; ++s) {
-        GaussTaps taps;
-        if (gauss_taps(h_sigmas[s], &taps) != FD4_OK) return 1;
-        TensorOut to;
-        to.idx = d_idx;
-        to.nfield = nf;
-        to.s = s;
-        to.grad_sq = p.grad_norm_squared;
-        k_gauss_tile<OUT_TENSOR><<<grid, NT, tile_smem_bytes(taps.r), st>>>(d_u, w, h, pitch, taps, so, to);
+    ImgDesc d{};
+    d.u = const_cast<float *>(d_u);  // read only by the tensor build
+    d.nfield = (float4 *)(ws + kHeaderBytes);
+    d.tensor = (float4 *)d_tensor;
+    d.idx = const_cast<uint8_t *>(d_idx);
+    d.w = w;
+    d.h = h;
+    d.pitch = pitch;
+    return launch_tensor_batch(single_batch(d), h_sigmas, n_sigma, p, st);
+}
+
+int persistent_grid(const void *kernel, int threads, size_t smem, int tiles)
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 152;
     }
-    RhoTaps rt;
-    if (rho_taps(p.rho, &rt) != FD4_OK) return 1;
-    k_tensor_finish<<<dim3((w + FX - 1) / FX, (h + FY - 1) / FY), FX * FY, 0, st>>>(
-        nf, w, h, pitch, rt, p.lambda, p.mode, (float4 *)d_tensor);
-    return cudaGetLastError() != cudaSuccess;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const long long g = (long long)per_sm * sms;
+    return (int)(tiles < g ? (tiles > 0 ? tiles : 1) : g);
 }
 
 }  // namespace fd4

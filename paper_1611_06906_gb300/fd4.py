@@ -21,6 +21,7 @@ from . import build as _build
 RIDGE, VALLEY, BOTH = 0, 1, 2
 NATURAL, PERIODIC = 0, 1
 OP_SELECT_SCALES, OP_BUILD_TENSOR, OP_FED_CYCLE, OP_FILTER = 0, 1, 2, 3
+STAGE_SELECT, STAGE_COPY, STAGE_TENSOR, STAGE_FED, STAGES_ALL = 1, 2, 4, 8, 15
 MAX_FED_STEPS = 4096
 
 _lock = threading.Lock()
@@ -38,7 +39,13 @@ class Params(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_float), ("rho", ctypes.c_float), ("beta", ctypes.c_float),
                 ("c", ctypes.c_float), ("gamma", ctypes.c_float), ("tau_max", ctypes.c_float),
                 ("mode", ctypes.c_int), ("boundary", ctypes.c_int), ("kappa", ctypes.c_int),
-                ("grad_norm_squared", ctypes.c_int)]
+                ("grad_norm_squared", ctypes.c_int), ("fed_steps_per_launch", ctypes.c_int)]
+
+
+class Image(ctypes.Structure):
+    """fd4_image (include/fd4.h)."""
+    _fields_ = [("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p), ("d_sigma_idx", ctypes.c_void_p),
+                ("w", ctypes.c_int), ("h", ctypes.c_int), ("pitch", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p
@@ -61,6 +68,14 @@ SIGNATURES = {
     "fd4_filter": (_i, [_vp, _vp, _i, _i, _i, _fp, _i, _pp, ctypes.c_double, _i, _i, _vp, _i, _vp,
                         _sz, _vp]),
     "fd4_fed_cycle_noalloc": (_i, [_vp, _i, _i, _i, _vp, _dp, _i, _i, _vp]),
+    "fd4_batch_workspace_bytes": (_sz, [_vp, _i, _i]),
+    "fd4_filter_batched": (_i, [_vp, _i, _fp, _i, _pp, ctypes.c_double, _i, _i, _i, _vp, _sz, _vp]),
+    "fd4_graph_create": (_i, [_vp, _i, _fp, _i, _pp, ctypes.c_double, _i, _i, _i, _i, _vp, _sz,
+                              ctypes.POINTER(ctypes.c_void_p)]),
+    "fd4_graph_launch": (_i, [_vp, _vp]),
+    "fd4_graph_destroy": (_i, [_vp]),
+    "fd4_autotune_batched": (_i, [_vp, _i, _fp, _i, _pp, ctypes.c_double, _i, _i, _vp, _sz, _vp, _ip,
+                                  _fp]),
 }
 NOALLOC_MAX_PIXELS = 4 * 1024 * 1024
 
@@ -238,3 +253,84 @@ def fed_cycle_noalloc(u, w: int, tensor, tau, boundary: int = NATURAL, stream=No
     _check(lib().fd4_fed_cycle_noalloc(_ptr(u), int(w), h, pitch, _ptr(tensor), t.ctypes.data_as(_dp),
                                        t.size, int(boundary), _stream(stream)), "fd4_fed_cycle_noalloc")
     return u
+
+
+# ---------------------------------------------------------------------------
+# Batches
+
+def image_list(inputs, widths, outputs=None, sigma_idx=None):
+    """ctypes array of fd4_image for device tensors (h, pitch) with widths w."""
+    n = len(inputs)
+    arr = (Image * n)()
+    for i, (u, w) in enumerate(zip(inputs, widths)):
+        arr[i].d_in = u.data_ptr()
+        arr[i].d_out = (outputs[i] if outputs is not None else u).data_ptr()
+        arr[i].d_sigma_idx = sigma_idx[i].data_ptr() if sigma_idx is not None else None
+        arr[i].w, arr[i].h, arr[i].pitch = int(w), int(u.shape[0]), int(u.shape[1])
+    return arr
+
+
+def batch_workspace(imgs, n_sigma: int, device="cuda"):
+    torch = _torch()
+    nbytes = int(lib().fd4_batch_workspace_bytes(ctypes.cast(imgs, ctypes.c_void_p), len(imgs), n_sigma))
+    if nbytes == 0:
+        raise Fd4Error(-1, "fd4_batch_workspace_bytes")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def filter_batched(imgs, sigmas, T: float, M: int, n: int = 0, prm: Params | None = None,
+                   sigma_given: bool = False, ws=None, stream=None):
+    """fd4_filter_batched on an image_list()."""
+    sg, K = _sigmas(sigmas)
+    if ws is None:
+        ws = batch_workspace(imgs, K)
+    _check(lib().fd4_filter_batched(ctypes.cast(imgs, ctypes.c_void_p), len(imgs), sg, K,
+                                    ctypes.byref(prm) if prm is not None else None, float(T), int(M), int(n),
+                                    int(sigma_given), _ptr(ws), ws.numel(), _stream(stream)),
+           "fd4_filter_batched")
+    return ws
+
+
+class Graph:
+    """fd4_graph: the batched schedule captured once, replayed by launch()."""
+
+    def __init__(self, imgs, sigmas, T: float, M: int, n: int = 0, prm: Params | None = None,
+                 sigma_given: bool = False, ws=None, stages: int = 15):
+        sg, K = _sigmas(sigmas)
+        self.ws = ws if ws is not None else batch_workspace(imgs, K)
+        self.imgs = imgs
+        h = ctypes.c_void_p(0)
+        _check(lib().fd4_graph_create(ctypes.cast(imgs, ctypes.c_void_p), len(imgs), sg, K,
+                                      ctypes.byref(prm) if prm is not None else None, float(T), int(M),
+                                      int(n), int(sigma_given), int(stages), _ptr(self.ws), self.ws.numel(),
+                                      ctypes.byref(h)), "fd4_graph_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(lib().fd4_graph_launch(self.handle, _stream(stream)), "fd4_graph_launch")
+
+    def close(self):
+        if self.handle:
+            lib().fd4_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune_batched(imgs, sigmas, T: float, M: int, n: int = 0, prm: Params | None = None, ws=None,
+                     stream=None):
+    """fd4_autotune_batched.  Returns (best steps per launch, times in ms for 1..4)."""
+    sg, K = _sigmas(sigmas)
+    if ws is None:
+        ws = batch_workspace(imgs, K)
+    best = ctypes.c_int(0)
+    times = (ctypes.c_float * 4)()
+    _check(lib().fd4_autotune_batched(ctypes.cast(imgs, ctypes.c_void_p), len(imgs), sg, K,
+                                      ctypes.byref(prm) if prm is not None else None, float(T), int(M), int(n),
+                                      _ptr(ws), ws.numel(), _stream(stream), ctypes.byref(best), times),
+           "fd4_autotune_batched")
+    return best.value, list(times)
