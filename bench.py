@@ -201,8 +201,18 @@ def run_fd4(args, rank, world, local_rank):
     # batched path: one launch per stage across the batch, replayed as a CUDA graph
     lst = fd4.image_list([b.u_in for b in ims], [b.w for b in ims], [b.out for b in ims], [b.idx for b in ims])
     ws = fd4.batch_workspace(lst, K, dev)
-    best, tune_ms = fd4.autotune_batched(lst, sig, T, M, n, fd4.params(mode=mode), ws=ws)
+    if args.fed_steps:
+        best, tune_ms = args.fed_steps, None
+    else:
+        best, tune_ms = fd4.autotune_batched(lst, sig, T, M, n, fd4.params(mode=mode), ws=ws)
     prm = fd4.params(mode=mode, fed_steps_per_launch=best)
+    if args.only_graph:  # profiling: warm-up and timed replays of the full graph only
+        g = fd4.Graph(lst, sig, T, M, n, prm, ws=ws)
+        for _ in range(args.warmup + args.steps):
+            g.launch()
+        torch.cuda.synchronize()
+        g.close()
+        return
     g_all = fd4.Graph(lst, sig, T, M, n, prm, ws=ws)
     g_sel = fd4.Graph(lst, sig, T, M, n, prm, ws=ws, stages=fd4.STAGE_SELECT)
     g_ten = fd4.Graph(lst, sig, T, M, n, prm, ws=ws, stages=fd4.STAGE_TENSOR)
@@ -368,6 +378,8 @@ def main():
     ap.add_argument("--limit", type=int, default=0, help="use only the first N images (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fed-steps", type=int, default=0, help="FED steps per launch (0: autotune)")
+    ap.add_argument("--only-graph", action="store_true", help="replay the full graph only (profiling)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per FED launch from an ncu capture of the current kernel")
     args = ap.parse_args()
