@@ -232,6 +232,46 @@ int fd4_autotune_batched(const fd4_image *h_imgs, int n_images, const float *h_s
                          const fd4_params *params, double T, int M, int n_in, void *d_ws, size_t ws_bytes,
                          fd4_stream_t stream, int *best_steps_per_launch, float *times_ms);
 
+/* ------------------------------------------------------------------------ */
+/* Learned scale selector.  No counterpart in the paper: a small network that
+ * predicts the per-pixel scale index the vesselness argmax (Sec. 3.3) would
+ * select, trained on labels the plain selection produces, with the plain
+ * selection as fallback and judge.  Network: four dilated 3x3 convolutions
+ * (dilations 1, 2, 4, 8; channels 1-32-32-32-8; zero padding), ReLU between
+ * them, softmax over 8 scale bins.  BF16 weights and activations, FP32
+ * accumulation on the tensor cores (tcgen05).
+ * Parameters live in a caller-owned device buffer of
+ * fd4_selector_param_bytes() bytes (256-byte aligned): FP32 master weights
+ * (order: per layer W[ky][kx][co][ci] then b[co]), Adam moments, accumulated
+ * gradients, and the BF16 kernel layouts derived from the master weights.
+ * Image stacks are n_img images of w x h, row pitch `pitch`, image after image
+ * (h * pitch floats apart).                                                  */
+size_t fd4_selector_param_bytes(void);
+size_t fd4_selector_workspace_bytes(int n_img, int w, int h, int pitch);
+/* He-normal weights from a seed, zero biases, zero moments (synchronous). */
+int fd4_selector_init(void *d_params, unsigned long long seed, fd4_stream_t stream);
+/* Master weights from / to the host (synchronous); which: 0 weights,
+ * 1 and 2 Adam moments, 3 accumulated gradients.                            */
+int fd4_selector_set_weights(void *d_params, const float *h_weights, fd4_stream_t stream);
+int fd4_selector_get_weights(const void *d_params, float *h_weights, int which, fd4_stream_t stream);
+/* Logits (8 floats per pixel, pixel layout of the stack) of every image.    */
+int fd4_selector_forward(const void *d_params, const float *d_imgs, int n_img, int w, int h, int pitch,
+                         float *d_logits, void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+/* Forward and backward pass: adds the gradient of the mean cross-entropy
+ * against d_labels (uint8 bin per pixel, stack layout) to the accumulated
+ * gradients, and the mean loss to *d_loss.                                  */
+int fd4_selector_grad(void *d_params, const float *d_imgs, const uint8_t *d_labels, int n_img, int w, int h,
+                      int pitch, float *d_loss, void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+/* Adam step (beta 0.9 / 0.999, eps 1e-8) on the accumulated gradients, which
+ * are then cleared; step counts from 1.                                     */
+int fd4_selector_update(void *d_params, float lr, int step, fd4_stream_t stream);
+/* Scale index (argmax bin) and confidence (its probability) per pixel.     */
+int fd4_selector_predict(const void *d_params, const float *d_img, int w, int h, int pitch, uint8_t *d_idx,
+                         float *d_conf, void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+/* Device status word of a selector workspace (FD4_ERR_TIMEOUT if a bounded
+ * wait in a tensor-core kernel gave up), read synchronously.                */
+int fd4_selector_status(const void *d_ws, int *status, fd4_stream_t stream);
+
 /* Allocation-free FED cycle.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory -- host applications
  * that own all device memory and pass a library only the buffers it works on,

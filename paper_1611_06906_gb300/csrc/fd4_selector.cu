@@ -1,0 +1,775 @@
+// Learned scale selector (no counterpart in the paper: the paper selects the
+// scale with the vesselness argmax of Sec. 3.3; this network predicts that
+// argmax and the plain sweep judges it).
+//
+// Network: four dilated 3 x 3 convolutions (dilations 1, 2, 4, 8; channels
+// 1 -> 32 -> 32 -> 32 -> 8), ReLU between them, softmax over 8 scale bins.
+// Activations are NHWC bf16 (16 channels for the input layer, 32 after);
+// weights bf16; accumulation FP32 in tensor memory.
+//
+// Convolution as implicit GEMM on the 5th-generation tensor cores: a block
+// owns 128 consecutive output pixels of one image row (the MMA's M = 128); it
+// stages the three input rows y - d, y, y + d (with a d-pixel margin) in shared
+// memory as 16-byte channel chunks laid out pixel-contiguous, so the A operand
+// of tap (ky, kx) is the same buffer shifted by kx * d pixels -- a plain
+// K-major no-swizzle descriptor, no im2col copy.  B (the weights of all nine
+// taps) is staged once per block.  One thread issues 9 * CI/16 MMAs of
+// 128 x CO x 16, commits them to an mbarrier, and the four warps read the
+// FP32 accumulator back from their TMEM lanes for the epilogue.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "fd4_internal.h"
+#include "fd4_tc.cuh"
+
+namespace fd4 {
+namespace {
+
+constexpr int TM = 128;           // output pixels per tile (MMA M)
+constexpr int CT = 128;           // threads: warp w owns TMEM lanes 32w .. 32w+31
+constexpr int kMaxDil = 8;
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+enum ConvMode { CONV_RELU_BF16 = 0, CONV_LOGITS_F32 = 1, CONV_MASK_BF16 = 2 };
+
+struct ConvArgs {
+    const __nv_bfloat16 *in;    // NHWC, CI channels
+    void *out;                  // NHWC, CO channels (bf16) or n_out floats per pixel (fp32)
+    const uint4 *wts;           // weights in tile layout: [tap][ci / 8][co] x 16 bytes
+    const float *bias;          // CO floats, nullable
+    const __nv_bfloat16 *mask;  // CONV_MASK_BF16: NHWC, CO channels; output zeroed where mask <= 0
+    int n_img, w, h, pitch, d;
+    long long img_stride;       // pixels between consecutive images
+    int n_out;                  // CONV_LOGITS_F32: channels written per pixel
+    int *status;                // FD4_ERR_TIMEOUT if a wait gives up
+};
+
+__host__ __device__ inline size_t conv_smem_bytes(int CI, int CO, int d)
+{
+    return (size_t)16 * (9 * (CI / 8) * CO + 3 * (CI / 8) * (TM + 2 * d));
+}
+
+template <int CI, int CO, int MODE>
+__global__ void __launch_bounds__(CT) k_conv_tc(ConvArgs a)
+{
+    constexpr int CJ = CI / 8;  // 16-byte channel chunks per pixel
+    extern __shared__ __align__(128) uint4 csm[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const int P = TM + 2 * a.d;  // staged pixels per row
+    uint4 *Bs = csm;             // 9 * CJ * CO chunks
+    uint4 *As = csm + 9 * CJ * CO;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    for (int i = tid; i < 9 * CJ * CO; i += CT) Bs[i] = a.wts[i];
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_base, 32);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(&mbar, 1);
+        abort_flag = 0;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(TM, CO);
+    const int tiles_x = (a.w + TM - 1) / TM;
+    const long long total = (long long)a.n_img * a.h * tiles_x;
+    uint32_t phase = 0;
+
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        const int tx = (int)(t % tiles_x);
+        const long long rr = t / tiles_x;
+        const int y = (int)(rr % a.h);
+        const int img = (int)(rr / a.h);
+        const int x0 = tx * TM;
+        const __nv_bfloat16 *in = a.in + (size_t)img * (size_t)a.img_stride * CI;
+        // A: rows y - d, y, y + d; pixels x0 - d .. x0 + TM - 1 + d; zero outside the image
+        for (int i = tid; i < 3 * P * CJ; i += CT) {
+            const int j = i % CJ;
+            const int p = (i / CJ) % P;
+            const int ky = i / (CJ * P);
+            const int gy = y + (ky - 1) * a.d, gx = x0 - a.d + p;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gy >= 0 && gy < a.h && gx >= 0 && gx < a.w)
+                v = *reinterpret_cast<const uint4 *>(in + ((size_t)gy * a.pitch + gx) * CI + 8 * j);
+            As[(ky * CJ + j) * P + p] = v;
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs);
+            uint32_t acc = 0;
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+                const int ky = tap / 3, kx = tap - 3 * (tap / 3);
+#pragma unroll
+                for (int k = 0; k < CI / 16; ++k) {
+                    const uint32_t aaddr = a0 + (uint32_t)(((ky * CJ + 2 * k) * P + kx * a.d) * 16);
+                    const uint32_t baddr = b0 + (uint32_t)((tap * CJ + 2 * k) * CO * 16);
+                    tc::mma_bf16(tmem, tc::sdesc_kmajor(aaddr, (uint32_t)(P * 16), 128),
+                                 tc::sdesc_kmajor(baddr, (uint32_t)(CO * 16), 128), idesc, acc);
+                    acc = 1;
+                }
+            }
+            tc::mma_commit(&mbar);
+        }
+        // wait for the MMAs, at most one second
+        {
+            const uint64_t t0 = globaltimer();
+            while (!tc::mbar_try_wait(&mbar, phase)) {
+                if (globaltimer() - t0 > 1000000000ull) {
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+            }
+        }
+        phase ^= 1u;
+        tc::fence_after_sync();
+        __syncthreads();
+        if (abort_flag) break;
+
+        const int i = warp * 32 + lane;  // tile pixel = TMEM lane
+        const int gx = x0 + i;
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        float v[CO];
+        if constexpr (CO == 32) {
+            tc::tmem_ld_x32(taddr, v);
+        } else {
+            tc::tmem_ld_x16(taddr, v);
+        }
+        if (gx < a.w) {
+            const size_t p = (size_t)img * (size_t)a.img_stride + (size_t)y * a.pitch + gx;
+            if (MODE == CONV_LOGITS_F32) {
+                float *o = reinterpret_cast<float *>(a.out) + p * a.n_out;
+                for (int c = 0; c < a.n_out; ++c) o[c] = v[c] + (a.bias ? a.bias[c] : 0.0f);
+            } else {
+                if (MODE == CONV_MASK_BF16) {
+                    const __nv_bfloat16 *m = a.mask + p * CO;
+#pragma unroll
+                    for (int c = 0; c < CO; ++c)
+                        if (!(__bfloat162float(m[c]) > 0.0f)) v[c] = 0.0f;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < CO; ++c) v[c] = fmaxf(v[c] + (a.bias ? a.bias[c] : 0.0f), 0.0f);
+                }
+                uint4 *o = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(a.out) + p * CO);
+#pragma unroll
+                for (int q = 0; q < CO / 8; ++q) {
+                    uint4 pk;
+                    __nv_bfloat162 b0 = __floats2bfloat162_rn(v[8 * q + 0], v[8 * q + 1]);
+                    __nv_bfloat162 b1 = __floats2bfloat162_rn(v[8 * q + 2], v[8 * q + 3]);
+                    __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * q + 4], v[8 * q + 5]);
+                    __nv_bfloat162 b3 = __floats2bfloat162_rn(v[8 * q + 6], v[8 * q + 7]);
+                    pk.x = *reinterpret_cast<uint32_t *>(&b0);
+                    pk.y = *reinterpret_cast<uint32_t *>(&b1);
+                    pk.z = *reinterpret_cast<uint32_t *>(&b2);
+                    pk.w = *reinterpret_cast<uint32_t *>(&b3);
+                    o[q] = pk;
+                }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();  // TMEM is read before the next tile's MMAs overwrite it
+    }
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 32);
+    if (tid == 0 && abort_flag && a.status) atomicExch(a.status, FD4_ERR_TIMEOUT);
+}
+
+
+// ---------------------------------------------------------------------------
+// Network geometry and the parameter buffer.
+
+constexpr int kLayers = 4;
+constexpr int kBins = 8;
+constexpr int CI_R[kLayers] = {1, 32, 32, 32};   // real channels
+constexpr int CO_R[kLayers] = {32, 32, 32, kBins};
+constexpr int CI_P[kLayers] = {16, 32, 32, 32};  // padded to the MMA's K and N granularity
+constexpr int CO_P[kLayers] = {32, 32, 32, 16};
+constexpr int DIL[kLayers] = {1, 2, 4, 8};
+
+struct SelLayout {
+    size_t w_off[kLayers], b_off[kLayers];  // master FP32 (floats), order [ky][kx][co][ci]
+    size_t n_master;                        // floats per copy (master, m, v, grad)
+    size_t fwd_off[kLayers];                // bytes: forward tile layout (bf16)
+    size_t dgr_off[kLayers];                // bytes: data-gradient tile layout (layers 1..3)
+    size_t bias_off;                        // bytes: padded biases (FP32, CO_P each)
+    size_t bytes;
+};
+
+SelLayout sel_layout()
+{
+    SelLayout L{};
+    size_t f = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        L.w_off[l] = f;
+        f += (size_t)9 * CO_R[l] * CI_R[l];
+        L.b_off[l] = f;
+        f += CO_R[l];
+    }
+    L.n_master = f;
+    size_t b = align_up(4 * 4 * f, 256);  // master, m, v, grad
+    for (int l = 0; l < kLayers; ++l) {
+        L.fwd_off[l] = b;
+        b += align_up((size_t)16 * 9 * (CI_P[l] / 8) * CO_P[l], 256);
+    }
+    for (int l = 1; l < kLayers; ++l) {
+        L.dgr_off[l] = b;
+        b += align_up((size_t)16 * 9 * (CO_P[l] / 8) * CI_R[l], 256);
+    }
+    L.bias_off = b;
+    b += align_up(sizeof(float) * 32 * kLayers, 256);
+    L.bytes = b;
+    return L;
+}
+
+struct CastArgs {
+    const float *master;
+    __nv_bfloat16 *fwd[kLayers];
+    __nv_bfloat16 *dgr[kLayers];
+    float *bias;  // kLayers x 32
+    long long w_off[kLayers], b_off[kLayers];
+    int ci_p[kLayers], co_p[kLayers], ci_r[kLayers], co_r[kLayers];
+};
+
+// Master FP32 weights -> bf16 tile layouts: forward [tap][ci/8][co][8] (zero
+// padded) and, for layers 1..3, the data-gradient layout
+// [tap'][co/8][ci][8] holding W[8 - tap'][co][ci] (flipped taps, swapped
+// channel roles), so the data gradient is the same convolution kernel.
+__global__ void k_sel_cast(CastArgs a)
+{
+    const int l = blockIdx.y;
+    const int ci_p = a.ci_p[l], co_p = a.co_p[l], ci_r = a.ci_r[l], co_r = a.co_r[l];
+    const float *W = a.master + a.w_off[l];
+    const int nf = 9 * ci_p * co_p;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
+        const int e = i & 7;
+        const int co = (i >> 3) % co_p;
+        const int j = (i >> 3) / co_p % (ci_p / 8);
+        const int t = (i >> 3) / co_p / (ci_p / 8);
+        const int ci = 8 * j + e;
+        const float v = (co < co_r && ci < ci_r) ? W[((size_t)t * co_r + co) * ci_r + ci] : 0.0f;
+        a.fwd[l][i] = __float2bfloat16_rn(v);
+    }
+    if (l >= 1) {
+        const int nd = 9 * co_p * ci_r;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += gridDim.x * blockDim.x) {
+            const int e = i & 7;
+            const int c = (i >> 3) % ci_r;              // data-gradient output channel (= forward ci)
+            const int j = (i >> 3) / ci_r % (co_p / 8);
+            const int t = (i >> 3) / ci_r / (co_p / 8);
+            const int k = 8 * j + e;                    // data-gradient input channel (= forward co)
+            const float v = k < co_r ? W[((size_t)(8 - t) * co_r + k) * ci_r + c] : 0.0f;
+            a.dgr[l][i] = __float2bfloat16_rn(v);
+        }
+    }
+    if (blockIdx.x == 0)
+        for (int c = threadIdx.x; c < 32; c += blockDim.x)
+            a.bias[l * 32 + c] = c < co_r ? a.master[a.b_off[l] + c] : 0.0f;
+}
+
+// Image -> input activations: channel 0 = intensity, channels 1..15 = 0.
+__global__ void k_sel_prep(const float *img, __nv_bfloat16 *act, int n_img, int w, int h, int pitch,
+                           long long img_stride)
+{
+    const long long total = (long long)n_img * img_stride;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % img_stride % pitch);
+        const float v = x < w ? img[i] : 0.0f;
+        uint4 *o = reinterpret_cast<uint4 *>(act + i * 16);
+        __nv_bfloat162 b = __floats2bfloat162_rn(v, 0.0f);
+        o[0] = make_uint4(*reinterpret_cast<uint32_t *>(&b), 0u, 0u, 0u);
+        o[1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// Softmax cross-entropy over the 8 logits of every pixel: mean loss added to
+// *loss, gradient (p - onehot) / npx written as bf16 (16 channels, 8..15 zero).
+__global__ void __launch_bounds__(256) k_sel_softmax_ce(const float *logits, const uint8_t *labels,
+                                                        __nv_bfloat16 *dz, int n_img, int w, int h, int pitch,
+                                                        long long img_stride, float inv_npx, float *loss)
+{
+    __shared__ float red[8];
+    float lsum = 0.0f;
+    const long long total = (long long)n_img * img_stride;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % img_stride % pitch);
+        float g[kBins];
+        if (x < w) {
+            const float *z = logits + i * kBins;
+            float m = z[0];
+            for (int c = 1; c < kBins; ++c) m = fmaxf(m, z[c]);
+            float sum = 0.0f;
+            for (int c = 0; c < kBins; ++c) {
+                g[c] = expf(z[c] - m);
+                sum += g[c];
+            }
+            const int lab = labels[i] < kBins ? labels[i] : kBins - 1;
+            lsum += logf(sum) - (z[lab] - m);
+            for (int c = 0; c < kBins; ++c) g[c] = (g[c] / sum - (c == lab ? 1.0f : 0.0f)) * inv_npx;
+        } else {
+            for (int c = 0; c < kBins; ++c) g[c] = 0.0f;
+        }
+        uint4 *o = reinterpret_cast<uint4 *>(dz + i * 16);
+        uint32_t q[4];
+        for (int c = 0; c < 4; ++c) {
+            __nv_bfloat162 b = __floats2bfloat162_rn(g[2 * c], g[2 * c + 1]);
+            q[c] = *reinterpret_cast<uint32_t *>(&b);
+        }
+        o[0] = make_uint4(q[0], q[1], q[2], q[3]);
+        o[1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+        atomicAdd(loss, s * inv_npx);
+    }
+}
+
+// Weight gradient of one layer on the CUDA cores (FP32):
+// gW[t][co][ci] += sum_px dZ[px][co] X[px + shift_t][ci], gb[co] += sum_px dZ[px][co].
+// A block owns 128-pixel row tiles (as the convolution) and keeps its partial
+// sums in registers across tiles; each thread covers one output channel and a
+// strided subset of (tap, input channel) pairs.
+template <int CIP, int COP>
+__global__ void __launch_bounds__(CT) k_sel_wgrad(const __nv_bfloat16 *X, const __nv_bfloat16 *dZ, int ci_r, int co_r,
+                                                  int n_img, int w, int h, int pitch, int d, long long img_stride,
+                                                  float *gW, float *gb)
+{
+    constexpr int NG = CT / COP;              // thread groups
+    constexpr int NP = 9 * CIP / NG;          // (tap, ci) pairs per thread
+    __shared__ __nv_bfloat16 xs[3][TM + 2 * kMaxDil][CIP];
+    __shared__ float zs[TM][COP + 1];
+    const int tid = threadIdx.x;
+    const int co = tid % COP, g = tid / COP;
+    float acc[NP];
+    float bacc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) acc[k] = 0.0f;
+    const int P = TM + 2 * d;
+    const int tiles_x = (w + TM - 1) / TM;
+    const long long total = (long long)n_img * h * tiles_x;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        const int tx = (int)(t % tiles_x);
+        const long long rr = t / tiles_x;
+        const int y = (int)(rr % h);
+        const int img = (int)(rr / h);
+        const int x0 = tx * TM;
+        const size_t base = (size_t)img * (size_t)img_stride;
+        __syncthreads();
+        for (int i = tid; i < 3 * P * CIP; i += CT) {
+            const int c = i % CIP, p = (i / CIP) % P, ky = i / (CIP * P);
+            const int gy = y + (ky - 1) * d, gx = x0 - d + p;
+            __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
+            if (gy >= 0 && gy < h && gx >= 0 && gx < w) v = X[(base + (size_t)gy * pitch + gx) * CIP + c];
+            xs[ky][p][c] = v;
+        }
+        for (int i = tid; i < TM * COP; i += CT) {
+            const int c = i % COP, p = i / COP;
+            const int gx = x0 + p;
+            zs[p][c] = gx < w ? __bfloat162float(dZ[(base + (size_t)y * pitch + gx) * COP + c]) : 0.0f;
+        }
+        __syncthreads();
+        for (int p = 0; p < TM; ++p) {
+            const float dz = zs[p][co];
+            if (g == 0) bacc += dz;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const int q = g + k * NG;          // pair index = tap * CIP + ci
+                const int tap = q / CIP, ci = q - tap * CIP;
+                const int ky = tap / 3, kx = tap - 3 * ky;
+                acc[k] = fmaf(dz, __bfloat162float(xs[ky][p + kx * d][ci]), acc[k]);
+            }
+        }
+    }
+    if (co < co_r) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const int q = g + k * NG;
+            const int tap = q / CIP, ci = q - tap * CIP;
+            if (ci < ci_r) atomicAdd(gW + ((size_t)tap * co_r + co) * ci_r + ci, acc[k]);
+        }
+        if (g == 0) atomicAdd(gb + co, bacc);
+    }
+}
+
+// Adam on the FP32 master weights; the gradient is cleared afterwards.
+__global__ void k_sel_adam(float *w, float *m, float *v, float *g, size_t n, float lr, float b1, float b2, float eps,
+                           float c1, float c2)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        g[i] = 0.0f;
+    }
+}
+
+// Inference read-out: scale bin = argmax of the logits (ties to the smaller
+// bin), confidence = its softmax probability.
+__global__ void k_sel_predict(const float *logits, int w, int h, int pitch, uint8_t *idx, float *conf)
+{
+    const long long total = (long long)h * pitch;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        if ((int)(i % pitch) >= w) continue;
+        const float *z = logits + i * kBins;
+        int arg = 0;
+        float m = z[0];
+        for (int c = 1; c < kBins; ++c)
+            if (z[c] > m) {
+                m = z[c];
+                arg = c;
+            }
+        float sum = 0.0f;
+        for (int c = 0; c < kBins; ++c) sum += expf(z[c] - m);
+        idx[i] = (uint8_t)arg;
+        if (conf) conf[i] = 1.0f / sum;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side.
+
+namespace {
+
+template <int CI, int CO, int MODE>
+int launch_conv(const ConvArgs &a, cudaStream_t st)
+{
+    const size_t smem = conv_smem_bytes(CI, CO, kMaxDil);
+    static int attr_dev = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (attr_dev != dev) {
+        if (cudaFuncSetAttribute(k_conv_tc<CI, CO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return 1;
+        attr_dev = dev;
+    }
+    const long long tiles = (long long)a.n_img * a.h * ((a.w + TM - 1) / TM);
+    const int grid = persistent_grid((const void *)k_conv_tc<CI, CO, MODE>, CT, conv_smem_bytes(CI, CO, a.d),
+                                     (int)(tiles < (1 << 30) ? tiles : (1 << 30)));
+    k_conv_tc<CI, CO, MODE><<<grid, CT, conv_smem_bytes(CI, CO, a.d), st>>>(a);
+    return cudaGetLastError() != cudaSuccess;
+}
+
+struct SelBufs {
+    __nv_bfloat16 *act[kLayers];  // inputs of layers 0..3 (16 / 32 / 32 / 32 channels)
+    float *logits;                // 8 per pixel
+    __nv_bfloat16 *dz16;          // gradient of the last layer's output (16 channels)
+    __nv_bfloat16 *dz[2];         // 32-channel gradients (ping-pong)
+    int *status;
+    size_t bytes;
+};
+
+SelBufs sel_bufs(char *ws, long long npx)
+{
+    SelBufs b{};
+    size_t o = 256;  // header: status word
+    b.status = (int *)ws;
+    const size_t per[kLayers] = {16, 32, 32, 32};
+    for (int l = 0; l < kLayers; ++l) {
+        b.act[l] = ws ? (__nv_bfloat16 *)(ws + o) : nullptr;
+        o += align_up((size_t)npx * per[l] * 2, 256);
+    }
+    b.logits = ws ? (float *)(ws + o) : nullptr;
+    o += align_up((size_t)npx * kBins * 4, 256);
+    b.dz16 = ws ? (__nv_bfloat16 *)(ws + o) : nullptr;
+    o += align_up((size_t)npx * 16 * 2, 256);
+    for (int k = 0; k < 2; ++k) {
+        b.dz[k] = ws ? (__nv_bfloat16 *)(ws + o) : nullptr;
+        o += align_up((size_t)npx * 32 * 2, 256);
+    }
+    b.bytes = o;
+    return b;
+}
+
+struct SelPtrs {
+    float *master, *m, *v, *grad;
+    const uint4 *fwd[kLayers];
+    const uint4 *dgr[kLayers];
+    const float *bias;
+};
+
+SelPtrs sel_ptrs(void *params)
+{
+    const SelLayout L = sel_layout();
+    char *p = (char *)params;
+    SelPtrs s{};
+    s.master = (float *)p;
+    s.m = s.master + L.n_master;
+    s.v = s.m + L.n_master;
+    s.grad = s.v + L.n_master;
+    for (int l = 0; l < kLayers; ++l) s.fwd[l] = (const uint4 *)(p + L.fwd_off[l]);
+    for (int l = 1; l < kLayers; ++l) s.dgr[l] = (const uint4 *)(p + L.dgr_off[l]);
+    s.bias = (const float *)(p + L.bias_off);
+    return s;
+}
+
+int sel_recast(void *params, cudaStream_t st)
+{
+    const SelLayout L = sel_layout();
+    char *p = (char *)params;
+    CastArgs a{};
+    a.master = (const float *)p;
+    for (int l = 0; l < kLayers; ++l) {
+        a.fwd[l] = (__nv_bfloat16 *)(p + L.fwd_off[l]);
+        a.dgr[l] = l ? (__nv_bfloat16 *)(p + L.dgr_off[l]) : nullptr;
+        a.w_off[l] = (long long)L.w_off[l];
+        a.b_off[l] = (long long)L.b_off[l];
+        a.ci_p[l] = CI_P[l];
+        a.co_p[l] = CO_P[l];
+        a.ci_r[l] = CI_R[l];
+        a.co_r[l] = CO_R[l];
+    }
+    a.bias = (float *)(p + L.bias_off);
+    k_sel_cast<<<dim3(16, kLayers), 256, 0, st>>>(a);
+    return cudaGetLastError() != cudaSuccess;
+}
+
+int check_stack(const void *d, int n_img, int w, int h, int pitch)
+{
+    if (n_img < 1) return FD4_ERR_BAD_ARG;
+    return check_image(d, w, h, pitch);
+}
+
+// Forward pass of the network over a stack of n_img images (img_stride = h * pitch).
+int sel_forward(const SelPtrs &P, const float *imgs, int n_img, int w, int h, int pitch, const SelBufs &B,
+                cudaStream_t st)
+{
+    const long long stride = (long long)h * pitch;
+    const long long npx = stride * n_img;
+    const int g = (int)((npx + 255) / 256 < 4096 ? (npx + 255) / 256 : 4096);
+    k_sel_prep<<<g, 256, 0, st>>>(imgs, B.act[0], n_img, w, h, pitch, stride);
+    ConvArgs a{};
+    a.n_img = n_img;
+    a.w = w;
+    a.h = h;
+    a.pitch = pitch;
+    a.img_stride = stride;
+    a.status = B.status;
+    for (int l = 0; l < kLayers; ++l) {
+        a.in = B.act[l];
+        a.wts = P.fwd[l];
+        a.bias = P.bias + 32 * l;
+        a.d = DIL[l];
+        a.mask = nullptr;
+        int rc;
+        if (l == 0) {
+            a.out = B.act[1];
+            rc = launch_conv<16, 32, CONV_RELU_BF16>(a, st);
+        } else if (l < kLayers - 1) {
+            a.out = B.act[l + 1];
+            rc = launch_conv<32, 32, CONV_RELU_BF16>(a, st);
+        } else {
+            a.out = B.logits;
+            a.n_out = kBins;
+            rc = launch_conv<32, 16, CONV_LOGITS_F32>(a, st);
+        }
+        if (rc) return 1;
+    }
+    return 0;
+}
+
+template <int CIP, int COP>
+int launch_wgrad(const __nv_bfloat16 *X, const __nv_bfloat16 *dZ, int l, const SelPtrs &P, int n_img, int w, int h,
+                 int pitch, cudaStream_t st)
+{
+    const SelLayout L = sel_layout();
+    const long long tiles = (long long)n_img * h * ((w + TM - 1) / TM);
+    const int grid = persistent_grid((const void *)k_sel_wgrad<CIP, COP>, CT, 0,
+                                     (int)(tiles < (1 << 30) ? tiles : (1 << 30)));
+    k_sel_wgrad<CIP, COP><<<grid, CT, 0, st>>>(X, dZ, CI_R[l], CO_R[l], n_img, w, h, pitch, DIL[l],
+                                               (long long)h * pitch, P.grad + L.w_off[l], P.grad + L.b_off[l]);
+    return cudaGetLastError() != cudaSuccess;
+}
+
+}  // namespace
+}  // namespace fd4
+
+using namespace fd4;
+
+extern "C" size_t fd4_selector_param_bytes(void) { return sel_layout().bytes; }
+
+extern "C" size_t fd4_selector_workspace_bytes(int n_img, int w, int h, int pitch)
+{
+    if (n_img < 1 || w < 1 || h < 1 || pitch < w) return 0;
+    return sel_bufs(nullptr, (long long)n_img * h * pitch).bytes;
+}
+
+extern "C" int fd4_selector_set_weights(void *d_params, const float *h_w, fd4_stream_t stream)
+{
+    if (!d_params || !h_w || ((uintptr_t)d_params & 255u)) return FD4_ERR_BAD_ARG;
+    const SelLayout L = sel_layout();
+    cudaStream_t st = (cudaStream_t)stream;
+    // master weights from the host; moments and gradients cleared
+    if (cudaMemcpyAsync(d_params, h_w, sizeof(float) * L.n_master, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return FD4_ERR_CUDA;
+    if (cudaMemsetAsync((float *)d_params + L.n_master, 0, sizeof(float) * 3 * L.n_master, st) != cudaSuccess)
+        return FD4_ERR_CUDA;
+    if (sel_recast(d_params, st)) return FD4_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? FD4_OK : FD4_ERR_CUDA;
+}
+
+extern "C" int fd4_selector_get_weights(const void *d_params, float *h_w, int which, fd4_stream_t stream)
+{
+    if (!d_params || !h_w || which < 0 || which > 3) return FD4_ERR_BAD_ARG;
+    const SelLayout L = sel_layout();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(h_w, (const float *)d_params + (size_t)which * L.n_master, sizeof(float) * L.n_master,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return FD4_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? FD4_OK : FD4_ERR_CUDA;
+}
+
+extern "C" int fd4_selector_init(void *d_params, unsigned long long seed, fd4_stream_t stream)
+{
+    // He-normal initialisation on the host (SplitMix64 + Box-Muller), biases 0
+    const SelLayout L = sel_layout();
+    float *h = new float[L.n_master]();
+    unsigned long long state = seed;
+    auto next = [&state]() {
+        unsigned long long z = (state += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    auto unif = [&next]() { return ((double)(next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); };
+    for (int l = 0; l < kLayers; ++l) {
+        const double std = sqrt(2.0 / (9.0 * CI_R[l]));
+        const size_t n = (size_t)9 * CO_R[l] * CI_R[l];
+        for (size_t i = 0; i < n; ++i) {
+            const double u1 = unif(), u2 = unif();
+            h[L.w_off[l] + i] = (float)(std * sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
+        }
+    }
+    const int rc = fd4_selector_set_weights(d_params, h, stream);
+    delete[] h;
+    return rc;
+}
+
+extern "C" int fd4_selector_forward(const void *d_params, const float *d_imgs, int n_img, int w, int h, int pitch,
+                                    float *d_logits, void *d_ws, size_t ws_bytes, fd4_stream_t stream)
+{
+    int rc;
+    if (!d_params || !d_logits) return FD4_ERR_BAD_ARG;
+    if ((rc = check_stack(d_imgs, n_img, w, h, pitch)) != FD4_OK) return rc;
+    const long long npx = (long long)n_img * h * pitch;
+    if (!d_ws || ws_bytes < fd4_selector_workspace_bytes(n_img, w, h, pitch)) return FD4_ERR_WS_TOO_SMALL;
+    cudaStream_t st = (cudaStream_t)stream;
+    SelBufs B = sel_bufs((char *)d_ws, npx);
+    if (cudaMemsetAsync(B.status, 0, sizeof(int), st) != cudaSuccess) return FD4_ERR_CUDA;
+    if (sel_forward(sel_ptrs((void *)d_params), d_imgs, n_img, w, h, pitch, B, st)) return FD4_ERR_CUDA;
+    if (cudaMemcpyAsync(d_logits, B.logits, sizeof(float) * kBins * npx, cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+        return FD4_ERR_CUDA;
+    return FD4_OK;
+}
+
+extern "C" int fd4_selector_grad(void *d_params, const float *d_imgs, const uint8_t *d_labels, int n_img, int w,
+                                 int h, int pitch, float *d_loss, void *d_ws, size_t ws_bytes, fd4_stream_t stream)
+{
+    int rc;
+    if (!d_params || !d_labels || !d_loss) return FD4_ERR_BAD_ARG;
+    if ((rc = check_stack(d_imgs, n_img, w, h, pitch)) != FD4_OK) return rc;
+    const long long npx = (long long)n_img * h * pitch;
+    if (!d_ws || ws_bytes < fd4_selector_workspace_bytes(n_img, w, h, pitch)) return FD4_ERR_WS_TOO_SMALL;
+    cudaStream_t st = (cudaStream_t)stream;
+    SelBufs B = sel_bufs((char *)d_ws, npx);
+    const SelPtrs P = sel_ptrs(d_params);
+    const long long stride = (long long)h * pitch;
+    if (cudaMemsetAsync(B.status, 0, sizeof(int), st) != cudaSuccess) return FD4_ERR_CUDA;
+    if (sel_forward(P, d_imgs, n_img, w, h, pitch, B, st)) return FD4_ERR_CUDA;
+    const int g = (int)((npx + 255) / 256 < 4096 ? (npx + 255) / 256 : 4096);
+    k_sel_softmax_ce<<<g, 256, 0, st>>>(B.logits, d_labels, B.dz16, n_img, w, h, pitch, stride,
+                                        1.0f / (float)((long long)n_img * w * h), d_loss);
+    ConvArgs a{};
+    a.n_img = n_img;
+    a.w = w;
+    a.h = h;
+    a.pitch = pitch;
+    a.img_stride = stride;
+    a.status = B.status;
+    // layer 3 (last): weight gradient, then data gradient into dz[0] masked by act[3] > 0
+    if (launch_wgrad<32, 16>(B.act[3], B.dz16, 3, P, n_img, w, h, pitch, st)) return FD4_ERR_CUDA;
+    a.in = B.dz16;
+    a.out = B.dz[0];
+    a.wts = P.dgr[3];
+    a.bias = nullptr;
+    a.mask = B.act[3];
+    a.d = DIL[3];
+    if (launch_conv<16, 32, CONV_MASK_BF16>(a, st)) return FD4_ERR_CUDA;
+    int cur = 0;
+    for (int l = 2; l >= 1; --l) {
+        if (launch_wgrad<32, 32>(B.act[l], B.dz[cur], l, P, n_img, w, h, pitch, st)) return FD4_ERR_CUDA;
+        a.in = B.dz[cur];
+        a.out = B.dz[cur ^ 1];
+        a.wts = P.dgr[l];
+        a.mask = B.act[l];
+        a.d = DIL[l];
+        if (launch_conv<32, 32, CONV_MASK_BF16>(a, st)) return FD4_ERR_CUDA;
+        cur ^= 1;
+    }
+    if (launch_wgrad<16, 32>(B.act[0], B.dz[cur], 0, P, n_img, w, h, pitch, st)) return FD4_ERR_CUDA;
+    return FD4_OK;
+}
+
+extern "C" int fd4_selector_update(void *d_params, float lr, int step, fd4_stream_t stream)
+{
+    if (!d_params || step < 1 || !(lr > 0.0f)) return FD4_ERR_BAD_ARG;
+    const SelLayout L = sel_layout();
+    const SelPtrs P = sel_ptrs(d_params);
+    cudaStream_t st = (cudaStream_t)stream;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = (float)(1.0 - pow(0.9, step)), c2 = (float)(1.0 - pow(0.999, step));
+    k_sel_adam<<<64, 256, 0, st>>>(P.master, P.m, P.v, P.grad, L.n_master, lr, b1, b2, 1e-8f, c1, c2);
+    if (sel_recast(d_params, st)) return FD4_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? FD4_OK : FD4_ERR_CUDA;
+}
+
+extern "C" int fd4_selector_predict(const void *d_params, const float *d_img, int w, int h, int pitch,
+                                    uint8_t *d_idx, float *d_conf, void *d_ws, size_t ws_bytes, fd4_stream_t stream)
+{
+    int rc;
+    if (!d_params || !d_idx) return FD4_ERR_BAD_ARG;
+    if ((rc = check_image(d_img, w, h, pitch)) != FD4_OK) return rc;
+    if (!d_ws || ws_bytes < fd4_selector_workspace_bytes(1, w, h, pitch)) return FD4_ERR_WS_TOO_SMALL;
+    cudaStream_t st = (cudaStream_t)stream;
+    SelBufs B = sel_bufs((char *)d_ws, (long long)h * pitch);
+    if (cudaMemsetAsync(B.status, 0, sizeof(int), st) != cudaSuccess) return FD4_ERR_CUDA;
+    if (sel_forward(sel_ptrs((void *)d_params), d_img, 1, w, h, pitch, B, st)) return FD4_ERR_CUDA;
+    const long long npx = (long long)h * pitch;
+    const int g = (int)((npx + 255) / 256 < 4096 ? (npx + 255) / 256 : 4096);
+    k_sel_predict<<<g, 256, 0, st>>>(B.logits, w, h, pitch, d_idx, d_conf);
+    return cudaGetLastError() == cudaSuccess ? FD4_OK : FD4_ERR_CUDA;
+}
+
+extern "C" int fd4_selector_status(const void *d_ws, int *status, fd4_stream_t stream)
+{
+    if (!d_ws || !status) return FD4_ERR_BAD_ARG;
+    if (cudaMemcpyAsync(status, d_ws, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
+        return FD4_ERR_CUDA;
+    return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? FD4_OK : FD4_ERR_CUDA;
+}

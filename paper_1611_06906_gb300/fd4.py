@@ -78,6 +78,19 @@ SIGNATURES = {
                                   _fp]),
 }
 NOALLOC_MAX_PIXELS = 4 * 1024 * 1024
+SELECTOR_SIGNATURES = {
+    "fd4_selector_param_bytes": (_sz, []),
+    "fd4_selector_workspace_bytes": (_sz, [_i, _i, _i, _i]),
+    "fd4_selector_set_weights": (_i, [_vp, _fp, _vp]),
+    "fd4_selector_get_weights": (_i, [_vp, _fp, _i, _vp]),
+    "fd4_selector_init": (_i, [_vp, ctypes.c_ulonglong, _vp]),
+    "fd4_selector_forward": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _sz, _vp]),
+    "fd4_selector_grad": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _sz, _vp]),
+    "fd4_selector_update": (_i, [_vp, ctypes.c_float, _i, _vp]),
+    "fd4_selector_predict": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _vp, _sz, _vp]),
+    "fd4_selector_status": (_i, [_vp, _ip, _vp]),
+}
+SIGNATURES.update(SELECTOR_SIGNATURES)
 
 
 def library_path() -> str:
@@ -334,3 +347,85 @@ def autotune_batched(imgs, sigmas, T: float, M: int, n: int = 0, prm: Params | N
                                       _ptr(ws), ws.numel(), _stream(stream), ctypes.byref(best), times),
            "fd4_autotune_batched")
     return best.value, list(times)
+
+
+# ---------------------------------------------------------------------------
+# Learned scale selector (network weights live in a caller-owned device buffer)
+
+SEL_BINS = 8
+SEL_LAYERS = [(1, 32), (32, 32), (32, 32), (32, SEL_BINS)]  # (in, out) channels
+
+
+def selector_n_master() -> int:
+    return sum(9 * co * ci + co for ci, co in SEL_LAYERS)
+
+
+class Selector:
+    """Parameters of the learned selector on the device and the calls on them."""
+
+    def __init__(self, device="cuda"):
+        torch = _torch()
+        self.device = device
+        self.params = torch.zeros(int(lib().fd4_selector_param_bytes()), dtype=torch.uint8, device=device)
+
+    def init(self, seed: int, stream=None):
+        _check(lib().fd4_selector_init(_ptr(self.params), int(seed), _stream(stream)), "fd4_selector_init")
+
+    def set_weights(self, flat: np.ndarray, stream=None):
+        f = np.ascontiguousarray(flat, dtype=np.float32)
+        assert f.size == selector_n_master()
+        _check(lib().fd4_selector_set_weights(_ptr(self.params), f.ctypes.data_as(_fp), _stream(stream)),
+               "fd4_selector_set_weights")
+
+    def get(self, which: int = 0, stream=None) -> np.ndarray:
+        """which: 0 weights, 1 Adam m, 2 Adam v, 3 accumulated gradients."""
+        f = np.zeros(selector_n_master(), dtype=np.float32)
+        _check(lib().fd4_selector_get_weights(_ptr(self.params), f.ctypes.data_as(_fp), int(which),
+                                              _stream(stream)), "fd4_selector_get_weights")
+        return f
+
+    @staticmethod
+    def workspace(n_img: int, w: int, h: int, pitch: int, device="cuda"):
+        torch = _torch()
+        return torch.empty(int(lib().fd4_selector_workspace_bytes(n_img, w, h, pitch)), dtype=torch.uint8,
+                           device=device)
+
+    def forward(self, imgs, w: int, ws=None, stream=None):
+        """imgs: (n, h, pitch) float32 -> logits (n, h, pitch, 8)."""
+        torch = _torch()
+        n, h, pitch = imgs.shape
+        ws = ws if ws is not None else self.workspace(n, w, h, pitch, imgs.device)
+        out = torch.empty((n, h, pitch, SEL_BINS), dtype=torch.float32, device=imgs.device)
+        _check(lib().fd4_selector_forward(_ptr(self.params), _ptr(imgs), n, int(w), h, pitch, _ptr(out), _ptr(ws),
+                                          ws.numel(), _stream(stream)), "fd4_selector_forward")
+        return out
+
+    def grad(self, imgs, labels, w: int, loss, ws=None, stream=None):
+        """Adds the loss gradient of the batch to the parameter buffer; loss += mean CE."""
+        n, h, pitch = imgs.shape
+        ws = ws if ws is not None else self.workspace(n, w, h, pitch, imgs.device)
+        _check(lib().fd4_selector_grad(_ptr(self.params), _ptr(imgs), _ptr(labels), n, int(w), h, pitch,
+                                       _ptr(loss), _ptr(ws), ws.numel(), _stream(stream)), "fd4_selector_grad")
+
+    def update(self, lr: float, step: int, stream=None):
+        _check(lib().fd4_selector_update(_ptr(self.params), float(lr), int(step), _stream(stream)),
+               "fd4_selector_update")
+
+    def predict(self, img, w: int, idx=None, conf=None, ws=None, stream=None):
+        """img: (h, pitch) float32 -> (scale index uint8, confidence float32), both (h, pitch)."""
+        torch = _torch()
+        h, pitch = img.shape
+        ws = ws if ws is not None else self.workspace(1, w, h, pitch, img.device)
+        if idx is None:
+            idx = torch.zeros((h, pitch), dtype=torch.uint8, device=img.device)
+        if conf is None:
+            conf = torch.zeros((h, pitch), dtype=torch.float32, device=img.device)
+        _check(lib().fd4_selector_predict(_ptr(self.params), _ptr(img), int(w), h, pitch, _ptr(idx), _ptr(conf),
+                                          _ptr(ws), ws.numel(), _stream(stream)), "fd4_selector_predict")
+        return idx, conf
+
+    @staticmethod
+    def status(ws, stream=None) -> int:
+        st = ctypes.c_int(0)
+        _check(lib().fd4_selector_status(_ptr(ws), ctypes.byref(st), _stream(stream)), "fd4_selector_status")
+        return st.value

@@ -1,0 +1,139 @@
+"""Learned scale selector on the tensor cores against its FP64 oracle.
+
+Tolerances come from the arithmetic: weights and activations are rounded to
+bf16 (relative 2^-9) before every layer and accumulated in FP32, so four
+layers carry a relative error of a few 1e-3 on the logits; the gradients go
+through bf16 gradients of the activations as well (relative ~1e-2)."""
+import numpy as np
+import pytest
+
+from oracle import selector_oracle as SO
+from paper_1611_06906_gb300 import fd4, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _flat(params):
+    return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in params]).astype(np.float32)
+
+
+def _unflat(flat):
+    out, o = [], 0
+    for ci, co in fd4.SEL_LAYERS:
+        n = 9 * co * ci
+        W = flat[o:o + n].reshape(3, 3, co, ci).astype(np.float64)
+        o += n
+        b = flat[o:o + co].astype(np.float64)
+        o += co
+        out.append((W, b))
+    return out
+
+
+def _stack(imgs):
+    import torch
+    h, w = imgs[0].shape
+    pitch = fd4.pitch_for(w)
+    t = torch.zeros((len(imgs), h, pitch), dtype=torch.float32, device="cuda")
+    for i, im in enumerate(imgs):
+        t[i, :, :w] = torch.from_numpy(im).cuda()
+    return t
+
+
+def _params(seed):
+    rng = np.random.default_rng(seed)
+    p = SO.init_params(rng)
+    return [(W, rng.normal(0, 0.05, size=b.shape)) for W, b in p]
+
+
+@pytest.mark.parametrize("shape", [(37, 150), (20, 128), (9, 300)])
+def test_forward_matches_oracle(shape):
+    h, w = shape
+    imgs = [synth.vessel_tree(7000 + i, w, h, depth=3, r0=3.0) for i in range(2)]
+    params = _params(1)
+    sel = fd4.Selector()
+    sel.set_weights(_flat(params))
+    logits = sel.forward(_stack(imgs), w).cpu().numpy()
+    for i, im in enumerate(imgs):
+        _, _, ref = SO.forward(im.astype(np.float64), _unflat(_flat(params)))
+        got = logits[i, :, :w, :]
+        scale = np.abs(ref).max() + 1.0
+        assert np.abs(got - ref).max() <= 2e-2 * scale
+        agree = (got.argmax(-1) == ref.argmax(-1)).mean()
+        assert agree >= 0.97
+
+
+def test_gradients_match_oracle():
+    import torch
+    h, w = 24, 140
+    imgs = [synth.vessel_tree(7100 + i, w, h, depth=3, r0=3.0) for i in range(2)]
+    params = _params(2)
+    flat = _flat(params)
+    rng = np.random.default_rng(3)
+    labels = rng.integers(0, 8, size=(2, h, w)).astype(np.uint8)
+    sel = fd4.Selector()
+    sel.set_weights(flat)
+    lab = torch.zeros((2, h, fd4.pitch_for(w)), dtype=torch.uint8, device="cuda")
+    lab[:, :, :w] = torch.from_numpy(labels).cuda()
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    sel.grad(_stack(imgs), lab, w, loss)
+    g = sel.get(3)
+    # the oracle's loss over both images (mean over all pixels of the stack)
+    P = _unflat(flat)
+    tot, grads = 0.0, None
+    for i in range(2):
+        l, gr = SO.loss_and_grads(imgs[i].astype(np.float64), labels[i], P)
+        tot += l / 2
+        gflat = np.concatenate([np.concatenate([gW.ravel(), gb.ravel()]) for gW, gb in gr]) / 2
+        grads = gflat if grads is None else grads + gflat
+    assert abs(float(loss.item()) - tot) <= 1e-2 * tot
+    o = 0
+    for ci, co in fd4.SEL_LAYERS:
+        n = 9 * co * ci + co
+        a, b = g[o:o + n], grads[o:o + n]
+        assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(b), (ci, co)
+        o += n
+    # the update consumes and clears the accumulated gradients
+    sel.update(1e-3, 1)
+    assert np.abs(sel.get(3)).max() == 0.0
+    assert np.abs(sel.get(0) - flat).max() > 0.0
+
+
+def test_predict_is_the_argmax_and_status_is_clean():
+    import torch
+    h, w = 50, 260
+    img = synth.vessel_tree(7200, w, h, depth=3, r0=3.0)
+    sel = fd4.Selector()
+    sel.init(5)
+    u = fd4.to_device(img)
+    ws = fd4.Selector.workspace(1, w, h, u.shape[1])
+    idx, conf = sel.predict(u, w, ws=ws)
+    logits = sel.forward(u[None], w)
+    torch.cuda.synchronize()
+    assert fd4.Selector.status(ws) == 0
+    ref = logits[0, :, :w].argmax(-1).to(torch.uint8)
+    assert torch.equal(idx[:, :w], ref)
+    c = conf[:, :w]
+    assert float(c.min()) >= 1.0 / 8 - 1e-6 and float(c.max()) <= 1.0
+
+
+def test_training_reduces_the_loss():
+    """A few Adam steps on labels from the plain selection lower the cross-entropy."""
+    import torch
+    h = w = 96
+    imgs = [synth.vessel_tree(7300 + i, w, h, depth=4, r0=4.0) for i in range(4)]
+    sig = list(synth.log_sigmas(1.0, 8.0, 8))
+    stack = _stack(imgs)
+    lab = torch.zeros(stack.shape, dtype=torch.uint8, device="cuda")
+    for i in range(4):
+        lab[i], _ = fd4.select_scales(stack[i], w, sig, fd4.params(mode=fd4.VALLEY))
+    sel = fd4.Selector()
+    sel.init(11)
+    ws = fd4.Selector.workspace(4, w, h, stack.shape[2])
+    losses = []
+    for step in range(1, 61):
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        sel.grad(stack, lab, w, loss, ws=ws)
+        sel.update(3e-3, step)
+        losses.append(float(loss.item()))
+    assert fd4.Selector.status(ws) == 0
+    assert np.mean(losses[-5:]) < 0.8 * losses[0]
