@@ -35,6 +35,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1611_06906_gb300.dist import max_over_ranks as _max_over_ranks, rank_seed  # noqa: E402
+
 METRIC = "Mpixel-steps/s, batched+learned vs plain GB300, at stated FP64-oracle error"
 UNIT = "Mpixel-steps/s"
 
@@ -50,10 +52,11 @@ def make_workload(name: str, rank: int, limit: int = 0):
     from paper_1611_06906_gb300 import synth
     wl = dict(synth.WORKLOADS[name])
     if name == "batch64_fundus":
-        sides = synth.batch_sides(3000 + 1000 * rank)
+        base = rank_seed(3000, rank)  # weak scaling: every rank filters its own batch
+        sides = synth.batch_sides(base)
         if limit:
             sides = sides[:limit]
-        seeds = [3000 + 1000 * rank + i for i in range(len(sides))]
+        seeds = [base + i for i in range(len(sides))]
         with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
             imgs = pool.map(_gen_one, list(zip(seeds, sides)))
     elif name == "tree_1024":
@@ -192,11 +195,7 @@ def run_fd4(args, rank, world, local_rank):
             dist.barrier()
 
     def max_over_ranks(ms):
-        if dist is None:
-            return ms
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return _max_over_ranks(ms, dev)
 
     # batched path: one launch per stage across the batch, replayed as a CUDA graph
     lst = fd4.image_list([b.u_in for b in ims], [b.w for b in ims], [b.out for b in ims], [b.idx for b in ims])
@@ -302,6 +301,8 @@ def run_fd4(args, rank, world, local_rank):
            "plain": {"value": plain_value, "ms_per_step": plain_ms,
                      "path": "per-image fd4_filter calls, one launch per FED step",
                      "speedup_of_batched": value / plain_value, "max_abs_diff_to_batched": diff_plain}}
+    if not args.no_learned:
+        out["learned"] = learned_variant(args, ims, sig, T, M, n, mode, best, stream, torch, fd4)
     if world == 1 and not args.no_cpu_baseline:
         res, secs, cores, pxs = oracle_sample(imgs, wl, mode)
         errs, agree, errs_inj = [], [], []
@@ -324,6 +325,64 @@ def run_fd4(args, rank, world, local_rank):
     for g in (g_all, g_sel, g_ten, g_fed):
         g.close()
     print(json.dumps(out), flush=True)
+
+
+def learned_variant(args, ims, sig, T, M, n, mode, best, stream, torch, fd4):
+    """Batched + learned path: the selector is trained here with the library's own
+    kernels (seeded 256^2 crops labelled by the plain selection), then a step is
+    the learned selection with plain fallback on low-confidence tiles, followed by
+    the batched filter with those scales given, replayed as a CUDA graph."""
+    from paper_1611_06906_gb300 import selector_train as ST
+    t0 = time.perf_counter()
+    crops, labels = ST.make_training_set(args.sel_crops, sig, mode)
+    sel = fd4.Selector()
+    sel.init(1)
+    losses = ST.train(sel, crops, labels, epochs=2, batch=32, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del crops, labels
+    prm = fd4.params(mode=mode, fed_steps_per_launch=best)
+    idx_l = [torch.zeros_like(b.idx) for b in ims]
+    outs_l = [torch.empty_like(b.u_in) for b in ims]
+    lst = fd4.image_list([b.u_in for b in ims], [b.w for b in ims], outs_l, idx_l)
+    ws = fd4.batch_workspace(lst, len(sig))
+    g = fd4.Graph(lst, sig, T, M, n, prm, sigma_given=True, ws=ws)
+    big = max(ims, key=lambda b: b.h * b.pitch)
+    wsl = torch.empty(int(fd4.lib().fd4_select_learned_workspace_bytes(big.pitch, big.h, big.pitch, len(sig))),
+                      dtype=torch.uint8, device=big.u_in.device)
+    thr = args.sel_threshold
+
+    def step():
+        for b, ix in zip(ims, idx_l):
+            sel.select_learned(b.u_in, b.w, sig, prm, conf_threshold=thr, idx=ix, ws=wsl)
+        g.launch()
+
+    step()
+    torch.cuda.synchronize()
+    ms = _timed(step, max(1, min(args.steps, 3)), stream, torch) / max(1, min(args.steps, 3))
+    px_steps = sum(b.npx for b in ims) * M * n
+    agree = sum(int((a[:, :b.w] == b.idx[:, :b.w]).sum().item()) for a, b in zip(idx_l, ims)) / sum(
+        b.npx for b in ims)
+    fb = 0
+    for b, ix in zip(ims, idx_l):
+        _, _, nfb = sel.select_learned(b.u_in, b.w, sig, prm, conf_threshold=thr, idx=ix, ws=wsl)
+        fb += int(nfb.item())
+    tiles = sum(((b.w + 31) // 32) * ((b.h + 63) // 64) for b in ims)
+    diff = max(float((o[:, :b.w] - b.out[:, :b.w]).abs().max()) for o, b in zip(outs_l, ims))
+    # the network alone (no fallback) for its agreement and time
+    def net_only():
+        for b, ix in zip(ims, idx_l):
+            sel.predict(b.u_in, b.w, idx=ix, ws=wsl)
+    net_ms = _timed(net_only, 1, stream, torch)
+    agree_net = sum(int((a[:, :b.w] == b.idx[:, :b.w]).sum().item()) for a, b in zip(idx_l, ims)) / sum(
+        b.npx for b in ims)
+    g.close()
+    return {"value": px_steps / (ms * 1e-3) / 1e6, "ms_per_step": ms, "conf_threshold": thr,
+            "sigma_agreement_with_plain": agree, "fallback_tile_fraction": fb / tiles,
+            "max_abs_diff_to_plain_batched": diff, "network_only_sigma_agreement": agree_net,
+            "network_only_ms": net_ms, "train": {"crops": args.sel_crops, "epochs": 2, "steps": len(losses),
+                                                 "loss_first": losses[0], "loss_last": float(np.mean(losses[-10:])),
+                                                 "seconds": train_s}}
 
 
 def run_reference(args, rank, world):
@@ -379,6 +438,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fed-steps", type=int, default=0, help="FED steps per launch (0: autotune)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the batched+learned variant")
+    ap.add_argument("--sel-crops", type=int, default=4096, help="training crops of the learned selector")
+    ap.add_argument("--sel-threshold", type=float, default=0.5, help="fallback confidence threshold")
     ap.add_argument("--only-graph", action="store_true", help="replay the full graph only (profiling)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per FED launch from an ncu capture of the current kernel")

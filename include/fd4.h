@@ -268,9 +268,33 @@ int fd4_selector_update(void *d_params, float lr, int step, fd4_stream_t stream)
 /* Scale index (argmax bin) and confidence (its probability) per pixel.     */
 int fd4_selector_predict(const void *d_params, const float *d_img, int w, int h, int pitch, uint8_t *d_idx,
                          float *d_conf, void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+/* Learned selection with the plain selection as fallback and judge.  The
+ * network predicts a scale index and a confidence (its softmax probability)
+ * per pixel; every 32 x 64 tile whose least confident pixel is below
+ * conf_threshold is recomputed with the plain vesselness selection
+ * (fd4_select_scales restricted to those tiles).  Reading for the restricted
+ * selection: c = half the maximum of S over the recomputed tiles (with every
+ * tile recomputed this is exactly fd4_select_scales).  n_sigma must be 8 (the
+ * network's bins); d_conf (nullable) receives the confidences, d_n_fallback
+ * (nullable, device int) the number of recomputed tiles.                    */
+size_t fd4_select_learned_workspace_bytes(int w, int h, int pitch, int n_sigma);
+int fd4_select_scales_learned(const void *d_params, const float *d_img, int w, int h, int pitch,
+                              const float *h_sigmas, int n_sigma, const fd4_params *params, float conf_threshold,
+                              uint8_t *d_sigma_idx, float *d_conf, int *d_n_fallback, void *d_ws,
+                              size_t ws_bytes, fd4_stream_t stream);
+
 /* Device status word of a selector workspace (FD4_ERR_TIMEOUT if a bounded
  * wait in a tensor-core kernel gave up), read synchronously.                */
 int fd4_selector_status(const void *d_ws, int *status, fd4_stream_t stream);
+
+/* Failure-detection self-test (no counterpart in the paper): launches the
+ * tensor-core convolution with its MMA commit withheld, so the kernel's
+ * bounded wait (about one second) runs out; the kernel records
+ * FD4_ERR_TIMEOUT in the workspace status word, frees its tensor memory and
+ * returns, leaving the context usable.  *status receives the status word read
+ * back (FD4_ERR_TIMEOUT when detection works).  Synchronous; d_ws needs
+ * fd4_selector_workspace_bytes(1, 128, 4, 128) bytes.                       */
+int fd4_selftest_wait_timeout(void *d_ws, size_t ws_bytes, int *status, fd4_stream_t stream);
 
 /* Allocation-free FED cycle.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory -- host applications

@@ -167,59 +167,18 @@ struct StepTaus {
     int n;
 };
 
-template <int S>
-__global__ void __launch_bounds__(FNT, 2) k_fed_fused(Imgs I, StepTaus taus, int parity, int periodic)
+// The S steps of one staged region.  INTERIOR: the region lies inside the
+// image (natural boundary), so every derivative row exists and no mask or
+// bounds test is needed; otherwise per-pixel masks follow the natural (or
+// periodic) boundary.  rowbits: bit j = pixel row j of the segment is inside
+// the image, bit 8 + j = its Lyy row exists.
+template <bool INTERIOR>
+__device__ __forceinline__ void fused_steps(float (*su)[FRX], float (*sxx)[FRX], float (*sxy)[FRX],
+                                            float (*syy)[FRX], const float *stau, int nsteps, int rx, int ry0,
+                                            const float4 (&tv)[FV], bool in_x, bool vx, unsigned rowbits)
 {
-    constexpr int H = 2 * S, TXo = FRX - 2 * H, TYo = FRY - 2 * H;
-    extern __shared__ float fsm[];
-    float (*su)[FRX] = reinterpret_cast<float (*)[FRX]>(fsm);
-    float (*sxx)[FRX] = reinterpret_cast<float (*)[FRX]>(fsm + FRX * FRY);
-    float (*sxy)[FRX] = reinterpret_cast<float (*)[FRX]>(fsm + 2 * FRX * FRY);
-    float (*syy)[FRX] = reinterpret_cast<float (*)[FRX]>(fsm + 3 * FRX * FRY);
-    __shared__ float stau[8];
-    __shared__ ImgDesc sd;
-    __shared__ int s_local;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < 8) stau[tid] = taus.t[tid];
-    // this thread's column segment of the staged region
-    const int rx = (warp % (FRX / 32)) * 32 + lane, ry0 = (warp / (FRX / 32)) * FV;
     const int xl = rx > 0 ? rx - 1 : 0, xr = rx < FRX - 1 ? rx + 1 : FRX - 1;
-
-    for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
-    __syncthreads();
-    if (tid == 0) find_tile(I, S, t, sd, s_local);
-    __syncthreads();
-    const int w = sd.w, h = sd.h, pitch = sd.pitch;
-    const float *uin = parity ? sd.tmp : sd.u;
-    float *uout = parity ? sd.u : sd.tmp;
-    const float4 *ten = sd.tensor;
-    const int tiles_x = (w + TXo - 1) / TXo;
-    const int gx0 = (s_local % tiles_x) * TXo - H, gy0 = (s_local / tiles_x) * TYo - H;
-
-    for (int i = tid; i < FRX * FRY; i += FNT) {
-        const int ry = i / FRX, rxx = i - ry * FRX;
-        const int gx = gx0 + rxx, gy = gy0 + ry;
-        float v = 0.0f;
-        if (periodic) v = uin[(size_t)wrap(gy, h) * pitch + wrap(gx, w)];
-        else if (gx >= 0 && gx < w && gy >= 0 && gy < h) v = uin[(size_t)gy * pitch + gx];
-        su[ry][rxx] = v;
-    }
-
-    // the tensor values of this thread's pixels (D is frozen over the cycle)
-    const int gx = gx0 + rx;
-    const int pgx = periodic ? wrap(gx, w) : gx;
-    const bool in_x = periodic || (gx >= 0 && gx < w);
-    const bool vx = periodic || (gx >= 1 && gx <= w - 2);
-    float4 tv[FV];
-#pragma unroll
-    for (int j = 0; j < FV; ++j) {
-        const int gy = gy0 + ry0 + j;
-        const bool in = in_x && (periodic || (gy >= 0 && gy < h));
-        tv[j] = in ? __ldg(ten + (size_t)(periodic ? wrap(gy, h) : gy) * pitch + pgx) : make_float4(1.f, 0.f, 0.f, 0.f);
-    }
-    __syncthreads();
-
-    for (int l = 0; l < taus.n; ++l) {
+    for (int l = 0; l < nsteps; ++l) {
         // T = M D M L u where the region shrunk by 2l+1 holds valid data
         const int lo_t = 2 * l + 1;
         const bool col_t = rx >= lo_t && rx < FRX - lo_t;
@@ -233,14 +192,14 @@ __global__ void __launch_bounds__(FNT, 2) k_fed_fused(Imgs I, StepTaus taus, int
                 const int rp = ry + 1 < FRY ? ry + 1 : FRY - 1;
                 const float cL = su[rp][xl], cC = su[rp][rx], cR = su[rp][xr];
                 if (col_t && ry >= lo_t && ry < FRY - lo_t) {
-                    const int gy = gy0 + ry;
-                    const bool in = in_x && (periodic || (gy >= 0 && gy < h));
-                    const bool vy = periodic || (gy >= 1 && gy <= h - 2);
+                    const bool in = INTERIOR || (in_x && ((rowbits >> j) & 1u));
+                    const bool vy = INTERIOR || ((rowbits >> (8 + j)) & 1u);
+                    const bool vxx = INTERIOR || vx;
                     float Txx = 0.0f, Txy = 0.0f, Tyy = 0.0f;
-                    if (in && (vx || vy)) {
-                        const float hxx = vx ? bL - 2.0f * bC + bR : 0.0f;
+                    if (in && (vxx || vy)) {
+                        const float hxx = vxx ? bL - 2.0f * bC + bR : 0.0f;
                         const float hyy = vy ? aC - 2.0f * bC + cC : 0.0f;
-                        const float hxy = (vx && vy) ? 0.25f * (aL + cR - cL - aR) : 0.0f;
+                        const float hxy = (vxx && vy) ? 0.25f * (aL + cR - cL - aR) : 0.0f;
                         const float4 tt = tv[j];
                         const float sh = 0.5f * (hxx + hyy), dh = 0.5f * (hxx - hyy);
                         const float h11 = sh + tt.x * dh + tt.y * hxy;
@@ -248,9 +207,9 @@ __global__ void __launch_bounds__(FNT, 2) k_fed_fused(Imgs I, StepTaus taus, int
                         const float h12 = tt.x * hxy - tt.y * dh;
                         const float t11 = tt.z * h11, t22 = tt.w * h22, t12 = 0.5f * (tt.z + tt.w) * h12;
                         const float st = 0.5f * (t11 + t22), dt = 0.5f * (t11 - t22);
-                        Txx = vx ? st + tt.x * dt - tt.y * t12 : 0.0f;
+                        Txx = vxx ? st + tt.x * dt - tt.y * t12 : 0.0f;
                         Tyy = vy ? st - tt.x * dt + tt.y * t12 : 0.0f;
-                        Txy = (vx && vy) ? tt.y * dt + tt.x * t12 : 0.0f;
+                        Txy = (vxx && vy) ? tt.y * dt + tt.x * t12 : 0.0f;
                     }
                     sxx[ry][rx] = Txx;
                     sxy[ry][rx] = Txy;
@@ -275,8 +234,7 @@ __global__ void __launch_bounds__(FNT, 2) k_fed_fused(Imgs I, StepTaus taus, int
                 const float yC = syy[rp][rx];
                 const float dLC = sxy[rp][xl], dRC = sxy[rp][xr];
                 if (ry >= lo_u && ry < FRY - lo_u) {
-                    const int gy = gy0 + ry;
-                    const bool in = in_x && (periodic || (gy >= 0 && gy < h));
+                    const bool in = INTERIOR || (in_x && ((rowbits >> j) & 1u));
                     if (in) {
                         const float div = (sxx[ry][xl] - 2.0f * sxx[ry][rx] + sxx[ry][xr]) +
                                           (yA - 2.0f * yB + yC) + 0.5f * (dRC + dLA - dRA - dLC);
@@ -290,13 +248,81 @@ __global__ void __launch_bounds__(FNT, 2) k_fed_fused(Imgs I, StepTaus taus, int
         }
         __syncthreads();
     }
+}
 
-    for (int i = tid; i < TXo * TYo; i += FNT) {
-        const int ty = i / TXo, tx = i - ty * TXo;
-        const int ox = gx0 + H + tx, oy = gy0 + H + ty;
-        if (ox < w && oy < h) uout[(size_t)oy * pitch + ox] = su[H + ty][H + tx];
+template <int S>
+__global__ void __launch_bounds__(FNT, 2) k_fed_fused(Imgs I, StepTaus taus, int parity, int periodic)
+{
+    constexpr int H = 2 * S, TXo = FRX - 2 * H, TYo = FRY - 2 * H;
+    extern __shared__ float fsm[];
+    float (*su)[FRX] = reinterpret_cast<float (*)[FRX]>(fsm);
+    float (*sxx)[FRX] = reinterpret_cast<float (*)[FRX]>(fsm + FRX * FRY);
+    float (*sxy)[FRX] = reinterpret_cast<float (*)[FRX]>(fsm + 2 * FRX * FRY);
+    float (*syy)[FRX] = reinterpret_cast<float (*)[FRX]>(fsm + 3 * FRX * FRY);
+    __shared__ float stau[8];
+    __shared__ ImgDesc sd;
+    __shared__ int s_local;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 8) stau[tid] = taus.t[tid];
+    // this thread's column segment of the staged region
+    const int rx = (warp % (FRX / 32)) * 32 + lane, ry0 = (warp / (FRX / 32)) * FV;
+
+    for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
+        __syncthreads();
+        if (tid == 0) find_tile(I, S, t, sd, s_local);
+        __syncthreads();
+        const int w = sd.w, h = sd.h, pitch = sd.pitch;
+        const float *uin = parity ? sd.tmp : sd.u;
+        float *uout = parity ? sd.u : sd.tmp;
+        const float4 *ten = sd.tensor;
+        const int tiles_x = (w + TXo - 1) / TXo;
+        const int gx0 = (s_local % tiles_x) * TXo - H, gy0 = (s_local / tiles_x) * TYo - H;
+        const bool interior = !periodic && gx0 >= 0 && gy0 >= 0 && gx0 + FRX <= w && gy0 + FRY <= h;
+
+        if (interior) {
+            for (int i = tid; i < FRX * FRY; i += FNT) {
+                const int ry = i / FRX, rxx = i - ry * FRX;
+                su[ry][rxx] = uin[(size_t)(gy0 + ry) * pitch + gx0 + rxx];
+            }
+        } else {
+            for (int i = tid; i < FRX * FRY; i += FNT) {
+                const int ry = i / FRX, rxx = i - ry * FRX;
+                const int gx = gx0 + rxx, gy = gy0 + ry;
+                float v = 0.0f;
+                if (periodic) v = uin[(size_t)wrap(gy, h) * pitch + wrap(gx, w)];
+                else if (gx >= 0 && gx < w && gy >= 0 && gy < h) v = uin[(size_t)gy * pitch + gx];
+                su[ry][rxx] = v;
+            }
+        }
+
+        // the tensor values of this thread's pixels (D is frozen over the cycle)
+        const int gx = gx0 + rx;
+        const int pgx = periodic ? wrap(gx, w) : gx;
+        const bool in_x = periodic || (gx >= 0 && gx < w);
+        const bool vx = periodic || (gx >= 1 && gx <= w - 2);
+        unsigned rowbits = 0u;
+        float4 tv[FV];
+#pragma unroll
+        for (int j = 0; j < FV; ++j) {
+            const int gy = gy0 + ry0 + j;
+            const bool iny = periodic || (gy >= 0 && gy < h);
+            const bool vy = periodic || (gy >= 1 && gy <= h - 2);
+            rowbits |= (iny ? 1u : 0u) << j;
+            rowbits |= (vy ? 1u : 0u) << (8 + j);
+            tv[j] = (in_x && iny) ? __ldg(ten + (size_t)(periodic ? wrap(gy, h) : gy) * pitch + pgx)
+                                  : make_float4(1.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+
+        if (interior) fused_steps<true>(su, sxx, sxy, syy, stau, taus.n, rx, ry0, tv, in_x, vx, rowbits);
+        else fused_steps<false>(su, sxx, sxy, syy, stau, taus.n, rx, ry0, tv, in_x, vx, rowbits);
+
+        for (int i = tid; i < TXo * TYo; i += FNT) {
+            const int ty = i / TXo, tx = i - ty * TXo;
+            const int ox = gx0 + H + tx, oy = gy0 + H + ty;
+            if (ox < w && oy < h) uout[(size_t)oy * pitch + ox] = su[H + ty][H + tx];
+        }
     }
-    }  // tile loop
 }
 
 }  // namespace

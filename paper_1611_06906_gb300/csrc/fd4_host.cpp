@@ -449,6 +449,8 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
         B->I.n = n;
         B->I.tiles = 0;
         B->I.one = ImgDesc{};
+        B->I.list = nullptr;
+        B->I.count = nullptr;
         for (int s = 0; s < kShapes; ++s) B->tiles[s] = t0[s];
         B->max_s2 = (unsigned *)(ws + ms_off);
         B->n_max_s2 = n;

@@ -67,6 +67,11 @@ struct Imgs {
     int n;
     int tiles;           // total tiles for the launched kernel's shape
     ImgDesc one;
+    // Optional subset (single image, sweep tiles): list[0 .. *count) holds the
+    // SHAPE_SWEEP tiles to process; a SHAPE_SMALL kernel then processes the 8
+    // small tiles (32 x 8) covering each listed 32 x 64 sweep tile.
+    const int *list;
+    const int *count;
 };
 
 inline int tiles_of(int w, int h, int shape)
@@ -79,6 +84,8 @@ inline Imgs single(const ImgDesc &d0, int shape)
 {
     Imgs I;
     I.table = nullptr;
+    I.list = nullptr;
+    I.count = nullptr;
     I.n = 1;
     I.one = d0;
     for (int s = 0; s < kShapes; ++s) I.one.t0[s] = 0;
@@ -94,6 +101,14 @@ __device__ __forceinline__ void find_tile(const Imgs &I, int shape, int t, ImgDe
     if (I.table == nullptr) {
         out = I.one;
         local = t;
+        if (I.list) {
+            if (shape == SHAPE_SWEEP) {
+                local = I.list[t];
+            } else {  // small tile k of listed sweep tile t / 8 (both tile grids are 32 wide)
+                const int st = I.list[t >> 3], tx = (out.w + 31) / 32;
+                local = (8 * (st / tx) + (t & 7)) * tx + st % tx;
+            }
+        }
         return;
     }
     int lo = 0, hi = I.n - 1;
@@ -104,6 +119,13 @@ __device__ __forceinline__ void find_tile(const Imgs &I, int shape, int t, ImgDe
     }
     out = I.table[lo];
     local = t - out.t0[shape];
+}
+// Number of tiles a persistent kernel walks: the host count, or the device
+// count of a tile list (8 small tiles per listed sweep tile).
+__device__ __forceinline__ int tile_count(const Imgs &I, int shape)
+{
+    if (I.list) return shape == SHAPE_SWEEP ? *I.count : 8 * *I.count;
+    return I.tiles;
 }
 #endif
 
@@ -153,6 +175,8 @@ int launch_tensor_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, 
 // 1 = one launch per step (k_fed_step), 2..4 = k_fed_fused<S>.
 int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundary, int steps_per_launch,
                      cudaStream_t st);
+int launch_select_tiles(const ImgDesc &d, const int *list, const int *count, const float *h_sigmas, int n_sigma,
+                        const fd4_params &p, cudaStream_t st);
 // Sets the shared-memory attributes of every kernel (call before stream capture).
 int prepare_scale_kernels();
 int prepare_fed_kernels();

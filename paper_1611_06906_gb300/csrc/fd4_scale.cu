@@ -20,13 +20,14 @@ namespace {
 
 constexpr int TX = 32;        // output tile width
 constexpr int TY = 64;        // output tile height
-constexpr int V = 8;          // outputs per thread in both passes
-constexpr int NT = 256;       // threads per block
+constexpr int VR = 8;         // row pass: outputs per thread along x
+constexpr int VC = 4;         // column pass: outputs per thread along y
+constexpr int NT = 512;       // threads per block
 constexpr int RS = TX + 1;    // row-pass output stride (conflict-free column reads)
 constexpr int kMaxSweep = 16; // scales per launch
 constexpr int kSweepFloats = kMaxSweep * 3 * (2 * kMaxRadius + 4);
 
-static_assert(TX * (TY / V) == NT, "column pass: one unit per thread");
+static_assert(TX * (TY / VC) == NT, "column pass: one unit per thread");
 
 // Taps of up to kMaxSweep scales.  Scale s uses the padded radius R[s] (a
 // multiple of 4, >= ceil(4 sigma)); its three kernels w0, w1, w2 (smoothing,
@@ -83,16 +84,16 @@ __device__ __forceinline__ float det2_sym(float a, float b, float d)
 enum { OUT_SELECT = 0, OUT_TENSOR = 1 };
 
 // Column pass of one field over the 12-row register window: acc_a += wa * field
-// (and acc_b += wb * field when TWO), V outputs down one column.
+// (and acc_b += wb * field when TWO), VC outputs down one column.
 template <bool TWO>
 __device__ __forceinline__ void column_pass(const float *src, const float *wa, const float *wb, int nch,
-                                            float (&acc_a)[V], float (&acc_b)[V])
+                                            float (&acc_a)[VC], float (&acc_b)[VC])
 {
-    float win[V + 4];
+    float win[VC + 4];
 #pragma unroll
-    for (int q = 0; q < V + 4; ++q) win[q] = src[q * RS];
+    for (int q = 0; q < VC + 4; ++q) win[q] = src[q * RS];
 #pragma unroll
-    for (int j = 0; j < V; ++j) {
+    for (int j = 0; j < VC; ++j) {
         acc_a[j] = 0.0f;
         if (TWO) acc_b[j] = 0.0f;
     }
@@ -105,16 +106,16 @@ __device__ __forceinline__ void column_pass(const float *src, const float *wa, c
 #pragma unroll
         for (int ii = 0; ii < 4; ++ii) {
 #pragma unroll
-            for (int j = 0; j < V; ++j) {
+            for (int j = 0; j < VC; ++j) {
                 acc_a[j] = fmaf(av[ii], win[j + ii], acc_a[j]);
                 if (TWO) acc_b[j] = fmaf(bv[ii], win[j + ii], acc_b[j]);
             }
         }
         if (ch + 1 < nch) {
 #pragma unroll
-            for (int q = 0; q < V; ++q) win[q] = win[q + 4];
+            for (int q = 0; q < VC; ++q) win[q] = win[q + 4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) win[V + q] = src[(4 * ch + V + 4 + q) * RS];
+            for (int q = 0; q < 4; ++q) win[VC + q] = src[(4 * ch + VC + 4 + q) * RS];
         }
     }
 }
@@ -136,7 +137,8 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < taps.wfloats; i += NT) wt[i] = taps.w[i];
 
-    for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
+    const int ntiles = tile_count(I, SHAPE_SWEEP);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     __syncthreads();   // the previous tile is done with shared memory
     if (tid == 0) {
         find_tile(I, SHAPE_SWEEP, t, sd, s_local);
@@ -152,19 +154,21 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
         for (int rx = lane; rx < in_w; rx += 32) tin[ry * S + rx] = __ldg(src + mirror(x0 - Rmax + rx, w));
     }
 
-    const int ox = tid & 31, oy0 = (tid >> 5) * V;
+    const int ox = tid & 31, oy0 = (tid >> 5) * VC;
     const int gx = x0 + ox;
-    float nxx[V], nxy[V], nyy[V];
-    int my_idx[V];
+    // tensor mode: this thread's 8 pixels' scale index within this launch (-1: none)
+    int my_local[VC];
     if (OUT == OUT_TENSOR) {
         unsigned bits = 0u;
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
-            nxx[j] = nxy[j] = nyy[j] = 0.0f;
+        for (int j = 0; j < VC; ++j) {
             const int gy = y0 + oy0 + j;
-            my_idx[j] = (gx < w && gy < h) ? (int)sd.idx[(size_t)gy * pitch + gx] : 255;
-            const int local = my_idx[j] - taps.s0;
-            if (local >= 0 && local < taps.K) bits |= 1u << local;
+            const int id = (gx < w && gy < h) ? (int)sd.idx[(size_t)gy * pitch + gx] : -1;
+            if (id >= 0 && taps.s0 == 0 && id >= taps.K_total)   // index outside the set: N = 0
+                sd.nfield[(size_t)gy * pitch + gx] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int local = id - taps.s0;
+            my_local[j] = (id >= 0 && local >= 0 && local < taps.K) ? local : -1;
+            if (my_local[j] >= 0) bits |= 1u << my_local[j];
         }
         if (bits) atomicOr(&present, bits);
     }
@@ -180,10 +184,10 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
 
         // Row pass on staged rows [off, off + TY + 2R + 4): three fields along x.
         const int nrows = TY + 2 * R + 4;
-        for (int u = tid; u < nrows * (TX / V); u += NT) {
-            const int sy = off + (u >> 2), xo = (u & 3) * V;
+        for (int u = tid; u < nrows * (TX / VR); u += NT) {
+            const int sy = off + (u >> 2), xo = (u & 3) * VR;
             const float *src = tin + sy * S + xo + off;
-            float win[V + 4];
+            float win[VR + 4];
             {
                 const float4 a = *reinterpret_cast<const float4 *>(src);
                 const float4 b = *reinterpret_cast<const float4 *>(src + 4);
@@ -192,9 +196,9 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
                 win[4] = b.x; win[5] = b.y; win[6] = b.z; win[7] = b.w;
                 win[8] = c.x; win[9] = c.y; win[10] = c.z; win[11] = c.w;
             }
-            float a0[V], a1[V], a2[V];
+            float a0[VR], a1[VR], a2[VR];
 #pragma unroll
-            for (int j = 0; j < V; ++j) a0[j] = a1[j] = a2[j] = 0.0f;
+            for (int j = 0; j < VR; ++j) a0[j] = a1[j] = a2[j] = 0.0f;
             for (int ch = 0; ch < nch; ++ch) {
                 const float4 W0 = *reinterpret_cast<const float4 *>(w0 + 4 * ch);
                 const float4 W1 = *reinterpret_cast<const float4 *>(w1 + 4 * ch);
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
 #pragma unroll
                 for (int ii = 0; ii < 4; ++ii) {
 #pragma unroll
-                    for (int j = 0; j < V; ++j) {
+                    for (int j = 0; j < VR; ++j) {
                         a0[j] = fmaf(c0[ii], win[j + ii], a0[j]);
                         a1[j] = fmaf(c1[ii], win[j + ii], a1[j]);
                         a2[j] = fmaf(c2[ii], win[j + ii], a2[j]);
@@ -213,14 +217,14 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
                 }
                 if (ch + 1 < nch) {
 #pragma unroll
-                    for (int q = 0; q < V; ++q) win[q] = win[q + 4];
+                    for (int q = 0; q < VR; ++q) win[q] = win[q + 4];
                     const float4 d = *reinterpret_cast<const float4 *>(src + 4 * ch + 12);
                     win[8] = d.x; win[9] = d.y; win[10] = d.z; win[11] = d.w;
                 }
             }
             float *d0 = trow + sy * RS + xo;
 #pragma unroll
-            for (int j = 0; j < V; ++j) {
+            for (int j = 0; j < VR; ++j) {
                 d0[j] = a0[j];
                 d0[rows * RS + j] = a1[j];
                 d0[2 * rows * RS + j] = a2[j];
@@ -228,21 +232,70 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
         }
         __syncthreads();
 
-        // Column pass: tile column ox, tile rows oy0 .. oy0 + V - 1.
-        const float *col = trow + (oy0 + off) * RS + ox;
-        float uxx[V], uxy[V], uyy[V], ux[V], uy[V];
-        column_pass<false>(col + 2 * rows * RS, w0, w0, nch, uxx, uxx);      // d2/dx2, smoothed in y
         if (OUT == OUT_TENSOR) {
-            column_pass<true>(col + rows * RS, w0, w1, nch, ux, uxy);        // d/dx: smoothed / d/dy
-            column_pass<true>(col, w1, w2, nch, uy, uyy);                   // smoothed in x: d/dy, d2/dy2
-        } else {
-            column_pass<false>(col + rows * RS, w1, w1, nch, uxy, uxy);
-            column_pass<false>(col, w2, w2, nch, uyy, uyy);
+            // Column pass only for the pixels whose selected scale is this one.
+            // Each warp packs its matching pixels (rows oy0.., all 32 columns)
+            // 32 at a time with ballots and evaluates the five derivatives of
+            // each as direct tap sums, one pixel per lane.
+            int entry = -1, pending = 0;
+#pragma unroll
+            for (int j = 0; j <= VC; ++j) {
+                unsigned m = j < VC ? __ballot_sync(0xffffffffu, my_local[j] == s) : 0u;
+                while (m != 0u || (j == VC && pending > 0)) {
+                    const int take = min(__popc(m), 32 - pending);
+                    const int r = lane - pending;
+                    if (r >= 0 && r < take) entry = ((oy0 + j) << 5) | (int)__fns(m, 0, r + 1);
+                    for (int q = 0; q < take; ++q) m &= m - 1u;   // drop the taken bits
+                    pending += take;
+                    if (pending == 32 || (j == VC && pending > 0)) {
+                        if (entry >= 0) {
+                            const int px = entry & 31, py = entry >> 5;
+                            const float *c0 = trow + (py + off) * RS + px;   // field 0: smoothed along x
+                            const float *c1 = c0 + rows * RS;                 // field 1: d/dx
+                            const float *c2 = c1 + rows * RS;                 // field 2: d2/dx2
+                            float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
+                            for (int ch = 0; ch < nch; ++ch) {
+                                const float4 A = *reinterpret_cast<const float4 *>(w0 + 4 * ch);
+                                const float4 B = *reinterpret_cast<const float4 *>(w1 + 4 * ch);
+                                const float4 C = *reinterpret_cast<const float4 *>(w2 + 4 * ch);
+                                const float a4[4] = {A.x, A.y, A.z, A.w}, b4[4] = {B.x, B.y, B.z, B.w};
+                                const float c4[4] = {C.x, C.y, C.z, C.w};
+#pragma unroll
+                                for (int ii = 0; ii < 4; ++ii) {
+                                    const int k = (4 * ch + ii) * RS;
+                                    const float v0 = c0[k], v1 = c1[k], v2 = c2[k];
+                                    sy = fmaf(b4[ii], v0, sy);
+                                    syy = fmaf(c4[ii], v0, syy);
+                                    sx = fmaf(a4[ii], v1, sx);
+                                    sxy = fmaf(b4[ii], v1, sxy);
+                                    sxx = fmaf(a4[ii], v2, sxx);
+                                }
+                            }
+                            const float g2 = fmaf(sx, sx, sy * sy);
+                            const float g = grad_sq ? g2 : sqrtf(g2);
+                            const float f = 1.0f / sqrtf(1.0f + g);
+                            sd.nfield[(size_t)(y0 + py) * pitch + x0 + px] =
+                                make_float4(f * sxx, f * sxy, f * syy, 0.0f);
+                        }
+                        entry = -1;
+                        pending = 0;
+                    }
+                    if (j == VC) break;
+                }
+            }
+            __syncthreads();   // trow is rewritten by the next scale's row pass
+            continue;
         }
+        // Column pass: tile column ox, tile rows oy0 .. oy0 + VC - 1.
+        const float *col = trow + (oy0 + off) * RS + ox;
+        float uxx[VC], uxy[VC], uyy[VC];
+        column_pass<false>(col + 2 * rows * RS, w0, w0, nch, uxx, uxx);      // d2/dx2, smoothed in y
+        column_pass<false>(col + rows * RS, w1, w1, nch, uxy, uxy);          // d/dx, then d/dy
+        column_pass<false>(col, w2, w2, nch, uyy, uyy);                      // d2/dy2 of the x-smoothed field
         __syncthreads();   // trow is rewritten by the next scale's row pass
 
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
+        for (int j = 0; j < VC; ++j) {
             const int gy = y0 + oy0 + j;
             if (gx >= w || gy >= h) continue;
             const float a = uxx[j], b = uxy[j], d = uyy[j];
@@ -264,13 +317,6 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
                 sd.vp[(size_t)(taps.s0 + s) * sd.plane + p] = vp;
                 sd.s2[(size_t)(taps.s0 + s) * sd.plane + p] = s2;
                 bmax = fmaxf(bmax, s2);
-            } else if (my_idx[j] == taps.s0 + s) {
-                const float g2 = fmaf(ux[j], ux[j], uy[j] * uy[j]);
-                const float g = grad_sq ? g2 : sqrtf(g2);
-                const float f = 1.0f / sqrtf(1.0f + g);
-                nxx[j] = f * a;
-                nxy[j] = f * b;
-                nyy[j] = f * d;
             }
         }
     }
@@ -279,16 +325,6 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
         if (lane == 0 && bmax > 0.0f) atomicMax(sd.max_s2, __float_as_uint(bmax));
-    } else {
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            const int gy = y0 + oy0 + j;
-            if (gx >= w || gy >= h) continue;
-            const int local = my_idx[j] - taps.s0;
-            const bool mine = local >= 0 && local < taps.K;
-            const bool orphan = taps.s0 == 0 && my_idx[j] >= taps.K_total;   // out-of-range index: N = 0
-            if (mine || orphan) sd.nfield[(size_t)gy * pitch + gx] = make_float4(nxx[j], nxy[j], nyy[j], 0.0f);
-        }
     }
     }  // tile loop
 }
@@ -301,7 +337,8 @@ __global__ void __launch_bounds__(256) k_select_argmax(Imgs I, int K, float c_us
     __shared__ ImgDesc sd;
     __shared__ int s_local;
     const int tid = threadIdx.x;
-    for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
+    const int ntiles = tile_count(I, SHAPE_SMALL);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         __syncthreads();
         if (tid == 0) find_tile(I, SHAPE_SMALL, t, sd, s_local);
         __syncthreads();
@@ -514,6 +551,18 @@ int launch_tensor_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, 
     const int grid = persistent_grid((const void *)k_tensor_finish, FX * FY, 0, I.tiles);
     k_tensor_finish<<<grid, FX * FY, 0, st>>>(I, rt, p.lambda, p.mode);
     return cudaGetLastError() != cudaSuccess;
+}
+
+// Plain selection on a subset of the 32 x 64 sweep tiles of one image (device
+// list of *count tiles): selection planes, the image's max S^2 over those
+// tiles, and the argmax written into d.idx on them only.
+int launch_select_tiles(const ImgDesc &d, const int *list, const int *count, const float *h_sigmas, int n_sigma,
+                        const fd4_params &p, cudaStream_t st)
+{
+    HostBatch B = single_batch(d);
+    B.I.list = list;
+    B.I.count = count;
+    return launch_select_batch(B, h_sigmas, n_sigma, p, st);
 }
 
 // Single-image stages: workspace [header | planes], descriptor passed inline.

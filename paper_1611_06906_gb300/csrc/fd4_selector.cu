@@ -49,6 +49,7 @@ struct ConvArgs {
     long long img_stride;       // pixels between consecutive images
     int n_out;                  // CONV_LOGITS_F32: channels written per pixel
     int *status;                // FD4_ERR_TIMEOUT if a wait gives up
+    int withhold_commit;        // self-test only: issue no MMA, so the wait runs out
 };
 
 __host__ __device__ inline size_t conv_smem_bytes(int CI, int CO, int d)
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(CT) k_conv_tc(ConvArgs a)
         }
         tc::fence_proxy_async();
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !a.withhold_commit) {
             tc::fence_after_sync();
             const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs);
             uint32_t acc = 0;
@@ -448,6 +449,30 @@ __global__ void k_sel_predict(const float *logits, int w, int h, int pitch, uint
     }
 }
 
+// Tiles (32 x 64, the scale sweep's tiling) whose least confident pixel is
+// below thr go to the fallback list.
+__global__ void __launch_bounds__(256) k_sel_fallback_tiles(const float *conf, int w, int h, int pitch, float thr,
+                                                            int *list, int *count)
+{
+    __shared__ float red[8];
+    const int tiles_x = (w + 31) / 32;
+    const int t = blockIdx.x;
+    const int x0 = (t % tiles_x) * 32, y0 = (t / tiles_x) * 64;
+    float m = 1.0f;
+    for (int i = threadIdx.x; i < 32 * 64; i += 256) {
+        const int x = x0 + (i & 31), y = y0 + (i >> 5);
+        if (x < w && y < h) m = fminf(m, conf[(size_t)y * pitch + x]);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < 8; ++i) m = fminf(m, red[i]);
+        m = fminf(m, red[0]);
+        if (m < thr) list[atomicAdd(count, 1)] = t;
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -772,4 +797,102 @@ extern "C" int fd4_selector_status(const void *d_ws, int *status, fd4_stream_t s
     if (cudaMemcpyAsync(status, d_ws, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
         return FD4_ERR_CUDA;
     return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? FD4_OK : FD4_ERR_CUDA;
+}
+
+// Learned selection with the plain selection as fallback.
+// Workspace: [selector buffers | confidence plane | selection workspace | tile list].
+static size_t learned_parts(int w, int h, int pitch, int n_sigma, size_t *o_conf, size_t *o_sel, size_t *o_list)
+{
+    size_t o = align_up(fd4_selector_workspace_bytes(1, w, h, pitch), 256);
+    *o_conf = o;
+    o += align_up((size_t)h * pitch * sizeof(float), 256);
+    *o_sel = o;
+    o += ws_select_bytes(h, pitch, n_sigma);
+    *o_list = o;
+    const int tiles = ((w + 31) / 32) * ((h + 63) / 64);
+    o += align_up(sizeof(int) * ((size_t)tiles + 1), 256);
+    return o;
+}
+
+extern "C" size_t fd4_select_learned_workspace_bytes(int w, int h, int pitch, int n_sigma)
+{
+    if (w < 1 || h < 1 || pitch < w || n_sigma < 1) return 0;
+    size_t a, b, c;
+    return learned_parts(w, h, pitch, n_sigma, &a, &b, &c);
+}
+
+extern "C" int fd4_select_scales_learned(const void *d_params, const float *d_img, int w, int h, int pitch,
+                                         const float *h_sigmas, int n_sigma, const fd4_params *params,
+                                         float conf_threshold, uint8_t *d_sigma_idx, float *d_conf,
+                                         int *d_n_fallback, void *d_ws, size_t ws_bytes, fd4_stream_t stream)
+{
+    int rc;
+    fd4_params p;
+    resolve_params(params, &p);
+    if (!d_params || !d_sigma_idx) return FD4_ERR_BAD_ARG;
+    if ((rc = check_image(d_img, w, h, pitch)) != FD4_OK) return rc;
+    if ((rc = check_sigmas(h_sigmas, n_sigma)) != FD4_OK) return rc;
+    if (n_sigma != kBins) return FD4_ERR_BAD_ARG;  // the network predicts 8 scale bins
+    if (!(conf_threshold >= 0.0f && conf_threshold <= 1.0f)) return FD4_ERR_BAD_ARG;
+    size_t o_conf, o_sel, o_list;
+    const size_t need = learned_parts(w, h, pitch, n_sigma, &o_conf, &o_sel, &o_list);
+    if (!d_ws || ((uintptr_t)d_ws & 255u)) return FD4_ERR_BAD_ARG;
+    if (ws_bytes < need) return FD4_ERR_WS_TOO_SMALL;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)d_ws;
+    float *conf = (float *)(ws + o_conf);
+    char *sel = ws + o_sel;
+    int *list = (int *)(ws + o_list);
+    const int tiles = ((w + 31) / 32) * ((h + 63) / 64);
+    int *count = list + tiles;
+    if ((rc = fd4_selector_predict(d_params, d_img, w, h, pitch, d_sigma_idx, conf, d_ws, ws_bytes, stream)) !=
+        FD4_OK)
+        return rc;
+    if (cudaMemsetAsync(count, 0, sizeof(int), st) != cudaSuccess) return FD4_ERR_CUDA;
+    k_sel_fallback_tiles<<<tiles, 256, 0, st>>>(conf, w, h, pitch, conf_threshold, list, count);
+    // plain selection on the listed tiles, overwriting the prediction there
+    const size_t pb = plane_bytes(h, pitch, 4);
+    ImgDesc d{};
+    d.in = d_img;
+    d.vp = (float *)(sel + kHeaderBytes);
+    d.s2 = (float *)(sel + kHeaderBytes + (size_t)n_sigma * pb);
+    d.plane = pb / 4;
+    d.idx = d_sigma_idx;
+    d.max_s2 = &((WsHeader *)sel)->max_s2;
+    d.w = w;
+    d.h = h;
+    d.pitch = pitch;
+    if (launch_select_tiles(d, list, count, h_sigmas, n_sigma, p, st)) return FD4_ERR_CUDA;
+    if (d_conf && cudaMemcpyAsync(d_conf, conf, sizeof(float) * (size_t)h * pitch, cudaMemcpyDeviceToDevice, st) !=
+                      cudaSuccess)
+        return FD4_ERR_CUDA;
+    if (d_n_fallback &&
+        cudaMemcpyAsync(d_n_fallback, count, sizeof(int), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return FD4_ERR_CUDA;
+    return FD4_OK;
+}
+
+extern "C" int fd4_selftest_wait_timeout(void *d_ws, size_t ws_bytes, int *status, fd4_stream_t stream)
+{
+    const int w = 128, h = 4, pitch = 128;
+    if (!d_ws || !status || ((uintptr_t)d_ws & 255u)) return FD4_ERR_BAD_ARG;
+    if (ws_bytes < fd4_selector_workspace_bytes(1, w, h, pitch)) return FD4_ERR_WS_TOO_SMALL;
+    cudaStream_t st = (cudaStream_t)stream;
+    SelBufs B = sel_bufs((char *)d_ws, (long long)h * pitch);
+    if (cudaMemsetAsync(d_ws, 0, fd4_selector_workspace_bytes(1, w, h, pitch), st) != cudaSuccess)
+        return FD4_ERR_CUDA;
+    ConvArgs a{};
+    a.in = B.act[1];
+    a.out = B.act[2];
+    a.wts = (const uint4 *)B.act[3];  // zeros; never multiplied
+    a.n_img = 1;
+    a.w = w;
+    a.h = h;
+    a.pitch = pitch;
+    a.d = 1;
+    a.img_stride = (long long)h * pitch;
+    a.status = B.status;
+    a.withhold_commit = 1;
+    if (launch_conv<32, 32, CONV_RELU_BF16>(a, st)) return FD4_ERR_CUDA;
+    return fd4_selector_status(d_ws, status, stream);
 }

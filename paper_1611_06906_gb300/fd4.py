@@ -89,6 +89,10 @@ SELECTOR_SIGNATURES = {
     "fd4_selector_update": (_i, [_vp, ctypes.c_float, _i, _vp]),
     "fd4_selector_predict": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _vp, _sz, _vp]),
     "fd4_selector_status": (_i, [_vp, _ip, _vp]),
+    "fd4_select_learned_workspace_bytes": (_sz, [_i, _i, _i, _i]),
+    "fd4_selftest_wait_timeout": (_i, [_vp, _sz, _ip, _vp]),
+    "fd4_select_scales_learned": (_i, [_vp, _vp, _i, _i, _i, _fp, _i, _pp, ctypes.c_float, _vp, _vp, _vp, _vp,
+                                       _sz, _vp]),
 }
 SIGNATURES.update(SELECTOR_SIGNATURES)
 
@@ -424,8 +428,37 @@ class Selector:
                                           _ptr(ws), ws.numel(), _stream(stream)), "fd4_selector_predict")
         return idx, conf
 
+    def select_learned(self, img, w: int, sigmas, prm: Params | None = None, conf_threshold: float = 0.5,
+                       idx=None, ws=None, stream=None):
+        """fd4_select_scales_learned: (scale index, confidence, device count of fallback tiles)."""
+        torch = _torch()
+        h, pitch = img.shape
+        sg, K = _sigmas(sigmas)
+        if ws is None:
+            ws = torch.empty(int(lib().fd4_select_learned_workspace_bytes(int(w), h, pitch, K)), dtype=torch.uint8,
+                             device=img.device)
+        if idx is None:
+            idx = torch.zeros((h, pitch), dtype=torch.uint8, device=img.device)
+        conf = None
+        nfb = torch.zeros(1, dtype=torch.int32, device=img.device)
+        _check(lib().fd4_select_scales_learned(_ptr(self.params), _ptr(img), int(w), h, pitch, sg, K,
+                                               ctypes.byref(prm) if prm is not None else None,
+                                               float(conf_threshold), _ptr(idx), _ptr(conf), _ptr(nfb), _ptr(ws),
+                                               ws.numel(), _stream(stream)), "fd4_select_scales_learned")
+        return idx, conf, nfb
+
     @staticmethod
     def status(ws, stream=None) -> int:
         st = ctypes.c_int(0)
         _check(lib().fd4_selector_status(_ptr(ws), ctypes.byref(st), _stream(stream)), "fd4_selector_status")
         return st.value
+
+
+def selftest_wait_timeout(stream=None) -> int:
+    """Runs fd4_selftest_wait_timeout; returns the device status word it read."""
+    torch = _torch()
+    ws = torch.empty(int(lib().fd4_selector_workspace_bytes(1, 128, 4, 128)), dtype=torch.uint8, device="cuda")
+    st = ctypes.c_int(0)
+    _check(lib().fd4_selftest_wait_timeout(_ptr(ws), ws.numel(), ctypes.byref(st), _stream(stream)),
+           "fd4_selftest_wait_timeout")
+    return st.value

@@ -1,0 +1,113 @@
+"""Training and evaluation driver of the learned scale selector.
+
+Every arithmetic step runs in libfd4 (forward and backward passes on the
+tensor cores, Adam on the device); this module only generates the seeded
+inputs, moves them to the device and loops.
+
+Training set: 256 x 256 crops of seeded fundus-like images (the
+`batch64_fundus` generator at side 2048, 64 crops each), labelled with the
+scale index the plain vesselness selection picks on the whole source image
+(so the labels see the same image-wide Frangi c as inference on full images).
+"""
+from __future__ import annotations
+
+import multiprocessing as mp
+import os
+
+import numpy as np
+
+from . import fd4, synth
+
+CROP = 256
+SOURCE = 2048
+
+
+def _render(seed):
+    return synth.fundus_like(seed, SOURCE)
+
+
+def source_images(n_sources: int, seed0: int = 900000, procs: int = 16):
+    """Seeded source images (host float32), rendered in a spawn pool (so the
+    calling script must guard its entry point with if __name__ == "__main__")."""
+    seeds = [seed0 + i for i in range(n_sources)]
+    with mp.get_context("spawn").Pool(max(1, min(procs, os.cpu_count() or 1))) as pool:
+        return pool.map(_render, seeds)
+
+
+def make_training_set(n_crops: int, sigmas, mode: int, seed0: int = 900000, device="cuda"):
+    """(crops (n, 256, 256) float32, labels (n, 256, 256) uint8) on the device."""
+    import torch
+    per = (SOURCE // CROP) ** 2
+    n_src = -(-n_crops // per)
+    srcs = source_images(n_src, seed0)
+    crops = torch.empty((n_crops, CROP, CROP), dtype=torch.float32, device=device)
+    labels = torch.empty((n_crops, CROP, CROP), dtype=torch.uint8, device=device)
+    prm = fd4.params(mode=mode)
+    ws = fd4.workspace(fd4.OP_SELECT_SCALES, SOURCE, SOURCE, len(sigmas), device)
+    k = 0
+    for img in srcs:
+        u = fd4.to_device(img, device)
+        idx, _ = fd4.select_scales(u, SOURCE, sigmas, prm, ws=ws)
+        for cy in range(0, SOURCE, CROP):
+            for cx in range(0, SOURCE, CROP):
+                if k == n_crops:
+                    break
+                crops[k] = u[cy:cy + CROP, cx:cx + CROP]
+                labels[k] = idx[cy:cy + CROP, cx:cx + CROP]
+                k += 1
+    return crops, labels
+
+
+def train(sel: "fd4.Selector", crops, labels, epochs: int = 1, batch: int = 32, lr: float = 2e-3,
+          seed: int = 1, log_every: int = 0):
+    """Adam over shuffled mini-batches.  Returns the per-step mean losses."""
+    import torch
+    n = crops.shape[0]
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    ws = fd4.Selector.workspace(batch, CROP, CROP, CROP, crops.device)
+    loss = torch.zeros(1, dtype=torch.float32, device=crops.device)
+    losses = []
+    step = 0
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=g)
+        for b0 in range(0, n - batch + 1, batch):
+            sel_idx = perm[b0:b0 + batch].to(crops.device)
+            xb = crops.index_select(0, sel_idx).contiguous()
+            yb = labels.index_select(0, sel_idx).contiguous()
+            loss.zero_()
+            sel.grad(xb, yb, CROP, loss, ws=ws)
+            step += 1
+            # cosine decay of the step size over the run
+            frac = step / max(1, epochs * (n // batch))
+            sel.update(lr * (0.1 + 0.9 * 0.5 * (1 + np.cos(np.pi * frac))), step)
+            losses.append(loss)
+            loss = torch.zeros(1, dtype=torch.float32, device=crops.device)
+            if log_every and step % log_every == 0:
+                print("step %d loss %.4f" % (step, float(losses[-1].item())), flush=True)
+    return [float(x.item()) for x in losses]
+
+
+def evaluate(sel: "fd4.Selector", images, widths, sigmas, mode: int, thresholds=(0.0, 0.5, 0.9)):
+    """Agreement of the learned selection with the plain selection per threshold.
+
+    images: list of device (h, pitch) tensors.  Returns a dict per threshold with
+    the pixel agreement and the fraction of 32 x 64 tiles that fell back."""
+    import torch
+    prm = fd4.params(mode=mode)
+    out = {}
+    plain = []
+    for u, w in zip(images, widths):
+        idx, _ = fd4.select_scales(u, w, sigmas, prm)
+        plain.append(idx)
+    for thr in thresholds:
+        agree = tot = fb = tiles = 0
+        for u, w, ref in zip(images, widths, plain):
+            h = u.shape[0]
+            idx, conf, nfb = sel.select_learned(u, w, sigmas, prm, conf_threshold=thr)
+            agree += int((idx[:, :w] == ref[:, :w]).sum().item())
+            tot += h * w
+            fb += int(nfb.item())
+            tiles += ((w + 31) // 32) * ((h + 63) // 64)
+        out[thr] = {"agreement": agree / tot, "fallback_tiles": fb / tiles}
+    return out

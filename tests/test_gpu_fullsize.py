@@ -1,0 +1,75 @@
+"""Full-size parity in the launch configuration bench.py times: the 64-image
+fundus batch (123 Mpixel) through the batched CUDA-graph path, checked against
+the FP64 oracle on sampled whole images (the oracle cannot run the whole
+batch in a test), plus properties that hold on every image; and the 1024^2
+vessel-tree configuration end to end."""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+from paper_1611_06906_gb300 import fd4, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_U = 1e-4
+
+
+def _gen(args):
+    seed, side = args
+    return synth.fundus_like(seed, side)
+
+
+@pytest.fixture(scope="module")
+def batch64():
+    sides = synth.batch_sides(3000)
+    with mp.get_context("spawn").Pool(8) as pool:
+        return pool.map(_gen, [(3000 + i, s) for i, s in enumerate(sides)])
+
+
+def test_batch64_graph_matches_oracle_on_samples(oracle, batch64):
+    import torch
+    wl = synth.WORKLOADS["batch64_fundus"]
+    sig, M, n, T = wl["sigmas"], wl["M"], wl["n"], wl["T"]
+    ins = [fd4.to_device(im) for im in batch64]
+    outs = [torch.zeros_like(u) for u in ins]
+    idx = [torch.zeros(u.shape, dtype=torch.uint8, device="cuda") for u in ins]
+    lst = fd4.image_list(ins, [im.shape[1] for im in batch64], outs, idx)
+    ws = fd4.batch_workspace(lst, len(sig))
+    best, _ = fd4.autotune_batched(lst, sig, T, M, n, fd4.params(mode=fd4.VALLEY), ws=ws)
+    g = fd4.Graph(lst, sig, T, M, n, fd4.params(mode=fd4.VALLEY, fed_steps_per_launch=best), ws=ws)
+    g.launch()
+    torch.cuda.synchronize()
+    # properties on every image: finite, mean preserved (natural boundary)
+    for im, o in zip(batch64, outs):
+        w = im.shape[1]
+        got = o[:, :w].double()
+        assert bool(torch.isfinite(got).all())
+        assert abs(float(got.mean()) - float(im.astype(np.float64).mean())) < 5e-6
+    # the oracle on whole images: the two smallest and one mid-size image
+    tau, _, _ = oracle.fed_taus(T, M, 0.05, n=n)
+    order = sorted(range(len(batch64)), key=lambda i: batch64[i].size)
+    for k in (order[0], order[1], order[len(order) // 2]):
+        ref, ridx = oracle.filter_image(batch64[k], sig, tau, M, mode=oracle.VALLEY)
+        w = batch64[k].shape[1]
+        agree = float((idx[k][:, :w].cpu().numpy() == ridx).mean())
+        assert agree >= 0.99
+        if agree == 1.0:
+            assert np.abs(outs[k][:, :w].cpu().numpy() - ref).max() <= TOL_U
+    g.close()
+
+
+def test_tree_1024_end_to_end(oracle):
+    wl = synth.WORKLOADS["tree_1024"]
+    sig, M, n, T = wl["sigmas"], wl["M"], wl["n"], wl["T"]
+    img = synth.vessel_tree(2000, 1024, 1024)
+    tau, _, _ = oracle.fed_taus(T, M, 0.05, n=n)
+    ref, ridx = oracle.filter_image(img, sig, tau, M, mode=oracle.VALLEY)
+    u = fd4.to_device(img)
+    out, idx = fd4.filter_image(u, 1024, sig, T, M, n, fd4.params(mode=fd4.VALLEY))
+    agree = float((idx[:, :1024].cpu().numpy() == ridx).mean())
+    assert agree >= 0.99
+    import torch
+    idx_o = torch.from_numpy(ridx).cuda()
+    out2, _ = fd4.filter_image(u, 1024, sig, T, M, n, fd4.params(mode=fd4.VALLEY), sigma_idx=idx_o)
+    assert np.abs(out2[:, :1024].cpu().numpy() - ref).max() <= TOL_U

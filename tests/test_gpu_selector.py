@@ -137,3 +137,42 @@ def test_training_reduces_the_loss():
         losses.append(float(loss.item()))
     assert fd4.Selector.status(ws) == 0
     assert np.mean(losses[-5:]) < 0.8 * losses[0]
+
+
+def test_learned_selection_fallback_extremes():
+    """Threshold 1: every tile falls back, so the result is the plain selection
+    exactly.  Threshold 0: nothing falls back, so it is the network's argmax."""
+    import torch
+    h, w = 130, 203
+    img = synth.vessel_tree(7400, w, h, depth=4, r0=4.0)
+    sig = list(synth.log_sigmas(1.0, 8.0, 8))
+    prm = fd4.params(mode=fd4.VALLEY)
+    u = fd4.to_device(img)
+    plain, _ = fd4.select_scales(u, w, sig, prm)
+    sel = fd4.Selector()
+    sel.init(21)
+    idx1, conf1, n1 = sel.select_learned(u, w, sig, prm, conf_threshold=1.0)
+    tiles = ((w + 31) // 32) * ((h + 63) // 64)
+    assert int(n1.item()) == tiles
+    assert torch.equal(idx1[:, :w], plain[:, :w])
+    idx0, conf0, n0 = sel.select_learned(u, w, sig, prm, conf_threshold=0.0)
+    pred, _ = sel.predict(u, w)
+    assert int(n0.item()) == 0
+    assert torch.equal(idx0[:, :w], pred[:, :w])
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A wait made to run out (its MMA commit withheld) ends with FD4_ERR_TIMEOUT
+    read on the host; the context keeps working afterwards."""
+    import torch
+    assert fd4.selftest_wait_timeout() == -6
+    # the device still computes correctly after the timed-out kernel
+    sel = fd4.Selector()
+    sel.init(3)
+    img = synth.vessel_tree(7500, 140, 20, depth=3, r0=3.0)
+    u = fd4.to_device(img)
+    ws = fd4.Selector.workspace(1, 140, 20, u.shape[1])
+    idx, conf = sel.predict(u, 140, ws=ws)
+    torch.cuda.synchronize()
+    assert fd4.Selector.status(ws) == 0
+    assert float(conf[:, :140].min()) > 0.0
