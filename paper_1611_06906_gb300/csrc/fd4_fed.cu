@@ -263,7 +263,10 @@ __global__ void __launch_bounds__(FNT, 2) k_fed_fused(Imgs I, StepTaus taus, int
     __shared__ ImgDesc sd;
     __shared__ int s_local;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < 8) stau[tid] = taus.t[tid];
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) stau[i] = taus.t[i];
+    }
     // this thread's column segment of the staged region
     const int rx = (warp % (FRX / 32)) * 32 + lane, ry0 = (warp / (FRX / 32)) * FV;
 
@@ -327,6 +330,116 @@ __global__ void __launch_bounds__(FNT, 2) k_fed_fused(Imgs I, StepTaus taus, int
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Pipelined fused variant (natural boundary, S = 2 or 4): while a block
+// advances one tile, cp.async copies bring the next tile's u region and tensor
+// values into a second shared buffer (16-byte copies, zero-filled outside the
+// image), so the staging latency overlaps the computation.
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+constexpr size_t kPipeSmem = sizeof(float) * FRX * FRY * (2 + 3 + 4);  // 2 u buffers, T, tensor: 72 KB
+
+template <int S>
+__device__ __forceinline__ void prefetch_tile(const ImgDesc &d, int local, float *u_dst, float4 *t_dst, int parity)
+{
+    constexpr int H = 2 * S, TXo = FRX - 2 * H, TYo = FRY - 2 * H;
+    const int tid = threadIdx.x;
+    const int w = d.w, h = d.h, pitch = d.pitch;
+    const int tiles_x = (w + TXo - 1) / TXo;
+    const int gx0 = (local % tiles_x) * TXo - H, gy0 = (local / tiles_x) * TYo - H;
+    const float *uin = parity ? d.tmp : d.u;
+    for (int c = tid; c < FRY * FRX / 4; c += FNT) {
+        const int ry = c / (FRX / 4), cx = (c % (FRX / 4)) * 4;
+        const int gy = gy0 + ry, gx = gx0 + cx;
+        // a chunk of 4 columns starting inside the image stays inside the row pitch
+        const bool valid = gy >= 0 && gy < h && gx >= 0 && gx < w;
+        cp_async16(u_dst + ry * FRX + cx, valid ? uin + (size_t)gy * pitch + gx : uin, valid);
+    }
+    for (int i = tid; i < FRY * FRX; i += FNT) {
+        const int ry = i / FRX, rx = i % FRX;
+        const int gy = gy0 + ry, gx = gx0 + rx;
+        const bool valid = gy >= 0 && gy < h && gx >= 0 && gx < w;
+        cp_async16(t_dst + i, valid ? d.tensor + (size_t)gy * pitch + gx : d.tensor, valid);
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(FNT, 2) k_fed_fused_pipe(Imgs I, StepTaus taus, int parity)
+{
+    constexpr int H = 2 * S, TXo = FRX - 2 * H, TYo = FRY - 2 * H;
+    static_assert(TXo % 4 == 0 && H % 4 == 0, "16-byte aligned region columns");
+    extern __shared__ __align__(16) float psm[];
+    // u buffers: psm + b * FRX * FRY for b = 0, 1
+    float (*sxx)[FRX] = reinterpret_cast<float (*)[FRX]>(psm + 2 * FRX * FRY);
+    float (*sxy)[FRX] = reinterpret_cast<float (*)[FRX]>(psm + 3 * FRX * FRY);
+    float (*syy)[FRX] = reinterpret_cast<float (*)[FRX]>(psm + 4 * FRX * FRY);
+    float4 *tbuf = reinterpret_cast<float4 *>(psm + 5 * FRX * FRY);
+    __shared__ float stau[8];
+    __shared__ ImgDesc sd[2];
+    __shared__ int s_local[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) stau[i] = taus.t[i];
+    }
+    const int rx = (warp % (FRX / 32)) * 32 + lane, ry0 = (warp / (FRX / 32)) * FV;
+    const int ntiles = I.tiles;
+    int cur = 0;
+    int t = blockIdx.x;
+    if (t < ntiles) {
+        if (tid == 0) find_tile(I, S, t, sd[0], s_local[0]);
+        __syncthreads();
+        prefetch_tile<S>(sd[0], s_local[0], psm, tbuf, parity);
+    }
+    cp_async_commit();
+    for (; t < ntiles; t += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();  // this tile's u region and tensor values have landed
+        const int w = sd[cur].w, h = sd[cur].h, pitch = sd[cur].pitch;
+        float *uout = parity ? sd[cur].u : sd[cur].tmp;
+        const int tiles_x = (w + TXo - 1) / TXo;
+        const int gx0 = (s_local[cur] % tiles_x) * TXo - H, gy0 = (s_local[cur] / tiles_x) * TYo - H;
+        const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + FRX <= w && gy0 + FRY <= h;
+        const int gx = gx0 + rx;
+        const bool in_x = gx >= 0 && gx < w;
+        const bool vx = gx >= 1 && gx <= w - 2;
+        unsigned rowbits = 0u;
+        float4 tv[FV];
+#pragma unroll
+        for (int j = 0; j < FV; ++j) {
+            const int gy = gy0 + ry0 + j;
+            rowbits |= (gy >= 0 && gy < h ? 1u : 0u) << j;
+            rowbits |= (gy >= 1 && gy <= h - 2 ? 1u : 0u) << (8 + j);
+            tv[j] = tbuf[(ry0 + j) * FRX + rx];
+        }
+        const int tn = t + gridDim.x;
+        if (tid == 0 && tn < ntiles) find_tile(I, S, tn, sd[cur ^ 1], s_local[cur ^ 1]);
+        __syncthreads();  // the tensor buffer is read; the next descriptor is ready
+        if (tn < ntiles) prefetch_tile<S>(sd[cur ^ 1], s_local[cur ^ 1], psm + (cur ^ 1) * FRX * FRY, tbuf, parity);
+        cp_async_commit();
+
+        float (*su)[FRX] = reinterpret_cast<float (*)[FRX]>(psm + cur * FRX * FRY);
+        if (interior) fused_steps<true>(su, sxx, sxy, syy, stau, taus.n, rx, ry0, tv, in_x, vx, rowbits);
+        else fused_steps<false>(su, sxx, sxy, syy, stau, taus.n, rx, ry0, tv, in_x, vx, rowbits);
+
+        for (int i = tid; i < TXo * TYo; i += FNT) {
+            const int ty = i / TXo, tx = i - ty * TXo;
+            const int ox = gx0 + H + tx, oy = gy0 + H + ty;
+            if (ox < w && oy < h) uout[(size_t)oy * pitch + ox] = su[H + ty][H + tx];
+        }
+        cur ^= 1;
+    }
+    cp_async_wait_all();
+}
+
 template <int S>
 static int set_fused_smem()
 {
@@ -342,7 +455,38 @@ static int set_fused_smem()
     return 0;
 }
 
-int prepare_fed_kernels() { return set_fused_smem<2>() || set_fused_smem<3>() || set_fused_smem<4>(); }
+template <int S>
+static int set_pipe_smem()
+{
+    static int attr_dev = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (attr_dev != dev) {
+        if (cudaFuncSetAttribute(k_fed_fused_pipe<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPipeSmem) !=
+            cudaSuccess)
+            return 1;
+        attr_dev = dev;
+    }
+    return 0;
+}
+
+int prepare_fed_kernels()
+{
+    return set_fused_smem<2>() || set_fused_smem<3>() || set_fused_smem<4>() || set_pipe_smem<2>() ||
+           set_pipe_smem<4>();
+}
+
+template <int S>
+static int launch_pipe(Imgs I, const double *tau, int n, int parity, cudaStream_t st)
+{
+    if (set_pipe_smem<S>()) return 1;
+    StepTaus t{};
+    t.n = n;
+    for (int i = 0; i < n; ++i) t.t[i] = (float)tau[i];
+    const int grid = persistent_grid((const void *)k_fed_fused_pipe<S>, FNT, kPipeSmem, I.tiles);
+    k_fed_fused_pipe<S><<<grid, FNT, kPipeSmem, st>>>(I, t, parity);
+    return 0;
+}
 
 template <int S>
 static int launch_fused(Imgs I, const double *tau, int n, int parity, int periodic, cudaStream_t st)
@@ -354,6 +498,14 @@ static int launch_fused(Imgs I, const double *tau, int n, int parity, int period
     const int grid = persistent_grid((const void *)k_fed_fused<S>, FNT, kFusedSmem, I.tiles);
     k_fed_fused<S><<<grid, FNT, kFusedSmem, st>>>(I, t, parity, periodic);
     return 0;
+}
+
+// The cp.async-pipelined kernel is used for S = 2 and 4 under the natural
+// boundary unless FD4_FED_PIPELINE=0 (the plain fused kernel then runs).
+static bool pipeline_enabled()
+{
+    const char *e = getenv("FD4_FED_PIPELINE");
+    return !(e && e[0] == '0');
 }
 
 int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundary, int steps_per_launch,
@@ -376,9 +528,12 @@ int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundar
         I.tiles = B.tiles[S];
         for (int i = 0; i < n; i += S) {
             const int k = n - i < S ? n - i : S;
-            const int rc = S == 2 ? launch_fused<2>(I, h_tau + i, k, parity, periodic, st)
-                         : S == 3 ? launch_fused<3>(I, h_tau + i, k, parity, periodic, st)
-                                  : launch_fused<4>(I, h_tau + i, k, parity, periodic, st);
+            int rc;
+            if (!periodic && S == 2 && pipeline_enabled()) rc = launch_pipe<2>(I, h_tau + i, k, parity, st);
+            else if (!periodic && S == 4 && pipeline_enabled()) rc = launch_pipe<4>(I, h_tau + i, k, parity, st);
+            else rc = S == 2 ? launch_fused<2>(I, h_tau + i, k, parity, periodic, st)
+                    : S == 3 ? launch_fused<3>(I, h_tau + i, k, parity, periodic, st)
+                             : launch_fused<4>(I, h_tau + i, k, parity, periodic, st);
             if (rc) return 1;
             parity ^= 1;
         }

@@ -66,6 +66,7 @@ __host__ __device__ inline size_t sweep_smem_bytes(int Rmax, int wfloats)
 
 __device__ __forceinline__ int mirror(int i, int n)
 {
+    if ((unsigned)i < (unsigned)n) return i;  // the common case: no reflection
     const int p = 2 * n;
     int m = i % p;
     if (m < 0) m += p;
