@@ -96,15 +96,17 @@ __global__ void __launch_bounds__(CT) k_conv_tc(ConvArgs a)
         const int x0 = tx * TM;
         const __nv_bfloat16 *in = a.in + (size_t)img * (size_t)a.img_stride * CI;
         // A: rows y - d, y, y + d; pixels x0 - d .. x0 + TM - 1 + d; zero outside the image
-        for (int i = tid; i < 3 * P * CJ; i += CT) {
-            const int j = i % CJ;
-            const int p = (i / CJ) % P;
-            const int ky = i / (CJ * P);
-            const int gy = y + (ky - 1) * a.d, gx = x0 - a.d + p;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (gy >= 0 && gy < a.h && gx >= 0 && gx < a.w)
-                v = *reinterpret_cast<const uint4 *>(in + ((size_t)gy * a.pitch + gx) * CI + 8 * j);
-            As[(ky * CJ + j) * P + p] = v;
+        for (int ky = 0; ky < 3; ++ky) {
+            const int gy = y + (ky - 1) * a.d;
+            const bool row_in = gy >= 0 && gy < a.h;
+            const __nv_bfloat16 *src = in + (size_t)(row_in ? gy : 0) * a.pitch * CI;
+            for (int e = tid; e < P * CJ; e += CT) {
+                const int j = e % CJ, p = e / CJ;  // CJ is a compile-time power of two
+                const int gx = x0 - a.d + p;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (row_in && gx >= 0 && gx < a.w) v = *reinterpret_cast<const uint4 *>(src + (size_t)gx * CI + 8 * j);
+                As[(ky * CJ + j) * P + p] = v;
+            }
         }
         tc::fence_proxy_async();
         __syncthreads();
@@ -285,15 +287,17 @@ __global__ void k_sel_cast(CastArgs a)
 __global__ void k_sel_prep(const float *img, __nv_bfloat16 *act, int n_img, int w, int h, int pitch,
                            long long img_stride)
 {
-    const long long total = (long long)n_img * img_stride;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % img_stride % pitch);
-        const float v = x < w ? img[i] : 0.0f;
-        uint4 *o = reinterpret_cast<uint4 *>(act + i * 16);
-        __nv_bfloat162 b = __floats2bfloat162_rn(v, 0.0f);
-        o[0] = make_uint4(*reinterpret_cast<uint32_t *>(&b), 0u, 0u, 0u);
-        o[1] = make_uint4(0u, 0u, 0u, 0u);
+    // one block-stride loop over the rows of the stack, threads over columns
+    for (int row = blockIdx.x; row < n_img * h; row += gridDim.x) {
+        const size_t base = (size_t)(row / h) * (size_t)img_stride + (size_t)(row % h) * pitch;
+        for (int x = threadIdx.x; x < pitch; x += blockDim.x) {
+            const size_t i = base + x;
+            const float v = x < w ? img[i] : 0.0f;
+            uint4 *o = reinterpret_cast<uint4 *>(act + i * 16);
+            __nv_bfloat162 b = __floats2bfloat162_rn(v, 0.0f);
+            o[0] = make_uint4(*reinterpret_cast<uint32_t *>(&b), 0u, 0u, 0u);
+            o[1] = make_uint4(0u, 0u, 0u, 0u);
+        }
     }
 }
 
@@ -305,10 +309,9 @@ __global__ void __launch_bounds__(256) k_sel_softmax_ce(const float *logits, con
 {
     __shared__ float red[8];
     float lsum = 0.0f;
-    const long long total = (long long)n_img * img_stride;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % img_stride % pitch);
+    for (int row = blockIdx.x; row < n_img * h; row += gridDim.x)
+    for (int x = threadIdx.x; x < pitch; x += blockDim.x) {
+        const size_t i = (size_t)(row / h) * (size_t)img_stride + (size_t)(row % h) * pitch + x;
         float g[kBins];
         if (x < w) {
             const float *z = logits + i * kBins;
@@ -375,12 +378,16 @@ __global__ void __launch_bounds__(CT) k_sel_wgrad(const __nv_bfloat16 *X, const 
         const int x0 = tx * TM;
         const size_t base = (size_t)img * (size_t)img_stride;
         __syncthreads();
-        for (int i = tid; i < 3 * P * CIP; i += CT) {
-            const int c = i % CIP, p = (i / CIP) % P, ky = i / (CIP * P);
-            const int gy = y + (ky - 1) * d, gx = x0 - d + p;
-            __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
-            if (gy >= 0 && gy < h && gx >= 0 && gx < w) v = X[(base + (size_t)gy * pitch + gx) * CIP + c];
-            xs[ky][p][c] = v;
+        for (int ky = 0; ky < 3; ++ky) {
+            const int gy = y + (ky - 1) * d;
+            const bool row_in = gy >= 0 && gy < h;
+            for (int e = tid; e < P * CIP; e += CT) {
+                const int c = e % CIP, p = e / CIP;  // CIP is a compile-time power of two
+                const int gx = x0 - d + p;
+                __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
+                if (row_in && gx >= 0 && gx < w) v = X[(base + (size_t)gy * pitch + gx) * CIP + c];
+                xs[ky][p][c] = v;
+            }
         }
         for (int i = tid; i < TM * COP; i += CT) {
             const int c = i % COP, p = i / COP;
@@ -430,10 +437,9 @@ __global__ void k_sel_adam(float *w, float *m, float *v, float *g, size_t n, flo
 // bin), confidence = its softmax probability.
 __global__ void k_sel_predict(const float *logits, int w, int h, int pitch, uint8_t *idx, float *conf)
 {
-    const long long total = (long long)h * pitch;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        if ((int)(i % pitch) >= w) continue;
+    for (int y = blockIdx.x; y < h; y += gridDim.x)
+    for (int x = threadIdx.x; x < w; x += blockDim.x) {
+        const size_t i = (size_t)y * pitch + x;
         const float *z = logits + i * kBins;
         int arg = 0;
         float m = z[0];
@@ -585,8 +591,7 @@ int sel_forward(const SelPtrs &P, const float *imgs, int n_img, int w, int h, in
                 cudaStream_t st)
 {
     const long long stride = (long long)h * pitch;
-    const long long npx = stride * n_img;
-    const int g = (int)((npx + 255) / 256 < 4096 ? (npx + 255) / 256 : 4096);
+    const int g = n_img * h < 8192 ? n_img * h : 8192;  // blocks stride over image rows
     k_sel_prep<<<g, 256, 0, st>>>(imgs, B.act[0], n_img, w, h, pitch, stride);
     ConvArgs a{};
     a.n_img = n_img;
@@ -727,7 +732,7 @@ extern "C" int fd4_selector_grad(void *d_params, const float *d_imgs, const uint
     const long long stride = (long long)h * pitch;
     if (cudaMemsetAsync(B.status, 0, sizeof(int), st) != cudaSuccess) return FD4_ERR_CUDA;
     if (sel_forward(P, d_imgs, n_img, w, h, pitch, B, st)) return FD4_ERR_CUDA;
-    const int g = (int)((npx + 255) / 256 < 4096 ? (npx + 255) / 256 : 4096);
+    const int g = n_img * h < 8192 ? n_img * h : 8192;
     k_sel_softmax_ce<<<g, 256, 0, st>>>(B.logits, d_labels, B.dz16, n_img, w, h, pitch, stride,
                                         1.0f / (float)((long long)n_img * w * h), d_loss);
     ConvArgs a{};
@@ -785,8 +790,7 @@ extern "C" int fd4_selector_predict(const void *d_params, const float *d_img, in
     SelBufs B = sel_bufs((char *)d_ws, (long long)h * pitch);
     if (cudaMemsetAsync(B.status, 0, sizeof(int), st) != cudaSuccess) return FD4_ERR_CUDA;
     if (sel_forward(sel_ptrs((void *)d_params), d_img, 1, w, h, pitch, B, st)) return FD4_ERR_CUDA;
-    const long long npx = (long long)h * pitch;
-    const int g = (int)((npx + 255) / 256 < 4096 ? (npx + 255) / 256 : 4096);
+    const int g = h < 8192 ? h : 8192;
     k_sel_predict<<<g, 256, 0, st>>>(B.logits, w, h, pitch, d_idx, d_conf);
     return cudaGetLastError() == cudaSuccess ? FD4_OK : FD4_ERR_CUDA;
 }
