@@ -212,16 +212,19 @@ def run_fd4(args, rank, world, local_rank):
         torch.cuda.synchronize()
         g.close()
         return
-    g_all = fd4.Graph(lst, sig, T, M, n, prm, ws=ws)
+    g_one = fd4.Graph(lst, sig, T, M, n, prm, ws=ws)
+    g_all = fd4.Graph(lst, sig, T, M, n, prm, ws=ws, stages=fd4.STAGES_ALL | fd4.GRAPH_TWO_STREAMS) \
+        if (args.two_streams and len(ims) > 1) else g_one
     g_sel = fd4.Graph(lst, sig, T, M, n, prm, ws=ws, stages=fd4.STAGE_SELECT)
     g_ten = fd4.Graph(lst, sig, T, M, n, prm, ws=ws, stages=fd4.STAGE_TENSOR)
     g_fed = fd4.Graph(lst, sig, T, M, n, prm, ws=ws, stages=fd4.STAGE_FED)
     L = -(-n // best) if best > 1 else n          # FED launches per cycle
     fed_launches = M * L
     sweeps = -(-K // 16)                          # sweep launches per stage (16 scales each)
+    groups = 2 if (args.two_streams and len(ims) > 1) else 1  # each stage runs once per image group
     launches_per_step = (-(-len(ims) // 128)      # descriptor upload
-                         + sweeps + 1 + 1         # selection sweep, argmax, input copy
-                         + M * (sweeps + 1 + L + (L % 2)))  # tensor sweep, finish, FED (+ copy-back)
+                         + groups * (sweeps + 1 + 1  # selection sweep, argmax, input copy
+                                     + M * (sweeps + 1 + L + (L % 2))))  # tensor sweep, finish, FED (+ copy-back)
 
     for _ in range(args.warmup):
         g_all.launch()
@@ -231,6 +234,7 @@ def run_fd4(args, rank, world, local_rank):
         barrier()
     ms = max_over_ranks(ms)
     value = world * px_steps * args.steps / (ms * 1e-3) / 1e6
+    one_stream_ms = _timed(g_one.launch, args.steps, stream, torch) / args.steps
     # stage split and the FED kernel alone (each graph replays one stage of the same schedule)
     sel_ms = _timed(g_sel.launch, args.steps, stream, torch) / args.steps
     ten_ms = _timed(g_ten.launch, args.steps, stream, torch) / args.steps
@@ -291,7 +295,9 @@ def run_fd4(args, rank, world, local_rank):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": args.workload, "images": len(ims), "mpixel": round(npx / 1e6, 3),
                       "sigmas": K, "mode": wl["mode"], "M": M, "n": n, "T": T,
-                      "path": "batched (one persistent launch per stage) + CUDA graph",
+                      "path": "batched (one persistent launch per stage) + CUDA graph" + (
+                          ", two image groups on two streams" if g_all is not g_one else ""),
+                      "one_stream_graph_ms_per_step": one_stream_ms,
                       "fed_steps_per_launch": best, "autotune_ms": tune_ms,
                       "l2": "inputs larger than L2 (images %.2f GB, tensor field %.2f GB per pass)" % (
                           npx * 4e-9, npx * 16e-9)},
@@ -322,7 +328,7 @@ def run_fd4(args, rank, world, local_rank):
         out["parity"] = {"vs": "FP64 oracle", "images": sample, "max_abs": max(errs),
                          "max_abs_oracle_sigma": max(errs_inj), "sigma_agreement": min(agree),
                          "tolerance": 1e-4}
-    for g in (g_all, g_sel, g_ten, g_fed):
+    for g in {id(x): x for x in (g_all, g_one, g_sel, g_ten, g_fed)}.values():
         g.close()
     print(json.dumps(out), flush=True)
 
@@ -439,6 +445,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fed-steps", type=int, default=0, help="FED steps per launch (0: autotune)")
     ap.add_argument("--no-learned", action="store_true", help="skip the batched+learned variant")
+    ap.add_argument("--two-streams", type=int, default=0, help="headline graph on two streams (1) or one (0)")
     ap.add_argument("--sel-crops", type=int, default=4096, help="training crops of the learned selector")
     ap.add_argument("--sel-threshold", type=float, default=0.5, help="fallback confidence threshold")
     ap.add_argument("--only-graph", action="store_true", help="replay the full graph only (profiling)")

@@ -216,6 +216,12 @@ int fd4_filter_batched(const fd4_image *h_imgs, int n_images, const float *h_sig
 #define FD4_STAGE_TENSOR 4
 #define FD4_STAGE_FED 8
 #define FD4_STAGES_ALL 15
+/* Option bit for fd4_graph_create with FD4_STAGES_ALL: capture the batch as two
+ * image groups on two streams (balanced pixel counts), the second starting
+ * after the first group's first tensor build, so the FMA-bound tensor builds
+ * of one group overlap the latency-bound FED steps of the other.  Results are
+ * identical to the one-stream graph.                                        */
+#define FD4_GRAPH_TWO_STREAMS 16
 typedef struct fd4_graph_st *fd4_graph;
 int fd4_graph_create(const fd4_image *h_imgs, int n_images, const float *h_sigmas, int n_sigma,
                      const fd4_params *params, double T, int M, int n_in, int sigma_given, int stages,

@@ -408,15 +408,23 @@ static size_t scratch_bytes(int h, int pitch, int n_sigma)
     return sc;
 }
 
+// split (0 < split < n): images [split, n) form a second group whose tile
+// numbering restarts at 0 and which B1 describes (B covers [0, split)).
 static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vector<ImgDesc> *descs, char *ws,
-                           HostBatch *B)
+                           HostBatch *B, int split = 0, HostBatch *B1 = nullptr)
 {
     size_t off = align_up(sizeof(ImgDesc) * (size_t)n, 256);
     const size_t ms_off = off;
     off += align_up(sizeof(unsigned) * (size_t)n, 256);
     int t0[kShapes] = {0, 0, 0, 0, 0};
     if (descs) descs->resize(n);
+    int t_split[kShapes] = {0, 0, 0, 0, 0};
     for (int i = 0; i < n; ++i) {
+        if (i == split && split > 0)
+            for (int s = 0; s < kShapes; ++s) {
+                t_split[s] = t0[s];
+                t0[s] = 0;
+            }
         const fd4_image &im = imgs[i];
         const size_t pb = plane_bytes(im.h, im.pitch, 4);
         const size_t o_idx = off, o_ten = o_idx + plane_bytes(im.h, im.pitch, 1);
@@ -444,18 +452,46 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
             t0[s] += tiles_of(im.w, im.h, s);
         }
     }
+    const bool two = split > 0 && split < n;
     if (B) {
         B->I.table = (const ImgDesc *)ws;
-        B->I.n = n;
+        B->I.n = two ? split : n;
         B->I.tiles = 0;
         B->I.one = ImgDesc{};
         B->I.list = nullptr;
         B->I.count = nullptr;
-        for (int s = 0; s < kShapes; ++s) B->tiles[s] = t0[s];
+        for (int s = 0; s < kShapes; ++s) B->tiles[s] = two ? t_split[s] : t0[s];
         B->max_s2 = (unsigned *)(ws + ms_off);
-        B->n_max_s2 = n;
+        B->n_max_s2 = two ? split : n;
+    }
+    if (B1 && two) {
+        *B1 = *B;
+        B1->I.table = (const ImgDesc *)ws + split;
+        B1->I.n = n - split;
+        for (int s = 0; s < kShapes; ++s) B1->tiles[s] = t0[s];
+        B1->max_s2 = (unsigned *)(ws + ms_off) + split;
+        B1->n_max_s2 = n - split;
     }
     return off;
+}
+
+// Split point that balances the pixel counts of the two groups.
+static int balanced_split(const fd4_image *imgs, int n)
+{
+    double tot = 0.0;
+    for (int i = 0; i < n; ++i) tot += (double)imgs[i].w * imgs[i].h;
+    double acc = 0.0;
+    int best = 1;
+    double err = 1e300;
+    for (int k = 1; k < n; ++k) {
+        acc += (double)imgs[k - 1].w * imgs[k - 1].h;
+        const double e = fabs(2.0 * acc - tot);
+        if (e < err) {
+            err = e;
+            best = k;
+        }
+    }
+    return best;
 }
 
 extern "C" size_t fd4_batch_workspace_bytes(const fd4_image *h_imgs, int n_images, int n_sigma)
@@ -485,6 +521,47 @@ static int batch_prepare(const fd4_image *imgs, int n_images, const float *h_sig
     if ((rc = ws_ok(d_ws, ws_bytes, fd4_batch_workspace_bytes(imgs, n_images, n_sigma))) != FD4_OK) return rc;
     tau.assign(FD4_MAX_FED_STEPS, 0.0);
     return fd4_fed_taus(T, M, p.tau_max, n_in, p.kappa, tau.data(), FD4_MAX_FED_STEPS, &n, nullptr);
+}
+
+// Two image groups on two streams: group 1 starts once group 0's first tensor
+// build is done, so from then on one group's FED steps (latency-bound) tend to
+// run beside the other group's tensor build (FMA-bound).  Each kernel's
+// persistent grid takes half the GPU so that kernels of both streams
+// co-reside on every SM.  The per-image arithmetic is unchanged.
+static int enqueue_batch_two_streams(const fd4_image *imgs, int n_images, const float *h_sigmas, int n_sigma,
+                                     const fd4_params &p, const double *tau, int n, int M, int sigma_given,
+                                     void *d_ws, cudaStream_t s0, cudaStream_t s1, cudaEvent_t ev_fork,
+                                     cudaEvent_t ev_go, cudaEvent_t ev_join)
+{
+    std::vector<ImgDesc> descs;
+    HostBatch B0, B1;
+    const int split = balanced_split(imgs, n_images);
+    batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B0, split, &B1);
+    if (launch_put_descs(descs.data(), n_images, (ImgDesc *)d_ws, s0)) return FD4_ERR_CUDA;
+    const int steps = p.fed_steps_per_launch > 0 ? p.fed_steps_per_launch : default_steps_per_launch();
+    if (cudaEventRecord(ev_fork, s0) != cudaSuccess || cudaStreamWaitEvent(s1, ev_fork, 0) != cudaSuccess)
+        return FD4_ERR_CUDA;
+    set_grid_divisor(2);
+    int rc = FD4_OK;
+    // group 0: selection, copy, first tensor build; then group 1 may start
+    if ((!sigma_given && launch_select_batch(B0, h_sigmas, n_sigma, p, s0)) || launch_copy_in_batch(B0, s0) ||
+        launch_tensor_batch(B0, h_sigmas, n_sigma, p, s0))
+        rc = FD4_ERR_CUDA;
+    if (rc == FD4_OK && (cudaEventRecord(ev_go, s0) != cudaSuccess || cudaStreamWaitEvent(s1, ev_go, 0) != cudaSuccess))
+        rc = FD4_ERR_CUDA;
+    if (rc == FD4_OK && ((!sigma_given && launch_select_batch(B1, h_sigmas, n_sigma, p, s1)) ||
+                         launch_copy_in_batch(B1, s1)))
+        rc = FD4_ERR_CUDA;
+    for (int k = 0; k < M && rc == FD4_OK; ++k) {
+        if (launch_fed_batch(B0, tau, n, p.boundary, steps, s0)) rc = FD4_ERR_CUDA;
+        if (rc == FD4_OK && k + 1 < M && launch_tensor_batch(B0, h_sigmas, n_sigma, p, s0)) rc = FD4_ERR_CUDA;
+        if (rc == FD4_OK && launch_tensor_batch(B1, h_sigmas, n_sigma, p, s1)) rc = FD4_ERR_CUDA;
+        if (rc == FD4_OK && launch_fed_batch(B1, tau, n, p.boundary, steps, s1)) rc = FD4_ERR_CUDA;
+    }
+    set_grid_divisor(1);
+    if (cudaEventRecord(ev_join, s1) != cudaSuccess || cudaStreamWaitEvent(s0, ev_join, 0) != cudaSuccess)
+        return FD4_ERR_CUDA;
+    return rc;
 }
 
 static int enqueue_batch(const fd4_image *imgs, int n_images, const float *h_sigmas, int n_sigma,
@@ -521,7 +598,8 @@ extern "C" int fd4_graph_create(const fd4_image *h_imgs, int n_images, const flo
                                 const fd4_params *params, double T, int M, int n_in, int sigma_given,
                                 int stages, void *d_ws, size_t ws_bytes, fd4_graph *out)
 {
-    if (!out || stages <= 0 || stages > FD4_STAGES_ALL) return FD4_ERR_BAD_ARG;
+    if (!out || (stages & FD4_STAGES_ALL) == 0 || (stages & ~(FD4_STAGES_ALL | FD4_GRAPH_TWO_STREAMS)) != 0)
+        return FD4_ERR_BAD_ARG;
     *out = nullptr;
     fd4_params p;
     resolve_params(params, &p);
@@ -531,16 +609,37 @@ extern "C" int fd4_graph_create(const fd4_image *h_imgs, int n_images, const flo
     if (rc != FD4_OK) return rc;
     // kernel attributes are set outside the capture
     if (prepare_scale_kernels() || prepare_fed_kernels()) return FD4_ERR_CUDA;
-    cudaStream_t s;
+    const bool two = (stages & FD4_GRAPH_TWO_STREAMS) && n_images >= 2;
+    stages &= FD4_STAGES_ALL;
+    cudaStream_t s, s1 = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return FD4_ERR_CUDA;
+    if (two) {
+        bool ok = cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; i < 3 && ok; ++i) ok = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            for (int i = 0; i < 3; ++i)
+                if (ev[i]) cudaEventDestroy(ev[i]);
+            if (s1) cudaStreamDestroy(s1);
+            cudaStreamDestroy(s);
+            return FD4_ERR_CUDA;
+        }
+    }
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaStreamDestroy(s);
         return FD4_ERR_CUDA;
     }
-    rc = enqueue_batch(h_imgs, n_images, h_sigmas, n_sigma, p, tau.data(), n, M, sigma_given, d_ws, s, stages);
+    if (two && stages == FD4_STAGES_ALL)
+        rc = enqueue_batch_two_streams(h_imgs, n_images, h_sigmas, n_sigma, p, tau.data(), n, M, sigma_given, d_ws, s,
+                                       s1, ev[0], ev[1], ev[2]);
+    else
+        rc = enqueue_batch(h_imgs, n_images, h_sigmas, n_sigma, p, tau.data(), n, M, sigma_given, d_ws, s, stages);
     const cudaError_t ec = cudaStreamEndCapture(s, &g);
     cudaStreamDestroy(s);
+    if (s1) cudaStreamDestroy(s1);
+    for (int i = 0; i < 3; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
     if (rc != FD4_OK || ec != cudaSuccess || !g) {
         if (g) cudaGraphDestroy(g);
         return rc != FD4_OK ? rc : FD4_ERR_CUDA;

@@ -131,6 +131,8 @@ __device__ __forceinline__ int tile_count(const Imgs &I, int shape)
 
 // Persistent grid size for a kernel: resident blocks per SM x SMs, capped by the tiles.
 int persistent_grid(const void *kernel, int threads, size_t smem, int tiles);
+// Divides every following persistent grid (used while two streams share the GPU).
+void set_grid_divisor(int d);
 
 // Host helpers (fd4_host.cpp).
 int gauss_taps(double sigma, GaussTaps *out);            // radius ceil(4 sigma)

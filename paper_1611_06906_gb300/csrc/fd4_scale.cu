@@ -600,6 +600,9 @@ int launch_tensor(const float *d_u, int w, int h, int pitch, const uint8_t *d_id
     return launch_tensor_batch(single_batch(d), h_sigmas, n_sigma, p, st);
 }
 
+static thread_local int g_grid_divisor = 1;
+void set_grid_divisor(int d) { g_grid_divisor = d > 0 ? d : 1; }
+
 int persistent_grid(const void *kernel, int threads, size_t smem, int tiles)
 {
     static int sms = 0;
@@ -611,7 +614,8 @@ int persistent_grid(const void *kernel, int threads, size_t smem, int tiles)
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
-    const long long g = (long long)per_sm * sms;
+    long long g = (long long)per_sm * sms / g_grid_divisor;
+    if (g < 1) g = 1;
     return (int)(tiles < g ? (tiles > 0 ? tiles : 1) : g);
 }
 

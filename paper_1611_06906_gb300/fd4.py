@@ -22,6 +22,7 @@ RIDGE, VALLEY, BOTH = 0, 1, 2
 NATURAL, PERIODIC = 0, 1
 OP_SELECT_SCALES, OP_BUILD_TENSOR, OP_FED_CYCLE, OP_FILTER = 0, 1, 2, 3
 STAGE_SELECT, STAGE_COPY, STAGE_TENSOR, STAGE_FED, STAGES_ALL = 1, 2, 4, 8, 15
+GRAPH_TWO_STREAMS = 16
 MAX_FED_STEPS = 4096
 
 _lock = threading.Lock()

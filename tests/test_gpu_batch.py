@@ -119,3 +119,29 @@ def test_bad_batch_is_rejected_before_launch():
     with pytest.raises(fd4.Fd4Error) as e:
         fd4.filter_batched(lst, SIGMAS, T, M, N, ws=fd4.batch_workspace(fd4.image_list(ins, [128, 37]), 4))
     assert e.value.status == -4
+
+
+def test_two_stream_graph_equals_one_stream_graph():
+    import torch
+    imgs = _images()
+    prm = fd4.params(mode=fd4.VALLEY)
+    ins, outs, idx, lst = _batch(imgs)
+    g1 = fd4.Graph(lst, SIGMAS, T, M, N, prm)
+    g1.launch()
+    torch.cuda.synchronize()
+    ref = [o.clone() for o in outs]
+    ref_idx = [i.clone() for i in idx]
+    for o in outs:
+        o.zero_()
+    for i in idx:
+        i.zero_()
+    g2 = fd4.Graph(lst, SIGMAS, T, M, N, prm, stages=fd4.STAGES_ALL | fd4.GRAPH_TWO_STREAMS)
+    for _ in range(2):
+        g2.launch()
+        torch.cuda.synchronize()
+        for o, r, i, ri, im in zip(outs, ref, idx, ref_idx, imgs):
+            w = im.shape[1]
+            assert torch.equal(i[:, :w], ri[:, :w])
+            assert float((o[:, :w] - r[:, :w]).abs().max()) == 0.0
+    g1.close()
+    g2.close()
