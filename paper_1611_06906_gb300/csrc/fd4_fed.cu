@@ -440,6 +440,250 @@ __global__ void __launch_bounds__(FNT, 2) k_fed_fused_pipe(Imgs I, StepTaus taus
     cp_async_wait_all();
 }
 
+// ---------------------------------------------------------------------------
+// Quad variant (natural boundary, S = 2 or 4), the default.  Same 64 x 32
+// region, cp.async staging of the next tile and S steps per launch, but each
+// of the 512 threads owns a row quad (4 adjacent pixels of one row) and keeps
+// its u, its T_xx and its tensor values in registers; horizontal neighbours
+// come from the adjacent lanes by shuffles, vertical ones from 16-byte shared
+// loads of the rows above and below (u, T_xy and T_yy planes only).  T and u
+// are computed on the whole region: the planes carry a zero ring, and the
+// values spoiled at the region border (ring reads, shuffles that wrap to the
+// other row of the warp) reach 2 pixels further in per step and stay inside
+// the H = 2S halo, so no step needs a shrinking-region test.  The tensor is
+// kept per pixel as (cos 2t, sin 2t, (mu1 + mu2) / 2, (mu1 - mu2) / 2), with
+// which T = D : H costs about 26 flops.
+
+constexpr int QNT = 512;                          // threads: 16 quads across x 32 rows
+constexpr int QPAD = 4;                           // ring columns (keeps quads 16-byte aligned)
+constexpr int QSW = FRX + 2 * QPAD;               // 72 floats per plane row
+constexpr int QPLANE = (FRY + 2) * QSW;           // one ring row above and below
+constexpr int QTS = 5;                            // float4 slots per quad in the tensor buffer (1 pad:
+                                                  // the 16-byte reads of 8 lanes hit distinct banks)
+constexpr int QTBUF = FRY * (FRX / 4) * QTS;      // float4 entries
+constexpr size_t kQuadSmem = sizeof(float) * 4 * QPLANE + sizeof(float4) * QTBUF;  // 2 u, T_xy, T_yy, tensor
+
+struct QuadCoef {
+    float4 c, s, p, q;  // per pixel of the quad: cos 2t, sin 2t, mean and half difference of mu
+};
+
+__device__ __forceinline__ void f4_to(const float4 v, float *d)
+{
+    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+}
+
+// The quad's 4 values with the left and right neighbours from adjacent lanes.
+__device__ __forceinline__ void quad_ext(const float4 m, float (&v)[6])
+{
+    v[0] = __shfl_up_sync(0xffffffffu, m.w, 1);
+    v[1] = m.x; v[2] = m.y; v[3] = m.z; v[4] = m.w;
+    v[5] = __shfl_down_sync(0xffffffffu, m.x, 1);
+}
+
+// T = M D M L u for the 4 pixels of one quad.  a, b, c: rows y-1, y, y+1 at
+// columns x-1 .. x+4.  BOUNDARY: apply the natural-boundary masks (bits 0-3:
+// pixel inside, 4-7: Lxx row exists, 8: Lyy row exists for this row).
+template <bool BOUNDARY>
+__device__ __forceinline__ void quad_T(const float (&a)[6], const float (&b)[6], const float (&c)[6],
+                                       const QuadCoef &k, unsigned mask, float4 &Txx, float4 &Txy, float4 &Tyy)
+{
+    float rxx[4], rxy[4], ryy[4];
+    float cc[4], ss[4], pp[4], qq[4];
+    f4_to(k.c, cc);
+    f4_to(k.s, ss);
+    f4_to(k.p, pp);
+    f4_to(k.q, qq);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float hxx = fmaf(-2.0f, b[i + 1], b[i] + b[i + 2]);
+        float hyy = fmaf(-2.0f, b[i + 1], a[i + 1] + c[i + 1]);
+        float hxy = 0.25f * ((a[i] + c[i + 2]) - (c[i] + a[i + 2]));
+        bool vx = true, vy = true, in = true;
+        if (BOUNDARY) {
+            in = (mask >> i) & 1u;
+            vx = (mask >> (4 + i)) & 1u;
+            vy = (mask >> 8) & 1u;
+            hxx = vx ? hxx : 0.0f;
+            hyy = vy ? hyy : 0.0f;
+            hxy = (vx && vy) ? hxy : 0.0f;
+        }
+        const float sh = 0.5f * (hxx + hyy), dh = 0.5f * (hxx - hyy);
+        const float z = fmaf(cc[i], dh, ss[i] * hxy);          // eigenframe: h11 = sh + z, h22 = sh - z
+        const float v = fmaf(cc[i], hxy, -ss[i] * dh);         // h12
+        const float st = fmaf(pp[i], sh, qq[i] * z);           // (t11 + t22) / 2
+        const float dt = fmaf(qq[i], sh, pp[i] * z);           // (t11 - t22) / 2
+        const float t12 = pp[i] * v;
+        float txx = fmaf(cc[i], dt, fmaf(-ss[i], t12, st));
+        float tyy = fmaf(2.0f, st, -txx);
+        float txy = fmaf(ss[i], dt, cc[i] * t12);
+        if (BOUNDARY) {
+            txx = (in && vx) ? txx : 0.0f;
+            tyy = (in && vy) ? tyy : 0.0f;
+            txy = (in && vx && vy) ? txy : 0.0f;
+        }
+        rxx[i] = txx;
+        rxy[i] = txy;
+        ryy[i] = tyy;
+    }
+    Txx = make_float4(rxx[0], rxx[1], rxx[2], rxx[3]);
+    Txy = make_float4(rxy[0], rxy[1], rxy[2], rxy[3]);
+    Tyy = make_float4(ryy[0], ryy[1], ryy[2], ryy[3]);
+}
+
+// S steps of one staged region; uo: this quad's u on entry, returned updated.
+template <bool BOUNDARY>
+__device__ __forceinline__ float4 quad_steps(float *su, float *sxy, float *syy, const float *stau, int nsteps,
+                                             int off, const QuadCoef &k, unsigned mask, float4 uo)
+{
+    for (int l = 0; l < nsteps; ++l) {
+        float a[6], b[6], c[6];
+        quad_ext(*reinterpret_cast<const float4 *>(su + off - QSW), a);
+        quad_ext(uo, b);
+        quad_ext(*reinterpret_cast<const float4 *>(su + off + QSW), c);
+        float4 txx, txy, tyy;
+        quad_T<BOUNDARY>(a, b, c, k, mask, txx, txy, tyy);
+        *reinterpret_cast<float4 *>(sxy + off) = txy;
+        *reinterpret_cast<float4 *>(syy + off) = tyy;
+        __syncthreads();
+        // u -= tau (Lxx' Txx + Lyy' Tyy + 2 Lxy' Txy)
+        float X[6], Zu[6], Zd[6], Yu[4], Yc[4], Yd[4];
+        quad_ext(txx, X);
+        quad_ext(*reinterpret_cast<const float4 *>(sxy + off - QSW), Zu);
+        quad_ext(*reinterpret_cast<const float4 *>(sxy + off + QSW), Zd);
+        f4_to(*reinterpret_cast<const float4 *>(syy + off - QSW), Yu);
+        f4_to(tyy, Yc);
+        f4_to(*reinterpret_cast<const float4 *>(syy + off + QSW), Yd);
+        const float tau = stau[l];
+        float r[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float div = fmaf(-2.0f, X[i + 1], X[i] + X[i + 2]) + fmaf(-2.0f, Yc[i], Yu[i] + Yd[i]) +
+                              0.5f * ((Zd[i + 2] + Zu[i]) - (Zu[i + 2] + Zd[i]));
+            r[i] = fmaf(-tau, div, b[i + 1]);
+            if (BOUNDARY && !((mask >> i) & 1u)) r[i] = b[i + 1];
+        }
+        uo = make_float4(r[0], r[1], r[2], r[3]);
+        *reinterpret_cast<float4 *>(su + off) = uo;
+        __syncthreads();
+    }
+    return uo;
+}
+
+template <int S>
+__device__ __forceinline__ void quad_prefetch(const ImgDesc &d, int local, float *u_dst, float4 *t_dst, int parity)
+{
+    constexpr int H = 2 * S, TXo = FRX - 2 * H, TYo = FRY - 2 * H;
+    const int tid = threadIdx.x;
+    const int w = d.w, h = d.h, pitch = d.pitch;
+    const int tiles_x = (w + TXo - 1) / TXo;
+    const int gx0 = (local % tiles_x) * TXo - H, gy0 = (local / tiles_x) * TYo - H;
+    const float *uin = parity ? d.tmp : d.u;
+    {
+        const int ry = tid >> 4, cx = (tid & 15) * 4;  // one 16-byte chunk per thread
+        const int gy = gy0 + ry, gx = gx0 + cx;
+        // a chunk of 4 columns starting inside the image stays inside the row pitch
+        const bool valid = gy >= 0 && gy < h && gx >= 0 && gx < w;
+        cp_async16(u_dst + (ry + 1) * QSW + QPAD + cx, valid ? uin + (size_t)gy * pitch + gx : uin, valid);
+    }
+#pragma unroll
+    for (int j = 0; j < FRX * FRY / QNT; ++j) {
+        const int i = tid + j * QNT;
+        const int ry = i / FRX, rx = i % FRX;
+        const int gy = gy0 + ry, gx = gx0 + rx;
+        const bool valid = gy >= 0 && gy < h && gx >= 0 && gx < w;
+        cp_async16(t_dst + (ry * (FRX / 4) + (rx >> 2)) * QTS + (rx & 3),
+                   valid ? d.tensor + (size_t)gy * pitch + gx : d.tensor, valid);
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(QNT, 2) k_fed_quad(Imgs I, StepTaus taus, int parity)
+{
+    constexpr int H = 2 * S, TXo = FRX - 2 * H, TYo = FRY - 2 * H;
+    static_assert(TXo % 4 == 0 && H % 4 == 0, "16-byte aligned region columns");
+    static_assert(QNT == (FRX / 4) * FRY, "one quad per thread");
+    extern __shared__ __align__(16) float qsm[];
+    // planes: u buffer 0, u buffer 1, T_xy, T_yy (each with the zero ring), then the tensor
+    float *sxy = qsm + 2 * QPLANE, *syy = qsm + 3 * QPLANE;
+    float4 *tbuf = reinterpret_cast<float4 *>(qsm + 4 * QPLANE);
+    __shared__ float stau[8];
+    __shared__ ImgDesc sd[2];
+    __shared__ int s_local[2];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) stau[i] = taus.t[i];
+    }
+    for (int i = tid; i < 4 * QPLANE; i += QNT) qsm[i] = 0.0f;  // the rings stay zero
+    const int q = tid & 15, ry = tid >> 4;
+    const int off = (ry + 1) * QSW + QPAD + 4 * q;  // this quad in a plane
+    const float4 *tq = tbuf + (ry * (FRX / 4) + q) * QTS;
+    const int ntiles = I.tiles;
+    int cur = 0;
+    int t = blockIdx.x;
+    __syncthreads();
+    if (t < ntiles) {
+        if (tid == 0) find_tile(I, S, t, sd[0], s_local[0]);
+        __syncthreads();
+        quad_prefetch<S>(sd[0], s_local[0], qsm, tbuf, parity);
+    }
+    cp_async_commit();
+    for (; t < ntiles; t += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();  // this tile's u region and tensor values have landed
+        const int w = sd[cur].w, h = sd[cur].h, pitch = sd[cur].pitch;
+        float *uout = parity ? sd[cur].u : sd[cur].tmp;
+        const int tiles_x = (w + TXo - 1) / TXo;
+        const int gx0 = (s_local[cur] % tiles_x) * TXo - H, gy0 = (s_local[cur] / tiles_x) * TYo - H;
+        const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + FRX <= w && gy0 + FRY <= h;
+        const int gx = gx0 + 4 * q, gy = gy0 + ry;
+        float *su = qsm + cur * QPLANE;
+        const float4 u0 = *reinterpret_cast<const float4 *>(su + off);
+        unsigned mask = 0u;
+        QuadCoef k;
+        {
+            float cc[4], ss[4], pp[4], qq[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 tt = tq[i];
+                cc[i] = tt.x;
+                ss[i] = tt.y;
+                pp[i] = 0.5f * (tt.z + tt.w);
+                qq[i] = 0.5f * (tt.z - tt.w);
+                const int x = gx + i;
+                mask |= (x >= 0 && x < w && gy >= 0 && gy < h ? 1u : 0u) << i;
+                mask |= (x >= 1 && x <= w - 2 ? 1u : 0u) << (4 + i);
+            }
+            mask |= (gy >= 1 && gy <= h - 2 ? 1u : 0u) << 8;
+            k.c = make_float4(cc[0], cc[1], cc[2], cc[3]);
+            k.s = make_float4(ss[0], ss[1], ss[2], ss[3]);
+            k.p = make_float4(pp[0], pp[1], pp[2], pp[3]);
+            k.q = make_float4(qq[0], qq[1], qq[2], qq[3]);
+        }
+        const int tn = t + gridDim.x;
+        if (tid == 0 && tn < ntiles) find_tile(I, S, tn, sd[cur ^ 1], s_local[cur ^ 1]);
+        __syncthreads();  // the tensor buffer is read; the next descriptor is ready
+        if (tn < ntiles) quad_prefetch<S>(sd[cur ^ 1], s_local[cur ^ 1], qsm + (cur ^ 1) * QPLANE, tbuf, parity);
+        cp_async_commit();
+
+        const float4 un = interior ? quad_steps<false>(su, sxy, syy, stau, taus.n, off, k, mask, u0)
+                                   : quad_steps<true>(su, sxy, syy, stau, taus.n, off, k, mask, u0);
+        // the exact interior: rows H .. H + TYo - 1, columns H .. H + TXo - 1 (whole quads)
+        if (ry >= H && ry < H + TYo && 4 * q >= H && 4 * q < H + TXo && gy < h) {
+            float *dst = uout + (size_t)gy * pitch + gx;
+            if (gx + 3 < w) {
+                *reinterpret_cast<float4 *>(dst) = un;
+            } else {
+                if (gx < w) dst[0] = un.x;
+                if (gx + 1 < w) dst[1] = un.y;
+                if (gx + 2 < w) dst[2] = un.z;
+            }
+        }
+        cur ^= 1;
+    }
+    cp_async_wait_all();
+}
+
 template <int S>
 static int set_fused_smem()
 {
@@ -470,10 +714,37 @@ static int set_pipe_smem()
     return 0;
 }
 
+template <int S>
+static int set_quad_smem()
+{
+    static int attr_dev = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (attr_dev != dev) {
+        if (cudaFuncSetAttribute(k_fed_quad<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQuadSmem) !=
+            cudaSuccess)
+            return 1;
+        attr_dev = dev;
+    }
+    return 0;
+}
+
 int prepare_fed_kernels()
 {
     return set_fused_smem<2>() || set_fused_smem<3>() || set_fused_smem<4>() || set_pipe_smem<2>() ||
-           set_pipe_smem<4>();
+           set_pipe_smem<4>() || set_quad_smem<2>() || set_quad_smem<4>();
+}
+
+template <int S>
+static int launch_quad(Imgs I, const double *tau, int n, int parity, cudaStream_t st)
+{
+    if (set_quad_smem<S>()) return 1;
+    StepTaus t{};
+    t.n = n;
+    for (int i = 0; i < n; ++i) t.t[i] = (float)tau[i];
+    const int grid = persistent_grid((const void *)k_fed_quad<S>, QNT, kQuadSmem, I.tiles);
+    k_fed_quad<S><<<grid, QNT, kQuadSmem, st>>>(I, t, parity);
+    return 0;
 }
 
 template <int S>
@@ -500,12 +771,15 @@ static int launch_fused(Imgs I, const double *tau, int n, int parity, int period
     return 0;
 }
 
-// The cp.async-pipelined kernel is used for S = 2 and 4 under the natural
-// boundary unless FD4_FED_PIPELINE=0 (the plain fused kernel then runs).
-static bool pipeline_enabled()
+// Kernel for S = 2 and 4 under the natural boundary, from FD4_FED_PIPELINE:
+// 0 = the plain fused kernel, 1 = its cp.async-pipelined form, unset or 2 =
+// the quad kernel.  S = 3 and the periodic boundary use the plain fused kernel.
+static int pipeline_kind()
 {
     const char *e = getenv("FD4_FED_PIPELINE");
-    return !(e && e[0] == '0');
+    if (e && e[0] == '0') return 0;
+    if (e && e[0] == '1') return 1;
+    return 2;
 }
 
 int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundary, int steps_per_launch,
@@ -529,8 +803,11 @@ int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundar
         for (int i = 0; i < n; i += S) {
             const int k = n - i < S ? n - i : S;
             int rc;
-            if (!periodic && S == 2 && pipeline_enabled()) rc = launch_pipe<2>(I, h_tau + i, k, parity, st);
-            else if (!periodic && S == 4 && pipeline_enabled()) rc = launch_pipe<4>(I, h_tau + i, k, parity, st);
+            const int kind = periodic || S == 3 ? 0 : pipeline_kind();
+            if (kind == 2) rc = S == 2 ? launch_quad<2>(I, h_tau + i, k, parity, st)
+                                       : launch_quad<4>(I, h_tau + i, k, parity, st);
+            else if (kind == 1) rc = S == 2 ? launch_pipe<2>(I, h_tau + i, k, parity, st)
+                                            : launch_pipe<4>(I, h_tau + i, k, parity, st);
             else rc = S == 2 ? launch_fused<2>(I, h_tau + i, k, parity, periodic, st)
                     : S == 3 ? launch_fused<3>(I, h_tau + i, k, parity, periodic, st)
                              : launch_fused<4>(I, h_tau + i, k, parity, periodic, st);

@@ -10,7 +10,10 @@
 // refilled four taps at a time (one 16-byte shared load in the row pass), so
 // the inner loops are almost pure FMA.  The work is FP32-FMA bound: about
 // 3 (2R+4)(1 + (2R+8)/64) + 5 (2R+4) FMAs per pixel and scale, R = ceil(4 sigma)
-// rounded up to a multiple of 4.
+// rounded up to a multiple of 4.  The tensor build needs each pixel's
+// derivatives at its own scale only: the tile's pixels are first grouped by
+// selected scale, and for each scale the row pass covers only the rows and
+// 8-column chunks those pixels reach, the column pass only those pixels.
 #include <cstdint>
 
 #include "fd4_internal.h"
@@ -127,7 +130,11 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
     extern __shared__ __align__(16) float smem[];
     __shared__ ImgDesc sd;
     __shared__ int s_local;
-    __shared__ unsigned present;
+    // tensor mode: the tile's pixels grouped by selected scale, (py << 5) | px,
+    // and per scale the count, list start, row range and 8-column chunks used
+    __shared__ unsigned short plist[OUT == OUT_TENSOR ? TX * TY : 1];
+    __shared__ int pcnt[kMaxSweep], pstart[kMaxSweep], prow0[kMaxSweep], prow1[kMaxSweep];
+    __shared__ unsigned pchunk[kMaxSweep];
     const int Rmax = taps.Rmax;
     const int S = sweep_in_stride(Rmax);
     const int rows = sweep_rows(Rmax);
@@ -141,9 +148,12 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
     const int ntiles = tile_count(I, SHAPE_SWEEP);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     __syncthreads();   // the previous tile is done with shared memory
-    if (tid == 0) {
-        find_tile(I, SHAPE_SWEEP, t, sd, s_local);
-        present = 0u;
+    if (tid == 0) find_tile(I, SHAPE_SWEEP, t, sd, s_local);
+    if (OUT == OUT_TENSOR && tid < kMaxSweep) {
+        pcnt[tid] = 0;
+        prow0[tid] = TY;
+        prow1[tid] = -1;
+        pchunk[tid] = 0u;
     }
     __syncthreads();
     const int w = sd.w, h = sd.h, pitch = sd.pitch;
@@ -157,10 +167,12 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
 
     const int ox = tid & 31, oy0 = (tid >> 5) * VC;
     const int gx = x0 + ox;
-    // tensor mode: this thread's 8 pixels' scale index within this launch (-1: none)
-    int my_local[VC];
+    // Tensor mode: group the tile's pixels by selected scale.  In a warp, the
+    // VC rows of this thread group are one tile row each, so the lanes that
+    // share a scale in row j are found with one match and counted with one
+    // shared atomic; the rank among them gives the slot in the scale's list.
     if (OUT == OUT_TENSOR) {
-        unsigned bits = 0u;
+        int my_local[VC], my_pos[VC];
 #pragma unroll
         for (int j = 0; j < VC; ++j) {
             const int gy = y0 + oy0 + j;
@@ -169,24 +181,60 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
                 sd.nfield[(size_t)gy * pitch + gx] = make_float4(0.f, 0.f, 0.f, 0.f);
             const int local = id - taps.s0;
             my_local[j] = (id >= 0 && local >= 0 && local < taps.K) ? local : -1;
-            if (my_local[j] >= 0) bits |= 1u << my_local[j];
+            const unsigned peers = __match_any_sync(0xffffffffu, my_local[j]);
+            const int leader = __ffs(peers) - 1;
+            int base = 0;
+            if (lane == leader && my_local[j] >= 0) {
+                const int s = my_local[j];
+                base = atomicAdd(&pcnt[s], __popc(peers));
+                atomicMin(&prow0[s], oy0 + j);
+                atomicMax(&prow1[s], oy0 + j);
+                const unsigned ch = ((peers & 0x000000FFu) ? 1u : 0u) | ((peers & 0x0000FF00u) ? 2u : 0u) |
+                                    ((peers & 0x00FF0000u) ? 4u : 0u) | ((peers & 0xFF000000u) ? 8u : 0u);
+                atomicOr(&pchunk[s], ch);
+            }
+            my_pos[j] = __shfl_sync(0xffffffffu, base, leader) + __popc(peers & ((1u << lane) - 1u));
         }
-        if (bits) atomicOr(&present, bits);
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            for (int s = 0; s < taps.K; ++s) {
+                pstart[s] = acc;
+                acc += pcnt[s];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < VC; ++j)
+            if (my_local[j] >= 0) plist[pstart[my_local[j]] + my_pos[j]] = (unsigned short)(((oy0 + j) << 5) | ox);
     }
     __syncthreads();
 
     float bmax = 0.0f;
     for (int s = 0; s < taps.K; ++s) {
-        if (OUT == OUT_TENSOR && !((present >> s) & 1u)) continue;   // block-uniform
+        if (OUT == OUT_TENSOR && pcnt[s] == 0) continue;   // block-uniform
         const int R = taps.R[s];
         const int L = 2 * R + 4, nch = L / 4;
         const int off = Rmax - R;
         const float *w0 = wt + taps.off[s], *w1 = w0 + L, *w2 = w1 + L;
 
-        // Row pass on staged rows [off, off + TY + 2R + 4): three fields along x.
-        const int nrows = TY + 2 * R + 4;
-        for (int u = tid; u < nrows * (TX / VR); u += NT) {
-            const int sy = off + (u >> 2), xo = (u & 3) * VR;
+        // Row pass: three fields along x on staged rows [off + r0, off + r0 + nrows).
+        // Selection needs every row and column of the tile; the tensor build
+        // only the rows within reach of a pixel of this scale and the 8-column
+        // chunks that hold one.
+        int r0 = 0, nrows = TY + 2 * R + 4;
+        unsigned cmask = 0xFu;
+        if (OUT == OUT_TENSOR) {
+            r0 = prow0[s];
+            nrows = prow1[s] - r0 + L;
+            cmask = pchunk[s];
+        }
+        const int ncx = __popc(cmask);
+        for (int u = tid; u < nrows * ncx; u += NT) {
+            int q = u / ncx, cx = u - q * ncx;
+            unsigned m = cmask;
+            for (; cx > 0; --cx) m &= m - 1u;
+            const int sy = off + r0 + q, xo = (__ffs(m) - 1) * VR;
             const float *src = tin + sy * S + xo + off;
             float win[VR + 4];
             {
@@ -234,55 +282,39 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
         __syncthreads();
 
         if (OUT == OUT_TENSOR) {
-            // Column pass only for the pixels whose selected scale is this one.
-            // Each warp packs its matching pixels (rows oy0.., all 32 columns)
-            // 32 at a time with ballots and evaluates the five derivatives of
-            // each as direct tap sums, one pixel per lane.
-            int entry = -1, pending = 0;
+            // Column pass only for the pixels whose selected scale is this one:
+            // the block walks the scale's list, one pixel per thread, and
+            // evaluates the five derivatives as direct tap sums.
+            const int cnt = pcnt[s];
+            const unsigned short *lst = plist + pstart[s];
+            for (int e = tid; e < cnt; e += NT) {
+                const int entry = lst[e];
+                const int px = entry & 31, py = entry >> 5;
+                const float *c0 = trow + (py + off) * RS + px;   // field 0: smoothed along x
+                const float *c1 = c0 + rows * RS;                 // field 1: d/dx
+                const float *c2 = c1 + rows * RS;                 // field 2: d2/dx2
+                float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
+                for (int ch = 0; ch < nch; ++ch) {
+                    const float4 A = *reinterpret_cast<const float4 *>(w0 + 4 * ch);
+                    const float4 B = *reinterpret_cast<const float4 *>(w1 + 4 * ch);
+                    const float4 C = *reinterpret_cast<const float4 *>(w2 + 4 * ch);
+                    const float a4[4] = {A.x, A.y, A.z, A.w}, b4[4] = {B.x, B.y, B.z, B.w};
+                    const float c4[4] = {C.x, C.y, C.z, C.w};
 #pragma unroll
-            for (int j = 0; j <= VC; ++j) {
-                unsigned m = j < VC ? __ballot_sync(0xffffffffu, my_local[j] == s) : 0u;
-                while (m != 0u || (j == VC && pending > 0)) {
-                    const int take = min(__popc(m), 32 - pending);
-                    const int r = lane - pending;
-                    if (r >= 0 && r < take) entry = ((oy0 + j) << 5) | (int)__fns(m, 0, r + 1);
-                    for (int q = 0; q < take; ++q) m &= m - 1u;   // drop the taken bits
-                    pending += take;
-                    if (pending == 32 || (j == VC && pending > 0)) {
-                        if (entry >= 0) {
-                            const int px = entry & 31, py = entry >> 5;
-                            const float *c0 = trow + (py + off) * RS + px;   // field 0: smoothed along x
-                            const float *c1 = c0 + rows * RS;                 // field 1: d/dx
-                            const float *c2 = c1 + rows * RS;                 // field 2: d2/dx2
-                            float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
-                            for (int ch = 0; ch < nch; ++ch) {
-                                const float4 A = *reinterpret_cast<const float4 *>(w0 + 4 * ch);
-                                const float4 B = *reinterpret_cast<const float4 *>(w1 + 4 * ch);
-                                const float4 C = *reinterpret_cast<const float4 *>(w2 + 4 * ch);
-                                const float a4[4] = {A.x, A.y, A.z, A.w}, b4[4] = {B.x, B.y, B.z, B.w};
-                                const float c4[4] = {C.x, C.y, C.z, C.w};
-#pragma unroll
-                                for (int ii = 0; ii < 4; ++ii) {
-                                    const int k = (4 * ch + ii) * RS;
-                                    const float v0 = c0[k], v1 = c1[k], v2 = c2[k];
-                                    sy = fmaf(b4[ii], v0, sy);
-                                    syy = fmaf(c4[ii], v0, syy);
-                                    sx = fmaf(a4[ii], v1, sx);
-                                    sxy = fmaf(b4[ii], v1, sxy);
-                                    sxx = fmaf(a4[ii], v2, sxx);
-                                }
-                            }
-                            const float g2 = fmaf(sx, sx, sy * sy);
-                            const float g = grad_sq ? g2 : sqrtf(g2);
-                            const float f = 1.0f / sqrtf(1.0f + g);
-                            sd.nfield[(size_t)(y0 + py) * pitch + x0 + px] =
-                                make_float4(f * sxx, f * sxy, f * syy, 0.0f);
-                        }
-                        entry = -1;
-                        pending = 0;
+                    for (int ii = 0; ii < 4; ++ii) {
+                        const int k = (4 * ch + ii) * RS;
+                        const float v0 = c0[k], v1 = c1[k], v2 = c2[k];
+                        sy = fmaf(b4[ii], v0, sy);
+                        syy = fmaf(c4[ii], v0, syy);
+                        sx = fmaf(a4[ii], v1, sx);
+                        sxy = fmaf(b4[ii], v1, sxy);
+                        sxx = fmaf(a4[ii], v2, sxx);
                     }
-                    if (j == VC) break;
                 }
+                const float g2 = fmaf(sx, sx, sy * sy);
+                const float g = grad_sq ? g2 : sqrtf(g2);
+                const float f = 1.0f / sqrtf(1.0f + g);
+                sd.nfield[(size_t)(y0 + py) * pitch + x0 + px] = make_float4(f * sxx, f * sxy, f * syy, 0.0f);
             }
             __syncthreads();   // trow is rewritten by the next scale's row pass
             continue;

@@ -18,6 +18,7 @@
 // FP32 accumulator back from their TMEM lanes for the epilogue.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "fd4_internal.h"
@@ -486,6 +487,40 @@ __global__ void __launch_bounds__(256) k_sel_fallback_tiles(const float *conf, i
 
 namespace {
 
+// Persistent grid of a kernel that allocates 32 TMEM columns per block.  The
+// runtime's occupancy query reports one block per SM for any kernel that uses
+// tcgen05.alloc, whatever its resources, so the blocks per SM are taken here
+// from registers and shared memory, and capped so that every resident block's
+// columns fit the SM's 512 (an allocation never waits on another block).
+int tmem_grid(const void *kernel, size_t dyn_smem, int tiles)
+{
+    static int sms = 0, regs_sm = 0, smem_sm = 0, smem_reserved = 0;
+    int dev = 0;
+    if (sms == 0) {
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
+            sms = 0;
+            return tiles < 152 ? (tiles > 0 ? tiles : 1) : 152;
+        }
+    }
+    cudaFuncAttributes fa;
+    int per_sm = 1;
+    if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) {
+        const int warps = (CT + 31) / 32;
+        const int regs_block = warps * ((fa.numRegs * 32 + 255) / 256) * 256;
+        const size_t smem_block = fa.sharedSizeBytes + dyn_smem + (size_t)smem_reserved;
+        per_sm = regs_block > 0 ? regs_sm / regs_block : 1;
+        if (smem_block > 0) per_sm = std::min<int>(per_sm, (int)((size_t)smem_sm / smem_block));
+        per_sm = std::min(per_sm, std::min(2048 / CT, 512 / 32));
+        if (per_sm < 1) per_sm = 1;
+    }
+    const long long g = (long long)per_sm * sms;
+    return (int)(tiles < g ? (tiles > 0 ? tiles : 1) : g);
+}
+
 template <int CI, int CO, int MODE>
 int launch_conv(const ConvArgs &a, cudaStream_t st)
 {
@@ -500,8 +535,8 @@ int launch_conv(const ConvArgs &a, cudaStream_t st)
         attr_dev = dev;
     }
     const long long tiles = (long long)a.n_img * a.h * ((a.w + TM - 1) / TM);
-    const int grid = persistent_grid((const void *)k_conv_tc<CI, CO, MODE>, CT, conv_smem_bytes(CI, CO, a.d),
-                                     (int)(tiles < (1 << 30) ? tiles : (1 << 30)));
+    const int grid = tmem_grid((const void *)k_conv_tc<CI, CO, MODE>, conv_smem_bytes(CI, CO, a.d),
+                               (int)(tiles < (1 << 30) ? tiles : (1 << 30)));
     k_conv_tc<CI, CO, MODE><<<grid, CT, conv_smem_bytes(CI, CO, a.d), st>>>(a);
     return cudaGetLastError() != cudaSuccess;
 }

@@ -62,11 +62,13 @@ def _tensor_to_device(t, w):
     return buf
 
 
-@pytest.fixture(params=[(0, 1), (2, 1), (2, 0), (3, 1), (4, 1), (4, 0)],
-                ids=["step", "fuse2", "fuse2-noprefetch", "fuse3", "fuse4", "fuse4-noprefetch"])
+@pytest.fixture(params=[(0, 2), (2, 2), (2, 1), (2, 0), (3, 2), (4, 2), (4, 1), (4, 0)],
+                ids=["step", "fuse2-quad", "fuse2-prefetch", "fuse2-plain", "fuse3", "fuse4-quad",
+                     "fuse4-prefetch", "fuse4-plain"])
 def fed_variant(request, monkeypatch):
     """FED kernel variant: one launch per step, or 2..4 steps fused per launch
-    (with or without the cp.async prefetch of the next tile)."""
+    (quad kernel, the scalar kernel with the cp.async prefetch of the next
+    tile, or the plain scalar kernel)."""
     monkeypatch.setenv("FD4_FED_FUSE", str(request.param[0]))
     monkeypatch.setenv("FD4_FED_PIPELINE", str(request.param[1]))
     return request.param
