@@ -220,11 +220,7 @@ def run_fd4(args, rank, world, local_rank):
     g_fed = fd4.Graph(lst, sig, T, M, n, prm, ws=ws, stages=fd4.STAGE_FED)
     L = -(-n // best) if best > 1 else n          # FED launches per cycle
     fed_launches = M * L
-    sweeps = -(-K // 16)                          # sweep launches per stage (16 scales each)
-    groups = 2 if (args.two_streams and len(ims) > 1) else 1  # each stage runs once per image group
-    launches_per_step = (-(-len(ims) // 128)      # descriptor upload
-                         + groups * (sweeps + 1 + 1  # selection sweep, argmax, input copy
-                                     + M * (sweeps + 1 + L + (L % 2))))  # tensor sweep, finish, FED (+ copy-back)
+    launches_per_step = g_all.kernel_count()      # kernel nodes of the captured graph
 
     for _ in range(args.warmup):
         g_all.launch()

@@ -227,6 +227,10 @@ int fd4_graph_create(const fd4_image *h_imgs, int n_images, const float *h_sigma
                      const fd4_params *params, double T, int M, int n_in, int sigma_given, int stages,
                      void *d_ws, size_t ws_bytes, fd4_graph *out);
 int fd4_graph_launch(fd4_graph g, fd4_stream_t stream);
+/* Number of kernel launches one fd4_graph_launch performs (the kernel nodes
+ * of the captured graph; every one is a kernel of this library).  No
+ * counterpart in the paper: launch accounting for benchmarks.               */
+int fd4_graph_kernel_count(fd4_graph g, int *n_kernels);
 int fd4_graph_destroy(fd4_graph g);
 
 /* Autotuner for the FED kernel schedule: runs the selection and one tensor

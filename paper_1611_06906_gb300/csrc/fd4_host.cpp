@@ -416,9 +416,9 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
     size_t off = align_up(sizeof(ImgDesc) * (size_t)n, 256);
     const size_t ms_off = off;
     off += align_up(sizeof(unsigned) * (size_t)n, 256);
-    int t0[kShapes] = {0, 0, 0, 0, 0};
+    int t0[kShapes] = {};
     if (descs) descs->resize(n);
-    int t_split[kShapes] = {0, 0, 0, 0, 0};
+    int t_split[kShapes] = {};
     for (int i = 0; i < n; ++i) {
         if (i == split && split > 0)
             for (int s = 0; s < kShapes; ++s) {
@@ -658,6 +658,23 @@ extern "C" int fd4_graph_launch(fd4_graph g, fd4_stream_t stream)
 {
     if (!g) return FD4_ERR_BAD_ARG;
     return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? FD4_OK : FD4_ERR_CUDA;
+}
+
+extern "C" int fd4_graph_kernel_count(fd4_graph g, int *n_kernels)
+{
+    if (!g || !n_kernels) return FD4_ERR_BAD_ARG;
+    size_t n = 0;
+    if (cudaGraphGetNodes(g->graph, nullptr, &n) != cudaSuccess) return FD4_ERR_CUDA;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n && cudaGraphGetNodes(g->graph, nodes.data(), &n) != cudaSuccess) return FD4_ERR_CUDA;
+    int k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess) return FD4_ERR_CUDA;
+        if (t == cudaGraphNodeTypeKernel) ++k;
+    }
+    *n_kernels = k;
+    return FD4_OK;
 }
 
 extern "C" int fd4_graph_destroy(fd4_graph g)

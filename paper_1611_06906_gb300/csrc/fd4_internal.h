@@ -40,10 +40,27 @@ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Batches.  Every stage kernel walks a flat list of tiles that spans all images
 // of a batch (a persistent grid striding over the list); the tile shape
 // depends on the kernel.
-enum TileShape { SHAPE_SWEEP = 0, SHAPE_SMALL = 1, SHAPE_FUSE2 = 2, SHAPE_FUSE3 = 3, SHAPE_FUSE4 = 4, kShapes = 5 };
+// SHAPE_SEG: a 32-column strip segment of 256 rows (the tensor build walks it
+// top to bottom).
+enum TileShape {
+    SHAPE_SWEEP = 0,
+    SHAPE_SMALL = 1,
+    SHAPE_FUSE2 = 2,
+    SHAPE_FUSE3 = 3,
+    SHAPE_FUSE4 = 4,
+    SHAPE_SEG = 5,
+    kShapes = 6
+};
+constexpr int kSegRows = 256;
 
-__host__ __device__ inline int shape_tx(int s) { return s == SHAPE_SWEEP ? 32 : s == SHAPE_SMALL ? 32 : 64 - 4 * s; }
-__host__ __device__ inline int shape_ty(int s) { return s == SHAPE_SWEEP ? 64 : s == SHAPE_SMALL ? 8 : 32 - 4 * s; }
+__host__ __device__ inline int shape_tx(int s)
+{
+    return (s == SHAPE_SWEEP || s == SHAPE_SMALL || s == SHAPE_SEG) ? 32 : 64 - 4 * s;
+}
+__host__ __device__ inline int shape_ty(int s)
+{
+    return s == SHAPE_SWEEP ? 64 : s == SHAPE_SMALL ? 8 : s == SHAPE_SEG ? kSegRows : 32 - 4 * s;
+}
 
 // Per-image pointers and sizes of one batch entry (planes laid out by the host).
 struct ImgDesc {
@@ -173,6 +190,9 @@ int launch_select_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, 
                         cudaStream_t st);
 int launch_tensor_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
                         cudaStream_t st);
+// nfield = N at each pixel's selected scale, one strip-walking launch per scale (fd4_tensor.cu).
+int launch_tensor_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
+                         cudaStream_t st);
 // n FED steps on every image; the result ends in ImgDesc::u.  steps_per_launch:
 // 1 = one launch per step (k_fed_step), 2..4 = k_fed_fused<S>.
 int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundary, int steps_per_launch,

@@ -15,6 +15,7 @@
 // selected scale, and for each scale the row pass covers only the rows and
 // 8-column chunks those pixels reach, the column pass only those pixels.
 #include <cstdint>
+#include <cstdlib>
 
 #include "fd4_internal.h"
 
@@ -576,7 +577,14 @@ int launch_select_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, 
 int launch_tensor_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
                         cudaStream_t st)
 {
-    if (sweep_launch(B, h_sigmas, n_sigma, p, true, st)) return 1;
+    // N at the selected scales: the per-scale strip kernels (fd4_tensor.cu),
+    // or with FD4_TENSOR_SWEEP=1 the multi-scale tile sweep (same result).
+    const char *e = getenv("FD4_TENSOR_SWEEP");
+    if (e && e[0] == '1') {
+        if (sweep_launch(B, h_sigmas, n_sigma, p, true, st)) return 1;
+    } else if (launch_tensor_strips(B, h_sigmas, n_sigma, p, st)) {
+        return 1;
+    }
     RhoTaps rt;
     if (rho_taps(p.rho, &rt) != FD4_OK) return 1;
     Imgs I = B.I;

@@ -1,0 +1,357 @@
+// Derivatives of u_sigma at each pixel's selected scale for the tensor build
+// (Sec. 3.3 Eq. 9: N = H(u_sigma*) / sqrt(1 + |grad u_sigma*|), the normalised
+// Hessian before its G_rho smoothing).
+//
+// One launch per scale of the set.  A block takes a strip segment (32 columns
+// x 256 rows of one image) and walks it top to bottom in chunks of 32 rows.
+// For every chunk it computes the separable row pass (smoothing, first- and
+// second-derivative taps along x) of the 32 new rows into a rolling buffer
+// that keeps the 2R rows shared with the previous chunk, so the row pass costs
+// 3 (2R+1) FMAs per pixel plus 2R/256 halo rows per segment instead of a full
+// halo per tile.  The column pass then runs only at the chunk's pixels whose
+// selected scale is this one.  The radius R is a template parameter: every tap
+// loop is unrolled and the weights are kernel parameters (constant-bank
+// operands of the FMAs).  The arithmetic and summation order are those of the
+// multi-scale sweep in fd4_scale.cu, so both give identical results.
+#include <cstdint>
+#include <cstdlib>
+
+#include "fd4_internal.h"
+
+namespace fd4 {
+namespace {
+
+constexpr int ST_TX = 32;    // strip width
+constexpr int ST_CH = 32;    // rows per chunk
+constexpr int ST_NT = 256;   // threads: row pass = 32 rows x 8 units of 4 outputs
+constexpr int ST_RS = 36;    // row-pass buffer stride (16-byte rows)
+
+template <int R>
+struct StripTaps {
+    float w0[2 * R + 1], w1[2 * R + 1], w2[2 * R + 1];  // tap i at offset i - R
+};
+
+__device__ __forceinline__ int st_mirror(int i, int n)
+{
+    if ((unsigned)i < (unsigned)n) return i;
+    const int p = 2 * n;
+    int m = i % p;
+    if (m < 0) m += p;
+    return m < n ? m : p - 1 - m;
+}
+
+__device__ __forceinline__ void st_cp16(float *dst, const float *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void st_cp4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void st_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void st_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void st_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int R>
+constexpr int st_sw() { return 36 + 2 * R; }  // staged input row stride: >= 32 + 2R, == 4 mod 8
+
+template <int R>
+constexpr size_t st_smem_bytes()
+{
+    return sizeof(float) * ((size_t)2 * ST_CH * st_sw<R>() + (size_t)3 * (ST_CH + 2 * R) * ST_RS);
+}
+
+// A segment is walked as a sequence of pieces, each the row pass of up to
+// ST_CH rows: pieces 0 .. NP0 - 1 fill the buffer for the first chunk (rows
+// ys - R .. ys + ST_CH - 1 + R), piece NP0 - 1 + c (c >= 1) adds the ST_CH new
+// rows of chunk c after the buffer keeps the 2R rows it shares with chunk c - 1.
+template <int R>
+struct Piece {
+    static constexpr int NB = ST_CH + 2 * R, NP0 = (NB + ST_CH - 1) / ST_CH;
+    int ya, b0, n, chunk;  // first image row, first buffer row, rows, chunk it belongs to
+    bool last;             // completes its chunk's buffer
+    __device__ __forceinline__ Piece(int ys, int i)
+    {
+        if (i < NP0) {
+            ya = ys - R + ST_CH * i;
+            b0 = ST_CH * i;
+            n = min(ST_CH, NB - ST_CH * i);
+            chunk = 0;
+            last = i == NP0 - 1;
+        } else {
+            chunk = i - NP0 + 1;
+            ya = ys + ST_CH * chunk + R;
+            b0 = 2 * R;
+            n = ST_CH;
+            last = true;
+        }
+    }
+};
+
+// cp.async of image rows ya .. ya + n - 1 (mirrored), columns x0 - R .. x0 + 31 + R.
+template <int R>
+__device__ __forceinline__ void st_stage(float *tin, const float *img, int w, int h, int pitch, int x0, int ya,
+                                         int n)
+{
+    constexpr int SW = st_sw<R>(), NC = 32 + 2 * R;
+    const int tid = threadIdx.x;
+    if (x0 - R >= 0 && x0 + 32 + R <= w) {  // 16-byte chunks: x0 - R and the pitch are multiples of 4
+        for (int i = tid; i < n * (NC / 4); i += ST_NT) {
+            const int r = i / (NC / 4), c = (i - r * (NC / 4)) * 4;
+            st_cp16(tin + r * SW + c, img + (size_t)st_mirror(ya + r, h) * pitch + x0 - R + c);
+        }
+    } else {
+        for (int i = tid; i < n * NC; i += ST_NT) {
+            const int r = i / NC, c = i - r * NC;
+            st_cp4(tin + r * SW + c, img + (size_t)st_mirror(ya + r, h) * pitch + st_mirror(x0 - R + c, w));
+        }
+    }
+}
+
+// Row pass of staged rows 0 .. n - 1 into buffer rows b0 .. b0 + n - 1: thread
+// (row tid / 8, columns 4 (tid % 8) .. + 3), three fields.
+template <int R>
+__device__ __forceinline__ void st_rows(const StripTaps<R> &tp, const float *tin, float *trow, int b0, int n)
+{
+    constexpr int SW = st_sw<R>(), NB = ST_CH + 2 * R;
+    const int tid = threadIdx.x;
+    const int r = tid >> 3, xo = (tid & 7) * 4;
+    if (r < n) {
+        const float *src = tin + r * SW + xo;
+        float a0[4], a1[4], a2[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a0[j] = a1[j] = a2[j] = 0.0f;
+#pragma unroll
+        for (int m4 = 0; m4 < (2 * R + 4 + 3) / 4; ++m4) {
+            const float4 v = *reinterpret_cast<const float4 *>(src + 4 * m4);
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int i = 4 * m4 + e - j;  // tap index of output j
+                    if (i >= 0 && i <= 2 * R) {
+                        a0[j] = fmaf(tp.w0[i], vv[e], a0[j]);
+                        a1[j] = fmaf(tp.w1[i], vv[e], a1[j]);
+                        a2[j] = fmaf(tp.w2[i], vv[e], a2[j]);
+                    }
+                }
+            }
+        }
+        float *d = trow + (b0 + r) * ST_RS + xo;
+        *reinterpret_cast<float4 *>(d) = make_float4(a0[0], a0[1], a0[2], a0[3]);
+        *reinterpret_cast<float4 *>(d + NB * ST_RS) = make_float4(a1[0], a1[1], a1[2], a1[3]);
+        *reinterpret_cast<float4 *>(d + 2 * NB * ST_RS) = make_float4(a2[0], a2[1], a2[2], a2[3]);
+    }
+}
+
+// Scale s (radius R) over every strip segment of the batch.  idx: selected
+// scale per pixel; only pixels with idx == s are written (nfield).  The s == 0
+// launch also zeroes N where idx lies outside the scale set (K_total).  The
+// next piece's rows (of this segment or of the block's next one) are copied
+// with cp.async while the current piece is computed.
+template <int R>
+__global__ void __launch_bounds__(ST_NT) k_tensor_strip(Imgs I, StripTaps<R> tp, int s, int K_total, int grad_sq)
+{
+    constexpr int NB = ST_CH + 2 * R, SW = st_sw<R>(), NP0 = Piece<R>::NP0;
+    extern __shared__ __align__(16) float stsm[];
+    float *trow = stsm + 2 * ST_CH * SW;  // 3 fields x NB rows x ST_RS; staged rows: two ST_CH x SW buffers
+    __shared__ unsigned short plist[ST_TX * ST_CH];
+    __shared__ int wtot[ST_NT / 32 + 1];
+    __shared__ ImgDesc sd[2];
+    __shared__ int s_local[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x;
+    int t = blockIdx.x;
+    if (t >= I.tiles) return;
+    if (tid == 0) find_tile(I, SHAPE_SEG, t, sd[0], s_local[0]);
+    __syncthreads();
+    int cur = 0, i = 0, buf = 0;
+    {
+        const int tx = (sd[0].w + ST_TX - 1) / ST_TX;
+        const Piece<R> p0((s_local[0] / tx) * kSegRows, 0);
+        st_stage<R>(stsm, sd[0].u, sd[0].w, sd[0].h, sd[0].pitch, (s_local[0] % tx) * ST_TX, p0.ya, p0.n);
+        st_commit();
+    }
+    for (;;) {
+        const int w = sd[cur].w, h = sd[cur].h, pitch = sd[cur].pitch;
+        const int tiles_x = (w + ST_TX - 1) / ST_TX;
+        const int x0 = (s_local[cur] % tiles_x) * ST_TX, ys = (s_local[cur] / tiles_x) * kSegRows;
+        const int nch = (min(ys + kSegRows, h) - ys + ST_CH - 1) / ST_CH;
+        const int P = NP0 + nch - 1;
+        const Piece<R> pc(ys, i);
+        // issue the next piece into the other staging buffer
+        float *nbuf = stsm + (buf ^ 1) * ST_CH * SW;
+        if (i + 1 < P) {
+            const Piece<R> pn(ys, i + 1);
+            st_stage<R>(nbuf, sd[cur].u, w, h, pitch, x0, pn.ya, pn.n);
+        } else if (t + G < I.tiles) {
+            const ImgDesc &dn = sd[cur ^ 1];  // looked up at piece 0, published by its barriers (P >= 2)
+            const int txn = (dn.w + ST_TX - 1) / ST_TX;
+            const Piece<R> pn((s_local[cur ^ 1] / txn) * kSegRows, 0);
+            st_stage<R>(nbuf, dn.u, dn.w, dn.h, dn.pitch, (s_local[cur ^ 1] % txn) * ST_TX, pn.ya, pn.n);
+        }
+        st_commit();
+        // the selected scales of the chunk this piece completes (rows 4 warp .. + 3)
+        const int y0 = ys + ST_CH * pc.chunk;
+        int ids[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gx = x0 + lane, gy = y0 + warp * 4 + j;
+            ids[j] = (pc.last && gx < w && gy < h) ? (int)sd[cur].idx[(size_t)gy * pitch + gx] : -1;
+        }
+        st_wait1();
+        __syncthreads();  // this piece's rows have landed; the previous chunk's column pass is done
+        // the block's next segment: its slot held the previous segment, whose last
+        // readers (the column pass above) are past this barrier
+        if (i == 0 && tid == 0 && t + G < I.tiles) find_tile(I, SHAPE_SEG, t + G, sd[cur ^ 1], s_local[cur ^ 1]);
+        if (i >= NP0) {
+            // keep buffer rows ST_CH .. ST_CH + 2R - 1 as rows 0 .. 2R - 1, in
+            // pieces that never overlap their own source
+            for (int k0 = 0; k0 < 2 * R; k0 += ST_CH) {
+                const int n = min(ST_CH, 2 * R - k0);
+                for (int q = tid; q < 3 * n * (ST_TX / 4); q += ST_NT) {
+                    const int f = q / (n * (ST_TX / 4)), rem = q - f * n * (ST_TX / 4);
+                    const int r = rem / (ST_TX / 4), c = (rem - r * (ST_TX / 4)) * 4;
+                    float *fb = trow + f * NB * ST_RS;
+                    *reinterpret_cast<float4 *>(fb + (k0 + r) * ST_RS + c) =
+                        *reinterpret_cast<const float4 *>(fb + (ST_CH + k0 + r) * ST_RS + c);
+                }
+                __syncthreads();
+            }
+        }
+        st_rows<R>(tp, stsm + buf * ST_CH * SW, trow, pc.b0, pc.n);
+        __syncthreads();
+
+        if (pc.last) {
+            // the chunk's pixels of this scale, grouped in plist
+            unsigned m[4];
+            int cnt = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (s == 0 && ids[j] >= K_total)
+                    sd[cur].nfield[(size_t)(y0 + warp * 4 + j) * pitch + x0 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+                m[j] = __ballot_sync(0xffffffffu, ids[j] == s);
+                cnt += __popc(m[j]);
+            }
+            if (lane == 0) wtot[warp] = cnt;
+            __syncthreads();
+            if (tid == 0) {
+                int acc = 0;
+                for (int k = 0; k < ST_NT / 32; ++k) {
+                    const int c = wtot[k];
+                    wtot[k] = acc;
+                    acc += c;
+                }
+                wtot[ST_NT / 32] = acc;
+            }
+            __syncthreads();
+            {
+                int pos = wtot[warp];
+                const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if ((m[j] >> lane) & 1u) plist[pos + __popc(m[j] & lt)] = (unsigned short)(((warp * 4 + j) << 5) | lane);
+                    pos += __popc(m[j]);
+                }
+            }
+            __syncthreads();
+            // column pass: output row y0 + py reads buffer rows py .. py + 2R
+            const int total = wtot[ST_NT / 32];
+            for (int e = tid; e < total; e += ST_NT) {
+                const int entry = plist[e];
+                const int px = entry & 31, py = entry >> 5;
+                const float *c0 = trow + py * ST_RS + px;   // smoothed along x
+                const float *c1 = c0 + NB * ST_RS;           // d/dx
+                const float *c2 = c1 + NB * ST_RS;           // d2/dx2
+                float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
+#pragma unroll
+                for (int k = 0; k <= 2 * R; ++k) {
+                    const float v0 = c0[k * ST_RS], v1 = c1[k * ST_RS], v2 = c2[k * ST_RS];
+                    sy = fmaf(tp.w1[k], v0, sy);
+                    syy = fmaf(tp.w2[k], v0, syy);
+                    sx = fmaf(tp.w0[k], v1, sx);
+                    sxy = fmaf(tp.w1[k], v1, sxy);
+                    sxx = fmaf(tp.w0[k], v2, sxx);
+                }
+                const float g2 = fmaf(sx, sx, sy * sy);
+                const float g = grad_sq ? g2 : sqrtf(g2);
+                const float f = 1.0f / sqrtf(1.0f + g);
+                sd[cur].nfield[(size_t)(y0 + py) * pitch + x0 + px] = make_float4(f * sxx, f * sxy, f * syy, 0.0f);
+            }
+        }
+        buf ^= 1;
+        if (++i == P) {
+            i = 0;
+            t += G;
+            cur ^= 1;
+            if (t >= I.tiles) break;
+        }
+    }
+    st_wait0();
+}
+
+template <int R>
+int launch_strip_scale(const HostBatch &B, const GaussTaps &g, int s, int K_total, int grad_sq, cudaStream_t st)
+{
+    static int attr_dev = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    constexpr size_t smem = st_smem_bytes<R>();
+    if (attr_dev != dev) {
+        if (cudaFuncSetAttribute(k_tensor_strip<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return 1;
+        attr_dev = dev;
+    }
+    StripTaps<R> tp;
+    const float *src[3] = {g.w0, g.w1, g.w2};
+    float *dst[3] = {tp.w0, tp.w1, tp.w2};
+    for (int k = 0; k < 3; ++k)
+        for (int i = 0; i <= 2 * R; ++i) {
+            const int o = i - R;
+            dst[k][i] = (o >= -g.r && o <= g.r) ? src[k][o + g.r] : 0.0f;
+        }
+    Imgs I = B.I;
+    I.tiles = B.tiles[SHAPE_SEG];
+    const int grid = persistent_grid((const void *)k_tensor_strip<R>, ST_NT, smem, I.tiles);
+    k_tensor_strip<R><<<grid, ST_NT, smem, st>>>(I, tp, s, K_total, grad_sq);
+    return cudaGetLastError() != cudaSuccess;
+}
+
+}  // namespace
+
+// N at each pixel's selected scale for every image of the batch (nfield).
+int launch_tensor_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
+                         cudaStream_t st)
+{
+    for (int s = 0; s < n_sigma; ++s) {
+        GaussTaps g;
+        if (gauss_taps(h_sigmas[s], &g) != FD4_OK) return 1;
+        const int R = (g.r + 3) / 4 * 4;
+        int rc = 1;
+        switch (R) {
+        case 4: rc = launch_strip_scale<4>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
+        case 8: rc = launch_strip_scale<8>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
+        case 12: rc = launch_strip_scale<12>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
+        case 16: rc = launch_strip_scale<16>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
+        case 20: rc = launch_strip_scale<20>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
+        case 24: rc = launch_strip_scale<24>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
+        case 28: rc = launch_strip_scale<28>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
+        case 32: rc = launch_strip_scale<32>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
+        case 36: rc = launch_strip_scale<36>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
+        case 40: rc = launch_strip_scale<40>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
+        case 44: rc = launch_strip_scale<44>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
+        case 48: rc = launch_strip_scale<48>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
+        default: rc = 1;
+        }
+        if (rc) return 1;
+    }
+    return 0;
+}
+
+}  // namespace fd4

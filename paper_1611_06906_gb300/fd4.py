@@ -75,6 +75,7 @@ SIGNATURES = {
                               ctypes.POINTER(ctypes.c_void_p)]),
     "fd4_graph_launch": (_i, [_vp, _vp]),
     "fd4_graph_destroy": (_i, [_vp]),
+    "fd4_graph_kernel_count": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "fd4_autotune_batched": (_i, [_vp, _i, _fp, _i, _pp, ctypes.c_double, _i, _i, _vp, _sz, _vp, _ip,
                                   _fp]),
 }
@@ -326,6 +327,12 @@ class Graph:
 
     def launch(self, stream=None):
         _check(lib().fd4_graph_launch(self.handle, _stream(stream)), "fd4_graph_launch")
+
+    def kernel_count(self) -> int:
+        """fd4_graph_kernel_count: kernel launches per launch()."""
+        n = ctypes.c_int(0)
+        _check(lib().fd4_graph_kernel_count(self.handle, ctypes.byref(n)), "fd4_graph_kernel_count")
+        return n.value
 
     def close(self):
         if self.handle:
