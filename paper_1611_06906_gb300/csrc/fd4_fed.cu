@@ -569,6 +569,8 @@ __device__ __forceinline__ float4 quad_steps(float *su, float *sxy, float *syy, 
     return uo;
 }
 
+// cp.async of a tile's region into the staging buffers: consecutive threads
+// copy consecutive 16-byte chunks (one u chunk and four tensor pixels each).
 template <int S>
 __device__ __forceinline__ void quad_prefetch(const ImgDesc &d, int local, float *u_dst, float4 *t_dst, int parity)
 {
@@ -579,7 +581,7 @@ __device__ __forceinline__ void quad_prefetch(const ImgDesc &d, int local, float
     const int gx0 = (local % tiles_x) * TXo - H, gy0 = (local / tiles_x) * TYo - H;
     const float *uin = parity ? d.tmp : d.u;
     {
-        const int ry = tid >> 4, cx = (tid & 15) * 4;  // one 16-byte chunk per thread
+        const int ry = tid >> 4, cx = (tid & 15) * 4;
         const int gy = gy0 + ry, gx = gx0 + cx;
         // a chunk of 4 columns starting inside the image stays inside the row pitch
         const bool valid = gy >= 0 && gy < h && gx >= 0 && gx < w;
@@ -640,6 +642,15 @@ __global__ void __launch_bounds__(QNT, 2) k_fed_quad(Imgs I, StepTaus taus, int 
         float *su = qsm + cur * QPLANE;
         const float4 u0 = *reinterpret_cast<const float4 *>(su + off);
         unsigned mask = 0u;
+        if (!interior) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int x = gx + i;
+                mask |= (x >= 0 && x < w && gy >= 0 && gy < h ? 1u : 0u) << i;
+                mask |= (x >= 1 && x <= w - 2 ? 1u : 0u) << (4 + i);
+            }
+            mask |= (gy >= 1 && gy <= h - 2 ? 1u : 0u) << 8;
+        }
         QuadCoef k;
         {
             float cc[4], ss[4], pp[4], qq[4];
@@ -650,11 +661,7 @@ __global__ void __launch_bounds__(QNT, 2) k_fed_quad(Imgs I, StepTaus taus, int 
                 ss[i] = tt.y;
                 pp[i] = 0.5f * (tt.z + tt.w);
                 qq[i] = 0.5f * (tt.z - tt.w);
-                const int x = gx + i;
-                mask |= (x >= 0 && x < w && gy >= 0 && gy < h ? 1u : 0u) << i;
-                mask |= (x >= 1 && x <= w - 2 ? 1u : 0u) << (4 + i);
             }
-            mask |= (gy >= 1 && gy <= h - 2 ? 1u : 0u) << 8;
             k.c = make_float4(cc[0], cc[1], cc[2], cc[3]);
             k.s = make_float4(ss[0], ss[1], ss[2], ss[3]);
             k.p = make_float4(pp[0], pp[1], pp[2], pp[3]);

@@ -201,6 +201,7 @@ int launch_select_tiles(const ImgDesc &d, const int *list, const int *count, con
                         const fd4_params &p, cudaStream_t st);
 // Sets the shared-memory attributes of every kernel (call before stream capture).
 int prepare_scale_kernels();
+int prepare_tensor_kernels();
 int prepare_fed_kernels();
 int default_steps_per_launch();
 int launch_copy_in_batch(const HostBatch &B, cudaStream_t st);

@@ -409,79 +409,119 @@ __device__ __forceinline__ float pm_mu(float nu, float lambda, int mode)
     return 1.0f / fmaf(q, q, 1.0f);
 }
 
-constexpr int FX = 32, FY = 8;   // tensor-finish tile (SHAPE_SMALL)
+// Tensor finish on 32 x 64 tiles (SHAPE_SWEEP), 256 threads: N_rho = G_rho * N
+// (mirror border; row pass then column pass, taps in increasing order), the
+// closed-form eigen-decomposition of N_rho and the Perona-Malik diffusivities
+// -> (cos 2t, sin 2t, mu1, mu2), e1 for nu1 >= nu2.  The G_rho radius r is a
+// template parameter (r = ceil(4 rho) <= 8).
+constexpr int FX = 32, FY = 64, FNT_T = 256;
 
-// N_rho = G_rho * N (mirror border), closed-form eigen-decomposition and
-// Perona-Malik diffusivities -> (cos 2t, sin 2t, mu1, mu2), e1 for nu1 >= nu2.
-__global__ void __launch_bounds__(FX * FY) k_tensor_finish(Imgs I, RhoTaps taps, float lambda, int mode)
+template <int r>
+constexpr size_t finish_smem_bytes()
 {
-    __shared__ float4 sin_[FY + 2 * kMaxRhoRadius][FX + 2 * kMaxRhoRadius];
-    __shared__ float4 srow[FY + 2 * kMaxRhoRadius][FX];
-    __shared__ float wr[2 * kMaxRhoRadius + 1];
+    return sizeof(float4) * ((size_t)(FY + 2 * r) * (FX + 2 * r) + (size_t)(FY + 2 * r) * FX);
+}
+
+template <int r>
+__global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, float lambda, int mode)
+{
+    constexpr int ROWS = FY + 2 * r, COLS = FX + 2 * r;
+    extern __shared__ __align__(16) float4 fsm4[];
+    float4 *sin_ = fsm4;                 // ROWS x COLS: N with the mirrored halo
+    float4 *srow = fsm4 + ROWS * COLS;   // ROWS x FX: smoothed along x
     __shared__ ImgDesc sd;
     __shared__ int s_local;
-    const int r = taps.r;
     const int tid = threadIdx.x;
-    if (tid <= 2 * r) wr[tid] = taps.w0[tid];
-    const int rows = FY + 2 * r, cols = FX + 2 * r;
-    for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
+    float wr[2 * r + 1];
+#pragma unroll
+    for (int k = 0; k <= 2 * r; ++k) wr[k] = taps.w0[k];
+    const int ntiles = tile_count(I, SHAPE_SWEEP);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         __syncthreads();
-        if (tid == 0) find_tile(I, SHAPE_SMALL, t, sd, s_local);
+        if (tid == 0) find_tile(I, SHAPE_SWEEP, t, sd, s_local);
         __syncthreads();
         const int w = sd.w, h = sd.h, pitch = sd.pitch;
         const int tiles_x = (w + FX - 1) / FX;
         const int x0 = (s_local % tiles_x) * FX, y0 = (s_local / tiles_x) * FY;
         const float4 *nf = sd.nfield;
-        for (int i = tid; i < rows * cols; i += FX * FY) {
-            const int ry = i / cols, rx = i - ry * cols;
-            sin_[ry][rx] = nf[(size_t)mirror(y0 - r + ry, h) * pitch + mirror(x0 - r + rx, w)];
+        for (int i = tid; i < ROWS * COLS; i += FNT_T) {
+            const int ry = i / COLS, rx = i - ry * COLS;
+            sin_[i] = nf[(size_t)mirror(y0 - r + ry, h) * pitch + mirror(x0 - r + rx, w)];
         }
         __syncthreads();
-        for (int i = tid; i < rows * FX; i += FX * FY) {
+        for (int i = tid; i < ROWS * FX; i += FNT_T) {
             const int ry = i / FX, rx = i - ry * FX;
             float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
             for (int k = 0; k <= 2 * r; ++k) {
-                const float c = wr[k];
-                const float4 v = sin_[ry][rx + k];
-                a.x = fmaf(c, v.x, a.x);
-                a.y = fmaf(c, v.y, a.y);
-                a.z = fmaf(c, v.z, a.z);
+                const float4 v = sin_[ry * COLS + rx + k];
+                a.x = fmaf(wr[k], v.x, a.x);
+                a.y = fmaf(wr[k], v.y, a.y);
+                a.z = fmaf(wr[k], v.z, a.z);
             }
-            srow[ry][rx] = a;
+            srow[i] = a;
         }
         __syncthreads();
-        const int tx = tid & (FX - 1), ty = tid / FX;
-        const int gx = x0 + tx, gy = y0 + ty;
-        if (gx >= w || gy >= h) continue;
-        float a = 0.f, b = 0.f, d = 0.f;
-        for (int k = 0; k <= 2 * r; ++k) {
-            const float c = wr[k];
-            const float4 v = srow[ty + k][tx];
-            a = fmaf(c, v.x, a);
-            b = fmaf(c, v.y, b);
-            d = fmaf(c, v.z, d);
+        // column pass: thread = column tid % 32, rows 8 (tid / 32) .. + 7
+        const int tx = tid & (FX - 1), ty0 = (tid >> 5) * 8;
+        const int gx = x0 + tx;
+        float4 win[8 + 2 * r];
+#pragma unroll
+        for (int q = 0; q < 8 + 2 * r; ++q) win[q] = srow[(ty0 + q) * FX + tx];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int gy = y0 + ty0 + j;
+            float a = 0.f, b = 0.f, d = 0.f;
+#pragma unroll
+            for (int k = 0; k <= 2 * r; ++k) {
+                a = fmaf(wr[k], win[j + k].x, a);
+                b = fmaf(wr[k], win[j + k].y, b);
+                d = fmaf(wr[k], win[j + k].z, d);
+            }
+            if (gx >= w || gy >= h) continue;
+            const float m = 0.5f * (a + d), q = 0.5f * (a - d);
+            const float rr = hypotf(q, b);
+            const float det = det2_sym(a, b, d);
+            float nu1, nu2;
+            if (m > 0.0f) {
+                nu1 = m + rr;
+                nu2 = det / nu1;
+            } else if (m < 0.0f) {
+                nu2 = m - rr;
+                nu1 = det / nu2;
+            } else {
+                nu1 = rr;
+                nu2 = -rr;
+            }
+            float c2 = 1.0f, s2 = 0.0f;
+            if (rr > 0.0f) {
+                c2 = q / rr;
+                s2 = b / rr;
+            }
+            sd.tensor[(size_t)gy * pitch + gx] =
+                make_float4(c2, s2, pm_mu(nu1, lambda, mode), pm_mu(nu2, lambda, mode));
         }
-        const float m = 0.5f * (a + d), q = 0.5f * (a - d);
-        const float rr = hypotf(q, b);
-        const float det = det2_sym(a, b, d);
-        float nu1, nu2;
-        if (m > 0.0f) {
-            nu1 = m + rr;
-            nu2 = det / nu1;
-        } else if (m < 0.0f) {
-            nu2 = m - rr;
-            nu1 = det / nu2;
-        } else {
-            nu1 = rr;
-            nu2 = -rr;
-        }
-        float c2 = 1.0f, s2 = 0.0f;
-        if (rr > 0.0f) {
-            c2 = q / rr;
-            s2 = b / rr;
-        }
-        sd.tensor[(size_t)gy * pitch + gx] = make_float4(c2, s2, pm_mu(nu1, lambda, mode), pm_mu(nu2, lambda, mode));
     }
+}
+
+template <int r>
+int launch_finish(const HostBatch &B, const RhoTaps &rt, const fd4_params &p, cudaStream_t st)
+{
+    static int attr_dev = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    constexpr size_t smem = finish_smem_bytes<r>();
+    if (attr_dev != dev) {
+        if (cudaFuncSetAttribute(k_tensor_finish<r>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return 1;
+        attr_dev = dev;
+    }
+    Imgs I = B.I;
+    I.tiles = B.tiles[SHAPE_SWEEP];
+    const int grid = persistent_grid((const void *)k_tensor_finish<r>, FNT_T, smem, I.tiles);
+    k_tensor_finish<r><<<grid, FNT_T, smem, st>>>(I, rt, p.lambda, p.mode);
+    return 0;
 }
 
 // Opts the sweep kernel into the dynamic shared memory a launch needs.
@@ -537,7 +577,19 @@ int pack_taps(const float *h_sigmas, int n_sigma, int s0, int K, double gamma, S
 
 }  // namespace
 
-int prepare_scale_kernels() { return set_sweep_smem(sweep_smem_bytes(kMaxRadius, kSweepFloats)); }
+template <int r>
+static int set_finish_smem()
+{
+    return cudaFuncSetAttribute(k_tensor_finish<r>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)finish_smem_bytes<r>()) != cudaSuccess;
+}
+
+int prepare_scale_kernels()
+{
+    return set_sweep_smem(sweep_smem_bytes(kMaxRadius, kSweepFloats)) || set_finish_smem<1>() ||
+           set_finish_smem<2>() || set_finish_smem<3>() || set_finish_smem<4>() || set_finish_smem<5>() ||
+           set_finish_smem<6>() || set_finish_smem<7>() || set_finish_smem<8>() || prepare_tensor_kernels();
+}
 
 static int sweep_launch(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p, bool tensor,
                         cudaStream_t st)
@@ -587,11 +639,19 @@ int launch_tensor_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, 
     }
     RhoTaps rt;
     if (rho_taps(p.rho, &rt) != FD4_OK) return 1;
-    Imgs I = B.I;
-    I.tiles = B.tiles[SHAPE_SMALL];
-    const int grid = persistent_grid((const void *)k_tensor_finish, FX * FY, 0, I.tiles);
-    k_tensor_finish<<<grid, FX * FY, 0, st>>>(I, rt, p.lambda, p.mode);
-    return cudaGetLastError() != cudaSuccess;
+    int rc = 1;
+    switch (rt.r) {
+    case 1: rc = launch_finish<1>(B, rt, p, st); break;
+    case 2: rc = launch_finish<2>(B, rt, p, st); break;
+    case 3: rc = launch_finish<3>(B, rt, p, st); break;
+    case 4: rc = launch_finish<4>(B, rt, p, st); break;
+    case 5: rc = launch_finish<5>(B, rt, p, st); break;
+    case 6: rc = launch_finish<6>(B, rt, p, st); break;
+    case 7: rc = launch_finish<7>(B, rt, p, st); break;
+    case 8: rc = launch_finish<8>(B, rt, p, st); break;
+    default: rc = 1;
+    }
+    return rc || cudaGetLastError() != cudaSuccess;
 }
 
 // Plain selection on a subset of the 32 x 64 sweep tiles of one image (device

@@ -323,7 +323,21 @@ int launch_strip_scale(const HostBatch &B, const GaussTaps &g, int s, int K_tota
     return cudaGetLastError() != cudaSuccess;
 }
 
+template <int R>
+int set_strip_smem()
+{
+    return cudaFuncSetAttribute(k_tensor_strip<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)st_smem_bytes<R>()) != cudaSuccess;
+}
+
 }  // namespace
+
+int prepare_tensor_kernels()
+{
+    return set_strip_smem<4>() || set_strip_smem<8>() || set_strip_smem<12>() || set_strip_smem<16>() ||
+           set_strip_smem<20>() || set_strip_smem<24>() || set_strip_smem<28>() || set_strip_smem<32>() ||
+           set_strip_smem<36>() || set_strip_smem<40>() || set_strip_smem<44>() || set_strip_smem<48>();
+}
 
 // N at each pixel's selected scale for every image of the batch (nfield).
 int launch_tensor_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
