@@ -441,9 +441,10 @@ __global__ void __launch_bounds__(FNT, 2) k_fed_fused_pipe(Imgs I, StepTaus taus
 }
 
 // ---------------------------------------------------------------------------
-// Quad variant (natural boundary, S = 2 or 4), the default.  Same 64 x 32
-// region, cp.async staging of the next tile and S steps per launch, but each
-// of the 512 threads owns a row quad (4 adjacent pixels of one row) and keeps
+// Quad variant (natural boundary, S = 2 or 4), the default.  A 64 x 64 region
+// (or 64 x 32), cp.async staging of the next tile and S steps per launch as in
+// the kernels above, but each thread owns a row quad (4 adjacent pixels of one
+// row; 16 quads per region row, one thread per quad) and keeps
 // its u, its T_xx and its tensor values in registers; horizontal neighbours
 // come from the adjacent lanes by shuffles, vertical ones from 16-byte shared
 // loads of the rows above and below (u, T_xy and T_yy planes only).  T and u
@@ -454,14 +455,22 @@ __global__ void __launch_bounds__(FNT, 2) k_fed_fused_pipe(Imgs I, StepTaus taus
 // kept per pixel as (cos 2t, sin 2t, (mu1 + mu2) / 2, (mu1 - mu2) / 2), with
 // which T = D : H costs about 26 flops.
 
-constexpr int QNT = 512;                          // threads: 16 quads across x 32 rows
 constexpr int QPAD = 4;                           // ring columns (keeps quads 16-byte aligned)
 constexpr int QSW = FRX + 2 * QPAD;               // 72 floats per plane row
-constexpr int QPLANE = (FRY + 2) * QSW;           // one ring row above and below
 constexpr int QTS = 5;                            // float4 slots per quad in the tensor buffer (1 pad:
                                                   // the 16-byte reads of 8 lanes hit distinct banks)
-constexpr int QTBUF = FRY * (FRX / 4) * QTS;      // float4 entries
-constexpr size_t kQuadSmem = sizeof(float) * 4 * QPLANE + sizeof(float4) * QTBUF;  // 2 u, T_xy, T_yy, tensor
+// Region height RY = 32 (512 threads, two blocks per SM) or 64 (1024 threads,
+// one block per SM, a smaller halo share: (64 - 4S)^2 of 64^2 pixels exact).
+template <int RY>
+constexpr int q_nt() { return (FRX / 4) * RY; }   // threads: 16 quads across x RY rows
+template <int RY>
+constexpr int q_plane() { return (RY + 2) * QSW; }  // one ring row above and below
+template <int RY>
+constexpr int q_tbuf() { return RY * (FRX / 4) * QTS; }  // float4 entries
+template <int RY>
+constexpr size_t q_smem() { return sizeof(float) * 4 * q_plane<RY>() + sizeof(float4) * q_tbuf<RY>(); }
+template <int S, int RY>
+constexpr int q_shape() { return RY == 32 ? S : (S == 2 ? SHAPE_Q64_2 : SHAPE_Q64_4); }
 
 struct QuadCoef {
     float4 c, s, p, q;  // per pixel of the quad: cos 2t, sin 2t, mean and half difference of mu
@@ -571,10 +580,10 @@ __device__ __forceinline__ float4 quad_steps(float *su, float *sxy, float *syy, 
 
 // cp.async of a tile's region into the staging buffers: consecutive threads
 // copy consecutive 16-byte chunks (one u chunk and four tensor pixels each).
-template <int S>
+template <int S, int RY>
 __device__ __forceinline__ void quad_prefetch(const ImgDesc &d, int local, float *u_dst, float4 *t_dst, int parity)
 {
-    constexpr int H = 2 * S, TXo = FRX - 2 * H, TYo = FRY - 2 * H;
+    constexpr int H = 2 * S, TXo = FRX - 2 * H, TYo = RY - 2 * H, QNT = q_nt<RY>();
     const int tid = threadIdx.x;
     const int w = d.w, h = d.h, pitch = d.pitch;
     const int tiles_x = (w + TXo - 1) / TXo;
@@ -588,7 +597,7 @@ __device__ __forceinline__ void quad_prefetch(const ImgDesc &d, int local, float
         cp_async16(u_dst + (ry + 1) * QSW + QPAD + cx, valid ? uin + (size_t)gy * pitch + gx : uin, valid);
     }
 #pragma unroll
-    for (int j = 0; j < FRX * FRY / QNT; ++j) {
+    for (int j = 0; j < FRX * RY / QNT; ++j) {
         const int i = tid + j * QNT;
         const int ry = i / FRX, rx = i % FRX;
         const int gy = gy0 + ry, gx = gx0 + rx;
@@ -598,12 +607,13 @@ __device__ __forceinline__ void quad_prefetch(const ImgDesc &d, int local, float
     }
 }
 
-template <int S>
-__global__ void __launch_bounds__(QNT, 2) k_fed_quad(Imgs I, StepTaus taus, int parity)
+template <int S, int RY>
+__global__ void __launch_bounds__(q_nt<RY>(), RY == 32 ? 2 : 1) k_fed_quad(Imgs I, StepTaus taus, int parity)
 {
-    constexpr int H = 2 * S, TXo = FRX - 2 * H, TYo = FRY - 2 * H;
+    constexpr int H = 2 * S, TXo = FRX - 2 * H, TYo = RY - 2 * H;
+    constexpr int QNT = q_nt<RY>(), QPLANE = q_plane<RY>(), SHAPE = q_shape<S, RY>();
     static_assert(TXo % 4 == 0 && H % 4 == 0, "16-byte aligned region columns");
-    static_assert(QNT == (FRX / 4) * FRY, "one quad per thread");
+    
     extern __shared__ __align__(16) float qsm[];
     // planes: u buffer 0, u buffer 1, T_xy, T_yy (each with the zero ring), then the tensor
     float *sxy = qsm + 2 * QPLANE, *syy = qsm + 3 * QPLANE;
@@ -625,9 +635,9 @@ __global__ void __launch_bounds__(QNT, 2) k_fed_quad(Imgs I, StepTaus taus, int 
     int t = blockIdx.x;
     __syncthreads();
     if (t < ntiles) {
-        if (tid == 0) find_tile(I, S, t, sd[0], s_local[0]);
+        if (tid == 0) find_tile(I, SHAPE, t, sd[0], s_local[0]);
         __syncthreads();
-        quad_prefetch<S>(sd[0], s_local[0], qsm, tbuf, parity);
+        quad_prefetch<S, RY>(sd[0], s_local[0], qsm, tbuf, parity);
     }
     cp_async_commit();
     for (; t < ntiles; t += gridDim.x) {
@@ -637,7 +647,7 @@ __global__ void __launch_bounds__(QNT, 2) k_fed_quad(Imgs I, StepTaus taus, int 
         float *uout = parity ? sd[cur].u : sd[cur].tmp;
         const int tiles_x = (w + TXo - 1) / TXo;
         const int gx0 = (s_local[cur] % tiles_x) * TXo - H, gy0 = (s_local[cur] / tiles_x) * TYo - H;
-        const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + FRX <= w && gy0 + FRY <= h;
+        const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + FRX <= w && gy0 + RY <= h;
         const int gx = gx0 + 4 * q, gy = gy0 + ry;
         float *su = qsm + cur * QPLANE;
         const float4 u0 = *reinterpret_cast<const float4 *>(su + off);
@@ -668,9 +678,9 @@ __global__ void __launch_bounds__(QNT, 2) k_fed_quad(Imgs I, StepTaus taus, int 
             k.q = make_float4(qq[0], qq[1], qq[2], qq[3]);
         }
         const int tn = t + gridDim.x;
-        if (tid == 0 && tn < ntiles) find_tile(I, S, tn, sd[cur ^ 1], s_local[cur ^ 1]);
+        if (tid == 0 && tn < ntiles) find_tile(I, SHAPE, tn, sd[cur ^ 1], s_local[cur ^ 1]);
         __syncthreads();  // the tensor buffer is read; the next descriptor is ready
-        if (tn < ntiles) quad_prefetch<S>(sd[cur ^ 1], s_local[cur ^ 1], qsm + (cur ^ 1) * QPLANE, tbuf, parity);
+        if (tn < ntiles) quad_prefetch<S, RY>(sd[cur ^ 1], s_local[cur ^ 1], qsm + (cur ^ 1) * QPLANE, tbuf, parity);
         cp_async_commit();
 
         const float4 un = interior ? quad_steps<false>(su, sxy, syy, stau, taus.n, off, k, mask, u0)
@@ -721,15 +731,15 @@ static int set_pipe_smem()
     return 0;
 }
 
-template <int S>
+template <int S, int RY>
 static int set_quad_smem()
 {
     static int attr_dev = -1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
     if (attr_dev != dev) {
-        if (cudaFuncSetAttribute(k_fed_quad<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQuadSmem) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(k_fed_quad<S, RY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)q_smem<RY>()) != cudaSuccess)
             return 1;
         attr_dev = dev;
     }
@@ -739,18 +749,21 @@ static int set_quad_smem()
 int prepare_fed_kernels()
 {
     return set_fused_smem<2>() || set_fused_smem<3>() || set_fused_smem<4>() || set_pipe_smem<2>() ||
-           set_pipe_smem<4>() || set_quad_smem<2>() || set_quad_smem<4>();
+           set_pipe_smem<4>() || set_quad_smem<2, 32>() || set_quad_smem<4, 32>() || set_quad_smem<2, 64>() ||
+           set_quad_smem<4, 64>();
 }
 
-template <int S>
-static int launch_quad(Imgs I, const double *tau, int n, int parity, cudaStream_t st)
+template <int S, int RY>
+static int launch_quad(const HostBatch &B, const double *tau, int n, int parity, cudaStream_t st)
 {
-    if (set_quad_smem<S>()) return 1;
+    if (set_quad_smem<S, RY>()) return 1;
     StepTaus t{};
     t.n = n;
     for (int i = 0; i < n; ++i) t.t[i] = (float)tau[i];
-    const int grid = persistent_grid((const void *)k_fed_quad<S>, QNT, kQuadSmem, I.tiles);
-    k_fed_quad<S><<<grid, QNT, kQuadSmem, st>>>(I, t, parity);
+    Imgs I = B.I;
+    I.tiles = B.tiles[q_shape<S, RY>()];
+    const int grid = persistent_grid((const void *)k_fed_quad<S, RY>, q_nt<RY>(), q_smem<RY>(), I.tiles);
+    k_fed_quad<S, RY><<<grid, q_nt<RY>(), q_smem<RY>(), st>>>(I, t, parity);
     return 0;
 }
 
@@ -781,6 +794,14 @@ static int launch_fused(Imgs I, const double *tau, int n, int parity, int period
 // Kernel for S = 2 and 4 under the natural boundary, from FD4_FED_PIPELINE:
 // 0 = the plain fused kernel, 1 = its cp.async-pipelined form, unset or 2 =
 // the quad kernel.  S = 3 and the periodic boundary use the plain fused kernel.
+// Region height of the quad kernel: 64 (64 x 64 regions, the default) or
+// FD4_FED_QUAD_ROWS=32 (64 x 32 regions, two blocks per SM).
+static int quad_rows()
+{
+    const char *e = getenv("FD4_FED_QUAD_ROWS");
+    return (e && atoi(e) == 32) ? 32 : 64;
+}
+
 static int pipeline_kind()
 {
     const char *e = getenv("FD4_FED_PIPELINE");
@@ -811,8 +832,12 @@ int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundar
             const int k = n - i < S ? n - i : S;
             int rc;
             const int kind = periodic || S == 3 ? 0 : pipeline_kind();
-            if (kind == 2) rc = S == 2 ? launch_quad<2>(I, h_tau + i, k, parity, st)
-                                       : launch_quad<4>(I, h_tau + i, k, parity, st);
+            if (kind == 2 && quad_rows() == 64)
+                rc = S == 2 ? launch_quad<2, 64>(B, h_tau + i, k, parity, st)
+                            : launch_quad<4, 64>(B, h_tau + i, k, parity, st);
+            else if (kind == 2)
+                rc = S == 2 ? launch_quad<2, 32>(B, h_tau + i, k, parity, st)
+                            : launch_quad<4, 32>(B, h_tau + i, k, parity, st);
             else if (kind == 1) rc = S == 2 ? launch_pipe<2>(I, h_tau + i, k, parity, st)
                                             : launch_pipe<4>(I, h_tau + i, k, parity, st);
             else rc = S == 2 ? launch_fused<2>(I, h_tau + i, k, parity, periodic, st)

@@ -49,17 +49,27 @@ enum TileShape {
     SHAPE_FUSE3 = 3,
     SHAPE_FUSE4 = 4,
     SHAPE_SEG = 5,
-    kShapes = 6
+    SHAPE_Q64_2 = 6,   // quad FED kernel on 64 x 64 regions: (64 - 4S)^2 outputs, S = 2
+    SHAPE_Q64_4 = 7,   //   ... S = 4
+    kShapes = 8
 };
 constexpr int kSegRows = 256;
 
 __host__ __device__ inline int shape_tx(int s)
 {
-    return (s == SHAPE_SWEEP || s == SHAPE_SMALL || s == SHAPE_SEG) ? 32 : 64 - 4 * s;
+    if (s == SHAPE_SWEEP || s == SHAPE_SMALL || s == SHAPE_SEG) return 32;
+    if (s == SHAPE_Q64_2) return 56;
+    if (s == SHAPE_Q64_4) return 48;
+    return 64 - 4 * s;
 }
 __host__ __device__ inline int shape_ty(int s)
 {
-    return s == SHAPE_SWEEP ? 64 : s == SHAPE_SMALL ? 8 : s == SHAPE_SEG ? kSegRows : 32 - 4 * s;
+    if (s == SHAPE_SWEEP) return 64;
+    if (s == SHAPE_SMALL) return 8;
+    if (s == SHAPE_SEG) return kSegRows;
+    if (s == SHAPE_Q64_2) return 56;
+    if (s == SHAPE_Q64_4) return 48;
+    return 32 - 4 * s;
 }
 
 // Per-image pointers and sizes of one batch entry (planes laid out by the host).
