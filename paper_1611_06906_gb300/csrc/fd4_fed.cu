@@ -540,11 +540,16 @@ __device__ __forceinline__ void quad_T(const float (&a)[6], const float (&b)[6],
 }
 
 // S steps of one staged region; uo: this quad's u on entry, returned updated.
+// Two block barriers per step: T is complete before the update reads it, the
+// update is complete before the next T phase reads u.  The first T phase reads
+// the staged region (published by the tile's barrier); after the last update
+// no barrier is needed before the next tile's.
 template <bool BOUNDARY>
 __device__ __forceinline__ float4 quad_steps(float *su, float *sxy, float *syy, const float *stau, int nsteps,
                                              int off, const QuadCoef &k, unsigned mask, float4 uo)
 {
     for (int l = 0; l < nsteps; ++l) {
+        if (l > 0) __syncthreads();
         float a[6], b[6], c[6];
         quad_ext(*reinterpret_cast<const float4 *>(su + off - QSW), a);
         quad_ext(uo, b);
@@ -573,7 +578,6 @@ __device__ __forceinline__ float4 quad_steps(float *su, float *sxy, float *syy, 
         }
         uo = make_float4(r[0], r[1], r[2], r[3]);
         *reinterpret_cast<float4 *>(su + off) = uo;
-        __syncthreads();
     }
     return uo;
 }
@@ -642,7 +646,7 @@ __global__ void __launch_bounds__(q_nt<RY>(), RY == 32 ? 2 : 1) k_fed_quad(Imgs 
     cp_async_commit();
     for (; t < ntiles; t += gridDim.x) {
         cp_async_wait_all();
-        __syncthreads();  // this tile's u region and tensor values have landed
+        __syncthreads();  // this tile's u region and tensor values have landed; every warp is past the last tile
         const int w = sd[cur].w, h = sd[cur].h, pitch = sd[cur].pitch;
         float *uout = parity ? sd[cur].u : sd[cur].tmp;
         const int tiles_x = (w + TXo - 1) / TXo;
