@@ -147,6 +147,15 @@ __device__ __forceinline__ void find_tile(const Imgs &I, int shape, int t, ImgDe
     out = I.table[lo];
     local = t - out.t0[shape];
 }
+// a d - b^2 with Kahan's fma compensation (error analysed by Jeannerod,
+// Louvet and Muller, Math. Comp. 2013): accurate even under cancellation.
+__device__ __forceinline__ float det2_sym(float a, float b, float d)
+{
+    const float bb = b * b;
+    const float err = fmaf(-b, b, bb);
+    return fmaf(a, d, -bb) + err;
+}
+
 // Number of tiles a persistent kernel walks: the host count, or the device
 // count of a tile list (8 small tiles per listed sweep tile).
 __device__ __forceinline__ int tile_count(const Imgs &I, int shape)
@@ -202,6 +211,10 @@ int launch_tensor_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, 
                         cudaStream_t st);
 // nfield = N at each pixel's selected scale, one strip-walking launch per scale (fd4_tensor.cu).
 int launch_tensor_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
+                         cudaStream_t st);
+// Selection planes of every scale and each image's max S^2, one strip-walking
+// launch per scale (fd4_tensor.cu); B.max_s2 must be cleared first.
+int launch_select_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
                          cudaStream_t st);
 // n FED steps on every image; the result ends in ImgDesc::u.  steps_per_launch:
 // 1 = one launch per step (k_fed_step), 2..4 = k_fed_fused<S>.

@@ -77,15 +77,6 @@ __device__ __forceinline__ int mirror(int i, int n)
     return m < n ? m : p - 1 - m;
 }
 
-// a d - b^2 with Kahan's fma compensation (error analysed by Jeannerod,
-// Louvet and Muller, Math. Comp. 2013): accurate even under cancellation.
-__device__ __forceinline__ float det2_sym(float a, float b, float d)
-{
-    const float bb = b * b;
-    const float err = fmaf(-b, b, bb);
-    return fmaf(a, d, -bb) + err;
-}
-
 enum { OUT_SELECT = 0, OUT_TENSOR = 1 };
 
 // Column pass of one field over the 12-row register window: acc_a += wa * field
@@ -618,7 +609,14 @@ int launch_select_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, 
                         cudaStream_t st)
 {
     if (cudaMemsetAsync(B.max_s2, 0, sizeof(unsigned) * (size_t)B.n_max_s2, st) != cudaSuccess) return 1;
-    if (sweep_launch(B, h_sigmas, n_sigma, p, false, st)) return 1;
+    // selection planes: the per-scale strip kernels (fd4_tensor.cu), or with
+    // FD4_SELECT_SWEEP=1 the multi-scale tile sweep (same result)
+    const char *e = getenv("FD4_SELECT_SWEEP");
+    if (e && e[0] == '1') {
+        if (sweep_launch(B, h_sigmas, n_sigma, p, false, st)) return 1;
+    } else if (launch_select_strips(B, h_sigmas, n_sigma, p, st)) {
+        return 1;
+    }
     Imgs I = B.I;
     I.tiles = B.tiles[SHAPE_SMALL];
     const int grid = persistent_grid((const void *)k_select_argmax, 256, 0, I.tiles);

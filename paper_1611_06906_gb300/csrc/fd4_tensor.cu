@@ -13,6 +13,7 @@
 // loop is unrolled and the weights are kernel parameters (constant-bank
 // operands of the FMAs).  The arithmetic and summation order are those of the
 // multi-scale sweep in fd4_scale.cu, so both give identical results.
+#include <cmath>
 #include <cstdint>
 #include <cstdlib>
 
@@ -149,13 +150,25 @@ __device__ __forceinline__ void st_rows(const StripTaps<R> &tp, const float *tin
     }
 }
 
-// Scale s (radius R) over every strip segment of the batch.  idx: selected
-// scale per pixel; only pixels with idx == s are written (nfield).  The s == 0
-// launch also zeroes N where idx lies outside the scale set (K_total).  The
-// next piece's rows (of this segment or of the block's next one) are copied
-// with cp.async while the current piece is computed.
-template <int R>
-__global__ void __launch_bounds__(ST_NT) k_tensor_strip(Imgs I, StripTaps<R> tp, int s, int K_total, int grad_sq)
+// Per-launch scalars of the strip kernels.
+struct StripArgs {
+    int s;          // scale index in the set
+    int K_total;    // size of the set
+    int grad_sq;    // tensor build: |grad u|^2 instead of |grad u| in the normalisation
+    int mode;       // selection: FD4_RIDGE / FD4_VALLEY / FD4_BOTH
+    float scale4;   // selection: sigma^(4 gamma)
+    float inv2b2;   // selection: 1 / (2 beta^2)
+};
+
+// Scale s (radius R) over every strip segment of the batch.
+// Tensor build (SEL false): idx holds each pixel's selected scale; only pixels
+// with idx == s are written (nfield), and the s == 0 launch also zeroes N where
+// idx lies outside the scale set.  Selection (SEL true): every pixel's Hessian
+// at scale s gives the vesselness factor and S^2 of plane s (vp, s2) and the
+// image's max S^2.  The next piece's rows (of this segment or of the block's
+// next one) are copied with cp.async while the current piece is computed.
+template <int R, bool SEL>
+__global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripArgs sa)
 {
     constexpr int NB = ST_CH + 2 * R, SW = st_sw<R>(), NP0 = Piece<R>::NP0;
     extern __shared__ __align__(16) float stsm[];
@@ -165,7 +178,8 @@ __global__ void __launch_bounds__(ST_NT) k_tensor_strip(Imgs I, StripTaps<R> tp,
     __shared__ ImgDesc sd[2];
     __shared__ int s_local[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int G = gridDim.x;
+    const int G = gridDim.x, s = sa.s;
+    float bmax = 0.0f;  // selection: max S^2 of this thread's pixels in the current segment
     int t = blockIdx.x;
     if (t >= I.tiles) return;
     if (tid == 0) find_tile(I, SHAPE_SEG, t, sd[0], s_local[0]);
@@ -174,7 +188,8 @@ __global__ void __launch_bounds__(ST_NT) k_tensor_strip(Imgs I, StripTaps<R> tp,
     {
         const int tx = (sd[0].w + ST_TX - 1) / ST_TX;
         const Piece<R> p0((s_local[0] / tx) * kSegRows, 0);
-        st_stage<R>(stsm, sd[0].u, sd[0].w, sd[0].h, sd[0].pitch, (s_local[0] % tx) * ST_TX, p0.ya, p0.n);
+        st_stage<R>(stsm, SEL ? sd[0].in : sd[0].u, sd[0].w, sd[0].h, sd[0].pitch, (s_local[0] % tx) * ST_TX, p0.ya,
+                    p0.n);
         st_commit();
     }
     for (;;) {
@@ -188,12 +203,13 @@ __global__ void __launch_bounds__(ST_NT) k_tensor_strip(Imgs I, StripTaps<R> tp,
         float *nbuf = stsm + (buf ^ 1) * ST_CH * SW;
         if (i + 1 < P) {
             const Piece<R> pn(ys, i + 1);
-            st_stage<R>(nbuf, sd[cur].u, w, h, pitch, x0, pn.ya, pn.n);
+            st_stage<R>(nbuf, SEL ? sd[cur].in : sd[cur].u, w, h, pitch, x0, pn.ya, pn.n);
         } else if (t + G < I.tiles) {
             const ImgDesc &dn = sd[cur ^ 1];  // looked up at piece 0, published by its barriers (P >= 2)
             const int txn = (dn.w + ST_TX - 1) / ST_TX;
             const Piece<R> pn((s_local[cur ^ 1] / txn) * kSegRows, 0);
-            st_stage<R>(nbuf, dn.u, dn.w, dn.h, dn.pitch, (s_local[cur ^ 1] % txn) * ST_TX, pn.ya, pn.n);
+            st_stage<R>(nbuf, SEL ? dn.in : dn.u, dn.w, dn.h, dn.pitch, (s_local[cur ^ 1] % txn) * ST_TX, pn.ya,
+                        pn.n);
         }
         st_commit();
         // the selected scales of the chunk this piece completes (rows 4 warp .. + 3)
@@ -202,7 +218,7 @@ __global__ void __launch_bounds__(ST_NT) k_tensor_strip(Imgs I, StripTaps<R> tp,
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int gx = x0 + lane, gy = y0 + warp * 4 + j;
-            ids[j] = (pc.last && gx < w && gy < h) ? (int)sd[cur].idx[(size_t)gy * pitch + gx] : -1;
+            ids[j] = (!SEL && pc.last && gx < w && gy < h) ? (int)sd[cur].idx[(size_t)gy * pitch + gx] : -1;
         }
         st_wait1();
         __syncthreads();  // this piece's rows have landed; the previous chunk's column pass is done
@@ -227,13 +243,65 @@ __global__ void __launch_bounds__(ST_NT) k_tensor_strip(Imgs I, StripTaps<R> tp,
         st_rows<R>(tp, stsm + buf * ST_CH * SW, trow, pc.b0, pc.n);
         __syncthreads();
 
-        if (pc.last) {
+        if (SEL && pc.last) {
+            // dense column pass: column lane, rows 4 warp .. + 3 of the chunk
+            // read buffer rows 4 warp .. 4 warp + 3 + 2R
+            const float *c0 = trow + (warp * 4) * ST_RS + lane;
+            const float *c1 = c0 + NB * ST_RS, *c2 = c1 + NB * ST_RS;
+            float uxx[4], uxy[4], uyy[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) uxx[j] = uxy[j] = uyy[j] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 2 * R + 4; ++k) {
+                const float v0 = c0[k * ST_RS], v1 = c1[k * ST_RS], v2 = c2[k * ST_RS];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int q = k - j;  // tap index of output row j
+                    if (q >= 0 && q <= 2 * R) {
+                        uxx[j] = fmaf(tp.w0[q], v2, uxx[j]);   // d2/dx2, smoothed in y
+                        uxy[j] = fmaf(tp.w1[q], v1, uxy[j]);   // d/dx, then d/dy
+                        uyy[j] = fmaf(tp.w2[q], v0, uyy[j]);   // d2/dy2 of the x-smoothed field
+                    }
+                }
+            }
+            const int gx = x0 + lane;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int gy = y0 + warp * 4 + j;
+                if (gx >= w || gy >= h) continue;
+                const float a = uxx[j], b = uxy[j], d = uyy[j];
+                // eigenvalues of H (sigma^(2 gamma) cancels in R_B and the sign
+                // test; S^2 picks it up as sigma^(4 gamma))
+                const float m = 0.5f * (a + d);
+                const float rr = hypotf(0.5f * (a - d), b);
+                const float far = m > 0.0f ? m + rr : m - rr;  // larger magnitude; ties -> negative
+                float vp = 0.0f;
+                const bool wrong = (sa.mode == FD4_RIDGE && far > 0.0f) || (sa.mode == FD4_VALLEY && far < 0.0f);
+                if (!wrong && far != 0.0f) {
+                    const float near = det2_sym(a, b, d) / far;  // cancellation-free
+                    const float rb = near / far;
+                    vp = expf(-rb * rb * sa.inv2b2);
+                }
+                const float s2 = sa.scale4 * fmaf(a, a, fmaf(2.0f * b, b, d * d));
+                const size_t p = (size_t)gy * pitch + gx;
+                sd[cur].vp[(size_t)s * sd[cur].plane + p] = vp;
+                sd[cur].s2[(size_t)s * sd[cur].plane + p] = s2;
+                bmax = fmaxf(bmax, s2);
+            }
+            if (i + 1 == P) {  // segment done: fold its max S^2 into the image's
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+                if (lane == 0 && bmax > 0.0f) atomicMax(sd[cur].max_s2, __float_as_uint(bmax));
+                bmax = 0.0f;
+            }
+        }
+        if (!SEL && pc.last) {
             // the chunk's pixels of this scale, grouped in plist
             unsigned m[4];
             int cnt = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                if (s == 0 && ids[j] >= K_total)
+                if (s == 0 && ids[j] >= sa.K_total)
                     sd[cur].nfield[(size_t)(y0 + warp * 4 + j) * pitch + x0 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
                 m[j] = __ballot_sync(0xffffffffu, ids[j] == s);
                 cnt += __popc(m[j]);
@@ -279,7 +347,7 @@ __global__ void __launch_bounds__(ST_NT) k_tensor_strip(Imgs I, StripTaps<R> tp,
                     sxx = fmaf(tp.w0[k], v2, sxx);
                 }
                 const float g2 = fmaf(sx, sx, sy * sy);
-                const float g = grad_sq ? g2 : sqrtf(g2);
+                const float g = sa.grad_sq ? g2 : sqrtf(g2);
                 const float f = 1.0f / sqrtf(1.0f + g);
                 sd[cur].nfield[(size_t)(y0 + py) * pitch + x0 + px] = make_float4(f * sxx, f * sxy, f * syy, 0.0f);
             }
@@ -295,15 +363,15 @@ __global__ void __launch_bounds__(ST_NT) k_tensor_strip(Imgs I, StripTaps<R> tp,
     st_wait0();
 }
 
-template <int R>
-int launch_strip_scale(const HostBatch &B, const GaussTaps &g, int s, int K_total, int grad_sq, cudaStream_t st)
+template <int R, bool SEL>
+int launch_strip_scale(const HostBatch &B, const GaussTaps &g, const StripArgs &sa, cudaStream_t st)
 {
     static int attr_dev = -1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
     constexpr size_t smem = st_smem_bytes<R>();
     if (attr_dev != dev) {
-        if (cudaFuncSetAttribute(k_tensor_strip<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        if (cudaFuncSetAttribute(k_strip<R, SEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return 1;
         attr_dev = dev;
@@ -318,15 +386,52 @@ int launch_strip_scale(const HostBatch &B, const GaussTaps &g, int s, int K_tota
         }
     Imgs I = B.I;
     I.tiles = B.tiles[SHAPE_SEG];
-    const int grid = persistent_grid((const void *)k_tensor_strip<R>, ST_NT, smem, I.tiles);
-    k_tensor_strip<R><<<grid, ST_NT, smem, st>>>(I, tp, s, K_total, grad_sq);
+    const int grid = persistent_grid((const void *)k_strip<R, SEL>, ST_NT, smem, I.tiles);
+    k_strip<R, SEL><<<grid, ST_NT, smem, st>>>(I, tp, sa);
     return cudaGetLastError() != cudaSuccess;
+}
+
+template <bool SEL>
+int launch_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p, cudaStream_t st)
+{
+    for (int s = 0; s < n_sigma; ++s) {
+        GaussTaps g;
+        if (gauss_taps(h_sigmas[s], &g) != FD4_OK) return 1;
+        const int R = (g.r + 3) / 4 * 4;
+        StripArgs sa;
+        sa.s = s;
+        sa.K_total = n_sigma;
+        sa.grad_sq = p.grad_norm_squared;
+        sa.mode = p.mode;
+        sa.scale4 = (float)pow((double)h_sigmas[s], 4.0 * p.gamma);
+        sa.inv2b2 = (float)(1.0 / (2.0 * (double)p.beta * p.beta));
+        int rc = 1;
+        switch (R) {
+        case 4: rc = launch_strip_scale<4, SEL>(B, g, sa, st); break;
+        case 8: rc = launch_strip_scale<8, SEL>(B, g, sa, st); break;
+        case 12: rc = launch_strip_scale<12, SEL>(B, g, sa, st); break;
+        case 16: rc = launch_strip_scale<16, SEL>(B, g, sa, st); break;
+        case 20: rc = launch_strip_scale<20, SEL>(B, g, sa, st); break;
+        case 24: rc = launch_strip_scale<24, SEL>(B, g, sa, st); break;
+        case 28: rc = launch_strip_scale<28, SEL>(B, g, sa, st); break;
+        case 32: rc = launch_strip_scale<32, SEL>(B, g, sa, st); break;
+        case 36: rc = launch_strip_scale<36, SEL>(B, g, sa, st); break;
+        case 40: rc = launch_strip_scale<40, SEL>(B, g, sa, st); break;
+        case 44: rc = launch_strip_scale<44, SEL>(B, g, sa, st); break;
+        case 48: rc = launch_strip_scale<48, SEL>(B, g, sa, st); break;
+        default: rc = 1;
+        }
+        if (rc) return 1;
+    }
+    return 0;
 }
 
 template <int R>
 int set_strip_smem()
 {
-    return cudaFuncSetAttribute(k_tensor_strip<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_strip<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)st_smem_bytes<R>()) != cudaSuccess ||
+           cudaFuncSetAttribute(k_strip<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)st_smem_bytes<R>()) != cudaSuccess;
 }
 
@@ -343,29 +448,15 @@ int prepare_tensor_kernels()
 int launch_tensor_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
                          cudaStream_t st)
 {
-    for (int s = 0; s < n_sigma; ++s) {
-        GaussTaps g;
-        if (gauss_taps(h_sigmas[s], &g) != FD4_OK) return 1;
-        const int R = (g.r + 3) / 4 * 4;
-        int rc = 1;
-        switch (R) {
-        case 4: rc = launch_strip_scale<4>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
-        case 8: rc = launch_strip_scale<8>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
-        case 12: rc = launch_strip_scale<12>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
-        case 16: rc = launch_strip_scale<16>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
-        case 20: rc = launch_strip_scale<20>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
-        case 24: rc = launch_strip_scale<24>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
-        case 28: rc = launch_strip_scale<28>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
-        case 32: rc = launch_strip_scale<32>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
-        case 36: rc = launch_strip_scale<36>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
-        case 40: rc = launch_strip_scale<40>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
-        case 44: rc = launch_strip_scale<44>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
-        case 48: rc = launch_strip_scale<48>(B, g, s, n_sigma, p.grad_norm_squared, st); break;
-        default: rc = 1;
-        }
-        if (rc) return 1;
-    }
-    return 0;
+    return launch_strips<false>(B, h_sigmas, n_sigma, p, st);
+}
+
+// Selection planes (vp, s2) of every scale and each image's max S^2 (which the
+// caller clears first).
+int launch_select_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
+                         cudaStream_t st)
+{
+    return launch_strips<true>(B, h_sigmas, n_sigma, p, st);
 }
 
 }  // namespace fd4

@@ -216,6 +216,27 @@ def test_tensor_strips_equal_tile_sweep(monkeypatch, shape):
     assert torch.equal(t_sweep[:, :w], t_strip[:, :w])
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(600, 97), (53, 37), (300, 1000)])
+def test_select_strips_equal_tile_sweep(monkeypatch, shape, mode):
+    """Selection by the per-scale strip kernels and by the multi-scale tile
+    sweep: the same sums in the same order, so identical sigma* and V."""
+    import torch
+    h, w = shape
+    img = synth.vessel_tree(2200 + h, w, h, depth=4, r0=4.0)
+    sig = [0.75, 1.0, 1.6, 2.5, 4.0, 6.0, 9.0, 12.0]
+    u = fd4.to_device(img)
+    prm = fd4.params(mode=mode)
+    monkeypatch.setenv("FD4_SELECT_SWEEP", "1")
+    i_sweep, v_sweep = fd4.select_scales(u, w, sig, prm, want_vmax=True)
+    i_sweep, v_sweep = i_sweep.clone(), v_sweep.clone()
+    monkeypatch.setenv("FD4_SELECT_SWEEP", "0")
+    i_strip, v_strip = fd4.select_scales(u, w, sig, prm, want_vmax=True)
+    torch.cuda.synchronize()
+    assert torch.equal(i_sweep[:, :w], i_strip[:, :w])
+    assert torch.equal(v_sweep[:, :w], v_strip[:, :w])
+
+
 def test_build_tensor_large_scales(oracle):
     img = synth.vessel_tree(2003, 131, 290, depth=4, r0=6.0)
     sig = [3.0, 6.0, 9.0, 12.0]
