@@ -279,7 +279,9 @@ def run_fd4(args, rank, world, local_rank):
     peak, peak_kind = load_peaks()
     fed_bytes = 24 * npx * M * n  # algorithmic bytes of the FED steps of one pass
     achieved = fed_bytes / (fed_ms * 1e-3) / 1e9
-    kname = "k_fed_fused<%d>" % best if best > 1 else "k_fed_step"
+    # the FED kernel the schedule runs (fd4_fed.cu): quad kernel on 64 x 64 regions for 2 and 4 steps
+    # per launch, the scalar fused kernel for 3, one launch per step for 1
+    kname = {1: "k_fed_step", 2: "k_fed_quad<2,64>", 3: "k_fed_fused<3>", 4: "k_fed_quad<4,64>"}[best]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": args.traffic, "kernel": kname,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind,

@@ -609,10 +609,11 @@ int launch_select_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, 
                         cudaStream_t st)
 {
     if (cudaMemsetAsync(B.max_s2, 0, sizeof(unsigned) * (size_t)B.n_max_s2, st) != cudaSuccess) return 1;
-    // selection planes: the per-scale strip kernels (fd4_tensor.cu), or with
-    // FD4_SELECT_SWEEP=1 the multi-scale tile sweep (same result)
+    // selection planes: the per-scale strip kernels (fd4_tensor.cu), or the
+    // multi-scale tile sweep (same result) for a subset of tiles (I.list, which
+    // the strips cannot walk) or with FD4_SELECT_SWEEP=1
     const char *e = getenv("FD4_SELECT_SWEEP");
-    if (e && e[0] == '1') {
+    if (B.I.list || (e && e[0] == '1')) {
         if (sweep_launch(B, h_sigmas, n_sigma, p, false, st)) return 1;
     } else if (launch_select_strips(B, h_sigmas, n_sigma, p, st)) {
         return 1;
@@ -630,7 +631,7 @@ int launch_tensor_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, 
     // N at the selected scales: the per-scale strip kernels (fd4_tensor.cu),
     // or with FD4_TENSOR_SWEEP=1 the multi-scale tile sweep (same result).
     const char *e = getenv("FD4_TENSOR_SWEEP");
-    if (e && e[0] == '1') {
+    if (B.I.list || (e && e[0] == '1')) {
         if (sweep_launch(B, h_sigmas, n_sigma, p, true, st)) return 1;
     } else if (launch_tensor_strips(B, h_sigmas, n_sigma, p, st)) {
         return 1;

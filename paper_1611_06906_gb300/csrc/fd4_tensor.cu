@@ -394,6 +394,7 @@ int launch_strip_scale(const HostBatch &B, const GaussTaps &g, const StripArgs &
 template <bool SEL>
 int launch_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p, cudaStream_t st)
 {
+    if (B.I.list) return 1;  // the strips walk whole images, never a tile subset
     for (int s = 0; s < n_sigma; ++s) {
         GaussTaps g;
         if (gauss_taps(h_sigmas[s], &g) != FD4_OK) return 1;
