@@ -37,6 +37,11 @@ sys.path.insert(0, ROOT)
 
 from paper_1611_06906_gb300.dist import max_over_ranks as _max_over_ranks, rank_seed  # noqa: E402
 
+# DRAM bytes (read + write) per pixel and launch of k_fed_quad<2,64>, from an ncu
+# capture of one launch over the first 8 batch64_fundus images (351.6 MB / 15.13
+# Mpixel); the roofline's `traffic` scales it to the launch timed here.  To be
+# re-measured (or the field left null) whenever that kernel changes.
+QUAD2_DRAM_B_PER_PX = 23.24
 METRIC = "Mpixel-steps/s, batched+learned vs plain GB300, at stated FP64-oracle error"
 UNIT = "Mpixel-steps/s"
 
@@ -282,8 +287,12 @@ def run_fd4(args, rank, world, local_rank):
     # the FED kernel the schedule runs (fd4_fed.cu): quad kernel on 64 x 64 regions for 2 and 4 steps
     # per launch, the scalar fused kernel for 3, one launch per step for 1
     kname = {1: "k_fed_step", 2: "k_fed_quad<2,64>", 3: "k_fed_fused<3>", 4: "k_fed_quad<4,64>"}[best]
+    default_kernels = not any(os.environ.get(v) for v in ("FD4_FED_PIPELINE", "FD4_FED_QUAD_ROWS", "FD4_FED_FUSE"))
+    traffic = args.traffic
+    if traffic is None and kname == "k_fed_quad<2,64>" and default_kernels:
+        traffic = QUAD2_DRAM_B_PER_PX * npx
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": args.traffic, "kernel": kname,
+            "traffic": traffic, "traffic_unit": "bytes per launch", "kernel": kname,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind,
             "bytes_per_px_step": 24, "steps_per_launch": best,
             "avg_launch_us": fed_ms * 1e3 / fed_launches,
@@ -448,7 +457,8 @@ def main():
     ap.add_argument("--sel-threshold", type=float, default=0.5, help="fallback confidence threshold")
     ap.add_argument("--only-graph", action="store_true", help="replay the full graph only (profiling)")
     ap.add_argument("--traffic", type=float, default=None,
-                    help="DRAM bytes per FED launch from an ncu capture of the current kernel")
+                    help="DRAM bytes per FED launch from an ncu capture of the current kernel "
+                         "(default: the stored per-pixel figure of k_fed_quad<2,64>, else null)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
