@@ -293,6 +293,13 @@ int fd4_select_scales_learned(const void *d_params, const float *d_img, int w, i
                               uint8_t *d_sigma_idx, float *d_conf, int *d_n_fallback, void *d_ws,
                               size_t ws_bytes, fd4_stream_t stream);
 
+/* Library-wide device status word of the FED kernels: FD4_ERR_TIMEOUT after a
+ * bounded wait of the TMA-staged FED kernel on a tile's copies gave up (the
+ * kernel then stops its work and returns), FD4_OK otherwise.  Synchronous
+ * (waits for the device); reset != 0 clears it after reading.  No
+ * counterpart in the paper: failure reporting of the device-side waits.     */
+int fd4_device_status(int *status, int reset);
+
 /* Device status word of a selector workspace (FD4_ERR_TIMEOUT if a bounded
  * wait in a tensor-core kernel gave up), read synchronously.                */
 int fd4_selector_status(const void *d_ws, int *status, fd4_stream_t stream);

@@ -10,6 +10,7 @@
 #include <cstdlib>
 
 #include "fd4_internal.h"
+#include "fd4_quad.cuh"
 
 namespace fd4 {
 namespace {
@@ -162,10 +163,6 @@ __global__ void __launch_bounds__(256) k_copy_back(Imgs I)
 constexpr int FRX = 64, FRY = 32, FV = 4, FNT = (FRX / 32) * (FRY / FV) * 32;  // 512 threads
 constexpr size_t kFusedSmem = 4 * sizeof(float) * FRX * FRY;                  // 32 KB
 
-struct StepTaus {
-    float t[8];
-    int n;
-};
 
 // The S steps of one staged region.  INTERIOR: the region lies inside the
 // image (natural boundary), so every derivative row exists and no mask or
@@ -472,116 +469,6 @@ constexpr size_t q_smem() { return sizeof(float) * 4 * q_plane<RY>() + sizeof(fl
 template <int S, int RY>
 constexpr int q_shape() { return RY == 32 ? S : (S == 2 ? SHAPE_Q64_2 : SHAPE_Q64_4); }
 
-struct QuadCoef {
-    float4 c, s, p, q;  // per pixel of the quad: cos 2t, sin 2t, mean and half difference of mu
-};
-
-__device__ __forceinline__ void f4_to(const float4 v, float *d)
-{
-    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
-}
-
-// The quad's 4 values with the left and right neighbours from adjacent lanes.
-__device__ __forceinline__ void quad_ext(const float4 m, float (&v)[6])
-{
-    v[0] = __shfl_up_sync(0xffffffffu, m.w, 1);
-    v[1] = m.x; v[2] = m.y; v[3] = m.z; v[4] = m.w;
-    v[5] = __shfl_down_sync(0xffffffffu, m.x, 1);
-}
-
-// T = M D M L u for the 4 pixels of one quad.  a, b, c: rows y-1, y, y+1 at
-// columns x-1 .. x+4.  BOUNDARY: apply the natural-boundary masks (bits 0-3:
-// pixel inside, 4-7: Lxx row exists, 8: Lyy row exists for this row).
-template <bool BOUNDARY>
-__device__ __forceinline__ void quad_T(const float (&a)[6], const float (&b)[6], const float (&c)[6],
-                                       const QuadCoef &k, unsigned mask, float4 &Txx, float4 &Txy, float4 &Tyy)
-{
-    float rxx[4], rxy[4], ryy[4];
-    float cc[4], ss[4], pp[4], qq[4];
-    f4_to(k.c, cc);
-    f4_to(k.s, ss);
-    f4_to(k.p, pp);
-    f4_to(k.q, qq);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        float hxx = fmaf(-2.0f, b[i + 1], b[i] + b[i + 2]);
-        float hyy = fmaf(-2.0f, b[i + 1], a[i + 1] + c[i + 1]);
-        float hxy = 0.25f * ((a[i] + c[i + 2]) - (c[i] + a[i + 2]));
-        bool vx = true, vy = true, in = true;
-        if (BOUNDARY) {
-            in = (mask >> i) & 1u;
-            vx = (mask >> (4 + i)) & 1u;
-            vy = (mask >> 8) & 1u;
-            hxx = vx ? hxx : 0.0f;
-            hyy = vy ? hyy : 0.0f;
-            hxy = (vx && vy) ? hxy : 0.0f;
-        }
-        const float sh = 0.5f * (hxx + hyy), dh = 0.5f * (hxx - hyy);
-        const float z = fmaf(cc[i], dh, ss[i] * hxy);          // eigenframe: h11 = sh + z, h22 = sh - z
-        const float v = fmaf(cc[i], hxy, -ss[i] * dh);         // h12
-        const float st = fmaf(pp[i], sh, qq[i] * z);           // (t11 + t22) / 2
-        const float dt = fmaf(qq[i], sh, pp[i] * z);           // (t11 - t22) / 2
-        const float t12 = pp[i] * v;
-        float txx = fmaf(cc[i], dt, fmaf(-ss[i], t12, st));
-        float tyy = fmaf(2.0f, st, -txx);
-        float txy = fmaf(ss[i], dt, cc[i] * t12);
-        if (BOUNDARY) {
-            txx = (in && vx) ? txx : 0.0f;
-            tyy = (in && vy) ? tyy : 0.0f;
-            txy = (in && vx && vy) ? txy : 0.0f;
-        }
-        rxx[i] = txx;
-        rxy[i] = txy;
-        ryy[i] = tyy;
-    }
-    Txx = make_float4(rxx[0], rxx[1], rxx[2], rxx[3]);
-    Txy = make_float4(rxy[0], rxy[1], rxy[2], rxy[3]);
-    Tyy = make_float4(ryy[0], ryy[1], ryy[2], ryy[3]);
-}
-
-// S steps of one staged region; uo: this quad's u on entry, returned updated.
-// Two block barriers per step: T is complete before the update reads it, the
-// update is complete before the next T phase reads u.  The first T phase reads
-// the staged region (published by the tile's barrier); after the last update
-// no barrier is needed before the next tile's.
-template <bool BOUNDARY>
-__device__ __forceinline__ float4 quad_steps(float *su, float *sxy, float *syy, const float *stau, int nsteps,
-                                             int off, const QuadCoef &k, unsigned mask, float4 uo)
-{
-    for (int l = 0; l < nsteps; ++l) {
-        if (l > 0) __syncthreads();
-        float a[6], b[6], c[6];
-        quad_ext(*reinterpret_cast<const float4 *>(su + off - QSW), a);
-        quad_ext(uo, b);
-        quad_ext(*reinterpret_cast<const float4 *>(su + off + QSW), c);
-        float4 txx, txy, tyy;
-        quad_T<BOUNDARY>(a, b, c, k, mask, txx, txy, tyy);
-        *reinterpret_cast<float4 *>(sxy + off) = txy;
-        *reinterpret_cast<float4 *>(syy + off) = tyy;
-        __syncthreads();
-        // u -= tau (Lxx' Txx + Lyy' Tyy + 2 Lxy' Txy)
-        float X[6], Zu[6], Zd[6], Yu[4], Yc[4], Yd[4];
-        quad_ext(txx, X);
-        quad_ext(*reinterpret_cast<const float4 *>(sxy + off - QSW), Zu);
-        quad_ext(*reinterpret_cast<const float4 *>(sxy + off + QSW), Zd);
-        f4_to(*reinterpret_cast<const float4 *>(syy + off - QSW), Yu);
-        f4_to(tyy, Yc);
-        f4_to(*reinterpret_cast<const float4 *>(syy + off + QSW), Yd);
-        const float tau = stau[l];
-        float r[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float div = fmaf(-2.0f, X[i + 1], X[i] + X[i + 2]) + fmaf(-2.0f, Yc[i], Yu[i] + Yd[i]) +
-                              0.5f * ((Zd[i + 2] + Zu[i]) - (Zu[i + 2] + Zd[i]));
-            r[i] = fmaf(-tau, div, b[i + 1]);
-            if (BOUNDARY && !((mask >> i) & 1u)) r[i] = b[i + 1];
-        }
-        uo = make_float4(r[0], r[1], r[2], r[3]);
-        *reinterpret_cast<float4 *>(su + off) = uo;
-    }
-    return uo;
-}
-
 // cp.async of a tile's region into the staging buffers: consecutive threads
 // copy consecutive 16-byte chunks (one u chunk and four tensor pixels each).
 template <int S, int RY>
@@ -687,8 +574,8 @@ __global__ void __launch_bounds__(q_nt<RY>(), RY == 32 ? 2 : 1) k_fed_quad(Imgs 
         if (tn < ntiles) quad_prefetch<S, RY>(sd[cur ^ 1], s_local[cur ^ 1], qsm + (cur ^ 1) * QPLANE, tbuf, parity);
         cp_async_commit();
 
-        const float4 un = interior ? quad_steps<false>(su, sxy, syy, stau, taus.n, off, k, mask, u0)
-                                   : quad_steps<true>(su, sxy, syy, stau, taus.n, off, k, mask, u0);
+        const float4 un = interior ? quad_steps<false, QSW>(su, sxy, syy, stau, taus.n, off, k, mask, u0)
+                                   : quad_steps<true, QSW>(su, sxy, syy, stau, taus.n, off, k, mask, u0);
         // the exact interior: rows H .. H + TYo - 1, columns H .. H + TXo - 1 (whole quads)
         if (ry >= H && ry < H + TYo && 4 * q >= H && 4 * q < H + TXo && gy < h) {
             float *dst = uout + (size_t)gy * pitch + gx;
@@ -754,7 +641,7 @@ int prepare_fed_kernels()
 {
     return set_fused_smem<2>() || set_fused_smem<3>() || set_fused_smem<4>() || set_pipe_smem<2>() ||
            set_pipe_smem<4>() || set_quad_smem<2, 32>() || set_quad_smem<4, 32>() || set_quad_smem<2, 64>() ||
-           set_quad_smem<4, 64>();
+           set_quad_smem<4, 64>() || prepare_tma_kernels();
 }
 
 template <int S, int RY>
@@ -795,9 +682,6 @@ static int launch_fused(Imgs I, const double *tau, int n, int parity, int period
     return 0;
 }
 
-// Kernel for S = 2 and 4 under the natural boundary, from FD4_FED_PIPELINE:
-// 0 = the plain fused kernel, 1 = its cp.async-pipelined form, unset or 2 =
-// the quad kernel.  S = 3 and the periodic boundary use the plain fused kernel.
 // Region height of the quad kernel: 64 (64 x 64 regions, the default) or
 // FD4_FED_QUAD_ROWS=32 (64 x 32 regions, two blocks per SM).
 static int quad_rows()
@@ -806,12 +690,17 @@ static int quad_rows()
     return (e && atoi(e) == 32) ? 32 : 64;
 }
 
+// Kernel for S = 2 and 4 under the natural boundary, from FD4_FED_PIPELINE:
+// 0 = the plain fused kernel, 1 = its cp.async-pipelined form, 2 = the quad
+// kernel with cp.async staging, unset or 3 = the quad kernel with TMA staging
+// (fd4_fed_tma.cu).  S = 3 and the periodic boundary use the plain fused kernel.
 static int pipeline_kind()
 {
     const char *e = getenv("FD4_FED_PIPELINE");
     if (e && e[0] == '0') return 0;
     if (e && e[0] == '1') return 1;
-    return 2;
+    if (e && e[0] == '2') return 2;
+    return 3;
 }
 
 int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundary, int steps_per_launch,
@@ -836,7 +725,10 @@ int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundar
             const int k = n - i < S ? n - i : S;
             int rc;
             const int kind = periodic || S == 3 ? 0 : pipeline_kind();
-            if (kind == 2 && quad_rows() == 64)
+            if (kind == 3)
+                rc = S == 2 ? launch_fed_tma<2>(B, h_tau + i, k, parity, st)
+                            : launch_fed_tma<4>(B, h_tau + i, k, parity, st);
+            else if (kind == 2 && quad_rows() == 64)
                 rc = S == 2 ? launch_quad<2, 64>(B, h_tau + i, k, parity, st)
                             : launch_quad<4, 64>(B, h_tau + i, k, parity, st);
             else if (kind == 2)

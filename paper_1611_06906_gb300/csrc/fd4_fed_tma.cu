@@ -1,0 +1,376 @@
+// FED cycle kernel with TMA staging (Sec. 3.4 Eq. 17, Sec. 3.5 Eq. 21):
+// u <- u - tau_i L^T D L u, S = 2 or 4 explicit steps per launch on 64 x 64
+// regions, the quad arithmetic of fd4_quad.cuh.
+//
+// Each tile's region of u and of the tensor field arrives by two tensor-map
+// copies (cp.async.bulk.tensor) that one thread issues and an mbarrier counts
+// in bytes: the hardware generates the addresses, zero-fills what lies outside
+// the image, and the next tile's copies overlap the current tile's steps.  Both
+// boxes land dense (u: 64 rows of 256 B, tensor: 64 rows of 1 KB); the threads
+// read their quads' tensor values in a lane-rotated order so that the 16-byte
+// reads of a quarter-warp hit distinct banks.  Per-thread 16-byte copies (the
+// cp.async kernels of fd4_fed.cu) reach about half of the HBM bandwidth on this
+// staging; the bulk copies stream it.
+#include <cuda.h>
+
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "fd4_internal.h"
+#include "fd4_quad.cuh"
+
+namespace fd4 {
+
+// Device status word of the FED kernels: FD4_ERR_TIMEOUT after a bounded wait
+// on a tile's copies gave up.  Sticky until read with reset.
+__device__ int g_fed_status;
+
+namespace {
+
+constexpr int TR = 64;                      // region side
+constexpr int TNT = (TR / 4) * TR;          // 1024 threads: 16 quads x 64 rows
+constexpr int TSW = TR;                     // plane row stride (floats)
+constexpr int TPLANE = (TR + 2) * TSW;      // one zero ring row above and below
+constexpr unsigned kUBytes = TR * TR * 4;   // u box
+constexpr unsigned kTBytes = TR * TR * 16;  // tensor box (cos 2t, sin 2t, mu1, mu2)
+// shared memory: tensor box (1024-byte aligned) | u planes x2 | T_xy, T_yy
+constexpr size_t kTmaSmem = 1024 + kTBytes + sizeof(float) * 4 * TPLANE;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded wait on a tile's copies
+
+struct TmaMaps {
+    CUtensorMap u, tmp, ten;  // 2-D maps: the two u planes {w, h}, the tensor field as floats {4 w, h}
+};
+
+__device__ __forceinline__ unsigned long long tma_now()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tma_mbar_init(uint64_t *m)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(m)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void tma_expect(uint64_t *m, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool tma_try_wait(uint64_t *m, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of m, at most kWaitNs; false if it gave up.
+__device__ __forceinline__ bool tma_wait(uint64_t *m, unsigned parity)
+{
+    if (tma_try_wait(m, parity)) return true;
+    const unsigned long long t0 = tma_now();
+    while (!tma_try_wait(m, parity))
+        if (tma_now() - t0 > kWaitNs) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *m)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_addr(m))
+        : "memory");
+}
+// Shared memory written or read through the generic proxy before the bulk copies overwrite it.
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// A tensor map in global memory written by a kernel (generic proxy) before the copies read it.
+__device__ __forceinline__ void fence_tensormap_acquire(const void *map)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
+template <int S>
+constexpr int tma_shape() { return S == 2 ? SHAPE_Q64_2 : SHAPE_Q64_4; }
+
+// Thread 0: the copies of the region of tile `local` of image d into u_dst (plane
+// row 1) and the tensor box.
+template <int S>
+__device__ __forceinline__ void tma_issue(const ImgDesc &d, int local, const TmaMaps &one, bool from_table,
+                                          int parity, float *u_dst, void *t_dst, uint64_t *mbar)
+{
+    constexpr int H = 2 * S, TO = TR - 2 * H;
+    const int tiles_x = (d.w + TO - 1) / TO;
+    const int gx0 = (local % tiles_x) * TO - H, gy0 = (local / tiles_x) * TO - H;  // gx0: a multiple of 4
+    const TmaMaps *m = from_table ? reinterpret_cast<const TmaMaps *>(d.maps) : &one;
+    const CUtensorMap *mu = parity ? &m->tmp : &m->u;
+    if (from_table) {
+        fence_tensormap_acquire(mu);
+        fence_tensormap_acquire(&m->ten);
+    }
+    fence_async_smem();
+    tma_expect(mbar, kUBytes + kTBytes);
+    tma_load_2d(u_dst + TSW, mu, gx0, gy0, mbar);         // x: 4 gx0 bytes, a multiple of 16
+    tma_load_2d(t_dst, &m->ten, 4 * gx0, gy0, mbar);      // x: 16 gx0 bytes
+}
+
+template <int S>
+__global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int parity, const __grid_constant__ TmaMaps one)
+{
+    constexpr int H = 2 * S, TO = TR - 2 * H, SHAPE = tma_shape<S>();
+    static_assert(TO % 4 == 0 && H % 4 == 0, "whole quads in the exact interior");
+    extern __shared__ unsigned char tma_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)tma_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *tbox = base;                                          // 64 rows x 64 pixels x 16 B
+    float *planes = reinterpret_cast<float *>(base + kTBytes);           // u0 | u1 | T_xy | T_yy
+    float *sxy = planes + 2 * TPLANE, *syy = planes + 3 * TPLANE;
+    __shared__ uint64_t mbar;
+    __shared__ float stau[8];
+    __shared__ ImgDesc sd[2];
+    __shared__ int s_local[2];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x;
+    const bool from_table = I.table != nullptr;
+    for (int i = tid; i < 4 * TPLANE; i += TNT) planes[i] = 0.0f;  // the ring rows stay zero
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) stau[i] = taus.t[i];
+        abort_flag = 0;
+        tma_mbar_init(&mbar);
+    }
+    const int q = tid & 15, ry = tid >> 4;
+    const int off = (ry + 1) * TSW + 4 * q;  // this quad in a plane
+    const int ntiles = I.tiles;
+    int t = blockIdx.x;
+    __syncthreads();
+    if (t < ntiles && tid == 0) {
+        find_tile(I, SHAPE, t, sd[0], s_local[0]);
+        tma_issue<S>(sd[0], s_local[0], one, from_table, parity, planes, tbox, &mbar);
+    }
+    unsigned phase = 0;
+    int cur = 0;
+    for (; t < ntiles; t += gridDim.x) {
+        if (!tma_wait(&mbar, phase)) abort_flag = 1;
+        phase ^= 1u;
+        __syncthreads();  // the region has landed; every warp is past the previous tile
+        if (abort_flag) break;
+        const ImgDesc &d = sd[cur];
+        const int w = d.w, h = d.h, pitch = d.pitch;
+        float *uout = parity ? d.u : d.tmp;
+        const int tiles_x = (w + TO - 1) / TO;
+        const int gx0 = (s_local[cur] % tiles_x) * TO - H, gy0 = (s_local[cur] / tiles_x) * TO - H;
+        const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + TR <= w && gy0 + TR <= h;
+        const int gx = gx0 + 4 * q, gy = gy0 + ry;
+        float *su = planes + cur * TPLANE;
+        const float4 u0 = *reinterpret_cast<const float4 *>(su + off);
+        unsigned mask = 0u;
+        if (!interior) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int x = gx + i;
+                mask |= (x >= 0 && x < w && gy >= 0 && gy < h ? 1u : 0u) << i;
+                mask |= (x >= 1 && x <= w - 2 ? 1u : 0u) << (4 + i);
+            }
+            mask |= (gy >= 1 && gy <= h - 2 ? 1u : 0u) << 8;
+        }
+        QuadCoef k;
+        {
+            // Read i of lane q takes pixel (i + r) mod 4 of its quad, r = (q / 2) mod 4:
+            // the 8 lanes of a quarter-warp then address 8 distinct 16-byte bank
+            // groups (quads are 64 bytes apart).  The values are rotated back by r.
+            const int r = (q >> 1) & 3;
+            const float4 *tq = reinterpret_cast<const float4 *>(tbox + (size_t)ry * (TR * 16)) + 4 * q;
+            float4 v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] = tq[(i + r) & 3];
+            if (r & 1) {  // v[i] holds pixel (i + r) mod 4: rotate back by 1, then by 2
+                const float4 t3 = v[3];
+                v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = t3;
+            }
+            if (r & 2) {
+                float4 t = v[0]; v[0] = v[2]; v[2] = t;
+                t = v[1]; v[1] = v[3]; v[3] = t;
+            }
+            float cc[4], ss[4], pp[4], qq[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 tt = v[i];
+                cc[i] = tt.x;
+                ss[i] = tt.y;
+                pp[i] = 0.5f * (tt.z + tt.w);
+                qq[i] = 0.5f * (tt.z - tt.w);
+            }
+            k.c = make_float4(cc[0], cc[1], cc[2], cc[3]);
+            k.s = make_float4(ss[0], ss[1], ss[2], ss[3]);
+            k.p = make_float4(pp[0], pp[1], pp[2], pp[3]);
+            k.q = make_float4(qq[0], qq[1], qq[2], qq[3]);
+        }
+        const int tn = t + gridDim.x;
+        if (tid == 0 && tn < ntiles) find_tile(I, SHAPE, tn, sd[cur ^ 1], s_local[cur ^ 1]);
+        __syncthreads();  // the tensor box is read; the next descriptor is ready
+        if (tid == 0 && tn < ntiles)
+            tma_issue<S>(sd[cur ^ 1], s_local[cur ^ 1], one, from_table, parity, planes + (cur ^ 1) * TPLANE, tbox,
+                         &mbar);
+
+        const float4 un = interior ? quad_steps<false, TSW>(su, sxy, syy, stau, taus.n, off, k, mask, u0)
+                                   : quad_steps<true, TSW>(su, sxy, syy, stau, taus.n, off, k, mask, u0);
+        // the exact interior: rows H .. H + TO - 1, columns H .. H + TO - 1 (whole quads)
+        if (ry >= H && ry < H + TO && 4 * q >= H && 4 * q < H + TO && gy < h) {
+            float *dst = uout + (size_t)gy * pitch + gx;
+            if (gx + 3 < w) {
+                *reinterpret_cast<float4 *>(dst) = un;
+            } else {
+                if (gx < w) dst[0] = un.x;
+                if (gx + 1 < w) dst[1] = un.y;
+                if (gx + 2 < w) dst[2] = un.z;
+            }
+        }
+        cur ^= 1;
+    }
+    if (abort_flag && tid == 0) {
+        atomicExch(&g_fed_status, FD4_ERR_TIMEOUT);
+        tma_wait(&mbar, phase ^ 1u);  // the copies in flight, again at most kWaitNs
+    }
+}
+
+// Map table writer: a chunk of per-image tensor maps passed as kernel parameters.
+constexpr int kMapChunk = 32;
+struct MapChunk {
+    int first, n;
+    TmaMaps m[kMapChunk];
+};
+__global__ void k_put_maps(const __grid_constant__ MapChunk c, TmaMaps *table)
+{
+    const int i = blockIdx.x, j = threadIdx.x;  // map i of the chunk, 16-byte word j of 24
+    if (i < c.n && j < (int)(sizeof(TmaMaps) / 16)) {
+        reinterpret_cast<uint4 *>(&table[c.first + i])[j] = reinterpret_cast<const uint4 *>(&c.m[i])[j];
+        asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// The three maps of one image (zero fill outside the image).
+int make_maps(const ImgDesc &d, TmaMaps *m)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return 1;
+    const cuuint64_t dim2[2] = {(cuuint64_t)d.w, (cuuint64_t)d.h};
+    const cuuint64_t str2[1] = {(cuuint64_t)d.pitch * 4};
+    const cuuint32_t box2[2] = {TR, TR};
+    const cuuint32_t one2[2] = {1, 1};
+    if (enc(&m->u, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)d.u, dim2, str2, box2, one2,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return 1;
+    if (enc(&m->tmp, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)d.tmp, dim2, str2, box2, one2,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return 1;
+    const cuuint64_t dimt[2] = {(cuuint64_t)d.w * 4, (cuuint64_t)d.h};
+    const cuuint64_t strt[1] = {(cuuint64_t)d.pitch * 16};
+    const cuuint32_t boxt[2] = {TR * 4, TR};
+    if (enc(&m->ten, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)d.tensor, dimt, strt, boxt, one2,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return 1;
+    return 0;
+}
+
+template <int S>
+int set_tma_smem()
+{
+    static int attr_dev = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (attr_dev != dev) {
+        if (cudaFuncSetAttribute(k_fed_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem) !=
+            cudaSuccess)
+            return 1;
+        attr_dev = dev;
+    }
+    return 0;
+}
+
+}  // namespace
+
+size_t tma_maps_bytes() { return sizeof(TmaMaps); }
+
+int prepare_tma_kernels() { return set_tma_smem<2>() || set_tma_smem<4>(); }
+
+// Writes the maps of the n descriptors (their maps fields point into a device
+// table) with kernels on st.
+int launch_put_maps(const ImgDesc *h_descs, int n, void *d_table, cudaStream_t st)
+{
+    thread_local static MapChunk c;  // 12 KB: kept off the stack
+    for (int first = 0; first < n; first += kMapChunk) {
+        c.first = first;
+        c.n = n - first < kMapChunk ? n - first : kMapChunk;
+        for (int i = 0; i < c.n; ++i)
+            if (make_maps(h_descs[first + i], &c.m[i])) return 1;
+        k_put_maps<<<c.n, (int)(sizeof(TmaMaps) / 16), 0, st>>>(c, (TmaMaps *)d_table);
+    }
+    return cudaGetLastError() != cudaSuccess;
+}
+
+// One launch of k steps (k <= S) of the TMA kernel over the batch.  Batches
+// (I.table) take each image's maps from its descriptor; a single inline image
+// gets its maps as a kernel parameter.
+template <int S>
+int launch_fed_tma(const HostBatch &B, const double *tau, int k, int parity, cudaStream_t st)
+{
+    if (set_tma_smem<S>()) return 1;
+    StepTaus t{};
+    t.n = k;
+    for (int i = 0; i < k; ++i) t.t[i] = (float)tau[i];
+    Imgs I = B.I;
+    I.tiles = B.tiles[tma_shape<S>()];
+    TmaMaps one;
+    memset(&one, 0, sizeof(one));
+    if (!I.table && make_maps(I.one, &one)) return 1;
+    const int grid = persistent_grid((const void *)k_fed_tma<S>, TNT, kTmaSmem, I.tiles);
+    k_fed_tma<S><<<grid, TNT, kTmaSmem, st>>>(I, t, parity, one);
+    return cudaGetLastError() != cudaSuccess;
+}
+
+template int launch_fed_tma<2>(const HostBatch &, const double *, int, int, cudaStream_t);
+template int launch_fed_tma<4>(const HostBatch &, const double *, int, int, cudaStream_t);
+
+}  // namespace fd4
+
+extern "C" int fd4_device_status(int *status, int reset)
+{
+    if (!status) return FD4_ERR_BAD_ARG;
+    if (cudaMemcpyFromSymbol(status, fd4::g_fed_status, sizeof(int)) != cudaSuccess) return FD4_ERR_CUDA;
+    if (reset) {
+        const int zero = 0;
+        if (cudaMemcpyToSymbol(fd4::g_fed_status, &zero, sizeof(int)) != cudaSuccess) return FD4_ERR_CUDA;
+    }
+    return FD4_OK;
+}

@@ -416,6 +416,8 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
     size_t off = align_up(sizeof(ImgDesc) * (size_t)n, 256);
     const size_t ms_off = off;
     off += align_up(sizeof(unsigned) * (size_t)n, 256);
+    const size_t maps_off = off;  // TMA tensor maps of the FED kernel, one set per image
+    off += align_up(tma_maps_bytes() * (size_t)n, 256);
     int t0[kShapes] = {};
     if (descs) descs->resize(n);
     int t_split[kShapes] = {};
@@ -443,6 +445,7 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
         d.idx = im.d_sigma_idx ? im.d_sigma_idx : (uint8_t *)(ws + o_idx);
         d.vmax = nullptr;
         d.max_s2 = (unsigned *)(ws + ms_off) + i;
+        d.maps = ws + maps_off + tma_maps_bytes() * (size_t)i;
         d.plane = pb / 4;
         d.w = im.w;
         d.h = im.h;
@@ -538,6 +541,7 @@ static int enqueue_batch_two_streams(const fd4_image *imgs, int n_images, const 
     const int split = balanced_split(imgs, n_images);
     batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B0, split, &B1);
     if (launch_put_descs(descs.data(), n_images, (ImgDesc *)d_ws, s0)) return FD4_ERR_CUDA;
+    if (n_images > 0 && launch_put_maps(descs.data(), n_images, (void *)descs[0].maps, s0)) return FD4_ERR_CUDA;
     const int steps = p.fed_steps_per_launch > 0 ? p.fed_steps_per_launch : default_steps_per_launch();
     if (cudaEventRecord(ev_fork, s0) != cudaSuccess || cudaStreamWaitEvent(s1, ev_fork, 0) != cudaSuccess)
         return FD4_ERR_CUDA;
@@ -572,6 +576,7 @@ static int enqueue_batch(const fd4_image *imgs, int n_images, const float *h_sig
     HostBatch B;
     batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B);
     if (launch_put_descs(descs.data(), n_images, (ImgDesc *)d_ws, st)) return FD4_ERR_CUDA;
+    if (n_images > 0 && launch_put_maps(descs.data(), n_images, (void *)descs[0].maps, st)) return FD4_ERR_CUDA;
     return enqueue_filter(B, h_sigmas, n_sigma, p, tau, n, M, sigma_given, st, stages);
 }
 
@@ -703,6 +708,7 @@ extern "C" int fd4_autotune_batched(const fd4_image *h_imgs, int n_images, const
     HostBatch B;
     batch_layout(h_imgs, n_images, n_sigma, &descs, (char *)d_ws, &B);
     if (launch_put_descs(descs.data(), n_images, (ImgDesc *)d_ws, st)) return FD4_ERR_CUDA;
+    if (n_images > 0 && launch_put_maps(descs.data(), n_images, (void *)descs[0].maps, st)) return FD4_ERR_CUDA;
     if (launch_select_batch(B, h_sigmas, n_sigma, p, st) || launch_copy_in_batch(B, st) ||
         launch_tensor_batch(B, h_sigmas, n_sigma, p, st))
         return FD4_ERR_CUDA;

@@ -84,6 +84,7 @@ struct ImgDesc {
     float *vmax;         // nullable
     unsigned *max_s2;    // max S^2 of the image (float bits)
     size_t plane;
+    const void *maps;    // batches: this image's TMA tensor maps (u, FED plane, tensor) in device memory
     int w, h, pitch;
     int t0[kShapes];     // first flat tile of this image, per tile shape
 };
@@ -229,6 +230,14 @@ int prepare_fed_kernels();
 int default_steps_per_launch();
 int launch_copy_in_batch(const HostBatch &B, cudaStream_t st);
 int launch_put_descs(const ImgDesc *h_descs, int n, ImgDesc *d_table, cudaStream_t st);
+// TMA staging of the FED kernel (fd4_fed_tma.cu): bytes of one image's maps, the
+// writer of a batch's map table (each descriptor's maps field points into it),
+// one launch of k <= S steps, and the kernels' shared-memory attributes.
+size_t tma_maps_bytes();
+int launch_put_maps(const ImgDesc *h_descs, int n, void *d_table, cudaStream_t st);
+template <int S>
+int launch_fed_tma(const HostBatch &B, const double *tau, int k, int parity, cudaStream_t st);
+int prepare_tma_kernels();
 
 // Single-image launchers used by the per-image entry points.
 int launch_select(const float *d_img, int w, int h, int pitch, const float *h_sigmas,

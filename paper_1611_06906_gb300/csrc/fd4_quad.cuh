@@ -1,0 +1,129 @@
+// Quad form of one FED step (Sec. 3.4 Eq. 17: u <- u - tau L^T D L u) shared
+// by the FED kernels that give each thread a row quad (4 adjacent pixels of one
+// row): T = M D M L u with D applied in its eigenframe, then the divergence.
+// Horizontal neighbours come from the adjacent lanes (shuffles), vertical ones
+// from the shared-memory planes (row stride SW floats).
+#pragma once
+
+#include "fd4_internal.h"
+
+namespace fd4 {
+
+// Step sizes of one fused launch (up to 8 steps).
+struct StepTaus {
+    float t[8];
+    int n;
+};
+
+struct QuadCoef {
+    float4 c, s, p, q;  // per pixel of the quad: cos 2t, sin 2t, mean and half difference of mu
+};
+
+__device__ __forceinline__ void f4_to(const float4 v, float *d)
+{
+    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+}
+
+// The quad's 4 values with the left and right neighbours from adjacent lanes.
+__device__ __forceinline__ void quad_ext(const float4 m, float (&v)[6])
+{
+    v[0] = __shfl_up_sync(0xffffffffu, m.w, 1);
+    v[1] = m.x; v[2] = m.y; v[3] = m.z; v[4] = m.w;
+    v[5] = __shfl_down_sync(0xffffffffu, m.x, 1);
+}
+
+// T = M D M L u for the 4 pixels of one quad.  a, b, c: rows y-1, y, y+1 at
+// columns x-1 .. x+4.  BOUNDARY: apply the natural-boundary masks (bits 0-3:
+// pixel inside, 4-7: Lxx row exists, 8: Lyy row exists for this row).
+template <bool BOUNDARY>
+__device__ __forceinline__ void quad_T(const float (&a)[6], const float (&b)[6], const float (&c)[6],
+                                       const QuadCoef &k, unsigned mask, float4 &Txx, float4 &Txy, float4 &Tyy)
+{
+    float rxx[4], rxy[4], ryy[4];
+    float cc[4], ss[4], pp[4], qq[4];
+    f4_to(k.c, cc);
+    f4_to(k.s, ss);
+    f4_to(k.p, pp);
+    f4_to(k.q, qq);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float hxx = fmaf(-2.0f, b[i + 1], b[i] + b[i + 2]);
+        float hyy = fmaf(-2.0f, b[i + 1], a[i + 1] + c[i + 1]);
+        float hxy = 0.25f * ((a[i] + c[i + 2]) - (c[i] + a[i + 2]));
+        bool vx = true, vy = true, in = true;
+        if (BOUNDARY) {
+            in = (mask >> i) & 1u;
+            vx = (mask >> (4 + i)) & 1u;
+            vy = (mask >> 8) & 1u;
+            hxx = vx ? hxx : 0.0f;
+            hyy = vy ? hyy : 0.0f;
+            hxy = (vx && vy) ? hxy : 0.0f;
+        }
+        const float sh = 0.5f * (hxx + hyy), dh = 0.5f * (hxx - hyy);
+        const float z = fmaf(cc[i], dh, ss[i] * hxy);          // eigenframe: h11 = sh + z, h22 = sh - z
+        const float v = fmaf(cc[i], hxy, -ss[i] * dh);         // h12
+        const float st = fmaf(pp[i], sh, qq[i] * z);           // (t11 + t22) / 2
+        const float dt = fmaf(qq[i], sh, pp[i] * z);           // (t11 - t22) / 2
+        const float t12 = pp[i] * v;
+        float txx = fmaf(cc[i], dt, fmaf(-ss[i], t12, st));
+        float tyy = fmaf(2.0f, st, -txx);
+        float txy = fmaf(ss[i], dt, cc[i] * t12);
+        if (BOUNDARY) {
+            txx = (in && vx) ? txx : 0.0f;
+            tyy = (in && vy) ? tyy : 0.0f;
+            txy = (in && vx && vy) ? txy : 0.0f;
+        }
+        rxx[i] = txx;
+        rxy[i] = txy;
+        ryy[i] = tyy;
+    }
+    Txx = make_float4(rxx[0], rxx[1], rxx[2], rxx[3]);
+    Txy = make_float4(rxy[0], rxy[1], rxy[2], rxy[3]);
+    Tyy = make_float4(ryy[0], ryy[1], ryy[2], ryy[3]);
+}
+
+// S steps of one staged region; uo: this quad's u on entry, returned updated.
+// Two block barriers per step: T is complete before the update reads it, the
+// update is complete before the next T phase reads u.  The first T phase reads
+// the staged region (published by the tile's barrier); after the last update
+// no barrier is needed before the next tile's.
+template <bool BOUNDARY, int SW>
+__device__ __forceinline__ float4 quad_steps(float *su, float *sxy, float *syy, const float *stau, int nsteps,
+                                             int off, const QuadCoef &k, unsigned mask, float4 uo)
+{
+    for (int l = 0; l < nsteps; ++l) {
+        if (l > 0) __syncthreads();
+        float a[6], b[6], c[6];
+        quad_ext(*reinterpret_cast<const float4 *>(su + off - SW), a);
+        quad_ext(uo, b);
+        quad_ext(*reinterpret_cast<const float4 *>(su + off + SW), c);
+        float4 txx, txy, tyy;
+        quad_T<BOUNDARY>(a, b, c, k, mask, txx, txy, tyy);
+        *reinterpret_cast<float4 *>(sxy + off) = txy;
+        *reinterpret_cast<float4 *>(syy + off) = tyy;
+        __syncthreads();
+        // u -= tau (Lxx' Txx + Lyy' Tyy + 2 Lxy' Txy)
+        float X[6], Zu[6], Zd[6], Yu[4], Yc[4], Yd[4];
+        quad_ext(txx, X);
+        quad_ext(*reinterpret_cast<const float4 *>(sxy + off - SW), Zu);
+        quad_ext(*reinterpret_cast<const float4 *>(sxy + off + SW), Zd);
+        f4_to(*reinterpret_cast<const float4 *>(syy + off - SW), Yu);
+        f4_to(tyy, Yc);
+        f4_to(*reinterpret_cast<const float4 *>(syy + off + SW), Yd);
+        const float tau = stau[l];
+        float r[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float div = fmaf(-2.0f, X[i + 1], X[i] + X[i + 2]) + fmaf(-2.0f, Yc[i], Yu[i] + Yd[i]) +
+                              0.5f * ((Zd[i + 2] + Zu[i]) - (Zu[i + 2] + Zd[i]));
+            r[i] = fmaf(-tau, div, b[i + 1]);
+            if (BOUNDARY && !((mask >> i) & 1u)) r[i] = b[i + 1];
+        }
+        uo = make_float4(r[0], r[1], r[2], r[3]);
+        *reinterpret_cast<float4 *>(su + off) = uo;
+    }
+    return uo;
+}
+
+
+}  // namespace fd4

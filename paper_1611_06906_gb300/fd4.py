@@ -76,6 +76,7 @@ SIGNATURES = {
     "fd4_graph_launch": (_i, [_vp, _vp]),
     "fd4_graph_destroy": (_i, [_vp]),
     "fd4_graph_kernel_count": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "fd4_device_status": (_i, [ctypes.POINTER(ctypes.c_int), _i]),
     "fd4_autotune_batched": (_i, [_vp, _i, _fp, _i, _pp, ctypes.c_double, _i, _i, _vp, _sz, _vp, _ip,
                                   _fp]),
 }
@@ -308,6 +309,13 @@ def filter_batched(imgs, sigmas, T: float, M: int, n: int = 0, prm: Params | Non
                                     int(sigma_given), _ptr(ws), ws.numel(), _stream(stream)),
            "fd4_filter_batched")
     return ws
+
+
+def device_status(reset: bool = False) -> int:
+    """fd4_device_status: the FED kernels' device status word (0 or FD4_ERR_TIMEOUT)."""
+    st = ctypes.c_int(0)
+    _check(lib().fd4_device_status(ctypes.byref(st), int(reset)), "fd4_device_status")
+    return st.value
 
 
 class Graph:

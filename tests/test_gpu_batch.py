@@ -129,6 +129,14 @@ def test_bad_batch_is_rejected_before_launch():
     assert e.value.status == -4
 
 
+def test_fed_kernels_report_no_timeout():
+    """After the batched runs above, no bounded device wait of the FED kernels gave up."""
+    imgs = _images()
+    ins, outs, idx, lst = _batch(imgs)
+    fd4.filter_batched(lst, SIGMAS, T, M, N, fd4.params(mode=fd4.VALLEY))
+    assert fd4.device_status(reset=True) == 0
+
+
 def test_two_stream_graph_equals_one_stream_graph():
     import torch
     imgs = _images()

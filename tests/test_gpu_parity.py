@@ -62,14 +62,15 @@ def _tensor_to_device(t, w):
     return buf
 
 
-@pytest.fixture(params=[(0, 2, 64), (2, 2, 64), (2, 2, 32), (2, 1, 32), (2, 0, 32), (3, 2, 64), (4, 2, 64),
-                        (4, 2, 32), (4, 1, 32), (4, 0, 32)],
-                ids=["step", "fuse2-quad64", "fuse2-quad32", "fuse2-prefetch", "fuse2-plain", "fuse3",
-                     "fuse4-quad64", "fuse4-quad32", "fuse4-prefetch", "fuse4-plain"])
+@pytest.fixture(params=[(0, 3, 64), (2, 3, 64), (2, 2, 64), (2, 2, 32), (2, 1, 32), (2, 0, 32), (3, 3, 64),
+                        (4, 3, 64), (4, 2, 64), (4, 2, 32), (4, 1, 32), (4, 0, 32)],
+                ids=["step", "fuse2-tma", "fuse2-quad64", "fuse2-quad32", "fuse2-prefetch", "fuse2-plain",
+                     "fuse3", "fuse4-tma", "fuse4-quad64", "fuse4-quad32", "fuse4-prefetch", "fuse4-plain"])
 def fed_variant(request, monkeypatch):
     """FED kernel variant: one launch per step, or 2..4 steps fused per launch
-    (quad kernel on 64 x 64 or 64 x 32 regions, the scalar kernel with the
-    cp.async prefetch of the next tile, or the plain scalar kernel)."""
+    (quad kernel with TMA staging, quad kernel with cp.async staging on 64 x 64
+    or 64 x 32 regions, the scalar kernel with the cp.async prefetch of the
+    next tile, or the plain scalar kernel)."""
     monkeypatch.setenv("FD4_FED_FUSE", str(request.param[0]))
     monkeypatch.setenv("FD4_FED_PIPELINE", str(request.param[1]))
     monkeypatch.setenv("FD4_FED_QUAD_ROWS", str(request.param[2]))
