@@ -37,11 +37,11 @@ sys.path.insert(0, ROOT)
 
 from paper_1611_06906_gb300.dist import max_over_ranks as _max_over_ranks, rank_seed  # noqa: E402
 
-# DRAM bytes (read + write) per pixel and launch of k_fed_quad<2,64>, from an ncu
-# capture of one launch over the first 8 batch64_fundus images (351.6 MB / 15.13
-# Mpixel); the roofline's `traffic` scales it to the launch timed here.  To be
-# re-measured (or the field left null) whenever that kernel changes.
-QUAD2_DRAM_B_PER_PX = 23.24
+# DRAM bytes (read + write) per pixel and launch of k_fed_tma<2>, from an ncu
+# capture of one launch over the first 8 batch64_fundus images; the roofline's
+# `traffic` scales it to the launch timed here.  None (the field null) until the
+# current kernel has been captured; re-measured whenever that kernel changes.
+TMA2_DRAM_B_PER_PX = None
 METRIC = "Mpixel-steps/s, batched+learned vs plain GB300, at stated FP64-oracle error"
 UNIT = "Mpixel-steps/s"
 
@@ -284,13 +284,13 @@ def run_fd4(args, rank, world, local_rank):
     peak, peak_kind = load_peaks()
     fed_bytes = 24 * npx * M * n  # algorithmic bytes of the FED steps of one pass
     achieved = fed_bytes / (fed_ms * 1e-3) / 1e9
-    # the FED kernel the schedule runs (fd4_fed.cu): quad kernel on 64 x 64 regions for 2 and 4 steps
-    # per launch, the scalar fused kernel for 3, one launch per step for 1
-    kname = {1: "k_fed_step", 2: "k_fed_quad<2,64>", 3: "k_fed_fused<3>", 4: "k_fed_quad<4,64>"}[best]
+    # the FED kernel the schedule runs: the TMA-staged quad kernel for 2 and 4 steps per launch
+    # (fd4_fed_tma.cu), the scalar fused kernel for 3, one launch per step for 1 (fd4_fed.cu)
+    kname = {1: "k_fed_step", 2: "k_fed_tma<2>", 3: "k_fed_fused<3>", 4: "k_fed_tma<4>"}[best]
     default_kernels = not any(os.environ.get(v) for v in ("FD4_FED_PIPELINE", "FD4_FED_QUAD_ROWS", "FD4_FED_FUSE"))
     traffic = args.traffic
-    if traffic is None and kname == "k_fed_quad<2,64>" and default_kernels:
-        traffic = QUAD2_DRAM_B_PER_PX * npx
+    if traffic is None and kname == "k_fed_tma<2>" and default_kernels and TMA2_DRAM_B_PER_PX is not None:
+        traffic = TMA2_DRAM_B_PER_PX * npx
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "traffic_unit": "bytes per launch", "kernel": kname,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind,

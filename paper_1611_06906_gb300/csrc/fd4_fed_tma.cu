@@ -34,8 +34,12 @@ constexpr int TSW = TR;                     // plane row stride (floats)
 constexpr int TPLANE = (TR + 2) * TSW;      // one zero ring row above and below
 constexpr unsigned kUBytes = TR * TR * 4;   // u box
 constexpr unsigned kTBytes = TR * TR * 16;  // tensor box (cos 2t, sin 2t, mu1, mu2)
-// shared memory: tensor box (1024-byte aligned) | u planes x2 | T_xy, T_yy
-constexpr size_t kTmaSmem = 1024 + kTBytes + sizeof(float) * 4 * TPLANE;
+// Tiles in flight per block: the copies of the next two tiles run during the
+// current tile's steps (one tile of 80 KB in flight per SM leaves the copies
+// latency-bound at about half the HBM bandwidth).
+constexpr int kAhead = 2;
+// shared memory: tensor boxes x2 (1024-byte aligned) | u planes x3 | T_xy, T_yy
+constexpr size_t kTmaSmem = 1024 + kAhead * kTBytes + sizeof(float) * (kAhead + 1 + 2) * TPLANE;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded wait on a tile's copies
 
 struct TmaMaps {
@@ -126,51 +130,54 @@ __device__ __forceinline__ void tma_issue(const ImgDesc &d, int local, const Tma
 template <int S>
 __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int parity, const __grid_constant__ TmaMaps one)
 {
-    constexpr int H = 2 * S, TO = TR - 2 * H, SHAPE = tma_shape<S>();
+    constexpr int H = 2 * S, TO = TR - 2 * H, SHAPE = tma_shape<S>(), NU = kAhead + 1;
     static_assert(TO % 4 == 0 && H % 4 == 0, "whole quads in the exact interior");
     extern __shared__ unsigned char tma_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)tma_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *tbox = base;                                          // 64 rows x 64 pixels x 16 B
-    float *planes = reinterpret_cast<float *>(base + kTBytes);           // u0 | u1 | T_xy | T_yy
-    float *sxy = planes + 2 * TPLANE, *syy = planes + 3 * TPLANE;
-    __shared__ uint64_t mbar;
+    // tensor boxes: tile j of this block in box j % kAhead (64 rows x 64 pixels x 16 B each)
+    float *planes = reinterpret_cast<float *>(base + kAhead * kTBytes);  // u planes x NU | T_xy | T_yy
+    float *sxy = planes + NU * TPLANE, *syy = planes + (NU + 1) * TPLANE;
+    __shared__ uint64_t mbar[kAhead];     // tile j waits on mbar[j % kAhead]
     __shared__ float stau[8];
-    __shared__ ImgDesc sd[2];
-    __shared__ int s_local[2];
+    __shared__ ImgDesc sd[NU];            // tile j's descriptor in sd[j % NU]
+    __shared__ int s_local[NU];
     __shared__ int abort_flag;
     const int tid = threadIdx.x;
     const bool from_table = I.table != nullptr;
-    for (int i = tid; i < 4 * TPLANE; i += TNT) planes[i] = 0.0f;  // the ring rows stay zero
+    for (int i = tid; i < (NU + 2) * TPLANE; i += TNT) planes[i] = 0.0f;  // the ring rows stay zero
     if (tid == 0) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) stau[i] = taus.t[i];
         abort_flag = 0;
-        tma_mbar_init(&mbar);
+        for (int i = 0; i < kAhead; ++i) tma_mbar_init(&mbar[i]);
     }
     const int q = tid & 15, ry = tid >> 4;
     const int off = (ry + 1) * TSW + 4 * q;  // this quad in a plane
-    const int ntiles = I.tiles;
-    int t = blockIdx.x;
+    const int ntiles = I.tiles, G = gridDim.x;
     __syncthreads();
-    if (t < ntiles && tid == 0) {
-        find_tile(I, SHAPE, t, sd[0], s_local[0]);
-        tma_issue<S>(sd[0], s_local[0], one, from_table, parity, planes, tbox, &mbar);
-    }
-    unsigned phase = 0;
-    int cur = 0;
-    for (; t < ntiles; t += gridDim.x) {
-        if (!tma_wait(&mbar, phase)) abort_flag = 1;
-        phase ^= 1u;
-        __syncthreads();  // the region has landed; every warp is past the previous tile
+    // prologue: the copies of the block's first kAhead tiles
+    if (tid == 0)
+        for (int j = 0; j < kAhead; ++j) {
+            const int tj = blockIdx.x + j * G;
+            if (tj >= ntiles) break;
+            find_tile(I, SHAPE, tj, sd[j], s_local[j]);
+            tma_issue<S>(sd[j], s_local[j], one, from_table, parity, planes + j * TPLANE, base + j * kTBytes,
+                         &mbar[j]);
+        }
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles; t += G, ++j) {
+        const int bj = j % kAhead, uj = j % NU;
+        if (!tma_wait(&mbar[bj], (unsigned)(j / kAhead) & 1u)) abort_flag = 1;
+        __syncthreads();  // tile j has landed; every warp is past tile j - 1
         if (abort_flag) break;
-        const ImgDesc &d = sd[cur];
+        const ImgDesc &d = sd[uj];
         const int w = d.w, h = d.h, pitch = d.pitch;
         float *uout = parity ? d.u : d.tmp;
         const int tiles_x = (w + TO - 1) / TO;
-        const int gx0 = (s_local[cur] % tiles_x) * TO - H, gy0 = (s_local[cur] / tiles_x) * TO - H;
+        const int gx0 = (s_local[uj] % tiles_x) * TO - H, gy0 = (s_local[uj] / tiles_x) * TO - H;
         const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + TR <= w && gy0 + TR <= h;
         const int gx = gx0 + 4 * q, gy = gy0 + ry;
-        float *su = planes + cur * TPLANE;
+        float *su = planes + uj * TPLANE;
         const float4 u0 = *reinterpret_cast<const float4 *>(su + off);
         unsigned mask = 0u;
         if (!interior) {
@@ -188,7 +195,8 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
             // the 8 lanes of a quarter-warp then address 8 distinct 16-byte bank
             // groups (quads are 64 bytes apart).  The values are rotated back by r.
             const int r = (q >> 1) & 3;
-            const float4 *tq = reinterpret_cast<const float4 *>(tbox + (size_t)ry * (TR * 16)) + 4 * q;
+            const float4 *tq =
+                reinterpret_cast<const float4 *>(base + bj * kTBytes + (size_t)ry * (TR * 16)) + 4 * q;
             float4 v[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) v[i] = tq[(i + r) & 3];
@@ -197,8 +205,8 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
                 v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = t3;
             }
             if (r & 2) {
-                float4 t = v[0]; v[0] = v[2]; v[2] = t;
-                t = v[1]; v[1] = v[3]; v[3] = t;
+                float4 tt = v[0]; v[0] = v[2]; v[2] = tt;
+                tt = v[1]; v[1] = v[3]; v[3] = tt;
             }
             float cc[4], ss[4], pp[4], qq[4];
 #pragma unroll
@@ -214,12 +222,14 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
             k.p = make_float4(pp[0], pp[1], pp[2], pp[3]);
             k.q = make_float4(qq[0], qq[1], qq[2], qq[3]);
         }
-        const int tn = t + gridDim.x;
-        if (tid == 0 && tn < ntiles) find_tile(I, SHAPE, tn, sd[cur ^ 1], s_local[cur ^ 1]);
-        __syncthreads();  // the tensor box is read; the next descriptor is ready
-        if (tid == 0 && tn < ntiles)
-            tma_issue<S>(sd[cur ^ 1], s_local[cur ^ 1], one, from_table, parity, planes + (cur ^ 1) * TPLANE, tbox,
-                         &mbar);
+        __syncthreads();  // tensor box bj is read; u plane (j + kAhead) % NU was last used by tile j - 1
+        const int ta = t + kAhead * G;  // tile j + kAhead: into box bj, plane (j + kAhead) % NU
+        if (tid == 0 && ta < ntiles) {
+            const int ua = (j + kAhead) % NU;
+            find_tile(I, SHAPE, ta, sd[ua], s_local[ua]);
+            tma_issue<S>(sd[ua], s_local[ua], one, from_table, parity, planes + ua * TPLANE, base + bj * kTBytes,
+                         &mbar[bj]);
+        }
 
         const float4 un = interior ? quad_steps<false, TSW>(su, sxy, syy, stau, taus.n, off, k, mask, u0)
                                    : quad_steps<true, TSW>(su, sxy, syy, stau, taus.n, off, k, mask, u0);
@@ -234,11 +244,14 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
                 if (gx + 2 < w) dst[2] = un.z;
             }
         }
-        cur ^= 1;
     }
     if (abort_flag && tid == 0) {
         atomicExch(&g_fed_status, FD4_ERR_TIMEOUT);
-        tma_wait(&mbar, phase ^ 1u);  // the copies in flight, again at most kWaitNs
+        // the copies still in flight (tiles j .. j + kAhead - 1), each wait again at most kWaitNs
+        for (int i = 0; i < kAhead; ++i) {
+            const int jj = j + i;
+            if (blockIdx.x + jj * G < ntiles) tma_wait(&mbar[jj % kAhead], (unsigned)(jj / kAhead) & 1u);
+        }
     }
 }
 
