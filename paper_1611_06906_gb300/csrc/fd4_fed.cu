@@ -29,10 +29,12 @@ __global__ void __launch_bounds__(BX *BY) k_fed_step(Imgs I, float tau, int pari
     __shared__ float sxx[BY + 2][BX + 2], sxy[BY + 2][BX + 2], syy[BY + 2][BX + 2];
     __shared__ ImgDesc sd;
     __shared__ int s_local;
+    __shared__ TileCache tcache;
+    if (threadIdx.x == 0) tc_reset(tcache);
     const int tid = threadIdx.y * BX + threadIdx.x;
     for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
         __syncthreads();
-        if (tid == 0) find_tile(I, SHAPE_SMALL, t, sd, s_local);
+        if (tid == 0) find_tile_cached(I, SHAPE_SMALL, t, tcache, sd, s_local);
         __syncthreads();
         const int w = sd.w, h = sd.h, pitch = sd.pitch;
         const float *uin = parity ? sd.tmp : sd.u;
@@ -106,10 +108,12 @@ __global__ void __launch_bounds__(256) k_copy_in(Imgs I)
 {
     __shared__ ImgDesc sd;
     __shared__ int s_local;
+    __shared__ TileCache tcache;
+    if (threadIdx.x == 0) tc_reset(tcache);
     const int tid = threadIdx.x;
     for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
         __syncthreads();
-        if (tid == 0) find_tile(I, SHAPE_SMALL, t, sd, s_local);
+        if (tid == 0) find_tile_cached(I, SHAPE_SMALL, t, tcache, sd, s_local);
         __syncthreads();
         if (sd.in == sd.u) continue;
         const int tiles_x = (sd.w + 31) / 32;
@@ -136,10 +140,12 @@ __global__ void __launch_bounds__(256) k_copy_back(Imgs I)
 {
     __shared__ ImgDesc sd;
     __shared__ int s_local;
+    __shared__ TileCache tcache;
+    if (threadIdx.x == 0) tc_reset(tcache);
     const int tid = threadIdx.x;
     for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
         __syncthreads();
-        if (tid == 0) find_tile(I, SHAPE_SMALL, t, sd, s_local);
+        if (tid == 0) find_tile_cached(I, SHAPE_SMALL, t, tcache, sd, s_local);
         __syncthreads();
         const int tiles_x = (sd.w + 31) / 32;
         const int x = (s_local % tiles_x) * 32 + (tid & 31), y = (s_local / tiles_x) * 8 + (tid >> 5);
@@ -512,6 +518,8 @@ __global__ void __launch_bounds__(q_nt<RY>(), RY == 32 ? 2 : 1) k_fed_quad(Imgs 
     __shared__ float stau[8];
     __shared__ ImgDesc sd[2];
     __shared__ int s_local[2];
+    __shared__ TileCache tcache;
+    if (threadIdx.x == 0) tc_reset(tcache);
     const int tid = threadIdx.x;
     if (tid == 0) {
 #pragma unroll
@@ -526,7 +534,7 @@ __global__ void __launch_bounds__(q_nt<RY>(), RY == 32 ? 2 : 1) k_fed_quad(Imgs 
     int t = blockIdx.x;
     __syncthreads();
     if (t < ntiles) {
-        if (tid == 0) find_tile(I, SHAPE, t, sd[0], s_local[0]);
+        if (tid == 0) find_tile_cached(I, SHAPE, t, tcache, sd[0], s_local[0]);
         __syncthreads();
         quad_prefetch<S, RY>(sd[0], s_local[0], qsm, tbuf, parity);
     }
@@ -569,7 +577,7 @@ __global__ void __launch_bounds__(q_nt<RY>(), RY == 32 ? 2 : 1) k_fed_quad(Imgs 
             k.q = make_float4(qq[0], qq[1], qq[2], qq[3]);
         }
         const int tn = t + gridDim.x;
-        if (tid == 0 && tn < ntiles) find_tile(I, SHAPE, tn, sd[cur ^ 1], s_local[cur ^ 1]);
+        if (tid == 0 && tn < ntiles) find_tile_cached(I, SHAPE, tn, tcache, sd[cur ^ 1], s_local[cur ^ 1]);
         __syncthreads();  // the tensor buffer is read; the next descriptor is ready
         if (tn < ntiles) quad_prefetch<S, RY>(sd[cur ^ 1], s_local[cur ^ 1], qsm + (cur ^ 1) * QPLANE, tbuf, parity);
         cp_async_commit();

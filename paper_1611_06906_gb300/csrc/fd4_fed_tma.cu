@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
     __shared__ ImgDesc sd[NU];            // tile j's descriptor in sd[j % NU]
     __shared__ int s_local[NU];
     __shared__ int abort_flag;
+    __shared__ TileCache tcache;
     const int tid = threadIdx.x;
     const bool from_table = I.table != nullptr;
     for (int i = tid; i < (NU + 2) * TPLANE; i += TNT) planes[i] = 0.0f;  // the ring rows stay zero
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
 #pragma unroll
         for (int i = 0; i < 8; ++i) stau[i] = taus.t[i];
         abort_flag = 0;
+        tc_reset(tcache);
         for (int i = 0; i < kAhead; ++i) tma_mbar_init(&mbar[i]);
     }
     const int q = tid & 15, ry = tid >> 4;
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
         for (int j = 0; j < kAhead; ++j) {
             const int tj = blockIdx.x + j * G;
             if (tj >= ntiles) break;
-            find_tile(I, SHAPE, tj, sd[j], s_local[j]);
+            find_tile_cached(I, SHAPE, tj, tcache, sd[j], s_local[j]);
             tma_issue<S>(sd[j], s_local[j], one, from_table, parity, planes + j * TPLANE, base + j * kTBytes,
                          &mbar[j]);
         }
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
         const int ta = t + kAhead * G;  // tile j + kAhead: into box bj, plane (j + kAhead) % NU
         if (tid == 0 && ta < ntiles) {
             const int ua = (j + kAhead) % NU;
-            find_tile(I, SHAPE, ta, sd[ua], s_local[ua]);
+            find_tile_cached(I, SHAPE, ta, tcache, sd[ua], s_local[ua]);
             tma_issue<S>(sd[ua], s_local[ua], one, from_table, parity, planes + ua * TPLANE, base + bj * kTBytes,
                          &mbar[bj]);
         }

@@ -157,6 +157,45 @@ __device__ __forceinline__ float det2_sym(float a, float b, float d)
     return fmaf(a, d, -bb) + err;
 }
 
+// Per-block cache of the last image find_tile_cached resolved: its tile range
+// [lo, hi) for one tile shape and its descriptor.  Kept in shared memory;
+// tc_reset empties it.
+struct TileCache {
+    int lo, hi;
+    ImgDesc d;
+};
+__device__ __forceinline__ void tc_reset(TileCache &c)
+{
+    c.lo = 1;
+    c.hi = 0;
+}
+
+// Thread 0 of a block: as find_tile, but a persistent block's tiles (t, t +
+// gridDim.x, ...) advance through the batch in image order, so most look-ups
+// stay within the cached image and need no search of the descriptor table in
+// global memory (each step of which is a dependent load).
+__device__ __forceinline__ void find_tile_cached(const Imgs &I, int shape, int t, TileCache &c, ImgDesc &out,
+                                                 int &local)
+{
+    if (I.table == nullptr || I.list) {
+        find_tile(I, shape, t, out, local);
+        return;
+    }
+    if (t < c.lo || t >= c.hi) {
+        int lo = 0, hi = I.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (I.table[mid].t0[shape] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        c.d = I.table[lo];
+        c.lo = c.d.t0[shape];
+        c.hi = lo + 1 < I.n ? I.table[lo + 1].t0[shape] : 0x7fffffff;
+    }
+    out = c.d;
+    local = t - c.lo;
+}
+
 // Number of tiles a persistent kernel walks: the host count, or the device
 // count of a tile list (8 small tiles per listed sweep tile).
 __device__ __forceinline__ int tile_count(const Imgs &I, int shape)

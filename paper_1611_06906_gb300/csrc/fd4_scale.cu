@@ -361,11 +361,13 @@ __global__ void __launch_bounds__(256) k_select_argmax(Imgs I, int K, float c_us
 {
     __shared__ ImgDesc sd;
     __shared__ int s_local;
+    __shared__ TileCache tcache;
+    if (threadIdx.x == 0) tc_reset(tcache);
     const int tid = threadIdx.x;
     const int ntiles = tile_count(I, SHAPE_SMALL);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         __syncthreads();
-        if (tid == 0) find_tile(I, SHAPE_SMALL, t, sd, s_local);
+        if (tid == 0) find_tile_cached(I, SHAPE_SMALL, t, tcache, sd, s_local);
         __syncthreads();
         const int tiles_x = (sd.w + 31) / 32;
         const int x = (s_local % tiles_x) * 32 + (tid & 31), y = (s_local / tiles_x) * 8 + (tid >> 5);
@@ -422,6 +424,8 @@ __global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, f
     float4 *srow = fsm4 + ROWS * COLS;   // ROWS x FX: smoothed along x
     __shared__ ImgDesc sd;
     __shared__ int s_local;
+    __shared__ TileCache tcache;
+    if (threadIdx.x == 0) tc_reset(tcache);
     const int tid = threadIdx.x;
     float wr[2 * r + 1];
 #pragma unroll
@@ -429,7 +433,7 @@ __global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, f
     const int ntiles = tile_count(I, SHAPE_SWEEP);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         __syncthreads();
-        if (tid == 0) find_tile(I, SHAPE_SWEEP, t, sd, s_local);
+        if (tid == 0) find_tile_cached(I, SHAPE_SWEEP, t, tcache, sd, s_local);
         __syncthreads();
         const int w = sd.w, h = sd.h, pitch = sd.pitch;
         const int tiles_x = (w + FX - 1) / FX;

@@ -177,12 +177,16 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
     __shared__ int wtot[ST_NT / 32 + 1];
     __shared__ ImgDesc sd[2];
     __shared__ int s_local[2];
+    __shared__ TileCache tcache;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, s = sa.s;
     float bmax = 0.0f;  // selection: max S^2 of this thread's pixels in the current segment
     int t = blockIdx.x;
     if (t >= I.tiles) return;
-    if (tid == 0) find_tile(I, SHAPE_SEG, t, sd[0], s_local[0]);
+    if (tid == 0) {
+        tc_reset(tcache);
+        find_tile_cached(I, SHAPE_SEG, t, tcache, sd[0], s_local[0]);
+    }
     __syncthreads();
     int cur = 0, i = 0, buf = 0;
     {
@@ -224,7 +228,8 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
         __syncthreads();  // this piece's rows have landed; the previous chunk's column pass is done
         // the block's next segment: its slot held the previous segment, whose last
         // readers (the column pass above) are past this barrier
-        if (i == 0 && tid == 0 && t + G < I.tiles) find_tile(I, SHAPE_SEG, t + G, sd[cur ^ 1], s_local[cur ^ 1]);
+        if (i == 0 && tid == 0 && t + G < I.tiles)
+            find_tile_cached(I, SHAPE_SEG, t + G, tcache, sd[cur ^ 1], s_local[cur ^ 1]);
         if (i >= NP0) {
             // keep buffer rows ST_CH .. ST_CH + 2R - 1 as rows 0 .. 2R - 1, in
             // pieces that never overlap their own source
