@@ -5,12 +5,14 @@
 // Each tile's region of u and of the tensor field arrives by two tensor-map
 // copies (cp.async.bulk.tensor) that one thread issues and an mbarrier counts
 // in bytes: the hardware generates the addresses, zero-fills what lies outside
-// the image, and the next tile's copies overlap the current tile's steps.  Both
-// boxes land dense (u: 64 rows of 256 B, tensor: 64 rows of 1 KB); the threads
-// read their quads' tensor values in a lane-rotated order so that the 16-byte
-// reads of a quarter-warp hit distinct banks.  Per-thread 16-byte copies (the
-// cp.async kernels of fd4_fed.cu) reach about half of the HBM bandwidth on this
-// staging; the bulk copies stream it.
+// the image, and the copies of the next two tiles overlap the current tile's
+// steps.  Both boxes land dense (u: 64 rows of 256 B, tensor: 64 rows of 1 KB);
+// the threads read their quads' tensor values in a lane-rotated order so that
+// the 16-byte reads of a quarter-warp hit distinct banks.  The issuing thread
+// also records the tile's geometry in shared memory, so the other threads do
+// no per-tile integer division.  Per-thread 16-byte copies
+// (the cp.async kernels of fd4_fed.cu) reach about half of the HBM bandwidth on
+// this staging; the bulk copies stream it.
 #include <cuda.h>
 
 #include <cstdint>
@@ -106,15 +108,25 @@ __device__ __forceinline__ void fence_tensormap_acquire(const void *map)
 template <int S>
 constexpr int tma_shape() { return S == 2 ? SHAPE_Q64_2 : SHAPE_Q64_4; }
 
+// Geometry of a staged tile, computed once by the thread that issues its copies.
+struct TileGeo {
+    int gx0, gy0;   // region origin in the image (gx0: a multiple of 4)
+    int interior;   // the region lies inside the image
+};
+
 // Thread 0: the copies of the region of tile `local` of image d into u_dst (plane
-// row 1) and the tensor box.
+// row 1) and the tensor box; the tile's geometry into *g.
 template <int S>
 __device__ __forceinline__ void tma_issue(const ImgDesc &d, int local, const TmaMaps &one, bool from_table,
-                                          int parity, float *u_dst, void *t_dst, uint64_t *mbar)
+                                          int parity, float *u_dst, void *t_dst, uint64_t *mbar, TileGeo *g)
 {
     constexpr int H = 2 * S, TO = TR - 2 * H;
     const int tiles_x = (d.w + TO - 1) / TO;
-    const int gx0 = (local % tiles_x) * TO - H, gy0 = (local / tiles_x) * TO - H;  // gx0: a multiple of 4
+    const int ty = local / tiles_x;
+    const int gx0 = (local - ty * tiles_x) * TO - H, gy0 = ty * TO - H;
+    g->gx0 = gx0;
+    g->gy0 = gy0;
+    g->interior = gx0 >= 0 && gy0 >= 0 && gx0 + TR <= d.w && gy0 + TR <= d.h;
     const TmaMaps *m = from_table ? reinterpret_cast<const TmaMaps *>(d.maps) : &one;
     const CUtensorMap *mu = parity ? &m->tmp : &m->u;
     if (from_table) {
@@ -141,6 +153,7 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
     __shared__ float stau[8];
     __shared__ ImgDesc sd[NU];            // tile j's descriptor in sd[j % NU]
     __shared__ int s_local[NU];
+    __shared__ TileGeo sgeo[NU];
     __shared__ int abort_flag;
     __shared__ TileCache tcache;
     const int tid = threadIdx.x;
@@ -155,6 +168,8 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
     }
     const int q = tid & 15, ry = tid >> 4;
     const int off = (ry + 1) * TSW + 4 * q;  // this quad in a plane
+    // this quad lies in the exact interior of every tile: rows and columns H .. H + TO - 1
+    const bool writes = ry >= H && ry < H + TO && 4 * q >= H && 4 * q < H + TO;
     const int ntiles = I.tiles, G = gridDim.x;
     __syncthreads();
     // prologue: the copies of the block's first kAhead tiles
@@ -164,7 +179,7 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
             if (tj >= ntiles) break;
             find_tile_cached(I, SHAPE, tj, tcache, sd[j], s_local[j]);
             tma_issue<S>(sd[j], s_local[j], one, from_table, parity, planes + j * TPLANE, base + j * kTBytes,
-                         &mbar[j]);
+                         &mbar[j], &sgeo[j]);
         }
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += G, ++j) {
@@ -173,12 +188,9 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
         __syncthreads();  // tile j has landed; every warp is past tile j - 1
         if (abort_flag) break;
         const ImgDesc &d = sd[uj];
-        const int w = d.w, h = d.h, pitch = d.pitch;
-        float *uout = parity ? d.u : d.tmp;
-        const int tiles_x = (w + TO - 1) / TO;
-        const int gx0 = (s_local[uj] % tiles_x) * TO - H, gy0 = (s_local[uj] / tiles_x) * TO - H;
-        const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + TR <= w && gy0 + TR <= h;
-        const int gx = gx0 + 4 * q, gy = gy0 + ry;
+        const int w = d.w, h = d.h;
+        const int gx = sgeo[uj].gx0 + 4 * q, gy = sgeo[uj].gy0 + ry;
+        const bool interior = sgeo[uj].interior != 0;
         float *su = planes + uj * TPLANE;
         const float4 u0 = *reinterpret_cast<const float4 *>(su + off);
         unsigned mask = 0u;
@@ -195,7 +207,9 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
         {
             // Read i of lane q takes pixel (i + r) mod 4 of its quad, r = (q / 2) mod 4:
             // the 8 lanes of a quarter-warp then address 8 distinct 16-byte bank
-            // groups (quads are 64 bytes apart).  The values are rotated back by r.
+            // groups (quads are 64 bytes apart), so the tile-start reads of all
+            // threads do not queue up in the shared-memory pipe.  The values are
+            // rotated back by r.
             const int r = (q >> 1) & 3;
             const float4 *tq =
                 reinterpret_cast<const float4 *>(base + bj * kTBytes + (size_t)ry * (TR * 16)) + 4 * q;
@@ -230,14 +244,14 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
             const int ua = (j + kAhead) % NU;
             find_tile_cached(I, SHAPE, ta, tcache, sd[ua], s_local[ua]);
             tma_issue<S>(sd[ua], s_local[ua], one, from_table, parity, planes + ua * TPLANE, base + bj * kTBytes,
-                         &mbar[bj]);
+                         &mbar[bj], &sgeo[ua]);
         }
 
         const float4 un = interior ? quad_steps<false, TSW>(su, sxy, syy, stau, taus.n, off, k, mask, u0)
                                    : quad_steps<true, TSW>(su, sxy, syy, stau, taus.n, off, k, mask, u0);
         // the exact interior: rows H .. H + TO - 1, columns H .. H + TO - 1 (whole quads)
-        if (ry >= H && ry < H + TO && 4 * q >= H && 4 * q < H + TO && gy < h) {
-            float *dst = uout + (size_t)gy * pitch + gx;
+        if (writes && gy < h) {
+            float *dst = (parity ? d.u : d.tmp) + (size_t)gy * d.pitch + gx;
             if (gx + 3 < w) {
                 *reinterpret_cast<float4 *>(dst) = un;
             } else {
