@@ -412,38 +412,68 @@ constexpr int FX = 32, FY = 64, FNT_T = 256;
 template <int r>
 constexpr size_t finish_smem_bytes()
 {
-    return sizeof(float4) * ((size_t)(FY + 2 * r) * (FX + 2 * r) + (size_t)(FY + 2 * r) * FX);
+    return sizeof(float4) * ((size_t)2 * (FY + 2 * r) * (FX + 2 * r) + (size_t)(FY + 2 * r) * FX);
 }
 
+// cp.async (16 bytes = one pixel of N) of a tile's N region with its mirrored halo.
+template <int r>
+__device__ __forceinline__ void finish_stage(const ImgDesc &d, int local, float4 *dst)
+{
+    constexpr int ROWS = FY + 2 * r, COLS = FX + 2 * r;
+    const int w = d.w, h = d.h, pitch = d.pitch;
+    const int tiles_x = (w + FX - 1) / FX;
+    const int ty = local / tiles_x;
+    const int x0 = (local - ty * tiles_x) * FX, y0 = ty * FY;
+    for (int i = threadIdx.x; i < ROWS * COLS; i += FNT_T) {
+        const int ry = i / COLS, rx = i - ry * COLS;
+        const float4 *src = d.nfield + (size_t)mirror(y0 - r + ry, h) * pitch + mirror(x0 - r + rx, w);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst + i)),
+                     "l"(src)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// The next tile's region is copied (cp.async, double buffer) while the current
+// tile is smoothed and decomposed.
 template <int r>
 __global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, float lambda, int mode)
 {
     constexpr int ROWS = FY + 2 * r, COLS = FX + 2 * r;
     extern __shared__ __align__(16) float4 fsm4[];
-    float4 *sin_ = fsm4;                 // ROWS x COLS: N with the mirrored halo
-    float4 *srow = fsm4 + ROWS * COLS;   // ROWS x FX: smoothed along x
-    __shared__ ImgDesc sd;
-    __shared__ int s_local;
+    // two ROWS x COLS buffers: N with the mirrored halo; then ROWS x FX: smoothed along x
+    float4 *srow = fsm4 + 2 * ROWS * COLS;
+    __shared__ ImgDesc sdb[2];
+    __shared__ int s_localb[2];
     __shared__ TileCache tcache;
-    if (threadIdx.x == 0) tc_reset(tcache);
     const int tid = threadIdx.x;
     float wr[2 * r + 1];
 #pragma unroll
     for (int k = 0; k <= 2 * r; ++k) wr[k] = taps.w0[k];
     const int ntiles = tile_count(I, SHAPE_SWEEP);
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int t = blockIdx.x, cur = 0;
+    if (t >= ntiles) return;
+    if (tid == 0) {
+        tc_reset(tcache);
+        find_tile_cached(I, SHAPE_SWEEP, t, tcache, sdb[0], s_localb[0]);
+    }
+    __syncthreads();
+    finish_stage<r>(sdb[0], s_localb[0], fsm4);
+    for (; t < ntiles; t += gridDim.x) {
+        const int tn = t + gridDim.x;
+        __syncthreads();  // every thread is done with the previous tile (its slot and buffer)
+        if (tid == 0 && tn < ntiles) find_tile_cached(I, SHAPE_SWEEP, tn, tcache, sdb[cur ^ 1], s_localb[cur ^ 1]);
         __syncthreads();
-        if (tid == 0) find_tile_cached(I, SHAPE_SWEEP, t, tcache, sd, s_local);
-        __syncthreads();
+        if (tn < ntiles) finish_stage<r>(sdb[cur ^ 1], s_localb[cur ^ 1], fsm4 + (cur ^ 1) * ROWS * COLS);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();  // this tile's region has landed
+        const ImgDesc &sd = sdb[cur];
+        const int s_local = s_localb[cur];
+        const float4 *sin_ = fsm4 + cur * ROWS * COLS;
         const int w = sd.w, h = sd.h, pitch = sd.pitch;
         const int tiles_x = (w + FX - 1) / FX;
         const int x0 = (s_local % tiles_x) * FX, y0 = (s_local / tiles_x) * FY;
-        const float4 *nf = sd.nfield;
-        for (int i = tid; i < ROWS * COLS; i += FNT_T) {
-            const int ry = i / COLS, rx = i - ry * COLS;
-            sin_[i] = nf[(size_t)mirror(y0 - r + ry, h) * pitch + mirror(x0 - r + rx, w)];
-        }
-        __syncthreads();
         for (int i = tid; i < ROWS * FX; i += FNT_T) {
             const int ry = i / FX, rx = i - ry * FX;
             float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -496,7 +526,9 @@ __global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, f
             sd.tensor[(size_t)gy * pitch + gx] =
                 make_float4(c2, s2, pm_mu(nu1, lambda, mode), pm_mu(nu2, lambda, mode));
         }
+        cur ^= 1;
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 template <int r>
