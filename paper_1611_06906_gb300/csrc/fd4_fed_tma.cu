@@ -16,6 +16,7 @@
 #include <cuda.h>
 
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -139,10 +140,14 @@ __device__ __forceinline__ void tma_issue(const ImgDesc &d, int local, const Tma
     tma_load_2d(t_dst, &m->ten, 4 * gx0, gy0, mbar);      // x: 16 gx0 bytes
 }
 
-template <int S>
-__global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int parity, const __grid_constant__ TmaMaps one)
+// NQ quads per thread: TNT / NQ threads, thread (row ry, quad column q) owns the
+// quads of rows ry + i TR / NQ, i < NQ.  With NQ = 2 a block barrier spans 16
+// warps instead of 32 and each thread has two independent quads in flight.
+template <int S, int NQ>
+__global__ void __launch_bounds__(TNT / NQ, 1) k_fed_tma(Imgs I, StepTaus taus, int parity,
+                                                        const __grid_constant__ TmaMaps one)
 {
-    constexpr int H = 2 * S, TO = TR - 2 * H, SHAPE = tma_shape<S>(), NU = kAhead + 1;
+    constexpr int H = 2 * S, TO = TR - 2 * H, SHAPE = tma_shape<S>(), NU = kAhead + 1, NT = TNT / NQ;
     static_assert(TO % 4 == 0 && H % 4 == 0, "whole quads in the exact interior");
     extern __shared__ unsigned char tma_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)tma_raw + 1023) & ~(uintptr_t)1023);
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
     __shared__ TileCache tcache;
     const int tid = threadIdx.x;
     const bool from_table = I.table != nullptr;
-    for (int i = tid; i < (NU + 2) * TPLANE; i += TNT) planes[i] = 0.0f;  // the ring rows stay zero
+    for (int i = tid; i < (NU + 2) * TPLANE; i += NT) planes[i] = 0.0f;  // the ring rows stay zero
     if (tid == 0) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) stau[i] = taus.t[i];
@@ -166,10 +171,16 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
         tc_reset(tcache);
         for (int i = 0; i < kAhead; ++i) tma_mbar_init(&mbar[i]);
     }
-    const int q = tid & 15, ry = tid >> 4;
-    const int off = (ry + 1) * TSW + 4 * q;  // this quad in a plane
-    // this quad lies in the exact interior of every tile: rows and columns H .. H + TO - 1
-    const bool writes = ry >= H && ry < H + TO && 4 * q >= H && 4 * q < H + TO;
+    const int q = tid & 15, ry0 = tid >> 4;
+    int off[NQ], rowq[NQ];
+    bool writes[NQ];
+#pragma unroll
+    for (int qd = 0; qd < NQ; ++qd) {
+        rowq[qd] = ry0 + qd * (TR / NQ);
+        off[qd] = (rowq[qd] + 1) * TSW + 4 * q;  // this quad in a plane
+        // the quad lies in the exact interior of every tile: rows and columns H .. H + TO - 1
+        writes[qd] = rowq[qd] >= H && rowq[qd] < H + TO && 4 * q >= H && 4 * q < H + TO;
+    }
     const int ntiles = I.tiles, G = gridDim.x;
     __syncthreads();
     // prologue: the copies of the block's first kAhead tiles
@@ -189,22 +200,26 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
         if (abort_flag) break;
         const ImgDesc &d = sd[uj];
         const int w = d.w, h = d.h;
-        const int gx = sgeo[uj].gx0 + 4 * q, gy = sgeo[uj].gy0 + ry;
+        const int gx = sgeo[uj].gx0 + 4 * q;
         const bool interior = sgeo[uj].interior != 0;
         float *su = planes + uj * TPLANE;
-        const float4 u0 = *reinterpret_cast<const float4 *>(su + off);
-        unsigned mask = 0u;
-        if (!interior) {
+        float4 uq[NQ];
+        unsigned mask[NQ];
+        QuadCoef k[NQ];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int x = gx + i;
-                mask |= (x >= 0 && x < w && gy >= 0 && gy < h ? 1u : 0u) << i;
-                mask |= (x >= 1 && x <= w - 2 ? 1u : 0u) << (4 + i);
+        for (int qd = 0; qd < NQ; ++qd) {
+            const int gy = sgeo[uj].gy0 + rowq[qd];
+            uq[qd] = *reinterpret_cast<const float4 *>(su + off[qd]);
+            mask[qd] = 0u;
+            if (!interior) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int x = gx + i;
+                    mask[qd] |= (x >= 0 && x < w && gy >= 0 && gy < h ? 1u : 0u) << i;
+                    mask[qd] |= (x >= 1 && x <= w - 2 ? 1u : 0u) << (4 + i);
+                }
+                mask[qd] |= (gy >= 1 && gy <= h - 2 ? 1u : 0u) << 8;
             }
-            mask |= (gy >= 1 && gy <= h - 2 ? 1u : 0u) << 8;
-        }
-        QuadCoef k;
-        {
             // Read i of lane q takes pixel (i + r) mod 4 of its quad, r = (q / 2) mod 4:
             // the 8 lanes of a quarter-warp then address 8 distinct 16-byte bank
             // groups (quads are 64 bytes apart), so the tile-start reads of all
@@ -212,7 +227,7 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
             // rotated back by r.
             const int r = (q >> 1) & 3;
             const float4 *tq =
-                reinterpret_cast<const float4 *>(base + bj * kTBytes + (size_t)ry * (TR * 16)) + 4 * q;
+                reinterpret_cast<const float4 *>(base + bj * kTBytes + (size_t)rowq[qd] * (TR * 16)) + 4 * q;
             float4 v[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) v[i] = tq[(i + r) & 3];
@@ -233,10 +248,10 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
                 pp[i] = 0.5f * (tt.z + tt.w);
                 qq[i] = 0.5f * (tt.z - tt.w);
             }
-            k.c = make_float4(cc[0], cc[1], cc[2], cc[3]);
-            k.s = make_float4(ss[0], ss[1], ss[2], ss[3]);
-            k.p = make_float4(pp[0], pp[1], pp[2], pp[3]);
-            k.q = make_float4(qq[0], qq[1], qq[2], qq[3]);
+            k[qd].c = make_float4(cc[0], cc[1], cc[2], cc[3]);
+            k[qd].s = make_float4(ss[0], ss[1], ss[2], ss[3]);
+            k[qd].p = make_float4(pp[0], pp[1], pp[2], pp[3]);
+            k[qd].q = make_float4(qq[0], qq[1], qq[2], qq[3]);
         }
         __syncthreads();  // tensor box bj is read; u plane (j + kAhead) % NU was last used by tile j - 1
         const int ta = t + kAhead * G;  // tile j + kAhead: into box bj, plane (j + kAhead) % NU
@@ -247,17 +262,22 @@ __global__ void __launch_bounds__(TNT, 1) k_fed_tma(Imgs I, StepTaus taus, int p
                          &mbar[bj], &sgeo[ua]);
         }
 
-        const float4 un = interior ? quad_steps<false, TSW>(su, sxy, syy, stau, taus.n, off, k, mask, u0)
-                                   : quad_steps<true, TSW>(su, sxy, syy, stau, taus.n, off, k, mask, u0);
+        if (interior) quad_steps_n<false, TSW, NQ>(su, sxy, syy, stau, taus.n, off, k, mask, uq);
+        else quad_steps_n<true, TSW, NQ>(su, sxy, syy, stau, taus.n, off, k, mask, uq);
         // the exact interior: rows H .. H + TO - 1, columns H .. H + TO - 1 (whole quads)
-        if (writes && gy < h) {
-            float *dst = (parity ? d.u : d.tmp) + (size_t)gy * d.pitch + gx;
-            if (gx + 3 < w) {
-                *reinterpret_cast<float4 *>(dst) = un;
-            } else {
-                if (gx < w) dst[0] = un.x;
-                if (gx + 1 < w) dst[1] = un.y;
-                if (gx + 2 < w) dst[2] = un.z;
+#pragma unroll
+        for (int qd = 0; qd < NQ; ++qd) {
+            const int gy = sgeo[uj].gy0 + rowq[qd];
+            if (writes[qd] && gy < h) {
+                float *dst = (parity ? d.u : d.tmp) + (size_t)gy * d.pitch + gx;
+                const float4 un = uq[qd];
+                if (gx + 3 < w) {
+                    *reinterpret_cast<float4 *>(dst) = un;
+                } else {
+                    if (gx < w) dst[0] = un.x;
+                    if (gx + 1 < w) dst[1] = un.y;
+                    if (gx + 2 < w) dst[2] = un.z;
+                }
             }
         }
     }
@@ -332,14 +352,14 @@ int make_maps(const ImgDesc &d, TmaMaps *m)
     return 0;
 }
 
-template <int S>
+template <int S, int NQ>
 int set_tma_smem()
 {
     static int attr_dev = -1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
     if (attr_dev != dev) {
-        if (cudaFuncSetAttribute(k_fed_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem) !=
+        if (cudaFuncSetAttribute(k_fed_tma<S, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem) !=
             cudaSuccess)
             return 1;
         attr_dev = dev;
@@ -347,11 +367,31 @@ int set_tma_smem()
     return 0;
 }
 
+// Quads per thread of the TMA kernel: 2 (512 threads, the default) or
+// FD4_FED_QUADS=1 (1024 threads).
+int tma_quads()
+{
+    const char *e = getenv("FD4_FED_QUADS");
+    return (e && e[0] == '1') ? 1 : 2;
+}
+
+template <int S, int NQ>
+int launch_tma_k(const Imgs &I, const StepTaus &t, int parity, const TmaMaps &one, cudaStream_t st)
+{
+    if (set_tma_smem<S, NQ>()) return 1;
+    const int grid = persistent_grid((const void *)k_fed_tma<S, NQ>, TNT / NQ, kTmaSmem, I.tiles);
+    k_fed_tma<S, NQ><<<grid, TNT / NQ, kTmaSmem, st>>>(I, t, parity, one);
+    return cudaGetLastError() != cudaSuccess;
+}
+
 }  // namespace
 
 size_t tma_maps_bytes() { return sizeof(TmaMaps); }
 
-int prepare_tma_kernels() { return set_tma_smem<2>() || set_tma_smem<4>(); }
+int prepare_tma_kernels()
+{
+    return set_tma_smem<2, 1>() || set_tma_smem<4, 1>() || set_tma_smem<2, 2>() || set_tma_smem<4, 2>();
+}
 
 // Writes the maps of the n descriptors (their maps fields point into a device
 // table) with kernels on st.
@@ -374,7 +414,6 @@ int launch_put_maps(const ImgDesc *h_descs, int n, void *d_table, cudaStream_t s
 template <int S>
 int launch_fed_tma(const HostBatch &B, const double *tau, int k, int parity, cudaStream_t st)
 {
-    if (set_tma_smem<S>()) return 1;
     StepTaus t{};
     t.n = k;
     for (int i = 0; i < k; ++i) t.t[i] = (float)tau[i];
@@ -383,9 +422,7 @@ int launch_fed_tma(const HostBatch &B, const double *tau, int k, int parity, cud
     TmaMaps one;
     memset(&one, 0, sizeof(one));
     if (!I.table && make_maps(I.one, &one)) return 1;
-    const int grid = persistent_grid((const void *)k_fed_tma<S>, TNT, kTmaSmem, I.tiles);
-    k_fed_tma<S><<<grid, TNT, kTmaSmem, st>>>(I, t, parity, one);
-    return cudaGetLastError() != cudaSuccess;
+    return tma_quads() == 2 ? launch_tma_k<S, 2>(I, t, parity, one, st) : launch_tma_k<S, 1>(I, t, parity, one, st);
 }
 
 template int launch_fed_tma<2>(const HostBatch &, const double *, int, int, cudaStream_t);

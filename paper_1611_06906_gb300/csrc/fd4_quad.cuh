@@ -82,48 +82,68 @@ __device__ __forceinline__ void quad_T(const float (&a)[6], const float (&b)[6],
     Tyy = make_float4(ryy[0], ryy[1], ryy[2], ryy[3]);
 }
 
-// S steps of one staged region; uo: this quad's u on entry, returned updated.
-// Two block barriers per step: T is complete before the update reads it, the
-// update is complete before the next T phase reads u.  The first T phase reads
-// the staged region (published by the tile's barrier); after the last update
-// no barrier is needed before the next tile's.
+// S steps of one staged region for NQ quads per thread; uo: the quads' u on
+// entry, updated in place.  Two block barriers per step: T is complete before
+// the update reads it, the update is complete before the next T phase reads u.
+// The first T phase reads the staged region (published by the tile's
+// barrier); after the last update no barrier is needed before the next tile's.
+template <bool BOUNDARY, int SW, int NQ>
+__device__ __forceinline__ void quad_steps_n(float *su, float *sxy, float *syy, const float *stau, int nsteps,
+                                             const int (&off)[NQ], const QuadCoef (&k)[NQ],
+                                             const unsigned (&mask)[NQ], float4 (&uo)[NQ])
+{
+    for (int l = 0; l < nsteps; ++l) {
+        if (l > 0) __syncthreads();
+        float4 txx[NQ], tyy[NQ];
+#pragma unroll
+        for (int qd = 0; qd < NQ; ++qd) {
+            float a[6], b[6], c[6];
+            quad_ext(*reinterpret_cast<const float4 *>(su + off[qd] - SW), a);
+            quad_ext(uo[qd], b);
+            quad_ext(*reinterpret_cast<const float4 *>(su + off[qd] + SW), c);
+            float4 txy;
+            quad_T<BOUNDARY>(a, b, c, k[qd], mask[qd], txx[qd], txy, tyy[qd]);
+            *reinterpret_cast<float4 *>(sxy + off[qd]) = txy;
+            *reinterpret_cast<float4 *>(syy + off[qd]) = tyy[qd];
+        }
+        __syncthreads();
+        const float tau = stau[l];
+#pragma unroll
+        for (int qd = 0; qd < NQ; ++qd) {
+            // u -= tau (Lxx' Txx + Lyy' Tyy + 2 Lxy' Txy)
+            float X[6], Zu[6], Zd[6], Yu[4], Yc[4], Yd[4], U[4];
+            quad_ext(txx[qd], X);
+            quad_ext(*reinterpret_cast<const float4 *>(sxy + off[qd] - SW), Zu);
+            quad_ext(*reinterpret_cast<const float4 *>(sxy + off[qd] + SW), Zd);
+            f4_to(*reinterpret_cast<const float4 *>(syy + off[qd] - SW), Yu);
+            f4_to(tyy[qd], Yc);
+            f4_to(*reinterpret_cast<const float4 *>(syy + off[qd] + SW), Yd);
+            f4_to(uo[qd], U);
+            float r[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float div = fmaf(-2.0f, X[i + 1], X[i] + X[i + 2]) + fmaf(-2.0f, Yc[i], Yu[i] + Yd[i]) +
+                                  0.5f * ((Zd[i + 2] + Zu[i]) - (Zu[i + 2] + Zd[i]));
+                r[i] = fmaf(-tau, div, U[i]);
+                if (BOUNDARY && !((mask[qd] >> i) & 1u)) r[i] = U[i];
+            }
+            uo[qd] = make_float4(r[0], r[1], r[2], r[3]);
+            *reinterpret_cast<float4 *>(su + off[qd]) = uo[qd];
+        }
+    }
+}
+
+// One quad per thread.
 template <bool BOUNDARY, int SW>
 __device__ __forceinline__ float4 quad_steps(float *su, float *sxy, float *syy, const float *stau, int nsteps,
                                              int off, const QuadCoef &k, unsigned mask, float4 uo)
 {
-    for (int l = 0; l < nsteps; ++l) {
-        if (l > 0) __syncthreads();
-        float a[6], b[6], c[6];
-        quad_ext(*reinterpret_cast<const float4 *>(su + off - SW), a);
-        quad_ext(uo, b);
-        quad_ext(*reinterpret_cast<const float4 *>(su + off + SW), c);
-        float4 txx, txy, tyy;
-        quad_T<BOUNDARY>(a, b, c, k, mask, txx, txy, tyy);
-        *reinterpret_cast<float4 *>(sxy + off) = txy;
-        *reinterpret_cast<float4 *>(syy + off) = tyy;
-        __syncthreads();
-        // u -= tau (Lxx' Txx + Lyy' Tyy + 2 Lxy' Txy)
-        float X[6], Zu[6], Zd[6], Yu[4], Yc[4], Yd[4];
-        quad_ext(txx, X);
-        quad_ext(*reinterpret_cast<const float4 *>(sxy + off - SW), Zu);
-        quad_ext(*reinterpret_cast<const float4 *>(sxy + off + SW), Zd);
-        f4_to(*reinterpret_cast<const float4 *>(syy + off - SW), Yu);
-        f4_to(tyy, Yc);
-        f4_to(*reinterpret_cast<const float4 *>(syy + off + SW), Yd);
-        const float tau = stau[l];
-        float r[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float div = fmaf(-2.0f, X[i + 1], X[i] + X[i + 2]) + fmaf(-2.0f, Yc[i], Yu[i] + Yd[i]) +
-                              0.5f * ((Zd[i + 2] + Zu[i]) - (Zu[i + 2] + Zd[i]));
-            r[i] = fmaf(-tau, div, b[i + 1]);
-            if (BOUNDARY && !((mask >> i) & 1u)) r[i] = b[i + 1];
-        }
-        uo = make_float4(r[0], r[1], r[2], r[3]);
-        *reinterpret_cast<float4 *>(su + off) = uo;
-    }
-    return uo;
+    const int o[1] = {off};
+    const QuadCoef kk[1] = {k};
+    const unsigned m[1] = {mask};
+    float4 u[1] = {uo};
+    quad_steps_n<BOUNDARY, SW, 1>(su, sxy, syy, stau, nsteps, o, kk, m, u);
+    return u[0];
 }
-
 
 }  // namespace fd4

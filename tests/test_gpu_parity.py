@@ -62,10 +62,11 @@ def _tensor_to_device(t, w):
     return buf
 
 
-@pytest.fixture(params=[(0, 3, 64), (2, 3, 64), (2, 2, 64), (2, 2, 32), (2, 1, 32), (2, 0, 32), (3, 3, 64),
-                        (4, 3, 64), (4, 2, 64), (4, 2, 32), (4, 1, 32), (4, 0, 32)],
-                ids=["step", "fuse2-tma", "fuse2-quad64", "fuse2-quad32", "fuse2-prefetch", "fuse2-plain",
-                     "fuse3", "fuse4-tma", "fuse4-quad64", "fuse4-quad32", "fuse4-prefetch", "fuse4-plain"])
+@pytest.fixture(params=[(0, 3, 64), (2, 3, 64), (2, 3, 64, 2), (2, 2, 64), (2, 2, 32), (2, 1, 32), (2, 0, 32),
+                        (3, 3, 64), (4, 3, 64), (4, 3, 64, 2), (4, 2, 64), (4, 2, 32), (4, 1, 32), (4, 0, 32)],
+                ids=["step", "fuse2-tma", "fuse2-tma-2quads", "fuse2-quad64", "fuse2-quad32", "fuse2-prefetch",
+                     "fuse2-plain", "fuse3", "fuse4-tma", "fuse4-tma-2quads", "fuse4-quad64", "fuse4-quad32",
+                     "fuse4-prefetch", "fuse4-plain"])
 def fed_variant(request, monkeypatch):
     """FED kernel variant: one launch per step, or 2..4 steps fused per launch
     (quad kernel with TMA staging, quad kernel with cp.async staging on 64 x 64
@@ -74,6 +75,7 @@ def fed_variant(request, monkeypatch):
     monkeypatch.setenv("FD4_FED_FUSE", str(request.param[0]))
     monkeypatch.setenv("FD4_FED_PIPELINE", str(request.param[1]))
     monkeypatch.setenv("FD4_FED_QUAD_ROWS", str(request.param[2]))
+    monkeypatch.setenv("FD4_FED_QUADS", str(request.param[3] if len(request.param) > 3 else 1))  # 1: one quad per thread
     return request.param
 
 
