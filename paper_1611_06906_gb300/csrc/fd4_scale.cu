@@ -395,10 +395,12 @@ __global__ void __launch_bounds__(256) k_select_argmax(Imgs I, int K, float c_us
     }
 }
 
-__device__ __forceinline__ float pm_mu(float nu, float lambda, int mode)
+// Perona-Malik diffusivity 1 / (1 + nu^2 / lambda^2) with ridge/valley gating;
+// inv_lambda = 1 / lambda.
+__device__ __forceinline__ float pm_mu(float nu, float inv_lambda, int mode)
 {
     if ((mode == FD4_RIDGE && nu >= 0.0f) || (mode == FD4_VALLEY && nu <= 0.0f)) return 1.0f;
-    const float q = nu / lambda;
+    const float q = nu * inv_lambda;
     return 1.0f / fmaf(q, q, 1.0f);
 }
 
@@ -450,6 +452,7 @@ __global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, f
     float wr[2 * r + 1];
 #pragma unroll
     for (int k = 0; k <= 2 * r; ++k) wr[k] = taps.w0[k];
+    const float inv_lambda = 1.0f / lambda;
     const int ntiles = tile_count(I, SHAPE_SWEEP);
     int t = blockIdx.x, cur = 0;
     if (t >= ntiles) return;
@@ -520,11 +523,12 @@ __global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, f
             }
             float c2 = 1.0f, s2 = 0.0f;
             if (rr > 0.0f) {
-                c2 = q / rr;
-                s2 = b / rr;
+                const float inv_rr = 1.0f / rr;
+                c2 = q * inv_rr;
+                s2 = b * inv_rr;
             }
             sd.tensor[(size_t)gy * pitch + gx] =
-                make_float4(c2, s2, pm_mu(nu1, lambda, mode), pm_mu(nu2, lambda, mode));
+                make_float4(c2, s2, pm_mu(nu1, inv_lambda, mode), pm_mu(nu2, inv_lambda, mode));
         }
         cur ^= 1;
     }
