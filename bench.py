@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 
 from paper_1611_06906_gb300.dist import max_over_ranks as _max_over_ranks, rank_seed  # noqa: E402
 
-# DRAM bytes (read + write) per pixel and launch of k_fed_tma<2> (two quads per
+# DRAM bytes (read + write) per pixel and launch of k_fed_tma<2,2> (two quads per
 # thread), from an ncu capture of one launch over the first 8 batch64_fundus
 # images (303.37 + 46.81 MB over 15.13 Mpixel); the roofline's `traffic` scales it
 # to the launch timed here.  Re-measured (or set to None: the field null)
@@ -287,11 +287,11 @@ def run_fd4(args, rank, world, local_rank):
     achieved = fed_bytes / (fed_ms * 1e-3) / 1e9
     # the FED kernel the schedule runs: the TMA-staged quad kernel for 2 and 4 steps per launch
     # (fd4_fed_tma.cu), the scalar fused kernel for 3, one launch per step for 1 (fd4_fed.cu)
-    kname = {1: "k_fed_step", 2: "k_fed_tma<2>", 3: "k_fed_fused<3>", 4: "k_fed_tma<4>"}[best]
+    kname = {1: "k_fed_step", 2: "k_fed_tma<2,2>", 3: "k_fed_fused<3>", 4: "k_fed_tma<4,2>"}[best]
     default_kernels = not any(os.environ.get(v) for v in ("FD4_FED_PIPELINE", "FD4_FED_QUAD_ROWS", "FD4_FED_FUSE",
                                                           "FD4_FED_QUADS"))
     traffic = args.traffic
-    if traffic is None and kname == "k_fed_tma<2>" and default_kernels and TMA2_DRAM_B_PER_PX is not None:
+    if traffic is None and kname == "k_fed_tma<2,2>" and default_kernels and TMA2_DRAM_B_PER_PX is not None:
         traffic = TMA2_DRAM_B_PER_PX * npx
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "traffic_unit": "bytes per launch", "kernel": kname,

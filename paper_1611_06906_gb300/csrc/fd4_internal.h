@@ -40,7 +40,7 @@ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Batches.  Every stage kernel walks a flat list of tiles that spans all images
 // of a batch (a persistent grid striding over the list); the tile shape
 // depends on the kernel.
-// SHAPE_SEG: a 32-column strip segment of 256 rows (the tensor build walks it
+// SHAPE_SEG: a 32-column strip segment of 512 rows (the tensor build walks it
 // top to bottom).
 enum TileShape {
     SHAPE_SWEEP = 0,
@@ -53,7 +53,7 @@ enum TileShape {
     SHAPE_Q64_4 = 7,   //   ... S = 4
     kShapes = 8
 };
-constexpr int kSegRows = 256;
+constexpr int kSegRows = 512;
 
 __host__ __device__ inline int shape_tx(int s)
 {

@@ -3,11 +3,11 @@
 // Hessian before its G_rho smoothing).
 //
 // One launch per scale of the set.  A block takes a strip segment (32 columns
-// x 256 rows of one image) and walks it top to bottom in chunks of 32 rows.
+// x 512 rows of one image) and walks it top to bottom in chunks of 32 rows.
 // For every chunk it computes the separable row pass (smoothing, first- and
 // second-derivative taps along x) of the 32 new rows into a rolling buffer
 // that keeps the 2R rows shared with the previous chunk, so the row pass costs
-// 3 (2R+1) FMAs per pixel plus 2R/256 halo rows per segment instead of a full
+// 3 (2R+1) FMAs per pixel plus 2R/512 halo rows per segment instead of a full
 // halo per tile.  The column pass then runs only at the chunk's pixels whose
 // selected scale is this one.  The radius R is a template parameter: every tap
 // loop is unrolled and the weights are kernel parameters (constant-bank
