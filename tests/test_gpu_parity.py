@@ -195,18 +195,22 @@ def test_build_tensor_tree_ragged(oracle, mode, grad_sq):
     _check_tensor(oracle, img, idx, sig, mode, grad_sq)
 
 
-@pytest.mark.parametrize("shape", [(600, 97), (53, 37), (300, 1000), (257, 64)])
-def test_tensor_strips_equal_tile_sweep(monkeypatch, shape):
+@pytest.mark.parametrize("dense", [False, True])
+@pytest.mark.parametrize("shape", [(600, 97), (53, 37), (300, 1000), (257, 64), (1100, 70)])
+def test_tensor_strips_equal_tile_sweep(monkeypatch, shape, dense):
     """The per-scale strip kernels and the multi-scale tile sweep compute the
     same sums in the same order: identical tensors, including the largest
     radius (sigma 12, R 48, whose rolling buffer is shifted in two pieces),
-    segment and strip edges, and selected indices outside the scale set."""
+    segment and strip edges, selected indices outside the scale set, and
+    (dense) chunks where one scale holds most of the pixels."""
     import torch
     h, w = shape
     rng = np.random.default_rng(h * 31 + w)
     img = synth.vessel_tree(2100 + h, w, h, depth=4, r0=4.0)
     sig = [0.75, 1.0, 1.6, 2.5, 4.0, 6.0, 9.0, 12.0]
     idx = rng.integers(0, len(sig) + 1, size=(h, w)).astype(np.uint8)   # len(sig): outside the set
+    if dense:
+        idx[rng.random((h, w)) < 0.6] = 0
     u = fd4.to_device(img)
     idx_d = torch.zeros((h, fd4.pitch_for(w)), dtype=torch.uint8, device="cuda")
     idx_d[:, :w] = torch.from_numpy(idx).cuda()
