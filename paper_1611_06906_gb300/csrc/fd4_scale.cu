@@ -356,7 +356,9 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
 
 // Second selection pass: V = vp (1 - exp(-S^2 / (2 c^2))) per scale, argmax with
 // ties to the smaller scale (strict comparison in increasing sigma order).
-// 32 x 8 tiles, one pixel per thread.
+// 32 x 64 tiles (SHAPE_SWEEP), 256 threads: thread (column quad tid % 8, rows
+// tid / 8 and tid / 8 + 32) reads each plane as two float4, so 8 pixels' loads
+// of a scale are in flight together.
 __global__ void __launch_bounds__(256) k_select_argmax(Imgs I, int K, float c_user)
 {
     __shared__ ImgDesc sd;
@@ -364,14 +366,16 @@ __global__ void __launch_bounds__(256) k_select_argmax(Imgs I, int K, float c_us
     __shared__ TileCache tcache;
     if (threadIdx.x == 0) tc_reset(tcache);
     const int tid = threadIdx.x;
-    const int ntiles = tile_count(I, SHAPE_SMALL);
+    const int qx = (tid & 7) * 4, ry = tid >> 3;
+    const int ntiles = tile_count(I, SHAPE_SWEEP);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         __syncthreads();
-        if (tid == 0) find_tile_cached(I, SHAPE_SMALL, t, tcache, sd, s_local);
+        if (tid == 0) find_tile_cached(I, SHAPE_SWEEP, t, tcache, sd, s_local);
         __syncthreads();
         const int tiles_x = (sd.w + 31) / 32;
-        const int x = (s_local % tiles_x) * 32 + (tid & 31), y = (s_local / tiles_x) * 8 + (tid >> 5);
-        if (x >= sd.w || y >= sd.h) continue;
+        const int ty = s_local / tiles_x;
+        const int x = (s_local - ty * tiles_x) * 32 + qx, y0 = ty * 64 + ry;
+        if (x >= sd.w) continue;
         float k2;  // 1 / (2 c^2)
         if (c_user > 0.0f) {
             k2 = 0.5f / (c_user * c_user);
@@ -379,19 +383,45 @@ __global__ void __launch_bounds__(256) k_select_argmax(Imgs I, int K, float c_us
             const float m = __uint_as_float(*sd.max_s2);  // max S^2 = (2c)^2
             k2 = m > 0.0f ? 2.0f / m : 0.0f;
         }
-        const size_t p = (size_t)y * sd.pitch + x;
-        float best = -1.0f;
-        int arg = 0;
+        // rows y0 and y0 + 32; a quad starting inside the row stays inside the pitch
+        const bool row_ok[2] = {y0 < sd.h, y0 + 32 < sd.h};
+        size_t p[2];
+        p[0] = (size_t)y0 * sd.pitch + x;
+        p[1] = p[0] + (size_t)32 * sd.pitch;
+        float best[8];
+        int arg[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            best[i] = -1.0f;
+            arg[i] = 0;
+        }
         for (int s = 0; s < K; ++s) {
-            float v = __ldg(sd.vp + s * sd.plane + p);
-            v = (v > 0.0f && k2 > 0.0f) ? v * -expm1f(-__ldg(sd.s2 + s * sd.plane + p) * k2) : 0.0f;
-            if (v > best) {
-                best = v;
-                arg = s;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (!row_ok[r]) continue;
+                const float4 v4 = __ldg(reinterpret_cast<const float4 *>(sd.vp + s * sd.plane + p[r]));
+                const float4 s4 = __ldg(reinterpret_cast<const float4 *>(sd.s2 + s * sd.plane + p[r]));
+                const float vv[4] = {v4.x, v4.y, v4.z, v4.w}, sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float v = (vv[i] > 0.0f && k2 > 0.0f) ? vv[i] * -expm1f(-sv[i] * k2) : 0.0f;
+                    if (v > best[4 * r + i]) {
+                        best[4 * r + i] = v;
+                        arg[4 * r + i] = s;
+                    }
+                }
             }
         }
-        sd.idx[p] = (uint8_t)arg;
-        if (sd.vmax) sd.vmax[p] = best;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (!row_ok[r]) continue;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (x + i >= sd.w) continue;
+                sd.idx[p[r] + i] = (uint8_t)arg[4 * r + i];
+                if (sd.vmax) sd.vmax[p[r] + i] = best[4 * r + i];
+            }
+        }
     }
 }
 
@@ -659,7 +689,7 @@ int launch_select_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, 
         return 1;
     }
     Imgs I = B.I;
-    I.tiles = B.tiles[SHAPE_SMALL];
+    I.tiles = B.tiles[SHAPE_SWEEP];
     const int grid = persistent_grid((const void *)k_select_argmax, 256, 0, I.tiles);
     k_select_argmax<<<grid, 256, 0, st>>>(I, n_sigma, p.c);
     return cudaGetLastError() != cudaSuccess;
