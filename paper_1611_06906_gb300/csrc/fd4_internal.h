@@ -40,8 +40,9 @@ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Batches.  Every stage kernel walks a flat list of tiles that spans all images
 // of a batch (a persistent grid striding over the list); the tile shape
 // depends on the kernel.
-// SHAPE_SEG: a 32-column strip segment of 512 rows (the tensor build walks it
-// top to bottom).
+// SHAPE_SEG / SHAPE_SEG_S: a 32-column strip segment of 512 / 128 rows (the
+// strip kernels walk it top to bottom; the short form for batches too small
+// to fill the GPU with long segments).
 enum TileShape {
     SHAPE_SWEEP = 0,
     SHAPE_SMALL = 1,
@@ -51,13 +52,14 @@ enum TileShape {
     SHAPE_SEG = 5,
     SHAPE_Q64_2 = 6,   // quad FED kernel on 64 x 64 regions: (64 - 4S)^2 outputs, S = 2
     SHAPE_Q64_4 = 7,   //   ... S = 4
-    kShapes = 8
+    SHAPE_SEG_S = 8,
+    kShapes = 9
 };
-constexpr int kSegRows = 512;
+constexpr int kSegRows = 512, kSegRowsShort = 128;
 
 __host__ __device__ inline int shape_tx(int s)
 {
-    if (s == SHAPE_SWEEP || s == SHAPE_SMALL || s == SHAPE_SEG) return 32;
+    if (s == SHAPE_SWEEP || s == SHAPE_SMALL || s == SHAPE_SEG || s == SHAPE_SEG_S) return 32;
     if (s == SHAPE_Q64_2) return 56;
     if (s == SHAPE_Q64_4) return 48;
     return 64 - 4 * s;
@@ -67,6 +69,7 @@ __host__ __device__ inline int shape_ty(int s)
     if (s == SHAPE_SWEEP) return 64;
     if (s == SHAPE_SMALL) return 8;
     if (s == SHAPE_SEG) return kSegRows;
+    if (s == SHAPE_SEG_S) return kSegRowsShort;
     if (s == SHAPE_Q64_2) return 56;
     if (s == SHAPE_Q64_4) return 48;
     return 32 - 4 * s;

@@ -3,11 +3,13 @@
 // Hessian before its G_rho smoothing).
 //
 // One launch per scale of the set.  A block takes a strip segment (32 columns
-// x 512 rows of one image) and walks it top to bottom in chunks of 32 rows.
+// x 512 rows of one image, or 128 rows where the batch is too small to give
+// every resident block several long segments) and walks it top to bottom in
+// chunks of 32 rows.
 // For every chunk it computes the separable row pass (smoothing, first- and
 // second-derivative taps along x) of the 32 new rows into a rolling buffer
 // that keeps the 2R rows shared with the previous chunk, so the row pass costs
-// 3 (2R+1) FMAs per pixel plus 2R/512 halo rows per segment instead of a full
+// 3 (2R+1) FMAs per pixel plus 2R halo rows per segment instead of a full
 // halo per tile.  The column pass then runs only at the chunk's pixels whose
 // selected scale is this one.  The radius R is a template parameter: every tap
 // loop is unrolled and the weights are kernel parameters (constant-bank
@@ -158,6 +160,8 @@ struct StripArgs {
     int mode;       // selection: FD4_RIDGE / FD4_VALLEY / FD4_BOTH
     float scale4;   // selection: sigma^(4 gamma)
     float inv2b2;   // selection: 1 / (2 beta^2)
+    int shape;      // SHAPE_SEG or SHAPE_SEG_S
+    int seg;        // its rows
 };
 
 // Scale s (radius R) over every strip segment of the batch.
@@ -185,13 +189,13 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
     if (t >= I.tiles) return;
     if (tid == 0) {
         tc_reset(tcache);
-        find_tile_cached(I, SHAPE_SEG, t, tcache, sd[0], s_local[0]);
+        find_tile_cached(I, sa.shape, t, tcache, sd[0], s_local[0]);
     }
     __syncthreads();
     int cur = 0, i = 0, buf = 0;
     {
         const int tx = (sd[0].w + ST_TX - 1) / ST_TX;
-        const Piece<R> p0((s_local[0] / tx) * kSegRows, 0);
+        const Piece<R> p0((s_local[0] / tx) * sa.seg, 0);
         st_stage<R>(stsm, SEL ? sd[0].in : sd[0].u, sd[0].w, sd[0].h, sd[0].pitch, (s_local[0] % tx) * ST_TX, p0.ya,
                     p0.n);
         st_commit();
@@ -199,8 +203,8 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
     for (;;) {
         const int w = sd[cur].w, h = sd[cur].h, pitch = sd[cur].pitch;
         const int tiles_x = (w + ST_TX - 1) / ST_TX;
-        const int x0 = (s_local[cur] % tiles_x) * ST_TX, ys = (s_local[cur] / tiles_x) * kSegRows;
-        const int nch = (min(ys + kSegRows, h) - ys + ST_CH - 1) / ST_CH;
+        const int x0 = (s_local[cur] % tiles_x) * ST_TX, ys = (s_local[cur] / tiles_x) * sa.seg;
+        const int nch = (min(ys + sa.seg, h) - ys + ST_CH - 1) / ST_CH;
         const int P = NP0 + nch - 1;
         const Piece<R> pc(ys, i);
         // issue the next piece into the other staging buffer
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
         } else if (t + G < I.tiles) {
             const ImgDesc &dn = sd[cur ^ 1];  // looked up at piece 0, published by its barriers (P >= 2)
             const int txn = (dn.w + ST_TX - 1) / ST_TX;
-            const Piece<R> pn((s_local[cur ^ 1] / txn) * kSegRows, 0);
+            const Piece<R> pn((s_local[cur ^ 1] / txn) * sa.seg, 0);
             st_stage<R>(nbuf, SEL ? dn.in : dn.u, dn.w, dn.h, dn.pitch, (s_local[cur ^ 1] % txn) * ST_TX, pn.ya,
                         pn.n);
         }
@@ -229,7 +233,7 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
         // the block's next segment: its slot held the previous segment, whose last
         // readers (the column pass above) are past this barrier
         if (i == 0 && tid == 0 && t + G < I.tiles)
-            find_tile_cached(I, SHAPE_SEG, t + G, tcache, sd[cur ^ 1], s_local[cur ^ 1]);
+            find_tile_cached(I, sa.shape, t + G, tcache, sd[cur ^ 1], s_local[cur ^ 1]);
         if (i >= NP0) {
             // keep buffer rows ST_CH .. ST_CH + 2R - 1 as rows 0 .. 2R - 1, in
             // pieces that never overlap their own source
@@ -389,10 +393,24 @@ int launch_strip_scale(const HostBatch &B, const GaussTaps &g, const StripArgs &
             const int o = i - R;
             dst[k][i] = (o >= -g.r && o <= g.r) ? src[k][o + g.r] : 0.0f;
         }
+    // Segment length: the one with the smaller estimated time, taken as the
+    // rounds of the persistent grid times the rows a block passes per segment
+    // (its rows, the 2R halo rows and one chunk for the segment's start, whose
+    // staging is not overlapped); FD4_STRIP_ROWS=512 or 128 forces one.
+    const int cap = persistent_grid((const void *)k_strip<R, SEL>, ST_NT, smem, 1 << 30);
+    const long long rounds_l = (B.tiles[SHAPE_SEG] + cap - 1) / cap;
+    const long long rounds_s = (B.tiles[SHAPE_SEG_S] + cap - 1) / cap;
+    bool lng = rounds_l * (kSegRows + 2 * R + ST_CH) <= rounds_s * (kSegRowsShort + 2 * R + ST_CH);
+    const char *e = getenv("FD4_STRIP_ROWS");
+    if (e && atoi(e) == kSegRows) lng = true;
+    if (e && atoi(e) == kSegRowsShort) lng = false;
+    StripArgs a = sa;
+    a.shape = lng ? SHAPE_SEG : SHAPE_SEG_S;
+    a.seg = lng ? kSegRows : kSegRowsShort;
     Imgs I = B.I;
-    I.tiles = B.tiles[SHAPE_SEG];
+    I.tiles = B.tiles[a.shape];
     const int grid = persistent_grid((const void *)k_strip<R, SEL>, ST_NT, smem, I.tiles);
-    k_strip<R, SEL><<<grid, ST_NT, smem, st>>>(I, tp, sa);
+    k_strip<R, SEL><<<grid, ST_NT, smem, st>>>(I, tp, a);
     return cudaGetLastError() != cudaSuccess;
 }
 
