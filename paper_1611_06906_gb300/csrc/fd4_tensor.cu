@@ -32,6 +32,9 @@ constexpr int ST_RS = 36;    // row-pass buffer stride (16-byte rows)
 template <int R>
 struct StripTaps {
     float w0[2 * R + 1], w1[2 * R + 1], w2[2 * R + 1];  // tap i at offset i - R
+    // the same taps in pairs (w[i], w[i - 1]), i = 0 .. 2R + 1, zero outside
+    // 0 .. 2R: the weights of two adjacent outputs for one input value
+    float2 p0[2 * R + 2], p1[2 * R + 2], p2[2 * R + 2];
 };
 
 __device__ __forceinline__ int st_mirror(int i, int n)
@@ -152,6 +155,47 @@ __device__ __forceinline__ void st_rows(const StripTaps<R> &tp, const float *tin
     }
 }
 
+// st_rows with packed pair FMAs (two FP32 lanes per instruction): outputs
+// (0, 1) and (2, 3) of a thread form pairs that take one input value with the
+// tap pair (w[i], w[i - 1]).  Each output receives the same products in the
+// same order as in st_rows (plus exact zeros at the ends), so the results are
+// identical.
+template <int R>
+__device__ __forceinline__ void st_rows2(const StripTaps<R> &tp, const float *tin, float *trow, int b0, int n)
+{
+    constexpr int SW = st_sw<R>(), NB = ST_CH + 2 * R;
+    const int tid = threadIdx.x;
+    const int r = tid >> 3, xo = (tid & 7) * 4;
+    if (r < n) {
+        const float *src = tin + r * SW + xo;
+        float2 a0[2], a1[2], a2[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) a0[j] = a1[j] = a2[j] = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int m4 = 0; m4 < (2 * R + 4 + 3) / 4; ++m4) {
+            const float4 v = *reinterpret_cast<const float4 *>(src + 4 * m4);
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 x2 = make_float2(vv[e], vv[e]);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int i = 4 * m4 + e - 2 * j;  // pair index of outputs 2j, 2j + 1
+                    if (i >= 0 && i <= 2 * R + 1) {
+                        a0[j] = __ffma2_rn(tp.p0[i], x2, a0[j]);
+                        a1[j] = __ffma2_rn(tp.p1[i], x2, a1[j]);
+                        a2[j] = __ffma2_rn(tp.p2[i], x2, a2[j]);
+                    }
+                }
+            }
+        }
+        float *d = trow + (b0 + r) * ST_RS + xo;
+        *reinterpret_cast<float4 *>(d) = make_float4(a0[0].x, a0[0].y, a0[1].x, a0[1].y);
+        *reinterpret_cast<float4 *>(d + NB * ST_RS) = make_float4(a1[0].x, a1[0].y, a1[1].x, a1[1].y);
+        *reinterpret_cast<float4 *>(d + 2 * NB * ST_RS) = make_float4(a2[0].x, a2[0].y, a2[1].x, a2[1].y);
+    }
+}
+
 // Per-launch scalars of the strip kernels.
 struct StripArgs {
     int s;          // scale index in the set
@@ -164,6 +208,24 @@ struct StripArgs {
     int seg;        // its rows
 };
 
+// Geometry of one strip segment, computed once by the thread that looks the
+// segment up (the other threads read it from shared memory, so no thread
+// divides by the image's strip count per piece).
+struct SegGeo {
+    int x0, ys;    // first column and row
+    int pieces;    // NP0 + chunks - 1
+};
+
+template <int R>
+__device__ __forceinline__ void seg_geo(const ImgDesc &d, int local, int seg, SegGeo &g)
+{
+    const int tiles_x = (d.w + ST_TX - 1) / ST_TX;
+    const int ty = local / tiles_x;
+    g.x0 = (local - ty * tiles_x) * ST_TX;
+    g.ys = ty * seg;
+    g.pieces = Piece<R>::NP0 + (min(g.ys + seg, d.h) - g.ys + ST_CH - 1) / ST_CH - 1;
+}
+
 // Scale s (radius R) over every strip segment of the batch.
 // Tensor build (SEL false): idx holds each pixel's selected scale; only pixels
 // with idx == s are written (nfield), and the s == 0 launch also zeroes N where
@@ -171,7 +233,7 @@ struct StripArgs {
 // at scale s gives the vesselness factor and S^2 of plane s (vp, s2) and the
 // image's max S^2.  The next piece's rows (of this segment or of the block's
 // next one) are copied with cp.async while the current piece is computed.
-template <int R, bool SEL>
+template <int R, bool SEL, bool F2>
 __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripArgs sa)
 {
     constexpr int NB = ST_CH + 2 * R, SW = st_sw<R>(), NP0 = Piece<R>::NP0;
@@ -181,6 +243,7 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
     __shared__ int wtot[ST_NT / 32 + 1];
     __shared__ ImgDesc sd[2];
     __shared__ int s_local[2];
+    __shared__ SegGeo sg[2];
     __shared__ TileCache tcache;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, s = sa.s;
@@ -190,22 +253,18 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
     if (tid == 0) {
         tc_reset(tcache);
         find_tile_cached(I, sa.shape, t, tcache, sd[0], s_local[0]);
+        seg_geo<R>(sd[0], s_local[0], sa.seg, sg[0]);
     }
     __syncthreads();
     int cur = 0, i = 0, buf = 0;
     {
-        const int tx = (sd[0].w + ST_TX - 1) / ST_TX;
-        const Piece<R> p0((s_local[0] / tx) * sa.seg, 0);
-        st_stage<R>(stsm, SEL ? sd[0].in : sd[0].u, sd[0].w, sd[0].h, sd[0].pitch, (s_local[0] % tx) * ST_TX, p0.ya,
-                    p0.n);
+        const Piece<R> p0(sg[0].ys, 0);
+        st_stage<R>(stsm, SEL ? sd[0].in : sd[0].u, sd[0].w, sd[0].h, sd[0].pitch, sg[0].x0, p0.ya, p0.n);
         st_commit();
     }
     for (;;) {
         const int w = sd[cur].w, h = sd[cur].h, pitch = sd[cur].pitch;
-        const int tiles_x = (w + ST_TX - 1) / ST_TX;
-        const int x0 = (s_local[cur] % tiles_x) * ST_TX, ys = (s_local[cur] / tiles_x) * sa.seg;
-        const int nch = (min(ys + sa.seg, h) - ys + ST_CH - 1) / ST_CH;
-        const int P = NP0 + nch - 1;
+        const int x0 = sg[cur].x0, ys = sg[cur].ys, P = sg[cur].pieces;
         const Piece<R> pc(ys, i);
         // issue the next piece into the other staging buffer
         float *nbuf = stsm + (buf ^ 1) * ST_CH * SW;
@@ -214,42 +273,48 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
             st_stage<R>(nbuf, SEL ? sd[cur].in : sd[cur].u, w, h, pitch, x0, pn.ya, pn.n);
         } else if (t + G < I.tiles) {
             const ImgDesc &dn = sd[cur ^ 1];  // looked up at piece 0, published by its barriers (P >= 2)
-            const int txn = (dn.w + ST_TX - 1) / ST_TX;
-            const Piece<R> pn((s_local[cur ^ 1] / txn) * sa.seg, 0);
-            st_stage<R>(nbuf, SEL ? dn.in : dn.u, dn.w, dn.h, dn.pitch, (s_local[cur ^ 1] % txn) * ST_TX, pn.ya,
-                        pn.n);
+            const Piece<R> pn(sg[cur ^ 1].ys, 0);
+            st_stage<R>(nbuf, SEL ? dn.in : dn.u, dn.w, dn.h, dn.pitch, sg[cur ^ 1].x0, pn.ya, pn.n);
         }
         st_commit();
         // the selected scales of the chunk this piece completes (rows 4 warp .. + 3)
         const int y0 = ys + ST_CH * pc.chunk;
-        int ids[4];
+        int ids[4] = {-1, -1, -1, -1};
+        if (!SEL && pc.last && x0 + lane < w) {
+            const uint8_t *ip = sd[cur].idx + (size_t)(y0 + warp * 4) * pitch + x0 + lane;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int gx = x0 + lane, gy = y0 + warp * 4 + j;
-            ids[j] = (!SEL && pc.last && gx < w && gy < h) ? (int)sd[cur].idx[(size_t)gy * pitch + gx] : -1;
+            for (int j = 0; j < 4; ++j)
+                if (y0 + warp * 4 + j < h) ids[j] = ip[(size_t)j * pitch];
         }
         st_wait1();
         __syncthreads();  // this piece's rows have landed; the previous chunk's column pass is done
         // the block's next segment: its slot held the previous segment, whose last
         // readers (the column pass above) are past this barrier
-        if (i == 0 && tid == 0 && t + G < I.tiles)
+        if (i == 0 && tid == 0 && t + G < I.tiles) {
             find_tile_cached(I, sa.shape, t + G, tcache, sd[cur ^ 1], s_local[cur ^ 1]);
-        if (i >= NP0) {
-            // keep buffer rows ST_CH .. ST_CH + 2R - 1 as rows 0 .. 2R - 1, in
-            // pieces that never overlap their own source
-            for (int k0 = 0; k0 < 2 * R; k0 += ST_CH) {
-                const int n = min(ST_CH, 2 * R - k0);
-                for (int q = tid; q < 3 * n * (ST_TX / 4); q += ST_NT) {
-                    const int f = q / (n * (ST_TX / 4)), rem = q - f * n * (ST_TX / 4);
-                    const int r = rem / (ST_TX / 4), c = (rem - r * (ST_TX / 4)) * 4;
-                    float *fb = trow + f * NB * ST_RS;
-                    *reinterpret_cast<float4 *>(fb + (k0 + r) * ST_RS + c) =
-                        *reinterpret_cast<const float4 *>(fb + (ST_CH + k0 + r) * ST_RS + c);
-                }
-                __syncthreads();
-            }
+            seg_geo<R>(sd[cur ^ 1], s_local[cur ^ 1], sa.seg, sg[cur ^ 1]);
         }
-        st_rows<R>(tp, stsm + buf * ST_CH * SW, trow, pc.b0, pc.n);
+        if (i >= NP0) {
+            // keep buffer rows ST_CH .. ST_CH + 2R - 1 as rows 0 .. 2R - 1.
+            // Thread (row r, columns c .. c + 3) moves rows k0 + r for k0 = 0,
+            // 32, ...: a row it overwrites in pass k0 + 32 is one it read
+            // itself in pass k0, so the passes need no barrier between them.
+            const int r = tid >> 3, c = (tid & 7) * 4;
+#pragma unroll
+            for (int k0 = 0; k0 < 2 * R; k0 += ST_CH) {
+                if (k0 + r < 2 * R) {
+#pragma unroll
+                    for (int f = 0; f < 3; ++f) {
+                        float *fb = trow + f * NB * ST_RS;
+                        *reinterpret_cast<float4 *>(fb + (k0 + r) * ST_RS + c) =
+                            *reinterpret_cast<const float4 *>(fb + (ST_CH + k0 + r) * ST_RS + c);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (F2) st_rows2<R>(tp, stsm + buf * ST_CH * SW, trow, pc.b0, pc.n);
+        else st_rows<R>(tp, stsm + buf * ST_CH * SW, trow, pc.b0, pc.n);
         __syncthreads();
 
         if (SEL && pc.last) {
@@ -317,14 +382,16 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
             }
             if (lane == 0) wtot[warp] = cnt;
             __syncthreads();
-            if (tid == 0) {
-                int acc = 0;
-                for (int k = 0; k < ST_NT / 32; ++k) {
-                    const int c = wtot[k];
-                    wtot[k] = acc;
-                    acc += c;
+            if (warp == 0) {  // exclusive prefix of the warps' counts, and their total
+                const int c0 = lane < ST_NT / 32 ? wtot[lane] : 0;
+                int c = c0;
+#pragma unroll
+                for (int o = 1; o < ST_NT / 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, c, o);
+                    if (lane >= o) c += v;
                 }
-                wtot[ST_NT / 32] = acc;
+                if (lane < ST_NT / 32) wtot[lane] = c - c0;
+                if (lane == ST_NT / 32 - 1) wtot[ST_NT / 32] = c;
             }
             __syncthreads();
             {
@@ -372,32 +439,52 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
     st_wait0();
 }
 
-template <int R, bool SEL>
-int launch_strip_scale(const HostBatch &B, const GaussTaps &g, const StripArgs &sa, cudaStream_t st)
+template <int R, bool SEL, bool F2>
+int launch_strip_k(const Imgs &I, const StripTaps<R> &tp, const StripArgs &a, cudaStream_t st)
 {
     static int attr_dev = -1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
     constexpr size_t smem = st_smem_bytes<R>();
     if (attr_dev != dev) {
-        if (cudaFuncSetAttribute(k_strip<R, SEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        if (cudaFuncSetAttribute(k_strip<R, SEL, F2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return 1;
         attr_dev = dev;
     }
+    const int grid = persistent_grid((const void *)k_strip<R, SEL, F2>, ST_NT, smem, I.tiles);
+    k_strip<R, SEL, F2><<<grid, ST_NT, smem, st>>>(I, tp, a);
+    return cudaGetLastError() != cudaSuccess;
+}
+
+// Row pass with packed pair FMAs unless FD4_STRIP_FMA2=0 (same results).
+inline bool strip_fma2()
+{
+    const char *e = getenv("FD4_STRIP_FMA2");
+    return !(e && e[0] == '0');
+}
+
+template <int R, bool SEL>
+int launch_strip_scale(const HostBatch &B, const GaussTaps &g, const StripArgs &sa, cudaStream_t st)
+{
+    constexpr size_t smem = st_smem_bytes<R>();
     StripTaps<R> tp;
     const float *src[3] = {g.w0, g.w1, g.w2};
     float *dst[3] = {tp.w0, tp.w1, tp.w2};
-    for (int k = 0; k < 3; ++k)
+    float2 *pd[3] = {tp.p0, tp.p1, tp.p2};
+    for (int k = 0; k < 3; ++k) {
         for (int i = 0; i <= 2 * R; ++i) {
             const int o = i - R;
             dst[k][i] = (o >= -g.r && o <= g.r) ? src[k][o + g.r] : 0.0f;
         }
+        for (int i = 0; i <= 2 * R + 1; ++i)
+            pd[k][i] = make_float2(i <= 2 * R ? dst[k][i] : 0.0f, i >= 1 ? dst[k][i - 1] : 0.0f);
+    }
     // Segment length: the one with the smaller estimated time, taken as the
     // rounds of the persistent grid times the rows a block passes per segment
     // (its rows, the 2R halo rows and one chunk for the segment's start, whose
     // staging is not overlapped); FD4_STRIP_ROWS=512 or 128 forces one.
-    const int cap = persistent_grid((const void *)k_strip<R, SEL>, ST_NT, smem, 1 << 30);
+    const int cap = persistent_grid((const void *)k_strip<R, SEL, true>, ST_NT, smem, 1 << 30);
     const long long rounds_l = (B.tiles[SHAPE_SEG] + cap - 1) / cap;
     const long long rounds_s = (B.tiles[SHAPE_SEG_S] + cap - 1) / cap;
     bool lng = rounds_l * (kSegRows + 2 * R + ST_CH) <= rounds_s * (kSegRowsShort + 2 * R + ST_CH);
@@ -409,9 +496,7 @@ int launch_strip_scale(const HostBatch &B, const GaussTaps &g, const StripArgs &
     a.seg = lng ? kSegRows : kSegRowsShort;
     Imgs I = B.I;
     I.tiles = B.tiles[a.shape];
-    const int grid = persistent_grid((const void *)k_strip<R, SEL>, ST_NT, smem, I.tiles);
-    k_strip<R, SEL><<<grid, ST_NT, smem, st>>>(I, tp, a);
-    return cudaGetLastError() != cudaSuccess;
+    return strip_fma2() ? launch_strip_k<R, SEL, true>(I, tp, a, st) : launch_strip_k<R, SEL, false>(I, tp, a, st);
 }
 
 template <bool SEL>
@@ -453,10 +538,11 @@ int launch_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const 
 template <int R>
 int set_strip_smem()
 {
-    return cudaFuncSetAttribute(k_strip<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)st_smem_bytes<R>()) != cudaSuccess ||
-           cudaFuncSetAttribute(k_strip<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)st_smem_bytes<R>()) != cudaSuccess;
+    const int b = (int)st_smem_bytes<R>();
+    return cudaFuncSetAttribute(k_strip<R, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) != cudaSuccess ||
+           cudaFuncSetAttribute(k_strip<R, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) != cudaSuccess ||
+           cudaFuncSetAttribute(k_strip<R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) != cudaSuccess ||
+           cudaFuncSetAttribute(k_strip<R, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) != cudaSuccess;
 }
 
 }  // namespace

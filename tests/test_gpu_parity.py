@@ -195,16 +195,16 @@ def test_build_tensor_tree_ragged(oracle, mode, grad_sq):
     _check_tensor(oracle, img, idx, sig, mode, grad_sq)
 
 
-@pytest.mark.parametrize("rows", ["512", "128"])
+@pytest.mark.parametrize("rows,fma2", [("512", "1"), ("128", "1"), ("512", "0")])
 @pytest.mark.parametrize("dense", [False, True])
 @pytest.mark.parametrize("shape", [(600, 97), (53, 37), (300, 1000), (257, 64), (1100, 70)])
-def test_tensor_strips_equal_tile_sweep(monkeypatch, shape, dense, rows):
+def test_tensor_strips_equal_tile_sweep(monkeypatch, shape, dense, rows, fma2):
     """The per-scale strip kernels and the multi-scale tile sweep compute the
     same sums in the same order: identical tensors, including the largest
     radius (sigma 12, R 48, whose rolling buffer is shifted in two pieces),
     segment and strip edges (segments of 512 or 128 rows), selected indices
-    outside the scale set, and (dense) chunks where one scale holds most of the
-    pixels."""
+    outside the scale set, (dense) chunks where one scale holds most of the
+    pixels, and the row pass with packed pair FMAs or scalar ones."""
     import torch
     h, w = shape
     rng = np.random.default_rng(h * 31 + w)
@@ -221,18 +221,19 @@ def test_tensor_strips_equal_tile_sweep(monkeypatch, shape, dense, rows):
     t_sweep = fd4.build_tensor(u, w, idx_d, sig, prm).clone()
     monkeypatch.setenv("FD4_TENSOR_SWEEP", "0")
     monkeypatch.setenv("FD4_STRIP_ROWS", rows)
+    monkeypatch.setenv("FD4_STRIP_FMA2", fma2)
     t_strip = fd4.build_tensor(u, w, idx_d, sig, prm)
     torch.cuda.synchronize()
     assert torch.equal(t_sweep[:, :w], t_strip[:, :w])
 
 
-@pytest.mark.parametrize("rows", ["512", "128"])
+@pytest.mark.parametrize("rows,fma2", [("512", "1"), ("128", "1"), ("512", "0")])
 @pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("shape", [(600, 97), (53, 37), (300, 1000)])
-def test_select_strips_equal_tile_sweep(monkeypatch, shape, mode, rows):
-    """Selection by the per-scale strip kernels (segments of 512 or 128 rows)
-    and by the multi-scale tile sweep: the same sums in the same order, so
-    identical sigma* and V."""
+def test_select_strips_equal_tile_sweep(monkeypatch, shape, mode, rows, fma2):
+    """Selection by the per-scale strip kernels (segments of 512 or 128 rows,
+    packed or scalar row-pass FMAs) and by the multi-scale tile sweep: the
+    same sums in the same order, so identical sigma* and V."""
     import torch
     h, w = shape
     img = synth.vessel_tree(2200 + h, w, h, depth=4, r0=4.0)
@@ -244,6 +245,7 @@ def test_select_strips_equal_tile_sweep(monkeypatch, shape, mode, rows):
     i_sweep, v_sweep = i_sweep.clone(), v_sweep.clone()
     monkeypatch.setenv("FD4_SELECT_SWEEP", "0")
     monkeypatch.setenv("FD4_STRIP_ROWS", rows)
+    monkeypatch.setenv("FD4_STRIP_FMA2", fma2)
     i_strip, v_strip = fd4.select_scales(u, w, sig, prm, want_vmax=True)
     torch.cuda.synchronize()
     assert torch.equal(i_sweep[:, :w], i_strip[:, :w])
