@@ -6,9 +6,11 @@
 // copies (cp.async.bulk.tensor) that one thread issues and an mbarrier counts
 // in bytes: the hardware generates the addresses, zero-fills what lies outside
 // the image, and the copies of the next two tiles overlap the current tile's
-// steps.  Both boxes land dense (u: 64 rows of 256 B, tensor: 64 rows of 1 KB);
-// the threads read their quads' tensor values in a lane-rotated order so that
-// the 16-byte reads of a quarter-warp hit distinct banks.  The issuing thread
+// steps.  The u box lands dense (64 rows of 256 B); the tensor box (64 rows of
+// 16 quads of 64 B) lands with the copy's 64-byte swizzle, which places the
+// four pixels of quad q in the 16-byte slots i ^ ((q / 2) mod 4), so that the
+// 16-byte reads of a quarter-warp hit distinct banks while each value goes
+// straight to its pixel's register.  The issuing thread
 // also records the tile's geometry in shared memory, so the other threads do
 // no per-tile integer division.  Per-thread 16-byte copies
 // (the cp.async kernels of fd4_fed.cu) reach about half of the HBM bandwidth on
@@ -46,7 +48,7 @@ constexpr size_t kTmaSmem = 1024 + kAhead * kTBytes + sizeof(float) * (kAhead + 
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded wait on a tile's copies
 
 struct TmaMaps {
-    CUtensorMap u, tmp, ten;  // 2-D maps: the two u planes {w, h}, the tensor field as floats {4 w, h}
+    CUtensorMap u, tmp, ten;  // 2-D maps of the two u planes {w, h}; 3-D map of the tensor field {16, quads, h}
 };
 
 __device__ __forceinline__ unsigned long long tma_now()
@@ -98,6 +100,14 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         "l"(map), "r"(x), "r"(y), "r"(smem_addr(m))
         : "memory");
 }
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *m)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(m))
+        : "memory");
+}
 // Shared memory written or read through the generic proxy before the bulk copies overwrite it.
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 // A tensor map in global memory written by a kernel (generic proxy) before the copies read it.
@@ -137,7 +147,7 @@ __device__ __forceinline__ void tma_issue(const ImgDesc &d, int local, const Tma
     fence_async_smem();
     tma_expect(mbar, kUBytes + kTBytes);
     tma_load_2d(u_dst + TSW, mu, gx0, gy0, mbar);         // x: 4 gx0 bytes, a multiple of 16
-    tma_load_2d(t_dst, &m->ten, 4 * gx0, gy0, mbar);      // x: 16 gx0 bytes
+    tma_load_3d(t_dst, &m->ten, 0, gx0 >> 2, gy0, mbar);  // x: 0; the quad index may be -1
 }
 
 // NQ quads per thread: TNT / NQ threads, thread (row ry, quad column q) owns the
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(TNT / NQ, 1) k_fed_tma(Imgs I, StepTaus taus, 
         tc_reset(tcache);
         for (int i = 0; i < kAhead; ++i) tma_mbar_init(&mbar[i]);
     }
-    const int q = tid & 15, ry0 = tid >> 4;
+    const int q = tid & 15, ry0 = tid >> 4, tswz = (q >> 1) & 3;
     int off[NQ], rowq[NQ];
     bool writes[NQ];
 #pragma unroll
@@ -220,25 +230,15 @@ __global__ void __launch_bounds__(TNT / NQ, 1) k_fed_tma(Imgs I, StepTaus taus, 
                 }
                 mask[qd] |= (gy >= 1 && gy <= h - 2 ? 1u : 0u) << 8;
             }
-            // Read i of lane q takes pixel (i + r) mod 4 of its quad, r = (q / 2) mod 4:
-            // the 8 lanes of a quarter-warp then address 8 distinct 16-byte bank
-            // groups (quads are 64 bytes apart), so the tile-start reads of all
-            // threads do not queue up in the shared-memory pipe.  The values are
-            // rotated back by r.
-            const int r = (q >> 1) & 3;
+            // The copy's 64-byte swizzle put pixel i of quad q in 16-byte slot
+            // i ^ r of the quad, r = (q / 2) mod 4: the 8 lanes of a quarter-warp
+            // then read 8 distinct 16-byte bank groups, and every value lands in
+            // its pixel's register.
             const float4 *tq =
                 reinterpret_cast<const float4 *>(base + bj * kTBytes + (size_t)rowq[qd] * (TR * 16)) + 4 * q;
             float4 v[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) v[i] = tq[(i + r) & 3];
-            if (r & 1) {  // v[i] holds pixel (i + r) mod 4: rotate back by 1, then by 2
-                const float4 t3 = v[3];
-                v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = t3;
-            }
-            if (r & 2) {
-                float4 tt = v[0]; v[0] = v[2]; v[2] = tt;
-                tt = v[1]; v[1] = v[3]; v[3] = tt;
-            }
+            for (int i = 0; i < 4; ++i) v[i] = tq[i ^ tswz];
             float cc[4], ss[4], pp[4], qq[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -342,11 +342,15 @@ int make_maps(const ImgDesc &d, TmaMaps *m)
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return 1;
-    const cuuint64_t dimt[2] = {(cuuint64_t)d.w * 4, (cuuint64_t)d.h};
-    const cuuint64_t strt[1] = {(cuuint64_t)d.pitch * 16};
-    const cuuint32_t boxt[2] = {TR * 4, TR};
-    if (enc(&m->ten, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)d.tensor, dimt, strt, boxt, one2,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    // tensor: floats of one quad (64 bytes) x quads of a row x rows, so that the
+    // 64-byte swizzle permutes the four pixels of each quad; the pitch is a
+    // multiple of 4, so the last (partial) quad of a row lies within the pitch
+    const cuuint64_t dimt[3] = {16, (cuuint64_t)(d.w + 3) / 4, (cuuint64_t)d.h};
+    const cuuint64_t strt[2] = {64, (cuuint64_t)d.pitch * 16};
+    const cuuint32_t boxt[3] = {16, TR / 4, TR};
+    const cuuint32_t one3[3] = {1, 1, 1};
+    if (enc(&m->ten, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)d.tensor, dimt, strt, boxt, one3,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return 1;
     return 0;
