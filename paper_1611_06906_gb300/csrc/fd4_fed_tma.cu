@@ -253,17 +253,24 @@ __global__ void __launch_bounds__(TNT / NQ, 1) k_fed_tma(Imgs I, StepTaus taus, 
             k[qd].p = make_float4(pp[0], pp[1], pp[2], pp[3]);
             k[qd].q = make_float4(qq[0], qq[1], qq[2], qq[3]);
         }
-        __syncthreads();  // tensor box bj is read; u plane (j + kAhead) % NU was last used by tile j - 1
-        const int ta = t + kAhead * G;  // tile j + kAhead: into box bj, plane (j + kAhead) % NU
-        if (tid == 0 && ta < ntiles) {
-            const int ua = (j + kAhead) % NU;
-            find_tile_cached(I, SHAPE, ta, tcache, sd[ua], s_local[ua]);
-            tma_issue<S>(sd[ua], s_local[ua], one, from_table, parity, planes + ua * TPLANE, base + bj * kTBytes,
-                         &mbar[bj], &sgeo[ua]);
+        // Tile j + kAhead goes into box bj and plane (j + kAhead) % NU, once every
+        // thread has read box bj (above) and is past tile j - 1, the last user of
+        // that plane and of its descriptor slot: after the first step's T barrier.
+        const int ta = t + kAhead * G;
+        const auto issue = [&]() {
+            if (tid == 0 && ta < ntiles) {
+                const int ua = (j + kAhead) % NU;
+                find_tile_cached(I, SHAPE, ta, tcache, sd[ua], s_local[ua]);
+                tma_issue<S>(sd[ua], s_local[ua], one, from_table, parity, planes + ua * TPLANE,
+                             base + bj * kTBytes, &mbar[bj], &sgeo[ua]);
+            }
+        };
+        if (taus.n < 1) {
+            __syncthreads();
+            issue();
         }
-
-        if (interior) quad_steps_n<false, TSW, NQ>(su, sxy, syy, stau, taus.n, off, k, mask, uq);
-        else quad_steps_n<true, TSW, NQ>(su, sxy, syy, stau, taus.n, off, k, mask, uq);
+        if (interior) quad_steps_n<false, TSW, NQ>(su, sxy, syy, stau, taus.n, off, k, mask, uq, issue);
+        else quad_steps_n<true, TSW, NQ>(su, sxy, syy, stau, taus.n, off, k, mask, uq, issue);
         // the exact interior: rows H .. H + TO - 1, columns H .. H + TO - 1 (whole quads)
 #pragma unroll
         for (int qd = 0; qd < NQ; ++qd) {

@@ -82,15 +82,22 @@ __device__ __forceinline__ void quad_T(const float (&a)[6], const float (&b)[6],
     Tyy = make_float4(ryy[0], ryy[1], ryy[2], ryy[3]);
 }
 
+struct NoHook {
+    __device__ void operator()() const {}
+};
+
 // S steps of one staged region for NQ quads per thread; uo: the quads' u on
 // entry, updated in place.  Two block barriers per step: T is complete before
 // the update reads it, the update is complete before the next T phase reads u.
 // The first T phase reads the staged region (published by the tile's
 // barrier); after the last update no barrier is needed before the next tile's.
-template <bool BOUNDARY, int SW, int NQ>
+// hook() runs once, right after the first step's T barrier (every thread is
+// then past whatever it read before the call).
+template <bool BOUNDARY, int SW, int NQ, class Hook = NoHook>
 __device__ __forceinline__ void quad_steps_n(float *su, float *sxy, float *syy, const float *stau, int nsteps,
                                              const int (&off)[NQ], const QuadCoef (&k)[NQ],
-                                             const unsigned (&mask)[NQ], float4 (&uo)[NQ])
+                                             const unsigned (&mask)[NQ], float4 (&uo)[NQ],
+                                             const Hook &hook = Hook())
 {
     for (int l = 0; l < nsteps; ++l) {
         if (l > 0) __syncthreads();
@@ -107,6 +114,7 @@ __device__ __forceinline__ void quad_steps_n(float *su, float *sxy, float *syy, 
             *reinterpret_cast<float4 *>(syy + off[qd]) = tyy[qd];
         }
         __syncthreads();
+        if (l == 0) hook();
         const float tau = stau[l];
 #pragma unroll
         for (int qd = 0; qd < NQ; ++qd) {
