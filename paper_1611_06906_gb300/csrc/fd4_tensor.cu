@@ -35,6 +35,8 @@ struct StripTaps {
     // the same taps in pairs (w[i], w[i - 1]), i = 0 .. 2R + 1, zero outside
     // 0 .. 2R: the weights of two adjacent outputs for one input value
     float2 p0[2 * R + 2], p1[2 * R + 2], p2[2 * R + 2];
+    // pairs of two fields' taps at one offset: (w1[k], w2[k]) and (w0[k], w1[k])
+    float2 q12[2 * R + 1], q01[2 * R + 1];
 };
 
 __device__ __forceinline__ int st_mirror(int i, int n)
@@ -323,18 +325,44 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
             const float *c0 = trow + (warp * 4) * ST_RS + lane;
             const float *c1 = c0 + NB * ST_RS, *c2 = c1 + NB * ST_RS;
             float uxx[4], uxy[4], uyy[4];
+            if (F2) {  // output rows (0, 1) and (2, 3) in packed pairs, as in st_rows2
+                float2 axx[2], axy[2], ayy[2];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) uxx[j] = uxy[j] = uyy[j] = 0.0f;
+                for (int j = 0; j < 2; ++j) axx[j] = axy[j] = ayy[j] = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int k = 0; k < 2 * R + 4; ++k) {
-                const float v0 = c0[k * ST_RS], v1 = c1[k * ST_RS], v2 = c2[k * ST_RS];
+                for (int k = 0; k < 2 * R + 4; ++k) {
+                    const float v0 = c0[k * ST_RS], v1 = c1[k * ST_RS], v2 = c2[k * ST_RS];
+                    const float2 x0 = make_float2(v0, v0), x1 = make_float2(v1, v1), x2 = make_float2(v2, v2);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int q = k - j;  // tap index of output row j
-                    if (q >= 0 && q <= 2 * R) {
-                        uxx[j] = fmaf(tp.w0[q], v2, uxx[j]);   // d2/dx2, smoothed in y
-                        uxy[j] = fmaf(tp.w1[q], v1, uxy[j]);   // d/dx, then d/dy
-                        uyy[j] = fmaf(tp.w2[q], v0, uyy[j]);   // d2/dy2 of the x-smoothed field
+                    for (int j = 0; j < 2; ++j) {
+                        const int q = k - 2 * j;  // tap pair of output rows 2j, 2j + 1
+                        if (q >= 0 && q <= 2 * R + 1) {
+                            axx[j] = __ffma2_rn(tp.p0[q], x2, axx[j]);
+                            axy[j] = __ffma2_rn(tp.p1[q], x1, axy[j]);
+                            ayy[j] = __ffma2_rn(tp.p2[q], x0, ayy[j]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    uxx[2 * j] = axx[j].x; uxx[2 * j + 1] = axx[j].y;
+                    uxy[2 * j] = axy[j].x; uxy[2 * j + 1] = axy[j].y;
+                    uyy[2 * j] = ayy[j].x; uyy[2 * j + 1] = ayy[j].y;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) uxx[j] = uxy[j] = uyy[j] = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 2 * R + 4; ++k) {
+                    const float v0 = c0[k * ST_RS], v1 = c1[k * ST_RS], v2 = c2[k * ST_RS];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int q = k - j;  // tap index of output row j
+                        if (q >= 0 && q <= 2 * R) {
+                            uxx[j] = fmaf(tp.w0[q], v2, uxx[j]);   // d2/dx2, smoothed in y
+                            uxy[j] = fmaf(tp.w1[q], v1, uxy[j]);   // d/dx, then d/dy
+                            uyy[j] = fmaf(tp.w2[q], v0, uyy[j]);   // d2/dy2 of the x-smoothed field
+                        }
                     }
                 }
             }
@@ -413,14 +441,26 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
                 const float *c1 = c0 + NB * ST_RS;           // d/dx
                 const float *c2 = c1 + NB * ST_RS;           // d2/dx2
                 float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
+                if (F2) {  // (sy, syy) and (sx, sxy) share their input: packed pairs
+                    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int k = 0; k <= 2 * R; ++k) {
-                    const float v0 = c0[k * ST_RS], v1 = c1[k * ST_RS], v2 = c2[k * ST_RS];
-                    sy = fmaf(tp.w1[k], v0, sy);
-                    syy = fmaf(tp.w2[k], v0, syy);
-                    sx = fmaf(tp.w0[k], v1, sx);
-                    sxy = fmaf(tp.w1[k], v1, sxy);
-                    sxx = fmaf(tp.w0[k], v2, sxx);
+                    for (int k = 0; k <= 2 * R; ++k) {
+                        const float v0 = c0[k * ST_RS], v1 = c1[k * ST_RS], v2 = c2[k * ST_RS];
+                        a = __ffma2_rn(tp.q12[k], make_float2(v0, v0), a);
+                        b = __ffma2_rn(tp.q01[k], make_float2(v1, v1), b);
+                        sxx = fmaf(tp.w0[k], v2, sxx);
+                    }
+                    sy = a.x; syy = a.y; sx = b.x; sxy = b.y;
+                } else {
+#pragma unroll
+                    for (int k = 0; k <= 2 * R; ++k) {
+                        const float v0 = c0[k * ST_RS], v1 = c1[k * ST_RS], v2 = c2[k * ST_RS];
+                        sy = fmaf(tp.w1[k], v0, sy);
+                        syy = fmaf(tp.w2[k], v0, syy);
+                        sx = fmaf(tp.w0[k], v1, sx);
+                        sxy = fmaf(tp.w1[k], v1, sxy);
+                        sxx = fmaf(tp.w0[k], v2, sxx);
+                    }
                 }
                 const float g2 = fmaf(sx, sx, sy * sy);
                 const float g = sa.grad_sq ? g2 : sqrtf(g2);
@@ -457,7 +497,8 @@ int launch_strip_k(const Imgs &I, const StripTaps<R> &tp, const StripArgs &a, cu
     return cudaGetLastError() != cudaSuccess;
 }
 
-// Row pass with packed pair FMAs unless FD4_STRIP_FMA2=0 (same results).
+// Row and column passes with packed pair FMAs unless FD4_STRIP_FMA2=0 (same
+// results).
 inline bool strip_fma2()
 {
     const char *e = getenv("FD4_STRIP_FMA2");
@@ -479,6 +520,10 @@ int launch_strip_scale(const HostBatch &B, const GaussTaps &g, const StripArgs &
         }
         for (int i = 0; i <= 2 * R + 1; ++i)
             pd[k][i] = make_float2(i <= 2 * R ? dst[k][i] : 0.0f, i >= 1 ? dst[k][i - 1] : 0.0f);
+    }
+    for (int i = 0; i <= 2 * R; ++i) {
+        tp.q12[i] = make_float2(tp.w1[i], tp.w2[i]);
+        tp.q01[i] = make_float2(tp.w0[i], tp.w1[i]);
     }
     // Segment length: the one with the smaller estimated time, taken as the
     // rounds of the persistent grid times the rows a block passes per segment
