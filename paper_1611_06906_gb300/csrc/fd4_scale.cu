@@ -449,21 +449,38 @@ constexpr size_t finish_smem_bytes()
 
 // cp.async (16 bytes = one pixel of N) of a tile's N region with its mirrored halo.
 template <int r>
-__device__ __forceinline__ void finish_stage(const ImgDesc &d, int local, float4 *dst)
+__device__ __forceinline__ void finish_stage(const ImgDesc &d, int2 o, float4 *dst)
 {
     constexpr int ROWS = FY + 2 * r, COLS = FX + 2 * r;
-    const int w = d.w, h = d.h, pitch = d.pitch;
-    const int tiles_x = (w + FX - 1) / FX;
-    const int ty = local / tiles_x;
-    const int x0 = (local - ty * tiles_x) * FX, y0 = ty * FY;
-    for (int i = threadIdx.x; i < ROWS * COLS; i += FNT_T) {
-        const int ry = i / COLS, rx = i - ry * COLS;
-        const float4 *src = d.nfield + (size_t)mirror(y0 - r + ry, h) * pitch + mirror(x0 - r + rx, w);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst + i)),
-                     "l"(src)
-                     : "memory");
+    const int w = d.w, h = d.h, pitch = d.pitch, x0 = o.x, y0 = o.y;
+    if (x0 >= r && y0 >= r && x0 + FX + r <= w && y0 + FY + r <= h) {  // no mirrored index
+        const float4 *base = d.nfield + (size_t)(y0 - r) * pitch + (x0 - r);
+        for (int i = threadIdx.x; i < ROWS * COLS; i += FNT_T) {
+            const int ry = i / COLS, rx = i - ry * COLS;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                             (unsigned)__cvta_generic_to_shared(dst + i)),
+                         "l"(base + (size_t)ry * pitch + rx)
+                         : "memory");
+        }
+    } else {
+        for (int i = threadIdx.x; i < ROWS * COLS; i += FNT_T) {
+            const int ry = i / COLS, rx = i - ry * COLS;
+            const float4 *src = d.nfield + (size_t)mirror(y0 - r + ry, h) * pitch + mirror(x0 - r + rx, w);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                             (unsigned)__cvta_generic_to_shared(dst + i)),
+                         "l"(src)
+                         : "memory");
+        }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// The origin of a finish tile, computed once by the thread that looks it up.
+__device__ __forceinline__ int2 finish_origin(const ImgDesc &d, int local)
+{
+    const int tiles_x = (d.w + FX - 1) / FX;
+    const int ty = local / tiles_x;
+    return make_int2((local - ty * tiles_x) * FX, ty * FY);
 }
 
 // The next tile's region is copied (cp.async, double buffer) while the current
@@ -477,6 +494,7 @@ __global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, f
     float4 *srow = fsm4 + 2 * ROWS * COLS;
     __shared__ ImgDesc sdb[2];
     __shared__ int s_localb[2];
+    __shared__ int2 sorg[2];
     __shared__ TileCache tcache;
     const int tid = threadIdx.x;
     float wr[2 * r + 1];
@@ -489,24 +507,26 @@ __global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, f
     if (tid == 0) {
         tc_reset(tcache);
         find_tile_cached(I, SHAPE_SWEEP, t, tcache, sdb[0], s_localb[0]);
+        sorg[0] = finish_origin(sdb[0], s_localb[0]);
     }
     __syncthreads();
-    finish_stage<r>(sdb[0], s_localb[0], fsm4);
+    finish_stage<r>(sdb[0], sorg[0], fsm4);
     for (; t < ntiles; t += gridDim.x) {
         const int tn = t + gridDim.x;
         __syncthreads();  // every thread is done with the previous tile (its slot and buffer)
-        if (tid == 0 && tn < ntiles) find_tile_cached(I, SHAPE_SWEEP, tn, tcache, sdb[cur ^ 1], s_localb[cur ^ 1]);
+        if (tid == 0 && tn < ntiles) {
+            find_tile_cached(I, SHAPE_SWEEP, tn, tcache, sdb[cur ^ 1], s_localb[cur ^ 1]);
+            sorg[cur ^ 1] = finish_origin(sdb[cur ^ 1], s_localb[cur ^ 1]);
+        }
         __syncthreads();
-        if (tn < ntiles) finish_stage<r>(sdb[cur ^ 1], s_localb[cur ^ 1], fsm4 + (cur ^ 1) * ROWS * COLS);
+        if (tn < ntiles) finish_stage<r>(sdb[cur ^ 1], sorg[cur ^ 1], fsm4 + (cur ^ 1) * ROWS * COLS);
         else asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 1;" ::: "memory");
         __syncthreads();  // this tile's region has landed
         const ImgDesc &sd = sdb[cur];
-        const int s_local = s_localb[cur];
         const float4 *sin_ = fsm4 + cur * ROWS * COLS;
         const int w = sd.w, h = sd.h, pitch = sd.pitch;
-        const int tiles_x = (w + FX - 1) / FX;
-        const int x0 = (s_local % tiles_x) * FX, y0 = (s_local / tiles_x) * FY;
+        const int x0 = sorg[cur].x, y0 = sorg[cur].y;
         for (int i = tid; i < ROWS * FX; i += FNT_T) {
             const int ry = i / FX, rx = i - ry * FX;
             float4 a = make_float4(0.f, 0.f, 0.f, 0.f);

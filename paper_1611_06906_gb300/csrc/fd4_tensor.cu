@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
     extern __shared__ __align__(16) float stsm[];
     float *trow = stsm + 2 * ST_CH * SW;  // 3 fields x NB rows x ST_RS; staged rows: two ST_CH x SW buffers
     __shared__ unsigned short plist[ST_TX * ST_CH];
-    __shared__ int wtot[ST_NT / 32 + 1];
+    __shared__ int wtot[ST_NT / 32];
     __shared__ ImgDesc sd[2];
     __shared__ int s_local[2];
     __shared__ SegGeo sg[2];
@@ -410,20 +410,20 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
             }
             if (lane == 0) wtot[warp] = cnt;
             __syncthreads();
-            if (warp == 0) {  // exclusive prefix of the warps' counts, and their total
-                const int c0 = lane < ST_NT / 32 ? wtot[lane] : 0;
-                int c = c0;
-#pragma unroll
-                for (int o = 1; o < ST_NT / 32; o <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, c, o);
-                    if (lane >= o) c += v;
-                }
-                if (lane < ST_NT / 32) wtot[lane] = c - c0;
-                if (lane == ST_NT / 32 - 1) wtot[ST_NT / 32] = c;
-            }
-            __syncthreads();
+            // every warp sums the counts itself: its first list slot and the total
+            int first, total;
             {
-                int pos = wtot[warp];
+                const int c = lane < warp ? wtot[lane] : 0, a = lane < ST_NT / 32 ? wtot[lane] : 0;
+                first = c;
+                total = a;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {  // every lane ends with the sums
+                    first += __shfl_xor_sync(0xffffffffu, first, o);
+                    total += __shfl_xor_sync(0xffffffffu, total, o);
+                }
+            }
+            {
+                int pos = first;
                 const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -433,7 +433,6 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
             }
             __syncthreads();
             // column pass: output row y0 + py reads buffer rows py .. py + 2R
-            const int total = wtot[ST_NT / 32];
             for (int e = tid; e < total; e += ST_NT) {
                 const int entry = plist[e];
                 const int px = entry & 31, py = entry >> 5;
