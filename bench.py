@@ -39,10 +39,10 @@ from paper_1611_06906_gb300.dist import max_over_ranks as _max_over_ranks, rank_
 
 # DRAM bytes (read + write) per pixel and launch of k_fed_tma<2,2> (two quads per
 # thread), from an ncu capture of one launch over the first 8 batch64_fundus
-# images (303.37 + 46.81 MB over 15.13 Mpixel); the roofline's `traffic` scales it
+# images (303.40 + 47.16 MB over 15.13 Mpixel); the roofline's `traffic` scales it
 # to the launch timed here.  Re-measured (or set to None: the field null)
 # whenever that kernel changes.
-TMA2_DRAM_B_PER_PX = 23.14
+TMA2_DRAM_B_PER_PX = 23.17
 METRIC = "Mpixel-steps/s, batched+learned vs plain GB300, at stated FP64-oracle error"
 UNIT = "Mpixel-steps/s"
 
