@@ -25,7 +25,9 @@
  *                         ||P|| <= 34, periodic biharmonic Fourier multiplier
  *   or_filter             whole-filter output: parity unpinned beyond the
  *                         invariants above (the paper prints no numeric
- *                         intermediate for it)
+ *                         intermediate for it); its cycle schedule (one
+ *                         selection, or one per cycle) pinned against the
+ *                         composition of the primitives above
  */
 #include <math.h>
 #include <stdint.h>
@@ -615,18 +617,22 @@ void or_fed_cycle(double *u, int w, int h, const double *tensor,
 /* The whole filter: sigma* once on the input (unless given), then M cycles of
  * (tensor from the current u at sigma*, one FED cycle).  u is filtered in
  * place.  sigma_idx_io: if sigma_given, read; else written.                 */
+/* The whole filter: M cycles of (tensor build at the selected scales, FED
+ * cycle).  The scale image is selected once on the input (the default
+ * reading), or, with reselect, again on the current image u^k before every
+ * cycle's tensor build; a given scale image is used for every cycle.        */
 void or_filter(double *u, int w, int h, const double *sigmas, int n_sigma,
                double lambda, double rho, double beta, double c_in,
                double gamma, int mode, int grad_sq, int boundary,
                const double *tau, int n, int M, uint8_t *sigma_idx_io,
-               int sigma_given)
+               int sigma_given, int reselect)
 {
     size_t np = (size_t)w * h;
-    if (!sigma_given)
-        or_select_scales(u, w, h, sigmas, n_sigma, mode, beta, c_in, gamma,
-                         sigma_idx_io, NULL, NULL);
     double *tensor = malloc(sizeof(double) * 4 * np);
     for (int k = 0; k < M; ++k) {
+        if (!sigma_given && (k == 0 || reselect))
+            or_select_scales(u, w, h, sigmas, n_sigma, mode, beta, c_in, gamma,
+                             sigma_idx_io, NULL, NULL);
         or_build_tensor(u, w, h, sigma_idx_io, sigmas, n_sigma, lambda, rho,
                         mode, grad_sq, tensor, NULL);
         or_fed_cycle(u, w, h, tensor, tau, n, boundary);

@@ -78,7 +78,7 @@ def _load():
                                   ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _u8p,
-                                  ctypes.c_int]
+                                  ctypes.c_int, ctypes.c_int]
         lib.or_num_threads.restype = ctypes.c_int
         _lib = lib
         return lib
@@ -208,8 +208,12 @@ def fed_cycle(u, tensor, tau, boundary=NATURAL):
 
 
 def filter_image(u, sigmas, tau, M, lam=0.005, rho=0.5, beta=0.5, c=0.0, gamma=1.0,
-                 mode=RIDGE, grad_sq=False, boundary=NATURAL, sigma_idx=None):
-    """Whole MAFOD filter (Sec. 3).  Returns (filtered u, sigma_idx)."""
+                 mode=RIDGE, grad_sq=False, boundary=NATURAL, sigma_idx=None, reselect=False):
+    """Whole MAFOD filter (Sec. 3).  Returns (filtered u, sigma_idx).
+
+    reselect: the scale image is selected again on the current image before
+    every cycle (otherwise once, on the input); sigma_idx returned is the last
+    selection."""
     u = _f64(u).copy()
     h, w = u.shape
     sig = _f64(sigmas)
@@ -222,5 +226,6 @@ def filter_image(u, sigmas, tau, M, lam=0.005, rho=0.5, beta=0.5, c=0.0, gamma=1
         given = 1
     _load().or_filter(_d(u), w, h, _d(sig), sig.size, float(lam), float(rho), float(beta),
                       float(c), float(gamma), int(mode), int(bool(grad_sq)), int(boundary),
-                      _d(tau), tau.size, int(M), idx.ctypes.data_as(_u8p), given)
+                      _d(tau), tau.size, int(M), idx.ctypes.data_as(_u8p), given,
+                      int(bool(reselect)))
     return u, idx
