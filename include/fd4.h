@@ -84,6 +84,13 @@ typedef struct fd4_params {
                                 FP32 rounding): 0 = library default (2),
                                 1 = one launch per explicit step, 2..4 = that many
                                 steps fused per launch (see fd4_autotune_batched) */
+    int reselect_each_cycle; /* whole filters (fd4_filter, fd4_filter_batched,
+                                fd4_graph_create): 0 = the scale image is selected
+                                once, on the input (default); 1 = selected again
+                                on the current image u^k before every cycle's
+                                tensor build (the other reading of Eq. 21, where
+                                sigma* is part of P(u^k)).  Ignored when the
+                                caller gives the scale image.                    */
 } fd4_params;
 
 /* Fills *p with the defaults listed above. */

@@ -23,6 +23,7 @@ extern "C" void fd4_default_params(fd4_params *p)
     p->boundary = FD4_BC_NATURAL;
     p->kappa = 0;
     p->grad_norm_squared = 0;
+    p->reselect_each_cycle = 0;
     p->fed_steps_per_launch = 0;
 }
 
@@ -229,6 +230,7 @@ static int check_params(const fd4_params &p)
     if (p.mode < FD4_RIDGE || p.mode > FD4_BOTH) return FD4_ERR_BAD_ARG;
     if (p.boundary != FD4_BC_NATURAL && p.boundary != FD4_BC_PERIODIC) return FD4_ERR_BAD_ARG;
     if (!(p.c >= 0.0f) && !(p.c < 0.0f)) return FD4_ERR_BAD_ARG;  // NaN
+    if (p.reselect_each_cycle != 0 && p.reselect_each_cycle != 1) return FD4_ERR_BAD_ARG;
     return FD4_OK;
 }
 
@@ -332,6 +334,17 @@ extern "C" int fd4_fed_cycle(float *d_u, int w, int h, int pitch, const float *d
 
 // The filter schedule on a batch: selection (unless given), input copy, then M
 // cycles of tensor build and FED cycle.  Everything is enqueued on `st`.
+// The batch as the selection sees it when it re-selects on the current image:
+// every descriptor's input is the image being filtered (u).  Single images
+// carry the descriptor inline; batches have a second device table for it.
+static HostBatch current_view(const HostBatch &B)
+{
+    HostBatch V = B;
+    if (B.I.table) V.I.table = B.table_u;
+    else V.I.one.in = V.I.one.u;
+    return V;
+}
+
 static int enqueue_filter(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
                           const double *tau, int n, int M, int sigma_given, cudaStream_t st,
                           int stages = FD4_STAGES_ALL)
@@ -340,7 +353,10 @@ static int enqueue_filter(const HostBatch &B, const float *h_sigmas, int n_sigma
     if ((stages & FD4_STAGE_SELECT) && !sigma_given && launch_select_batch(B, h_sigmas, n_sigma, p, st))
         return FD4_ERR_CUDA;
     if ((stages & FD4_STAGE_COPY) && launch_copy_in_batch(B, st)) return FD4_ERR_CUDA;
+    const bool reselect = p.reselect_each_cycle && !sigma_given && (stages & FD4_STAGE_SELECT);
     for (int k = 0; k < M; ++k) {
+        if (k > 0 && reselect && launch_select_batch(current_view(B), h_sigmas, n_sigma, p, st))
+            return FD4_ERR_CUDA;
         if ((stages & FD4_STAGE_TENSOR) && launch_tensor_batch(B, h_sigmas, n_sigma, p, st)) return FD4_ERR_CUDA;
         if ((stages & FD4_STAGE_FED) && launch_fed_batch(B, tau, n, p.boundary, steps, st)) return FD4_ERR_CUDA;
     }
@@ -414,6 +430,8 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
                            HostBatch *B, int split = 0, HostBatch *B1 = nullptr)
 {
     size_t off = align_up(sizeof(ImgDesc) * (size_t)n, 256);
+    const size_t tu_off = off;  // the same descriptors with in = u (re-selection)
+    off += align_up(sizeof(ImgDesc) * (size_t)n, 256);
     const size_t ms_off = off;
     off += align_up(sizeof(unsigned) * (size_t)n, 256);
     const size_t maps_off = off;  // TMA tensor maps of the FED kernel, one set per image
@@ -466,6 +484,7 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
         for (int s = 0; s < kShapes; ++s) B->tiles[s] = two ? t_split[s] : t0[s];
         B->max_s2 = (unsigned *)(ws + ms_off);
         B->n_max_s2 = two ? split : n;
+        B->table_u = (const ImgDesc *)(ws + tu_off);
     }
     if (B1 && two) {
         *B1 = *B;
@@ -474,6 +493,7 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
         for (int s = 0; s < kShapes; ++s) B1->tiles[s] = t0[s];
         B1->max_s2 = (unsigned *)(ws + ms_off) + split;
         B1->n_max_s2 = n - split;
+        B1->table_u = (const ImgDesc *)(ws + tu_off) + split;
     }
     return off;
 }
@@ -526,6 +546,22 @@ static int batch_prepare(const fd4_image *imgs, int n_images, const float *h_sig
     return fd4_fed_taus(T, M, p.tau_max, n_in, p.kappa, tau.data(), FD4_MAX_FED_STEPS, &n, nullptr);
 }
 
+// The device tables of a batch: the descriptors, the FED kernel's tensor maps
+// and, when the filter re-selects on the current image, the descriptors with
+// in = u (B.table_u).
+static int put_tables(const std::vector<ImgDesc> &descs, int n, const HostBatch &B, void *d_ws, bool with_u,
+                      cudaStream_t st)
+{
+    if (launch_put_descs(descs.data(), n, (ImgDesc *)d_ws, st)) return 1;
+    if (n > 0 && launch_put_maps(descs.data(), n, (void *)descs[0].maps, st)) return 1;
+    if (with_u) {
+        std::vector<ImgDesc> du(descs);
+        for (ImgDesc &d : du) d.in = d.u;
+        if (launch_put_descs(du.data(), n, (ImgDesc *)B.table_u, st)) return 1;
+    }
+    return 0;
+}
+
 // Two image groups on two streams: group 1 starts once group 0's first tensor
 // build is done, so from then on one group's FED steps (latency-bound) tend to
 // run beside the other group's tensor build (FMA-bound).  Each kernel's
@@ -540,8 +576,8 @@ static int enqueue_batch_two_streams(const fd4_image *imgs, int n_images, const 
     HostBatch B0, B1;
     const int split = balanced_split(imgs, n_images);
     batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B0, split, &B1);
-    if (launch_put_descs(descs.data(), n_images, (ImgDesc *)d_ws, s0)) return FD4_ERR_CUDA;
-    if (n_images > 0 && launch_put_maps(descs.data(), n_images, (void *)descs[0].maps, s0)) return FD4_ERR_CUDA;
+    const bool reselect = p.reselect_each_cycle && !sigma_given;
+    if (put_tables(descs, n_images, B0, d_ws, reselect, s0)) return FD4_ERR_CUDA;
     const int steps = p.fed_steps_per_launch > 0 ? p.fed_steps_per_launch : default_steps_per_launch();
     if (cudaEventRecord(ev_fork, s0) != cudaSuccess || cudaStreamWaitEvent(s1, ev_fork, 0) != cudaSuccess)
         return FD4_ERR_CUDA;
@@ -558,7 +594,11 @@ static int enqueue_batch_two_streams(const fd4_image *imgs, int n_images, const 
         rc = FD4_ERR_CUDA;
     for (int k = 0; k < M && rc == FD4_OK; ++k) {
         if (launch_fed_batch(B0, tau, n, p.boundary, steps, s0)) rc = FD4_ERR_CUDA;
+        if (rc == FD4_OK && k + 1 < M && reselect && launch_select_batch(current_view(B0), h_sigmas, n_sigma, p, s0))
+            rc = FD4_ERR_CUDA;
         if (rc == FD4_OK && k + 1 < M && launch_tensor_batch(B0, h_sigmas, n_sigma, p, s0)) rc = FD4_ERR_CUDA;
+        if (rc == FD4_OK && k > 0 && reselect && launch_select_batch(current_view(B1), h_sigmas, n_sigma, p, s1))
+            rc = FD4_ERR_CUDA;
         if (rc == FD4_OK && launch_tensor_batch(B1, h_sigmas, n_sigma, p, s1)) rc = FD4_ERR_CUDA;
         if (rc == FD4_OK && launch_fed_batch(B1, tau, n, p.boundary, steps, s1)) rc = FD4_ERR_CUDA;
     }
@@ -575,8 +615,8 @@ static int enqueue_batch(const fd4_image *imgs, int n_images, const float *h_sig
     std::vector<ImgDesc> descs;
     HostBatch B;
     batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B);
-    if (launch_put_descs(descs.data(), n_images, (ImgDesc *)d_ws, st)) return FD4_ERR_CUDA;
-    if (n_images > 0 && launch_put_maps(descs.data(), n_images, (void *)descs[0].maps, st)) return FD4_ERR_CUDA;
+    const bool reselect = p.reselect_each_cycle && !sigma_given && (stages & FD4_STAGE_SELECT);
+    if (put_tables(descs, n_images, B, d_ws, reselect, st)) return FD4_ERR_CUDA;
     return enqueue_filter(B, h_sigmas, n_sigma, p, tau, n, M, sigma_given, st, stages);
 }
 

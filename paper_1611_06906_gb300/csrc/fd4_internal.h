@@ -234,6 +234,7 @@ struct HostBatch {
     int tiles[kShapes];
     unsigned *max_s2;
     int n_max_s2;
+    const ImgDesc *table_u;  // batches: the descriptor table with in = u (nullptr for single images)
 };
 
 // One image: inline descriptor.
@@ -244,6 +245,7 @@ inline HostBatch single_batch(const ImgDesc &d)
     for (int s = 0; s < kShapes; ++s) B.tiles[s] = tiles_of(d.w, d.h, s);
     B.max_s2 = d.max_s2;
     B.n_max_s2 = 1;
+    B.table_u = nullptr;
     return B;
 }
 

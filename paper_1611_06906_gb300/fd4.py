@@ -40,7 +40,8 @@ class Params(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_float), ("rho", ctypes.c_float), ("beta", ctypes.c_float),
                 ("c", ctypes.c_float), ("gamma", ctypes.c_float), ("tau_max", ctypes.c_float),
                 ("mode", ctypes.c_int), ("boundary", ctypes.c_int), ("kappa", ctypes.c_int),
-                ("grad_norm_squared", ctypes.c_int), ("fed_steps_per_launch", ctypes.c_int)]
+                ("grad_norm_squared", ctypes.c_int), ("fed_steps_per_launch", ctypes.c_int),
+                ("reselect_each_cycle", ctypes.c_int)]
 
 
 class Image(ctypes.Structure):

@@ -33,6 +33,7 @@ def test_defaults_and_strerror():
     p = fd4.params()
     assert abs(p.lambda_ - 0.005) < 1e-9 and p.rho == 0.5 and p.beta == 0.5 and p.tau_max == pytest.approx(0.05)
     assert p.mode == fd4.BOTH and p.boundary == fd4.NATURAL and p.c == 0.0 and p.gamma == 1.0
+    assert p.reselect_each_cycle == 0 and p.grad_norm_squared == 0 and p.fed_steps_per_launch == 0
     assert fd4.strerror(0) == "ok"
     assert "workspace" in fd4.strerror(-5)
     assert fd4.lib().fd4_version() >= 100
@@ -104,3 +105,35 @@ def test_host_side_argument_errors():
     p = fd4.params(tau_max=0.05)
     assert L.fd4_filter(fake, fake, 8, 8, 8, sig, 2, ctypes.byref(p), 35.0, 5, 10, None, 0, ws,
                         1 << 40, None) == -2
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of fd4_params and fd4_image have the header's size and
+    field offsets (compiled with the host C compiler)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"fd4_params": fd4.Params, "fd4_image": fd4.Image}
+    lines = ['#include <stdio.h>', '#include "fd4.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in py._fields_:
+            c_field = "lambda" if fname == "lambda_" else fname
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, c_field))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            a, b, v = line.split()
+            got[(a, b)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py)
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

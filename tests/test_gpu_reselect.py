@@ -1,0 +1,109 @@
+"""Re-selection of the scale image before every cycle (reselect_each_cycle:
+sigma* from the current image u^k, the other reading of Eq. 21) on the
+per-image entry point, the batched path, its CUDA graph and the two-stream
+graph, against the FP64 oracle's schedule and each other."""
+import numpy as np
+import pytest
+
+from paper_1611_06906_gb300 import fd4, synth
+
+pytestmark = pytest.mark.gpu
+
+SIGMAS = [1.0, 1.6, 2.5, 4.0]
+M, N = 3, 10
+T = M * N * (N + 1) * 0.05 / 3
+
+
+def _images():
+    shapes = [(128, 128), (53, 37), (150, 211), (97, 64), (61, 300)]
+    return [synth.vessel_tree(4200 + i, w, h, depth=4, r0=4.0) for i, (h, w) in enumerate(shapes)]
+
+
+def _batch(imgs):
+    import torch
+    ins = [fd4.to_device(im) for im in imgs]
+    outs = [torch.zeros_like(u) for u in ins]
+    idx = [torch.zeros(u.shape, dtype=torch.uint8, device="cuda") for u in ins]
+    return ins, outs, idx, fd4.image_list(ins, [im.shape[1] for im in imgs], outs, idx)
+
+
+@pytest.mark.parametrize("mode", [fd4.VALLEY, fd4.BOTH])
+def test_reselect_matches_oracle(oracle, mode):
+    imgs = _images()
+    ins, outs, idx, lst = _batch(imgs)
+    fd4.filter_batched(lst, SIGMAS, T, M, N, fd4.params(mode=mode, reselect_each_cycle=1))
+    tau, _, _ = oracle.fed_taus(T, M, 0.05, n=N)
+    for k in (0, 2, 3):
+        im = imgs[k]
+        w = im.shape[1]
+        ref, ridx = oracle.filter_image(im, SIGMAS, tau, M, mode=mode, reselect=True)
+        agree = float((idx[k][:, :w].cpu().numpy() == ridx).mean())
+        assert agree >= 0.99
+        if agree == 1.0:
+            assert np.abs(outs[k][:, :w].cpu().numpy() - ref).max() <= 1e-4
+
+
+def test_reselect_batched_graph_and_two_streams_equal_per_image():
+    import torch
+    imgs = _images()
+    prm = fd4.params(mode=fd4.VALLEY, reselect_each_cycle=1)
+    ins, outs, idx, lst = _batch(imgs)
+    fd4.filter_batched(lst, SIGMAS, T, M, N, prm)
+    torch.cuda.synchronize()
+    ref = [o.clone() for o in outs]
+    ref_idx = [i.clone() for i in idx]
+    for im, u_in, o, ix in zip(imgs, ins, outs, idx):
+        w = im.shape[1]
+        single, single_idx = fd4.filter_image(u_in, w, SIGMAS, T, M, N, prm)
+        assert torch.equal(ix[:, :w], single_idx[:, :w])
+        assert float((o[:, :w] - single[:, :w]).abs().max()) == 0.0
+    for stages in (15, 15 | fd4.GRAPH_TWO_STREAMS):
+        for o in outs:
+            o.zero_()
+        for i in idx:
+            i.zero_()
+        g = fd4.Graph(lst, SIGMAS, T, M, N, prm, stages=stages)
+        g.launch()
+        torch.cuda.synchronize()
+        for o, r, ix, ri, im in zip(outs, ref, idx, ref_idx, imgs):
+            w = im.shape[1]
+            assert torch.equal(ix[:, :w], ri[:, :w])
+            assert float((o[:, :w] - r[:, :w]).abs().max()) == 0.0
+        g.close()
+
+
+def test_reselect_schedule_and_launch_count():
+    import torch
+    imgs = _images()
+    once = fd4.params(mode=fd4.VALLEY)
+    again = fd4.params(mode=fd4.VALLEY, reselect_each_cycle=1)
+    # one cycle: both schedules are the same filter
+    a = _batch(imgs)
+    b = _batch(imgs)
+    fd4.filter_batched(a[3], SIGMAS, T / M, 1, N, once)
+    fd4.filter_batched(b[3], SIGMAS, T / M, 1, N, again)
+    torch.cuda.synchronize()
+    for x, y in zip(a[1], b[1]):
+        assert torch.equal(x, y)
+    # several cycles: the last selection follows the filtered image
+    a = _batch(imgs)
+    b = _batch(imgs)
+    fd4.filter_batched(a[3], SIGMAS, T, M, N, once)
+    fd4.filter_batched(b[3], SIGMAS, T, M, N, again)
+    torch.cuda.synchronize()
+    assert any(not torch.equal(x, y) for x, y in zip(a[2], b[2]))
+    # the graph holds (M - 1) more selections (K strip launches and the argmax
+    # each) and the copy of the descriptor table the re-selection reads
+    ga = fd4.Graph(a[3], SIGMAS, T, M, N, once)
+    gb = fd4.Graph(b[3], SIGMAS, T, M, N, again)
+    assert gb.kernel_count() == ga.kernel_count() + (M - 1) * (len(SIGMAS) + 1) + 1
+    ga.close()
+    gb.close()
+
+
+def test_reselect_flag_is_validated():
+    import torch
+    u = fd4.to_device(synth.vessel_tree(4300, 32, 32, depth=3, r0=3.0))
+    with pytest.raises(fd4.Fd4Error):
+        fd4.filter_image(u, 32, SIGMAS, T, M, N, fd4.params(reselect_each_cycle=2))
+    torch.cuda.synchronize()
