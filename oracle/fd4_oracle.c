@@ -23,6 +23,10 @@
  *                         parameter sets, cycle polynomial bound
  *   or_apply_P / or_fed_*  pinned: dense P symmetric PSD, P1 = 0, 1'P = 0,
  *                         ||P|| <= 34, periodic biharmonic Fourier multiplier
+ *   or_postprocess_*      pinned: hand-built cross-sections along the axes and
+ *                         the diagonal (row, column and diagonal means), the
+ *                         walk cap, empty mask, isotropic Hessians, a straight
+ *                         ridge (one scale per cross-section)
  *   or_filter             whole-filter output: parity unpinned beyond the
  *                         invariants above (the paper prints no numeric
  *                         intermediate for it); its cycle schedule (one
@@ -268,6 +272,121 @@ double or_select_scales(const double *u, int w, int h, const double *sigmas,
     }
     free(nu1); free(nu2); free(a); free(b); free(d);
     return c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Scale-image post-processing (Sec. 3.3, the paragraphs after Eq. 9).  Pixels
+ * whose vesselness V = max_sigma V_sigma exceeds theta form the vessel mask.
+ * For a mask pixel p the vessel cross-section through p is traced along the
+ * eigenvector of the Hessian at p's selected scale that belongs to the
+ * eigenvalue of largest magnitude (the one the tie rule of or_select_scales
+ * calls nu2: on equal magnitudes the negative one), and p takes the scale of
+ * the set nearest to the mean scale of the cross-section's pixels.
+ * Readings (the paper gives no discretisation): the cross-section is the
+ * digital line through p with one pixel per unit step along its major axis
+ * (the minor coordinate rounded half up), walked both ways from p while the
+ * pixels lie inside the image and the mask, at most cap pixels per side; an
+ * isotropic Hessian (equal eigenvalues) gives no direction and p keeps its
+ * scale; ties of the nearest scale go to the smaller sigma; all pixels are
+ * updated from the scale image as selected, not from updated neighbours.     */
+
+/* Unit eigenvector of [a b; b d] for its eigenvalue of largest magnitude
+ * (the negative one on a tie); 0 if the eigenvalues are equal.              */
+int or_strong_direction(double a, double b, double d, double *ex, double *ey)
+{
+    double m = 0.5 * (a + d), q = 0.5 * (a - d);
+    double r = hypot(q, b);
+    if (r == 0.0)
+        return 0;
+    double vx, vy; /* eigenvector of m + r: a row of [q - r, b; b, -q - r] is orthogonal to it */
+    if (q >= 0.0) { vx = q + r; vy = b; }
+    else          { vx = b;     vy = r - q; }
+    double n = hypot(vx, vy);
+    vx /= n;
+    vy /= n;
+    if (fabs(m + r) > fabs(m - r)) { *ex = vx;  *ey = vy; }
+    else                            { *ex = -vy; *ey = vx; }
+    return 1;
+}
+
+/* The post-processing from given Hessian fields (any positive multiple of the
+ * Hessian at each pixel's selected scale gives the same directions).        */
+void or_postprocess_core(uint8_t *idx_io, const double *vmax, const double *hxx,
+                         const double *hxy, const double *hyy, int w, int h,
+                         const double *sigmas, int n_sigma, double theta, int cap)
+{
+    size_t np = (size_t)w * h;
+    uint8_t *out = malloc(np);
+    memcpy(out, idx_io, np);
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            size_t p = (size_t)y * w + x;
+            double ex, ey;
+            if (!(vmax[p] > theta) || !or_strong_direction(hxx[p], hxy[p], hyy[p], &ex, &ey))
+                continue;
+            double mx = fmax(fabs(ex), fabs(ey));
+            double sx = ex / mx, sy = ey / mx; /* one of them is +-1 */
+            double sum = sigmas[idx_io[p]];
+            int cnt = 1;
+            for (int dir = -1; dir <= 1; dir += 2)
+                for (int k = 1; k <= cap; ++k) {
+                    int qx = x + (int)floor(dir * k * sx + 0.5);
+                    int qy = y + (int)floor(dir * k * sy + 0.5);
+                    if (qx < 0 || qy < 0 || qx >= w || qy >= h)
+                        break;
+                    size_t q = (size_t)qy * w + qx;
+                    if (!(vmax[q] > theta))
+                        break;
+                    sum += sigmas[idx_io[q]];
+                    ++cnt;
+                }
+            double mean = sum / cnt;
+            int arg = 0;
+            double best = fabs(sigmas[0] - mean);
+            for (int s = 1; s < n_sigma; ++s) {
+                double dd = fabs(sigmas[s] - mean);
+                if (dd < best) {
+                    best = dd;
+                    arg = s;
+                }
+            }
+            out[p] = (uint8_t)arg;
+        }
+    memcpy(idx_io, out, np);
+    free(out);
+}
+
+/* The post-processing of the scale image selected on u: the Hessian of u_sigma
+ * at each pixel's selected scale, the walk capped at the largest kernel radius
+ * ceil(4 sigma_max).                                                         */
+void or_postprocess_scales(const double *u, int w, int h, uint8_t *idx_io,
+                           const double *vmax, const double *sigmas, int n_sigma,
+                           double theta)
+{
+    size_t np = (size_t)w * h;
+    double *hxx = calloc(np, sizeof(double));
+    double *hxy = calloc(np, sizeof(double));
+    double *hyy = calloc(np, sizeof(double));
+    double *a = malloc(sizeof(double) * np);
+    double *b = malloc(sizeof(double) * np);
+    double *d = malloc(sizeof(double) * np);
+    for (int s = 0; s < n_sigma; ++s) {
+        or_derivatives(u, w, h, sigmas[s], NULL, NULL, a, b, d);
+        for (size_t p = 0; p < np; ++p)
+            if (idx_io[p] == s) {
+                hxx[p] = a[p];
+                hxy[p] = b[p];
+                hyy[p] = d[p];
+            }
+    }
+    double smax = sigmas[0];
+    for (int s = 1; s < n_sigma; ++s)
+        if (sigmas[s] > smax)
+            smax = sigmas[s];
+    or_postprocess_core(idx_io, vmax, hxx, hxy, hyy, w, h, sigmas, n_sigma, theta,
+                        or_gauss_radius(smax));
+    free(hxx); free(hxy); free(hyy); free(a); free(b); free(d);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -620,22 +739,29 @@ void or_fed_cycle(double *u, int w, int h, const double *tensor,
 /* The whole filter: M cycles of (tensor build at the selected scales, FED
  * cycle).  The scale image is selected once on the input (the default
  * reading), or, with reselect, again on the current image u^k before every
- * cycle's tensor build; a given scale image is used for every cycle.        */
+ * cycle's tensor build; with postprocess every selection is followed by the
+ * scale-image post-processing at threshold theta; a given scale image is used
+ * for every cycle as it is.                                                  */
 void or_filter(double *u, int w, int h, const double *sigmas, int n_sigma,
                double lambda, double rho, double beta, double c_in,
                double gamma, int mode, int grad_sq, int boundary,
                const double *tau, int n, int M, uint8_t *sigma_idx_io,
-               int sigma_given, int reselect)
+               int sigma_given, int reselect, int postprocess, double theta)
 {
     size_t np = (size_t)w * h;
     double *tensor = malloc(sizeof(double) * 4 * np);
+    double *vmax = postprocess ? malloc(sizeof(double) * np) : NULL;
     for (int k = 0; k < M; ++k) {
-        if (!sigma_given && (k == 0 || reselect))
+        if (!sigma_given && (k == 0 || reselect)) {
             or_select_scales(u, w, h, sigmas, n_sigma, mode, beta, c_in, gamma,
-                             sigma_idx_io, NULL, NULL);
+                             sigma_idx_io, vmax, NULL);
+            if (postprocess)
+                or_postprocess_scales(u, w, h, sigma_idx_io, vmax, sigmas, n_sigma, theta);
+        }
         or_build_tensor(u, w, h, sigma_idx_io, sigmas, n_sigma, lambda, rho,
                         mode, grad_sq, tensor, NULL);
         or_fed_cycle(u, w, h, tensor, tau, n, boundary);
     }
     free(tensor);
+    free(vmax);
 }

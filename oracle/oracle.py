@@ -78,7 +78,13 @@ def _load():
                                   ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _u8p,
-                                  ctypes.c_int, ctypes.c_int]
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        lib.or_strong_direction.argtypes = [ctypes.c_double] * 3 + [_dp, _dp]
+        lib.or_strong_direction.restype = ctypes.c_int
+        lib.or_postprocess_core.argtypes = [_u8p, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp,
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_int]
+        lib.or_postprocess_scales.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _u8p, _dp, _dp,
+                                              ctypes.c_int, ctypes.c_double]
         lib.or_num_threads.restype = ctypes.c_int
         _lib = lib
         return lib
@@ -207,13 +213,50 @@ def fed_cycle(u, tensor, tau, boundary=NATURAL):
     return u
 
 
+def strong_direction(a, b, d):
+    """Unit eigenvector of [a b; b d] for its eigenvalue of largest magnitude
+    (the negative one on a tie), or None for equal eigenvalues."""
+    ex, ey = np.zeros(1), np.zeros(1)
+    if not _load().or_strong_direction(float(a), float(b), float(d), _d(ex), _d(ey)):
+        return None
+    return float(ex[0]), float(ey[0])
+
+
+def postprocess_core(sigma_idx, vmax, hxx, hxy, hyy, sigmas, theta, cap):
+    """Scale-image post-processing (Sec. 3.3, after Eq. 9) from given Hessian
+    fields; returns the new scale index image."""
+    idx = np.ascontiguousarray(sigma_idx, dtype=np.uint8).copy()
+    h, w = idx.shape
+    f = [_f64(a) for a in (vmax, hxx, hxy, hyy)]
+    assert all(a.shape == (h, w) for a in f)
+    sig = _f64(sigmas)
+    _load().or_postprocess_core(idx.ctypes.data_as(_u8p), _d(f[0]), _d(f[1]), _d(f[2]), _d(f[3]), w, h,
+                                _d(sig), sig.size, float(theta), int(cap))
+    return idx
+
+
+def postprocess_scales(u, sigma_idx, vmax, sigmas, theta):
+    """Scale-image post-processing of the scale image selected on u (Hessian at
+    each pixel's selected scale, walk capped at ceil(4 sigma_max))."""
+    u = _f64(u)
+    h, w = u.shape
+    idx = np.ascontiguousarray(sigma_idx, dtype=np.uint8).copy()
+    vm = _f64(vmax)
+    sig = _f64(sigmas)
+    _load().or_postprocess_scales(_d(u), w, h, idx.ctypes.data_as(_u8p), _d(vm), _d(sig), sig.size,
+                                  float(theta))
+    return idx
+
+
 def filter_image(u, sigmas, tau, M, lam=0.005, rho=0.5, beta=0.5, c=0.0, gamma=1.0,
-                 mode=RIDGE, grad_sq=False, boundary=NATURAL, sigma_idx=None, reselect=False):
+                 mode=RIDGE, grad_sq=False, boundary=NATURAL, sigma_idx=None, reselect=False,
+                 postprocess=False, theta=0.2):
     """Whole MAFOD filter (Sec. 3).  Returns (filtered u, sigma_idx).
 
     reselect: the scale image is selected again on the current image before
-    every cycle (otherwise once, on the input); sigma_idx returned is the last
-    selection."""
+    every cycle (otherwise once, on the input); postprocess: every selection is
+    followed by the scale-image post-processing at threshold theta; sigma_idx
+    returned is the last (post-processed) selection."""
     u = _f64(u).copy()
     h, w = u.shape
     sig = _f64(sigmas)
@@ -227,5 +270,5 @@ def filter_image(u, sigmas, tau, M, lam=0.005, rho=0.5, beta=0.5, c=0.0, gamma=1
     _load().or_filter(_d(u), w, h, _d(sig), sig.size, float(lam), float(rho), float(beta),
                       float(c), float(gamma), int(mode), int(bool(grad_sq)), int(boundary),
                       _d(tau), tau.size, int(M), idx.ctypes.data_as(_u8p), given,
-                      int(bool(reselect)))
+                      int(bool(reselect)), int(bool(postprocess)), float(theta))
     return u, idx
