@@ -288,7 +288,9 @@ double or_select_scales(const double *u, int w, int h, const double *sigmas,
  * pixels lie inside the image and the mask, at most cap pixels per side; an
  * isotropic Hessian (equal eigenvalues) gives no direction and p keeps its
  * scale; ties of the nearest scale go to the smaller sigma; all pixels are
- * updated from the scale image as selected, not from updated neighbours.     */
+ * updated from the scale image as selected, not from updated neighbours; an
+ * index outside the scale set (only a caller-given scale image has one) keeps
+ * its value and ends a walk like a pixel outside the mask.                   */
 
 /* Unit eigenvector of [a b; b d] for its eigenvalue of largest magnitude
  * (the negative one on a tie); 0 if the eigenvalues are equal.              */
@@ -323,7 +325,8 @@ void or_postprocess_core(uint8_t *idx_io, const double *vmax, const double *hxx,
         for (int x = 0; x < w; ++x) {
             size_t p = (size_t)y * w + x;
             double ex, ey;
-            if (!(vmax[p] > theta) || !or_strong_direction(hxx[p], hxy[p], hyy[p], &ex, &ey))
+            if (idx_io[p] >= n_sigma || !(vmax[p] > theta) ||
+                !or_strong_direction(hxx[p], hxy[p], hyy[p], &ex, &ey))
                 continue;
             double mx = fmax(fabs(ex), fabs(ey));
             double sx = ex / mx, sy = ey / mx; /* one of them is +-1 */
@@ -336,7 +339,7 @@ void or_postprocess_core(uint8_t *idx_io, const double *vmax, const double *hxx,
                     if (qx < 0 || qy < 0 || qx >= w || qy >= h)
                         break;
                     size_t q = (size_t)qy * w + qx;
-                    if (!(vmax[q] > theta))
+                    if (!(vmax[q] > theta) || idx_io[q] >= n_sigma)
                         break;
                     sum += sigmas[idx_io[q]];
                     ++cnt;

@@ -152,3 +152,14 @@ def test_digital_line_of_slope_one_third(oracle):
     out = oracle.postprocess_core(idx, np.ones((h, w)), *_fields(h, w, H[0, 0], H[0, 1], H[1, 1]), SIG, 0.2, 3)
     cells = [(3, 2), (3, 3), (4, 4), (4, 5), (4, 6), (5, 7), (5, 8)]  # (y, x)
     assert out[4, 5] == _nearest(np.mean([SIG[idx[y, x]] for y, x in cells]))
+
+
+def test_index_outside_the_set_ends_the_walk(oracle):
+    h, w = 3, 9
+    idx = np.full((h, w), 1, dtype=np.uint8)
+    idx[:, 0:3] = 3
+    idx[:, 4] = 7  # not a scale of the set: kept, and it cuts the rows at x = 4
+    out = oracle.postprocess_core(idx, np.ones((h, w)), *_fields(h, w, -1, 0, 0), SIG, 0.2, 100)
+    assert np.all(out[:, 4] == 7)
+    assert np.all(out[:, 0:4] == _nearest(SIG[[3, 3, 3, 1]].mean()))
+    assert np.all(out[:, 5:] == 1)
