@@ -91,6 +91,14 @@ typedef struct fd4_params {
                                 tensor build (the other reading of Eq. 21, where
                                 sigma* is part of P(u^k)).  Ignored when the
                                 caller gives the scale image.                    */
+    int postprocess_scales;  /* whole filters: 0 = the scale image as selected
+                                (default); 1 = every selection is followed by
+                                the scale-image post-processing of Sec. 3.3 (see
+                                fd4_postprocess_scales).  Ignored when the caller
+                                gives the scale image.                           */
+    float theta;             /* vesselness threshold of the post-processing's
+                                vessel mask, in [0, 1] (default 0.2, the paper's
+                                synthetic setting; 0.13 for its fundus images)   */
 } fd4_params;
 
 /* Fills *p with the defaults listed above. */
@@ -126,7 +134,8 @@ typedef enum fd4_op {
     FD4_OP_SELECT_SCALES = 0,
     FD4_OP_BUILD_TENSOR = 1,
     FD4_OP_FED_CYCLE = 2,
-    FD4_OP_FILTER = 3
+    FD4_OP_FILTER = 3,
+    FD4_OP_POSTPROCESS = 4
 } fd4_op;
 size_t fd4_workspace_bytes(int op, int w, int h, int n_sigma);
 
@@ -146,6 +155,27 @@ int fd4_select_scales(const float *d_img, int w, int h, int pitch,
                       const float *h_sigmas, int n_sigma, const fd4_params *params,
                       uint8_t *d_sigma_idx, float *d_vmax,
                       void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+
+/* Scale-image post-processing (Sec. 3.3, the paragraphs after Eq. 9), in place
+ * on d_sigma_idx: the pixels whose vesselness d_vmax exceeds params->theta form
+ * the vessel mask; each of them takes the scale of the set nearest to the mean
+ * scale of its vessel cross-section.  The cross-section is traced from the
+ * pixel along the eigenvector of the Hessian of u_sigma at the pixel's selected
+ * scale that belongs to the eigenvalue of largest magnitude (the negative one
+ * on a tie): the digital line with one pixel per unit step along its major
+ * axis (minor coordinate rounded half up), walked both ways while it stays in
+ * the image and the mask, at most ceil(4 sigma_max) pixels per side.  Pixels
+ * outside the mask, pixels whose Hessian has equal eigenvalues and pixels
+ * whose index is not < n_sigma keep their index; an index not < n_sigma also
+ * ends a walk.  All pixels are updated from the scale image as given.
+ *   d_u          image the scales were selected on, float32 (h, pitch)
+ *   d_sigma_idx  uint8 (h, pitch): selected scale indices in, post-processed out
+ *   d_vmax       float32 (h, pitch): max_sigma V_sigma (fd4_select_scales' v_max)
+ *   workspace    fd4_workspace_bytes(FD4_OP_POSTPROCESS, pitch, h, n_sigma)
+ * Errors as for fd4_select_scales; nothing is written on an error.          */
+int fd4_postprocess_scales(const float *d_u, int w, int h, int pitch, uint8_t *d_sigma_idx,
+                           const float *d_vmax, const float *h_sigmas, int n_sigma,
+                           const fd4_params *params, void *d_ws, size_t ws_bytes, fd4_stream_t stream);
 
 /* Fourth-order diffusion tensor field (Sec. 3.1 Eq. 6, Sec. 3.2 Eq. 7-8).
  * N = H(u_s) / sqrt(1 + |grad u_s|) at s = h_sigmas[d_sigma_idx[p]] per pixel

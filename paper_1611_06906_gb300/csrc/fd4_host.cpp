@@ -24,6 +24,8 @@ extern "C" void fd4_default_params(fd4_params *p)
     p->kappa = 0;
     p->grad_norm_squared = 0;
     p->reselect_each_cycle = 0;
+    p->postprocess_scales = 0;
+    p->theta = 0.2f;
     p->fed_steps_per_launch = 0;
 }
 
@@ -231,6 +233,8 @@ static int check_params(const fd4_params &p)
     if (p.boundary != FD4_BC_NATURAL && p.boundary != FD4_BC_PERIODIC) return FD4_ERR_BAD_ARG;
     if (!(p.c >= 0.0f) && !(p.c < 0.0f)) return FD4_ERR_BAD_ARG;  // NaN
     if (p.reselect_each_cycle != 0 && p.reselect_each_cycle != 1) return FD4_ERR_BAD_ARG;
+    if (p.postprocess_scales != 0 && p.postprocess_scales != 1) return FD4_ERR_BAD_ARG;
+    if (!(p.theta >= 0.0f && p.theta <= 1.0f)) return FD4_ERR_BAD_ARG;
     return FD4_OK;
 }
 
@@ -266,6 +270,7 @@ extern "C" size_t fd4_workspace_bytes(int op, int w, int h, int n_sigma)
     case FD4_OP_BUILD_TENSOR: return ws_tensor_bytes(h, pitch);
     case FD4_OP_FED_CYCLE: return ws_fed_bytes(h, pitch);
     case FD4_OP_FILTER: return ws_filter_bytes(h, pitch, n_sigma);
+    case FD4_OP_POSTPROCESS: return plane_bytes(h, pitch, 16) + plane_bytes(h, pitch, 1);
     default: return 0;
     }
 }
@@ -297,6 +302,33 @@ extern "C" int fd4_select_scales(const float *d_img, int w, int h, int pitch, co
     if ((rc = ws_ok(d_ws, ws_bytes, ws_select_bytes(h, pitch, n_sigma))) != FD4_OK) return rc;
     return cuda_status(launch_select(d_img, w, h, pitch, h_sigmas, n_sigma, p, d_sigma_idx, d_vmax,
                                      (char *)d_ws, (cudaStream_t)stream));
+}
+
+extern "C" int fd4_postprocess_scales(const float *d_u, int w, int h, int pitch, uint8_t *d_sigma_idx,
+                                      const float *d_vmax, const float *h_sigmas, int n_sigma,
+                                      const fd4_params *params, void *d_ws, size_t ws_bytes, fd4_stream_t stream)
+{
+    int rc;
+    fd4_params p;
+    resolve_params(params, &p);
+    if ((rc = check_image(d_u, w, h, pitch)) != FD4_OK) return rc;
+    if ((rc = check_sigmas(h_sigmas, n_sigma)) != FD4_OK) return rc;
+    if ((rc = check_params(p)) != FD4_OK) return rc;
+    if (!d_sigma_idx || !d_vmax) return FD4_ERR_BAD_ARG;
+    if ((uintptr_t)d_vmax & 3u) return FD4_ERR_ALIGN;
+    const size_t p16 = plane_bytes(h, pitch, 16);
+    if ((rc = ws_ok(d_ws, ws_bytes, p16 + plane_bytes(h, pitch, 1))) != FD4_OK) return rc;
+    // workspace: [N at the selected scales | second index plane]
+    ImgDesc d{};
+    d.u = const_cast<float *>(d_u);  // read only
+    d.idx = d_sigma_idx;
+    d.vmax = const_cast<float *>(d_vmax);  // read only
+    d.nfield = (float4 *)d_ws;
+    d.idx2 = (uint8_t *)d_ws + p16;
+    d.w = w;
+    d.h = h;
+    d.pitch = pitch;
+    return cuda_status(launch_postprocess_batch(single_batch(d), h_sigmas, n_sigma, p, (cudaStream_t)stream));
 }
 
 extern "C" int fd4_build_tensor(const float *d_u, int w, int h, int pitch, const uint8_t *d_sigma_idx,
@@ -353,9 +385,15 @@ static int enqueue_filter(const HostBatch &B, const float *h_sigmas, int n_sigma
     if ((stages & FD4_STAGE_SELECT) && !sigma_given && launch_select_batch(B, h_sigmas, n_sigma, p, st))
         return FD4_ERR_CUDA;
     if ((stages & FD4_STAGE_COPY) && launch_copy_in_batch(B, st)) return FD4_ERR_CUDA;
+    // the post-processing reads u (the strips' N at the selected scales), so the
+    // first one follows the copy of the input into u
+    const bool post = p.postprocess_scales && !sigma_given && (stages & FD4_STAGE_SELECT);
+    if (post && launch_postprocess_batch(B, h_sigmas, n_sigma, p, st)) return FD4_ERR_CUDA;
     const bool reselect = p.reselect_each_cycle && !sigma_given && (stages & FD4_STAGE_SELECT);
     for (int k = 0; k < M; ++k) {
         if (k > 0 && reselect && launch_select_batch(current_view(B), h_sigmas, n_sigma, p, st))
+            return FD4_ERR_CUDA;
+        if (k > 0 && reselect && post && launch_postprocess_batch(B, h_sigmas, n_sigma, p, st))
             return FD4_ERR_CUDA;
         if ((stages & FD4_STAGE_TENSOR) && launch_tensor_batch(B, h_sigmas, n_sigma, p, st)) return FD4_ERR_CUDA;
         if ((stages & FD4_STAGE_FED) && launch_fed_batch(B, tau, n, p.boundary, steps, st)) return FD4_ERR_CUDA;
@@ -403,7 +441,11 @@ extern "C" int fd4_filter(const float *d_in, float *d_out, int w, int h, int pit
     d.nfield = (float4 *)scratch;
     d.tensor = (float4 *)(ws + plane_bytes(h, pitch, 1));
     d.idx = d_sigma_idx ? d_sigma_idx : (uint8_t *)ws;
-    d.vmax = nullptr;
+    // post-processing: V_max (4 B per pixel) and the second index plane (1 B)
+    // packed into the tensor plane (16 B per pixel), which no stage uses
+    // between a selection and the cycle's tensor build
+    d.vmax = (p.postprocess_scales && !sigma_given) ? (float *)d.tensor : nullptr;
+    d.idx2 = (uint8_t *)d.tensor + 4 * (size_t)h * pitch;
     d.max_s2 = &((WsHeader *)sws)->max_s2;
     d.plane = pb / 4;
     d.w = w;
@@ -427,7 +469,7 @@ static size_t scratch_bytes(int h, int pitch, int n_sigma)
 // split (0 < split < n): images [split, n) form a second group whose tile
 // numbering restarts at 0 and which B1 describes (B covers [0, split)).
 static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vector<ImgDesc> *descs, char *ws,
-                           HostBatch *B, int split = 0, HostBatch *B1 = nullptr)
+                           HostBatch *B, int split = 0, HostBatch *B1 = nullptr, bool post = false)
 {
     size_t off = align_up(sizeof(ImgDesc) * (size_t)n, 256);
     const size_t tu_off = off;  // the same descriptors with in = u (re-selection)
@@ -461,7 +503,10 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
         d.nfield = (float4 *)(ws + o_sc);
         d.tensor = (float4 *)(ws + o_ten);
         d.idx = im.d_sigma_idx ? im.d_sigma_idx : (uint8_t *)(ws + o_idx);
-        d.vmax = nullptr;
+        // post-processing: V_max (4 B per pixel) and the second index plane (1 B)
+        // packed into the tensor plane (16 B per pixel)
+        d.vmax = post ? (float *)(ws + o_ten) : nullptr;
+        d.idx2 = (uint8_t *)(ws + o_ten) + 4 * (size_t)im.h * im.pitch;
         d.max_s2 = (unsigned *)(ws + ms_off) + i;
         d.maps = ws + maps_off + tma_maps_bytes() * (size_t)i;
         d.plane = pb / 4;
@@ -575,7 +620,8 @@ static int enqueue_batch_two_streams(const fd4_image *imgs, int n_images, const 
     std::vector<ImgDesc> descs;
     HostBatch B0, B1;
     const int split = balanced_split(imgs, n_images);
-    batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B0, split, &B1);
+    const bool post = p.postprocess_scales && !sigma_given;
+    batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B0, split, &B1, post);
     const bool reselect = p.reselect_each_cycle && !sigma_given;
     if (put_tables(descs, n_images, B0, d_ws, reselect, s0)) return FD4_ERR_CUDA;
     const int steps = p.fed_steps_per_launch > 0 ? p.fed_steps_per_launch : default_steps_per_launch();
@@ -585,19 +631,24 @@ static int enqueue_batch_two_streams(const fd4_image *imgs, int n_images, const 
     int rc = FD4_OK;
     // group 0: selection, copy, first tensor build; then group 1 may start
     if ((!sigma_given && launch_select_batch(B0, h_sigmas, n_sigma, p, s0)) || launch_copy_in_batch(B0, s0) ||
+        (post && launch_postprocess_batch(B0, h_sigmas, n_sigma, p, s0)) ||
         launch_tensor_batch(B0, h_sigmas, n_sigma, p, s0))
         rc = FD4_ERR_CUDA;
     if (rc == FD4_OK && (cudaEventRecord(ev_go, s0) != cudaSuccess || cudaStreamWaitEvent(s1, ev_go, 0) != cudaSuccess))
         rc = FD4_ERR_CUDA;
     if (rc == FD4_OK && ((!sigma_given && launch_select_batch(B1, h_sigmas, n_sigma, p, s1)) ||
-                         launch_copy_in_batch(B1, s1)))
+                         launch_copy_in_batch(B1, s1) || (post && launch_postprocess_batch(B1, h_sigmas, n_sigma, p, s1))))
         rc = FD4_ERR_CUDA;
     for (int k = 0; k < M && rc == FD4_OK; ++k) {
         if (launch_fed_batch(B0, tau, n, p.boundary, steps, s0)) rc = FD4_ERR_CUDA;
         if (rc == FD4_OK && k + 1 < M && reselect && launch_select_batch(current_view(B0), h_sigmas, n_sigma, p, s0))
             rc = FD4_ERR_CUDA;
+        if (rc == FD4_OK && k + 1 < M && reselect && post && launch_postprocess_batch(B0, h_sigmas, n_sigma, p, s0))
+            rc = FD4_ERR_CUDA;
         if (rc == FD4_OK && k + 1 < M && launch_tensor_batch(B0, h_sigmas, n_sigma, p, s0)) rc = FD4_ERR_CUDA;
         if (rc == FD4_OK && k > 0 && reselect && launch_select_batch(current_view(B1), h_sigmas, n_sigma, p, s1))
+            rc = FD4_ERR_CUDA;
+        if (rc == FD4_OK && k > 0 && reselect && post && launch_postprocess_batch(B1, h_sigmas, n_sigma, p, s1))
             rc = FD4_ERR_CUDA;
         if (rc == FD4_OK && launch_tensor_batch(B1, h_sigmas, n_sigma, p, s1)) rc = FD4_ERR_CUDA;
         if (rc == FD4_OK && launch_fed_batch(B1, tau, n, p.boundary, steps, s1)) rc = FD4_ERR_CUDA;
@@ -614,7 +665,8 @@ static int enqueue_batch(const fd4_image *imgs, int n_images, const float *h_sig
 {
     std::vector<ImgDesc> descs;
     HostBatch B;
-    batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B);
+    const bool post = p.postprocess_scales && !sigma_given && (stages & FD4_STAGE_SELECT);
+    batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B, 0, nullptr, post);
     const bool reselect = p.reselect_each_cycle && !sigma_given && (stages & FD4_STAGE_SELECT);
     if (put_tables(descs, n_images, B, d_ws, reselect, st)) return FD4_ERR_CUDA;
     return enqueue_filter(B, h_sigmas, n_sigma, p, tau, n, M, sigma_given, st, stages);

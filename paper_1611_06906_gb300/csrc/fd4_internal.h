@@ -84,7 +84,8 @@ struct ImgDesc {
     float4 *nfield;      // normalised Hessian (Nxx, Nxy, Nyy, 0)
     float4 *tensor;      // (cos 2t, sin 2t, mu1, mu2)
     uint8_t *idx;        // selected scale index
-    float *vmax;         // nullable
+    uint8_t *idx2;       // post-processed scale index before its copy into idx
+    float *vmax;         // nullable (set when the scale image is post-processed)
     unsigned *max_s2;    // max S^2 of the image (float bits)
     size_t plane;
     const void *maps;    // batches: this image's TMA tensor maps (u, FED plane, tensor) in device memory
@@ -257,6 +258,10 @@ int launch_tensor_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, 
 // nfield = N at each pixel's selected scale, one strip-walking launch per scale (fd4_tensor.cu).
 int launch_tensor_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
                          cudaStream_t st);
+// Scale-image post-processing of every image of a batch from idx, vmax and u
+// (fd4_postproc.cu): nfield, idx2 and idx are written.
+int launch_postprocess_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
+                             cudaStream_t st);
 // Selection planes of every scale and each image's max S^2, one strip-walking
 // launch per scale (fd4_tensor.cu); B.max_s2 must be cleared first.
 int launch_select_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,

@@ -20,7 +20,7 @@ from . import build as _build
 
 RIDGE, VALLEY, BOTH = 0, 1, 2
 NATURAL, PERIODIC = 0, 1
-OP_SELECT_SCALES, OP_BUILD_TENSOR, OP_FED_CYCLE, OP_FILTER = 0, 1, 2, 3
+OP_SELECT_SCALES, OP_BUILD_TENSOR, OP_FED_CYCLE, OP_FILTER, OP_POSTPROCESS = 0, 1, 2, 3, 4
 STAGE_SELECT, STAGE_COPY, STAGE_TENSOR, STAGE_FED, STAGES_ALL = 1, 2, 4, 8, 15
 GRAPH_TWO_STREAMS = 16
 MAX_FED_STEPS = 4096
@@ -41,7 +41,8 @@ class Params(ctypes.Structure):
                 ("c", ctypes.c_float), ("gamma", ctypes.c_float), ("tau_max", ctypes.c_float),
                 ("mode", ctypes.c_int), ("boundary", ctypes.c_int), ("kappa", ctypes.c_int),
                 ("grad_norm_squared", ctypes.c_int), ("fed_steps_per_launch", ctypes.c_int),
-                ("reselect_each_cycle", ctypes.c_int)]
+                ("reselect_each_cycle", ctypes.c_int), ("postprocess_scales", ctypes.c_int),
+                ("theta", ctypes.c_float)]
 
 
 class Image(ctypes.Structure):
@@ -66,6 +67,7 @@ SIGNATURES = {
     "fd4_workspace_bytes": (_sz, [_i, _i, _i, _i]),
     "fd4_select_scales": (_i, [_vp, _i, _i, _i, _fp, _i, _pp, _vp, _vp, _vp, _sz, _vp]),
     "fd4_build_tensor": (_i, [_vp, _i, _i, _i, _vp, _fp, _i, _pp, _vp, _vp, _sz, _vp]),
+    "fd4_postprocess_scales": (_i, [_vp, _i, _i, _i, _vp, _vp, _fp, _i, _pp, _vp, _sz, _vp]),
     "fd4_fed_cycle": (_i, [_vp, _i, _i, _i, _vp, _dp, _i, _i, _vp, _sz, _vp]),
     "fd4_filter": (_i, [_vp, _vp, _i, _i, _i, _fp, _i, _pp, ctypes.c_double, _i, _i, _vp, _i, _vp,
                         _sz, _vp]),
@@ -217,6 +219,19 @@ def select_scales(img, w: int, sigmas, prm: Params | None = None, want_vmax: boo
                                    ctypes.byref(prm) if prm is not None else None, _ptr(idx), _ptr(vmax),
                                    _ptr(ws), ws.numel(), _stream(stream)), "fd4_select_scales")
     return idx, vmax
+
+
+def postprocess_scales(u, w: int, sigma_idx, vmax, sigmas, prm: Params | None = None, ws=None, stream=None):
+    """fd4_postprocess_scales, in place on sigma_idx (uint8 (h, pitch)); vmax is
+    the selection's V_max (float32 (h, pitch)).  Returns sigma_idx."""
+    h, pitch = u.shape
+    sg, K = _sigmas(sigmas)
+    if ws is None:
+        ws = workspace(OP_POSTPROCESS, pitch, h, K, u.device)
+    _check(lib().fd4_postprocess_scales(_ptr(u), int(w), h, pitch, _ptr(sigma_idx), _ptr(vmax), sg, K,
+                                        ctypes.byref(prm) if prm is not None else None, _ptr(ws), ws.numel(),
+                                        _stream(stream)), "fd4_postprocess_scales")
+    return sigma_idx
 
 
 def build_tensor(u, w: int, sigma_idx, sigmas, prm: Params | None = None, out=None, ws=None, stream=None):
