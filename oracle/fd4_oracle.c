@@ -27,6 +27,9 @@
  *                         the diagonal (row, column and diagonal means), the
  *                         walk cap, empty mask, isotropic Hessians, a straight
  *                         ridge (one scale per cross-section)
+ *   or_*_ifod             pinned: g = 1 on constants, g in closed form on
+ *                         quadratics, g -> 1 as lambda grows (the cycle then
+ *                         equals the biharmonic one), mean conservation
  *   or_filter             whole-filter output: parity unpinned beyond the
  *                         invariants above (the paper prints no numeric
  *                         intermediate for it); its cycle schedule (one
@@ -739,6 +742,47 @@ void or_fed_cycle(double *u, int w, int h, const double *tensor,
 /* The whole filter: sigma* once on the input (unless given), then M cycles of
  * (tensor from the current u at sigma*, one FED cycle).  u is filtered in
  * place.  sigma_idx_io: if sigma_given, read; else written.                 */
+/* ------------------------------------------------------------------------ */
+/* The isotropic fourth-order comparator (IFOD, Eq. 2, the nonlinear
+ * fourth-order diffusion of Lysaker et al. in the form of Didas et al.): the
+ * diffusivity is the scalar g(||H(u)||_F^2) on every second derivative, i.e.
+ * D = g I, which in this parameterisation is the tensor (1, 0, g, g) (both
+ * eigenvalues g; the orientation is immaterial).  Readings: H is the Hessian
+ * of u_sigma at the one regularisation scale sigma (1.0 in the paper's
+ * experiments), ||H||_F^2 = u_xx^2 + 2 u_xy^2 + u_yy^2, and g has the
+ * Perona-Malik form of Eq. 7, g(s) = 1 / (1 + s / lambda^2); no integration
+ * scale and no gradient normalisation; g is rebuilt from u^k every cycle.    */
+void or_build_tensor_ifod(const double *u, int w, int h, double sigma, double lambda,
+                          double *tensor)
+{
+    size_t np = (size_t)w * h;
+    double *a = malloc(sizeof(double) * np);
+    double *b = malloc(sizeof(double) * np);
+    double *d = malloc(sizeof(double) * np);
+    or_derivatives(u, w, h, sigma, NULL, NULL, a, b, d);
+    for (size_t p = 0; p < np; ++p) {
+        double f2 = a[p] * a[p] + 2.0 * b[p] * b[p] + d[p] * d[p];
+        double g = 1.0 / (1.0 + f2 / (lambda * lambda));
+        tensor[p] = 1.0;
+        tensor[np + p] = 0.0;
+        tensor[2 * np + p] = g;
+        tensor[3 * np + p] = g;
+    }
+    free(a); free(b); free(d);
+}
+
+void or_filter_ifod(double *u, int w, int h, double sigma, double lambda, int boundary,
+                    const double *tau, int n, int M)
+{
+    size_t np = (size_t)w * h;
+    double *tensor = malloc(sizeof(double) * 4 * np);
+    for (int k = 0; k < M; ++k) {
+        or_build_tensor_ifod(u, w, h, sigma, lambda, tensor);
+        or_fed_cycle(u, w, h, tensor, tau, n, boundary);
+    }
+    free(tensor);
+}
+
 /* The whole filter: M cycles of (tensor build at the selected scales, FED
  * cycle).  The scale image is selected once on the input (the default
  * reading), or, with reselect, again on the current image u^k before every

@@ -79,6 +79,10 @@ def _load():
                                   ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _u8p,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        lib.or_build_tensor_ifod.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_double, _dp]
+        lib.or_filter_ifod.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int]
         lib.or_strong_direction.argtypes = [ctypes.c_double] * 3 + [_dp, _dp]
         lib.or_strong_direction.restype = ctypes.c_int
         lib.or_postprocess_core.argtypes = [_u8p, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp,
@@ -210,6 +214,24 @@ def fed_cycle(u, tensor, tau, boundary=NATURAL):
     t = _f64(tensor)
     tau = _f64(tau)
     _load().or_fed_cycle(_d(u), w, h, _d(t), _d(tau), tau.size, int(boundary))
+    return u
+
+
+def build_tensor_ifod(u, sigma=1.0, lam=0.005):
+    """IFOD tensor field (1, 0, g, g) as (4, h, w), g = 1 / (1 + ||H(u_sigma)||_F^2 / lambda^2) (Eq. 2)."""
+    u = _f64(u)
+    h, w = u.shape
+    t = np.zeros((4, h, w))
+    _load().or_build_tensor_ifod(_d(u), w, h, float(sigma), float(lam), _d(t))
+    return t
+
+
+def filter_ifod(u, tau, M, sigma=1.0, lam=0.005, boundary=NATURAL):
+    """The IFOD filter: M cycles of (IFOD tensor from u^k, FED cycle).  Returns a new array."""
+    u = _f64(u).copy()
+    h, w = u.shape
+    tau = _f64(tau)
+    _load().or_filter_ifod(_d(u), w, h, float(sigma), float(lam), int(boundary), _d(tau), tau.size, int(M))
     return u
 
 
