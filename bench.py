@@ -276,6 +276,21 @@ def run_fd4(args, rank, world, local_rank):
                 "_out": {i: (ims[i].out[:, :ims[i].w].cpu().numpy().astype(np.float64),
                              ims[i].idx[:, :ims[i].w].cpu().numpy()) for i in order}}
         g_po.close()
+
+    # the IFOD comparator of Eq. 2 (sigma 1, the paper's setting) on the same batch
+    ifod = None
+    if not args.no_ifod:
+        g_if = fd4.Graph(lst, sig, T, M, n, fd4.params(mode=mode, fed_steps_per_launch=best,
+                                                          model=fd4.MODEL_IFOD, ifod_sigma=1.0), ws=ws)
+        g_if.launch()
+        barrier()
+        if_ms = max_over_ranks(_timed(g_if.launch, args.steps, stream, torch)) / args.steps
+        order = sorted(range(len(ims)), key=lambda i: ims[i].npx)[:2]
+        ifod = {"value": world * px_steps / (if_ms * 1e-3) / 1e6, "ms_per_step": if_ms, "sigma": 1.0,
+                "gpu_launches_per_step": g_if.kernel_count(),
+                "path": "batched graph, IFOD tensor (1, 0, g, g) rebuilt every cycle, same FED cycles",
+                "_out": {i: ims[i].out[:, :ims[i].w].cpu().numpy().astype(np.float64) for i in order}}
+        g_if.close()
     g_all.launch()  # leave the outputs of a complete filter pass in place
     barrier()
 
@@ -400,6 +415,16 @@ def run_fd4(args, rank, world, local_rank):
             post["parity"] = {"vs": "FP64 oracle, post-processed scale image", "images": sample,
                               "max_abs": max(p_err), "max_abs_oracle_sigma": max(p_inj),
                               "sigma_agreement": min(p_agree), "tolerance": 1e-4}
+        if ifod is not None:
+            from oracle import oracle as O
+            tau_o, _, _ = O.fed_taus(T, M, 0.05, n=n)
+            errs_if = [float(np.abs(got - O.filter_ifod(imgs[i], tau_o, M, sigma=1.0, lam=0.005)).max())
+                       for i, got in ifod["_out"].items()]
+            ifod["parity"] = {"vs": "FP64 oracle IFOD filter", "images": sample, "max_abs": max(errs_if),
+                              "tolerance": 1e-4}
+    if ifod is not None:
+        ifod.pop("_out", None)
+        out["ifod"] = ifod
     if resel is not None:
         resel.pop("_out", None)
         out["reselect"] = resel
@@ -525,6 +550,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the batched+learned variant")
     ap.add_argument("--no-reselect", action="store_true", help="skip the per-cycle re-selection variant")
     ap.add_argument("--no-postprocess", action="store_true", help="skip the scale post-processing variant")
+    ap.add_argument("--no-ifod", action="store_true", help="skip the IFOD comparator")
     ap.add_argument("--two-streams", type=int, default=0, help="headline graph on two streams (1) or one (0)")
     ap.add_argument("--sel-crops", type=int, default=4096, help="training crops of the learned selector")
     ap.add_argument("--sel-threshold", type=float, default=0.5, help="fallback confidence threshold")

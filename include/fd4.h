@@ -99,7 +99,19 @@ typedef struct fd4_params {
     float theta;             /* vesselness threshold of the post-processing's
                                 vessel mask, in [0, 1] (default 0.2, the paper's
                                 synthetic setting; 0.13 for its fundus images)   */
+    int model;               /* whole filters: fd4_model (default FD4_MODEL_MAFOD) */
+    float ifod_sigma;        /* FD4_MODEL_IFOD: the regularisation scale of
+                                H(u_sigma) (default 1.0, the paper's setting;
+                                at most FD4_MAX_SIGMA)                           */
 } fd4_params;
+
+/* The filter a whole-filter call runs.  MAFOD: the paper's method (scale
+ * selection, tensor D from N at the selected scales).  IFOD: its isotropic
+ * fourth-order comparator (Eq. 2): D = g(|H(u_sigma)|_F^2) I with the
+ * Perona-Malik g of Eq. 7 at the one scale ifod_sigma, rebuilt from u^k every
+ * cycle, the same FED cycles; the scale set and scale image are not used (a
+ * valid scale set is still required by the argument checks).               */
+typedef enum fd4_model { FD4_MODEL_MAFOD = 0, FD4_MODEL_IFOD = 1 } fd4_model;
 
 /* Fills *p with the defaults listed above. */
 void fd4_default_params(fd4_params *p);
@@ -176,6 +188,13 @@ int fd4_select_scales(const float *d_img, int w, int h, int pitch,
 int fd4_postprocess_scales(const float *d_u, int w, int h, int pitch, uint8_t *d_sigma_idx,
                            const float *d_vmax, const float *h_sigmas, int n_sigma,
                            const fd4_params *params, void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+
+/* IFOD tensor field (Eq. 2): D = g I as (1, 0, g, g) per pixel with
+ * g = 1 / (1 + |H(u_s)|_F^2 / lambda^2), |H|_F^2 = u_xx^2 + 2 u_xy^2 + u_yy^2
+ * at s = params->ifod_sigma (Gaussian derivatives as in fd4_select_scales).
+ * d_tensor: 4 floats per pixel, row pitch `pitch` pixels.  No workspace.    */
+int fd4_build_tensor_ifod(const float *d_u, int w, int h, int pitch, const fd4_params *params,
+                          float *d_tensor, fd4_stream_t stream);
 
 /* Fourth-order diffusion tensor field (Sec. 3.1 Eq. 6, Sec. 3.2 Eq. 7-8).
  * N = H(u_s) / sqrt(1 + |grad u_s|) at s = h_sigmas[d_sigma_idx[p]] per pixel

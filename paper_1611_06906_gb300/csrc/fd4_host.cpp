@@ -26,6 +26,8 @@ extern "C" void fd4_default_params(fd4_params *p)
     p->reselect_each_cycle = 0;
     p->postprocess_scales = 0;
     p->theta = 0.2f;
+    p->model = FD4_MODEL_MAFOD;
+    p->ifod_sigma = 1.0f;
     p->fed_steps_per_launch = 0;
 }
 
@@ -235,6 +237,8 @@ static int check_params(const fd4_params &p)
     if (p.reselect_each_cycle != 0 && p.reselect_each_cycle != 1) return FD4_ERR_BAD_ARG;
     if (p.postprocess_scales != 0 && p.postprocess_scales != 1) return FD4_ERR_BAD_ARG;
     if (!(p.theta >= 0.0f && p.theta <= 1.0f)) return FD4_ERR_BAD_ARG;
+    if (p.model != FD4_MODEL_MAFOD && p.model != FD4_MODEL_IFOD) return FD4_ERR_BAD_ARG;
+    if (!(p.ifod_sigma > 0.0f && p.ifod_sigma <= FD4_MAX_SIGMA)) return FD4_ERR_BAD_ARG;
     return FD4_OK;
 }
 
@@ -331,6 +335,25 @@ extern "C" int fd4_postprocess_scales(const float *d_u, int w, int h, int pitch,
     return cuda_status(launch_postprocess_batch(single_batch(d), h_sigmas, n_sigma, p, (cudaStream_t)stream));
 }
 
+extern "C" int fd4_build_tensor_ifod(const float *d_u, int w, int h, int pitch, const fd4_params *params,
+                                     float *d_tensor, fd4_stream_t stream)
+{
+    int rc;
+    fd4_params p;
+    resolve_params(params, &p);
+    if ((rc = check_image(d_u, w, h, pitch)) != FD4_OK) return rc;
+    if ((rc = check_params(p)) != FD4_OK) return rc;
+    if (!d_tensor) return FD4_ERR_BAD_ARG;
+    if ((uintptr_t)d_tensor & 15u) return FD4_ERR_ALIGN;
+    ImgDesc d{};
+    d.u = const_cast<float *>(d_u);  // read only
+    d.tensor = (float4 *)d_tensor;
+    d.w = w;
+    d.h = h;
+    d.pitch = pitch;
+    return cuda_status(launch_ifod_tensor(single_batch(d), p.ifod_sigma, p, (cudaStream_t)stream));
+}
+
 extern "C" int fd4_build_tensor(const float *d_u, int w, int h, int pitch, const uint8_t *d_sigma_idx,
                                 const float *h_sigmas, int n_sigma, const fd4_params *params,
                                 float *d_tensor, void *d_ws, size_t ws_bytes, fd4_stream_t stream)
@@ -366,6 +389,14 @@ extern "C" int fd4_fed_cycle(float *d_u, int w, int h, int pitch, const float *d
 
 // The filter schedule on a batch: selection (unless given), input copy, then M
 // cycles of tensor build and FED cycle.  Everything is enqueued on `st`.
+// The tensor field of one cycle: MAFOD's at the selected scales, or IFOD's.
+static int launch_cycle_tensor(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
+                               cudaStream_t st)
+{
+    if (p.model == FD4_MODEL_IFOD) return launch_ifod_tensor(B, p.ifod_sigma, p, st);
+    return launch_tensor_batch(B, h_sigmas, n_sigma, p, st);
+}
+
 // The batch as the selection sees it when it re-selects on the current image:
 // every descriptor's input is the image being filtered (u).  Single images
 // carry the descriptor inline; batches have a second device table for it.
@@ -382,20 +413,21 @@ static int enqueue_filter(const HostBatch &B, const float *h_sigmas, int n_sigma
                           int stages = FD4_STAGES_ALL)
 {
     const int steps = p.fed_steps_per_launch > 0 ? p.fed_steps_per_launch : default_steps_per_launch();
-    if ((stages & FD4_STAGE_SELECT) && !sigma_given && launch_select_batch(B, h_sigmas, n_sigma, p, st))
+    const bool mafod = p.model == FD4_MODEL_MAFOD;  // IFOD selects no scales
+    if (mafod && (stages & FD4_STAGE_SELECT) && !sigma_given && launch_select_batch(B, h_sigmas, n_sigma, p, st))
         return FD4_ERR_CUDA;
     if ((stages & FD4_STAGE_COPY) && launch_copy_in_batch(B, st)) return FD4_ERR_CUDA;
     // the post-processing reads u (the strips' N at the selected scales), so the
     // first one follows the copy of the input into u
-    const bool post = p.postprocess_scales && !sigma_given && (stages & FD4_STAGE_SELECT);
+    const bool post = mafod && p.postprocess_scales && !sigma_given && (stages & FD4_STAGE_SELECT);
     if (post && launch_postprocess_batch(B, h_sigmas, n_sigma, p, st)) return FD4_ERR_CUDA;
-    const bool reselect = p.reselect_each_cycle && !sigma_given && (stages & FD4_STAGE_SELECT);
+    const bool reselect = mafod && p.reselect_each_cycle && !sigma_given && (stages & FD4_STAGE_SELECT);
     for (int k = 0; k < M; ++k) {
         if (k > 0 && reselect && launch_select_batch(current_view(B), h_sigmas, n_sigma, p, st))
             return FD4_ERR_CUDA;
         if (k > 0 && reselect && post && launch_postprocess_batch(B, h_sigmas, n_sigma, p, st))
             return FD4_ERR_CUDA;
-        if ((stages & FD4_STAGE_TENSOR) && launch_tensor_batch(B, h_sigmas, n_sigma, p, st)) return FD4_ERR_CUDA;
+        if ((stages & FD4_STAGE_TENSOR) && launch_cycle_tensor(B, h_sigmas, n_sigma, p, st)) return FD4_ERR_CUDA;
         if ((stages & FD4_STAGE_FED) && launch_fed_batch(B, tau, n, p.boundary, steps, st)) return FD4_ERR_CUDA;
     }
     return FD4_OK;
@@ -444,7 +476,7 @@ extern "C" int fd4_filter(const float *d_in, float *d_out, int w, int h, int pit
     // post-processing: V_max (4 B per pixel) and the second index plane (1 B)
     // packed into the tensor plane (16 B per pixel), which no stage uses
     // between a selection and the cycle's tensor build
-    d.vmax = (p.postprocess_scales && !sigma_given) ? (float *)d.tensor : nullptr;
+    d.vmax = (p.model == FD4_MODEL_MAFOD && p.postprocess_scales && !sigma_given) ? (float *)d.tensor : nullptr;
     d.idx2 = (uint8_t *)d.tensor + 4 * (size_t)h * pitch;
     d.max_s2 = &((WsHeader *)sws)->max_s2;
     d.plane = pb / 4;
@@ -620,9 +652,11 @@ static int enqueue_batch_two_streams(const fd4_image *imgs, int n_images, const 
     std::vector<ImgDesc> descs;
     HostBatch B0, B1;
     const int split = balanced_split(imgs, n_images);
-    const bool post = p.postprocess_scales && !sigma_given;
+    const bool mafod = p.model == FD4_MODEL_MAFOD;
+    const bool sel = mafod && !sigma_given;
+    const bool post = sel && p.postprocess_scales;
     batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B0, split, &B1, post);
-    const bool reselect = p.reselect_each_cycle && !sigma_given;
+    const bool reselect = sel && p.reselect_each_cycle;
     if (put_tables(descs, n_images, B0, d_ws, reselect, s0)) return FD4_ERR_CUDA;
     const int steps = p.fed_steps_per_launch > 0 ? p.fed_steps_per_launch : default_steps_per_launch();
     if (cudaEventRecord(ev_fork, s0) != cudaSuccess || cudaStreamWaitEvent(s1, ev_fork, 0) != cudaSuccess)
@@ -630,13 +664,13 @@ static int enqueue_batch_two_streams(const fd4_image *imgs, int n_images, const 
     set_grid_divisor(2);
     int rc = FD4_OK;
     // group 0: selection, copy, first tensor build; then group 1 may start
-    if ((!sigma_given && launch_select_batch(B0, h_sigmas, n_sigma, p, s0)) || launch_copy_in_batch(B0, s0) ||
+    if ((sel && launch_select_batch(B0, h_sigmas, n_sigma, p, s0)) || launch_copy_in_batch(B0, s0) ||
         (post && launch_postprocess_batch(B0, h_sigmas, n_sigma, p, s0)) ||
-        launch_tensor_batch(B0, h_sigmas, n_sigma, p, s0))
+        launch_cycle_tensor(B0, h_sigmas, n_sigma, p, s0))
         rc = FD4_ERR_CUDA;
     if (rc == FD4_OK && (cudaEventRecord(ev_go, s0) != cudaSuccess || cudaStreamWaitEvent(s1, ev_go, 0) != cudaSuccess))
         rc = FD4_ERR_CUDA;
-    if (rc == FD4_OK && ((!sigma_given && launch_select_batch(B1, h_sigmas, n_sigma, p, s1)) ||
+    if (rc == FD4_OK && ((sel && launch_select_batch(B1, h_sigmas, n_sigma, p, s1)) ||
                          launch_copy_in_batch(B1, s1) || (post && launch_postprocess_batch(B1, h_sigmas, n_sigma, p, s1))))
         rc = FD4_ERR_CUDA;
     for (int k = 0; k < M && rc == FD4_OK; ++k) {
@@ -645,12 +679,12 @@ static int enqueue_batch_two_streams(const fd4_image *imgs, int n_images, const 
             rc = FD4_ERR_CUDA;
         if (rc == FD4_OK && k + 1 < M && reselect && post && launch_postprocess_batch(B0, h_sigmas, n_sigma, p, s0))
             rc = FD4_ERR_CUDA;
-        if (rc == FD4_OK && k + 1 < M && launch_tensor_batch(B0, h_sigmas, n_sigma, p, s0)) rc = FD4_ERR_CUDA;
+        if (rc == FD4_OK && k + 1 < M && launch_cycle_tensor(B0, h_sigmas, n_sigma, p, s0)) rc = FD4_ERR_CUDA;
         if (rc == FD4_OK && k > 0 && reselect && launch_select_batch(current_view(B1), h_sigmas, n_sigma, p, s1))
             rc = FD4_ERR_CUDA;
         if (rc == FD4_OK && k > 0 && reselect && post && launch_postprocess_batch(B1, h_sigmas, n_sigma, p, s1))
             rc = FD4_ERR_CUDA;
-        if (rc == FD4_OK && launch_tensor_batch(B1, h_sigmas, n_sigma, p, s1)) rc = FD4_ERR_CUDA;
+        if (rc == FD4_OK && launch_cycle_tensor(B1, h_sigmas, n_sigma, p, s1)) rc = FD4_ERR_CUDA;
         if (rc == FD4_OK && launch_fed_batch(B1, tau, n, p.boundary, steps, s1)) rc = FD4_ERR_CUDA;
     }
     set_grid_divisor(1);
@@ -665,9 +699,10 @@ static int enqueue_batch(const fd4_image *imgs, int n_images, const float *h_sig
 {
     std::vector<ImgDesc> descs;
     HostBatch B;
-    const bool post = p.postprocess_scales && !sigma_given && (stages & FD4_STAGE_SELECT);
+    const bool sel = p.model == FD4_MODEL_MAFOD && !sigma_given && (stages & FD4_STAGE_SELECT);
+    const bool post = sel && p.postprocess_scales;
     batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B, 0, nullptr, post);
-    const bool reselect = p.reselect_each_cycle && !sigma_given && (stages & FD4_STAGE_SELECT);
+    const bool reselect = sel && p.reselect_each_cycle;
     if (put_tables(descs, n_images, B, d_ws, reselect, st)) return FD4_ERR_CUDA;
     return enqueue_filter(B, h_sigmas, n_sigma, p, tau, n, M, sigma_given, st, stages);
 }
@@ -801,8 +836,8 @@ extern "C" int fd4_autotune_batched(const fd4_image *h_imgs, int n_images, const
     batch_layout(h_imgs, n_images, n_sigma, &descs, (char *)d_ws, &B);
     if (launch_put_descs(descs.data(), n_images, (ImgDesc *)d_ws, st)) return FD4_ERR_CUDA;
     if (n_images > 0 && launch_put_maps(descs.data(), n_images, (void *)descs[0].maps, st)) return FD4_ERR_CUDA;
-    if (launch_select_batch(B, h_sigmas, n_sigma, p, st) || launch_copy_in_batch(B, st) ||
-        launch_tensor_batch(B, h_sigmas, n_sigma, p, st))
+    if ((p.model == FD4_MODEL_MAFOD && launch_select_batch(B, h_sigmas, n_sigma, p, st)) ||
+        launch_copy_in_batch(B, st) || launch_cycle_tensor(B, h_sigmas, n_sigma, p, st))
         return FD4_ERR_CUDA;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return FD4_ERR_CUDA;

@@ -15,6 +15,11 @@
 // loop is unrolled and the weights are kernel parameters (constant-bank
 // operands of the FMAs).  The arithmetic and summation order are those of the
 // multi-scale sweep in fd4_scale.cu, so both give identical results.
+//
+// The same kernels run the selection (a dense column pass and the vesselness
+// factors of every pixel at each scale) and the IFOD comparator of Eq. 2 (a
+// dense column pass at one scale and the tensor (1, 0, g, g) with
+// g = 1 / (1 + |H(u_sigma)|_F^2 / lambda^2)).
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -208,6 +213,14 @@ struct StripArgs {
     float inv2b2;   // selection: 1 / (2 beta^2)
     int shape;      // SHAPE_SEG or SHAPE_SEG_S
     int seg;        // its rows
+    float inv_lam2; // IFOD: 1 / lambda^2
+};
+
+// What a strip launch computes (the kernels' MODE).
+enum StripMode {
+    ST_TENSOR = 0,  // N at the pixels whose selected scale this is (sparse column pass)
+    ST_SELECT = 1,  // vesselness planes of this scale at every pixel (dense column pass)
+    ST_IFOD = 2     // IFOD tensor (1, 0, g, g), g = 1 / (1 + |H|_F^2 / lambda^2), at every pixel
 };
 
 // Geometry of one strip segment, computed once by the thread that looks the
@@ -229,15 +242,16 @@ __device__ __forceinline__ void seg_geo(const ImgDesc &d, int local, int seg, Se
 }
 
 // Scale s (radius R) over every strip segment of the batch.
-// Tensor build (SEL false): idx holds each pixel's selected scale; only pixels
+// Tensor build (ST_TENSOR): idx holds each pixel's selected scale; only pixels
 // with idx == s are written (nfield), and the s == 0 launch also zeroes N where
-// idx lies outside the scale set.  Selection (SEL true): every pixel's Hessian
+// idx lies outside the scale set.  Selection (ST_SELECT): every pixel's Hessian
 // at scale s gives the vesselness factor and S^2 of plane s (vp, s2) and the
 // image's max S^2.  The next piece's rows (of this segment or of the block's
 // next one) are copied with cp.async while the current piece is computed.
-template <int R, bool SEL, bool F2>
+template <int R, int MODE, bool F2>
 __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripArgs sa)
 {
+    constexpr bool SEL = MODE == ST_SELECT, DENSE = MODE != ST_TENSOR;
     constexpr int NB = ST_CH + 2 * R, SW = st_sw<R>(), NP0 = Piece<R>::NP0;
     extern __shared__ __align__(16) float stsm[];
     float *trow = stsm + 2 * ST_CH * SW;  // 3 fields x NB rows x ST_RS; staged rows: two ST_CH x SW buffers
@@ -282,7 +296,7 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
         // the selected scales of the chunk this piece completes (rows 4 warp .. + 3)
         const int y0 = ys + ST_CH * pc.chunk;
         int ids[4] = {-1, -1, -1, -1};
-        if (!SEL && pc.last && x0 + lane < w) {
+        if (!DENSE && pc.last && x0 + lane < w) {
             const uint8_t *ip = sd[cur].idx + (size_t)(y0 + warp * 4) * pitch + x0 + lane;
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -319,7 +333,7 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
         else st_rows<R>(tp, stsm + buf * ST_CH * SW, trow, pc.b0, pc.n);
         __syncthreads();
 
-        if (SEL && pc.last) {
+        if (DENSE && pc.last) {
             // dense column pass: column lane, rows 4 warp .. + 3 of the chunk
             // read buffer rows 4 warp .. 4 warp + 3 + 2R
             const float *c0 = trow + (warp * 4) * ST_RS + lane;
@@ -372,6 +386,12 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
                 const int gy = y0 + warp * 4 + j;
                 if (gx >= w || gy >= h) continue;
                 const float a = uxx[j], b = uxy[j], d = uyy[j];
+                if (!SEL) {  // IFOD: D = g I
+                    const float f2 = fmaf(a, a, fmaf(2.0f * b, b, d * d));
+                    const float g = 1.0f / fmaf(f2, sa.inv_lam2, 1.0f);
+                    sd[cur].tensor[(size_t)gy * pitch + gx] = make_float4(1.0f, 0.0f, g, g);
+                    continue;
+                }
                 // eigenvalues of H (sigma^(2 gamma) cancels in R_B and the sign
                 // test; S^2 picks it up as sigma^(4 gamma))
                 const float m = 0.5f * (a + d);
@@ -390,14 +410,14 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
                 sd[cur].s2[(size_t)s * sd[cur].plane + p] = s2;
                 bmax = fmaxf(bmax, s2);
             }
-            if (i + 1 == P) {  // segment done: fold its max S^2 into the image's
+            if (SEL && i + 1 == P) {  // segment done: fold its max S^2 into the image's
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
                 if (lane == 0 && bmax > 0.0f) atomicMax(sd[cur].max_s2, __float_as_uint(bmax));
                 bmax = 0.0f;
             }
         }
-        if (!SEL && pc.last) {
+        if (!DENSE && pc.last) {
             // the chunk's pixels of this scale, grouped in plist
             unsigned m[4];
             int cnt = 0;
@@ -478,7 +498,7 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
     st_wait0();
 }
 
-template <int R, bool SEL, bool F2>
+template <int R, int MODE, bool F2>
 int launch_strip_k(const Imgs &I, const StripTaps<R> &tp, const StripArgs &a, cudaStream_t st)
 {
     static int attr_dev = -1;
@@ -486,13 +506,13 @@ int launch_strip_k(const Imgs &I, const StripTaps<R> &tp, const StripArgs &a, cu
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
     constexpr size_t smem = st_smem_bytes<R>();
     if (attr_dev != dev) {
-        if (cudaFuncSetAttribute(k_strip<R, SEL, F2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        if (cudaFuncSetAttribute(k_strip<R, MODE, F2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return 1;
         attr_dev = dev;
     }
-    const int grid = persistent_grid((const void *)k_strip<R, SEL, F2>, ST_NT, smem, I.tiles);
-    k_strip<R, SEL, F2><<<grid, ST_NT, smem, st>>>(I, tp, a);
+    const int grid = persistent_grid((const void *)k_strip<R, MODE, F2>, ST_NT, smem, I.tiles);
+    k_strip<R, MODE, F2><<<grid, ST_NT, smem, st>>>(I, tp, a);
     return cudaGetLastError() != cudaSuccess;
 }
 
@@ -504,7 +524,7 @@ inline bool strip_fma2()
     return !(e && e[0] == '0');
 }
 
-template <int R, bool SEL>
+template <int R, int MODE>
 int launch_strip_scale(const HostBatch &B, const GaussTaps &g, const StripArgs &sa, cudaStream_t st)
 {
     constexpr size_t smem = st_smem_bytes<R>();
@@ -528,7 +548,7 @@ int launch_strip_scale(const HostBatch &B, const GaussTaps &g, const StripArgs &
     // rounds of the persistent grid times the rows a block passes per segment
     // (its rows, the 2R halo rows and one chunk for the segment's start, whose
     // staging is not overlapped); FD4_STRIP_ROWS=512 or 128 forces one.
-    const int cap = persistent_grid((const void *)k_strip<R, SEL, true>, ST_NT, smem, 1 << 30);
+    const int cap = persistent_grid((const void *)k_strip<R, MODE, true>, ST_NT, smem, 1 << 30);
     const long long rounds_l = (B.tiles[SHAPE_SEG] + cap - 1) / cap;
     const long long rounds_s = (B.tiles[SHAPE_SEG_S] + cap - 1) / cap;
     bool lng = rounds_l * (kSegRows + 2 * R + ST_CH) <= rounds_s * (kSegRowsShort + 2 * R + ST_CH);
@@ -540,10 +560,10 @@ int launch_strip_scale(const HostBatch &B, const GaussTaps &g, const StripArgs &
     a.seg = lng ? kSegRows : kSegRowsShort;
     Imgs I = B.I;
     I.tiles = B.tiles[a.shape];
-    return strip_fma2() ? launch_strip_k<R, SEL, true>(I, tp, a, st) : launch_strip_k<R, SEL, false>(I, tp, a, st);
+    return strip_fma2() ? launch_strip_k<R, MODE, true>(I, tp, a, st) : launch_strip_k<R, MODE, false>(I, tp, a, st);
 }
 
-template <bool SEL>
+template <int MODE>
 int launch_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p, cudaStream_t st)
 {
     if (B.I.list) return 1;  // the strips walk whole images, never a tile subset
@@ -558,20 +578,21 @@ int launch_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const 
         sa.mode = p.mode;
         sa.scale4 = (float)pow((double)h_sigmas[s], 4.0 * p.gamma);
         sa.inv2b2 = (float)(1.0 / (2.0 * (double)p.beta * p.beta));
+        sa.inv_lam2 = (float)(1.0 / ((double)p.lambda * p.lambda));
         int rc = 1;
         switch (R) {
-        case 4: rc = launch_strip_scale<4, SEL>(B, g, sa, st); break;
-        case 8: rc = launch_strip_scale<8, SEL>(B, g, sa, st); break;
-        case 12: rc = launch_strip_scale<12, SEL>(B, g, sa, st); break;
-        case 16: rc = launch_strip_scale<16, SEL>(B, g, sa, st); break;
-        case 20: rc = launch_strip_scale<20, SEL>(B, g, sa, st); break;
-        case 24: rc = launch_strip_scale<24, SEL>(B, g, sa, st); break;
-        case 28: rc = launch_strip_scale<28, SEL>(B, g, sa, st); break;
-        case 32: rc = launch_strip_scale<32, SEL>(B, g, sa, st); break;
-        case 36: rc = launch_strip_scale<36, SEL>(B, g, sa, st); break;
-        case 40: rc = launch_strip_scale<40, SEL>(B, g, sa, st); break;
-        case 44: rc = launch_strip_scale<44, SEL>(B, g, sa, st); break;
-        case 48: rc = launch_strip_scale<48, SEL>(B, g, sa, st); break;
+        case 4: rc = launch_strip_scale<4, MODE>(B, g, sa, st); break;
+        case 8: rc = launch_strip_scale<8, MODE>(B, g, sa, st); break;
+        case 12: rc = launch_strip_scale<12, MODE>(B, g, sa, st); break;
+        case 16: rc = launch_strip_scale<16, MODE>(B, g, sa, st); break;
+        case 20: rc = launch_strip_scale<20, MODE>(B, g, sa, st); break;
+        case 24: rc = launch_strip_scale<24, MODE>(B, g, sa, st); break;
+        case 28: rc = launch_strip_scale<28, MODE>(B, g, sa, st); break;
+        case 32: rc = launch_strip_scale<32, MODE>(B, g, sa, st); break;
+        case 36: rc = launch_strip_scale<36, MODE>(B, g, sa, st); break;
+        case 40: rc = launch_strip_scale<40, MODE>(B, g, sa, st); break;
+        case 44: rc = launch_strip_scale<44, MODE>(B, g, sa, st); break;
+        case 48: rc = launch_strip_scale<48, MODE>(B, g, sa, st); break;
         default: rc = 1;
         }
         if (rc) return 1;
@@ -583,10 +604,13 @@ template <int R>
 int set_strip_smem()
 {
     const int b = (int)st_smem_bytes<R>();
-    return cudaFuncSetAttribute(k_strip<R, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) != cudaSuccess ||
-           cudaFuncSetAttribute(k_strip<R, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) != cudaSuccess ||
-           cudaFuncSetAttribute(k_strip<R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) != cudaSuccess ||
-           cudaFuncSetAttribute(k_strip<R, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) != cudaSuccess;
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    return cudaFuncSetAttribute(k_strip<R, ST_TENSOR, false>, a, b) != cudaSuccess ||
+           cudaFuncSetAttribute(k_strip<R, ST_SELECT, false>, a, b) != cudaSuccess ||
+           cudaFuncSetAttribute(k_strip<R, ST_IFOD, false>, a, b) != cudaSuccess ||
+           cudaFuncSetAttribute(k_strip<R, ST_TENSOR, true>, a, b) != cudaSuccess ||
+           cudaFuncSetAttribute(k_strip<R, ST_SELECT, true>, a, b) != cudaSuccess ||
+           cudaFuncSetAttribute(k_strip<R, ST_IFOD, true>, a, b) != cudaSuccess;
 }
 
 }  // namespace
@@ -602,7 +626,7 @@ int prepare_tensor_kernels()
 int launch_tensor_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
                          cudaStream_t st)
 {
-    return launch_strips<false>(B, h_sigmas, n_sigma, p, st);
+    return launch_strips<ST_TENSOR>(B, h_sigmas, n_sigma, p, st);
 }
 
 // Selection planes (vp, s2) of every scale and each image's max S^2 (which the
@@ -610,7 +634,14 @@ int launch_tensor_strips(const HostBatch &B, const float *h_sigmas, int n_sigma,
 int launch_select_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
                          cudaStream_t st)
 {
-    return launch_strips<true>(B, h_sigmas, n_sigma, p, st);
+    return launch_strips<ST_SELECT>(B, h_sigmas, n_sigma, p, st);
+}
+
+// IFOD tensor field (1, 0, g, g) of every image of the batch from u: one dense
+// strip launch at the regularisation scale sigma.
+int launch_ifod_tensor(const HostBatch &B, float sigma, const fd4_params &p, cudaStream_t st)
+{
+    return launch_strips<ST_IFOD>(B, &sigma, 1, p, st);
 }
 
 }  // namespace fd4

@@ -21,6 +21,7 @@ from . import build as _build
 RIDGE, VALLEY, BOTH = 0, 1, 2
 NATURAL, PERIODIC = 0, 1
 OP_SELECT_SCALES, OP_BUILD_TENSOR, OP_FED_CYCLE, OP_FILTER, OP_POSTPROCESS = 0, 1, 2, 3, 4
+MODEL_MAFOD, MODEL_IFOD = 0, 1
 STAGE_SELECT, STAGE_COPY, STAGE_TENSOR, STAGE_FED, STAGES_ALL = 1, 2, 4, 8, 15
 GRAPH_TWO_STREAMS = 16
 MAX_FED_STEPS = 4096
@@ -42,7 +43,7 @@ class Params(ctypes.Structure):
                 ("mode", ctypes.c_int), ("boundary", ctypes.c_int), ("kappa", ctypes.c_int),
                 ("grad_norm_squared", ctypes.c_int), ("fed_steps_per_launch", ctypes.c_int),
                 ("reselect_each_cycle", ctypes.c_int), ("postprocess_scales", ctypes.c_int),
-                ("theta", ctypes.c_float)]
+                ("theta", ctypes.c_float), ("model", ctypes.c_int), ("ifod_sigma", ctypes.c_float)]
 
 
 class Image(ctypes.Structure):
@@ -68,6 +69,7 @@ SIGNATURES = {
     "fd4_select_scales": (_i, [_vp, _i, _i, _i, _fp, _i, _pp, _vp, _vp, _vp, _sz, _vp]),
     "fd4_build_tensor": (_i, [_vp, _i, _i, _i, _vp, _fp, _i, _pp, _vp, _vp, _sz, _vp]),
     "fd4_postprocess_scales": (_i, [_vp, _i, _i, _i, _vp, _vp, _fp, _i, _pp, _vp, _sz, _vp]),
+    "fd4_build_tensor_ifod": (_i, [_vp, _i, _i, _i, _pp, _vp, _vp]),
     "fd4_fed_cycle": (_i, [_vp, _i, _i, _i, _vp, _dp, _i, _i, _vp, _sz, _vp]),
     "fd4_filter": (_i, [_vp, _vp, _i, _i, _i, _fp, _i, _pp, ctypes.c_double, _i, _i, _vp, _i, _vp,
                         _sz, _vp]),
@@ -232,6 +234,17 @@ def postprocess_scales(u, w: int, sigma_idx, vmax, sigmas, prm: Params | None = 
                                         ctypes.byref(prm) if prm is not None else None, _ptr(ws), ws.numel(),
                                         _stream(stream)), "fd4_postprocess_scales")
     return sigma_idx
+
+
+def build_tensor_ifod(u, w: int, prm: Params | None = None, out=None, stream=None):
+    """fd4_build_tensor_ifod.  Returns the (h, pitch, 4) IFOD tensor field (1, 0, g, g)."""
+    torch = _torch()
+    h, pitch = u.shape
+    if out is None:
+        out = torch.zeros((h, pitch, 4), dtype=torch.float32, device=u.device)
+    _check(lib().fd4_build_tensor_ifod(_ptr(u), int(w), h, pitch, ctypes.byref(prm) if prm is not None else None,
+                                       _ptr(out), _stream(stream)), "fd4_build_tensor_ifod")
+    return out
 
 
 def build_tensor(u, w: int, sigma_idx, sigmas, prm: Params | None = None, out=None, ws=None, stream=None):
