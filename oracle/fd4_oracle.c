@@ -27,6 +27,10 @@
  *                         the diagonal (row, column and diagonal means), the
  *                         walk cap, empty mask, isotropic Hessians, a straight
  *                         ridge (one scale per cross-section)
+ *   or_crease_field /     pinned: d and nu in closed form on quadratics, the
+ *   or_marching_squares   exact zero line of a linear field, both saddle
+ *                         resolutions, a straight ridge's centre line, the
+ *                         crease-type filter
  *   or_*_ifod             pinned: g = 1 on constants, g in closed form on
  *                         quadratics, g -> 1 as lambda grows (the cycle then
  *                         equals the biharmonic one), mean conservation
@@ -742,6 +746,89 @@ void or_fed_cycle(double *u, int w, int h, const double *tensor,
 /* The whole filter: sigma* once on the input (unless given), then M cycles of
  * (tensor from the current u at sigma*, one FED cycle).  u is filtered in
  * place.  sigma_idx_io: if sigma_given, read; else written.                 */
+/* ------------------------------------------------------------------------ */
+/* Crease extraction (Sec. 4, ridge and valley extraction): the zero contour
+ * of d = det(g | Hg), g the gradient and H the Hessian of u_sigma, by marching
+ * squares.  Readings (the paper names the method, not its discretisation):
+ * derivatives of u_sigma at one scale sigma with the kernels of
+ * or_gauss_kernels; cell (i, j) has the corners (i, j), (i+1, j), (i+1, j+1),
+ * (i, j+1) (x to the right, y down), a corner is inside where d > 0, edge
+ * crossings are linearly interpolated, a saddle cell (two diagonal corners
+ * inside) is resolved by the mean of its corners (mean > 0: the inside corners
+ * are connected); the zero set of d is a superset of the creases, and a cell's
+ * segments are kept where the mean over its corners of the strongest Hessian
+ * eigenvalue (the tie rule of or_select_scales) is negative (ridges) or
+ * positive (valleys), or non-zero (both).                                   */
+void or_crease_field(const double *u, int w, int h, double sigma, double *dfield, double *nu)
+{
+    size_t np = (size_t)w * h;
+    double *ux = malloc(sizeof(double) * np), *uy = malloc(sizeof(double) * np);
+    double *a = malloc(sizeof(double) * np), *b = malloc(sizeof(double) * np);
+    double *d = malloc(sizeof(double) * np);
+    or_derivatives(u, w, h, sigma, ux, uy, a, b, d);
+    for (size_t p = 0; p < np; ++p) {
+        double hgx = a[p] * ux[p] + b[p] * uy[p], hgy = b[p] * ux[p] + d[p] * uy[p];
+        dfield[p] = ux[p] * hgy - uy[p] * hgx;
+        double m = 0.5 * (a[p] + d[p]), r = hypot(0.5 * (a[p] - d[p]), b[p]);
+        nu[p] = m > 0.0 ? m + r : m - r;
+    }
+    free(ux); free(uy); free(a); free(b); free(d);
+}
+
+/* Segments of the zero contour of d: 4 doubles (x0, y0, x1, y1) and a key
+ * 2 * cell + k (cell = j * (w - 1) + i, k = 0 or 1) each, in key order; at most
+ * max_segs written; returns the number found.                               */
+int or_marching_squares(const double *d, const double *nu, int w, int h, int mode,
+                        double *segs, int *keys, int max_segs)
+{
+    int n = 0;
+    for (int j = 0; j + 1 < h; ++j)
+        for (int i = 0; i + 1 < w; ++i) {
+            double c[4] = {d[(size_t)j * w + i], d[(size_t)j * w + i + 1],
+                           d[(size_t)(j + 1) * w + i + 1], d[(size_t)(j + 1) * w + i]};
+            int cs = (c[0] > 0.0) | (c[1] > 0.0) << 1 | (c[2] > 0.0) << 2 | (c[3] > 0.0) << 3;
+            if (cs == 0 || cs == 15)
+                continue;
+            double nm = 0.25 * (nu[(size_t)j * w + i] + nu[(size_t)j * w + i + 1] +
+                                nu[(size_t)(j + 1) * w + i + 1] + nu[(size_t)(j + 1) * w + i]);
+            if ((mode == OR_RIDGE && !(nm < 0.0)) || (mode == OR_VALLEY && !(nm > 0.0)) ||
+                (mode == OR_BOTH && nm == 0.0))
+                continue;
+            /* crossing points on the edges top (0-1), right (1-2), bottom (3-2), left (0-3) */
+            double ex[4], ey[4];
+            ex[0] = i + c[0] / (c[0] - c[1]); ey[0] = j;
+            ex[1] = i + 1;                    ey[1] = j + c[1] / (c[1] - c[2]);
+            ex[2] = i + c[3] / (c[3] - c[2]); ey[2] = j + 1;
+            ex[3] = i;                        ey[3] = j + c[0] / (c[0] - c[3]);
+            int e0[2], e1[2], ns = 0;
+            if (cs == 5 || cs == 10) { /* saddle: corners 0 and 2, or 1 and 3, inside */
+                double mean = 0.25 * (c[0] + c[1] + c[2] + c[3]);
+                int cut02 = (cs == 5) != (mean > 0.0); /* the segments cut off corners 0 and 2 */
+                if (cut02) { e0[0] = 0; e1[0] = 3; e0[1] = 1; e1[1] = 2; }
+                else       { e0[0] = 0; e1[0] = 1; e0[1] = 2; e1[1] = 3; }
+                ns = 2;
+            } else {
+                static const int P0[4] = {0, 1, 3, 0}, P1[4] = {1, 2, 2, 3}; /* corners of edge e */
+                int cross[4], nc = 0;
+                for (int e = 0; e < 4; ++e)
+                    if ((c[P0[e]] > 0.0) != (c[P1[e]] > 0.0))
+                        cross[nc++] = e;
+                e0[0] = cross[0];
+                e1[0] = cross[1];
+                ns = 1;
+            }
+            for (int k = 0; k < ns; ++k) {
+                if (n < max_segs) {
+                    segs[4 * n + 0] = ex[e0[k]]; segs[4 * n + 1] = ey[e0[k]];
+                    segs[4 * n + 2] = ex[e1[k]]; segs[4 * n + 3] = ey[e1[k]];
+                    keys[n] = 2 * (j * (w - 1) + i) + k;
+                }
+                ++n;
+            }
+        }
+    return n;
+}
+
 /* ------------------------------------------------------------------------ */
 /* The isotropic fourth-order comparator (IFOD, Eq. 2, the nonlinear
  * fourth-order diffusion of Lysaker et al. in the form of Didas et al.): the

@@ -83,6 +83,10 @@ def _load():
                                              ctypes.c_double, _dp]
         lib.or_filter_ifod.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int]
+        lib.or_crease_field.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp]
+        lib.or_marching_squares.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
+                                            ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+        lib.or_marching_squares.restype = ctypes.c_int
         lib.or_strong_direction.argtypes = [ctypes.c_double] * 3 + [_dp, _dp]
         lib.or_strong_direction.restype = ctypes.c_int
         lib.or_postprocess_core.argtypes = [_u8p, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp,
@@ -233,6 +237,34 @@ def filter_ifod(u, tau, M, sigma=1.0, lam=0.005, boundary=NATURAL):
     tau = _f64(tau)
     _load().or_filter_ifod(_d(u), w, h, float(sigma), float(lam), int(boundary), _d(tau), tau.size, int(M))
     return u
+
+
+def crease_field(u, sigma=1.0):
+    """d = det(g | Hg) and the strongest Hessian eigenvalue of u_sigma, each (h, w) (Sec. 4)."""
+    u = _f64(u)
+    h, w = u.shape
+    d, nu = np.zeros((h, w)), np.zeros((h, w))
+    _load().or_crease_field(_d(u), w, h, float(sigma), _d(d), _d(nu))
+    return d, nu
+
+
+def marching_squares(d, nu, mode=BOTH):
+    """Zero-contour segments of d kept by the crease-type filter on nu.
+    Returns (segments (n, 4) as x0, y0, x1, y1; keys (n,) = 2 * cell + k)."""
+    d, nu = _f64(d), _f64(nu)
+    h, w = d.shape
+    cap = 2 * max(w - 1, 1) * max(h - 1, 1)
+    segs = np.zeros((cap, 4))
+    keys = np.zeros(cap, dtype=np.int32)
+    n = _load().or_marching_squares(_d(d), _d(nu), w, h, int(mode), _d(segs),
+                                    keys.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), cap)
+    return segs[:n].copy(), keys[:n].copy()
+
+
+def extract_creases(u, sigma=1.0, mode=BOTH):
+    """Crease extraction of Sec. 4 on u: marching squares on det(g | Hg) of u_sigma."""
+    d, nu = crease_field(u, sigma)
+    return marching_squares(d, nu, mode)
 
 
 def strong_direction(a, b, d):
