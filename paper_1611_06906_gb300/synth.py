@@ -196,6 +196,18 @@ def vessel_tree(seed: int, w: int = 1024, h: int = 1024, depth: int = 6, r0: flo
     return img.astype(np.float32)
 
 
+def vessel_tree_centrelines(seed: int, w: int = 1024, h: int = 1024, depth: int = 6, r0: float = 8.0,
+                            r1: float = 1.0, noise=None):
+    """The centre-line segments (ax, ay, bx, by, radius) of vessel_tree with the same
+    arguments: the generator's draws replayed up to the tree (the ground truth of the
+    crease evaluation)."""
+    rng = SplitMix64(seed)
+    if noise is None:
+        rng.scalar()
+    rng.scalar()  # gradient angle
+    return _tree_segments(rng, w, h, depth, r0, r1)
+
+
 def fundus_like(seed: int, side: int, depth: int = 6, noise: float = 0.1):
     """Fundus-like square image: circular field of view, radial vignetting, dark tree."""
     tree = vessel_tree(seed, side, side, depth=depth, noise=0.0).astype(np.float64)
