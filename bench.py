@@ -425,6 +425,8 @@ def run_fd4(args, rank, world, local_rank):
     if ifod is not None:
         ifod.pop("_out", None)
         out["ifod"] = ifod
+    if world == 1 and not args.no_creases and args.workload == "batch64_fundus":
+        out["creases"] = crease_leg(args, ims, mode, stream, torch, fd4)
     if resel is not None:
         resel.pop("_out", None)
         out["reselect"] = resel
@@ -434,6 +436,54 @@ def run_fd4(args, rank, world, local_rank):
     for g in {id(x): x for x in (g_all, g_one, g_sel, g_ten, g_fed)}.values():
         g.close()
     print(json.dumps(out), flush=True)
+
+
+def crease_leg(args, ims, mode, stream, torch, fd4):
+    """Crease extraction (Sec. 4) timed over the filtered batch, and the accuracy
+    of Sec. 5 (E, p against the generator's centre lines inside the field of
+    view, 6-pixel neighbourhood) of the creases of the input and of the
+    filtered output of the two smallest images."""
+    import ctypes
+    from paper_1611_06906_gb300 import creases, synth
+    sigma_d = 1.0
+    maxw = max(b.w for b in ims)
+    maxh = max(b.h for b in ims)
+    cap = 2 * (maxw - 1) * (maxh - 1)
+    segs = torch.empty((cap, 4), dtype=torch.float32, device=ims[0].out.device)
+    keys = torch.empty(cap, dtype=torch.int32, device=segs.device)
+    count = torch.zeros(1, dtype=torch.int32, device=segs.device)
+    ws = fd4.workspace(fd4.OP_CREASES, max(b.pitch for b in ims), maxh, 0, segs.device)
+
+    def run_all():
+        for b in ims:
+            rc = fd4.lib().fd4_extract_creases(ctypes.c_void_p(b.out.data_ptr()), b.w, b.h, b.pitch, sigma_d, mode,
+                                               ctypes.c_void_p(segs.data_ptr()), ctypes.c_void_p(keys.data_ptr()),
+                                               cap, ctypes.c_void_p(count.data_ptr()),
+                                               ctypes.c_void_p(ws.data_ptr()), ws.numel(), None)
+            if rc != 0:
+                raise fd4.Fd4Error(rc, "fd4_extract_creases")
+
+    run_all()
+    torch.cuda.synchronize()
+    ms = _timed(run_all, 3, stream, torch) / 3
+    base = rank_seed(3000, 0)
+    sides = synth.batch_sides(base)
+    order = sorted(range(len(ims)), key=lambda i: ims[i].npx)[:2]
+    acc = []
+    for i in order:
+        side = sides[i]
+        c = (side - 1) / 2.0
+        gt = [g for g in synth.vessel_tree_centrelines(base + i, side, side, depth=6, noise=0.0)
+              if max(math.hypot(g[0] - c, g[1] - c), math.hypot(g[2] - c, g[3] - c)) < 0.9 * 0.48 * side]
+        s_in, _ = fd4.extract_creases(ims[i].u_in, ims[i].w, sigma_d, mode)
+        s_out, _ = fd4.extract_creases(ims[i].out, ims[i].w, sigma_d, mode)
+        e_in, p_in = creases.evaluate(s_in, gt)
+        e_out, p_out = creases.evaluate(s_out, gt)
+        acc.append({"image": "%dx%d" % (ims[i].w, ims[i].h), "E_input": e_in, "p_input": p_in,
+                    "E_filtered": e_out, "p_filtered": p_out, "segments_input": int(len(s_in)),
+                    "segments_filtered": int(len(s_out)), "truth_segments": len(gt)})
+    return {"sigma": sigma_d, "ms_per_batch": ms, "mpixel_per_s": sum(b.npx for b in ims) / (ms * 1e-3) / 1e6,
+            "path": "fd4_extract_creases per filtered image (field + marching squares)", "accuracy": acc}
 
 
 def learned_variant(args, ims, sig, T, M, n, mode, best, stream, torch, fd4):
@@ -551,6 +601,7 @@ def main():
     ap.add_argument("--no-reselect", action="store_true", help="skip the per-cycle re-selection variant")
     ap.add_argument("--no-postprocess", action="store_true", help="skip the scale post-processing variant")
     ap.add_argument("--no-ifod", action="store_true", help="skip the IFOD comparator")
+    ap.add_argument("--no-creases", action="store_true", help="skip the crease extraction and its accuracy")
     ap.add_argument("--two-streams", type=int, default=0, help="headline graph on two streams (1) or one (0)")
     ap.add_argument("--sel-crops", type=int, default=4096, help="training crops of the learned selector")
     ap.add_argument("--sel-threshold", type=float, default=0.5, help="fallback confidence threshold")

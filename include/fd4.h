@@ -147,7 +147,8 @@ typedef enum fd4_op {
     FD4_OP_BUILD_TENSOR = 1,
     FD4_OP_FED_CYCLE = 2,
     FD4_OP_FILTER = 3,
-    FD4_OP_POSTPROCESS = 4
+    FD4_OP_POSTPROCESS = 4,
+    FD4_OP_CREASES = 5
 } fd4_op;
 size_t fd4_workspace_bytes(int op, int w, int h, int n_sigma);
 
@@ -195,6 +196,29 @@ int fd4_postprocess_scales(const float *d_u, int w, int h, int pitch, uint8_t *d
  * d_tensor: 4 floats per pixel, row pitch `pitch` pixels.  No workspace.    */
 int fd4_build_tensor_ifod(const float *d_u, int w, int h, int pitch, const fd4_params *params,
                           float *d_tensor, fd4_stream_t stream);
+
+/* Crease extraction (Sec. 4, ridge and valley extraction): the zero contour of
+ * d = det(g | Hg), g the gradient and H the Hessian of u_s at s = sigma
+ * (0 < sigma <= 4; derivatives as in fd4_select_scales), by marching squares on
+ * the pixel grid.  Cell (i, j) has the corners (i, j), (i+1, j), (i+1, j+1),
+ * (i, j+1) (x to the right, y down); a corner is inside where d > 0; edge
+ * crossings are linearly interpolated; a saddle cell is resolved by the mean
+ * of its corners (mean > 0: the inside corners are connected).  The zero set
+ * of d is a superset of the creases: a cell's segments are kept where the
+ * mean over its corners of the strongest Hessian eigenvalue (the one of
+ * largest magnitude, the negative one on a tie) is negative (FD4_RIDGE),
+ * positive (FD4_VALLEY) or non-zero (FD4_BOTH).
+ *   d_segs   4 floats per segment (x0, y0, x1, y1, pixel units), 16-byte aligned
+ *   d_keys   one int per segment: 2 * (j * (w - 1) + i) + k, k = 0 or 1 (a
+ *            saddle cell has two segments), ordering the segments by cell
+ *   d_count  one device int: the number of segments found (the first
+ *            max_segs of them, in any order, are written)
+ *   workspace fd4_workspace_bytes(FD4_OP_CREASES, pitch, h, 0)
+ * Errors: FD4_ERR_BAD_ARG for sigma outside (0, 4], a bad mode, null outputs
+ * or max_segs < 0, otherwise as for fd4_select_scales.                      */
+int fd4_extract_creases(const float *d_u, int w, int h, int pitch, float sigma, int mode, float *d_segs,
+                        int *d_keys, int max_segs, int *d_count, void *d_ws, size_t ws_bytes,
+                        fd4_stream_t stream);
 
 /* Fourth-order diffusion tensor field (Sec. 3.1 Eq. 6, Sec. 3.2 Eq. 7-8).
  * N = H(u_s) / sqrt(1 + |grad u_s|) at s = h_sigmas[d_sigma_idx[p]] per pixel

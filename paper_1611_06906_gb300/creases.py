@@ -25,27 +25,21 @@ import numpy as np
 def chains(segs: np.ndarray, tol: float = 1e-6):
     """Polygonal chains of segments (n, 4) joined at shared endpoints: a list of
     index arrays into segs (connected components)."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
     n = len(segs)
     if n == 0:
         return []
-    parent = np.arange(n)
-
-    def find(i):
-        while parent[i] != i:
-            parent[i] = parent[parent[i]]
-            i = parent[i]
-        return i
-
-    pts = np.concatenate([segs[:, 0:2], segs[:, 2:4]])  # endpoint k of segment k % n
+    pts = np.concatenate([segs[:, 0:2], segs[:, 2:4]])  # endpoint k belongs to segment k % n
     key = np.round(pts / tol).astype(np.int64)
     order = np.lexsort((key[:, 1], key[:, 0]))
-    for a, b in zip(order[:-1], order[1:]):
-        if key[a, 0] == key[b, 0] and key[a, 1] == key[b, 1]:
-            ra, rb = find(a % n), find(b % n)
-            if ra != rb:
-                parent[ra] = rb
-    roots = np.array([find(i) for i in range(n)])
-    return [np.nonzero(roots == r)[0] for r in np.unique(roots)]
+    same = np.all(key[order[1:]] == key[order[:-1]], axis=1)
+    a, b = order[:-1][same] % n, order[1:][same] % n
+    graph = coo_matrix((np.ones(a.size), (a, b)), shape=(n, n))
+    _, label = connected_components(graph, directed=False)
+    srt = np.argsort(label, kind="stable")
+    bounds = np.flatnonzero(np.diff(label[srt])) + 1
+    return np.split(srt, bounds)
 
 
 def _point_segment_dist(p: np.ndarray, a: np.ndarray, b: np.ndarray) -> np.ndarray:
@@ -62,7 +56,9 @@ def evaluate(segs: np.ndarray, truth, neighbourhood: float = 6.0, step: float = 
     """E and p of crease segments (n, 4) = (x0, y0, x1, y1) against ground-truth
     segments [(ax, ay, bx, by, ...), ...].  Returns (E or nan, p)."""
     segs = np.asarray(segs, dtype=np.float64).reshape(-1, 4)
-    groups = chains(segs)
+    chain_of = np.full(len(segs), -1, dtype=np.int64)
+    for c, idx in enumerate(chains(segs)):
+        chain_of[idx] = c
     dists, lengths, matched = [], [], []
     for g in truth:
         a = np.array(g[0:2], dtype=np.float64)
@@ -73,20 +69,20 @@ def evaluate(segs: np.ndarray, truth, neighbourhood: float = 6.0, step: float = 
         k = max(int(np.ceil(L / step)), 1)
         samples = a[None, :] + np.linspace(0.0, 1.0, k + 1)[:, None] * (b - a)[None, :]
         best = None
-        for idx in groups:
-            s = segs[idx]
-            # keep the chain's segments whose endpoints both lie in the neighbourhood
-            d0 = _point_segment_dist(s[:, 0:2], a[None, :], b[None, :])[:, 0]
-            d1 = _point_segment_dist(s[:, 2:4], a[None, :], b[None, :])[:, 0]
-            keep = (d0 <= neighbourhood) & (d1 <= neighbourhood)
-            if not keep.any():
-                continue
-            s = s[keep]
-            to_chain = _point_segment_dist(samples, s[:, 0:2], s[:, 2:4]).min(axis=1)
-            to_truth = np.maximum(d0[keep], d1[keep])
-            haus = max(float(to_chain.max()), float(to_truth.max()))
-            if best is None or haus < best[0]:
-                best = (haus, float(to_chain.mean()))
+        if len(segs):
+            # the segments whose endpoints both lie in the neighbourhood, by chain
+            d0 = _point_segment_dist(segs[:, 0:2], a[None, :], b[None, :])[:, 0]
+            d1 = _point_segment_dist(segs[:, 2:4], a[None, :], b[None, :])[:, 0]
+            idx = np.flatnonzero((d0 <= neighbourhood) & (d1 <= neighbourhood))
+            idx = idx[np.argsort(chain_of[idx], kind="stable")]
+            groups = np.split(idx, np.flatnonzero(np.diff(chain_of[idx])) + 1) if idx.size else []
+            for sel in groups:
+                s = segs[sel]
+                to_chain = _point_segment_dist(samples, s[:, 0:2], s[:, 2:4]).min(axis=1)
+                to_truth = np.maximum(d0[sel], d1[sel])
+                haus = max(float(to_chain.max()), float(to_truth.max()))
+                if best is None or haus < best[0]:
+                    best = (haus, float(to_chain.mean()))
         lengths.append(L)
         matched.append(best is not None)
         if best is not None:

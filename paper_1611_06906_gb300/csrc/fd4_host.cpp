@@ -275,6 +275,7 @@ extern "C" size_t fd4_workspace_bytes(int op, int w, int h, int n_sigma)
     case FD4_OP_FED_CYCLE: return ws_fed_bytes(h, pitch);
     case FD4_OP_FILTER: return ws_filter_bytes(h, pitch, n_sigma);
     case FD4_OP_POSTPROCESS: return plane_bytes(h, pitch, 16) + plane_bytes(h, pitch, 1);
+    case FD4_OP_CREASES: return plane_bytes(h, pitch, 8);
     default: return 0;
     }
 }
@@ -333,6 +334,20 @@ extern "C" int fd4_postprocess_scales(const float *d_u, int w, int h, int pitch,
     d.h = h;
     d.pitch = pitch;
     return cuda_status(launch_postprocess_batch(single_batch(d), h_sigmas, n_sigma, p, (cudaStream_t)stream));
+}
+
+extern "C" int fd4_extract_creases(const float *d_u, int w, int h, int pitch, float sigma, int mode,
+                                   float *d_segs, int *d_keys, int max_segs, int *d_count, void *d_ws,
+                                   size_t ws_bytes, fd4_stream_t stream)
+{
+    int rc;
+    if ((rc = check_image(d_u, w, h, pitch)) != FD4_OK) return rc;
+    if (!(sigma > 0.0f && sigma <= 4.0f) || mode < FD4_RIDGE || mode > FD4_BOTH) return FD4_ERR_BAD_ARG;
+    if (!d_segs || !d_keys || !d_count || max_segs < 0) return FD4_ERR_BAD_ARG;
+    if ((uintptr_t)d_segs & 15u) return FD4_ERR_ALIGN;
+    if ((rc = ws_ok(d_ws, ws_bytes, plane_bytes(h, pitch, 8))) != FD4_OK) return rc;
+    return cuda_status(launch_creases(d_u, w, h, pitch, sigma, mode, d_segs, d_keys, max_segs, d_count, d_ws,
+                                      (cudaStream_t)stream));
 }
 
 extern "C" int fd4_build_tensor_ifod(const float *d_u, int w, int h, int pitch, const fd4_params *params,

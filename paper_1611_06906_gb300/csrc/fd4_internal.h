@@ -258,6 +258,9 @@ int launch_tensor_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, 
 // nfield = N at each pixel's selected scale, one strip-walking launch per scale (fd4_tensor.cu).
 int launch_tensor_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
                          cudaStream_t st);
+// Crease segments of one image (fd4_creases.cu); d_ws holds the d / nu field.
+int launch_creases(const float *d_u, int w, int h, int pitch, float sigma, int mode, float *d_segs, int *d_keys,
+                   int max_segs, int *d_count, void *d_ws, cudaStream_t st);
 // IFOD tensor (1, 0, g, g) of every image of a batch from u (fd4_tensor.cu).
 int launch_ifod_tensor(const HostBatch &B, float sigma, const fd4_params &p, cudaStream_t st);
 // Scale-image post-processing of every image of a batch from idx, vmax and u

@@ -20,7 +20,7 @@ from . import build as _build
 
 RIDGE, VALLEY, BOTH = 0, 1, 2
 NATURAL, PERIODIC = 0, 1
-OP_SELECT_SCALES, OP_BUILD_TENSOR, OP_FED_CYCLE, OP_FILTER, OP_POSTPROCESS = 0, 1, 2, 3, 4
+OP_SELECT_SCALES, OP_BUILD_TENSOR, OP_FED_CYCLE, OP_FILTER, OP_POSTPROCESS, OP_CREASES = 0, 1, 2, 3, 4, 5
 MODEL_MAFOD, MODEL_IFOD = 0, 1
 STAGE_SELECT, STAGE_COPY, STAGE_TENSOR, STAGE_FED, STAGES_ALL = 1, 2, 4, 8, 15
 GRAPH_TWO_STREAMS = 16
@@ -70,6 +70,7 @@ SIGNATURES = {
     "fd4_build_tensor": (_i, [_vp, _i, _i, _i, _vp, _fp, _i, _pp, _vp, _vp, _sz, _vp]),
     "fd4_postprocess_scales": (_i, [_vp, _i, _i, _i, _vp, _vp, _fp, _i, _pp, _vp, _sz, _vp]),
     "fd4_build_tensor_ifod": (_i, [_vp, _i, _i, _i, _pp, _vp, _vp]),
+    "fd4_extract_creases": (_i, [_vp, _i, _i, _i, ctypes.c_float, _i, _vp, _vp, _i, _vp, _vp, _sz, _vp]),
     "fd4_fed_cycle": (_i, [_vp, _i, _i, _i, _vp, _dp, _i, _i, _vp, _sz, _vp]),
     "fd4_filter": (_i, [_vp, _vp, _i, _i, _i, _fp, _i, _pp, ctypes.c_double, _i, _i, _vp, _i, _vp,
                         _sz, _vp]),
@@ -234,6 +235,27 @@ def postprocess_scales(u, w: int, sigma_idx, vmax, sigmas, prm: Params | None = 
                                         ctypes.byref(prm) if prm is not None else None, _ptr(ws), ws.numel(),
                                         _stream(stream)), "fd4_postprocess_scales")
     return sigma_idx
+
+
+def extract_creases(u, w: int, sigma: float = 1.0, mode: int = BOTH, max_segs: int = 0, ws=None, stream=None):
+    """fd4_extract_creases.  Returns (segments (n, 4) float64 as x0, y0, x1, y1;
+    keys (n,)), sorted by key (the cell walk's order)."""
+    torch = _torch()
+    h, pitch = u.shape
+    if max_segs <= 0:
+        max_segs = 2 * max(w - 1, 1) * max(h - 1, 1)
+    segs = torch.empty((max_segs, 4), dtype=torch.float32, device=u.device)
+    keys = torch.empty(max_segs, dtype=torch.int32, device=u.device)
+    count = torch.zeros(1, dtype=torch.int32, device=u.device)
+    if ws is None:
+        ws = workspace(OP_CREASES, pitch, h, 0, u.device)
+    _check(lib().fd4_extract_creases(_ptr(u), int(w), h, pitch, float(sigma), int(mode), _ptr(segs), _ptr(keys),
+                                     int(max_segs), _ptr(count), _ptr(ws), ws.numel(), _stream(stream)),
+           "fd4_extract_creases")
+    n = min(int(count.item()), max_segs)
+    k = keys[:n].cpu().numpy()
+    order = np.argsort(k, kind="stable")
+    return segs[:n].cpu().numpy().astype(np.float64)[order], k[order]
 
 
 def build_tensor_ifod(u, w: int, prm: Params | None = None, out=None, stream=None):
