@@ -5,8 +5,9 @@
 // border of the selection); one thread per cell then emits the cell's
 // segments, kept where the mean nu of the cell's corners has the crease's
 // sign (ridges negative, valleys positive; both: non-zero).  A saddle cell is
-// resolved by the mean of its corners.  Segments are appended in any order,
-// each with the key 2 * cell + k that orders them as the cell walk would.
+// resolved by the mean of its corners.  Segments are appended in any order
+// (one counter atomic per warp), each with the key 2 * cell + k that orders
+// them as the cell walk would.
 #include <cmath>
 #include <cstdint>
 
@@ -82,51 +83,63 @@ __global__ void __launch_bounds__(256) k_crease_field(const float *u, int w, int
 }
 
 // One thread per cell (i, j): corners (i, j), (i+1, j), (i+1, j+1), (i, j+1).
+// The segments of a warp are appended with one atomic on the counter (an
+// inclusive scan of the lanes' counts), so no thread leaves before the scan.
 __global__ void __launch_bounds__(256) k_marching(const float2 *field, int w, int h, int pitch, int mode,
                                                   float4 *segs, int *keys, int max_segs, int *count)
 {
-    const int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (i + 1 >= w || j + 1 >= h) return;
-    const float2 f0 = field[(size_t)j * pitch + i], f1 = field[(size_t)j * pitch + i + 1];
-    const float2 f2 = field[(size_t)(j + 1) * pitch + i + 1], f3 = field[(size_t)(j + 1) * pitch + i];
-    const float c[4] = {f0.x, f1.x, f2.x, f3.x};
-    const int cs = (c[0] > 0.0f) | (c[1] > 0.0f) << 1 | (c[2] > 0.0f) << 2 | (c[3] > 0.0f) << 3;
-    if (cs == 0 || cs == 15) return;
-    const float nm = 0.25f * (f0.y + f1.y + f2.y + f3.y);
-    if ((mode == FD4_RIDGE && !(nm < 0.0f)) || (mode == FD4_VALLEY && !(nm > 0.0f)) ||
-        (mode == FD4_BOTH && nm == 0.0f))
-        return;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 32 + lane, j = blockIdx.y * 8 + (threadIdx.x >> 5);
+    int ns = 0, e0[2] = {0, 0}, e1[2] = {0, 0};
     float ex[4], ey[4];  // crossings on the edges top (0-1), right (1-2), bottom (3-2), left (0-3)
-    ex[0] = i + c[0] / (c[0] - c[1]);
-    ey[0] = (float)j;
-    ex[1] = (float)(i + 1);
-    ey[1] = j + c[1] / (c[1] - c[2]);
-    ex[2] = i + c[3] / (c[3] - c[2]);
-    ey[2] = (float)(j + 1);
-    ex[3] = (float)i;
-    ey[3] = j + c[0] / (c[0] - c[3]);
-    int e0[2] = {0, 0}, e1[2] = {0, 0}, ns;
-    if (cs == 5 || cs == 10) {  // saddle
-        const float mean = 0.25f * (c[0] + c[1] + c[2] + c[3]);
-        const bool cut02 = (cs == 5) != (mean > 0.0f);
-        if (cut02) {
-            e0[0] = 0; e1[0] = 3; e0[1] = 1; e1[1] = 2;
-        } else {
-            e0[0] = 0; e1[0] = 1; e0[1] = 2; e1[1] = 3;
-        }
-        ns = 2;
-    } else {
-        const int P0[4] = {0, 1, 3, 0}, P1[4] = {1, 2, 2, 3};
-        int nc = 0;
-        for (int e = 0; e < 4; ++e)
-            if ((c[P0[e]] > 0.0f) != (c[P1[e]] > 0.0f)) {
-                if (nc == 0) e0[0] = e;
-                else e1[0] = e;
-                ++nc;
+    if (i + 1 < w && j + 1 < h) {
+        const float2 f0 = field[(size_t)j * pitch + i], f1 = field[(size_t)j * pitch + i + 1];
+        const float2 f2 = field[(size_t)(j + 1) * pitch + i + 1], f3 = field[(size_t)(j + 1) * pitch + i];
+        const float c[4] = {f0.x, f1.x, f2.x, f3.x};
+        const int cs = (c[0] > 0.0f) | (c[1] > 0.0f) << 1 | (c[2] > 0.0f) << 2 | (c[3] > 0.0f) << 3;
+        const float nm = 0.25f * (f0.y + f1.y + f2.y + f3.y);
+        const bool keep = (mode == FD4_RIDGE && nm < 0.0f) || (mode == FD4_VALLEY && nm > 0.0f) ||
+                          (mode == FD4_BOTH && nm != 0.0f);
+        if (cs != 0 && cs != 15 && keep) {
+            ex[0] = i + c[0] / (c[0] - c[1]);
+            ey[0] = (float)j;
+            ex[1] = (float)(i + 1);
+            ey[1] = j + c[1] / (c[1] - c[2]);
+            ex[2] = i + c[3] / (c[3] - c[2]);
+            ey[2] = (float)(j + 1);
+            ex[3] = (float)i;
+            ey[3] = j + c[0] / (c[0] - c[3]);
+            if (cs == 5 || cs == 10) {  // saddle
+                const float mean = 0.25f * (c[0] + c[1] + c[2] + c[3]);
+                const bool cut02 = (cs == 5) != (mean > 0.0f);
+                if (cut02) {
+                    e0[0] = 0; e1[0] = 3; e0[1] = 1; e1[1] = 2;
+                } else {
+                    e0[0] = 0; e1[0] = 1; e0[1] = 2; e1[1] = 3;
+                }
+                ns = 2;
+            } else {
+                const int P0[4] = {0, 1, 3, 0}, P1[4] = {1, 2, 2, 3};
+                int nc = 0;
+                for (int e = 0; e < 4; ++e)
+                    if ((c[P0[e]] > 0.0f) != (c[P1[e]] > 0.0f)) {
+                        if (nc == 0) e0[0] = e;
+                        else e1[0] = e;
+                        ++nc;
+                    }
+                ns = 1;
             }
-        ns = 1;
+        }
     }
-    const int base = atomicAdd(count, ns);
+    int incl = ns;  // inclusive scan of the warp's counts
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    int base = 0;
+    if (lane == 31 && incl > 0) base = atomicAdd(count, incl);
+    base = __shfl_sync(0xffffffffu, base, 31) + incl - ns;
     for (int k = 0; k < ns; ++k)
         if (base + k < max_segs) {
             segs[base + k] = make_float4(ex[e0[k]], ey[e0[k]], ex[e1[k]], ey[e1[k]]);
