@@ -326,7 +326,7 @@ int fd4_autotune_batched(const fd4_image *h_imgs, int n_images, const float *h_s
 /* Learned scale selector.  No counterpart in the paper: a small network that
  * predicts the per-pixel scale index the vesselness argmax (Sec. 3.3) would
  * select, trained on labels the plain selection produces, with the plain
- * selection as fallback and judge.  Network: four dilated 3x3 convolutions
+ * selection as fallback and reference.  Network: four dilated 3x3 convolutions
  * (dilations 1, 2, 4, 8; channels 1-32-32-32-8; zero padding), ReLU between
  * them, softmax over 8 scale bins.  BF16 weights and activations, FP32
  * accumulation on the tensor cores (tcgen05).
@@ -358,7 +358,7 @@ int fd4_selector_update(void *d_params, float lr, int step, fd4_stream_t stream)
 /* Scale index (argmax bin) and confidence (its probability) per pixel.     */
 int fd4_selector_predict(const void *d_params, const float *d_img, int w, int h, int pitch, uint8_t *d_idx,
                          float *d_conf, void *d_ws, size_t ws_bytes, fd4_stream_t stream);
-/* Learned selection with the plain selection as fallback and judge.  The
+/* Learned selection with the plain selection as fallback and reference.  The
  * network predicts a scale index and a confidence (its softmax probability)
  * per pixel; every 32 x 64 tile whose least confident pixel is below
  * conf_threshold is recomputed with the plain vesselness selection

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY (imported by tests/ and never by the library).
 
 The paper selects the scale per pixel with the vesselness argmax (Sec. 3.3);
 the learned selector is an addition of this project that predicts that
-argmax with a small convolutional network, judged against the plain sweep.
+argmax with a small convolutional network, checked against the plain sweep.
 Network (all 3 x 3 correlations, zero padding, "same" output size):
 
     layer l: out[y, x, co] = b[co] + sum_{ky, kx, ci} W[ky, kx, co, ci] in[y + d (ky - 1), x + d (kx - 1), ci]

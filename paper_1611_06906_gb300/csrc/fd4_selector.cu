@@ -1,6 +1,6 @@
 // Learned scale selector (no counterpart in the paper: the paper selects the
 // scale with the vesselness argmax of Sec. 3.3; this network predicts that
-// argmax and the plain sweep judges it).
+// argmax and the plain sweep checks it).
 //
 // Network: four dilated 3 x 3 convolutions (dilations 1, 2, 4, 8; channels
 // 1 -> 32 -> 32 -> 32 -> 8), ReLU between them, softmax over 8 scale bins.
