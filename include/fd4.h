@@ -287,7 +287,9 @@ int fd4_filter_batched(const fd4_image *h_imgs, int n_images, const float *h_sig
  * graph and replayed by fd4_graph_launch.  `stages` selects what is captured:
  * FD4_STAGES_ALL for the filter; a subset replays only those stages on the
  * current workspace contents (for timing one stage: FD4_STAGE_FED alone runs
- * M FED cycles on the images with the tensor fields left by a previous run).
+ * M FED cycles on the images with the tensor fields left by a previous run;
+ * the scale-image post-processing, which reads the copied input, runs only
+ * when FD4_STAGE_COPY is captured too).
  * The graph keeps the device pointers of h_imgs and d_ws: those buffers must
  * stay allocated while the graph exists; their contents are read at each
  * launch.  The host arrays may be freed after the call.                     */

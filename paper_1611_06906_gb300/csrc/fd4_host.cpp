@@ -433,8 +433,10 @@ static int enqueue_filter(const HostBatch &B, const float *h_sigmas, int n_sigma
         return FD4_ERR_CUDA;
     if ((stages & FD4_STAGE_COPY) && launch_copy_in_batch(B, st)) return FD4_ERR_CUDA;
     // the post-processing reads u (the strips' N at the selected scales), so the
-    // first one follows the copy of the input into u
-    const bool post = mafod && p.postprocess_scales && !sigma_given && (stages & FD4_STAGE_SELECT);
+    // first one follows the copy of the input into u; a schedule without that
+    // copy (a stage-split graph) selects without post-processing
+    const bool post = mafod && p.postprocess_scales && !sigma_given && (stages & FD4_STAGE_SELECT) &&
+                      (stages & FD4_STAGE_COPY);
     if (post && launch_postprocess_batch(B, h_sigmas, n_sigma, p, st)) return FD4_ERR_CUDA;
     const bool reselect = mafod && p.reselect_each_cycle && !sigma_given && (stages & FD4_STAGE_SELECT);
     for (int k = 0; k < M; ++k) {
@@ -715,7 +717,7 @@ static int enqueue_batch(const fd4_image *imgs, int n_images, const float *h_sig
     std::vector<ImgDesc> descs;
     HostBatch B;
     const bool sel = p.model == FD4_MODEL_MAFOD && !sigma_given && (stages & FD4_STAGE_SELECT);
-    const bool post = sel && p.postprocess_scales;
+    const bool post = sel && p.postprocess_scales && (stages & FD4_STAGE_COPY);
     batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B, 0, nullptr, post);
     const bool reselect = sel && p.reselect_each_cycle;
     if (put_tables(descs, n_images, B, d_ws, reselect, st)) return FD4_ERR_CUDA;
