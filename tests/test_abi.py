@@ -137,3 +137,49 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(py)
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_host_side_argument_errors_of_the_added_entry_points():
+    """Scale post-processing, IFOD tensor, crease extraction and the added
+    filter parameters: every check below fails before any CUDA call."""
+    L = fd4.lib()
+    sig = (ctypes.c_float * 2)(1.0, 2.0)
+    fake = ctypes.c_void_p(1 << 20)
+    odd = ctypes.c_void_p((1 << 20) + 2)
+    ws = ctypes.c_void_p(1 << 24)
+    big = 1 << 40
+    # post-processing: null index / V map, unaligned V map, small workspace, theta outside [0, 1]
+    assert L.fd4_postprocess_scales(fake, 8, 8, 8, None, fake, sig, 2, None, ws, big, None) == -1
+    assert L.fd4_postprocess_scales(fake, 8, 8, 8, fake, None, sig, 2, None, ws, big, None) == -1
+    assert L.fd4_postprocess_scales(fake, 8, 8, 8, fake, odd, sig, 2, None, ws, big, None) == -8
+    assert L.fd4_postprocess_scales(fake, 8, 8, 8, fake, fake, sig, 2, None, ws, 16, None) == -5
+    p = fd4.params(theta=1.5)
+    assert L.fd4_postprocess_scales(fake, 8, 8, 8, fake, fake, sig, 2, ctypes.byref(p), ws, big, None) == -1
+    # IFOD tensor: null / unaligned output, bad scale, bad model
+    assert L.fd4_build_tensor_ifod(fake, 8, 8, 8, None, None, None) == -1
+    assert L.fd4_build_tensor_ifod(fake, 8, 8, 8, None, ctypes.c_void_p((1 << 20) + 4), None) == -8
+    for kw in (dict(ifod_sigma=0.0), dict(ifod_sigma=13.0), dict(model=5)):
+        p = fd4.params(**kw)
+        assert L.fd4_build_tensor_ifod(fake, 8, 8, 8, ctypes.byref(p), fake, None) == -1
+    # creases: scale, mode, outputs, capacity, alignment, workspace
+    cnt = ctypes.c_void_p(1 << 22)
+    assert L.fd4_extract_creases(fake, 8, 8, 8, 5.0, 0, fake, fake, 10, cnt, ws, big, None) == -1
+    assert L.fd4_extract_creases(fake, 8, 8, 8, 1.0, 3, fake, fake, 10, cnt, ws, big, None) == -1
+    assert L.fd4_extract_creases(fake, 8, 8, 8, 1.0, 0, None, fake, 10, cnt, ws, big, None) == -1
+    assert L.fd4_extract_creases(fake, 8, 8, 8, 1.0, 0, fake, fake, -1, cnt, ws, big, None) == -1
+    assert L.fd4_extract_creases(fake, 8, 8, 8, 1.0, 0, ctypes.c_void_p((1 << 20) + 4), fake, 10, cnt, ws, big,
+                                 None) == -8
+    assert L.fd4_extract_creases(fake, 8, 8, 8, 1.0, 0, fake, fake, 10, cnt, ws, 16, None) == -5
+    # whole filter: the added switches take 0 or 1, theta lies in [0, 1]
+    for kw in (dict(reselect_each_cycle=2), dict(postprocess_scales=-1), dict(theta=-0.5), dict(model=2)):
+        p = fd4.params(**kw)
+        assert L.fd4_filter(fake, fake, 8, 8, 8, sig, 2, ctypes.byref(p), 11 / 3, 2, 10, None, 0, ws, big,
+                            None) == -1
+
+
+def test_workspace_sizes_of_the_added_entry_points():
+    a = fd4.workspace_bytes(fd4.OP_POSTPROCESS, 100, 100, 4)
+    b = fd4.workspace_bytes(fd4.OP_POSTPROCESS, 200, 100, 4)
+    assert 0 < a < b and a >= 100 * 100 * 17
+    c = fd4.workspace_bytes(fd4.OP_CREASES, 100, 100, 0)
+    assert c >= 100 * 100 * 8
