@@ -43,3 +43,29 @@ def test_chains_join_at_shared_endpoints():
     s = np.array([[0, 0, 1, 0], [1, 0, 2, 1], [5, 5, 6, 5], [2, 1, 3, 1]], dtype=np.float64)
     groups = sorted(sorted(g.tolist()) for g in creases.chains(s))
     assert groups == [[0, 1, 3], [2]]
+
+
+def test_replayed_centre_lines_lie_on_the_rendered_vessels():
+    """The ground truth of the evaluation: the generator's centre lines, replayed
+    from its seed, run through the dark vessels it rendered (noise-free tree:
+    the centre of every piece of radius >= 2 is at least 0.3 below the local
+    background)."""
+    from paper_1611_06906_gb300 import synth
+    w, h = 200, 160
+    img = synth.vessel_tree(77, w, h, depth=4, r0=4.0, noise=0.0).astype(np.float64)
+    segs = synth.vessel_tree_centrelines(77, w, h, depth=4, r0=4.0, noise=0.0)
+    assert len(segs) == 3 * (2 ** 4 - 1)
+    checked = 0
+    for ax, ay, bx, by, rad in segs:
+        mx, my = 0.5 * (ax + bx), 0.5 * (ay + by)
+        x, y = int(round(mx)), int(round(my))
+        if rad < 2.0 or not (8 <= x < w - 8 and 8 <= y < h - 8):
+            continue
+        nx, ny = -(by - ay), bx - ax  # normal of the piece
+        n = math.hypot(nx, ny)
+        ox, oy = int(round(mx + 3 * rad * nx / n)), int(round(my + 3 * rad * ny / n))
+        if not (0 <= ox < w and 0 <= oy < h):
+            continue
+        assert img[oy, ox] - img[y, x] > 0.3
+        checked += 1
+    assert checked >= 5
