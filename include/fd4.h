@@ -407,8 +407,10 @@ int fd4_selftest_wait_timeout(void *d_ws, size_t ws_bytes, int *status, fd4_stre
  *   - h * pitch must not exceed FD4_NOALLOC_MAX_PIXELS, else
  *     FD4_ERR_WS_TOO_SMALL (the built-in scratch is too small for the image).
  *   - The first call on a device looks up the scratch array's device address
- *     (once per device, with that device current); make that first call before
- *     any stream capture.
+ *     (with that device current) and caches it for the device's context; make
+ *     that first call before any stream capture.  After a device reset
+ *     (cudaDeviceReset) the next call finds a new context and looks the
+ *     address up again, so it too should come before any capture.
  *   - All calls share the one scratch array, which keeps the last call's
  *     contents; nothing in it has to start at zero.  Calls whose work overlaps
  *     on the GPU (different streams, or different host threads on one device)

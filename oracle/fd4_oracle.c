@@ -15,6 +15,9 @@
  * Parity status per function (pins live in tests/test_oracle_*.py):
  *   or_gauss_kernels      pinned: moments, polynomial exactness, continuum limit
  *   or_derivatives        pinned: polynomials, direct 2-D sum, analytic ridge
+ *   or_mirror (border)    pinned: scipy.ndimage 'reflect' and numpy
+ *                         'symmetric' padding on random images (radius larger
+ *                         than the image included), a 4-pixel case by hand
  *   or_select_scales      pinned: width-scale relation, rotation invariance,
  *                         polarity, closed-form eigenvalues
  *   or_build_tensor       pinned: analytic eigen-structure, D:E_k = mu_k E_k,

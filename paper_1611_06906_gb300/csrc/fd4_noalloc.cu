@@ -8,6 +8,8 @@
 // asks for, so this entry point uses a scratch buffer that lives in the
 // library itself: a file-scope __device__ array that every GPU which loads
 // the library holds until the process exits.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "fd4_internal.h"
@@ -20,25 +22,68 @@ namespace {
 constexpr size_t kScratchBytes = fd4::kHeaderBytes + (size_t)FD4_NOALLOC_MAX_PIXELS * sizeof(float);
 static __device__ __align__(256) unsigned char g_fed_scratch[kScratchBytes];
 
+// In host code the array's name is only a host-side stand-in, so its device
+// address is looked up with cudaGetSymbolAddress, with the device current,
+// and cached per device together with the identity of the context it belongs
+// to.  A device reset (cudaDeviceReset) ends that context and the array moves
+// with the module into the next one: a call that finds another context looks
+// the address up again instead of passing a stale one to the kernel.
+struct ScratchAddr {
+    void *addr;
+    unsigned long long ctx_id;
+};
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
-void *g_scratch_addr[kMaxDevices] = {};
+ScratchAddr g_scratch[kMaxDevices] = {};
 
-// Device address of g_fed_scratch on the current device.  In host code the
-// array's name is only a host-side stand-in, so the address is looked up once
-// per device with that device current, and cached.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+template <class Fn>
+Fn driver_fn(const char *name)
+{
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        return nullptr;
+    return reinterpret_cast<Fn>(p);
+}
+
+// Identity of the calling thread's current context (false if none is current).
+bool current_ctx_id(unsigned long long *id)
+{
+    static const CtxGetCurrentFn get_current = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent");
+    static const CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId");
+    CUcontext ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_fed_scratch on the current device.
 int scratch_for_current_device(char **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return FD4_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return FD4_ERR_BAD_ARG;
+    unsigned long long id = 0;
+    const bool have_id = current_ctx_id(&id);
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_fed_scratch) != cudaSuccess || !p) return FD4_ERR_CUDA;
-        g_scratch_addr[dev] = p;
+    ScratchAddr &c = g_scratch[dev];
+    if (c.addr && have_id && c.ctx_id == id) {
+        *out = (char *)c.addr;
+        return FD4_OK;
     }
-    *out = (char *)g_scratch_addr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_fed_scratch) != cudaSuccess || !p) return FD4_ERR_CUDA;
+    // the look-up made the device's context current on this thread
+    if (current_ctx_id(&id)) {
+        c.addr = p;
+        c.ctx_id = id;
+    } else {
+        c.addr = nullptr;  // no context identity: look the address up on every call
+    }
+    *out = (char *)p;
     return FD4_OK;
 }
 

@@ -20,6 +20,8 @@ fundus data, which are not available; widths are Gaussian standard deviations):
   fundus_like         vessel_tree inside a circular field of view with radial
                       vignetting (1 - 0.4 rho^2)
   batch_uneven        64 fundus_like images with sides drawn from 512..2048
+  tree16              4096x4096 depth-8 tree, radii 12 -> 0.75 px, mixed polarity,
+                      noise sd 0.15 (16 of them form the full-size workload)
 """
 from __future__ import annotations
 
@@ -219,6 +221,12 @@ def fundus_like(seed: int, side: int, depth: int = 6, noise: float = 0.1):
     fov = 1.0 / (1.0 + np.exp((rho - 1.0) * side / 8.0))  # soft circular mask
     img = tree * vign * fov + noise * rng.normal(side * side).reshape(side, side)
     return img.astype(np.float32)
+
+
+def tree16(seed: int, side: int = 4096):
+    """One image of the full-size workload: a depth-8 tree with radii 12 -> 0.75 px,
+    each branch a ridge or a valley at random, noise sd 0.15, side x side."""
+    return vessel_tree(seed, side, side, depth=8, r0=12.0, r1=0.75, noise=0.15, polarity_mix=True)
 
 
 def batch_sides(seed: int = 3000, count: int = 64, lo: int = 512, hi: int = 2048):

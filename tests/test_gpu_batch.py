@@ -48,15 +48,24 @@ def test_batched_matches_oracle(oracle):
     imgs = _images()
     ins, outs, idx, lst = _batch(imgs)
     fd4.filter_batched(lst, SIGMAS, T, M, N, fd4.params(mode=fd4.VALLEY))
+    import torch
     tau, _, _ = oracle.fed_taus(T, M, 0.05, n=N)
+    refs = {}
     for k in (0, 2, 3):
         im = imgs[k]
         w = im.shape[1]
         ref, ridx = oracle.filter_image(im, SIGMAS, tau, M, mode=oracle.VALLEY)
         agree = float((idx[k][:, :w].cpu().numpy() == ridx).mean())
         assert agree >= 0.99
-        if agree == 1.0:
-            assert np.abs(outs[k][:, :w].cpu().numpy() - ref).max() <= 1e-4
+        refs[k] = ref
+        # where FP32 and FP64 pick different scales at near-ties the outputs
+        # legitimately differ there: the batch is filtered again with the
+        # oracle's scale image given, and every output pixel is compared
+        idx[k][:, :w] = torch.from_numpy(ridx).cuda()
+    fd4.filter_batched(lst, SIGMAS, T, M, N, fd4.params(mode=fd4.VALLEY), sigma_given=True)
+    for k, ref in refs.items():
+        w = imgs[k].shape[1]
+        assert np.abs(outs[k][:, :w].cpu().numpy() - ref).max() <= 1e-4
 
 
 def test_graph_replays_the_batched_filter():

@@ -72,22 +72,50 @@ def _batch(imgs):
     return ins, outs, idx, fd4.image_list(ins, [im.shape[1] for im in imgs], outs, idx)
 
 
-@pytest.mark.parametrize("reselect", [0, 1])
-def test_filter_matches_oracle(oracle, reselect):
+def test_filter_matches_oracle(oracle):
+    import torch
     imgs = _images()
     ins, outs, idx, lst = _batch(imgs)
-    prm = fd4.params(mode=fd4.VALLEY, postprocess_scales=1, theta=THETA, reselect_each_cycle=reselect)
+    prm = fd4.params(mode=fd4.VALLEY, postprocess_scales=1, theta=THETA)
     fd4.filter_batched(lst, SIGMAS, T, M, N, prm)
     tau, _, _ = oracle.fed_taus(T, M, 0.05, n=N)
+    refs = {}
     for k in (0, 2, 3):
         im = imgs[k]
         w = im.shape[1]
-        ref, ridx = oracle.filter_image(im, SIGMAS, tau, M, mode=oracle.VALLEY, reselect=bool(reselect),
-                                        postprocess=True, theta=THETA)
+        ref, ridx = oracle.filter_image(im, SIGMAS, tau, M, mode=oracle.VALLEY, postprocess=True, theta=THETA)
         agree = float((idx[k][:, :w].cpu().numpy() == ridx).mean())
         assert agree >= 0.99
-        if agree == 1.0:
-            assert np.abs(outs[k][:, :w].cpu().numpy() - ref).max() <= 1e-4
+        refs[k] = ref
+        idx[k][:, :w] = torch.from_numpy(ridx).cuda()
+    # the cycles again from the oracle's post-processed scale images: every
+    # output pixel is compared, also where a near-tie moved a scale
+    fd4.filter_batched(lst, SIGMAS, T, M, N, prm, sigma_given=True)
+    for k, ref in refs.items():
+        w = imgs[k].shape[1]
+        assert np.abs(outs[k][:, :w].cpu().numpy() - ref).max() <= 1e-4
+
+
+# Re-selection with post-processing cannot be given the oracle's scale images;
+# these inputs (chosen with the oracle alone) have every selected scale ahead
+# of its runner-up by at least 3e-4 relative at every re-selection, so the
+# scale images must agree exactly and u within the tolerance.
+RESEL_CASES = [(4204, 53, 37), (4218, 53, 37), (4236, 53, 37), (4248, 64, 80)]
+
+
+def test_filter_reselect_matches_oracle(oracle, selection_margin):
+    imgs = [synth.vessel_tree(s, w, h, depth=4, r0=4.0) for s, h, w in RESEL_CASES]
+    ins, outs, idx, lst = _batch(imgs)
+    prm = fd4.params(mode=fd4.VALLEY, postprocess_scales=1, theta=THETA, reselect_each_cycle=1)
+    fd4.filter_batched(lst, SIGMAS, T, M, N, prm)
+    tau, _, _ = oracle.fed_taus(T, M, 0.05, n=N)
+    for k, im in enumerate(imgs):
+        w = im.shape[1]
+        assert selection_margin(im, SIGMAS, tau, M, oracle.VALLEY) >= 3e-4
+        ref, ridx = oracle.filter_image(im, SIGMAS, tau, M, mode=oracle.VALLEY, reselect=True,
+                                        postprocess=True, theta=THETA)
+        assert np.array_equal(idx[k][:, :w].cpu().numpy(), ridx)
+        assert np.abs(outs[k][:, :w].cpu().numpy() - ref).max() <= 1e-4
 
 
 @pytest.mark.parametrize("reselect", [0, 1])

@@ -27,20 +27,31 @@ def _batch(imgs):
     return ins, outs, idx, fd4.image_list(ins, [im.shape[1] for im in imgs], outs, idx)
 
 
+# Inputs of the parity test below.  The re-selecting schedule cannot be given
+# the oracle's scale images (each cycle selects on its own u^k), so where two
+# scales are equally good within FP32 rounding the GPU and the oracle may go
+# different, equally valid ways.  These images were chosen (with the oracle
+# alone) so that at every re-selection the best scale leads the runner-up by
+# at least 3e-4 relative at every pixel: sigma* must then agree exactly and
+# u within the tolerance.  The test checks that precondition itself.
+RESEL_CASES = [(4204, 53, 37), (4218, 53, 37), (4236, 53, 37), (4248, 64, 80)]
+MIN_LEAD = 3e-4
+
+
 @pytest.mark.parametrize("mode", [fd4.VALLEY, fd4.BOTH])
-def test_reselect_matches_oracle(oracle, mode):
-    imgs = _images()
+def test_reselect_matches_oracle(oracle, selection_margin, mode):
+    imgs = [synth.vessel_tree(s, w, h, depth=4, r0=4.0) for s, h, w in RESEL_CASES]
+    if mode == fd4.BOTH:
+        imgs = imgs[:3]
     ins, outs, idx, lst = _batch(imgs)
     fd4.filter_batched(lst, SIGMAS, T, M, N, fd4.params(mode=mode, reselect_each_cycle=1))
     tau, _, _ = oracle.fed_taus(T, M, 0.05, n=N)
-    for k in (0, 2, 3):
-        im = imgs[k]
+    for k, im in enumerate(imgs):
         w = im.shape[1]
+        assert selection_margin(im, SIGMAS, tau, M, mode) >= MIN_LEAD
         ref, ridx = oracle.filter_image(im, SIGMAS, tau, M, mode=mode, reselect=True)
-        agree = float((idx[k][:, :w].cpu().numpy() == ridx).mean())
-        assert agree >= 0.99
-        if agree == 1.0:
-            assert np.abs(outs[k][:, :w].cpu().numpy() - ref).max() <= 1e-4
+        assert np.array_equal(idx[k][:, :w].cpu().numpy(), ridx)
+        assert np.abs(outs[k][:, :w].cpu().numpy() - ref).max() <= 1e-4
 
 
 def test_reselect_batched_graph_and_two_streams_equal_per_image():

@@ -103,3 +103,71 @@ def test_analytic_gaussian_ridge(oracle, w_r, sigma):
     assert np.abs(uxx[inner, col]).max() < 1e-12
     assert np.abs(uxy[inner, col]).max() < 1e-12
     assert abs(uyy[c, col] + w_r / s ** 3) < 1e-2 * w_r / s ** 3
+
+
+# --- the border extension of every Gaussian sum ------------------------------
+# Sec. 3.1 only writes u_sigma = u * G_sigma; the oracle extends the image by
+# the half-sample symmetric fold (u[-1-i] = u[i], u[n+i] = u[n-1-i], period 2n
+# for any offset).  These pins check that fold against two library routines
+# that implement it independently and against values worked out by hand, so
+# that a whole-sample fold (u[-1] = u[1]) or a wrong period fails.
+
+def _separable_lib(u, wx, wy, mode):
+    import scipy.ndimage as ndi
+    a = ndi.correlate1d(u, wx, axis=1, mode=mode)
+    return ndi.correlate1d(a, wy, axis=0, mode=mode)
+
+
+def _direct_padded(u, wx, wy, r):
+    """Direct 2-D correlation on numpy's 'symmetric' padding (edge value repeated)."""
+    p = np.pad(u, r, mode="symmetric")
+    h, w = u.shape
+    out = np.empty((h, w))
+    k2 = wy[:, None] * wx[None, :]
+    for y in range(h):
+        for x in range(w):
+            out[y, x] = (k2 * p[y:y + 2 * r + 1, x:x + 2 * r + 1]).sum()
+    return out
+
+
+@pytest.mark.parametrize("shape,sigma", [((5, 7), 2.0), ((13, 17), 1.5), ((4, 4), 1.25), ((3, 9), 3.0)])
+def test_border_fold_matches_library_reflect(oracle, shape, sigma):
+    """All five derivatives on random images equal scipy.ndimage's 'reflect'
+    mode (d c b a | a b c d) and numpy's 'symmetric' padding, including radii
+    larger than the image (the fold repeats with period 2n)."""
+    rng = np.random.default_rng(shape[0] * 100 + shape[1])
+    u = rng.random(shape)
+    w0, w1, w2 = oracle.gauss_kernels(sigma)
+    r = oracle.gauss_radius(sigma)
+    pairs = [(w1, w0), (w0, w1), (w2, w0), (w1, w1), (w0, w2)]
+    outs = oracle.derivatives(u, sigma)
+    for o, (wx, wy) in zip(outs, pairs):
+        assert np.abs(o - _separable_lib(u, wx, wy, "reflect")).max() < 1e-14
+        assert np.abs(o - _direct_padded(u, wx, wy, r)).max() < 1e-14
+    # the whole-sample fold (scipy's 'mirror': c b | a b c) is a different
+    # extension and must not match at the border
+    worst = max(np.abs(o - _separable_lib(u, wx, wy, "mirror")).max() for o, (wx, wy) in zip(outs, pairs))
+    assert worst > 1e-3
+
+
+def test_border_fold_hand_worked_4_pixels(oracle):
+    """sigma = 1/4 gives radius 1, where the normalised kernels are exactly the
+    central differences (-1/2, 0, 1/2) and (1, -2, 1).  On rows [0, 1, 3, 7]
+    (constant down the columns) the half-sample fold u[-1] = u[0], u[4] = u[3]
+    gives u_x = [1/2, 3/2, 3, 2] and u_xx = [1, 1, 2, -4]; a whole-sample fold
+    would give u_x[0] = 0, u_xx[0] = 2."""
+    w0, w1, w2 = oracle.gauss_kernels(0.25)
+    assert np.allclose(w1, [-0.5, 0.0, 0.5], atol=1e-15)
+    assert np.allclose(w2, [1.0, -2.0, 1.0], atol=1e-12)
+    u = np.tile(np.array([0.0, 1.0, 3.0, 7.0]), (4, 1))
+    ux, uy, uxx, uxy, uyy = oracle.derivatives(u, 0.25)
+    for row in range(4):
+        assert np.allclose(ux[row], [0.5, 1.5, 3.0, 2.0], atol=1e-12)
+        assert np.allclose(uxx[row], [1.0, 1.0, 2.0, -4.0], atol=1e-11)
+    assert np.abs(uy).max() < 1e-15 and np.abs(uxy).max() < 1e-15 and np.abs(uyy).max() < 1e-11
+    # the same along y: rows y = 0..3 hold 0, 1, 3, 7 (a 4 x 3 image)
+    v = np.tile(np.array([[0.0], [1.0], [3.0], [7.0]]), (1, 3))
+    vx, vy, vxx, vxy, vyy = oracle.derivatives(v, 0.25)
+    for col in range(3):
+        assert np.allclose(vy[:, col], [0.5, 1.5, 3.0, 2.0], atol=1e-12)
+        assert np.allclose(vyy[:, col], [1.0, 1.0, 2.0, -4.0], atol=1e-11)
