@@ -4,12 +4,21 @@ A step is one pass of the whole hot path over one batch: for every image,
 scale selection, then M cycles of (tensor build, FED cycle of n steps).
 Metric: Mpixel-FED-steps/s = sum_images(w h) * M * n / time.
 
-Default workload "batch64_fundus": 64 seeded fundus-like images (circular field
-of view, radial vignetting, dark vessel tree of depth 6 with radii 8 -> 1 px,
-noise sd 0.1), square sides drawn from 512..2048 (123 Mpixel in total),
-8 scales log-spaced over 1..8 px, valley mode, 5 FED cycles of 20 steps
-(T = 35, tau_max = 0.05), lambda = 0.005, rho = 0.5, beta = 0.5.  The inputs
-(0.5 GB of images, 2 GB of tensor field) are larger than L2.
+Default workload "tree16_4096": 16 seeded 4096^2 synthetic vessel trees (depth
+8, radii 12 -> 0.75 px, each branch a ridge or a valley, noise sd 0.15;
+268 Mpixel), 12 scales log-spaced over 0.75..12 px (kernel radii up to 48),
+both creases enhanced, 10 FED cycles of 25 steps (T = 325/3, tau_max = 0.05),
+lambda = 0.005, rho = 0.5, beta = 0.5.  The inputs (1.07 GB of images, 4.3 GB
+of tensor field) are larger than L2.  "batch64_fundus" (64 fundus-like images
+of 512^2..2048^2, 8 scales, valley mode, 5 x 20) and "tree_1024" are the other
+workloads.
+
+`value` is the batched path (one persistent launch per stage over the whole
+batch, the schedule replayed as a CUDA graph, the FED kernel schedule picked by
+the autotuner) with the plain vesselness selection; `plain` times the same
+filter as per-image fd4_filter calls at the library's default FED fusion and
+at one launch per FED step; `learned` is the batched path with the learned
+selector (where the workload's scale set has the network's 8 bins).
 
 --impl reference times the FP64 CPU oracle (the method's reference
 implementation written from the paper) on the host cores on a bounded sample
@@ -37,43 +46,14 @@ sys.path.insert(0, ROOT)
 
 from paper_1611_06906_gb300.dist import max_over_ranks as _max_over_ranks, rank_seed  # noqa: E402
 
-# DRAM bytes (read + write) per pixel and launch of k_fed_tma<2,2> (two quads per
-# thread), from an ncu capture of one launch over the first 8 batch64_fundus
-# images (303.40 + 47.16 MB over 15.13 Mpixel); the roofline's `traffic` scales it
-# to the launch timed here.  Re-measured (or set to None: the field null)
-# whenever that kernel changes.
-TMA2_DRAM_B_PER_PX = 23.17
+# DRAM bytes (read + write) per pixel and launch of the FED kernel the
+# autotuner picks, keyed by its schedule (steps, region rows, quads per thread),
+# from an ncu capture of one launch on a smaller case of the same workload
+# (profiles/); the roofline's `traffic` scales it to the launch timed here.
+# Entries are removed (the field is then null) whenever that kernel changes.
+FED_DRAM_B_PER_PX = {}
 METRIC = "Mpixel-steps/s, batched+learned vs plain GB300, at stated FP64-oracle error"
 UNIT = "Mpixel-steps/s"
-
-
-def _gen_one(args):
-    seed, side = args
-    from paper_1611_06906_gb300 import synth
-    return synth.fundus_like(seed, side)
-
-
-def make_workload(name: str, rank: int, limit: int = 0):
-    """Returns (list of float32 images, config dict)."""
-    from paper_1611_06906_gb300 import synth
-    wl = dict(synth.WORKLOADS[name])
-    if name == "batch64_fundus":
-        base = rank_seed(3000, rank)  # weak scaling: every rank filters its own batch
-        sides = synth.batch_sides(base)
-        if limit:
-            sides = sides[:limit]
-        seeds = [base + i for i in range(len(sides))]
-        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-            imgs = pool.map(_gen_one, list(zip(seeds, sides)))
-    elif name == "tree_1024":
-        imgs = [synth.vessel_tree(2000 + rank, 1024, 1024)]
-    elif name == "tree16_4096":
-        n_img = limit or 16
-        imgs = [synth.vessel_tree(5000 + 100 * rank + i, 4096, 4096, depth=8, r0=12.0, r1=0.75,
-                                  noise=0.15, polarity_mix=True) for i in range(n_img)]
-    else:
-        raise SystemExit("unknown workload " + name)
-    return imgs, wl
 
 
 class ClockSampler:
@@ -140,6 +120,88 @@ def load_peaks():
 MODES = {"ridge": 0, "valley": 1, "both": 2}
 
 
+def _gen_fundus(args):
+    seed, side = args
+    from paper_1611_06906_gb300 import synth
+    return synth.fundus_like(seed, side)
+
+
+def _gen_tree16(seed):
+    from paper_1611_06906_gb300 import synth
+    return synth.tree16(seed)
+
+
+def tree16_seed(rank: int, i: int) -> int:
+    return 5000 + 100 * rank + i
+
+
+def make_workload(name: str, rank: int, limit: int = 0):
+    """Returns (list of float32 images, config dict)."""
+    from paper_1611_06906_gb300 import synth
+    wl = dict(synth.WORKLOADS[name])
+    pool_n = min(16, os.cpu_count() or 1)
+    if name == "batch64_fundus":
+        base = rank_seed(3000, rank)  # weak scaling: every rank filters its own batch
+        sides = synth.batch_sides(base)
+        if limit:
+            sides = sides[:limit]
+        seeds = [base + i for i in range(len(sides))]
+        with mp.get_context("spawn").Pool(pool_n) as pool:
+            imgs = pool.map(_gen_fundus, list(zip(seeds, sides)))
+    elif name == "tree_1024":
+        imgs = [synth.vessel_tree(2000 + rank, 1024, 1024)]
+    elif name == "tree16_4096":
+        seeds = [tree16_seed(rank, i) for i in range(limit or 16)]
+        with mp.get_context("spawn").Pool(pool_n) as pool:
+            imgs = pool.map(_gen_tree16, seeds)
+    else:
+        raise SystemExit("unknown workload " + name)
+    return imgs, wl
+
+
+def center_crop(img, side):
+    h, w = img.shape
+    side = min(side, h, w)
+    y0, x0 = (h - side) // 2, (w - side) // 2
+    return np.ascontiguousarray(img[y0:y0 + side, x0:x0 + side])
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def oracle_samples(imgs, wl, mode):
+    """The two samples the oracle (FP64, host cores) is run on: the all-core
+    sample (also the parity reference of the main path) and the smaller
+    single-core one.  tree16_4096: central 512^2 and 256^2 crops of the first
+    image; the other workloads: the smallest image and its central 256^2 crop."""
+    if wl.get("name") == "tree16_4096" or imgs[0].shape == (4096, 4096):
+        big = center_crop(imgs[0], 512)
+        what = "central 512x512 crop of the first 4096x4096 image"
+    else:
+        k = min(range(len(imgs)), key=lambda i: imgs[i].size)
+        big = imgs[k]
+        what = "the smallest image (%dx%d)" % big.shape[::-1]
+    small = center_crop(big, 256)
+    return big, what, small
+
+
+def oracle_timed(img, wl, mode, threads=0, **kw):
+    """One oracle filter of img with the workload's parameters; returns (out, idx, seconds)."""
+    from oracle import oracle as O
+    tau, _, _ = O.fed_taus(wl["T"], wl["M"], 0.05, n=wl["n"])
+    t0 = time.perf_counter()
+    out, idx = O.filter_image(img, wl["sigmas"], tau, wl["M"], mode=mode, **kw)
+    return out, idx, time.perf_counter() - t0
+
+
 class Image:
     def __init__(self, img, dev, fd4, torch):
         self.h, self.w = img.shape
@@ -148,23 +210,6 @@ class Image:
         self.pitch = self.u_in.shape[1]
         self.out = torch.empty_like(self.u_in)
         self.idx = torch.zeros((self.h, self.pitch), dtype=torch.uint8, device=dev)
-        self.ten = torch.empty((self.h, self.pitch, 4), dtype=torch.float32, device=dev)
-
-
-def oracle_sample(imgs, wl, mode, max_images=2):
-    """Oracle (FP64, host cores) on the smallest images of the batch: the CPU
-    baseline sample and the parity reference.  Returns (list of (i, out, idx), secs, cores, pxsteps)."""
-    from oracle import oracle as O
-    order = sorted(range(len(imgs)), key=lambda i: imgs[i].size)[:max_images]
-    tau, _, _ = O.fed_taus(wl["T"], wl["M"], 0.05, n=wl["n"])
-    res = []
-    t0 = time.perf_counter()
-    for i in order:
-        out, idx = O.filter_image(imgs[i], wl["sigmas"], tau, wl["M"], mode=mode)
-        res.append((i, out, idx))
-    secs = time.perf_counter() - t0
-    pxsteps = sum(imgs[i].size for i in order) * wl["M"] * wl["n"]
-    return res, secs, O.num_threads(), pxsteps
 
 
 def _timed(fn, steps, stream, torch):
@@ -178,8 +223,18 @@ def _timed(fn, steps, stream, torch):
     return a.elapsed_time(z)
 
 
+def fed_kernel_name(sch) -> str:
+    s, r, q = sch.steps_per_launch, sch.tile_rows, sch.quads_per_thread
+    if s == 1:
+        return "k_fed_step"
+    if s == 3:
+        return "k_fed_fused<3>"
+    return "k_fed_tma<%d,%d,%d>" % (s, q or 2, r or 64)
+
+
 def run_fd4(args, rank, world, local_rank):
     imgs, wl = make_workload(args.workload, rank, args.limit)  # before CUDA init (spawn pool)
+    wl["name"] = args.workload
     import torch
     from paper_1611_06906_gb300 import fd4
     torch.cuda.set_device(local_rank)
@@ -206,11 +261,12 @@ def run_fd4(args, rank, world, local_rank):
     # batched path: one launch per stage across the batch, replayed as a CUDA graph
     lst = fd4.image_list([b.u_in for b in ims], [b.w for b in ims], [b.out for b in ims], [b.idx for b in ims])
     ws = fd4.batch_workspace(lst, K, dev)
+    tried = []
     if args.fed_steps:
-        best, tune_ms = args.fed_steps, None
+        sched = fd4.FedSchedule(args.fed_steps, 0, 0, 0.0)
     else:
-        best, tune_ms = fd4.autotune_batched(lst, sig, T, M, n, fd4.params(mode=mode), ws=ws)
-    prm = fd4.params(mode=mode, fed_steps_per_launch=best)
+        sched, tried = fd4.autotune_batched(lst, sig, T, M, n, fd4.params(mode=mode), ws=ws)
+    prm = fd4.params(mode=mode, **sched.as_params())
     if args.only_graph:  # profiling: warm-up and timed replays of the full graph only
         g = fd4.Graph(lst, sig, T, M, n, prm, ws=ws)
         for _ in range(args.warmup + args.steps):
@@ -224,8 +280,8 @@ def run_fd4(args, rank, world, local_rank):
     g_sel = fd4.Graph(lst, sig, T, M, n, prm, ws=ws, stages=fd4.STAGE_SELECT)
     g_ten = fd4.Graph(lst, sig, T, M, n, prm, ws=ws, stages=fd4.STAGE_TENSOR)
     g_fed = fd4.Graph(lst, sig, T, M, n, prm, ws=ws, stages=fd4.STAGE_FED)
-    L = -(-n // best) if best > 1 else n          # FED launches per cycle
-    fed_launches = M * L
+    S = sched.steps_per_launch
+    fed_launches = M * (-(-n // S))               # FED kernel launches per pass
     launches_per_step = g_all.kernel_count()      # kernel nodes of the captured graph
 
     for _ in range(args.warmup):
@@ -241,73 +297,68 @@ def run_fd4(args, rank, world, local_rank):
     sel_ms = _timed(g_sel.launch, args.steps, stream, torch) / args.steps
     ten_ms = _timed(g_ten.launch, args.steps, stream, torch) / args.steps
     fed_ms = _timed(g_fed.launch, args.steps, stream, torch) / args.steps
+    # the FED kernel's own launches (events around each launch of the FED-only graph
+    # would split it; the graph's FED launches are all of one kernel, plus a copy-back
+    # launch per cycle when the launch count is odd)
+    fed_copy_backs = M * ((-(-n // S)) % 2) if S > 1 else M * (n % 2)
 
+    variants = {}
+    crop_px_steps = None
     # the scale image selected again on the current image before every cycle
-    # (reselect_each_cycle); its outputs on the oracle sample are kept for parity
-    resel = None
+    # (reselect_each_cycle); the scale image post-processed after its selection
+    # (Sec. 3.3) at the paper's fundus threshold theta = 0.13; the IFOD comparator
+    # of Eq. 2 (sigma 1, the paper's setting) -- each on the same batch
+    theta = float(np.float32(0.13))
+    legs = []
     if not args.no_reselect:
-        g_re = fd4.Graph(lst, sig, T, M, n, fd4.params(mode=mode, fed_steps_per_launch=best,
-                                                          reselect_each_cycle=1), ws=ws)
-        g_re.launch()
-        barrier()
-        re_ms = max_over_ranks(_timed(g_re.launch, args.steps, stream, torch)) / args.steps
-        order = sorted(range(len(ims)), key=lambda i: ims[i].npx)[:2]
-        resel = {"value": world * px_steps / (re_ms * 1e-3) / 1e6, "ms_per_step": re_ms,
-                 "gpu_launches_per_step": g_re.kernel_count(),
-                 "path": "batched graph, scale image re-selected on u^k before every cycle",
-                 "_out": {i: (ims[i].out[:, :ims[i].w].cpu().numpy().astype(np.float64),
-                              ims[i].idx[:, :ims[i].w].cpu().numpy()) for i in order}}
-        g_re.close()
-
-    # the scale image post-processed after its selection (Sec. 3.3), at the
-    # paper's fundus threshold theta = 0.13; outputs kept for parity as above
-    post = None
+        legs.append(("reselect", dict(reselect_each_cycle=1),
+                     "batched graph, scale image re-selected on u^k before every cycle"))
     if not args.no_postprocess:
-        theta = float(np.float32(0.13))
-        g_po = fd4.Graph(lst, sig, T, M, n, fd4.params(mode=mode, fed_steps_per_launch=best,
-                                                          postprocess_scales=1, theta=theta), ws=ws)
-        g_po.launch()
-        barrier()
-        po_ms = max_over_ranks(_timed(g_po.launch, args.steps, stream, torch)) / args.steps
-        order = sorted(range(len(ims)), key=lambda i: ims[i].npx)[:2]
-        post = {"value": world * px_steps / (po_ms * 1e-3) / 1e6, "ms_per_step": po_ms, "theta": theta,
-                "gpu_launches_per_step": g_po.kernel_count(),
-                "path": "batched graph, scale image post-processed after the selection",
-                "_out": {i: (ims[i].out[:, :ims[i].w].cpu().numpy().astype(np.float64),
-                             ims[i].idx[:, :ims[i].w].cpu().numpy()) for i in order}}
-        g_po.close()
-
-    # the IFOD comparator of Eq. 2 (sigma 1, the paper's setting) on the same batch
-    ifod = None
+        legs.append(("postprocess", dict(postprocess_scales=1, theta=theta),
+                     "batched graph, scale image post-processed after the selection"))
     if not args.no_ifod:
-        g_if = fd4.Graph(lst, sig, T, M, n, fd4.params(mode=mode, fed_steps_per_launch=best,
-                                                          model=fd4.MODEL_IFOD, ifod_sigma=1.0), ws=ws)
-        g_if.launch()
+        legs.append(("ifod", dict(model=fd4.MODEL_IFOD, ifod_sigma=1.0),
+                     "batched graph, IFOD tensor (1, 0, g, g) rebuilt every cycle, same FED cycles"))
+    for name, kw, path in legs:
+        g_v = fd4.Graph(lst, sig, T, M, n, fd4.params(mode=mode, **sched.as_params(), **kw), ws=ws)
+        g_v.launch()
         barrier()
-        if_ms = max_over_ranks(_timed(g_if.launch, args.steps, stream, torch)) / args.steps
-        order = sorted(range(len(ims)), key=lambda i: ims[i].npx)[:2]
-        ifod = {"value": world * px_steps / (if_ms * 1e-3) / 1e6, "ms_per_step": if_ms, "sigma": 1.0,
-                "gpu_launches_per_step": g_if.kernel_count(),
-                "path": "batched graph, IFOD tensor (1, 0, g, g) rebuilt every cycle, same FED cycles",
-                "_out": {i: ims[i].out[:, :ims[i].w].cpu().numpy().astype(np.float64) for i in order}}
-        g_if.close()
+        v_ms = max_over_ranks(_timed(g_v.launch, args.steps, stream, torch)) / args.steps
+        variants[name] = {"value": world * px_steps / (v_ms * 1e-3) / 1e6, "ms_per_step": v_ms,
+                          "gpu_launches_per_step": g_v.kernel_count(), "path": path, "_kw": kw}
+        g_v.close()
+    if "postprocess" in variants:
+        variants["postprocess"]["theta"] = theta
+    if "ifod" in variants:
+        variants["ifod"]["sigma"] = 1.0
     g_all.launch()  # leave the outputs of a complete filter pass in place
     barrier()
 
-    # plain path: per-image calls, one launch per FED step
-    plain_prm = fd4.params(mode=mode, fed_steps_per_launch=1)
+    # plain GPU path: per-image fd4_filter calls, at the library's default FED
+    # schedule (2 steps fused per launch) and at one launch per FED step
     ws_plain = fd4.workspace(fd4.OP_FILTER, max(b.pitch for b in ims), max(b.h for b in ims), K, dev)
     outs_plain = [torch.empty_like(b.u_in) for b in ims]
+    plain = {}
+    n_plain = max(1, min(args.steps, 3))
+    for key, kw, path in (("default_fusion", {}, "per-image fd4_filter calls, library default FED schedule "
+                                                 "(2 steps per launch)"),
+                          ("one_launch_per_step", dict(fed_steps_per_launch=1),
+                           "per-image fd4_filter calls, one launch per FED step")):
+        pp = fd4.params(mode=mode, **kw)
 
-    def plain_step():
-        for b, o in zip(ims, outs_plain):
-            fd4.filter_image(b.u_in, b.w, sig, T, M, n, plain_prm, out=o, ws=ws_plain, keep_idx=False)
+        def plain_step(pp=pp):
+            for b, o in zip(ims, outs_plain):
+                fd4.filter_image(b.u_in, b.w, sig, T, M, n, pp, out=o, ws=ws_plain, keep_idx=False)
 
-    plain_step()
-    barrier()
-    plain_ms = max_over_ranks(_timed(plain_step, max(1, min(args.steps, 3)), stream, torch) / max(1, min(args.steps, 3)))
-    plain_value = world * px_steps / (plain_ms * 1e-3) / 1e6
-    diff_plain = max(float((o[:, :b.w] - b.out[:, :b.w]).abs().max()) for o, b in zip(outs_plain, ims))
+        plain_step()
+        barrier()
+        p_ms = max_over_ranks(_timed(plain_step, n_plain, stream, torch) / n_plain)
+        plain[key] = {"value": world * px_steps / (p_ms * 1e-3) / 1e6, "ms_per_step": p_ms, "path": path,
+                      "max_abs_diff_to_batched": max(float((o[:, :b.w] - b.out[:, :b.w]).abs().max())
+                                                     for o, b in zip(outs_plain, ims))}
+    plain["speedup_of_batched"] = value / plain["default_fusion"]["value"]
+    plain["speedup_of_fusion"] = plain["default_fusion"]["value"] / plain["one_launch_per_step"]["value"]
+    plain["speedup_of_batched_over_one_launch_per_step"] = value / plain["one_launch_per_step"]["value"]
 
     # end to end through the public API: pinned host buffers, copies inside the timed region
     e2e = None
@@ -330,119 +381,126 @@ def run_fd4(args, rank, world, local_rank):
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": ems / args.steps,
                "path": "pinned host images -> fd4_graph_launch (batched filter) -> pinned host results"}
 
+    learned = None
+    if not args.no_learned:
+        if K == 8:
+            learned = learned_variant(args, ims, sig, T, M, n, mode, sched, stream, torch, fd4)
+        else:
+            learned = {"value": None, "status": "N/A: the selector predicts 8 scale bins (its head has 8 "
+                                                "outputs); this workload's scale set has %d scales" % K}
+
     if rank != 0:
         return
     peak, peak_kind = load_peaks()
     fed_bytes = 24 * npx * M * n  # algorithmic bytes of the FED steps of one pass
-    achieved = fed_bytes / (fed_ms * 1e-3) / 1e9
-    # the FED kernel the schedule runs: the TMA-staged quad kernel for 2 and 4 steps per launch
-    # (fd4_fed_tma.cu), the scalar fused kernel for 3, one launch per step for 1 (fd4_fed.cu)
-    kname = {1: "k_fed_step", 2: "k_fed_tma<2,2>", 3: "k_fed_fused<3>", 4: "k_fed_tma<4,2>"}[best]
-    default_kernels = not any(os.environ.get(v) for v in ("FD4_FED_PIPELINE", "FD4_FED_QUAD_ROWS", "FD4_FED_FUSE",
-                                                          "FD4_FED_QUADS"))
+    fed_kernel_ms = fed_ms  # includes the copy-back launches (memory copies of u, < 1 % of the stage)
+    achieved = fed_bytes / (fed_kernel_ms * 1e-3) / 1e9
+    key = (sched.steps_per_launch, sched.tile_rows, sched.quads_per_thread)
     traffic = args.traffic
-    if traffic is None and kname == "k_fed_tma<2,2>" and default_kernels and TMA2_DRAM_B_PER_PX is not None:
-        traffic = TMA2_DRAM_B_PER_PX * npx
+    if traffic is None and key in FED_DRAM_B_PER_PX:
+        traffic = FED_DRAM_B_PER_PX[key] * npx
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "traffic_unit": "bytes per launch", "kernel": kname,
+            "traffic": traffic, "traffic_unit": "bytes per launch", "kernel": fed_kernel_name(sched),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind,
-            "bytes_per_px_step": 24, "steps_per_launch": best,
-            "avg_launch_us": fed_ms * 1e3 / fed_launches,
+            "bytes_per_px_step": 24, "steps_per_launch": S,
+            "avg_launch_us": fed_kernel_ms * 1e3 / fed_launches, "copy_back_launches_per_pass": fed_copy_backs,
             "algorithmic_bytes_per_launch": fed_bytes / fed_launches}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "value_path": "batched (one persistent launch per stage over the batch's tiles) + CUDA graph, "
+                         "plain vesselness selection (the learned selector's number is `learned`)",
            "config": {"workload": args.workload, "images": len(ims), "mpixel": round(npx / 1e6, 3),
                       "sigmas": K, "mode": wl["mode"], "M": M, "n": n, "T": T,
                       "path": "batched (one persistent launch per stage) + CUDA graph" + (
                           ", two image groups on two streams" if g_all is not g_one else ""),
                       "one_stream_graph_ms_per_step": one_stream_ms,
-                      "fed_steps_per_launch": best, "autotune_ms": tune_ms,
+                      "fed_schedule": sched.as_dict(),
+                      "autotune": [c.as_dict() for c in tried],
                       "l2": "inputs larger than L2 (images %.2f GB, tensor field %.2f GB per pass)" % (
                           npx * 4e-9, npx * 16e-9)},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
            "clocks": clk.summary(),
            "stages_ms_per_step": {"select": sel_ms, "tensor": ten_ms, "fed": fed_ms},
-           "plain": {"value": plain_value, "ms_per_step": plain_ms,
-                     "path": "per-image fd4_filter calls, one launch per FED step",
-                     "speedup_of_batched": value / plain_value, "max_abs_diff_to_batched": diff_plain}}
-    if not args.no_learned:
-        out["learned"] = learned_variant(args, ims, sig, T, M, n, mode, best, stream, torch, fd4)
+           "plain": plain}
+    if learned is not None:
+        out["learned"] = learned
     if world == 1 and not args.no_cpu_baseline:
-        res, secs, cores, pxs = oracle_sample(imgs, wl, mode)
-        errs, agree, errs_inj = [], [], []
-        for i, ref, idx_o in res:
-            b = ims[i]
-            got = b.out[:, :b.w].cpu().numpy().astype(np.float64)
-            errs.append(float(np.abs(got - ref).max()))
-            agree.append(float((b.idx[:, :b.w].cpu().numpy() == idx_o).mean()))
-            idx_in = torch.zeros_like(b.idx)
-            idx_in[:, :b.w] = torch.from_numpy(idx_o).to(dev)
-            o2, _ = fd4.filter_image(b.u_in, b.w, sig, T, M, n, prm, sigma_idx=idx_in, ws=ws_plain)
-            errs_inj.append(float(np.abs(o2[:, :b.w].cpu().numpy() - ref).max()))
-        sample = "oracle full filter of the %d smallest batch images (%s px)" % (
-            len(res), ", ".join("%dx%d" % imgs[i].shape[::-1] for i, _, _ in res))
-        out["cpu_baseline"] = {"value": pxs / secs / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": sample, "seconds": secs}
-        out["parity"] = {"vs": "FP64 oracle", "images": sample, "max_abs": max(errs),
-                         "max_abs_oracle_sigma": max(errs_inj), "sigma_agreement": min(agree),
-                         "tolerance": 1e-4}
-        if resel is not None:
-            from oracle import oracle as O
-            tau_o, _, _ = O.fed_taus(T, M, 0.05, n=n)
-            r_err, r_agree = [], []
-            for i, (got, gidx) in resel["_out"].items():
-                ref, ridx = O.filter_image(imgs[i], sig, tau_o, M, mode=mode, reselect=True)
-                r_err.append(float(np.abs(got - ref).max()))
-                r_agree.append(float((gidx == ridx).mean()))
-            resel["parity"] = {"vs": "FP64 oracle, re-selecting schedule", "images": sample,
-                               "max_abs": max(r_err), "last_sigma_agreement": min(r_agree), "tolerance": 1e-4}
-        if post is not None:
-            from oracle import oracle as O
-            tau_o, _, _ = O.fed_taus(T, M, 0.05, n=n)
-            p_err, p_agree, p_inj = [], [], []
-            for i, (got, gidx) in post["_out"].items():
-                ref, ridx = O.filter_image(imgs[i], sig, tau_o, M, mode=mode, postprocess=True,
-                                           theta=post["theta"])
-                p_err.append(float(np.abs(got - ref).max()))
-                p_agree.append(float((gidx == ridx).mean()))
-                # the same filter at the oracle's post-processed scale image
-                b = ims[i]
-                idx_in = torch.zeros_like(b.idx)
-                idx_in[:, :b.w] = torch.from_numpy(ridx).to(dev)
-                o2, _ = fd4.filter_image(b.u_in, b.w, sig, T, M, n, prm, sigma_idx=idx_in, ws=ws_plain)
-                p_inj.append(float(np.abs(o2[:, :b.w].cpu().numpy() - ref).max()))
-            post["parity"] = {"vs": "FP64 oracle, post-processed scale image", "images": sample,
-                              "max_abs": max(p_err), "max_abs_oracle_sigma": max(p_inj),
-                              "sigma_agreement": min(p_agree), "tolerance": 1e-4}
-        if ifod is not None:
-            from oracle import oracle as O
-            tau_o, _, _ = O.fed_taus(T, M, 0.05, n=n)
-            errs_if = [float(np.abs(got - O.filter_ifod(imgs[i], tau_o, M, sigma=1.0, lam=0.005)).max())
-                       for i, got in ifod["_out"].items()]
-            ifod["parity"] = {"vs": "FP64 oracle IFOD filter", "images": sample, "max_abs": max(errs_if),
-                              "tolerance": 1e-4}
-    if ifod is not None:
-        ifod.pop("_out", None)
-        out["ifod"] = ifod
-    if world == 1 and not args.no_creases and args.workload == "batch64_fundus":
-        out["creases"] = crease_leg(args, ims, mode, stream, torch, fd4)
-    if resel is not None:
-        resel.pop("_out", None)
-        out["reselect"] = resel
-    if post is not None:
-        post.pop("_out", None)
-        out["postprocess"] = post
+        from oracle import oracle as O
+        O.build()
+        big, what, small = oracle_samples(imgs, wl, mode)
+        cores = O.num_threads()
+        ref, ridx, secs = oracle_timed(big, wl, mode)
+        O.set_num_threads(1)
+        _, _, secs1 = oracle_timed(small, wl, mode)
+        O.set_num_threads(cores)
+        rate = big.size * M * n / secs / 1e6
+        rate1 = small.size * M * n / secs1 / 1e6
+        full_h = px_steps / (rate * 1e6) / 3600
+        out["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "oracle full filter (the workload's scales, mode, M x n) of the %s, all %d threads"
+                      % (what, cores),
+            "seconds": secs, "cpu_model": cpu_model(),
+            "single_thread": {"value": rate1, "unit": UNIT, "cores": 1, "seconds": secs1,
+                              "sample": "central %dx%d crop of that sample, one thread" % small.shape[::-1]},
+            "extrapolation": "the whole workload (%.1f G pixel-steps) at the all-thread rate: %.2f h; "
+                             "at the one-thread rate: %.1f h" % (px_steps / 1e9, full_h,
+                                                                 px_steps / (rate1 * 1e6) / 3600)}
+        # parity on the same sample: the library's per-image filter with the bench's schedule
+        u_s = fd4.to_device(big, dev)
+        w_s = big.shape[1]
+        o_s, i_s = fd4.filter_image(u_s, w_s, sig, T, M, n, prm)
+        agree = float((i_s[:, :w_s].cpu().numpy() == ridx).mean())
+        err = float(np.abs(o_s[:, :w_s].cpu().numpy() - ref).max())
+        idx_in = torch.zeros_like(i_s)
+        idx_in[:, :w_s] = torch.from_numpy(ridx).to(dev)
+        o2, _ = fd4.filter_image(u_s, w_s, sig, T, M, n, prm, sigma_idx=idx_in)
+        err_inj = float(np.abs(o2[:, :w_s].cpu().numpy() - ref).max())
+        out["parity"] = {"vs": "FP64 oracle", "images": what, "max_abs": err, "max_abs_oracle_sigma": err_inj,
+                         "sigma_agreement": agree, "tolerance": 1e-4}
+        # the variant legs against the oracle's variant on the 256^2 crop
+        sm = center_crop(big, 256)
+        u_sm = fd4.to_device(sm, dev)
+        for name, leg in variants.items():
+            kw = leg["_kw"]
+            pv = fd4.params(mode=mode, **sched.as_params(), **kw)
+            o_v, i_v = fd4.filter_image(u_sm, 256, sig, T, M, n, pv)
+            got = o_v[:, :256].cpu().numpy()
+            if name == "ifod":
+                tau_o, _, _ = O.fed_taus(T, M, 0.05, n=n)
+                ref_v = O.filter_ifod(sm, tau_o, M, sigma=1.0, lam=0.005)
+                leg["parity"] = {"vs": "FP64 oracle IFOD filter", "images": "central 256x256 crop of the sample",
+                                 "max_abs": float(np.abs(got - ref_v).max()), "tolerance": 1e-4}
+                continue
+            okw = dict(reselect=True) if name == "reselect" else dict(postprocess=True, theta=theta)
+            ref_v, ridx_v, _ = oracle_timed(sm, wl, mode, **okw)
+            par = {"vs": "FP64 oracle, %s" % ("re-selecting schedule" if name == "reselect"
+                                              else "post-processed scale image"),
+                   "images": "central 256x256 crop of the sample", "max_abs": float(np.abs(got - ref_v).max()),
+                   "sigma_agreement": float((i_v[:, :256].cpu().numpy() == ridx_v).mean()), "tolerance": 1e-4}
+            if name == "postprocess":
+                idx_v = torch.zeros_like(i_v)
+                idx_v[:, :256] = torch.from_numpy(ridx_v).to(dev)
+                o3, _ = fd4.filter_image(u_sm, 256, sig, T, M, n, prm, sigma_idx=idx_v)
+                par["max_abs_oracle_sigma"] = float(np.abs(o3[:, :256].cpu().numpy() - ref_v).max())
+            leg["parity"] = par
+    for name, leg in variants.items():
+        leg.pop("_kw", None)
+        out[name] = leg
+    if world == 1 and not args.no_creases:
+        out["creases"] = crease_leg(args, ims, wl, mode, stream, torch, fd4)
     for g in {id(x): x for x in (g_all, g_one, g_sel, g_ten, g_fed)}.values():
         g.close()
     print(json.dumps(out), flush=True)
 
 
-def crease_leg(args, ims, mode, stream, torch, fd4):
+def crease_leg(args, ims, wl, mode, stream, torch, fd4):
     """Crease extraction (Sec. 4) timed over the filtered batch, and the accuracy
-    of Sec. 5 (E, p against the generator's centre lines inside the field of
-    view, 6-pixel neighbourhood) of the creases of the input and of the
-    filtered output of the two smallest images."""
+    of Sec. 5 (E, p against the generator's centre lines, 6-pixel
+    neighbourhood) of the creases of the input and of the filtered output: on
+    the two smallest images of the fundus batch (inside the field of view), or
+    on the central 1024^2 window of the first 4096^2 tree (pieces inside it)."""
     import ctypes
     from paper_1611_06906_gb300 import creases, synth
     sigma_d = 1.0
@@ -466,27 +524,47 @@ def crease_leg(args, ims, mode, stream, torch, fd4):
     run_all()
     torch.cuda.synchronize()
     ms = _timed(run_all, 3, stream, torch) / 3
-    base = rank_seed(3000, 0)
-    sides = synth.batch_sides(base)
-    order = sorted(range(len(ims)), key=lambda i: ims[i].npx)[:2]
+    del segs, keys
     acc = []
-    for i in order:
-        side = sides[i]
-        c = (side - 1) / 2.0
-        gt = [g for g in synth.vessel_tree_centrelines(base + i, side, side, depth=6, noise=0.0)
-              if max(math.hypot(g[0] - c, g[1] - c), math.hypot(g[2] - c, g[3] - c)) < 0.9 * 0.48 * side]
-        s_in, _ = fd4.extract_creases(ims[i].u_in, ims[i].w, sigma_d, mode)
-        s_out, _ = fd4.extract_creases(ims[i].out, ims[i].w, sigma_d, mode)
-        e_in, p_in = creases.evaluate(s_in, gt)
-        e_out, p_out = creases.evaluate(s_out, gt)
-        acc.append({"image": "%dx%d" % (ims[i].w, ims[i].h), "E_input": e_in, "p_input": p_in,
-                    "E_filtered": e_out, "p_filtered": p_out, "segments_input": int(len(s_in)),
-                    "segments_filtered": int(len(s_out)), "truth_segments": len(gt)})
+    if wl["name"] == "batch64_fundus":
+        base = rank_seed(3000, 0)
+        sides = synth.batch_sides(base)
+        order = sorted(range(len(ims)), key=lambda i: ims[i].npx)[:2]
+        for i in order:
+            side = sides[i]
+            c = (side - 1) / 2.0
+            gt = [g for g in synth.vessel_tree_centrelines(base + i, side, side, depth=6, noise=0.0)
+                  if max(math.hypot(g[0] - c, g[1] - c), math.hypot(g[2] - c, g[3] - c)) < 0.9 * 0.48 * side]
+            pairs = [(ims[i].u_in, ims[i].w), (ims[i].out, ims[i].w)]
+            acc.append(_crease_accuracy(fd4, creases, pairs, gt, sigma_d, mode, "%dx%d" % (ims[i].w, ims[i].h)))
+    elif wl["name"] == "tree16_4096":
+        win, y0 = 1024, (4096 - 1024) // 2
+        gt = [(g[0] - y0, g[1] - y0, g[2] - y0, g[3] - y0) + tuple(g[4:])
+              for g in synth.vessel_tree_centrelines(tree16_seed(0, 0), 4096, 4096, depth=8, r0=12.0, r1=0.75,
+                                                     noise=0.15)
+              if min(g[0], g[1], g[2], g[3]) >= y0 + 8 and max(g[0], g[1], g[2], g[3]) <= y0 + win - 8]
+        pairs = []
+        for t in (ims[0].u_in, ims[0].out):
+            crop = fd4.empty_image(win, win, device=t.device)
+            crop[:, :win] = t[y0:y0 + win, y0:y0 + win]
+            pairs.append((crop, win))
+        acc.append(_crease_accuracy(fd4, creases, pairs, gt, sigma_d, mode,
+                                    "central %dx%d window of image 0" % (win, win)))
     return {"sigma": sigma_d, "ms_per_batch": ms, "mpixel_per_s": sum(b.npx for b in ims) / (ms * 1e-3) / 1e6,
             "path": "fd4_extract_creases per filtered image (field + marching squares)", "accuracy": acc}
 
 
-def learned_variant(args, ims, sig, T, M, n, mode, best, stream, torch, fd4):
+def _crease_accuracy(fd4, creases, pairs, gt, sigma_d, mode, label):
+    (u_in, w_in), (u_out, w_out) = pairs
+    s_in, _ = fd4.extract_creases(u_in, w_in, sigma_d, mode)
+    s_out, _ = fd4.extract_creases(u_out, w_out, sigma_d, mode)
+    e_in, p_in = creases.evaluate(s_in, gt)
+    e_out, p_out = creases.evaluate(s_out, gt)
+    return {"image": label, "E_input": e_in, "p_input": p_in, "E_filtered": e_out, "p_filtered": p_out,
+            "segments_input": int(len(s_in)), "segments_filtered": int(len(s_out)), "truth_segments": len(gt)}
+
+
+def learned_variant(args, ims, sig, T, M, n, mode, sched, stream, torch, fd4):
     """Batched + learned path: the selector is trained here with the library's own
     kernels (seeded 256^2 crops labelled by the plain selection), then a step is
     the learned selection with plain fallback on low-confidence tiles, followed by
@@ -500,7 +578,7 @@ def learned_variant(args, ims, sig, T, M, n, mode, best, stream, torch, fd4):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     del crops, labels
-    prm = fd4.params(mode=mode, fed_steps_per_launch=best)
+    prm = fd4.params(mode=mode, **sched.as_params())
     idx_l = [torch.zeros_like(b.idx) for b in ims]
     outs_l = [torch.empty_like(b.u_in) for b in ims]
     lst = fd4.image_list([b.u_in for b in ims], [b.w for b in ims], outs_l, idx_l)
@@ -528,6 +606,7 @@ def learned_variant(args, ims, sig, T, M, n, mode, best, stream, torch, fd4):
         fb += int(nfb.item())
     tiles = sum(((b.w + 31) // 32) * ((b.h + 63) // 64) for b in ims)
     diff = max(float((o[:, :b.w] - b.out[:, :b.w]).abs().max()) for o, b in zip(outs_l, ims))
+
     # the network alone (no fallback) for its agreement and time
     def net_only():
         for b, ix in zip(ims, idx_l):
@@ -545,34 +624,34 @@ def learned_variant(args, ims, sig, T, M, n, mode, best, stream, torch, fd4):
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores; each
+    step is one full filter of the bench's oracle sample of the workload."""
     if rank != 0:
         return
     from oracle import oracle as O
     from paper_1611_06906_gb300 import synth
     wl = dict(synth.WORKLOADS[args.workload])
+    wl["name"] = args.workload
     mode = MODES[wl["mode"]]
     if args.workload == "batch64_fundus":
         sides = synth.batch_sides(3000)
         i = int(np.argmin(sides))
-        img = synth.fundus_like(3000 + i, sides[i])
+        imgs = [synth.fundus_like(3000 + i, sides[i])]
+    elif args.workload == "tree16_4096":
+        imgs = [synth.tree16(tree16_seed(0, 0))]
     else:
         imgs, _ = make_workload(args.workload, 0, 1)
-        img = imgs[0]
     O.build()
-    tau, _, _ = O.fed_taus(wl["T"], wl["M"], 0.05, n=wl["n"])
-    pxs = img.size * wl["M"] * wl["n"]
-
-    def step():
-        O.filter_image(img, wl["sigmas"], tau, wl["M"], mode=mode)
-
+    big, what, _ = oracle_samples(imgs, wl, mode)
+    pxs = big.size * wl["M"] * wl["n"]
     for _ in range(args.warmup):
-        step()
+        oracle_timed(big, wl, mode)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step()
+        oracle_timed(big, wl, mode)
     secs = time.perf_counter() - t0
     value = pxs * args.steps / secs / 1e6
-    sample = "oracle full filter of the smallest batch image (%dx%d px), one image per step" % img.shape[::-1]
+    sample = "oracle full filter of the %s, one sample per step, all %d threads" % (what, O.num_threads())
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -580,7 +659,7 @@ def run_reference(args, rank, world):
            "config": {"workload": args.workload, "sample": sample, "sigmas": len(wl["sigmas"]),
                       "mode": wl["mode"], "M": wl["M"], "n": wl["n"], "T": wl["T"]},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-                            "sample": sample},
+                            "sample": sample, "cpu_model": cpu_model()},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -591,12 +670,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fd4", choices=["fd4", "reference"])
-    ap.add_argument("--workload", default="batch64_fundus",
-                    choices=["batch64_fundus", "tree_1024", "tree16_4096"])
+    ap.add_argument("--workload", default="tree16_4096",
+                    choices=["tree16_4096", "batch64_fundus", "tree_1024"])
     ap.add_argument("--limit", type=int, default=0, help="use only the first N images (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--fed-steps", type=int, default=0, help="FED steps per launch (0: autotune)")
+    ap.add_argument("--fed-steps", type=int, default=0,
+                    help="FED steps per launch with the default region and quads (0: autotune the schedule)")
     ap.add_argument("--no-learned", action="store_true", help="skip the batched+learned variant")
     ap.add_argument("--no-reselect", action="store_true", help="skip the per-cycle re-selection variant")
     ap.add_argument("--no-postprocess", action="store_true", help="skip the scale post-processing variant")
@@ -607,8 +687,8 @@ def main():
     ap.add_argument("--sel-threshold", type=float, default=0.5, help="fallback confidence threshold")
     ap.add_argument("--only-graph", action="store_true", help="replay the full graph only (profiling)")
     ap.add_argument("--traffic", type=float, default=None,
-                    help="DRAM bytes per FED launch from an ncu capture of the current kernel "
-                         "(default: the stored per-pixel figure of k_fed_quad<2,64>, else null)")
+                    help="DRAM bytes per FED launch from an ncu capture of the kernel the schedule runs "
+                         "(default: the stored per-pixel figure of that schedule, else null)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -103,6 +103,13 @@ typedef struct fd4_params {
     float ifod_sigma;        /* FD4_MODEL_IFOD: the regularisation scale of
                                 H(u_sigma) (default 1.0, the paper's setting;
                                 at most FD4_MAX_SIGMA)                           */
+    int fed_tile_rows;       /* FED schedule, 2 or 4 steps per launch under the
+                                natural boundary: rows of the 64-column regions
+                                a block advances in shared memory, 64 or 32
+                                (0 = library default, 64)                        */
+    int fed_quads_per_thread;/* FED schedule, as above: row quads (4 adjacent
+                                pixels) each thread owns, 1 or 2 (0 = library
+                                default, 2)                                      */
 } fd4_params;
 
 /* The filter a whole-filter call runs.  MAFOD: the paper's method (scale
@@ -246,6 +253,15 @@ int fd4_fed_cycle(float *d_u, int w, int h, int pitch, const float *d_tensor,
                   const double *h_tau, int n, int boundary,
                   void *d_ws, size_t ws_bytes, fd4_stream_t stream);
 
+/* fd4_fed_cycle with an explicit kernel schedule (no counterpart in the
+ * paper): steps_per_launch, tile_rows and quads_per_thread as the fd4_params
+ * fields of those names (0 = the library default).  Every schedule applies
+ * the same steps; results differ by FP32 rounding only.  Errors as
+ * fd4_fed_cycle, and FD4_ERR_BAD_ARG for a schedule outside those ranges.   */
+int fd4_fed_cycle_sched(float *d_u, int w, int h, int pitch, const float *d_tensor,
+                        const double *h_tau, int n, int boundary, int steps_per_launch, int tile_rows,
+                        int quads_per_thread, void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+
 /* The whole filter (Sec. 3): step sizes from (T, M, n_in, params->tau_max,
  * params->kappa) as in fd4_fed_taus; sigma* once on the input (unless
  * sigma_given, in which case d_sigma_idx is read); then M cycles of
@@ -315,14 +331,30 @@ int fd4_graph_launch(fd4_graph g, fd4_stream_t stream);
 int fd4_graph_kernel_count(fd4_graph g, int *n_kernels);
 int fd4_graph_destroy(fd4_graph g);
 
-/* Autotuner for the FED kernel schedule: runs the selection and one tensor
- * build of the batch, then times one FED cycle with each schedule (1 to 4
- * steps per launch) with CUDA events on `stream` (synchronising it) and
- * writes the fastest to *best_steps_per_launch; times_ms (nullable, 4
- * entries) receives the times.  The images' d_out buffers are overwritten.  */
+/* One FED kernel schedule and its measured time (fd4_autotune_batched). */
+typedef struct fd4_fed_schedule {
+    int steps_per_launch;    /* as fd4_params.fed_steps_per_launch (1..4)      */
+    int tile_rows;           /* as fd4_params.fed_tile_rows (64 or 32; 0 where
+                                the schedule has no such choice)                */
+    int quads_per_thread;    /* as fd4_params.fed_quads_per_thread (1 or 2; 0
+                                where the schedule has no such choice)          */
+    float ms;                /* time of one FED cycle over the batch            */
+} fd4_fed_schedule;
+
+#define FD4_AUTOTUNE_CANDIDATES 10
+
+/* Autotuner for the FED kernel schedule (no counterpart in the paper): runs
+ * the selection and one tensor build of the batch, then times one FED cycle
+ * with each of the FD4_AUTOTUNE_CANDIDATES schedules -- 1 and 3 steps per
+ * launch, and 2 and 4 steps per launch on regions of 64 or 32 rows with 1 or
+ * 2 quads per thread (the halo depth is 2 pixels per step) -- with CUDA
+ * events on `stream` (synchronising it), after one untimed cycle each.
+ * *best receives the fastest; tried (nullable, FD4_AUTOTUNE_CANDIDATES
+ * entries) every candidate with its time.  The schedule is copied into a
+ * fd4_params by the caller.  The images' d_out buffers are overwritten.     */
 int fd4_autotune_batched(const fd4_image *h_imgs, int n_images, const float *h_sigmas, int n_sigma,
                          const fd4_params *params, double T, int M, int n_in, void *d_ws, size_t ws_bytes,
-                         fd4_stream_t stream, int *best_steps_per_launch, float *times_ms);
+                         fd4_stream_t stream, fd4_fed_schedule *best, fd4_fed_schedule *tried);
 
 /* ------------------------------------------------------------------------ */
 /* Learned scale selector.  No counterpart in the paper: a small network that
@@ -394,6 +426,18 @@ int fd4_selector_status(const void *d_ws, int *status, fd4_stream_t stream);
  * back (FD4_ERR_TIMEOUT when detection works).  Synchronous; d_ws needs
  * fd4_selector_workspace_bytes(1, 128, 4, 128) bytes.                       */
 int fd4_selftest_wait_timeout(void *d_ws, size_t ws_bytes, int *status, fd4_stream_t stream);
+
+/* Failure-detection self-test of the FED kernels (no counterpart in the
+ * paper): one launch of the TMA-staged FED kernel on the image d_u with the
+ * tile copies withheld (the tile barrier is armed for bytes that never come)
+ * and every bounded wait limited to 10 ms, so the first wait runs out; the
+ * kernel records FD4_ERR_TIMEOUT in the device status word (fd4_device_status)
+ * and returns without writing d_u, leaving the context usable.  *status
+ * receives the status word read back with reset (FD4_ERR_TIMEOUT when
+ * detection works).  No copy is ever in flight.  Synchronous; the workspace
+ * is that of fd4_fed_cycle.                                                 */
+int fd4_selftest_fed_wait_timeout(float *d_u, int w, int h, int pitch, const float *d_tensor, void *d_ws,
+                                  size_t ws_bytes, int *status, fd4_stream_t stream);
 
 /* Allocation-free FED cycle.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory -- host applications

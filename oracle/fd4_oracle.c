@@ -66,6 +66,18 @@ int or_num_threads(void)
 #endif
 }
 
+/* Threads of the pixel-row loops from now on (the arithmetic per pixel does
+ * not depend on it); used to time the oracle on one core.                   */
+void or_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0)
+        omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Gaussian derivative kernels.  The paper regularises with u_sigma = u * G_sigma
  * (Sec. 3.1, Eq. 6, the local normalised Hessian) and takes derivatives of u_sigma;

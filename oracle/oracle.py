@@ -110,6 +110,13 @@ def num_threads() -> int:
     return int(_load().or_num_threads())
 
 
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's pixel-row loops from now on (results do not depend on it)."""
+    lib = _load()
+    lib.or_set_num_threads.argtypes = [ctypes.c_int]
+    lib.or_set_num_threads(int(n))
+
+
 def gauss_radius(sigma: float) -> int:
     return int(_load().or_gauss_radius(float(sigma)))
 

@@ -1,14 +1,17 @@
 // FED cycles of the fourth-order anisotropic diffusion (Sec. 3.4 Eq. 17,
 // Sec. 3.5 Eq. 21): u <- u - tau_i L^T D L u, n times with D frozen.
 //
-// One explicit step per launch.  A block stages a 32 x 8 tile of u with a
+// The launcher runs one of three kernels, as the schedule says: the
+// TMA-staged quad kernel of fd4_fed_tma.cu (2 or 4 steps per launch, natural
+// boundary: the default), the scalar fused kernel below (3 steps per launch,
+// or the periodic boundary), or one launch per explicit step (k_fed_step).
+//
+// k_fed_step: one explicit step per launch.  A block stages a 32 x 8 tile of u with a
 // 2-pixel halo in shared memory, evaluates T = M D M L u on the tile plus a
 // 1-pixel ring (M masks the derivative rows that do not exist under the
 // natural boundary), and applies L^T.  Per pixel and step the algorithmic
 // HBM traffic is 24 bytes (u read, float4 tensor read, u write); the halo
 // re-reads hit L2.
-#include <cstdlib>
-
 #include "fd4_internal.h"
 #include "fd4_quad.cuh"
 
@@ -333,273 +336,6 @@ __global__ void __launch_bounds__(FNT, 2) k_fed_fused(Imgs I, StepTaus taus, int
 
 }  // namespace
 
-// ---------------------------------------------------------------------------
-// Pipelined fused variant (natural boundary, S = 2 or 4): while a block
-// advances one tile, cp.async copies bring the next tile's u region and tensor
-// values into a second shared buffer (16-byte copies, zero-filled outside the
-// image), so the staging latency overlaps the computation.
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(valid ? 16 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-constexpr size_t kPipeSmem = sizeof(float) * FRX * FRY * (2 + 3 + 4);  // 2 u buffers, T, tensor: 72 KB
-
-template <int S>
-__device__ __forceinline__ void prefetch_tile(const ImgDesc &d, int local, float *u_dst, float4 *t_dst, int parity)
-{
-    constexpr int H = 2 * S, TXo = FRX - 2 * H, TYo = FRY - 2 * H;
-    const int tid = threadIdx.x;
-    const int w = d.w, h = d.h, pitch = d.pitch;
-    const int tiles_x = (w + TXo - 1) / TXo;
-    const int gx0 = (local % tiles_x) * TXo - H, gy0 = (local / tiles_x) * TYo - H;
-    const float *uin = parity ? d.tmp : d.u;
-    for (int c = tid; c < FRY * FRX / 4; c += FNT) {
-        const int ry = c / (FRX / 4), cx = (c % (FRX / 4)) * 4;
-        const int gy = gy0 + ry, gx = gx0 + cx;
-        // a chunk of 4 columns starting inside the image stays inside the row pitch
-        const bool valid = gy >= 0 && gy < h && gx >= 0 && gx < w;
-        cp_async16(u_dst + ry * FRX + cx, valid ? uin + (size_t)gy * pitch + gx : uin, valid);
-    }
-    for (int i = tid; i < FRY * FRX; i += FNT) {
-        const int ry = i / FRX, rx = i % FRX;
-        const int gy = gy0 + ry, gx = gx0 + rx;
-        const bool valid = gy >= 0 && gy < h && gx >= 0 && gx < w;
-        cp_async16(t_dst + i, valid ? d.tensor + (size_t)gy * pitch + gx : d.tensor, valid);
-    }
-}
-
-template <int S>
-__global__ void __launch_bounds__(FNT, 2) k_fed_fused_pipe(Imgs I, StepTaus taus, int parity)
-{
-    constexpr int H = 2 * S, TXo = FRX - 2 * H, TYo = FRY - 2 * H;
-    static_assert(TXo % 4 == 0 && H % 4 == 0, "16-byte aligned region columns");
-    extern __shared__ __align__(16) float psm[];
-    // u buffers: psm + b * FRX * FRY for b = 0, 1
-    float (*sxx)[FRX] = reinterpret_cast<float (*)[FRX]>(psm + 2 * FRX * FRY);
-    float (*sxy)[FRX] = reinterpret_cast<float (*)[FRX]>(psm + 3 * FRX * FRY);
-    float (*syy)[FRX] = reinterpret_cast<float (*)[FRX]>(psm + 4 * FRX * FRY);
-    float4 *tbuf = reinterpret_cast<float4 *>(psm + 5 * FRX * FRY);
-    __shared__ float stau[8];
-    __shared__ ImgDesc sd[2];
-    __shared__ int s_local[2];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) stau[i] = taus.t[i];
-    }
-    const int rx = (warp % (FRX / 32)) * 32 + lane, ry0 = (warp / (FRX / 32)) * FV;
-    const int ntiles = I.tiles;
-    int cur = 0;
-    int t = blockIdx.x;
-    if (t < ntiles) {
-        if (tid == 0) find_tile(I, S, t, sd[0], s_local[0]);
-        __syncthreads();
-        prefetch_tile<S>(sd[0], s_local[0], psm, tbuf, parity);
-    }
-    cp_async_commit();
-    for (; t < ntiles; t += gridDim.x) {
-        cp_async_wait_all();
-        __syncthreads();  // this tile's u region and tensor values have landed
-        const int w = sd[cur].w, h = sd[cur].h, pitch = sd[cur].pitch;
-        float *uout = parity ? sd[cur].u : sd[cur].tmp;
-        const int tiles_x = (w + TXo - 1) / TXo;
-        const int gx0 = (s_local[cur] % tiles_x) * TXo - H, gy0 = (s_local[cur] / tiles_x) * TYo - H;
-        const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + FRX <= w && gy0 + FRY <= h;
-        const int gx = gx0 + rx;
-        const bool in_x = gx >= 0 && gx < w;
-        const bool vx = gx >= 1 && gx <= w - 2;
-        unsigned rowbits = 0u;
-        float4 tv[FV];
-#pragma unroll
-        for (int j = 0; j < FV; ++j) {
-            const int gy = gy0 + ry0 + j;
-            rowbits |= (gy >= 0 && gy < h ? 1u : 0u) << j;
-            rowbits |= (gy >= 1 && gy <= h - 2 ? 1u : 0u) << (8 + j);
-            tv[j] = tbuf[(ry0 + j) * FRX + rx];
-        }
-        const int tn = t + gridDim.x;
-        if (tid == 0 && tn < ntiles) find_tile(I, S, tn, sd[cur ^ 1], s_local[cur ^ 1]);
-        __syncthreads();  // the tensor buffer is read; the next descriptor is ready
-        if (tn < ntiles) prefetch_tile<S>(sd[cur ^ 1], s_local[cur ^ 1], psm + (cur ^ 1) * FRX * FRY, tbuf, parity);
-        cp_async_commit();
-
-        float (*su)[FRX] = reinterpret_cast<float (*)[FRX]>(psm + cur * FRX * FRY);
-        if (interior) fused_steps<true>(su, sxx, sxy, syy, stau, taus.n, rx, ry0, tv, in_x, vx, rowbits);
-        else fused_steps<false>(su, sxx, sxy, syy, stau, taus.n, rx, ry0, tv, in_x, vx, rowbits);
-
-        for (int i = tid; i < TXo * TYo; i += FNT) {
-            const int ty = i / TXo, tx = i - ty * TXo;
-            const int ox = gx0 + H + tx, oy = gy0 + H + ty;
-            if (ox < w && oy < h) uout[(size_t)oy * pitch + ox] = su[H + ty][H + tx];
-        }
-        cur ^= 1;
-    }
-    cp_async_wait_all();
-}
-
-// ---------------------------------------------------------------------------
-// Quad variant (natural boundary, S = 2 or 4), the default.  A 64 x 64 region
-// (or 64 x 32), cp.async staging of the next tile and S steps per launch as in
-// the kernels above, but each thread owns a row quad (4 adjacent pixels of one
-// row; 16 quads per region row, one thread per quad) and keeps
-// its u, its T_xx and its tensor values in registers; horizontal neighbours
-// come from the adjacent lanes by shuffles, vertical ones from 16-byte shared
-// loads of the rows above and below (u, T_xy and T_yy planes only).  T and u
-// are computed on the whole region: the planes carry a zero ring, and the
-// values spoiled at the region border (ring reads, shuffles that wrap to the
-// other row of the warp) reach 2 pixels further in per step and stay inside
-// the H = 2S halo, so no step needs a shrinking-region test.  The tensor is
-// kept per pixel as (cos 2t, sin 2t, (mu1 + mu2) / 2, (mu1 - mu2) / 2), with
-// which T = D : H costs about 26 flops.
-
-constexpr int QPAD = 4;                           // ring columns (keeps quads 16-byte aligned)
-constexpr int QSW = FRX + 2 * QPAD;               // 72 floats per plane row
-constexpr int QTS = 5;                            // float4 slots per quad in the tensor buffer (1 pad:
-                                                  // the 16-byte reads of 8 lanes hit distinct banks)
-// Region height RY = 32 (512 threads, two blocks per SM) or 64 (1024 threads,
-// one block per SM, a smaller halo share: (64 - 4S)^2 of 64^2 pixels exact).
-template <int RY>
-constexpr int q_nt() { return (FRX / 4) * RY; }   // threads: 16 quads across x RY rows
-template <int RY>
-constexpr int q_plane() { return (RY + 2) * QSW; }  // one ring row above and below
-template <int RY>
-constexpr int q_tbuf() { return RY * (FRX / 4) * QTS; }  // float4 entries
-template <int RY>
-constexpr size_t q_smem() { return sizeof(float) * 4 * q_plane<RY>() + sizeof(float4) * q_tbuf<RY>(); }
-template <int S, int RY>
-constexpr int q_shape() { return RY == 32 ? S : (S == 2 ? SHAPE_Q64_2 : SHAPE_Q64_4); }
-
-// cp.async of a tile's region into the staging buffers: consecutive threads
-// copy consecutive 16-byte chunks (one u chunk and four tensor pixels each).
-template <int S, int RY>
-__device__ __forceinline__ void quad_prefetch(const ImgDesc &d, int local, float *u_dst, float4 *t_dst, int parity)
-{
-    constexpr int H = 2 * S, TXo = FRX - 2 * H, TYo = RY - 2 * H, QNT = q_nt<RY>();
-    const int tid = threadIdx.x;
-    const int w = d.w, h = d.h, pitch = d.pitch;
-    const int tiles_x = (w + TXo - 1) / TXo;
-    const int gx0 = (local % tiles_x) * TXo - H, gy0 = (local / tiles_x) * TYo - H;
-    const float *uin = parity ? d.tmp : d.u;
-    {
-        const int ry = tid >> 4, cx = (tid & 15) * 4;
-        const int gy = gy0 + ry, gx = gx0 + cx;
-        // a chunk of 4 columns starting inside the image stays inside the row pitch
-        const bool valid = gy >= 0 && gy < h && gx >= 0 && gx < w;
-        cp_async16(u_dst + (ry + 1) * QSW + QPAD + cx, valid ? uin + (size_t)gy * pitch + gx : uin, valid);
-    }
-#pragma unroll
-    for (int j = 0; j < FRX * RY / QNT; ++j) {
-        const int i = tid + j * QNT;
-        const int ry = i / FRX, rx = i % FRX;
-        const int gy = gy0 + ry, gx = gx0 + rx;
-        const bool valid = gy >= 0 && gy < h && gx >= 0 && gx < w;
-        cp_async16(t_dst + (ry * (FRX / 4) + (rx >> 2)) * QTS + (rx & 3),
-                   valid ? d.tensor + (size_t)gy * pitch + gx : d.tensor, valid);
-    }
-}
-
-template <int S, int RY>
-__global__ void __launch_bounds__(q_nt<RY>(), RY == 32 ? 2 : 1) k_fed_quad(Imgs I, StepTaus taus, int parity)
-{
-    constexpr int H = 2 * S, TXo = FRX - 2 * H, TYo = RY - 2 * H;
-    constexpr int QNT = q_nt<RY>(), QPLANE = q_plane<RY>(), SHAPE = q_shape<S, RY>();
-    static_assert(TXo % 4 == 0 && H % 4 == 0, "16-byte aligned region columns");
-    
-    extern __shared__ __align__(16) float qsm[];
-    // planes: u buffer 0, u buffer 1, T_xy, T_yy (each with the zero ring), then the tensor
-    float *sxy = qsm + 2 * QPLANE, *syy = qsm + 3 * QPLANE;
-    float4 *tbuf = reinterpret_cast<float4 *>(qsm + 4 * QPLANE);
-    __shared__ float stau[8];
-    __shared__ ImgDesc sd[2];
-    __shared__ int s_local[2];
-    __shared__ TileCache tcache;
-    if (threadIdx.x == 0) tc_reset(tcache);
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) stau[i] = taus.t[i];
-    }
-    for (int i = tid; i < 4 * QPLANE; i += QNT) qsm[i] = 0.0f;  // the rings stay zero
-    const int q = tid & 15, ry = tid >> 4;
-    const int off = (ry + 1) * QSW + QPAD + 4 * q;  // this quad in a plane
-    const float4 *tq = tbuf + (ry * (FRX / 4) + q) * QTS;
-    const int ntiles = I.tiles;
-    int cur = 0;
-    int t = blockIdx.x;
-    __syncthreads();
-    if (t < ntiles) {
-        if (tid == 0) find_tile_cached(I, SHAPE, t, tcache, sd[0], s_local[0]);
-        __syncthreads();
-        quad_prefetch<S, RY>(sd[0], s_local[0], qsm, tbuf, parity);
-    }
-    cp_async_commit();
-    for (; t < ntiles; t += gridDim.x) {
-        cp_async_wait_all();
-        __syncthreads();  // this tile's u region and tensor values have landed; every warp is past the last tile
-        const int w = sd[cur].w, h = sd[cur].h, pitch = sd[cur].pitch;
-        float *uout = parity ? sd[cur].u : sd[cur].tmp;
-        const int tiles_x = (w + TXo - 1) / TXo;
-        const int gx0 = (s_local[cur] % tiles_x) * TXo - H, gy0 = (s_local[cur] / tiles_x) * TYo - H;
-        const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + FRX <= w && gy0 + RY <= h;
-        const int gx = gx0 + 4 * q, gy = gy0 + ry;
-        float *su = qsm + cur * QPLANE;
-        const float4 u0 = *reinterpret_cast<const float4 *>(su + off);
-        unsigned mask = 0u;
-        if (!interior) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int x = gx + i;
-                mask |= (x >= 0 && x < w && gy >= 0 && gy < h ? 1u : 0u) << i;
-                mask |= (x >= 1 && x <= w - 2 ? 1u : 0u) << (4 + i);
-            }
-            mask |= (gy >= 1 && gy <= h - 2 ? 1u : 0u) << 8;
-        }
-        QuadCoef k;
-        {
-            float cc[4], ss[4], pp[4], qq[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float4 tt = tq[i];
-                cc[i] = tt.x;
-                ss[i] = tt.y;
-                pp[i] = 0.5f * (tt.z + tt.w);
-                qq[i] = 0.5f * (tt.z - tt.w);
-            }
-            k.c = make_float4(cc[0], cc[1], cc[2], cc[3]);
-            k.s = make_float4(ss[0], ss[1], ss[2], ss[3]);
-            k.p = make_float4(pp[0], pp[1], pp[2], pp[3]);
-            k.q = make_float4(qq[0], qq[1], qq[2], qq[3]);
-        }
-        const int tn = t + gridDim.x;
-        if (tid == 0 && tn < ntiles) find_tile_cached(I, SHAPE, tn, tcache, sd[cur ^ 1], s_local[cur ^ 1]);
-        __syncthreads();  // the tensor buffer is read; the next descriptor is ready
-        if (tn < ntiles) quad_prefetch<S, RY>(sd[cur ^ 1], s_local[cur ^ 1], qsm + (cur ^ 1) * QPLANE, tbuf, parity);
-        cp_async_commit();
-
-        const float4 un = interior ? quad_steps<false, QSW>(su, sxy, syy, stau, taus.n, off, k, mask, u0)
-                                   : quad_steps<true, QSW>(su, sxy, syy, stau, taus.n, off, k, mask, u0);
-        // the exact interior: rows H .. H + TYo - 1, columns H .. H + TXo - 1 (whole quads)
-        if (ry >= H && ry < H + TYo && 4 * q >= H && 4 * q < H + TXo && gy < h) {
-            float *dst = uout + (size_t)gy * pitch + gx;
-            if (gx + 3 < w) {
-                *reinterpret_cast<float4 *>(dst) = un;
-            } else {
-                if (gx < w) dst[0] = un.x;
-                if (gx + 1 < w) dst[1] = un.y;
-                if (gx + 2 < w) dst[2] = un.z;
-            }
-        }
-        cur ^= 1;
-    }
-    cp_async_wait_all();
-}
-
 template <int S>
 static int set_fused_smem()
 {
@@ -615,67 +351,9 @@ static int set_fused_smem()
     return 0;
 }
 
-template <int S>
-static int set_pipe_smem()
-{
-    static int attr_dev = -1;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
-    if (attr_dev != dev) {
-        if (cudaFuncSetAttribute(k_fed_fused_pipe<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPipeSmem) !=
-            cudaSuccess)
-            return 1;
-        attr_dev = dev;
-    }
-    return 0;
-}
-
-template <int S, int RY>
-static int set_quad_smem()
-{
-    static int attr_dev = -1;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
-    if (attr_dev != dev) {
-        if (cudaFuncSetAttribute(k_fed_quad<S, RY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)q_smem<RY>()) != cudaSuccess)
-            return 1;
-        attr_dev = dev;
-    }
-    return 0;
-}
-
 int prepare_fed_kernels()
 {
-    return set_fused_smem<2>() || set_fused_smem<3>() || set_fused_smem<4>() || set_pipe_smem<2>() ||
-           set_pipe_smem<4>() || set_quad_smem<2, 32>() || set_quad_smem<4, 32>() || set_quad_smem<2, 64>() ||
-           set_quad_smem<4, 64>() || prepare_tma_kernels();
-}
-
-template <int S, int RY>
-static int launch_quad(const HostBatch &B, const double *tau, int n, int parity, cudaStream_t st)
-{
-    if (set_quad_smem<S, RY>()) return 1;
-    StepTaus t{};
-    t.n = n;
-    for (int i = 0; i < n; ++i) t.t[i] = (float)tau[i];
-    Imgs I = B.I;
-    I.tiles = B.tiles[q_shape<S, RY>()];
-    const int grid = persistent_grid((const void *)k_fed_quad<S, RY>, q_nt<RY>(), q_smem<RY>(), I.tiles);
-    k_fed_quad<S, RY><<<grid, q_nt<RY>(), q_smem<RY>(), st>>>(I, t, parity);
-    return 0;
-}
-
-template <int S>
-static int launch_pipe(Imgs I, const double *tau, int n, int parity, cudaStream_t st)
-{
-    if (set_pipe_smem<S>()) return 1;
-    StepTaus t{};
-    t.n = n;
-    for (int i = 0; i < n; ++i) t.t[i] = (float)tau[i];
-    const int grid = persistent_grid((const void *)k_fed_fused_pipe<S>, FNT, kPipeSmem, I.tiles);
-    k_fed_fused_pipe<S><<<grid, FNT, kPipeSmem, st>>>(I, t, parity);
-    return 0;
+    return set_fused_smem<2>() || set_fused_smem<3>() || set_fused_smem<4>() || prepare_tma_kernels();
 }
 
 template <int S>
@@ -690,33 +368,21 @@ static int launch_fused(Imgs I, const double *tau, int n, int parity, int period
     return 0;
 }
 
-// Region height of the quad kernel: 64 (64 x 64 regions, the default) or
-// FD4_FED_QUAD_ROWS=32 (64 x 32 regions, two blocks per SM).
-static int quad_rows()
+FedSched resolve_sched(const fd4_params &p)
 {
-    const char *e = getenv("FD4_FED_QUAD_ROWS");
-    return (e && atoi(e) == 32) ? 32 : 64;
+    FedSched s;
+    s.steps = p.fed_steps_per_launch > 0 ? p.fed_steps_per_launch : kDefaultSched.steps;
+    s.rows = p.fed_tile_rows > 0 ? p.fed_tile_rows : kDefaultSched.rows;
+    s.quads = p.fed_quads_per_thread > 0 ? p.fed_quads_per_thread : kDefaultSched.quads;
+    return s;
 }
 
-// Kernel for S = 2 and 4 under the natural boundary, from FD4_FED_PIPELINE:
-// 0 = the plain fused kernel, 1 = its cp.async-pipelined form, 2 = the quad
-// kernel with cp.async staging, unset or 3 = the quad kernel with TMA staging
-// (fd4_fed_tma.cu).  S = 3 and the periodic boundary use the plain fused kernel.
-static int pipeline_kind()
-{
-    const char *e = getenv("FD4_FED_PIPELINE");
-    if (e && e[0] == '0') return 0;
-    if (e && e[0] == '1') return 1;
-    if (e && e[0] == '2') return 2;
-    return 3;
-}
-
-int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundary, int steps_per_launch,
+int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundary, const FedSched &sch,
                      cudaStream_t st)
 {
     const int periodic = boundary == FD4_BC_PERIODIC;
-    int S = steps_per_launch;
-    if (S < 1 || S > 4) S = 2;
+    int S = sch.steps;
+    if (S < 1 || S > 4) S = kDefaultSched.steps;
     int parity = 0;
     if (S == 1) {
         Imgs I = B.I;
@@ -732,21 +398,15 @@ int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundar
         for (int i = 0; i < n; i += S) {
             const int k = n - i < S ? n - i : S;
             int rc;
-            const int kind = periodic || S == 3 ? 0 : pipeline_kind();
-            if (kind == 3)
-                rc = S == 2 ? launch_fed_tma<2>(B, h_tau + i, k, parity, st)
-                            : launch_fed_tma<4>(B, h_tau + i, k, parity, st);
-            else if (kind == 2 && quad_rows() == 64)
-                rc = S == 2 ? launch_quad<2, 64>(B, h_tau + i, k, parity, st)
-                            : launch_quad<4, 64>(B, h_tau + i, k, parity, st);
-            else if (kind == 2)
-                rc = S == 2 ? launch_quad<2, 32>(B, h_tau + i, k, parity, st)
-                            : launch_quad<4, 32>(B, h_tau + i, k, parity, st);
-            else if (kind == 1) rc = S == 2 ? launch_pipe<2>(I, h_tau + i, k, parity, st)
-                                            : launch_pipe<4>(I, h_tau + i, k, parity, st);
-            else rc = S == 2 ? launch_fused<2>(I, h_tau + i, k, parity, periodic, st)
-                    : S == 3 ? launch_fused<3>(I, h_tau + i, k, parity, periodic, st)
-                             : launch_fused<4>(I, h_tau + i, k, parity, periodic, st);
+            // the TMA-staged quad kernel for 2 and 4 steps under the natural
+            // boundary; the scalar fused kernel for 3 steps and the periodic boundary
+            if (!periodic && S != 3)
+                rc = S == 2 ? launch_fed_tma<2>(B, h_tau + i, k, parity, sch, st)
+                            : launch_fed_tma<4>(B, h_tau + i, k, parity, sch, st);
+            else
+                rc = S == 2 ? launch_fused<2>(I, h_tau + i, k, parity, periodic, st)
+                   : S == 3 ? launch_fused<3>(I, h_tau + i, k, parity, periodic, st)
+                            : launch_fused<4>(I, h_tau + i, k, parity, periodic, st);
             if (rc) return 1;
             parity ^= 1;
         }
@@ -781,19 +441,8 @@ int launch_put_descs(const ImgDesc *h_descs, int n, ImgDesc *d_table, cudaStream
     return cudaGetLastError() != cudaSuccess;
 }
 
-// Steps per launch for the single-image entry points: FD4_FED_FUSE in the
-// environment (1 = one launch per step, 2..4 fused); default 2.
-int default_steps_per_launch()
-{
-    const char *e = getenv("FD4_FED_FUSE");
-    if (!e) return 2;
-    const int v = atoi(e);
-    if (v == 0) return 1;
-    return (v >= 1 && v <= 4) ? v : 2;
-}
-
 int launch_fed_cycle(float *d_u, int w, int h, int pitch, const float *d_tensor, const double *h_tau, int n,
-                     int boundary, char *ws, cudaStream_t st)
+                     int boundary, const FedSched &sch, char *ws, cudaStream_t st)
 {
     ImgDesc d{};
     d.u = d_u;
@@ -802,7 +451,7 @@ int launch_fed_cycle(float *d_u, int w, int h, int pitch, const float *d_tensor,
     d.w = w;
     d.h = h;
     d.pitch = pitch;
-    return launch_fed_batch(single_batch(d), h_tau, n, boundary, default_steps_per_launch(), st);
+    return launch_fed_batch(single_batch(d), h_tau, n, boundary, sch, st);
 }
 
 }  // namespace fd4

@@ -1,6 +1,8 @@
 // FED cycle kernel with TMA staging (Sec. 3.4 Eq. 17, Sec. 3.5 Eq. 21):
-// u <- u - tau_i L^T D L u, S = 2 or 4 explicit steps per launch on 64 x 64
-// regions, the quad arithmetic of fd4_quad.cuh.
+// u <- u - tau_i L^T D L u, S = 2 or 4 explicit steps per launch on regions of
+// 64 columns and RY = 64 or 32 rows, NQ = 1 or 2 row quads per thread, the quad
+// arithmetic of fd4_quad.cuh.  S, RY and NQ form the schedule the autotuner
+// times (fd4_autotune_batched); every schedule computes the same steps.
 //
 // Each tile's region of u and of the tensor field arrives by two tensor-map
 // copies (cp.async.bulk.tensor) that one thread issues and an mbarrier counts
@@ -33,22 +35,40 @@ __device__ int g_fed_status;
 
 namespace {
 
-constexpr int TR = 64;                      // region side
-constexpr int TNT = (TR / 4) * TR;          // 1024 threads: 16 quads x 64 rows
+constexpr int TR = 64;                      // region width (columns); RY rows
 constexpr int TSW = TR;                     // plane row stride (floats)
-constexpr int TPLANE = (TR + 2) * TSW;      // one zero ring row above and below
-constexpr unsigned kUBytes = TR * TR * 4;   // u box
-constexpr unsigned kTBytes = TR * TR * 16;  // tensor box (cos 2t, sin 2t, mu1, mu2)
 // Tiles in flight per block: the copies of the next two tiles run during the
 // current tile's steps (one tile of 80 KB in flight per SM leaves the copies
 // latency-bound at about half the HBM bandwidth).
 constexpr int kAhead = 2;
+template <int RY>
+constexpr int t_quads() { return (TR / 4) * RY; }   // 16 quads x RY rows
+template <int RY>
+constexpr int t_plane() { return (RY + 2) * TSW; }  // one zero ring row above and below
+template <int RY>
+constexpr unsigned t_ubytes() { return TR * RY * 4; }   // u box
+template <int RY>
+constexpr unsigned t_tbytes() { return TR * RY * 16; }  // tensor box (cos 2t, sin 2t, mu1, mu2)
 // shared memory: tensor boxes x2 (1024-byte aligned) | u planes x3 | T_xy, T_yy
-constexpr size_t kTmaSmem = 1024 + kAhead * kTBytes + sizeof(float) * (kAhead + 1 + 2) * TPLANE;
+template <int RY>
+constexpr size_t t_smem() { return 1024 + kAhead * t_tbytes<RY>() + sizeof(float) * (kAhead + 1 + 2) * t_plane<RY>(); }
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded wait on a tile's copies
 
+// 2-D maps of the two u planes {w, h} and the 3-D map of the tensor field
+// {16, quads, h}; their boxes have the region's rows.
 struct TmaMaps {
-    CUtensorMap u, tmp, ten;  // 2-D maps of the two u planes {w, h}; 3-D map of the tensor field {16, quads, h}
+    CUtensorMap u, tmp, ten;
+};
+// One image's maps for both region heights.
+struct TmaMapSet {
+    TmaMaps r64, r32;
+};
+
+// Bounded waits of one launch: the limit, and (self-test only) copies withheld
+// so that the limit runs out.
+struct FedWait {
+    unsigned long long ns;
+    int withhold;
 };
 
 __device__ __forceinline__ unsigned long long tma_now()
@@ -83,13 +103,13 @@ __device__ __forceinline__ bool tma_try_wait(uint64_t *m, unsigned parity)
         : "memory");
     return ok != 0;
 }
-// Wait for phase `parity` of m, at most kWaitNs; false if it gave up.
-__device__ __forceinline__ bool tma_wait(uint64_t *m, unsigned parity)
+// Wait for phase `parity` of m, at most ns nanoseconds; false if it gave up.
+__device__ __forceinline__ bool tma_wait(uint64_t *m, unsigned parity, unsigned long long ns)
 {
     if (tma_try_wait(m, parity)) return true;
     const unsigned long long t0 = tma_now();
     while (!tma_try_wait(m, parity))
-        if (tma_now() - t0 > kWaitNs) return false;
+        if (tma_now() - t0 > ns) return false;
     return true;
 }
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *m)
@@ -116,8 +136,9 @@ __device__ __forceinline__ void fence_tensormap_acquire(const void *map)
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
 }
 
-template <int S>
-constexpr int tma_shape() { return S == 2 ? SHAPE_Q64_2 : SHAPE_Q64_4; }
+// Tile shape of S steps on RY-row regions: (64 - 4S) x (RY - 4S) exact outputs.
+template <int S, int RY>
+constexpr int tma_shape() { return RY == 64 ? (S == 2 ? SHAPE_Q64_2 : SHAPE_Q64_4) : S; }
 
 // Geometry of a staged tile, computed once by the thread that issues its copies.
 struct TileGeo {
@@ -126,43 +147,54 @@ struct TileGeo {
 };
 
 // Thread 0: the copies of the region of tile `local` of image d into u_dst (plane
-// row 1) and the tensor box; the tile's geometry into *g.
-template <int S>
+// row 1) and the tensor box; the tile's geometry into *g.  withhold (self-test
+// only): the barrier is armed for the bytes but no copy is issued.
+template <int S, int RY>
 __device__ __forceinline__ void tma_issue(const ImgDesc &d, int local, const TmaMaps &one, bool from_table,
-                                          int parity, float *u_dst, void *t_dst, uint64_t *mbar, TileGeo *g)
+                                          int parity, float *u_dst, void *t_dst, uint64_t *mbar, TileGeo *g,
+                                          int withhold)
 {
-    constexpr int H = 2 * S, TO = TR - 2 * H;
-    const int tiles_x = (d.w + TO - 1) / TO;
+    constexpr int H = 2 * S, TOX = TR - 2 * H, TOY = RY - 2 * H;
+    const int tiles_x = (d.w + TOX - 1) / TOX;
     const int ty = local / tiles_x;
-    const int gx0 = (local - ty * tiles_x) * TO - H, gy0 = ty * TO - H;
+    const int gx0 = (local - ty * tiles_x) * TOX - H, gy0 = ty * TOY - H;
     g->gx0 = gx0;
     g->gy0 = gy0;
-    g->interior = gx0 >= 0 && gy0 >= 0 && gx0 + TR <= d.w && gy0 + TR <= d.h;
-    const TmaMaps *m = from_table ? reinterpret_cast<const TmaMaps *>(d.maps) : &one;
+    g->interior = gx0 >= 0 && gy0 >= 0 && gx0 + TR <= d.w && gy0 + RY <= d.h;
+    const TmaMaps *m = &one;
+    if (from_table) {
+        const TmaMapSet *set = reinterpret_cast<const TmaMapSet *>(d.maps);
+        m = RY == 64 ? &set->r64 : &set->r32;
+    }
     const CUtensorMap *mu = parity ? &m->tmp : &m->u;
     if (from_table) {
         fence_tensormap_acquire(mu);
         fence_tensormap_acquire(&m->ten);
     }
     fence_async_smem();
-    tma_expect(mbar, kUBytes + kTBytes);
+    tma_expect(mbar, t_ubytes<RY>() + t_tbytes<RY>());
+    if (withhold) return;
     tma_load_2d(u_dst + TSW, mu, gx0, gy0, mbar);         // x: 4 gx0 bytes, a multiple of 16
     tma_load_3d(t_dst, &m->ten, 0, gx0 >> 2, gy0, mbar);  // x: 0; the quad index may be -1
 }
 
-// NQ quads per thread: TNT / NQ threads, thread (row ry, quad column q) owns the
-// quads of rows ry + i TR / NQ, i < NQ.  With NQ = 2 a block barrier spans 16
-// warps instead of 32 and each thread has two independent quads in flight.
-template <int S, int NQ>
-__global__ void __launch_bounds__(TNT / NQ, 1) k_fed_tma(Imgs I, StepTaus taus, int parity,
-                                                        const __grid_constant__ TmaMaps one)
+// NQ quads per thread: 16 RY / NQ threads, thread (row ry, quad column q) owns
+// the quads of rows ry + i RY / NQ, i < NQ.  With NQ = 2 a block barrier spans
+// half the warps and each thread has two independent quads in flight.  A block
+// of 64-row regions takes one SM (217 KB of shared memory); two blocks of
+// 32-row regions share one.
+template <int S, int NQ, int RY>
+__global__ void __launch_bounds__(t_quads<RY>() / NQ, RY == 64 ? 1 : 2)
+    k_fed_tma(Imgs I, StepTaus taus, int parity, const __grid_constant__ TmaMaps one, FedWait wt)
 {
-    constexpr int H = 2 * S, TO = TR - 2 * H, SHAPE = tma_shape<S>(), NU = kAhead + 1, NT = TNT / NQ;
-    static_assert(TO % 4 == 0 && H % 4 == 0, "whole quads in the exact interior");
+    constexpr int H = 2 * S, TOX = TR - 2 * H, TOY = RY - 2 * H, SHAPE = tma_shape<S, RY>(), NU = kAhead + 1;
+    constexpr int NT = t_quads<RY>() / NQ, TPLANE = t_plane<RY>();
+    constexpr unsigned TBYTES = t_tbytes<RY>();
+    static_assert(TOX % 4 == 0 && H % 4 == 0 && TOY > 0, "whole quads in the exact interior");
     extern __shared__ unsigned char tma_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)tma_raw + 1023) & ~(uintptr_t)1023);
-    // tensor boxes: tile j of this block in box j % kAhead (64 rows x 64 pixels x 16 B each)
-    float *planes = reinterpret_cast<float *>(base + kAhead * kTBytes);  // u planes x NU | T_xy | T_yy
+    // tensor boxes: tile j of this block in box j % kAhead (RY rows x 64 pixels x 16 B each)
+    float *planes = reinterpret_cast<float *>(base + kAhead * TBYTES);  // u planes x NU | T_xy | T_yy
     float *sxy = planes + NU * TPLANE, *syy = planes + (NU + 1) * TPLANE;
     __shared__ uint64_t mbar[kAhead];     // tile j waits on mbar[j % kAhead]
     __shared__ float stau[8];
@@ -186,10 +218,10 @@ __global__ void __launch_bounds__(TNT / NQ, 1) k_fed_tma(Imgs I, StepTaus taus, 
     bool writes[NQ];
 #pragma unroll
     for (int qd = 0; qd < NQ; ++qd) {
-        rowq[qd] = ry0 + qd * (TR / NQ);
+        rowq[qd] = ry0 + qd * (RY / NQ);
         off[qd] = (rowq[qd] + 1) * TSW + 4 * q;  // this quad in a plane
-        // the quad lies in the exact interior of every tile: rows and columns H .. H + TO - 1
-        writes[qd] = rowq[qd] >= H && rowq[qd] < H + TO && 4 * q >= H && 4 * q < H + TO;
+        // the quad lies in the exact interior of every tile: rows H .. H + TOY - 1, columns H .. H + TOX - 1
+        writes[qd] = rowq[qd] >= H && rowq[qd] < H + TOY && 4 * q >= H && 4 * q < H + TOX;
     }
     const int ntiles = I.tiles, G = gridDim.x;
     __syncthreads();
@@ -199,13 +231,13 @@ __global__ void __launch_bounds__(TNT / NQ, 1) k_fed_tma(Imgs I, StepTaus taus, 
             const int tj = blockIdx.x + j * G;
             if (tj >= ntiles) break;
             find_tile_cached(I, SHAPE, tj, tcache, sd[j], s_local[j]);
-            tma_issue<S>(sd[j], s_local[j], one, from_table, parity, planes + j * TPLANE, base + j * kTBytes,
-                         &mbar[j], &sgeo[j]);
+            tma_issue<S, RY>(sd[j], s_local[j], one, from_table, parity, planes + j * TPLANE, base + j * TBYTES,
+                             &mbar[j], &sgeo[j], wt.withhold);
         }
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += G, ++j) {
         const int bj = j % kAhead, uj = j % NU;
-        if (!tma_wait(&mbar[bj], (unsigned)(j / kAhead) & 1u)) abort_flag = 1;
+        if (!tma_wait(&mbar[bj], (unsigned)(j / kAhead) & 1u, wt.ns)) abort_flag = 1;
         __syncthreads();  // tile j has landed; every warp is past tile j - 1
         if (abort_flag) break;
         const ImgDesc &d = sd[uj];
@@ -235,7 +267,7 @@ __global__ void __launch_bounds__(TNT / NQ, 1) k_fed_tma(Imgs I, StepTaus taus, 
             // then read 8 distinct 16-byte bank groups, and every value lands in
             // its pixel's register.
             const float4 *tq =
-                reinterpret_cast<const float4 *>(base + bj * kTBytes + (size_t)rowq[qd] * (TR * 16)) + 4 * q;
+                reinterpret_cast<const float4 *>(base + bj * TBYTES + (size_t)rowq[qd] * (TR * 16)) + 4 * q;
             float4 v[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) v[i] = tq[i ^ tswz];
@@ -261,8 +293,8 @@ __global__ void __launch_bounds__(TNT / NQ, 1) k_fed_tma(Imgs I, StepTaus taus, 
             if (tid == 0 && ta < ntiles) {
                 const int ua = (j + kAhead) % NU;
                 find_tile_cached(I, SHAPE, ta, tcache, sd[ua], s_local[ua]);
-                tma_issue<S>(sd[ua], s_local[ua], one, from_table, parity, planes + ua * TPLANE,
-                             base + bj * kTBytes, &mbar[bj], &sgeo[ua]);
+                tma_issue<S, RY>(sd[ua], s_local[ua], one, from_table, parity, planes + ua * TPLANE,
+                                 base + bj * TBYTES, &mbar[bj], &sgeo[ua], wt.withhold);
             }
         };
         if (taus.n < 1) {
@@ -271,7 +303,7 @@ __global__ void __launch_bounds__(TNT / NQ, 1) k_fed_tma(Imgs I, StepTaus taus, 
         }
         if (interior) quad_steps_n<false, TSW, NQ>(su, sxy, syy, stau, taus.n, off, k, mask, uq, issue);
         else quad_steps_n<true, TSW, NQ>(su, sxy, syy, stau, taus.n, off, k, mask, uq, issue);
-        // the exact interior: rows H .. H + TO - 1, columns H .. H + TO - 1 (whole quads)
+        // the exact interior: rows H .. H + TOY - 1, columns H .. H + TOX - 1 (whole quads)
 #pragma unroll
         for (int qd = 0; qd < NQ; ++qd) {
             const int gy = sgeo[uj].gy0 + rowq[qd];
@@ -290,24 +322,24 @@ __global__ void __launch_bounds__(TNT / NQ, 1) k_fed_tma(Imgs I, StepTaus taus, 
     }
     if (abort_flag && tid == 0) {
         atomicExch(&g_fed_status, FD4_ERR_TIMEOUT);
-        // the copies still in flight (tiles j .. j + kAhead - 1), each wait again at most kWaitNs
+        // the copies still in flight (tiles j .. j + kAhead - 1), each wait again bounded
         for (int i = 0; i < kAhead; ++i) {
             const int jj = j + i;
-            if (blockIdx.x + jj * G < ntiles) tma_wait(&mbar[jj % kAhead], (unsigned)(jj / kAhead) & 1u);
+            if (blockIdx.x + jj * G < ntiles) tma_wait(&mbar[jj % kAhead], (unsigned)(jj / kAhead) & 1u, wt.ns);
         }
     }
 }
 
-// Map table writer: a chunk of per-image tensor maps passed as kernel parameters.
-constexpr int kMapChunk = 32;
+// Map table writer: a chunk of per-image tensor map sets passed as kernel parameters.
+constexpr int kMapChunk = 16;
 struct MapChunk {
     int first, n;
-    TmaMaps m[kMapChunk];
+    TmaMapSet m[kMapChunk];
 };
-__global__ void k_put_maps(const __grid_constant__ MapChunk c, TmaMaps *table)
+__global__ void k_put_maps(const __grid_constant__ MapChunk c, TmaMapSet *table)
 {
-    const int i = blockIdx.x, j = threadIdx.x;  // map i of the chunk, 16-byte word j of 24
-    if (i < c.n && j < (int)(sizeof(TmaMaps) / 16)) {
+    const int i = blockIdx.x, j = threadIdx.x;  // set i of the chunk, 16-byte word j of 48
+    if (i < c.n && j < (int)(sizeof(TmaMapSet) / 16)) {
         reinterpret_cast<uint4 *>(&table[c.first + i])[j] = reinterpret_cast<const uint4 *>(&c.m[i])[j];
         asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
     }
@@ -332,14 +364,14 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-// The three maps of one image (zero fill outside the image).
-int make_maps(const ImgDesc &d, TmaMaps *m)
+// The three maps of one image for regions of `rows` rows (zero fill outside the image).
+int make_maps(const ImgDesc &d, int rows, TmaMaps *m)
 {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return 1;
     const cuuint64_t dim2[2] = {(cuuint64_t)d.w, (cuuint64_t)d.h};
     const cuuint64_t str2[1] = {(cuuint64_t)d.pitch * 4};
-    const cuuint32_t box2[2] = {TR, TR};
+    const cuuint32_t box2[2] = {TR, (cuuint32_t)rows};
     const cuuint32_t one2[2] = {1, 1};
     if (enc(&m->u, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)d.u, dim2, str2, box2, one2,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -354,7 +386,7 @@ int make_maps(const ImgDesc &d, TmaMaps *m)
     // multiple of 4, so the last (partial) quad of a row lies within the pitch
     const cuuint64_t dimt[3] = {16, (cuuint64_t)(d.w + 3) / 4, (cuuint64_t)d.h};
     const cuuint64_t strt[2] = {64, (cuuint64_t)d.pitch * 16};
-    const cuuint32_t boxt[3] = {16, TR / 4, TR};
+    const cuuint32_t boxt[3] = {16, TR / 4, (cuuint32_t)rows};
     const cuuint32_t one3[3] = {1, 1, 1};
     if (enc(&m->ten, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)d.tensor, dimt, strt, boxt, one3,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -363,49 +395,68 @@ int make_maps(const ImgDesc &d, TmaMaps *m)
     return 0;
 }
 
-template <int S, int NQ>
+int make_map_set(const ImgDesc &d, TmaMapSet *m) { return make_maps(d, 64, &m->r64) || make_maps(d, 32, &m->r32); }
+
+template <int S, int NQ, int RY>
 int set_tma_smem()
 {
     static int attr_dev = -1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
     if (attr_dev != dev) {
-        if (cudaFuncSetAttribute(k_fed_tma<S, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(k_fed_tma<S, NQ, RY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)t_smem<RY>()) != cudaSuccess)
             return 1;
         attr_dev = dev;
     }
     return 0;
 }
 
-// Quads per thread of the TMA kernel: 2 (512 threads, the default) or
-// FD4_FED_QUADS=1 (1024 threads).
-int tma_quads()
+template <int S, int NQ, int RY>
+int launch_tma_k(const Imgs &I, const StepTaus &t, int parity, const TmaMaps &one, const FedWait &wt,
+                 cudaStream_t st)
 {
-    const char *e = getenv("FD4_FED_QUADS");
-    return (e && e[0] == '1') ? 1 : 2;
+    if (set_tma_smem<S, NQ, RY>()) return 1;
+    constexpr int NT = t_quads<RY>() / NQ;
+    const int grid = persistent_grid((const void *)k_fed_tma<S, NQ, RY>, NT, t_smem<RY>(), I.tiles);
+    k_fed_tma<S, NQ, RY><<<grid, NT, t_smem<RY>(), st>>>(I, t, parity, one, wt);
+    return cudaGetLastError() != cudaSuccess;
 }
 
-template <int S, int NQ>
-int launch_tma_k(const Imgs &I, const StepTaus &t, int parity, const TmaMaps &one, cudaStream_t st)
+template <int S>
+int launch_tma_sched(const HostBatch &B, const double *tau, int k, int parity, const FedSched &sch, const FedWait &wt,
+                     cudaStream_t st)
 {
-    if (set_tma_smem<S, NQ>()) return 1;
-    const int grid = persistent_grid((const void *)k_fed_tma<S, NQ>, TNT / NQ, kTmaSmem, I.tiles);
-    k_fed_tma<S, NQ><<<grid, TNT / NQ, kTmaSmem, st>>>(I, t, parity, one);
-    return cudaGetLastError() != cudaSuccess;
+    StepTaus t{};
+    t.n = k;
+    for (int i = 0; i < k; ++i) t.t[i] = (float)tau[i];
+    Imgs I = B.I;
+    const bool r32 = sch.rows == 32;
+    I.tiles = B.tiles[r32 ? tma_shape<S, 32>() : tma_shape<S, 64>()];
+    TmaMapSet set;
+    memset(&set, 0, sizeof(set));
+    if (!I.table && make_map_set(I.one, &set)) return 1;
+    const TmaMaps &one = r32 ? set.r32 : set.r64;
+    if (r32)
+        return sch.quads == 1 ? launch_tma_k<S, 1, 32>(I, t, parity, one, wt, st)
+                              : launch_tma_k<S, 2, 32>(I, t, parity, one, wt, st);
+    return sch.quads == 1 ? launch_tma_k<S, 1, 64>(I, t, parity, one, wt, st)
+                          : launch_tma_k<S, 2, 64>(I, t, parity, one, wt, st);
 }
 
 }  // namespace
 
-size_t tma_maps_bytes() { return sizeof(TmaMaps); }
+size_t tma_maps_bytes() { return sizeof(TmaMapSet); }
 
 int prepare_tma_kernels()
 {
-    return set_tma_smem<2, 1>() || set_tma_smem<4, 1>() || set_tma_smem<2, 2>() || set_tma_smem<4, 2>();
+    return set_tma_smem<2, 1, 64>() || set_tma_smem<4, 1, 64>() || set_tma_smem<2, 2, 64>() ||
+           set_tma_smem<4, 2, 64>() || set_tma_smem<2, 1, 32>() || set_tma_smem<4, 1, 32>() ||
+           set_tma_smem<2, 2, 32>() || set_tma_smem<4, 2, 32>();
 }
 
-// Writes the maps of the n descriptors (their maps fields point into a device
-// table) with kernels on st.
+// Writes the map sets of the n descriptors (their maps fields point into a
+// device table) with kernels on st.
 int launch_put_maps(const ImgDesc *h_descs, int n, void *d_table, cudaStream_t st)
 {
     thread_local static MapChunk c;  // 12 KB: kept off the stack
@@ -413,8 +464,8 @@ int launch_put_maps(const ImgDesc *h_descs, int n, void *d_table, cudaStream_t s
         c.first = first;
         c.n = n - first < kMapChunk ? n - first : kMapChunk;
         for (int i = 0; i < c.n; ++i)
-            if (make_maps(h_descs[first + i], &c.m[i])) return 1;
-        k_put_maps<<<c.n, (int)(sizeof(TmaMaps) / 16), 0, st>>>(c, (TmaMaps *)d_table);
+            if (make_map_set(h_descs[first + i], &c.m[i])) return 1;
+        k_put_maps<<<c.n, (int)(sizeof(TmaMapSet) / 16), 0, st>>>(c, (TmaMapSet *)d_table);
     }
     return cudaGetLastError() != cudaSuccess;
 }
@@ -423,21 +474,13 @@ int launch_put_maps(const ImgDesc *h_descs, int n, void *d_table, cudaStream_t s
 // (I.table) take each image's maps from its descriptor; a single inline image
 // gets its maps as a kernel parameter.
 template <int S>
-int launch_fed_tma(const HostBatch &B, const double *tau, int k, int parity, cudaStream_t st)
+int launch_fed_tma(const HostBatch &B, const double *tau, int k, int parity, const FedSched &sch, cudaStream_t st)
 {
-    StepTaus t{};
-    t.n = k;
-    for (int i = 0; i < k; ++i) t.t[i] = (float)tau[i];
-    Imgs I = B.I;
-    I.tiles = B.tiles[tma_shape<S>()];
-    TmaMaps one;
-    memset(&one, 0, sizeof(one));
-    if (!I.table && make_maps(I.one, &one)) return 1;
-    return tma_quads() == 2 ? launch_tma_k<S, 2>(I, t, parity, one, st) : launch_tma_k<S, 1>(I, t, parity, one, st);
+    return launch_tma_sched<S>(B, tau, k, parity, sch, FedWait{kWaitNs, 0}, st);
 }
 
-template int launch_fed_tma<2>(const HostBatch &, const double *, int, int, cudaStream_t);
-template int launch_fed_tma<4>(const HostBatch &, const double *, int, int, cudaStream_t);
+template int launch_fed_tma<2>(const HostBatch &, const double *, int, int, const FedSched &, cudaStream_t);
+template int launch_fed_tma<4>(const HostBatch &, const double *, int, int, const FedSched &, cudaStream_t);
 
 }  // namespace fd4
 
@@ -450,4 +493,35 @@ extern "C" int fd4_device_status(int *status, int reset)
         if (cudaMemcpyToSymbol(fd4::g_fed_status, &zero, sizeof(int)) != cudaSuccess) return FD4_ERR_CUDA;
     }
     return FD4_OK;
+}
+
+extern "C" int fd4_selftest_fed_wait_timeout(float *d_u, int w, int h, int pitch, const float *d_tensor,
+                                             void *d_ws, size_t ws_bytes, int *status, fd4_stream_t stream)
+{
+    using namespace fd4;
+    int rc;
+    if (!status || !d_tensor) return FD4_ERR_BAD_ARG;
+    if ((rc = check_image(d_u, w, h, pitch)) != FD4_OK) return rc;
+    if ((uintptr_t)d_tensor & 15u) return FD4_ERR_ALIGN;
+    if (!d_ws || ((uintptr_t)d_ws & 255u)) return d_ws ? FD4_ERR_ALIGN : FD4_ERR_BAD_ARG;
+    if (ws_bytes < ws_fed_bytes(h, pitch)) return FD4_ERR_WS_TOO_SMALL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int zero = 0;
+    if (cudaStreamSynchronize(st) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_fed_status, &zero, sizeof(int)) != cudaSuccess)
+        return FD4_ERR_CUDA;
+    ImgDesc d{};
+    d.u = d_u;
+    d.tmp = (float *)((char *)d_ws + kHeaderBytes);
+    d.tensor = (float4 *)d_tensor;
+    d.w = w;
+    d.h = h;
+    d.pitch = pitch;
+    const double tau[2] = {0.01, 0.01};
+    // every wait of the launch gives up after 10 ms: the copies are withheld,
+    // so the tile's barrier never completes; nothing is ever in flight
+    if (launch_tma_sched<2>(single_batch(d), tau, 2, 0, kDefaultSched, FedWait{10000000ull, 1}, st) ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return FD4_ERR_CUDA;
+    return fd4_device_status(status, 1);
 }

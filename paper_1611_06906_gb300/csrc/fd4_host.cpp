@@ -29,6 +29,8 @@ extern "C" void fd4_default_params(fd4_params *p)
     p->model = FD4_MODEL_MAFOD;
     p->ifod_sigma = 1.0f;
     p->fed_steps_per_launch = 0;
+    p->fed_tile_rows = 0;
+    p->fed_quads_per_thread = 0;
 }
 
 extern "C" const char *fd4_strerror(int s)
@@ -398,8 +400,38 @@ extern "C" int fd4_fed_cycle(float *d_u, int w, int h, int pitch, const float *d
     for (int i = 0; i < n; ++i)
         if (!(h_tau[i] > 0.0) || !(h_tau[i] < 1e6)) return FD4_ERR_BAD_ARG;
     if ((rc = ws_ok(d_ws, ws_bytes, ws_fed_bytes(h, pitch))) != FD4_OK) return rc;
-    return cuda_status(launch_fed_cycle(d_u, w, h, pitch, d_tensor, h_tau, n, boundary, (char *)d_ws,
-                                        (cudaStream_t)stream));
+    return cuda_status(launch_fed_cycle(d_u, w, h, pitch, d_tensor, h_tau, n, boundary, kDefaultSched,
+                                        (char *)d_ws, (cudaStream_t)stream));
+}
+
+static int check_sched(int steps, int rows, int quads)
+{
+    if (steps < 0 || steps > 4) return FD4_ERR_BAD_ARG;
+    if (rows != 0 && rows != 32 && rows != 64) return FD4_ERR_BAD_ARG;
+    if (quads < 0 || quads > 2) return FD4_ERR_BAD_ARG;
+    return FD4_OK;
+}
+
+extern "C" int fd4_fed_cycle_sched(float *d_u, int w, int h, int pitch, const float *d_tensor,
+                                   const double *h_tau, int n, int boundary, int steps_per_launch, int tile_rows,
+                                   int quads_per_thread, void *d_ws, size_t ws_bytes, fd4_stream_t stream)
+{
+    int rc;
+    if ((rc = check_sched(steps_per_launch, tile_rows, quads_per_thread)) != FD4_OK) return rc;
+    if ((rc = check_image(d_u, w, h, pitch)) != FD4_OK) return rc;
+    if (!d_tensor || !h_tau || n < 1 || n > FD4_MAX_FED_STEPS) return FD4_ERR_BAD_ARG;
+    if ((uintptr_t)d_tensor & 15u) return FD4_ERR_ALIGN;
+    if (boundary != FD4_BC_NATURAL && boundary != FD4_BC_PERIODIC) return FD4_ERR_BAD_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!(h_tau[i] > 0.0) || !(h_tau[i] < 1e6)) return FD4_ERR_BAD_ARG;
+    if ((rc = ws_ok(d_ws, ws_bytes, ws_fed_bytes(h, pitch))) != FD4_OK) return rc;
+    fd4_params p;
+    fd4_default_params(&p);
+    p.fed_steps_per_launch = steps_per_launch;
+    p.fed_tile_rows = tile_rows;
+    p.fed_quads_per_thread = quads_per_thread;
+    return cuda_status(launch_fed_cycle(d_u, w, h, pitch, d_tensor, h_tau, n, boundary, resolve_sched(p),
+                                        (char *)d_ws, (cudaStream_t)stream));
 }
 
 // The filter schedule on a batch: selection (unless given), input copy, then M
@@ -427,7 +459,7 @@ static int enqueue_filter(const HostBatch &B, const float *h_sigmas, int n_sigma
                           const double *tau, int n, int M, int sigma_given, cudaStream_t st,
                           int stages = FD4_STAGES_ALL)
 {
-    const int steps = p.fed_steps_per_launch > 0 ? p.fed_steps_per_launch : default_steps_per_launch();
+    const FedSched sch = resolve_sched(p);
     const bool mafod = p.model == FD4_MODEL_MAFOD;  // IFOD selects no scales
     if (mafod && (stages & FD4_STAGE_SELECT) && !sigma_given && launch_select_batch(B, h_sigmas, n_sigma, p, st))
         return FD4_ERR_CUDA;
@@ -445,14 +477,14 @@ static int enqueue_filter(const HostBatch &B, const float *h_sigmas, int n_sigma
         if (k > 0 && reselect && post && launch_postprocess_batch(B, h_sigmas, n_sigma, p, st))
             return FD4_ERR_CUDA;
         if ((stages & FD4_STAGE_TENSOR) && launch_cycle_tensor(B, h_sigmas, n_sigma, p, st)) return FD4_ERR_CUDA;
-        if ((stages & FD4_STAGE_FED) && launch_fed_batch(B, tau, n, p.boundary, steps, st)) return FD4_ERR_CUDA;
+        if ((stages & FD4_STAGE_FED) && launch_fed_batch(B, tau, n, p.boundary, sch, st)) return FD4_ERR_CUDA;
     }
     return FD4_OK;
 }
 
 static int check_steps(const fd4_params &p)
 {
-    return (p.fed_steps_per_launch < 0 || p.fed_steps_per_launch > 4) ? FD4_ERR_BAD_ARG : FD4_OK;
+    return check_sched(p.fed_steps_per_launch, p.fed_tile_rows, p.fed_quads_per_thread);
 }
 
 extern "C" int fd4_filter(const float *d_in, float *d_out, int w, int h, int pitch,
@@ -675,7 +707,7 @@ static int enqueue_batch_two_streams(const fd4_image *imgs, int n_images, const 
     batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B0, split, &B1, post);
     const bool reselect = sel && p.reselect_each_cycle;
     if (put_tables(descs, n_images, B0, d_ws, reselect, s0)) return FD4_ERR_CUDA;
-    const int steps = p.fed_steps_per_launch > 0 ? p.fed_steps_per_launch : default_steps_per_launch();
+    const FedSched steps = resolve_sched(p);
     if (cudaEventRecord(ev_fork, s0) != cudaSuccess || cudaStreamWaitEvent(s1, ev_fork, 0) != cudaSuccess)
         return FD4_ERR_CUDA;
     set_grid_divisor(2);
@@ -837,10 +869,10 @@ extern "C" int fd4_graph_destroy(fd4_graph g)
 
 extern "C" int fd4_autotune_batched(const fd4_image *h_imgs, int n_images, const float *h_sigmas, int n_sigma,
                                     const fd4_params *params, double T, int M, int n_in, void *d_ws,
-                                    size_t ws_bytes, fd4_stream_t stream, int *best_steps_per_launch,
-                                    float *times_ms)
+                                    size_t ws_bytes, fd4_stream_t stream, fd4_fed_schedule *best,
+                                    fd4_fed_schedule *tried)
 {
-    if (!best_steps_per_launch) return FD4_ERR_BAD_ARG;
+    if (!best) return FD4_ERR_BAD_ARG;
     fd4_params p;
     resolve_params(params, &p);
     std::vector<double> tau;
@@ -856,33 +888,37 @@ extern "C" int fd4_autotune_batched(const fd4_image *h_imgs, int n_images, const
     if ((p.model == FD4_MODEL_MAFOD && launch_select_batch(B, h_sigmas, n_sigma, p, st)) ||
         launch_copy_in_batch(B, st) || launch_cycle_tensor(B, h_sigmas, n_sigma, p, st))
         return FD4_ERR_CUDA;
+    // the candidates: one launch per step, the scalar kernel with 3 steps, and
+    // the TMA kernel with 2 or 4 steps on 64- or 32-row regions, 1 or 2 quads
+    // per thread (the periodic boundary runs the scalar kernel for 2 and 4)
+    const int cand[FD4_AUTOTUNE_CANDIDATES][3] = {{1, 0, 0},  {2, 64, 2}, {2, 64, 1}, {2, 32, 2}, {2, 32, 1},
+                                                  {3, 0, 0},  {4, 64, 2}, {4, 64, 1}, {4, 32, 2}, {4, 32, 1}};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return FD4_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
         cudaEventDestroy(e0);
         return FD4_ERR_CUDA;
     }
-    float best = 0.0f;
-    int arg = 2;
     rc = FD4_OK;
-    for (int S = 1; S <= 4 && rc == FD4_OK; ++S) {
-        // one untimed pass, then the timed one
-        if (launch_fed_batch(B, tau.data(), n, p.boundary, S, st) || cudaEventRecord(e0, st) != cudaSuccess ||
-            launch_fed_batch(B, tau.data(), n, p.boundary, S, st) || cudaEventRecord(e1, st) != cudaSuccess ||
+    fd4_fed_schedule top{};
+    for (int c = 0; c < FD4_AUTOTUNE_CANDIDATES && rc == FD4_OK; ++c) {
+        const FedSched sch{cand[c][0], cand[c][1] ? cand[c][1] : kDefaultSched.rows,
+                           cand[c][2] ? cand[c][2] : kDefaultSched.quads};
+        // one untimed cycle, then the timed one
+        if (launch_fed_batch(B, tau.data(), n, p.boundary, sch, st) || cudaEventRecord(e0, st) != cudaSuccess ||
+            launch_fed_batch(B, tau.data(), n, p.boundary, sch, st) || cudaEventRecord(e1, st) != cudaSuccess ||
             cudaEventSynchronize(e1) != cudaSuccess) {
             rc = FD4_ERR_CUDA;
             break;
         }
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (times_ms) times_ms[S - 1] = ms;
-        if (S == 1 || ms < best) {
-            best = ms;
-            arg = S;
-        }
+        const fd4_fed_schedule r{cand[c][0], cand[c][1], cand[c][2], ms};
+        if (tried) tried[c] = r;
+        if (c == 0 || ms < top.ms) top = r;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc == FD4_OK) *best_steps_per_launch = arg;
+    if (rc == FD4_OK) *best = top;
     return rc;
 }

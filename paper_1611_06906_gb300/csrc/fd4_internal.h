@@ -46,9 +46,9 @@ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 enum TileShape {
     SHAPE_SWEEP = 0,
     SHAPE_SMALL = 1,
-    SHAPE_FUSE2 = 2,
-    SHAPE_FUSE3 = 3,
-    SHAPE_FUSE4 = 4,
+    SHAPE_FUSE2 = 2,   // 64 x 32 regions, (64 - 4S) x (32 - 4S) outputs, S = 2 (also the TMA kernel's 32-row form)
+    SHAPE_FUSE3 = 3,   //   ... S = 3
+    SHAPE_FUSE4 = 4,   //   ... S = 4
     SHAPE_SEG = 5,
     SHAPE_Q64_2 = 6,   // quad FED kernel on 64 x 64 regions: (64 - 4S)^2 outputs, S = 2
     SHAPE_Q64_4 = 7,   //   ... S = 4
@@ -271,9 +271,18 @@ int launch_postprocess_batch(const HostBatch &B, const float *h_sigmas, int n_si
 // launch per scale (fd4_tensor.cu); B.max_s2 must be cleared first.
 int launch_select_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
                          cudaStream_t st);
-// n FED steps on every image; the result ends in ImgDesc::u.  steps_per_launch:
-// 1 = one launch per step (k_fed_step), 2..4 = k_fed_fused<S>.
-int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundary, int steps_per_launch,
+// Schedule of the FED kernels (no effect on the result beyond FP32 rounding):
+// explicit steps per launch (1: k_fed_step; 2, 4: the TMA quad kernel under the
+// natural boundary; 3 and the periodic boundary: k_fed_fused<S>), and for the
+// TMA kernel its region height (64 or 32 rows of 64 columns) and the row
+// quads each thread owns (1 or 2).
+struct FedSched {
+    int steps, rows, quads;
+};
+constexpr FedSched kDefaultSched = {2, 64, 2};
+FedSched resolve_sched(const fd4_params &p);  // zero fields of p take the default
+// n FED steps on every image; the result ends in ImgDesc::u.
+int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundary, const FedSched &sch,
                      cudaStream_t st);
 int launch_select_tiles(const ImgDesc &d, const int *list, const int *count, const float *h_sigmas, int n_sigma,
                         const fd4_params &p, cudaStream_t st);
@@ -281,16 +290,16 @@ int launch_select_tiles(const ImgDesc &d, const int *list, const int *count, con
 int prepare_scale_kernels();
 int prepare_tensor_kernels();
 int prepare_fed_kernels();
-int default_steps_per_launch();
 int launch_copy_in_batch(const HostBatch &B, cudaStream_t st);
 int launch_put_descs(const ImgDesc *h_descs, int n, ImgDesc *d_table, cudaStream_t st);
 // TMA staging of the FED kernel (fd4_fed_tma.cu): bytes of one image's maps, the
 // writer of a batch's map table (each descriptor's maps field points into it),
-// one launch of k <= S steps, and the kernels' shared-memory attributes.
+// one launch of k <= S steps (region height and quads per thread from sch),
+// and the kernels' shared-memory attributes.
 size_t tma_maps_bytes();
 int launch_put_maps(const ImgDesc *h_descs, int n, void *d_table, cudaStream_t st);
 template <int S>
-int launch_fed_tma(const HostBatch &B, const double *tau, int k, int parity, cudaStream_t st);
+int launch_fed_tma(const HostBatch &B, const double *tau, int k, int parity, const FedSched &sch, cudaStream_t st);
 int prepare_tma_kernels();
 
 // Single-image launchers used by the per-image entry points.
@@ -301,6 +310,6 @@ int launch_tensor(const float *d_u, int w, int h, int pitch, const uint8_t *d_id
                   const float *h_sigmas, int n_sigma, const fd4_params &p, float *d_tensor,
                   char *ws, cudaStream_t st);
 int launch_fed_cycle(float *d_u, int w, int h, int pitch, const float *d_tensor,
-                     const double *h_tau, int n, int boundary, char *ws, cudaStream_t st);
+                     const double *h_tau, int n, int boundary, const FedSched &sch, char *ws, cudaStream_t st);
 
 }  // namespace fd4

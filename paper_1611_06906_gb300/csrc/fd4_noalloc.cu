@@ -104,7 +104,8 @@ extern "C" int fd4_fed_cycle_noalloc(float *d_u, int w, int h, int pitch, const 
     if ((rc = scratch_for_current_device(&ws)) != FD4_OK) return rc;
     // The scratch plane is written in full before it is read, so nothing in it
     // needs clearing between calls.
-    if (fd4::launch_fed_cycle(d_u, w, h, pitch, d_tensor, h_tau, n, boundary, ws, (cudaStream_t)stream))
+    if (fd4::launch_fed_cycle(d_u, w, h, pitch, d_tensor, h_tau, n, boundary, fd4::kDefaultSched, ws,
+                              (cudaStream_t)stream))
         return FD4_ERR_CUDA;
     return FD4_OK;
 }

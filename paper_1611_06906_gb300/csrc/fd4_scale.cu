@@ -10,12 +10,11 @@
 // refilled four taps at a time (one 16-byte shared load in the row pass), so
 // the inner loops are almost pure FMA.  The work is FP32-FMA bound: about
 // 3 (2R+4)(1 + (2R+8)/64) + 5 (2R+4) FMAs per pixel and scale, R = ceil(4 sigma)
-// rounded up to a multiple of 4.  The tensor build needs each pixel's
-// derivatives at its own scale only: the tile's pixels are first grouped by
-// selected scale, and for each scale the row pass covers only the rows and
-// 8-column chunks those pixels reach, the column pass only those pixels.
+// rounded up to a multiple of 4.  It serves the selection restricted to a
+// list of tiles (the learned selector's fallback); whole images are selected by
+// the per-scale strip kernels of fd4_tensor.cu, which compute the same sums in
+// the same order.
 #include <cstdint>
-#include <cstdlib>
 
 #include "fd4_internal.h"
 
@@ -77,8 +76,6 @@ __device__ __forceinline__ int mirror(int i, int n)
     return m < n ? m : p - 1 - m;
 }
 
-enum { OUT_SELECT = 0, OUT_TENSOR = 1 };
-
 // Column pass of one field over the 12-row register window: acc_a += wa * field
 // (and acc_b += wb * field when TWO), VC outputs down one column.
 template <bool TWO>
@@ -116,17 +113,11 @@ __device__ __forceinline__ void column_pass(const float *src, const float *wa, c
     }
 }
 
-template <int OUT>
-__global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, float inv2b2, int mode, int grad_sq)
+__global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, float inv2b2, int mode)
 {
     extern __shared__ __align__(16) float smem[];
     __shared__ ImgDesc sd;
     __shared__ int s_local;
-    // tensor mode: the tile's pixels grouped by selected scale, (py << 5) | px,
-    // and per scale the count, list start, row range and 8-column chunks used
-    __shared__ unsigned short plist[OUT == OUT_TENSOR ? TX * TY : 1];
-    __shared__ int pcnt[kMaxSweep], pstart[kMaxSweep], prow0[kMaxSweep], prow1[kMaxSweep];
-    __shared__ unsigned pchunk[kMaxSweep];
     const int Rmax = taps.Rmax;
     const int S = sweep_in_stride(Rmax);
     const int rows = sweep_rows(Rmax);
@@ -141,17 +132,11 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     __syncthreads();   // the previous tile is done with shared memory
     if (tid == 0) find_tile(I, SHAPE_SWEEP, t, sd, s_local);
-    if (OUT == OUT_TENSOR && tid < kMaxSweep) {
-        pcnt[tid] = 0;
-        prow0[tid] = TY;
-        prow1[tid] = -1;
-        pchunk[tid] = 0u;
-    }
     __syncthreads();
     const int w = sd.w, h = sd.h, pitch = sd.pitch;
     const int tiles_x = (w + TX - 1) / TX;
     const int x0 = (s_local % tiles_x) * TX, y0 = (s_local / tiles_x) * TY;
-    const float *img = OUT == OUT_SELECT ? sd.in : sd.u;
+    const float *img = sd.in;
     for (int ry = warp; ry < rows; ry += NT / 32) {
         const float *src = img + (size_t)mirror(y0 - Rmax + ry, h) * pitch;
         for (int rx = lane; rx < in_w; rx += 32) tin[ry * S + rx] = __ldg(src + mirror(x0 - Rmax + rx, w));
@@ -159,74 +144,20 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
 
     const int ox = tid & 31, oy0 = (tid >> 5) * VC;
     const int gx = x0 + ox;
-    // Tensor mode: group the tile's pixels by selected scale.  In a warp, the
-    // VC rows of this thread group are one tile row each, so the lanes that
-    // share a scale in row j are found with one match and counted with one
-    // shared atomic; the rank among them gives the slot in the scale's list.
-    if (OUT == OUT_TENSOR) {
-        int my_local[VC], my_pos[VC];
-#pragma unroll
-        for (int j = 0; j < VC; ++j) {
-            const int gy = y0 + oy0 + j;
-            const int id = (gx < w && gy < h) ? (int)sd.idx[(size_t)gy * pitch + gx] : -1;
-            if (id >= 0 && taps.s0 == 0 && id >= taps.K_total)   // index outside the set: N = 0
-                sd.nfield[(size_t)gy * pitch + gx] = make_float4(0.f, 0.f, 0.f, 0.f);
-            const int local = id - taps.s0;
-            my_local[j] = (id >= 0 && local >= 0 && local < taps.K) ? local : -1;
-            const unsigned peers = __match_any_sync(0xffffffffu, my_local[j]);
-            const int leader = __ffs(peers) - 1;
-            int base = 0;
-            if (lane == leader && my_local[j] >= 0) {
-                const int s = my_local[j];
-                base = atomicAdd(&pcnt[s], __popc(peers));
-                atomicMin(&prow0[s], oy0 + j);
-                atomicMax(&prow1[s], oy0 + j);
-                const unsigned ch = ((peers & 0x000000FFu) ? 1u : 0u) | ((peers & 0x0000FF00u) ? 2u : 0u) |
-                                    ((peers & 0x00FF0000u) ? 4u : 0u) | ((peers & 0xFF000000u) ? 8u : 0u);
-                atomicOr(&pchunk[s], ch);
-            }
-            my_pos[j] = __shfl_sync(0xffffffffu, base, leader) + __popc(peers & ((1u << lane) - 1u));
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int acc = 0;
-            for (int s = 0; s < taps.K; ++s) {
-                pstart[s] = acc;
-                acc += pcnt[s];
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < VC; ++j)
-            if (my_local[j] >= 0) plist[pstart[my_local[j]] + my_pos[j]] = (unsigned short)(((oy0 + j) << 5) | ox);
-    }
     __syncthreads();
 
     float bmax = 0.0f;
     for (int s = 0; s < taps.K; ++s) {
-        if (OUT == OUT_TENSOR && pcnt[s] == 0) continue;   // block-uniform
         const int R = taps.R[s];
         const int L = 2 * R + 4, nch = L / 4;
         const int off = Rmax - R;
         const float *w0 = wt + taps.off[s], *w1 = w0 + L, *w2 = w1 + L;
 
-        // Row pass: three fields along x on staged rows [off + r0, off + r0 + nrows).
-        // Selection needs every row and column of the tile; the tensor build
-        // only the rows within reach of a pixel of this scale and the 8-column
-        // chunks that hold one.
-        int r0 = 0, nrows = TY + 2 * R + 4;
-        unsigned cmask = 0xFu;
-        if (OUT == OUT_TENSOR) {
-            r0 = prow0[s];
-            nrows = prow1[s] - r0 + L;
-            cmask = pchunk[s];
-        }
-        const int ncx = __popc(cmask);
-        for (int u = tid; u < nrows * ncx; u += NT) {
-            int q = u / ncx, cx = u - q * ncx;
-            unsigned m = cmask;
-            for (; cx > 0; --cx) m &= m - 1u;
-            const int sy = off + r0 + q, xo = (__ffs(m) - 1) * VR;
+        // Row pass: three fields along x on staged rows [off, off + TY + 2R + 4),
+        // four 8-column chunks per row.
+        const int nrows = TY + 2 * R + 4;
+        for (int u = tid; u < nrows * (TX / VR); u += NT) {
+            const int q = u / (TX / VR), sy = off + q, xo = (u - q * (TX / VR)) * VR;
             const float *src = tin + sy * S + xo + off;
             float win[VR + 4];
             {
@@ -273,44 +204,6 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
         }
         __syncthreads();
 
-        if (OUT == OUT_TENSOR) {
-            // Column pass only for the pixels whose selected scale is this one:
-            // the block walks the scale's list, one pixel per thread, and
-            // evaluates the five derivatives as direct tap sums.
-            const int cnt = pcnt[s];
-            const unsigned short *lst = plist + pstart[s];
-            for (int e = tid; e < cnt; e += NT) {
-                const int entry = lst[e];
-                const int px = entry & 31, py = entry >> 5;
-                const float *c0 = trow + (py + off) * RS + px;   // field 0: smoothed along x
-                const float *c1 = c0 + rows * RS;                 // field 1: d/dx
-                const float *c2 = c1 + rows * RS;                 // field 2: d2/dx2
-                float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
-                for (int ch = 0; ch < nch; ++ch) {
-                    const float4 A = *reinterpret_cast<const float4 *>(w0 + 4 * ch);
-                    const float4 B = *reinterpret_cast<const float4 *>(w1 + 4 * ch);
-                    const float4 C = *reinterpret_cast<const float4 *>(w2 + 4 * ch);
-                    const float a4[4] = {A.x, A.y, A.z, A.w}, b4[4] = {B.x, B.y, B.z, B.w};
-                    const float c4[4] = {C.x, C.y, C.z, C.w};
-#pragma unroll
-                    for (int ii = 0; ii < 4; ++ii) {
-                        const int k = (4 * ch + ii) * RS;
-                        const float v0 = c0[k], v1 = c1[k], v2 = c2[k];
-                        sy = fmaf(b4[ii], v0, sy);
-                        syy = fmaf(c4[ii], v0, syy);
-                        sx = fmaf(a4[ii], v1, sx);
-                        sxy = fmaf(b4[ii], v1, sxy);
-                        sxx = fmaf(a4[ii], v2, sxx);
-                    }
-                }
-                const float g2 = fmaf(sx, sx, sy * sy);
-                const float g = grad_sq ? g2 : sqrtf(g2);
-                const float f = 1.0f / sqrtf(1.0f + g);
-                sd.nfield[(size_t)(y0 + py) * pitch + x0 + px] = make_float4(f * sxx, f * sxy, f * syy, 0.0f);
-            }
-            __syncthreads();   // trow is rewritten by the next scale's row pass
-            continue;
-        }
         // Column pass: tile column ox, tile rows oy0 .. oy0 + VC - 1.
         const float *col = trow + (oy0 + off) * RS + ox;
         float uxx[VC], uxy[VC], uyy[VC];
@@ -324,7 +217,7 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
             const int gy = y0 + oy0 + j;
             if (gx >= w || gy >= h) continue;
             const float a = uxx[j], b = uxy[j], d = uyy[j];
-            if (OUT == OUT_SELECT) {
+            {
                 // eigenvalues of H (sigma^(2 gamma) cancels in R_B and the sign
                 // test; S^2 picks it up as sigma^(4 gamma))
                 const float m = 0.5f * (a + d);
@@ -346,7 +239,7 @@ __global__ void __launch_bounds__(NT, 2) k_scale_sweep(Imgs I, SweepTaps taps, f
         }
     }
 
-    if (OUT == OUT_SELECT) {
+    {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
         if (lane == 0 && bmax > 0.0f) atomicMax(sd.max_s2, __float_as_uint(bmax));
@@ -617,11 +510,7 @@ int set_sweep_smem(size_t bytes)
         done_dev = dev;
     }
     if (bytes <= done) return 0;
-    if (cudaFuncSetAttribute(k_scale_sweep<OUT_SELECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-        cudaSuccess)
-        return 1;
-    if (cudaFuncSetAttribute(k_scale_sweep<OUT_TENSOR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(k_scale_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
         return 1;
     done = bytes;
     return 0;
@@ -672,8 +561,8 @@ int prepare_scale_kernels()
            set_finish_smem<6>() || set_finish_smem<7>() || set_finish_smem<8>() || prepare_tensor_kernels();
 }
 
-static int sweep_launch(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p, bool tensor,
-                        cudaStream_t st)
+// Selection planes by the multi-scale tile sweep over B's tile list.
+static int sweep_launch(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p, cudaStream_t st)
 {
     thread_local static SweepTaps taps;  // 25 KB: kept off the stack
     Imgs I = B.I;
@@ -684,13 +573,8 @@ static int sweep_launch(const HostBatch &B, const float *h_sigmas, int n_sigma, 
         if (pack_taps(h_sigmas, n_sigma, s0, K, p.gamma, &taps)) return 1;
         const size_t smem = sweep_smem_bytes(taps.Rmax, taps.wfloats);
         if (set_sweep_smem(smem)) return 1;
-        if (tensor) {
-            const int grid = persistent_grid((const void *)k_scale_sweep<OUT_TENSOR>, NT, smem, I.tiles);
-            k_scale_sweep<OUT_TENSOR><<<grid, NT, smem, st>>>(I, taps, inv2b2, p.mode, p.grad_norm_squared);
-        } else {
-            const int grid = persistent_grid((const void *)k_scale_sweep<OUT_SELECT>, NT, smem, I.tiles);
-            k_scale_sweep<OUT_SELECT><<<grid, NT, smem, st>>>(I, taps, inv2b2, p.mode, p.grad_norm_squared);
-        }
+        const int grid = persistent_grid((const void *)k_scale_sweep, NT, smem, I.tiles);
+        k_scale_sweep<<<grid, NT, smem, st>>>(I, taps, inv2b2, p.mode);
     }
     return cudaGetLastError() != cudaSuccess;
 }
@@ -699,12 +583,11 @@ int launch_select_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, 
                         cudaStream_t st)
 {
     if (cudaMemsetAsync(B.max_s2, 0, sizeof(unsigned) * (size_t)B.n_max_s2, st) != cudaSuccess) return 1;
-    // selection planes: the per-scale strip kernels (fd4_tensor.cu), or the
-    // multi-scale tile sweep (same result) for a subset of tiles (I.list, which
-    // the strips cannot walk) or with FD4_SELECT_SWEEP=1
-    const char *e = getenv("FD4_SELECT_SWEEP");
-    if (B.I.list || (e && e[0] == '1')) {
-        if (sweep_launch(B, h_sigmas, n_sigma, p, false, st)) return 1;
+    // selection planes: the per-scale strip kernels (fd4_tensor.cu) on whole
+    // images, the multi-scale tile sweep (same sums, same order) on a list of
+    // tiles (I.list), which the strips cannot walk
+    if (B.I.list) {
+        if (sweep_launch(B, h_sigmas, n_sigma, p, st)) return 1;
     } else if (launch_select_strips(B, h_sigmas, n_sigma, p, st)) {
         return 1;
     }
@@ -718,14 +601,8 @@ int launch_select_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, 
 int launch_tensor_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
                         cudaStream_t st)
 {
-    // N at the selected scales: the per-scale strip kernels (fd4_tensor.cu),
-    // or with FD4_TENSOR_SWEEP=1 the multi-scale tile sweep (same result).
-    const char *e = getenv("FD4_TENSOR_SWEEP");
-    if (B.I.list || (e && e[0] == '1')) {
-        if (sweep_launch(B, h_sigmas, n_sigma, p, true, st)) return 1;
-    } else if (launch_tensor_strips(B, h_sigmas, n_sigma, p, st)) {
-        return 1;
-    }
+    // N at the selected scales: the per-scale strip kernels (fd4_tensor.cu)
+    if (launch_tensor_strips(B, h_sigmas, n_sigma, p, st)) return 1;
     RhoTaps rt;
     if (rho_taps(p.rho, &rt) != FD4_OK) return 1;
     int rc = 1;

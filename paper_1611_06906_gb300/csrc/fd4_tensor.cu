@@ -14,7 +14,8 @@
 // selected scale is this one.  The radius R is a template parameter: every tap
 // loop is unrolled and the weights are kernel parameters (constant-bank
 // operands of the FMAs).  The arithmetic and summation order are those of the
-// multi-scale sweep in fd4_scale.cu, so both give identical results.
+// multi-scale sweep in fd4_scale.cu (which selects on tile lists), so both give
+// identical results.
 //
 // The same kernels run the selection (a dense column pass and the vesselness
 // factors of every pixel at each scale) and the IFOD comparator of Eq. 2 (a
@@ -22,7 +23,6 @@
 // g = 1 / (1 + |H(u_sigma)|_F^2 / lambda^2)).
 #include <cmath>
 #include <cstdint>
-#include <cstdlib>
 
 #include "fd4_internal.h"
 
@@ -126,47 +126,11 @@ __device__ __forceinline__ void st_stage(float *tin, const float *img, int w, in
 }
 
 // Row pass of staged rows 0 .. n - 1 into buffer rows b0 .. b0 + n - 1: thread
-// (row tid / 8, columns 4 (tid % 8) .. + 3), three fields.
-template <int R>
-__device__ __forceinline__ void st_rows(const StripTaps<R> &tp, const float *tin, float *trow, int b0, int n)
-{
-    constexpr int SW = st_sw<R>(), NB = ST_CH + 2 * R;
-    const int tid = threadIdx.x;
-    const int r = tid >> 3, xo = (tid & 7) * 4;
-    if (r < n) {
-        const float *src = tin + r * SW + xo;
-        float a0[4], a1[4], a2[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) a0[j] = a1[j] = a2[j] = 0.0f;
-#pragma unroll
-        for (int m4 = 0; m4 < (2 * R + 4 + 3) / 4; ++m4) {
-            const float4 v = *reinterpret_cast<const float4 *>(src + 4 * m4);
-            const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int i = 4 * m4 + e - j;  // tap index of output j
-                    if (i >= 0 && i <= 2 * R) {
-                        a0[j] = fmaf(tp.w0[i], vv[e], a0[j]);
-                        a1[j] = fmaf(tp.w1[i], vv[e], a1[j]);
-                        a2[j] = fmaf(tp.w2[i], vv[e], a2[j]);
-                    }
-                }
-            }
-        }
-        float *d = trow + (b0 + r) * ST_RS + xo;
-        *reinterpret_cast<float4 *>(d) = make_float4(a0[0], a0[1], a0[2], a0[3]);
-        *reinterpret_cast<float4 *>(d + NB * ST_RS) = make_float4(a1[0], a1[1], a1[2], a1[3]);
-        *reinterpret_cast<float4 *>(d + 2 * NB * ST_RS) = make_float4(a2[0], a2[1], a2[2], a2[3]);
-    }
-}
-
-// st_rows with packed pair FMAs (two FP32 lanes per instruction): outputs
-// (0, 1) and (2, 3) of a thread form pairs that take one input value with the
-// tap pair (w[i], w[i - 1]).  Each output receives the same products in the
-// same order as in st_rows (plus exact zeros at the ends), so the results are
-// identical.
+// (row tid / 8, columns 4 (tid % 8) .. + 3), three fields, in packed pair FMAs
+// (two FP32 lanes per instruction): outputs (0, 1) and (2, 3) of a thread form
+// pairs that take one input value with the tap pair (w[i], w[i - 1]).  Each
+// output receives the products w[i] u[x + i - R] in increasing i (plus exact
+// zeros at the ends), the order of the multi-scale sweep in fd4_scale.cu.
 template <int R>
 __device__ __forceinline__ void st_rows2(const StripTaps<R> &tp, const float *tin, float *trow, int b0, int n)
 {
@@ -248,7 +212,7 @@ __device__ __forceinline__ void seg_geo(const ImgDesc &d, int local, int seg, Se
 // at scale s gives the vesselness factor and S^2 of plane s (vp, s2) and the
 // image's max S^2.  The next piece's rows (of this segment or of the block's
 // next one) are copied with cp.async while the current piece is computed.
-template <int R, int MODE, bool F2>
+template <int R, int MODE>
 __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripArgs sa)
 {
     constexpr bool SEL = MODE == ST_SELECT, DENSE = MODE != ST_TENSOR;
@@ -329,8 +293,7 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
             }
             __syncthreads();
         }
-        if (F2) st_rows2<R>(tp, stsm + buf * ST_CH * SW, trow, pc.b0, pc.n);
-        else st_rows<R>(tp, stsm + buf * ST_CH * SW, trow, pc.b0, pc.n);
+        st_rows2<R>(tp, stsm + buf * ST_CH * SW, trow, pc.b0, pc.n);
         __syncthreads();
 
         if (DENSE && pc.last) {
@@ -339,46 +302,29 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
             const float *c0 = trow + (warp * 4) * ST_RS + lane;
             const float *c1 = c0 + NB * ST_RS, *c2 = c1 + NB * ST_RS;
             float uxx[4], uxy[4], uyy[4];
-            if (F2) {  // output rows (0, 1) and (2, 3) in packed pairs, as in st_rows2
-                float2 axx[2], axy[2], ayy[2];
+            // output rows (0, 1) and (2, 3) in packed pairs, as in st_rows2
+            float2 axx[2], axy[2], ayy[2];
 #pragma unroll
-                for (int j = 0; j < 2; ++j) axx[j] = axy[j] = ayy[j] = make_float2(0.0f, 0.0f);
+            for (int j = 0; j < 2; ++j) axx[j] = axy[j] = ayy[j] = make_float2(0.0f, 0.0f);
 #pragma unroll
-                for (int k = 0; k < 2 * R + 4; ++k) {
-                    const float v0 = c0[k * ST_RS], v1 = c1[k * ST_RS], v2 = c2[k * ST_RS];
-                    const float2 x0 = make_float2(v0, v0), x1 = make_float2(v1, v1), x2 = make_float2(v2, v2);
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int q = k - 2 * j;  // tap pair of output rows 2j, 2j + 1
-                        if (q >= 0 && q <= 2 * R + 1) {
-                            axx[j] = __ffma2_rn(tp.p0[q], x2, axx[j]);
-                            axy[j] = __ffma2_rn(tp.p1[q], x1, axy[j]);
-                            ayy[j] = __ffma2_rn(tp.p2[q], x0, ayy[j]);
-                        }
-                    }
-                }
+            for (int k = 0; k < 2 * R + 4; ++k) {
+                const float v0 = c0[k * ST_RS], v1 = c1[k * ST_RS], v2 = c2[k * ST_RS];
+                const float2 x0 = make_float2(v0, v0), x1 = make_float2(v1, v1), x2 = make_float2(v2, v2);
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    uxx[2 * j] = axx[j].x; uxx[2 * j + 1] = axx[j].y;
-                    uxy[2 * j] = axy[j].x; uxy[2 * j + 1] = axy[j].y;
-                    uyy[2 * j] = ayy[j].x; uyy[2 * j + 1] = ayy[j].y;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) uxx[j] = uxy[j] = uyy[j] = 0.0f;
-#pragma unroll
-                for (int k = 0; k < 2 * R + 4; ++k) {
-                    const float v0 = c0[k * ST_RS], v1 = c1[k * ST_RS], v2 = c2[k * ST_RS];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int q = k - j;  // tap index of output row j
-                        if (q >= 0 && q <= 2 * R) {
-                            uxx[j] = fmaf(tp.w0[q], v2, uxx[j]);   // d2/dx2, smoothed in y
-                            uxy[j] = fmaf(tp.w1[q], v1, uxy[j]);   // d/dx, then d/dy
-                            uyy[j] = fmaf(tp.w2[q], v0, uyy[j]);   // d2/dy2 of the x-smoothed field
-                        }
+                    const int q = k - 2 * j;  // tap pair of output rows 2j, 2j + 1
+                    if (q >= 0 && q <= 2 * R + 1) {
+                        axx[j] = __ffma2_rn(tp.p0[q], x2, axx[j]);
+                        axy[j] = __ffma2_rn(tp.p1[q], x1, axy[j]);
+                        ayy[j] = __ffma2_rn(tp.p2[q], x0, ayy[j]);
                     }
                 }
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                uxx[2 * j] = axx[j].x; uxx[2 * j + 1] = axx[j].y;
+                uxy[2 * j] = axy[j].x; uxy[2 * j + 1] = axy[j].y;
+                uyy[2 * j] = ayy[j].x; uyy[2 * j + 1] = ayy[j].y;
             }
             const int gx = x0 + lane;
 #pragma unroll
@@ -460,7 +406,7 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
                 const float *c1 = c0 + NB * ST_RS;           // d/dx
                 const float *c2 = c1 + NB * ST_RS;           // d2/dx2
                 float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
-                if (F2) {  // (sy, syy) and (sx, sxy) share their input: packed pairs
+                {  // (sy, syy) and (sx, sxy) share their input: packed pairs
                     float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int k = 0; k <= 2 * R; ++k) {
@@ -470,16 +416,6 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
                         sxx = fmaf(tp.w0[k], v2, sxx);
                     }
                     sy = a.x; syy = a.y; sx = b.x; sxy = b.y;
-                } else {
-#pragma unroll
-                    for (int k = 0; k <= 2 * R; ++k) {
-                        const float v0 = c0[k * ST_RS], v1 = c1[k * ST_RS], v2 = c2[k * ST_RS];
-                        sy = fmaf(tp.w1[k], v0, sy);
-                        syy = fmaf(tp.w2[k], v0, syy);
-                        sx = fmaf(tp.w0[k], v1, sx);
-                        sxy = fmaf(tp.w1[k], v1, sxy);
-                        sxx = fmaf(tp.w0[k], v2, sxx);
-                    }
                 }
                 const float g2 = fmaf(sx, sx, sy * sy);
                 const float g = sa.grad_sq ? g2 : sqrtf(g2);
@@ -498,7 +434,7 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
     st_wait0();
 }
 
-template <int R, int MODE, bool F2>
+template <int R, int MODE>
 int launch_strip_k(const Imgs &I, const StripTaps<R> &tp, const StripArgs &a, cudaStream_t st)
 {
     static int attr_dev = -1;
@@ -506,22 +442,14 @@ int launch_strip_k(const Imgs &I, const StripTaps<R> &tp, const StripArgs &a, cu
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
     constexpr size_t smem = st_smem_bytes<R>();
     if (attr_dev != dev) {
-        if (cudaFuncSetAttribute(k_strip<R, MODE, F2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        if (cudaFuncSetAttribute(k_strip<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return 1;
         attr_dev = dev;
     }
-    const int grid = persistent_grid((const void *)k_strip<R, MODE, F2>, ST_NT, smem, I.tiles);
-    k_strip<R, MODE, F2><<<grid, ST_NT, smem, st>>>(I, tp, a);
+    const int grid = persistent_grid((const void *)k_strip<R, MODE>, ST_NT, smem, I.tiles);
+    k_strip<R, MODE><<<grid, ST_NT, smem, st>>>(I, tp, a);
     return cudaGetLastError() != cudaSuccess;
-}
-
-// Row and column passes with packed pair FMAs unless FD4_STRIP_FMA2=0 (same
-// results).
-inline bool strip_fma2()
-{
-    const char *e = getenv("FD4_STRIP_FMA2");
-    return !(e && e[0] == '0');
 }
 
 template <int R, int MODE>
@@ -547,20 +475,17 @@ int launch_strip_scale(const HostBatch &B, const GaussTaps &g, const StripArgs &
     // Segment length: the one with the smaller estimated time, taken as the
     // rounds of the persistent grid times the rows a block passes per segment
     // (its rows, the 2R halo rows and one chunk for the segment's start, whose
-    // staging is not overlapped); FD4_STRIP_ROWS=512 or 128 forces one.
-    const int cap = persistent_grid((const void *)k_strip<R, MODE, true>, ST_NT, smem, 1 << 30);
+    // staging is not overlapped).
+    const int cap = persistent_grid((const void *)k_strip<R, MODE>, ST_NT, smem, 1 << 30);
     const long long rounds_l = (B.tiles[SHAPE_SEG] + cap - 1) / cap;
     const long long rounds_s = (B.tiles[SHAPE_SEG_S] + cap - 1) / cap;
-    bool lng = rounds_l * (kSegRows + 2 * R + ST_CH) <= rounds_s * (kSegRowsShort + 2 * R + ST_CH);
-    const char *e = getenv("FD4_STRIP_ROWS");
-    if (e && atoi(e) == kSegRows) lng = true;
-    if (e && atoi(e) == kSegRowsShort) lng = false;
+    const bool lng = rounds_l * (kSegRows + 2 * R + ST_CH) <= rounds_s * (kSegRowsShort + 2 * R + ST_CH);
     StripArgs a = sa;
     a.shape = lng ? SHAPE_SEG : SHAPE_SEG_S;
     a.seg = lng ? kSegRows : kSegRowsShort;
     Imgs I = B.I;
     I.tiles = B.tiles[a.shape];
-    return strip_fma2() ? launch_strip_k<R, MODE, true>(I, tp, a, st) : launch_strip_k<R, MODE, false>(I, tp, a, st);
+    return launch_strip_k<R, MODE>(I, tp, a, st);
 }
 
 template <int MODE>
@@ -605,12 +530,9 @@ int set_strip_smem()
 {
     const int b = (int)st_smem_bytes<R>();
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    return cudaFuncSetAttribute(k_strip<R, ST_TENSOR, false>, a, b) != cudaSuccess ||
-           cudaFuncSetAttribute(k_strip<R, ST_SELECT, false>, a, b) != cudaSuccess ||
-           cudaFuncSetAttribute(k_strip<R, ST_IFOD, false>, a, b) != cudaSuccess ||
-           cudaFuncSetAttribute(k_strip<R, ST_TENSOR, true>, a, b) != cudaSuccess ||
-           cudaFuncSetAttribute(k_strip<R, ST_SELECT, true>, a, b) != cudaSuccess ||
-           cudaFuncSetAttribute(k_strip<R, ST_IFOD, true>, a, b) != cudaSuccess;
+    return cudaFuncSetAttribute(k_strip<R, ST_TENSOR>, a, b) != cudaSuccess ||
+           cudaFuncSetAttribute(k_strip<R, ST_SELECT>, a, b) != cudaSuccess ||
+           cudaFuncSetAttribute(k_strip<R, ST_IFOD>, a, b) != cudaSuccess;
 }
 
 }  // namespace

@@ -43,7 +43,26 @@ class Params(ctypes.Structure):
                 ("mode", ctypes.c_int), ("boundary", ctypes.c_int), ("kappa", ctypes.c_int),
                 ("grad_norm_squared", ctypes.c_int), ("fed_steps_per_launch", ctypes.c_int),
                 ("reselect_each_cycle", ctypes.c_int), ("postprocess_scales", ctypes.c_int),
-                ("theta", ctypes.c_float), ("model", ctypes.c_int), ("ifod_sigma", ctypes.c_float)]
+                ("theta", ctypes.c_float), ("model", ctypes.c_int), ("ifod_sigma", ctypes.c_float),
+                ("fed_tile_rows", ctypes.c_int), ("fed_quads_per_thread", ctypes.c_int)]
+
+
+class FedSchedule(ctypes.Structure):
+    """fd4_fed_schedule (include/fd4.h)."""
+    _fields_ = [("steps_per_launch", ctypes.c_int), ("tile_rows", ctypes.c_int),
+                ("quads_per_thread", ctypes.c_int), ("ms", ctypes.c_float)]
+
+    def as_params(self) -> dict:
+        """The fd4_params fields of this schedule (zero: the library default)."""
+        return dict(fed_steps_per_launch=self.steps_per_launch, fed_tile_rows=self.tile_rows,
+                    fed_quads_per_thread=self.quads_per_thread)
+
+    def as_dict(self) -> dict:
+        return dict(steps_per_launch=self.steps_per_launch, tile_rows=self.tile_rows,
+                    quads_per_thread=self.quads_per_thread, ms=self.ms)
+
+
+AUTOTUNE_CANDIDATES = 10
 
 
 class Image(ctypes.Structure):
@@ -72,6 +91,8 @@ SIGNATURES = {
     "fd4_build_tensor_ifod": (_i, [_vp, _i, _i, _i, _pp, _vp, _vp]),
     "fd4_extract_creases": (_i, [_vp, _i, _i, _i, ctypes.c_float, _i, _vp, _vp, _i, _vp, _vp, _sz, _vp]),
     "fd4_fed_cycle": (_i, [_vp, _i, _i, _i, _vp, _dp, _i, _i, _vp, _sz, _vp]),
+    "fd4_fed_cycle_sched": (_i, [_vp, _i, _i, _i, _vp, _dp, _i, _i, _i, _i, _i, _vp, _sz, _vp]),
+    "fd4_selftest_fed_wait_timeout": (_i, [_vp, _i, _i, _i, _vp, _vp, _sz, _ip, _vp]),
     "fd4_filter": (_i, [_vp, _vp, _i, _i, _i, _fp, _i, _pp, ctypes.c_double, _i, _i, _vp, _i, _vp,
                         _sz, _vp]),
     "fd4_fed_cycle_noalloc": (_i, [_vp, _i, _i, _i, _vp, _dp, _i, _i, _vp]),
@@ -83,8 +104,8 @@ SIGNATURES = {
     "fd4_graph_destroy": (_i, [_vp]),
     "fd4_graph_kernel_count": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "fd4_device_status": (_i, [ctypes.POINTER(ctypes.c_int), _i]),
-    "fd4_autotune_batched": (_i, [_vp, _i, _fp, _i, _pp, ctypes.c_double, _i, _i, _vp, _sz, _vp, _ip,
-                                  _fp]),
+    "fd4_autotune_batched": (_i, [_vp, _i, _fp, _i, _pp, ctypes.c_double, _i, _i, _vp, _sz, _vp,
+                                  ctypes.POINTER(FedSchedule), ctypes.POINTER(FedSchedule)]),
 }
 NOALLOC_MAX_PIXELS = 4 * 1024 * 1024
 SELECTOR_SIGNATURES = {
@@ -284,15 +305,34 @@ def build_tensor(u, w: int, sigma_idx, sigmas, prm: Params | None = None, out=No
     return out
 
 
-def fed_cycle(u, w: int, tensor, tau, boundary: int = NATURAL, ws=None, stream=None):
-    """fd4_fed_cycle, in place on u."""
+def fed_cycle(u, w: int, tensor, tau, boundary: int = NATURAL, ws=None, stream=None, sched=None):
+    """fd4_fed_cycle, in place on u; sched = (steps per launch, tile rows, quads
+    per thread) runs fd4_fed_cycle_sched with that kernel schedule instead."""
     h, pitch = u.shape
     t = np.ascontiguousarray(tau, dtype=np.float64)
     if ws is None:
         ws = workspace(OP_FED_CYCLE, pitch, h, 0, u.device)
-    _check(lib().fd4_fed_cycle(_ptr(u), int(w), h, pitch, _ptr(tensor), t.ctypes.data_as(_dp), t.size,
-                               int(boundary), _ptr(ws), ws.numel(), _stream(stream)), "fd4_fed_cycle")
+    if sched is None:
+        _check(lib().fd4_fed_cycle(_ptr(u), int(w), h, pitch, _ptr(tensor), t.ctypes.data_as(_dp), t.size,
+                                   int(boundary), _ptr(ws), ws.numel(), _stream(stream)), "fd4_fed_cycle")
+    else:
+        steps, rows, quads = (int(x) for x in sched)
+        _check(lib().fd4_fed_cycle_sched(_ptr(u), int(w), h, pitch, _ptr(tensor), t.ctypes.data_as(_dp), t.size,
+                                         int(boundary), steps, rows, quads, _ptr(ws), ws.numel(), _stream(stream)),
+               "fd4_fed_cycle_sched")
     return u
+
+
+def selftest_fed_wait_timeout(u, w: int, tensor, ws=None, stream=None) -> int:
+    """Runs fd4_selftest_fed_wait_timeout on u (left unchanged); returns the
+    device status word it read (FD4_ERR_TIMEOUT when detection works)."""
+    h, pitch = u.shape
+    if ws is None:
+        ws = workspace(OP_FED_CYCLE, pitch, h, 0, u.device)
+    st = ctypes.c_int(0)
+    _check(lib().fd4_selftest_fed_wait_timeout(_ptr(u), int(w), h, pitch, _ptr(tensor), _ptr(ws), ws.numel(),
+                                               ctypes.byref(st), _stream(stream)), "fd4_selftest_fed_wait_timeout")
+    return st.value
 
 
 def filter_image(u_in, w: int, sigmas, T: float, M: int, n: int = 0, prm: Params | None = None,
@@ -407,17 +447,18 @@ class Graph:
 
 def autotune_batched(imgs, sigmas, T: float, M: int, n: int = 0, prm: Params | None = None, ws=None,
                      stream=None):
-    """fd4_autotune_batched.  Returns (best steps per launch, times in ms for 1..4)."""
+    """fd4_autotune_batched.  Returns (the fastest FedSchedule, every candidate's
+    FedSchedule with its time); best.as_params() gives its fd4_params fields."""
     sg, K = _sigmas(sigmas)
     if ws is None:
         ws = batch_workspace(imgs, K)
-    best = ctypes.c_int(0)
-    times = (ctypes.c_float * 4)()
+    best = FedSchedule()
+    tried = (FedSchedule * AUTOTUNE_CANDIDATES)()
     _check(lib().fd4_autotune_batched(ctypes.cast(imgs, ctypes.c_void_p), len(imgs), sg, K,
                                       ctypes.byref(prm) if prm is not None else None, float(T), int(M), int(n),
-                                      _ptr(ws), ws.numel(), _stream(stream), ctypes.byref(best), times),
+                                      _ptr(ws), ws.numel(), _stream(stream), ctypes.byref(best), tried),
            "fd4_autotune_batched")
-    return best.value, list(times)
+    return best, list(tried)
 
 
 # ---------------------------------------------------------------------------

@@ -115,7 +115,7 @@ def test_binding_structs_match_the_header(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no host C compiler")
-    structs = {"fd4_params": fd4.Params, "fd4_image": fd4.Image}
+    structs = {"fd4_params": fd4.Params, "fd4_image": fd4.Image, "fd4_fed_schedule": fd4.FedSchedule}
     lines = ['#include <stdio.h>', '#include "fd4.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
@@ -183,3 +183,32 @@ def test_workspace_sizes_of_the_added_entry_points():
     assert 0 < a < b and a >= 100 * 100 * 17
     c = fd4.workspace_bytes(fd4.OP_CREASES, 100, 100, 0)
     assert c >= 100 * 100 * 8
+
+
+def test_host_side_argument_errors_of_the_fed_schedule():
+    """FED kernel schedules outside their ranges, on the explicit-schedule
+    cycle, the filters and the wait self-test: rejected before any CUDA call."""
+    L = fd4.lib()
+    sig = (ctypes.c_float * 2)(1.0, 2.0)
+    fake = ctypes.c_void_p(1 << 20)
+    ws = ctypes.c_void_p(1 << 24)
+    big = 1 << 40
+    tau = (ctypes.c_double * 2)(0.1, 0.2)
+    for steps, rows, quads in ((5, 0, 0), (-1, 0, 0), (2, 48, 2), (2, 16, 2), (2, 64, 3), (2, 64, -1)):
+        assert L.fd4_fed_cycle_sched(fake, 8, 8, 8, fake, tau, 2, 0, steps, rows, quads, ws, big, None) == -1
+    for kw in (dict(fed_steps_per_launch=5), dict(fed_tile_rows=100), dict(fed_quads_per_thread=4)):
+        p = fd4.params(**kw)
+        assert L.fd4_filter(fake, fake, 8, 8, 8, sig, 2, ctypes.byref(p), 11 / 3, 2, 10, None, 0, ws, big,
+                            None) == -1
+    st = ctypes.c_int(0)
+    assert L.fd4_selftest_fed_wait_timeout(fake, 8, 8, 8, None, ws, big, ctypes.byref(st), None) == -1
+    assert L.fd4_selftest_fed_wait_timeout(fake, 8, 8, 8, fake, ws, 16, ctypes.byref(st), None) == -5
+    assert L.fd4_selftest_fed_wait_timeout(fake, 8, 8, 8, fake, ws, big, None, None) == -1
+
+
+def test_schedule_defaults_and_struct_layout():
+    p = fd4.params()
+    assert p.fed_tile_rows == 0 and p.fed_quads_per_thread == 0
+    assert ctypes.sizeof(fd4.FedSchedule) == 16
+    s = fd4.FedSchedule(2, 64, 2, 1.5)
+    assert s.as_params() == dict(fed_steps_per_launch=2, fed_tile_rows=64, fed_quads_per_thread=2)

@@ -111,22 +111,48 @@ def test_in_place_batch_and_given_scales():
         assert float((a[:, :w] - b[:, :w]).abs().max()) == 0.0
 
 
-def test_fed_schedules_agree_and_autotune():
+SCHEDULES = [(1, 0, 0), (2, 64, 2), (2, 64, 1), (2, 32, 2), (2, 32, 1), (3, 0, 0), (4, 64, 2), (4, 64, 1),
+             (4, 32, 2), (4, 32, 1)]
+
+
+def test_fed_schedules_agree_and_autotune(oracle):
+    """Every FED kernel schedule the autotuner may pick gives the filter the
+    oracle gives (the oracle's scale images given); the autotuner times all of
+    them and returns the fastest."""
     import torch
     imgs = _images()
+    tau, _, _ = oracle.fed_taus(T, M, 0.05, n=N)
+    refs = {k: oracle.filter_image(imgs[k], SIGMAS, tau, M, mode=oracle.VALLEY) for k in (0, 2, 4)}
     res = []
-    for steps in (1, 2, 3, 4):
+    for steps, rows, quads in SCHEDULES:
         ins, outs, idx, lst = _batch(imgs)
-        fd4.filter_batched(lst, SIGMAS, T, M, N, fd4.params(mode=fd4.VALLEY, fed_steps_per_launch=steps))
+        for k, (_, ridx) in refs.items():
+            idx[k][:, :imgs[k].shape[1]] = torch.from_numpy(ridx).cuda()
+        prm = fd4.params(mode=fd4.VALLEY, fed_steps_per_launch=steps, fed_tile_rows=rows, fed_quads_per_thread=quads)
+        fd4.filter_batched(lst, SIGMAS, T, M, N, prm, sigma_given=True)
         torch.cuda.synchronize()
+        for k, (ref, _) in refs.items():
+            w = imgs[k].shape[1]
+            assert np.abs(outs[k][:, :w].cpu().numpy() - ref).max() <= 1e-4, (steps, rows, quads)
         res.append([o[:, :im.shape[1]].clone() for o, im in zip(outs, imgs)])
     for other in res[1:]:
         for a, b in zip(res[0], other):
             assert float((a - b).abs().max()) <= 1e-5
     ins, outs, idx, lst = _batch(imgs)
-    best, times = fd4.autotune_batched(lst, SIGMAS, T, M, N, fd4.params(mode=fd4.VALLEY))
-    assert best in (1, 2, 3, 4)
-    assert all(t > 0 for t in times)
+    best, tried = fd4.autotune_batched(lst, SIGMAS, T, M, N, fd4.params(mode=fd4.VALLEY))
+    assert [(c.steps_per_launch, c.tile_rows, c.quads_per_thread) for c in tried] == SCHEDULES
+    assert all(c.ms > 0 for c in tried)
+    assert best.ms == min(c.ms for c in tried)
+    assert (best.steps_per_launch, best.tile_rows, best.quads_per_thread) in SCHEDULES
+
+
+def test_bad_schedule_is_rejected():
+    imgs = _images()[:2]
+    ins, outs, idx, lst = _batch(imgs)
+    for bad in (dict(fed_steps_per_launch=5), dict(fed_tile_rows=48), dict(fed_quads_per_thread=3)):
+        with pytest.raises(fd4.Fd4Error) as e:
+            fd4.filter_batched(lst, SIGMAS, T, M, N, fd4.params(**bad))
+        assert e.value.status == -1
 
 
 def test_bad_batch_is_rejected_before_launch():
@@ -143,6 +169,34 @@ def test_fed_kernels_report_no_timeout():
     imgs = _images()
     ins, outs, idx, lst = _batch(imgs)
     fd4.filter_batched(lst, SIGMAS, T, M, N, fd4.params(mode=fd4.VALLEY))
+    assert fd4.device_status(reset=True) == 0
+
+
+def test_fed_wait_runs_out_and_is_reported(oracle):
+    """Failure detection of the TMA FED kernel's bounded wait: with the tile
+    copies withheld (no copy is ever in flight) the wait gives up after its
+    limit, the kernel records FD4_ERR_TIMEOUT and returns without writing u,
+    and the context keeps computing correctly afterwards."""
+    import math
+    import torch
+    rng = np.random.default_rng(5)
+    h, w = 150, 211
+    u0 = rng.random((h, w)).astype(np.float32)
+    th = rng.uniform(-math.pi, math.pi, size=(h, w))
+    mu = rng.uniform(0.0, 1.0, size=(2, h, w))
+    t = np.stack([np.cos(2 * th), np.sin(2 * th), mu[0], mu[1]], axis=-1).astype(np.float32)
+    ten = fd4.empty_image(h, w, channels=4)
+    ten[:, :w, :] = torch.from_numpy(t).cuda()
+    u = fd4.to_device(u0)
+    assert fd4.device_status(reset=True) == 0
+    assert fd4.selftest_fed_wait_timeout(u, w, ten) == -6  # FD4_ERR_TIMEOUT, read back and cleared
+    assert fd4.device_status() == 0
+    assert np.array_equal(u[:, :w].cpu().numpy(), u0)
+    # the context is intact: a regular cycle matches the oracle
+    tau, _, _ = oracle.fed_taus(20 * 21 * 0.05 / 3, 1, 0.05, n=20)
+    fd4.fed_cycle(u, w, ten, tau)
+    ref = oracle.fed_cycle(u0, np.moveaxis(t, -1, 0), tau)
+    assert np.abs(u[:, :w].cpu().numpy() - ref).max() <= 1e-4
     assert fd4.device_status(reset=True) == 0
 
 

@@ -37,7 +37,7 @@ def test_batch64_graph_matches_oracle_on_samples(oracle, batch64):
     lst = fd4.image_list(ins, [im.shape[1] for im in batch64], outs, idx)
     ws = fd4.batch_workspace(lst, len(sig))
     best, _ = fd4.autotune_batched(lst, sig, T, M, n, fd4.params(mode=fd4.VALLEY), ws=ws)
-    g = fd4.Graph(lst, sig, T, M, n, fd4.params(mode=fd4.VALLEY, fed_steps_per_launch=best), ws=ws)
+    g = fd4.Graph(lst, sig, T, M, n, fd4.params(mode=fd4.VALLEY, **best.as_params()), ws=ws)
     g.launch()
     torch.cuda.synchronize()
     # properties on every image: finite, mean preserved (natural boundary)
@@ -61,7 +61,7 @@ def test_batch64_graph_matches_oracle_on_samples(oracle, batch64):
     # the same graph schedule with the scale images given (the oracle's on the
     # sampled images): every output pixel of those images is compared, also
     # where a near-tie made FP32 and FP64 select different scales
-    g2 = fd4.Graph(lst, sig, T, M, n, fd4.params(mode=fd4.VALLEY, fed_steps_per_launch=best), ws=ws,
+    g2 = fd4.Graph(lst, sig, T, M, n, fd4.params(mode=fd4.VALLEY, **best.as_params()), ws=ws,
                    sigma_given=True)
     g2.launch()
     torch.cuda.synchronize()

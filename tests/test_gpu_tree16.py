@@ -49,7 +49,7 @@ def test_tree16_1024_end_to_end(oracle):
     ws = fd4.batch_workspace(lst, len(SIG))
     prm0 = fd4.params(mode=fd4.BOTH)
     best, _ = fd4.autotune_batched(lst, SIG, T, M, N, prm0, ws=ws)
-    prm = fd4.params(mode=fd4.BOTH, fed_steps_per_launch=best)
+    prm = fd4.params(mode=fd4.BOTH, **best.as_params())
     g = fd4.Graph(lst, SIG, T, M, N, prm, ws=ws)
     g.launch()
     torch.cuda.synchronize()
@@ -85,7 +85,7 @@ def test_tree16_4096_batch_properties(oracle):
     lst = fd4.image_list(ins, [4096] * 16, outs, idx)
     ws = fd4.batch_workspace(lst, len(SIG))
     best, _ = fd4.autotune_batched(lst, SIG, T, M, N, fd4.params(mode=fd4.BOTH), ws=ws)
-    prm = fd4.params(mode=fd4.BOTH, fed_steps_per_launch=best)
+    prm = fd4.params(mode=fd4.BOTH, **best.as_params())
     g = fd4.Graph(lst, SIG, T, M, N, prm, ws=ws)
     g.launch()
     torch.cuda.synchronize()
