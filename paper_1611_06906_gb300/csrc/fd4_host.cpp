@@ -254,17 +254,18 @@ size_t fd4::ws_select_bytes(int h, int pitch, int n_sigma)
     return kHeaderBytes + 2 * (size_t)n_sigma * plane_bytes(h, pitch, 4);
 }
 
-size_t fd4::ws_tensor_bytes(int h, int pitch) { return kHeaderBytes + plane_bytes(h, pitch, 16); }
+// tensor build: header | N field | chunk masks of the scale image
+size_t fd4::ws_tensor_bytes(int h, int pitch) { return kHeaderBytes + plane_bytes(h, pitch, 16) + cmask_bytes(pitch, h); }
 
 size_t fd4::ws_fed_bytes(int h, int pitch) { return kHeaderBytes + plane_bytes(h, pitch, 4); }
 
-// filter: sigma* (u8) | tensor field (float4) | stage workspace shared by the stages
+// filter: sigma* (u8) | tensor field (float4) | chunk masks | stage workspace shared by the stages
 size_t fd4::ws_filter_bytes(int h, int pitch, int n_sigma)
 {
     size_t stage = ws_select_bytes(h, pitch, n_sigma);
     if (ws_tensor_bytes(h, pitch) > stage) stage = ws_tensor_bytes(h, pitch);
     if (ws_fed_bytes(h, pitch) > stage) stage = ws_fed_bytes(h, pitch);
-    return plane_bytes(h, pitch, 1) + plane_bytes(h, pitch, 16) + stage;
+    return plane_bytes(h, pitch, 1) + plane_bytes(h, pitch, 16) + cmask_bytes(pitch, h) + stage;
 }
 
 extern "C" size_t fd4_workspace_bytes(int op, int w, int h, int n_sigma)
@@ -510,7 +511,8 @@ extern "C" int fd4_filter(const float *d_in, float *d_out, int w, int h, int pit
     // [sigma* plane | tensor plane | stage workspace = header + scratch]; the
     // stages run in order on one stream, so they share the scratch.
     char *ws = (char *)d_ws;
-    char *sws = ws + plane_bytes(h, pitch, 1) + plane_bytes(h, pitch, 16);
+    uint32_t *cmask = (uint32_t *)(ws + plane_bytes(h, pitch, 1) + plane_bytes(h, pitch, 16));
+    char *sws = (char *)cmask + cmask_bytes(pitch, h);
     char *scratch = sws + kHeaderBytes;
     const size_t pb = plane_bytes(h, pitch, 4);
     ImgDesc d{};
@@ -528,6 +530,7 @@ extern "C" int fd4_filter(const float *d_in, float *d_out, int w, int h, int pit
     d.vmax = (p.model == FD4_MODEL_MAFOD && p.postprocess_scales && !sigma_given) ? (float *)d.tensor : nullptr;
     d.idx2 = (uint8_t *)d.tensor + 4 * (size_t)h * pitch;
     d.max_s2 = &((WsHeader *)sws)->max_s2;
+    d.cmask = cmask;
     d.plane = pb / 4;
     d.w = w;
     d.h = h;
@@ -571,7 +574,8 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
         const fd4_image &im = imgs[i];
         const size_t pb = plane_bytes(im.h, im.pitch, 4);
         const size_t o_idx = off, o_ten = o_idx + plane_bytes(im.h, im.pitch, 1);
-        const size_t o_sc = o_ten + plane_bytes(im.h, im.pitch, 16);
+        const size_t o_cm = o_ten + plane_bytes(im.h, im.pitch, 16);
+        const size_t o_sc = o_cm + cmask_bytes(im.pitch, im.h);
         off = o_sc + scratch_bytes(im.h, im.pitch, n_sigma);
         if (!descs) continue;
         ImgDesc &d = (*descs)[i];
@@ -589,6 +593,7 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
         d.vmax = post ? (float *)(ws + o_ten) : nullptr;
         d.idx2 = (uint8_t *)(ws + o_ten) + 4 * (size_t)im.h * im.pitch;
         d.max_s2 = (unsigned *)(ws + ms_off) + i;
+        d.cmask = (uint32_t *)(ws + o_cm);
         d.maps = ws + maps_off + tma_maps_bytes() * (size_t)i;
         d.plane = pb / 4;
         d.w = im.w;
@@ -611,6 +616,7 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
         B->max_s2 = (unsigned *)(ws + ms_off);
         B->n_max_s2 = two ? split : n;
         B->table_u = (const ImgDesc *)(ws + tu_off);
+        B->has_cmask = true;
     }
     if (B1 && two) {
         *B1 = *B;

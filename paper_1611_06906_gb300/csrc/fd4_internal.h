@@ -86,6 +86,8 @@ struct ImgDesc {
     uint8_t *idx;        // selected scale index
     uint8_t *idx2;       // post-processed scale index before its copy into idx
     float *vmax;         // nullable (set when the scale image is post-processed)
+    uint32_t *cmask;     // nullable: per 32 x 32 chunk of the scale image, bit s set where a
+                         // pixel selected scale s (an index outside the set counts as 0)
     unsigned *max_s2;    // max S^2 of the image (float bits)
     size_t plane;
     const void *maps;    // batches: this image's TMA tensor maps (u, FED plane, tensor) in device memory
@@ -236,6 +238,7 @@ struct HostBatch {
     unsigned *max_s2;
     int n_max_s2;
     const ImgDesc *table_u;  // batches: the descriptor table with in = u (nullptr for single images)
+    bool has_cmask;          // every descriptor has its chunk-mask plane (cmask)
 };
 
 // One image: inline descriptor.
@@ -247,8 +250,13 @@ inline HostBatch single_batch(const ImgDesc &d)
     B.max_s2 = d.max_s2;
     B.n_max_s2 = 1;
     B.table_u = nullptr;
+    B.has_cmask = d.cmask != nullptr;
     return B;
 }
+
+// Chunk masks of the scale image: one word per 32 x 32 chunk, (h/32) rows of (w/32).
+inline size_t cmask_words(int w, int h) { return (size_t)((w + 31) / 32) * (size_t)((h + 31) / 32); }
+inline size_t cmask_bytes(int w, int h) { return align_up(4 * cmask_words(w, h), 256); }
 
 // Stage launchers over a batch (fd4_scale.cu, fd4_fed.cu); nonzero on a CUDA error.
 int launch_select_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,

@@ -658,6 +658,7 @@ int launch_tensor(const float *d_u, int w, int h, int pitch, const uint8_t *d_id
     ImgDesc d{};
     d.u = const_cast<float *>(d_u);  // read only by the tensor build
     d.nfield = (float4 *)(ws + kHeaderBytes);
+    d.cmask = (uint32_t *)(ws + kHeaderBytes + plane_bytes(h, pitch, 16));
     d.tensor = (float4 *)d_tensor;
     d.idx = const_cast<uint8_t *>(d_idx);
     d.w = w;

@@ -11,7 +11,9 @@
 // that keeps the 2R rows shared with the previous chunk, so the row pass costs
 // 3 (2R+1) FMAs per pixel plus 2R halo rows per segment instead of a full
 // halo per tile.  The column pass then runs only at the chunk's pixels whose
-// selected scale is this one.  The radius R is a template parameter: every tap
+// selected scale is this one, and (with the scale image's chunk masks) only on
+// the chunks that hold such a pixel, the row pass only on the rows those
+// chunks read.  The radius R is a template parameter: every tap
 // loop is unrolled and the weights are kernel parameters (constant-bank
 // operands of the FMAs).  The arithmetic and summation order are those of the
 // multi-scale sweep in fd4_scale.cu (which selects on tile lists), so both give
@@ -79,28 +81,35 @@ constexpr size_t st_smem_bytes()
 }
 
 // A segment is walked as a sequence of pieces, each the row pass of up to
-// ST_CH rows: pieces 0 .. NP0 - 1 fill the buffer for the first chunk (rows
-// ys - R .. ys + ST_CH - 1 + R), piece NP0 - 1 + c (c >= 1) adds the ST_CH new
-// rows of chunk c after the buffer keeps the 2R rows it shares with chunk c - 1.
+// ST_CH rows into the rolling buffer, listed by a plan (SegGeo::code).  A
+// "fill" piece k (k < NP0) of chunk c writes buffer rows 32k .. of the NB = 32 +
+// 2R rows chunk c's column pass reads (image rows ys + 32c - R + 32k ..); a
+// "roll" piece of chunk c keeps the 2R rows chunk c shares with chunk c - 1
+// and adds its 32 new rows (image rows ys + 32c + R ..).  Code byte: bits 0-3
+// the chunk, bits 4-6 the fill index k or NP0 for a roll, bit 7 set where the
+// chunk's column pass runs after the piece.
 template <int R>
 struct Piece {
     static constexpr int NB = ST_CH + 2 * R, NP0 = (NB + ST_CH - 1) / ST_CH;
+    static_assert(NP0 >= 2 && NP0 < 8, "a fill takes 2 .. 7 pieces");
     int ya, b0, n, chunk;  // first image row, first buffer row, rows, chunk it belongs to
-    bool last;             // completes its chunk's buffer
-    __device__ __forceinline__ Piece(int ys, int i)
+    bool roll;             // shift the shared rows down first
+    bool col;              // the chunk's buffer is complete and its column pass runs
+    __device__ __forceinline__ Piece(int ys, unsigned code)
     {
-        if (i < NP0) {
-            ya = ys - R + ST_CH * i;
-            b0 = ST_CH * i;
-            n = min(ST_CH, NB - ST_CH * i);
-            chunk = 0;
-            last = i == NP0 - 1;
+        chunk = code & 15u;
+        const int k = (code >> 4) & 7u;
+        col = (code >> 7) & 1u;
+        if (k < NP0) {
+            ya = ys + ST_CH * chunk - R + ST_CH * k;
+            b0 = ST_CH * k;
+            n = min(ST_CH, NB - ST_CH * k);
+            roll = false;
         } else {
-            chunk = i - NP0 + 1;
             ya = ys + ST_CH * chunk + R;
             b0 = 2 * R;
             n = ST_CH;
-            last = true;
+            roll = true;
         }
     }
 };
@@ -187,22 +196,64 @@ enum StripMode {
     ST_IFOD = 2     // IFOD tensor (1, 0, g, g), g = 1 / (1 + |H|_F^2 / lambda^2), at every pixel
 };
 
-// Geometry of one strip segment, computed once by the thread that looks the
-// segment up (the other threads read it from shared memory, so no thread
-// divides by the image's strip count per piece).
+// Geometry of one strip segment and the plan of its pieces, computed once by
+// the thread that looks the segment up (the other threads read it from shared
+// memory, so no thread divides by the image's strip count per piece).
+constexpr int kMaxPlan = 24;  // pieces of a 512-row segment: at most NP0 - 1 + 16 <= 19
+static_assert(kSegRows / ST_CH <= 16, "chunk index in 4 bits");
 struct SegGeo {
     int x0, ys;    // first column and row
-    int pieces;    // NP0 + chunks - 1
+    int pieces;    // plan length (0: nothing of this segment is needed)
+    unsigned char code[kMaxPlan];
 };
 
+// The plan of a segment.  Dense launches (selection, IFOD) and images without
+// chunk masks run every chunk: NP0 fill pieces, then one roll per chunk.  The
+// tensor build runs the column pass only on the chunks that hold a pixel of
+// scale s, and the row pass only for the rows those chunks read: between two
+// such chunks the buffer rolls through the chunks in between or is filled
+// afresh, whichever passes fewer rows (a segment without such a chunk has an
+// empty plan).  Every row the column pass reads is computed as in the dense
+// walk, so the sums are unchanged.
 template <int R>
-__device__ __forceinline__ void seg_geo(const ImgDesc &d, int local, int seg, SegGeo &g)
+__device__ __forceinline__ void seg_geo(const ImgDesc &d, int local, int seg, int s, bool dense, SegGeo &g)
 {
+    constexpr int NP0 = Piece<R>::NP0, NB = Piece<R>::NB;
     const int tiles_x = (d.w + ST_TX - 1) / ST_TX;
     const int ty = local / tiles_x;
     g.x0 = (local - ty * tiles_x) * ST_TX;
     g.ys = ty * seg;
-    g.pieces = Piece<R>::NP0 + (min(g.ys + seg, d.h) - g.ys + ST_CH - 1) / ST_CH - 1;
+    const int nch = (min(g.ys + seg, d.h) - g.ys + ST_CH - 1) / ST_CH;
+    const uint32_t *cm = dense ? nullptr : d.cmask;
+    const int cw = (d.w + 31) / 32;
+    const uint32_t *row = cm ? cm + (size_t)(g.ys / ST_CH) * cw + g.x0 / ST_TX : nullptr;
+    int np = 0, prev = -1;
+    for (int c = 0; c < nch; ++c) {
+        if (row && !((row[(size_t)c * cw] >> s) & 1u)) continue;
+        if (prev >= 0 && (c - prev) * ST_CH <= NB) {
+            for (int cc = prev + 1; cc < c; ++cc) g.code[np++] = (unsigned char)(cc | (NP0 << 4));
+            g.code[np++] = (unsigned char)(c | (NP0 << 4) | 0x80);
+        } else {
+            for (int k = 0; k < NP0; ++k) g.code[np++] = (unsigned char)(c | (k << 4) | (k == NP0 - 1 ? 0x80 : 0));
+        }
+        prev = c;
+    }
+    g.pieces = np;
+}
+
+// Thread 0: the block's next segment with a non-empty plan, from flat segment
+// t on in steps of the grid: its descriptor, index in its image and plan into
+// the slot; the segment's number (>= I.tiles: none left).
+template <int R>
+__device__ __forceinline__ int next_segment(const Imgs &I, const StripArgs &sa, bool dense, int t, TileCache &tc,
+                                            ImgDesc &d, int &local, SegGeo &g)
+{
+    for (; t < I.tiles; t += gridDim.x) {
+        find_tile_cached(I, sa.shape, t, tc, d, local);
+        seg_geo<R>(d, local, sa.seg, sa.s, dense, g);
+        if (g.pieces > 0) break;
+    }
+    return t;
 }
 
 // Scale s (radius R) over every strip segment of the batch.
@@ -216,7 +267,7 @@ template <int R, int MODE>
 __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripArgs sa)
 {
     constexpr bool SEL = MODE == ST_SELECT, DENSE = MODE != ST_TENSOR;
-    constexpr int NB = ST_CH + 2 * R, SW = st_sw<R>(), NP0 = Piece<R>::NP0;
+    constexpr int NB = ST_CH + 2 * R, SW = st_sw<R>();
     extern __shared__ __align__(16) float stsm[];
     float *trow = stsm + 2 * ST_CH * SW;  // 3 fields x NB rows x ST_RS; staged rows: two ST_CH x SW buffers
     __shared__ unsigned short plist[ST_TX * ST_CH];
@@ -224,43 +275,46 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
     __shared__ ImgDesc sd[2];
     __shared__ int s_local[2];
     __shared__ SegGeo sg[2];
+    __shared__ int s_t[2];  // flat segment number of each slot
     __shared__ TileCache tcache;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, s = sa.s;
     float bmax = 0.0f;  // selection: max S^2 of this thread's pixels in the current segment
-    int t = blockIdx.x;
-    if (t >= I.tiles) return;
+    if (blockIdx.x >= I.tiles) return;
     if (tid == 0) {
         tc_reset(tcache);
-        find_tile_cached(I, sa.shape, t, tcache, sd[0], s_local[0]);
-        seg_geo<R>(sd[0], s_local[0], sa.seg, sg[0]);
+        s_t[0] = next_segment<R>(I, sa, DENSE, blockIdx.x, tcache, sd[0], s_local[0], sg[0]);
     }
     __syncthreads();
+    int t = s_t[0];
+    if (t >= I.tiles) return;  // block-uniform: no segment of this block needs scale s
     int cur = 0, i = 0, buf = 0;
     {
-        const Piece<R> p0(sg[0].ys, 0);
+        const Piece<R> p0(sg[0].ys, sg[0].code[0]);
         st_stage<R>(stsm, SEL ? sd[0].in : sd[0].u, sd[0].w, sd[0].h, sd[0].pitch, sg[0].x0, p0.ya, p0.n);
         st_commit();
     }
     for (;;) {
         const int w = sd[cur].w, h = sd[cur].h, pitch = sd[cur].pitch;
         const int x0 = sg[cur].x0, ys = sg[cur].ys, P = sg[cur].pieces;
-        const Piece<R> pc(ys, i);
-        // issue the next piece into the other staging buffer
+        const Piece<R> pc(ys, sg[cur].code[i]);
+        // issue the next piece into the other staging buffer; the next segment
+        // was looked up at piece 0 and published by that piece's barriers (a
+        // non-empty plan has at least NP0 >= 2 pieces)
         float *nbuf = stsm + (buf ^ 1) * ST_CH * SW;
         if (i + 1 < P) {
-            const Piece<R> pn(ys, i + 1);
+            const Piece<R> pn(ys, sg[cur].code[i + 1]);
             st_stage<R>(nbuf, SEL ? sd[cur].in : sd[cur].u, w, h, pitch, x0, pn.ya, pn.n);
-        } else if (t + G < I.tiles) {
-            const ImgDesc &dn = sd[cur ^ 1];  // looked up at piece 0, published by its barriers (P >= 2)
-            const Piece<R> pn(sg[cur ^ 1].ys, 0);
+        } else if (s_t[cur ^ 1] < I.tiles) {
+            const ImgDesc &dn = sd[cur ^ 1];
+            const Piece<R> pn(sg[cur ^ 1].ys, sg[cur ^ 1].code[0]);
             st_stage<R>(nbuf, SEL ? dn.in : dn.u, dn.w, dn.h, dn.pitch, sg[cur ^ 1].x0, pn.ya, pn.n);
         }
         st_commit();
         // the selected scales of the chunk this piece completes (rows 4 warp .. + 3)
         const int y0 = ys + ST_CH * pc.chunk;
         int ids[4] = {-1, -1, -1, -1};
-        if (!DENSE && pc.last && x0 + lane < w) {
+        if (!DENSE && pc.col && x0 + lane < w) {
             const uint8_t *ip = sd[cur].idx + (size_t)(y0 + warp * 4) * pitch + x0 + lane;
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -270,11 +324,9 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
         __syncthreads();  // this piece's rows have landed; the previous chunk's column pass is done
         // the block's next segment: its slot held the previous segment, whose last
         // readers (the column pass above) are past this barrier
-        if (i == 0 && tid == 0 && t + G < I.tiles) {
-            find_tile_cached(I, sa.shape, t + G, tcache, sd[cur ^ 1], s_local[cur ^ 1]);
-            seg_geo<R>(sd[cur ^ 1], s_local[cur ^ 1], sa.seg, sg[cur ^ 1]);
-        }
-        if (i >= NP0) {
+        if (i == 0 && tid == 0)
+            s_t[cur ^ 1] = next_segment<R>(I, sa, DENSE, t + G, tcache, sd[cur ^ 1], s_local[cur ^ 1], sg[cur ^ 1]);
+        if (pc.roll) {
             // keep buffer rows ST_CH .. ST_CH + 2R - 1 as rows 0 .. 2R - 1.
             // Thread (row r, columns c .. c + 3) moves rows k0 + r for k0 = 0,
             // 32, ...: a row it overwrites in pass k0 + 32 is one it read
@@ -296,7 +348,7 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
         st_rows2<R>(tp, stsm + buf * ST_CH * SW, trow, pc.b0, pc.n);
         __syncthreads();
 
-        if (DENSE && pc.last) {
+        if (DENSE && pc.col) {
             // dense column pass: column lane, rows 4 warp .. + 3 of the chunk
             // read buffer rows 4 warp .. 4 warp + 3 + 2R
             const float *c0 = trow + (warp * 4) * ST_RS + lane;
@@ -363,7 +415,7 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
                 bmax = 0.0f;
             }
         }
-        if (!DENSE && pc.last) {
+        if (!DENSE && pc.col) {
             // the chunk's pixels of this scale, grouped in plist
             unsigned m[4];
             int cnt = 0;
@@ -426,12 +478,53 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
         buf ^= 1;
         if (++i == P) {
             i = 0;
-            t += G;
+            t = s_t[cur ^ 1];
             cur ^= 1;
             if (t >= I.tiles) break;
         }
     }
     st_wait0();
+}
+
+// Chunk masks of the scale image for the tensor build: for each 32 x 32 chunk,
+// bit s set where one of its pixels selected scale s; an index outside the set
+// sets bit 0 (the scale-0 launch zeroes N there).  32 x 64 tiles (two chunks),
+// 256 threads: lane = column, warp w = rows 8w .. 8w + 7 of the tile.
+__global__ void __launch_bounds__(256) k_chunk_masks(Imgs I, int K)
+{
+    __shared__ ImgDesc sd;
+    __shared__ int s_local;
+    __shared__ unsigned sm[2];
+    __shared__ TileCache tcache;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) tc_reset(tcache);
+    for (int t = blockIdx.x; t < I.tiles; t += gridDim.x) {
+        __syncthreads();
+        if (tid == 0) {
+            find_tile_cached(I, SHAPE_SWEEP, t, tcache, sd, s_local);
+            sm[0] = sm[1] = 0u;
+        }
+        __syncthreads();
+        const int w = sd.w, h = sd.h, pitch = sd.pitch;
+        const int cw = (w + 31) / 32;
+        const int x0 = (s_local % cw) * 32, y0 = (s_local / cw) * 64;
+        const int x = x0 + lane;
+        unsigned m = 0u;
+        if (x < w) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int y = y0 + warp * 8 + j;
+                if (y < h) {
+                    const int v = sd.idx[(size_t)y * pitch + x];
+                    m |= v < K ? 1u << v : 1u;
+                }
+            }
+        }
+        m = __reduce_or_sync(0xffffffffu, m);
+        if (lane == 0) atomicOr(&sm[warp >> 2], m);
+        __syncthreads();
+        if (tid < 2 && y0 + 32 * tid < h) sd.cmask[(size_t)(y0 / 32 + tid) * cw + x0 / 32] = sm[tid];
+    }
 }
 
 template <int R, int MODE>
@@ -548,6 +641,13 @@ int prepare_tensor_kernels()
 int launch_tensor_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
                          cudaStream_t st)
 {
+    if (B.has_cmask) {  // which chunks hold which scales: the strips skip the others
+        Imgs I = B.I;
+        I.tiles = B.tiles[SHAPE_SWEEP];
+        const int grid = persistent_grid((const void *)k_chunk_masks, 256, 0, I.tiles);
+        k_chunk_masks<<<grid, 256, 0, st>>>(I, n_sigma);
+        if (cudaGetLastError() != cudaSuccess) return 1;
+    }
     return launch_strips<ST_TENSOR>(B, h_sigmas, n_sigma, p, st);
 }
 

@@ -217,6 +217,29 @@ def test_select_strips_edges_match_oracle(oracle, shape, mode):
     _check_selection(oracle, img, [0.75, 1.0, 1.6, 2.5, 4.0, 6.0, 9.0, 12.0], mode)
 
 
+@pytest.mark.parametrize("shape", [(2560, 2560), (700, 97)])
+def test_tensor_sparse_scales_match_oracle(oracle, shape):
+    """The tensor build's strips walk only the 32 x 32 chunks that hold a
+    pixel of their scale (and the rows those chunks read): scale images where
+    most chunks hold scale 0 only and each other scale sits in a few scattered
+    chunks -- gaps of every length between them (rolled through or refilled),
+    segments without any, indices outside the set -- give the oracle's tensor.
+    The 2560^2 image takes both segment lengths (512 rows for the largest
+    radii, 128 for the smallest)."""
+    h, w = shape
+    rng = np.random.default_rng(h + w)
+    img = synth.vessel_tree(2400 + h, w, h, depth=5, r0=6.0)
+    sig = [0.75, 1.0, 1.6, 2.5, 4.0, 6.0, 9.0, 12.0]
+    idx = np.zeros((h, w), dtype=np.uint8)
+    ch, cw = (h + 31) // 32, (w + 31) // 32
+    for s in range(1, len(sig) + 1):  # len(sig): an index outside the set
+        for cy, cx in zip(*np.nonzero(rng.random((ch, cw)) < 0.08)):
+            y = min(32 * cy + int(rng.integers(0, 30)), h - 3)
+            x = min(32 * cx + int(rng.integers(0, 30)), w - 3)
+            idx[y:y + 3, x:x + 3] = s
+    _check_tensor(oracle, img, idx, sig, fd4.BOTH)
+
+
 def test_index_outside_the_set_gives_zero_tensor_input():
     """A selected index outside the scale set (caller-given scale images only)
     zeroes N there: mu = 1 and the orientation (1, 0)."""
