@@ -154,8 +154,9 @@ def test_launch_count_and_threshold_validation():
     _, _, _, lst = _batch(imgs)
     plain = fd4.Graph(lst, SIGMAS, T, M, N, fd4.params(mode=fd4.VALLEY))
     post = fd4.Graph(lst, SIGMAS, T, M, N, fd4.params(mode=fd4.VALLEY, postprocess_scales=1))
-    # one post-processing: K strip launches (N at the selected scales), the walk, the copy
-    assert post.kernel_count() == plain.kernel_count() + len(SIGMAS) + 2
+    # one post-processing: the chunk masks and K strip launches (N at the selected
+    # scales), the walk, the copy
+    assert post.kernel_count() == plain.kernel_count() + 1 + len(SIGMAS) + 2
     plain.close()
     post.close()
     u = fd4.to_device(synth.vessel_tree(4800, 32, 32, depth=3, r0=3.0))
