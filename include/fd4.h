@@ -361,46 +361,56 @@ int fd4_autotune_batched(const fd4_image *h_imgs, int n_images, const float *h_s
  * predicts the per-pixel scale index the vesselness argmax (Sec. 3.3) would
  * select, trained on labels the plain selection produces, with the plain
  * selection as fallback and reference.  Network: four dilated 3x3 convolutions
- * (dilations 1, 2, 4, 8; channels 1-32-32-32-8; zero padding), ReLU between
- * them, softmax over 8 scale bins.  BF16 weights and activations, FP32
- * accumulation on the tensor cores (tcgen05).
+ * (dilations 1, 2, 4, 8; channels 1-32-32-32-16; zero padding), ReLU between
+ * them, softmax over the first n_bins outputs (one bin per scale of the set,
+ * 2 <= n_bins <= FD4_SELECTOR_MAX_BINS; the other outputs are unused).  BF16
+ * weights and activations, FP32 accumulation on the tensor cores (tcgen05).
  * Parameters live in a caller-owned device buffer of
  * fd4_selector_param_bytes() bytes (256-byte aligned): FP32 master weights
  * (order: per layer W[ky][kx][co][ci] then b[co]), Adam moments, accumulated
  * gradients, and the BF16 kernel layouts derived from the master weights.
  * Image stacks are n_img images of w x h, row pitch `pitch`, image after image
  * (h * pitch floats apart).                                                  */
+#define FD4_SELECTOR_MAX_BINS 16
 size_t fd4_selector_param_bytes(void);
+/* Workspace of fd4_selector_grad (training: every layer's input is kept). */
 size_t fd4_selector_workspace_bytes(int n_img, int w, int h, int pitch);
+/* Workspace of fd4_selector_forward and fd4_selector_predict (inference). */
+size_t fd4_selector_infer_workspace_bytes(int n_img, int w, int h, int pitch);
 /* He-normal weights from a seed, zero biases, zero moments (synchronous). */
 int fd4_selector_init(void *d_params, unsigned long long seed, fd4_stream_t stream);
 /* Master weights from / to the host (synchronous); which: 0 weights,
  * 1 and 2 Adam moments, 3 accumulated gradients.                            */
 int fd4_selector_set_weights(void *d_params, const float *h_weights, fd4_stream_t stream);
 int fd4_selector_get_weights(const void *d_params, float *h_weights, int which, fd4_stream_t stream);
-/* Logits (8 floats per pixel, pixel layout of the stack) of every image.    */
+/* Logits (n_bins floats per pixel, pixel layout of the stack) of every image. */
 int fd4_selector_forward(const void *d_params, const float *d_imgs, int n_img, int w, int h, int pitch,
-                         float *d_logits, void *d_ws, size_t ws_bytes, fd4_stream_t stream);
-/* Forward and backward pass: adds the gradient of the mean cross-entropy
- * against d_labels (uint8 bin per pixel, stack layout) to the accumulated
- * gradients, and the mean loss to *d_loss.                                  */
+                         int n_bins, float *d_logits, void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+/* Forward and backward pass: adds the gradient of the mean cross-entropy of
+ * the softmax over n_bins against d_labels (uint8 bin per pixel, stack
+ * layout; labels >= n_bins count as n_bins - 1) to the accumulated gradients,
+ * and the mean loss to *d_loss.                                             */
 int fd4_selector_grad(void *d_params, const float *d_imgs, const uint8_t *d_labels, int n_img, int w, int h,
-                      int pitch, float *d_loss, void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+                      int pitch, int n_bins, float *d_loss, void *d_ws, size_t ws_bytes, fd4_stream_t stream);
 /* Adam step (beta 0.9 / 0.999, eps 1e-8) on the accumulated gradients, which
  * are then cleared; step counts from 1.                                     */
 int fd4_selector_update(void *d_params, float lr, int step, fd4_stream_t stream);
-/* Scale index (argmax bin) and confidence (its probability) per pixel.     */
-int fd4_selector_predict(const void *d_params, const float *d_img, int w, int h, int pitch, uint8_t *d_idx,
-                         float *d_conf, void *d_ws, size_t ws_bytes, fd4_stream_t stream);
+/* Scale index (argmax of the n_bins logits, ties to the smaller) and
+ * confidence (its softmax probability, nullable) per pixel of every image of
+ * the stack (one launch per layer for the whole stack); d_idx and d_conf in
+ * the stack's pixel layout.                                                 */
+int fd4_selector_predict(const void *d_params, const float *d_imgs, int n_img, int w, int h, int pitch, int n_bins,
+                         uint8_t *d_idx, float *d_conf, void *d_ws, size_t ws_bytes, fd4_stream_t stream);
 /* Learned selection with the plain selection as fallback and reference.  The
  * network predicts a scale index and a confidence (its softmax probability)
  * per pixel; every 32 x 64 tile whose least confident pixel is below
  * conf_threshold is recomputed with the plain vesselness selection
  * (fd4_select_scales restricted to those tiles).  Reading for the restricted
  * selection: c = half the maximum of S over the recomputed tiles (with every
- * tile recomputed this is exactly fd4_select_scales).  n_sigma must be 8 (the
- * network's bins); d_conf (nullable) receives the confidences, d_n_fallback
- * (nullable, device int) the number of recomputed tiles.                    */
+ * tile recomputed this is exactly fd4_select_scales).  The network's bins are
+ * the n_sigma scales (2 <= n_sigma <= FD4_SELECTOR_MAX_BINS); d_conf (nullable)
+ * receives the confidences, d_n_fallback (nullable, device int) the number of
+ * recomputed tiles.                                                         */
 size_t fd4_select_learned_workspace_bytes(int w, int h, int pitch, int n_sigma);
 int fd4_select_scales_learned(const void *d_params, const float *d_img, int w, int h, int pitch,
                               const float *h_sigmas, int n_sigma, const fd4_params *params, float conf_threshold,

@@ -3,7 +3,8 @@
 // argmax and the plain sweep checks it).
 //
 // Network: four dilated 3 x 3 convolutions (dilations 1, 2, 4, 8; channels
-// 1 -> 32 -> 32 -> 32 -> 8), ReLU between them, softmax over 8 scale bins.
+// 1 -> 32 -> 32 -> 32 -> 16), ReLU between them, softmax over the first n_bins
+// (<= 16) outputs, one bin per scale of the set (8 or 12 in the workloads).
 // Activations are NHWC bf16 (16 channels for the input layer, 32 after);
 // weights bf16; accumulation FP32 in tensor memory.
 //
@@ -197,9 +198,9 @@ __global__ void __launch_bounds__(CT) k_conv_tc(ConvArgs a)
 // Network geometry and the parameter buffer.
 
 constexpr int kLayers = 4;
-constexpr int kBins = 8;
+constexpr int kMaxBins = FD4_SELECTOR_MAX_BINS;  // outputs of the last layer; n_bins of them are used
 constexpr int CI_R[kLayers] = {1, 32, 32, 32};   // real channels
-constexpr int CO_R[kLayers] = {32, 32, 32, kBins};
+constexpr int CO_R[kLayers] = {32, 32, 32, kMaxBins};
 constexpr int CI_P[kLayers] = {16, 32, 32, 32};  // padded to the MMA's K and N granularity
 constexpr int CO_P[kLayers] = {32, 32, 32, 16};
 constexpr int DIL[kLayers] = {1, 2, 4, 8};
@@ -302,41 +303,47 @@ __global__ void k_sel_prep(const float *img, __nv_bfloat16 *act, int n_img, int 
     }
 }
 
-// Softmax cross-entropy over the 8 logits of every pixel: mean loss added to
-// *loss, gradient (p - onehot) / npx written as bf16 (16 channels, 8..15 zero).
+// Softmax cross-entropy over the n_bins logits of every pixel (n_bins floats
+// per pixel): mean loss added to *loss, gradient (p - onehot) / npx written as
+// bf16 (16 channels, those from n_bins on zero).
 __global__ void __launch_bounds__(256) k_sel_softmax_ce(const float *logits, const uint8_t *labels,
                                                         __nv_bfloat16 *dz, int n_img, int w, int h, int pitch,
-                                                        long long img_stride, float inv_npx, float *loss)
+                                                        long long img_stride, float inv_npx, float *loss, int n_bins)
 {
     __shared__ float red[8];
     float lsum = 0.0f;
     for (int row = blockIdx.x; row < n_img * h; row += gridDim.x)
     for (int x = threadIdx.x; x < pitch; x += blockDim.x) {
         const size_t i = (size_t)(row / h) * (size_t)img_stride + (size_t)(row % h) * pitch + x;
-        float g[kBins];
+        float g[kMaxBins];
+#pragma unroll
+        for (int c = 0; c < kMaxBins; ++c) g[c] = 0.0f;
         if (x < w) {
-            const float *z = logits + i * kBins;
+            const float *z = logits + i * n_bins;
             float m = z[0];
-            for (int c = 1; c < kBins; ++c) m = fmaxf(m, z[c]);
+            for (int c = 1; c < n_bins; ++c) m = fmaxf(m, z[c]);
             float sum = 0.0f;
-            for (int c = 0; c < kBins; ++c) {
-                g[c] = expf(z[c] - m);
-                sum += g[c];
-            }
-            const int lab = labels[i] < kBins ? labels[i] : kBins - 1;
+#pragma unroll
+            for (int c = 0; c < kMaxBins; ++c)
+                if (c < n_bins) {
+                    g[c] = expf(z[c] - m);
+                    sum += g[c];
+                }
+            const int lab = labels[i] < n_bins ? labels[i] : n_bins - 1;
             lsum += logf(sum) - (z[lab] - m);
-            for (int c = 0; c < kBins; ++c) g[c] = (g[c] / sum - (c == lab ? 1.0f : 0.0f)) * inv_npx;
-        } else {
-            for (int c = 0; c < kBins; ++c) g[c] = 0.0f;
+#pragma unroll
+            for (int c = 0; c < kMaxBins; ++c)
+                if (c < n_bins) g[c] = (g[c] / sum - (c == lab ? 1.0f : 0.0f)) * inv_npx;
         }
         uint4 *o = reinterpret_cast<uint4 *>(dz + i * 16);
-        uint32_t q[4];
-        for (int c = 0; c < 4; ++c) {
+        uint32_t q[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
             __nv_bfloat162 b = __floats2bfloat162_rn(g[2 * c], g[2 * c + 1]);
             q[c] = *reinterpret_cast<uint32_t *>(&b);
         }
         o[0] = make_uint4(q[0], q[1], q[2], q[3]);
-        o[1] = make_uint4(0u, 0u, 0u, 0u);
+        o[1] = make_uint4(q[4], q[5], q[6], q[7]);
     }
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lsum;
@@ -434,23 +441,24 @@ __global__ void k_sel_adam(float *w, float *m, float *v, float *g, size_t n, flo
     }
 }
 
-// Inference read-out: scale bin = argmax of the logits (ties to the smaller
-// bin), confidence = its softmax probability.
-__global__ void k_sel_predict(const float *logits, int w, int h, int pitch, uint8_t *idx, float *conf)
+// Inference read-out over a stack of n_img images: scale bin = argmax of the
+// n_bins logits (ties to the smaller bin), confidence = its softmax probability.
+__global__ void k_sel_predict(const float *logits, int n_img, int w, int h, int pitch, int n_bins, uint8_t *idx,
+                              float *conf)
 {
-    for (int y = blockIdx.x; y < h; y += gridDim.x)
+    for (int row = blockIdx.x; row < n_img * h; row += gridDim.x)
     for (int x = threadIdx.x; x < w; x += blockDim.x) {
-        const size_t i = (size_t)y * pitch + x;
-        const float *z = logits + i * kBins;
+        const size_t i = (size_t)row * pitch + x;
+        const float *z = logits + i * n_bins;
         int arg = 0;
         float m = z[0];
-        for (int c = 1; c < kBins; ++c)
+        for (int c = 1; c < n_bins; ++c)
             if (z[c] > m) {
                 m = z[c];
                 arg = c;
             }
         float sum = 0.0f;
-        for (int c = 0; c < kBins; ++c) sum += expf(z[c] - m);
+        for (int c = 0; c < n_bins; ++c) sum += expf(z[c] - m);
         idx[i] = (uint8_t)arg;
         if (conf) conf[i] = 1.0f / sum;
     }
@@ -543,25 +551,37 @@ int launch_conv(const ConvArgs &a, cudaStream_t st)
 
 struct SelBufs {
     __nv_bfloat16 *act[kLayers];  // inputs of layers 0..3 (16 / 32 / 32 / 32 channels)
-    float *logits;                // 8 per pixel
+    float *logits;                // n_bins per pixel (room for kMaxBins)
     __nv_bfloat16 *dz16;          // gradient of the last layer's output (16 channels)
     __nv_bfloat16 *dz[2];         // 32-channel gradients (ping-pong)
     int *status;
     size_t bytes;
 };
 
-SelBufs sel_bufs(char *ws, long long npx)
+// Workspace of the network.  Training keeps every layer's input for the
+// backward pass; inference (infer) needs the input of the current layer only,
+// so layers 1 and 3 share one buffer: [status | act0 (16 channels) | A | B |
+// logits], with act1 = act3 = A and act2 = B.
+SelBufs sel_bufs(char *ws, long long npx, bool infer = false)
 {
     SelBufs b{};
     size_t o = 256;  // header: status word
     b.status = (int *)ws;
     const size_t per[kLayers] = {16, 32, 32, 32};
     for (int l = 0; l < kLayers; ++l) {
+        if (infer && l == 3) {
+            b.act[3] = b.act[1];
+            continue;
+        }
         b.act[l] = ws ? (__nv_bfloat16 *)(ws + o) : nullptr;
         o += align_up((size_t)npx * per[l] * 2, 256);
     }
     b.logits = ws ? (float *)(ws + o) : nullptr;
-    o += align_up((size_t)npx * kBins * 4, 256);
+    o += align_up((size_t)npx * kMaxBins * 4, 256);
+    if (infer) {
+        b.bytes = o;
+        return b;
+    }
     b.dz16 = ws ? (__nv_bfloat16 *)(ws + o) : nullptr;
     o += align_up((size_t)npx * 16 * 2, 256);
     for (int k = 0; k < 2; ++k) {
@@ -622,8 +642,8 @@ int check_stack(const void *d, int n_img, int w, int h, int pitch)
 }
 
 // Forward pass of the network over a stack of n_img images (img_stride = h * pitch).
-int sel_forward(const SelPtrs &P, const float *imgs, int n_img, int w, int h, int pitch, const SelBufs &B,
-                cudaStream_t st)
+int sel_forward(const SelPtrs &P, const float *imgs, int n_img, int w, int h, int pitch, int n_bins,
+                const SelBufs &B, cudaStream_t st)
 {
     const long long stride = (long long)h * pitch;
     const int g = n_img * h < 8192 ? n_img * h : 8192;  // blocks stride over image rows
@@ -650,7 +670,7 @@ int sel_forward(const SelPtrs &P, const float *imgs, int n_img, int w, int h, in
             rc = launch_conv<32, 32, CONV_RELU_BF16>(a, st);
         } else {
             a.out = B.logits;
-            a.n_out = kBins;
+            a.n_out = n_bins;
             rc = launch_conv<32, 16, CONV_LOGITS_F32>(a, st);
         }
         if (rc) return 1;
@@ -682,6 +702,12 @@ extern "C" size_t fd4_selector_workspace_bytes(int n_img, int w, int h, int pitc
 {
     if (n_img < 1 || w < 1 || h < 1 || pitch < w) return 0;
     return sel_bufs(nullptr, (long long)n_img * h * pitch).bytes;
+}
+
+extern "C" size_t fd4_selector_infer_workspace_bytes(int n_img, int w, int h, int pitch)
+{
+    if (n_img < 1 || w < 1 || h < 1 || pitch < w) return 0;
+    return sel_bufs(nullptr, (long long)n_img * h * pitch, true).bytes;
 }
 
 extern "C" int fd4_selector_set_weights(void *d_params, const float *h_w, fd4_stream_t stream)
@@ -735,29 +761,32 @@ extern "C" int fd4_selector_init(void *d_params, unsigned long long seed, fd4_st
     return rc;
 }
 
+static bool bins_ok(int n_bins) { return n_bins >= 2 && n_bins <= kMaxBins; }
+
 extern "C" int fd4_selector_forward(const void *d_params, const float *d_imgs, int n_img, int w, int h, int pitch,
-                                    float *d_logits, void *d_ws, size_t ws_bytes, fd4_stream_t stream)
+                                    int n_bins, float *d_logits, void *d_ws, size_t ws_bytes, fd4_stream_t stream)
 {
     int rc;
-    if (!d_params || !d_logits) return FD4_ERR_BAD_ARG;
+    if (!d_params || !d_logits || !bins_ok(n_bins)) return FD4_ERR_BAD_ARG;
     if ((rc = check_stack(d_imgs, n_img, w, h, pitch)) != FD4_OK) return rc;
     const long long npx = (long long)n_img * h * pitch;
-    if (!d_ws || ws_bytes < fd4_selector_workspace_bytes(n_img, w, h, pitch)) return FD4_ERR_WS_TOO_SMALL;
+    if (!d_ws || ws_bytes < fd4_selector_infer_workspace_bytes(n_img, w, h, pitch)) return FD4_ERR_WS_TOO_SMALL;
     cudaStream_t st = (cudaStream_t)stream;
-    SelBufs B = sel_bufs((char *)d_ws, npx);
+    SelBufs B = sel_bufs((char *)d_ws, npx, true);
     if (cudaMemsetAsync(B.status, 0, sizeof(int), st) != cudaSuccess) return FD4_ERR_CUDA;
-    if (sel_forward(sel_ptrs((void *)d_params), d_imgs, n_img, w, h, pitch, B, st)) return FD4_ERR_CUDA;
-    if (cudaMemcpyAsync(d_logits, B.logits, sizeof(float) * kBins * npx, cudaMemcpyDeviceToDevice, st) !=
+    if (sel_forward(sel_ptrs((void *)d_params), d_imgs, n_img, w, h, pitch, n_bins, B, st)) return FD4_ERR_CUDA;
+    if (cudaMemcpyAsync(d_logits, B.logits, sizeof(float) * n_bins * npx, cudaMemcpyDeviceToDevice, st) !=
         cudaSuccess)
         return FD4_ERR_CUDA;
     return FD4_OK;
 }
 
 extern "C" int fd4_selector_grad(void *d_params, const float *d_imgs, const uint8_t *d_labels, int n_img, int w,
-                                 int h, int pitch, float *d_loss, void *d_ws, size_t ws_bytes, fd4_stream_t stream)
+                                 int h, int pitch, int n_bins, float *d_loss, void *d_ws, size_t ws_bytes,
+                                 fd4_stream_t stream)
 {
     int rc;
-    if (!d_params || !d_labels || !d_loss) return FD4_ERR_BAD_ARG;
+    if (!d_params || !d_labels || !d_loss || !bins_ok(n_bins)) return FD4_ERR_BAD_ARG;
     if ((rc = check_stack(d_imgs, n_img, w, h, pitch)) != FD4_OK) return rc;
     const long long npx = (long long)n_img * h * pitch;
     if (!d_ws || ws_bytes < fd4_selector_workspace_bytes(n_img, w, h, pitch)) return FD4_ERR_WS_TOO_SMALL;
@@ -766,10 +795,10 @@ extern "C" int fd4_selector_grad(void *d_params, const float *d_imgs, const uint
     const SelPtrs P = sel_ptrs(d_params);
     const long long stride = (long long)h * pitch;
     if (cudaMemsetAsync(B.status, 0, sizeof(int), st) != cudaSuccess) return FD4_ERR_CUDA;
-    if (sel_forward(P, d_imgs, n_img, w, h, pitch, B, st)) return FD4_ERR_CUDA;
+    if (sel_forward(P, d_imgs, n_img, w, h, pitch, n_bins, B, st)) return FD4_ERR_CUDA;
     const int g = n_img * h < 8192 ? n_img * h : 8192;
     k_sel_softmax_ce<<<g, 256, 0, st>>>(B.logits, d_labels, B.dz16, n_img, w, h, pitch, stride,
-                                        1.0f / (float)((long long)n_img * w * h), d_loss);
+                                        1.0f / (float)((long long)n_img * w * h), d_loss, n_bins);
     ConvArgs a{};
     a.n_img = n_img;
     a.w = w;
@@ -814,19 +843,20 @@ extern "C" int fd4_selector_update(void *d_params, float lr, int step, fd4_strea
     return cudaGetLastError() == cudaSuccess ? FD4_OK : FD4_ERR_CUDA;
 }
 
-extern "C" int fd4_selector_predict(const void *d_params, const float *d_img, int w, int h, int pitch,
-                                    uint8_t *d_idx, float *d_conf, void *d_ws, size_t ws_bytes, fd4_stream_t stream)
+extern "C" int fd4_selector_predict(const void *d_params, const float *d_imgs, int n_img, int w, int h, int pitch,
+                                    int n_bins, uint8_t *d_idx, float *d_conf, void *d_ws, size_t ws_bytes,
+                                    fd4_stream_t stream)
 {
     int rc;
-    if (!d_params || !d_idx) return FD4_ERR_BAD_ARG;
-    if ((rc = check_image(d_img, w, h, pitch)) != FD4_OK) return rc;
-    if (!d_ws || ws_bytes < fd4_selector_workspace_bytes(1, w, h, pitch)) return FD4_ERR_WS_TOO_SMALL;
+    if (!d_params || !d_idx || !bins_ok(n_bins)) return FD4_ERR_BAD_ARG;
+    if ((rc = check_stack(d_imgs, n_img, w, h, pitch)) != FD4_OK) return rc;
+    if (!d_ws || ws_bytes < fd4_selector_infer_workspace_bytes(n_img, w, h, pitch)) return FD4_ERR_WS_TOO_SMALL;
     cudaStream_t st = (cudaStream_t)stream;
-    SelBufs B = sel_bufs((char *)d_ws, (long long)h * pitch);
+    SelBufs B = sel_bufs((char *)d_ws, (long long)n_img * h * pitch, true);
     if (cudaMemsetAsync(B.status, 0, sizeof(int), st) != cudaSuccess) return FD4_ERR_CUDA;
-    if (sel_forward(sel_ptrs((void *)d_params), d_img, 1, w, h, pitch, B, st)) return FD4_ERR_CUDA;
-    const int g = h < 8192 ? h : 8192;
-    k_sel_predict<<<g, 256, 0, st>>>(B.logits, w, h, pitch, d_idx, d_conf);
+    if (sel_forward(sel_ptrs((void *)d_params), d_imgs, n_img, w, h, pitch, n_bins, B, st)) return FD4_ERR_CUDA;
+    const int g = n_img * h < 8192 ? n_img * h : 8192;
+    k_sel_predict<<<g, 256, 0, st>>>(B.logits, n_img, w, h, pitch, n_bins, d_idx, d_conf);
     return cudaGetLastError() == cudaSuccess ? FD4_OK : FD4_ERR_CUDA;
 }
 
@@ -842,7 +872,7 @@ extern "C" int fd4_selector_status(const void *d_ws, int *status, fd4_stream_t s
 // Workspace: [selector buffers | confidence plane | selection workspace | tile list].
 static size_t learned_parts(int w, int h, int pitch, int n_sigma, size_t *o_conf, size_t *o_sel, size_t *o_list)
 {
-    size_t o = align_up(fd4_selector_workspace_bytes(1, w, h, pitch), 256);
+    size_t o = align_up(fd4_selector_infer_workspace_bytes(1, w, h, pitch), 256);
     *o_conf = o;
     o += align_up((size_t)h * pitch * sizeof(float), 256);
     *o_sel = o;
@@ -871,7 +901,7 @@ extern "C" int fd4_select_scales_learned(const void *d_params, const float *d_im
     if (!d_params || !d_sigma_idx) return FD4_ERR_BAD_ARG;
     if ((rc = check_image(d_img, w, h, pitch)) != FD4_OK) return rc;
     if ((rc = check_sigmas(h_sigmas, n_sigma)) != FD4_OK) return rc;
-    if (n_sigma != kBins) return FD4_ERR_BAD_ARG;  // the network predicts 8 scale bins
+    if (!bins_ok(n_sigma)) return FD4_ERR_BAD_ARG;  // one bin per scale, at most kMaxBins
     if (!(conf_threshold >= 0.0f && conf_threshold <= 1.0f)) return FD4_ERR_BAD_ARG;
     size_t o_conf, o_sel, o_list;
     const size_t need = learned_parts(w, h, pitch, n_sigma, &o_conf, &o_sel, &o_list);
@@ -884,8 +914,8 @@ extern "C" int fd4_select_scales_learned(const void *d_params, const float *d_im
     int *list = (int *)(ws + o_list);
     const int tiles = ((w + 31) / 32) * ((h + 63) / 64);
     int *count = list + tiles;
-    if ((rc = fd4_selector_predict(d_params, d_img, w, h, pitch, d_sigma_idx, conf, d_ws, ws_bytes, stream)) !=
-        FD4_OK)
+    if ((rc = fd4_selector_predict(d_params, d_img, 1, w, h, pitch, n_sigma, d_sigma_idx, conf, d_ws, ws_bytes,
+                                   stream)) != FD4_OK)
         return rc;
     if (cudaMemsetAsync(count, 0, sizeof(int), st) != cudaSuccess) return FD4_ERR_CUDA;
     k_sel_fallback_tiles<<<tiles, 256, 0, st>>>(conf, w, h, pitch, conf_threshold, list, count);

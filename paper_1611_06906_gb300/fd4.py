@@ -111,13 +111,14 @@ NOALLOC_MAX_PIXELS = 4 * 1024 * 1024
 SELECTOR_SIGNATURES = {
     "fd4_selector_param_bytes": (_sz, []),
     "fd4_selector_workspace_bytes": (_sz, [_i, _i, _i, _i]),
+    "fd4_selector_infer_workspace_bytes": (_sz, [_i, _i, _i, _i]),
     "fd4_selector_set_weights": (_i, [_vp, _fp, _vp]),
     "fd4_selector_get_weights": (_i, [_vp, _fp, _i, _vp]),
     "fd4_selector_init": (_i, [_vp, ctypes.c_ulonglong, _vp]),
-    "fd4_selector_forward": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _sz, _vp]),
-    "fd4_selector_grad": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _sz, _vp]),
+    "fd4_selector_forward": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _sz, _vp]),
+    "fd4_selector_grad": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _sz, _vp]),
     "fd4_selector_update": (_i, [_vp, ctypes.c_float, _i, _vp]),
-    "fd4_selector_predict": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _vp, _sz, _vp]),
+    "fd4_selector_predict": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _sz, _vp]),
     "fd4_selector_status": (_i, [_vp, _ip, _vp]),
     "fd4_select_learned_workspace_bytes": (_sz, [_i, _i, _i, _i]),
     "fd4_selftest_wait_timeout": (_i, [_vp, _sz, _ip, _vp]),
@@ -464,8 +465,8 @@ def autotune_batched(imgs, sigmas, T: float, M: int, n: int = 0, prm: Params | N
 # ---------------------------------------------------------------------------
 # Learned scale selector (network weights live in a caller-owned device buffer)
 
-SEL_BINS = 8
-SEL_LAYERS = [(1, 32), (32, 32), (32, 32), (32, SEL_BINS)]  # (in, out) channels
+SEL_MAX_BINS = 16  # FD4_SELECTOR_MAX_BINS: outputs of the last layer, the first n_bins used
+SEL_LAYERS = [(1, 32), (32, 32), (32, 32), (32, SEL_MAX_BINS)]  # (in, out) channels
 
 
 def selector_n_master() -> int:
@@ -497,43 +498,46 @@ class Selector:
         return f
 
     @staticmethod
-    def workspace(n_img: int, w: int, h: int, pitch: int, device="cuda"):
+    def workspace(n_img: int, w: int, h: int, pitch: int, device="cuda", infer: bool = False):
+        """Workspace of grad (training), or of forward / predict with infer=True."""
         torch = _torch()
-        return torch.empty(int(lib().fd4_selector_workspace_bytes(n_img, w, h, pitch)), dtype=torch.uint8,
-                           device=device)
+        fn = lib().fd4_selector_infer_workspace_bytes if infer else lib().fd4_selector_workspace_bytes
+        return torch.empty(int(fn(n_img, w, h, pitch)), dtype=torch.uint8, device=device)
 
-    def forward(self, imgs, w: int, ws=None, stream=None):
-        """imgs: (n, h, pitch) float32 -> logits (n, h, pitch, 8)."""
+    def forward(self, imgs, w: int, n_bins: int = 8, ws=None, stream=None):
+        """imgs: (n, h, pitch) float32 -> logits (n, h, pitch, n_bins)."""
         torch = _torch()
         n, h, pitch = imgs.shape
-        ws = ws if ws is not None else self.workspace(n, w, h, pitch, imgs.device)
-        out = torch.empty((n, h, pitch, SEL_BINS), dtype=torch.float32, device=imgs.device)
-        _check(lib().fd4_selector_forward(_ptr(self.params), _ptr(imgs), n, int(w), h, pitch, _ptr(out), _ptr(ws),
-                                          ws.numel(), _stream(stream)), "fd4_selector_forward")
+        ws = ws if ws is not None else self.workspace(n, w, h, pitch, imgs.device, infer=True)
+        out = torch.empty((n, h, pitch, n_bins), dtype=torch.float32, device=imgs.device)
+        _check(lib().fd4_selector_forward(_ptr(self.params), _ptr(imgs), n, int(w), h, pitch, int(n_bins), _ptr(out),
+                                          _ptr(ws), ws.numel(), _stream(stream)), "fd4_selector_forward")
         return out
 
-    def grad(self, imgs, labels, w: int, loss, ws=None, stream=None):
+    def grad(self, imgs, labels, w: int, loss, n_bins: int = 8, ws=None, stream=None):
         """Adds the loss gradient of the batch to the parameter buffer; loss += mean CE."""
         n, h, pitch = imgs.shape
         ws = ws if ws is not None else self.workspace(n, w, h, pitch, imgs.device)
         _check(lib().fd4_selector_grad(_ptr(self.params), _ptr(imgs), _ptr(labels), n, int(w), h, pitch,
-                                       _ptr(loss), _ptr(ws), ws.numel(), _stream(stream)), "fd4_selector_grad")
+                                       int(n_bins), _ptr(loss), _ptr(ws), ws.numel(), _stream(stream)),
+               "fd4_selector_grad")
 
     def update(self, lr: float, step: int, stream=None):
         _check(lib().fd4_selector_update(_ptr(self.params), float(lr), int(step), _stream(stream)),
                "fd4_selector_update")
 
-    def predict(self, img, w: int, idx=None, conf=None, ws=None, stream=None):
-        """img: (h, pitch) float32 -> (scale index uint8, confidence float32), both (h, pitch)."""
+    def predict(self, img, w: int, n_bins: int = 8, idx=None, conf=None, ws=None, stream=None):
+        """img: (h, pitch) or a stack (n, h, pitch) of float32 -> (scale index uint8,
+        confidence float32), both of img's shape (one launch per layer for the stack)."""
         torch = _torch()
-        h, pitch = img.shape
-        ws = ws if ws is not None else self.workspace(1, w, h, pitch, img.device)
+        n, h, pitch = (1,) + tuple(img.shape) if img.dim() == 2 else tuple(img.shape)
+        ws = ws if ws is not None else self.workspace(n, w, h, pitch, img.device, infer=True)
         if idx is None:
-            idx = torch.zeros((h, pitch), dtype=torch.uint8, device=img.device)
+            idx = torch.zeros(img.shape, dtype=torch.uint8, device=img.device)
         if conf is None:
-            conf = torch.zeros((h, pitch), dtype=torch.float32, device=img.device)
-        _check(lib().fd4_selector_predict(_ptr(self.params), _ptr(img), int(w), h, pitch, _ptr(idx), _ptr(conf),
-                                          _ptr(ws), ws.numel(), _stream(stream)), "fd4_selector_predict")
+            conf = torch.zeros(img.shape, dtype=torch.float32, device=img.device)
+        _check(lib().fd4_selector_predict(_ptr(self.params), _ptr(img), n, int(w), h, pitch, int(n_bins), _ptr(idx),
+                                          _ptr(conf), _ptr(ws), ws.numel(), _stream(stream)), "fd4_selector_predict")
         return idx, conf
 
     def select_learned(self, img, w: int, sigmas, prm: Params | None = None, conf_threshold: float = 0.5,

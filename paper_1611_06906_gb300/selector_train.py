@@ -4,10 +4,12 @@ Every arithmetic step runs in libfd4 (forward and backward passes on the
 tensor cores, Adam on the device); this module only generates the seeded
 inputs, moves them to the device and loops.
 
-Training set: 256 x 256 crops of seeded fundus-like images (the
-`batch64_fundus` generator at side 2048, 64 crops each), labelled with the
+Training set: 256 x 256 crops of seeded source images, labelled with the
 scale index the plain vesselness selection picks on the whole source image
 (so the labels see the same image-wide Frangi c as inference on full images).
+Sources: "fundus" -- the `batch64_fundus` generator at side 2048 (64 crops
+each); "tree16" -- the full-size workload's 4096^2 trees (256 crops each).
+The seeds (from 900000 on) are disjoint from the benchmark's images.
 """
 from __future__ import annotations
 
@@ -19,37 +21,41 @@ import numpy as np
 from . import fd4, synth
 
 CROP = 256
-SOURCE = 2048
+SOURCES = {"fundus": 2048, "tree16": 4096}
 
 
-def _render(seed):
-    return synth.fundus_like(seed, SOURCE)
+def _render(args):
+    kind, seed = args
+    if kind == "tree16":
+        return synth.tree16(seed)
+    return synth.fundus_like(seed, SOURCES["fundus"])
 
 
-def source_images(n_sources: int, seed0: int = 900000, procs: int = 16):
+def source_images(n_sources: int, kind: str = "fundus", seed0: int = 900000, procs: int = 16):
     """Seeded source images (host float32), rendered in a spawn pool (so the
     calling script must guard its entry point with if __name__ == "__main__")."""
-    seeds = [seed0 + i for i in range(n_sources)]
+    args = [(kind, seed0 + i) for i in range(n_sources)]
     with mp.get_context("spawn").Pool(max(1, min(procs, os.cpu_count() or 1))) as pool:
-        return pool.map(_render, seeds)
+        return pool.map(_render, args)
 
 
-def make_training_set(n_crops: int, sigmas, mode: int, seed0: int = 900000, device="cuda"):
+def make_training_set(n_crops: int, sigmas, mode: int, kind: str = "fundus", seed0: int = 900000, device="cuda"):
     """(crops (n, 256, 256) float32, labels (n, 256, 256) uint8) on the device."""
     import torch
-    per = (SOURCE // CROP) ** 2
+    side = SOURCES[kind]
+    per = (side // CROP) ** 2
     n_src = -(-n_crops // per)
-    srcs = source_images(n_src, seed0)
+    srcs = source_images(n_src, kind, seed0)
     crops = torch.empty((n_crops, CROP, CROP), dtype=torch.float32, device=device)
     labels = torch.empty((n_crops, CROP, CROP), dtype=torch.uint8, device=device)
     prm = fd4.params(mode=mode)
-    ws = fd4.workspace(fd4.OP_SELECT_SCALES, SOURCE, SOURCE, len(sigmas), device)
+    ws = fd4.workspace(fd4.OP_SELECT_SCALES, side, side, len(sigmas), device)
     k = 0
     for img in srcs:
         u = fd4.to_device(img, device)
-        idx, _ = fd4.select_scales(u, SOURCE, sigmas, prm, ws=ws)
-        for cy in range(0, SOURCE, CROP):
-            for cx in range(0, SOURCE, CROP):
+        idx, _ = fd4.select_scales(u, side, sigmas, prm, ws=ws)
+        for cy in range(0, side, CROP):
+            for cx in range(0, side, CROP):
                 if k == n_crops:
                     break
                 crops[k] = u[cy:cy + CROP, cx:cx + CROP]
@@ -58,7 +64,7 @@ def make_training_set(n_crops: int, sigmas, mode: int, seed0: int = 900000, devi
     return crops, labels
 
 
-def train(sel: "fd4.Selector", crops, labels, epochs: int = 1, batch: int = 32, lr: float = 2e-3,
+def train(sel: "fd4.Selector", crops, labels, n_bins: int, epochs: int = 1, batch: int = 32, lr: float = 2e-3,
           seed: int = 1, log_every: int = 0):
     """Adam over shuffled mini-batches.  Returns the per-step mean losses."""
     import torch
@@ -76,7 +82,7 @@ def train(sel: "fd4.Selector", crops, labels, epochs: int = 1, batch: int = 32, 
             xb = crops.index_select(0, sel_idx).contiguous()
             yb = labels.index_select(0, sel_idx).contiguous()
             loss.zero_()
-            sel.grad(xb, yb, CROP, loss, ws=ws)
+            sel.grad(xb, yb, CROP, loss, n_bins=n_bins, ws=ws)
             step += 1
             # cosine decay of the step size over the run
             frac = step / max(1, epochs * (n // batch))
