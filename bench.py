@@ -405,6 +405,16 @@ def run_fd4(args, rank, world, local_rank):
             "bytes_per_px_step": 24, "steps_per_launch": S,
             "avg_launch_us": fed_kernel_ms * 1e3 / fed_launches, "copy_back_launches_per_pass": fed_copy_backs,
             "algorithmic_bytes_per_launch": fed_bytes / fed_launches}
+    # the selection stage is FP32-FMA bound: its algorithmic FMAs per pass (row and
+    # column pass of 3 fields at every scale, radius ceil(4 sigma)) against the
+    # FMA rate measured on this GPU
+    fma_sel = sum(6 * (2 * math.ceil(4 * sg) + 1) for sg in sig) * npx
+    fma_scalar, fma_pair = fd4.measure_fma_rate()
+    fma_peak = max(fma_scalar, fma_pair)
+    alu = {"fp32_fma_rate_measured_tfma": {"scalar": fma_scalar, "packed_pairs": fma_pair},
+           "selection_stage": {"algorithmic_fma_per_pass": fma_sel,
+                               "achieved_tfma": fma_sel / (sel_ms * 1e-3) / 1e12,
+                               "frac_of_measured_fma_rate": fma_sel / (sel_ms * 1e-3) / 1e12 / fma_peak}}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -421,7 +431,7 @@ def run_fd4(args, rank, world, local_rank):
                           npx * 4e-9, npx * 16e-9)},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
            "clocks": clk.summary(),
-           "stages_ms_per_step": {"select": sel_ms, "tensor": ten_ms, "fed": fed_ms},
+           "stages_ms_per_step": {"select": sel_ms, "tensor": ten_ms, "fed": fed_ms}, "alu": alu,
            "plain": plain}
     if learned is not None:
         out["learned"] = learned
@@ -464,6 +474,15 @@ def run_fd4(args, rank, world, local_rank):
                          "sigma_agreement": agree,
                          "sigma_disagreements": _tie_report(O, big, sig, mode, i_s[:, :w_s].cpu().numpy(), ridx),
                          "max_abs_own_selection": err}
+        # the learned selector's scale image on the same sample: the filter's
+        # distance from the oracle's (the method with the plain selection)
+        if learned is not None and "_sel" in learned:
+            i_n, _ = learned["_sel"].predict(u_s, w_s, n_bins=K)
+            o_n, _ = fd4.filter_image(u_s, w_s, sig, T, M, n, prm, sigma_idx=i_n)
+            dn = np.abs(o_n[:, :w_s].cpu().numpy() - ref)
+            learned["network_only"]["vs_oracle"] = {
+                "images": what, "max_abs": float(dn.max()), "mean_abs": float(dn.mean()),
+                "sigma_agreement_with_oracle": float((i_n[:, :w_s].cpu().numpy() == ridx).mean())}
         # the variant legs against the oracle's variant on the 256^2 crop
         sm = center_crop(big, 256)
         u_sm = fd4.to_device(sm, dev)
@@ -498,7 +517,10 @@ def run_fd4(args, rank, world, local_rank):
         leg.pop("_kw", None)
         out[name] = leg
     if world == 1 and not args.no_creases:
-        out["creases"] = crease_leg(args, ims, wl, mode, stream, torch, fd4)
+        out["creases"] = crease_leg(args, ims, wl, mode, stream, torch, fd4,
+                                    learned.get("_sel") if learned is not None else None, prm)
+    if learned is not None:
+        learned.pop("_sel", None)
     for g in {id(x): x for x in (g_all, g_one, g_sel, g_ten, g_fed)}.values():
         g.close()
     print(json.dumps(out), flush=True)
@@ -521,15 +543,50 @@ def _tie_report(O, img, sig, mode, idx_gpu, idx_oracle):
     return rep
 
 
-def crease_leg(args, ims, wl, mode, stream, torch, fd4):
+def _clip_split(gt, lo, hi, shift, max_len=32.0):
+    """Ground-truth centre-line pieces clipped to the square [lo, hi]^2 (then
+    shifted by -shift) and cut into pieces of at most max_len pixels: a chain
+    of the reconstruction is matched piece by piece, so a branch hundreds of
+    pixels long is scored along its whole length."""
+    out = []
+    for g in gt:
+        ax, ay, bx, by = g[0], g[1], g[2], g[3]
+        t0, t1 = 0.0, 1.0
+        ok = True
+        for p, q in ((-(bx - ax), ax - lo), (bx - ax, hi - ax), (-(by - ay), ay - lo), (by - ay, hi - ay)):
+            if p == 0.0:
+                if q < 0.0:
+                    ok = False
+                continue
+            r = q / p
+            if p < 0.0:
+                t0 = max(t0, r)
+            else:
+                t1 = min(t1, r)
+        if not ok or t1 <= t0:
+            continue
+        x0, y0 = ax + t0 * (bx - ax), ay + t0 * (by - ay)
+        x1, y1 = ax + t1 * (bx - ax), ay + t1 * (by - ay)
+        k = max(1, int(math.ceil(math.hypot(x1 - x0, y1 - y0) / max_len)))
+        for i in range(k):
+            f0, f1 = i / k, (i + 1) / k
+            out.append((x0 + f0 * (x1 - x0) - shift, y0 + f0 * (y1 - y0) - shift,
+                        x0 + f1 * (x1 - x0) - shift, y0 + f1 * (y1 - y0) - shift) + tuple(g[4:]))
+    return out
+
+
+def crease_leg(args, ims, wl, mode, stream, torch, fd4, sel=None, prm=None):
     """Crease extraction (Sec. 4) timed over the filtered batch, and the accuracy
     of Sec. 5 (E, p against the generator's centre lines, 6-pixel
-    neighbourhood) of the creases of the input and of the filtered output: on
-    the two smallest images of the fundus batch (inside the field of view), or
-    on the central 1024^2 window of the first 4096^2 tree (pieces inside it)."""
+    neighbourhood) of the creases of the input, of the filtered output and of
+    the output filtered from the learned selector's scales: on the two smallest
+    images of the fundus batch (pieces inside the field of view), or on the
+    central 1024^2 window of the first 4096^2 tree; the centre lines are cut
+    into pieces of at most 32 px."""
     import ctypes
     from paper_1611_06906_gb300 import creases, synth
     sigma_d = 1.0
+    sig, M, n, T = wl["sigmas"], wl["M"], wl["n"], wl["T"]
     maxw = max(b.w for b in ims)
     maxh = max(b.h for b in ims)
     cap = 2 * (maxw - 1) * (maxh - 1)
@@ -551,6 +608,14 @@ def crease_leg(args, ims, wl, mode, stream, torch, fd4):
     torch.cuda.synchronize()
     ms = _timed(run_all, 3, stream, torch) / 3
     del segs, keys
+
+    def learned_out(b):
+        if sel is None:
+            return None
+        idx, _ = sel.predict(b.u_in, b.w, n_bins=len(sig))
+        o, _ = fd4.filter_image(b.u_in, b.w, sig, T, M, n, prm, sigma_idx=idx)
+        return o
+
     acc = []
     if wl["name"] == "batch64_fundus":
         base = rank_seed(3000, 0)
@@ -561,16 +626,19 @@ def crease_leg(args, ims, wl, mode, stream, torch, fd4):
             c = (side - 1) / 2.0
             gt = [g for g in synth.vessel_tree_centrelines(base + i, side, side, depth=6, noise=0.0)
                   if max(math.hypot(g[0] - c, g[1] - c), math.hypot(g[2] - c, g[3] - c)) < 0.9 * 0.48 * side]
+            gt = _clip_split(gt, 0.0, side - 1.0, 0.0)
             pairs = [(ims[i].u_in, ims[i].w), (ims[i].out, ims[i].w)]
+            lo = learned_out(ims[i])
+            if lo is not None:
+                pairs.append((lo, ims[i].w))
             acc.append(_crease_accuracy(fd4, creases, pairs, gt, sigma_d, mode, "%dx%d" % (ims[i].w, ims[i].h)))
     elif wl["name"] == "tree16_4096":
         win, y0 = 1024, (4096 - 1024) // 2
-        gt = [(g[0] - y0, g[1] - y0, g[2] - y0, g[3] - y0) + tuple(g[4:])
-              for g in synth.vessel_tree_centrelines(tree16_seed(0, 0), 4096, 4096, depth=8, r0=12.0, r1=0.75,
-                                                     noise=0.15)
-              if min(g[0], g[1], g[2], g[3]) >= y0 + 8 and max(g[0], g[1], g[2], g[3]) <= y0 + win - 8]
+        gt = _clip_split(synth.vessel_tree_centrelines(tree16_seed(0, 0), 4096, 4096, depth=8, r0=12.0, r1=0.75,
+                                                       noise=0.15), y0 + 8.0, y0 + win - 9.0, float(y0))
         pairs = []
-        for t in (ims[0].u_in, ims[0].out):
+        lo = learned_out(ims[0])
+        for t in (ims[0].u_in, ims[0].out) + ((lo,) if lo is not None else ()):
             crop = fd4.empty_image(win, win, device=t.device)
             crop[:, :win] = t[y0:y0 + win, y0:y0 + win]
             pairs.append((crop, win))
@@ -581,13 +649,14 @@ def crease_leg(args, ims, wl, mode, stream, torch, fd4):
 
 
 def _crease_accuracy(fd4, creases, pairs, gt, sigma_d, mode, label):
-    (u_in, w_in), (u_out, w_out) = pairs
-    s_in, _ = fd4.extract_creases(u_in, w_in, sigma_d, mode)
-    s_out, _ = fd4.extract_creases(u_out, w_out, sigma_d, mode)
-    e_in, p_in = creases.evaluate(s_in, gt)
-    e_out, p_out = creases.evaluate(s_out, gt)
-    return {"image": label, "E_input": e_in, "p_input": p_in, "E_filtered": e_out, "p_filtered": p_out,
-            "segments_input": int(len(s_in)), "segments_filtered": int(len(s_out)), "truth_segments": len(gt)}
+    res = {"image": label, "truth_segments": len(gt)}
+    for name, (u, w) in zip(("input", "filtered", "filtered_learned_scales"), pairs):
+        s_, _ = fd4.extract_creases(u, w, sigma_d, mode)
+        e, p = creases.evaluate(s_, gt)
+        res["E_" + name] = e
+        res["p_" + name] = p
+        res["segments_" + name] = int(len(s_))
+    return res
 
 
 def learned_variant(args, ims, wl, sig, T, M, n, mode, sched, stream, torch, fd4):
@@ -600,9 +669,10 @@ def learned_variant(args, ims, wl, sig, T, M, n, mode, sched, stream, torch, fd4
         batch when the images have one size), then the batched filter graph
         with those scales given -- its rate, its scale agreement with the plain
         selection and its output's distance from the plain filter's;
-      * network with the exact fallback: every 32 x 64 tile holding a pixel
-        below the confidence threshold is selected again by the plain sweep --
-        the result is the plain filter where every tile falls back."""
+      * network with the plain fallback: every 32 x 64 tile holding a pixel
+        below the confidence threshold is selected again by the plain sweep
+        (with the threshold at 1 every tile is, and the result is the plain
+        filter's)."""
     from paper_1611_06906_gb300 import selector_train as ST
     K = len(sig)
     kind = "tree16" if wl["name"] == "tree16_4096" else "fundus"
@@ -658,7 +728,7 @@ def learned_variant(args, ims, wl, sig, T, M, n, mode, sched, stream, torch, fd4
                "max_abs_diff_to_plain_filter": max(float(d.max()) for d in diff),
                "mean_abs_diff_to_plain_filter": sum(float(d.double().sum()) for d in diff) / npx,
                "launches_per_layer": 1 if same else len(ims)}
-    # the exact path: the network's confident tiles, the plain sweep on the rest
+    # the fallback path: the network's confident tiles, the plain sweep on the rest
     thr = args.sel_threshold
     big = max(ims, key=lambda b: b.h * b.pitch)
     wsl = torch.empty(int(fd4.lib().fd4_select_learned_workspace_bytes(big.pitch, big.h, big.pitch, K)),
@@ -677,14 +747,15 @@ def learned_variant(args, ims, wl, sig, T, M, n, mode, sched, stream, torch, fd4
     fb = sum(int(x.item()) for x in nfb_l)
     tiles = sum(((b.w + 31) // 32) * ((b.h + 63) // 64) for b in ims)
     agree = sum(int((a[:, :b.w] == b.idx[:, :b.w]).sum().item()) for a, b in zip(idx_l, ims)) / npx
-    exact = {"value": px_steps / (ex_ms * 1e-3) / 1e6, "ms_per_step": ex_ms, "conf_threshold": thr,
+    fallback = {"value": px_steps / (ex_ms * 1e-3) / 1e6, "ms_per_step": ex_ms, "conf_threshold": thr,
              "sigma_agreement_with_plain": agree, "fallback_tile_fraction": fb / tiles,
              "max_abs_diff_to_plain_filter": max(float((o[:, :b.w] - b.out[:, :b.w]).abs().max())
                                                  for o, b in zip(outs_l, ims))}
     g.close()
-    return {"value": exact["value"], "ms_per_step": ex_ms,
-            "value_is": "network with the exact fallback (the result of the plain filter)",
-            "bins": K, "exact": exact, "network_only": net_out,
+    return {"value": net_out["value"], "ms_per_step": net_ms,
+            "value_is": "network-only scale selection + the batched filter graph (an approximation of the "
+                        "method: see its agreement and its distance from the plain filter and the oracle)",
+            "bins": K, "network_only": net_out, "with_fallback": fallback, "_sel": sel,
             "train": {"crops": args.sel_crops, "source": kind, "epochs": args.sel_epochs, "steps": len(losses),
                       "loss_first": losses[0], "loss_last": float(np.mean(losses[-10:])),
                       "set_seconds": t_set, "train_seconds": train_s}}
@@ -751,7 +822,7 @@ def main():
     ap.add_argument("--no-creases", action="store_true", help="skip the crease extraction and its accuracy")
     ap.add_argument("--two-streams", type=int, default=0, help="headline graph on two streams (1) or one (0)")
     ap.add_argument("--sel-crops", type=int, default=10000, help="training crops (256^2) of the learned selector")
-    ap.add_argument("--sel-epochs", type=int, default=2, help="training epochs of the learned selector")
+    ap.add_argument("--sel-epochs", type=int, default=4, help="training epochs of the learned selector")
     ap.add_argument("--sel-threshold", type=float, default=0.5, help="fallback confidence threshold")
     ap.add_argument("--only-graph", action="store_true", help="replay the full graph only (profiling)")
     ap.add_argument("--traffic", type=float, default=None,

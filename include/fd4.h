@@ -437,6 +437,16 @@ int fd4_selector_status(const void *d_ws, int *status, fd4_stream_t stream);
  * fd4_selector_workspace_bytes(1, 128, 4, 128) bytes.                       */
 int fd4_selftest_wait_timeout(void *d_ws, size_t ws_bytes, int *status, fd4_stream_t stream);
 
+/* FP32 FMA rate of the current GPU, measured (no counterpart in the paper):
+ * the denominator of the fractions quoted for the FMA-bound kernels.  Times
+ * a kernel of independent FMA chains on every SM in the scalar form and in
+ * packed pairs (two FP32 lanes per instruction), best of three launches after
+ * one warm-up, with CUDA events on `stream` (synchronous).  *scalar_tfma and
+ * *pair_tfma receive the rates in 1e12 FMA/s.  d_scratch: device memory of at
+ * least 8 x 4 x (the SM count) bytes (a sink the kernels never write).      */
+int fd4_measure_fma_rate(void *d_scratch, size_t scratch_bytes, double *scalar_tfma, double *pair_tfma,
+                         fd4_stream_t stream);
+
 /* Failure-detection self-test of the FED kernels (no counterpart in the
  * paper): one launch of the TMA-staged FED kernel on the image d_u with the
  * tile copies withheld (the tile barrier is armed for bytes that never come)

@@ -93,6 +93,7 @@ SIGNATURES = {
     "fd4_fed_cycle": (_i, [_vp, _i, _i, _i, _vp, _dp, _i, _i, _vp, _sz, _vp]),
     "fd4_fed_cycle_sched": (_i, [_vp, _i, _i, _i, _vp, _dp, _i, _i, _i, _i, _i, _vp, _sz, _vp]),
     "fd4_selftest_fed_wait_timeout": (_i, [_vp, _i, _i, _i, _vp, _vp, _sz, _ip, _vp]),
+    "fd4_measure_fma_rate": (_i, [_vp, _sz, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _vp]),
     "fd4_filter": (_i, [_vp, _vp, _i, _i, _i, _fp, _i, _pp, ctypes.c_double, _i, _i, _vp, _i, _vp,
                         _sz, _vp]),
     "fd4_fed_cycle_noalloc": (_i, [_vp, _i, _i, _i, _vp, _dp, _i, _i, _vp]),
@@ -322,6 +323,16 @@ def fed_cycle(u, w: int, tensor, tau, boundary: int = NATURAL, ws=None, stream=N
                                          int(boundary), steps, rows, quads, _ptr(ws), ws.numel(), _stream(stream)),
                "fd4_fed_cycle_sched")
     return u
+
+
+def measure_fma_rate(stream=None):
+    """fd4_measure_fma_rate: (scalar, packed-pair) FP32 FMA rates in 1e12 FMA/s."""
+    torch = _torch()
+    buf = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().fd4_measure_fma_rate(_ptr(buf), buf.numel(), ctypes.byref(a), ctypes.byref(b), _stream(stream)),
+           "fd4_measure_fma_rate")
+    return a.value, b.value
 
 
 def selftest_fed_wait_timeout(u, w: int, tensor, ws=None, stream=None) -> int:

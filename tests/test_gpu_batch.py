@@ -224,3 +224,11 @@ def test_two_stream_graph_equals_one_stream_graph():
             assert float((o[:, :w] - r[:, :w]).abs().max()) == 0.0
     g1.close()
     g2.close()
+
+
+def test_measured_fma_rate_is_plausible():
+    """The FP32 FMA rate measured by fd4_measure_fma_rate lies between a tenth
+    and twice of 152 SMs x 128 lanes x 2.07 GHz (40.3e12 FMA/s)."""
+    scalar, pair = fd4.measure_fma_rate()
+    for r in (scalar, pair):
+        assert 4.0 < r < 81.0, (scalar, pair)
