@@ -16,7 +16,9 @@
 // K-major no-swizzle descriptor, no im2col copy.  B (the weights of all nine
 // taps) is staged once per block.  One thread issues 9 * CI/16 MMAs of
 // 128 x CO x 16, commits them to an mbarrier, and the four warps read the
-// FP32 accumulator back from their TMEM lanes for the epilogue.
+// FP32 accumulator back from their TMEM lanes for the epilogue.  The weight
+// gradient is a tensor-core product too, with the pixels as the reduction
+// dimension (k_sel_wgrad_tc).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -355,29 +357,73 @@ __global__ void __launch_bounds__(256) k_sel_softmax_ce(const float *logits, con
     }
 }
 
-// Weight gradient of one layer on the CUDA cores (FP32):
-// gW[t][co][ci] += sum_px dZ[px][co] X[px + shift_t][ci], gb[co] += sum_px dZ[px][co].
-// A block owns 128-pixel row tiles (as the convolution) and keeps its partial
-// sums in registers across tiles; each thread covers one output channel and a
-// strided subset of (tap, input channel) pairs.
-template <int CIP, int COP>
-__global__ void __launch_bounds__(CT) k_sel_wgrad(const __nv_bfloat16 *X, const __nv_bfloat16 *dZ, int ci_r, int co_r,
-                                                  int n_img, int w, int h, int pitch, int d, long long img_stride,
-                                                  float *gW, float *gb)
+// Weight gradient of one layer on the tensor cores:
+//   gW[t][co][ci] += sum_px dZ[px][co] X[px + shift_t][ci],  gb[co] += sum_px dZ[px][co],
+// as the product D[m][n] = sum_k A[m][k] B[n][k] over the pixels k of a
+// 128-pixel row tile (the MMA's K, 16 per instruction): A's rows m are the
+// output channels (COP of the 128 rows; the rest stay zero), B's rows n are
+// the tap-shifted inputs n = t CIP + ci, then a row of ones whose product is
+// the bias gradient, then zero rows up to a multiple of 16.  Both operands
+// are K-major without swizzle (8 x 16-byte core matrices: LBO 128 bytes
+// along K, SBO 2048 bytes along M / N).  A persistent block accumulates all
+// its tiles in tensor memory (lane = output channel, column = n) and adds the
+// sums to gW and gb once at the end.
+template <int CIP>
+constexpr int wg_rows() { return 9 * CIP + 16; }
+template <int CIP>
+constexpr size_t wg_smem()
 {
-    constexpr int NG = CT / COP;              // thread groups
-    constexpr int NP = 9 * CIP / NG;          // (tap, ci) pairs per thread
-    __shared__ __nv_bfloat16 xs[3][TM + 2 * kMaxDil][CIP];
-    __shared__ float zs[TM][COP + 1];
-    const int tid = threadIdx.x;
-    const int co = tid % COP, g = tid / COP;
-    float acc[NP];
-    float bacc = 0.0f;
-#pragma unroll
-    for (int k = 0; k < NP; ++k) acc[k] = 0.0f;
+    return 1024 + (size_t)2 * 128 * TM + (size_t)2 * wg_rows<CIP>() * TM + (size_t)2 * 3 * (TM + 2 * kMaxDil) * CIP;
+}
+
+__device__ __forceinline__ uint32_t wg_off(int row, int k)  // byte offset of element (row, k), K-major core layout
+{
+    return (uint32_t)((row >> 3) * 2048 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+template <int CIP, int COP>
+__global__ void __launch_bounds__(CT, 1)
+    k_sel_wgrad_tc(const __nv_bfloat16 *X, const __nv_bfloat16 *dZ, int ci_r, int co_r, int n_img, int w, int h,
+                   int pitch, int d, long long img_stride, float *gW, float *gb, int *status)
+{
+    constexpr int NB = wg_rows<CIP>(), CJ = CIP / 8;
+    constexpr int N0 = NB > 256 ? ((NB / 2 + 15) / 16) * 16 : NB;  // first chunk of B rows (MMA N <= 256)
+    constexpr int N1 = NB - N0;
+    static_assert(N0 % 16 == 0 && N1 % 16 == 0 && N0 <= 256 && N1 <= 256, "MMA N of M = 128");
+    extern __shared__ unsigned char wg_raw[];
+    unsigned char *As = reinterpret_cast<unsigned char *>(((uintptr_t)wg_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *Bs = As + 2 * 128 * TM;
+    __nv_bfloat16 *Xs = reinterpret_cast<__nv_bfloat16 *>(Bs + 2 * NB * TM);  // [3][P][CIP]
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int P = TM + 2 * d;
+    // A: all zero (rows from COP on stay so); B: the ones row and the zero rows after it
+    for (int i = tid; i < 128 * TM * 2 / 16; i += CT) reinterpret_cast<uint4 *>(As)[i] = make_uint4(0u, 0u, 0u, 0u);
+    {
+        const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
+        for (int i = tid; i < (NB - 9 * CIP) * TM; i += CT) {
+            const int row = 9 * CIP + i / TM, k = i % TM;
+            *reinterpret_cast<__nv_bfloat16 *>(Bs + wg_off(row, k)) = row == 9 * CIP ? one : zero;
+        }
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_base, 512);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(&mbar, 1);
+        abort_flag = 0;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
     const int tiles_x = (w + TM - 1) / TM;
     const long long total = (long long)n_img * h * tiles_x;
+    uint32_t phase = 0;
+    bool any = false;
     for (long long t = blockIdx.x; t < total; t += gridDim.x) {
         const int tx = (int)(t % tiles_x);
         const long long rr = t / tiles_x;
@@ -385,45 +431,111 @@ __global__ void __launch_bounds__(CT) k_sel_wgrad(const __nv_bfloat16 *X, const 
         const int img = (int)(rr / h);
         const int x0 = tx * TM;
         const size_t base = (size_t)img * (size_t)img_stride;
-        __syncthreads();
+        // X rows y - d, y, y + d; pixels x0 - d .. x0 + TM - 1 + d (zero outside the image)
         for (int ky = 0; ky < 3; ++ky) {
             const int gy = y + (ky - 1) * d;
             const bool row_in = gy >= 0 && gy < h;
-            for (int e = tid; e < P * CIP; e += CT) {
-                const int c = e % CIP, p = e / CIP;  // CIP is a compile-time power of two
+            for (int e = tid; e < P * CJ; e += CT) {
+                const int j = e % CJ, p = e / CJ;
                 const int gx = x0 - d + p;
-                __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
-                if (row_in && gx >= 0 && gx < w) v = X[(base + (size_t)gy * pitch + gx) * CIP + c];
-                xs[ky][p][c] = v;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (row_in && gx >= 0 && gx < w)
+                    v = *reinterpret_cast<const uint4 *>(X + (base + (size_t)gy * pitch + gx) * CIP + 8 * j);
+                *reinterpret_cast<uint4 *>(Xs + ((size_t)ky * P + p) * CIP + 8 * j) = v;
             }
         }
-        for (int i = tid; i < TM * COP; i += CT) {
-            const int c = i % COP, p = i / COP;
-            const int gx = x0 + p;
-            zs[p][c] = gx < w ? __bfloat162float(dZ[(base + (size_t)y * pitch + gx) * COP + c]) : 0.0f;
+        // A rows co < COP: dZ of the tile's pixels (zero beyond the image)
+        for (int e = tid; e < TM * (COP / 8); e += CT) {
+            const int k = e % TM, g = e / TM;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (x0 + k < w) v = *reinterpret_cast<const uint4 *>(dZ + (base + (size_t)y * pitch + x0 + k) * COP + 8 * g);
+            const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                *reinterpret_cast<unsigned short *>(As + wg_off(8 * g + r, k)) =
+                    (unsigned short)(vw[r >> 1] >> (16 * (r & 1)));
         }
+        __syncthreads();  // Xs is complete
+        // B rows n = t CIP + ci: core matrix (8 channels x 8 pixels) from 8 pixel chunks
+        for (int e = tid; e < (9 * CJ) * (TM / 8); e += CT) {
+            const int kg = e % (TM / 8), ng = e / (TM / 8);
+            const int tap = ng / CJ, j = ng % CJ, ky = tap / 3, kx = tap % 3;
+            uint4 px[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                px[q] = *reinterpret_cast<const uint4 *>(Xs + ((size_t)ky * P + 8 * kg + q + kx * d) * CIP + 8 * j);
+            // channel c of pixel q: half (c % 2) of word c / 2 of px[q]; row c of the
+            // core matrix packs pixels (2i, 2i + 1) into word i
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const unsigned sel = (c & 1) ? 0x7632u : 0x5410u;
+                uint32_t wq[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    wq[q] = (c >> 1) == 0 ? px[q].x : (c >> 1) == 1 ? px[q].y : (c >> 1) == 2 ? px[q].z : px[q].w;
+                uint4 row;
+                row.x = __byte_perm(wq[0], wq[1], sel);
+                row.y = __byte_perm(wq[2], wq[3], sel);
+                row.z = __byte_perm(wq[4], wq[5], sel);
+                row.w = __byte_perm(wq[6], wq[7], sel);
+                *reinterpret_cast<uint4 *>(Bs + wg_off(8 * ng + c, 8 * kg)) = row;
+            }
+        }
+        tc::fence_proxy_async();
         __syncthreads();
-        for (int p = 0; p < TM; ++p) {
-            const float dz = zs[p][co];
-            if (g == 0) bacc += dz;
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs);
+#pragma unroll 1
+            for (int ks = 0; ks < TM / 16; ++ks) {
+                const uint32_t acc = (any || ks > 0) ? 1u : 0u;
+                const uint64_t ad = tc::sdesc_kmajor(a0 + ks * 256, 128, 2048);
+                tc::mma_bf16(tmem, ad, tc::sdesc_kmajor(b0 + ks * 256, 128, 2048), tc::idesc_bf16_f32(128, N0), acc);
+                if (N1 > 0)
+                    tc::mma_bf16(tmem + N0, ad, tc::sdesc_kmajor(b0 + (N0 / 8) * 2048 + ks * 256, 128, 2048),
+                                 tc::idesc_bf16_f32(128, N1), acc);
+            }
+            tc::mma_commit(&mbar);
+        }
+        any = true;
+        {  // the MMAs have read the operands before they are restaged: at most one second
+            const uint64_t t0 = globaltimer();
+            while (!tc::mbar_try_wait(&mbar, phase)) {
+                if (globaltimer() - t0 > 1000000000ull) {
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+            }
+        }
+        phase ^= 1u;
+        tc::fence_after_sync();
+        __syncthreads();
+        if (abort_flag) break;
+    }
+    // the sums: warp 0's lanes are the output channels
+    if (any && !abort_flag && warp == 0) {
+#pragma unroll 1
+        for (int cb = 0; cb < (NB + 31) / 32; ++cb) {
+            float v[32];
+            tc::tmem_ld_x32(tmem + (uint32_t)(cb * 32), v);
+            if (lane < co_r) {
 #pragma unroll
-            for (int k = 0; k < NP; ++k) {
-                const int q = g + k * NG;          // pair index = tap * CIP + ci
-                const int tap = q / CIP, ci = q - tap * CIP;
-                const int ky = tap / 3, kx = tap - 3 * ky;
-                acc[k] = fmaf(dz, __bfloat162float(xs[ky][p + kx * d][ci]), acc[k]);
+                for (int i = 0; i < 32; ++i) {
+                    const int n = cb * 32 + i;
+                    if (n < 9 * CIP) {
+                        const int tap = n / CIP, ci = n - tap * CIP;
+                        if (ci < ci_r) atomicAdd(gW + ((size_t)tap * co_r + lane) * ci_r + ci, v[i]);
+                    } else if (n == 9 * CIP) {
+                        atomicAdd(gb + lane, v[i]);
+                    }
+                }
             }
         }
     }
-    if (co < co_r) {
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            const int q = g + k * NG;
-            const int tap = q / CIP, ci = q - tap * CIP;
-            if (ci < ci_r) atomicAdd(gW + ((size_t)tap * co_r + co) * ci_r + ci, acc[k]);
-        }
-        if (g == 0) atomicAdd(gb + co, bacc);
-    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if (tid == 0 && abort_flag && status) atomicExch(status, FD4_ERR_TIMEOUT);
 }
 
 // Adam on the FP32 master weights; the gradient is cleared afterwards.
@@ -680,14 +792,25 @@ int sel_forward(const SelPtrs &P, const float *imgs, int n_img, int w, int h, in
 
 template <int CIP, int COP>
 int launch_wgrad(const __nv_bfloat16 *X, const __nv_bfloat16 *dZ, int l, const SelPtrs &P, int n_img, int w, int h,
-                 int pitch, cudaStream_t st)
+                 int pitch, int *status, cudaStream_t st)
 {
     const SelLayout L = sel_layout();
+    static int attr_dev = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (attr_dev != dev) {
+        if (cudaFuncSetAttribute(k_sel_wgrad_tc<CIP, COP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)wg_smem<CIP>()) != cudaSuccess)
+            return 1;
+        attr_dev = dev;
+    }
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long tiles = (long long)n_img * h * ((w + TM - 1) / TM);
-    const int grid = persistent_grid((const void *)k_sel_wgrad<CIP, COP>, CT, 0,
-                                     (int)(tiles < (1 << 30) ? tiles : (1 << 30)));
-    k_sel_wgrad<CIP, COP><<<grid, CT, 0, st>>>(X, dZ, CI_R[l], CO_R[l], n_img, w, h, pitch, DIL[l],
-                                               (long long)h * pitch, P.grad + L.w_off[l], P.grad + L.b_off[l]);
+    const int grid = (int)(tiles < sms ? (tiles > 0 ? tiles : 1) : sms);  // one block (all of TMEM) per SM
+    k_sel_wgrad_tc<CIP, COP><<<grid, CT, wg_smem<CIP>(), st>>>(X, dZ, CI_R[l], CO_R[l], n_img, w, h, pitch, DIL[l],
+                                                               (long long)h * pitch, P.grad + L.w_off[l],
+                                                               P.grad + L.b_off[l], status);
     return cudaGetLastError() != cudaSuccess;
 }
 
@@ -807,7 +930,7 @@ extern "C" int fd4_selector_grad(void *d_params, const float *d_imgs, const uint
     a.img_stride = stride;
     a.status = B.status;
     // layer 3 (last): weight gradient, then data gradient into dz[0] masked by act[3] > 0
-    if (launch_wgrad<32, 16>(B.act[3], B.dz16, 3, P, n_img, w, h, pitch, st)) return FD4_ERR_CUDA;
+    if (launch_wgrad<32, 16>(B.act[3], B.dz16, 3, P, n_img, w, h, pitch, B.status, st)) return FD4_ERR_CUDA;
     a.in = B.dz16;
     a.out = B.dz[0];
     a.wts = P.dgr[3];
@@ -817,7 +940,7 @@ extern "C" int fd4_selector_grad(void *d_params, const float *d_imgs, const uint
     if (launch_conv<16, 32, CONV_MASK_BF16>(a, st)) return FD4_ERR_CUDA;
     int cur = 0;
     for (int l = 2; l >= 1; --l) {
-        if (launch_wgrad<32, 32>(B.act[l], B.dz[cur], l, P, n_img, w, h, pitch, st)) return FD4_ERR_CUDA;
+        if (launch_wgrad<32, 32>(B.act[l], B.dz[cur], l, P, n_img, w, h, pitch, B.status, st)) return FD4_ERR_CUDA;
         a.in = B.dz[cur];
         a.out = B.dz[cur ^ 1];
         a.wts = P.dgr[l];
@@ -826,7 +949,7 @@ extern "C" int fd4_selector_grad(void *d_params, const float *d_imgs, const uint
         if (launch_conv<32, 32, CONV_MASK_BF16>(a, st)) return FD4_ERR_CUDA;
         cur ^= 1;
     }
-    if (launch_wgrad<16, 32>(B.act[0], B.dz[cur], 0, P, n_img, w, h, pitch, st)) return FD4_ERR_CUDA;
+    if (launch_wgrad<16, 32>(B.act[0], B.dz[cur], 0, P, n_img, w, h, pitch, B.status, st)) return FD4_ERR_CUDA;
     return FD4_OK;
 }
 

@@ -216,20 +216,22 @@ struct SegGeo {
 // empty plan).  Every row the column pass reads is computed as in the dense
 // walk, so the sums are unchanged.
 template <int R>
-__device__ __forceinline__ void seg_geo(const ImgDesc &d, int local, int seg, int s, bool dense, SegGeo &g)
+__device__ __forceinline__ void seg_geo(const ImgDesc &d, int local, int seg, SegGeo &g)
 {
-    constexpr int NP0 = Piece<R>::NP0, NB = Piece<R>::NB;
     const int tiles_x = (d.w + ST_TX - 1) / ST_TX;
     const int ty = local / tiles_x;
     g.x0 = (local - ty * tiles_x) * ST_TX;
     g.ys = ty * seg;
-    const int nch = (min(g.ys + seg, d.h) - g.ys + ST_CH - 1) / ST_CH;
-    const uint32_t *cm = dense ? nullptr : d.cmask;
-    const int cw = (d.w + 31) / 32;
-    const uint32_t *row = cm ? cm + (size_t)(g.ys / ST_CH) * cw + g.x0 / ST_TX : nullptr;
+}
+
+// The plan from the chunks to visit (bit c of need: chunk c of the segment).
+template <int R>
+__device__ __forceinline__ int seg_plan(unsigned need, int nch, SegGeo &g)
+{
+    constexpr int NP0 = Piece<R>::NP0, NB = Piece<R>::NB;
     int np = 0, prev = -1;
     for (int c = 0; c < nch; ++c) {
-        if (row && !((row[(size_t)c * cw] >> s) & 1u)) continue;
+        if (!((need >> c) & 1u)) continue;
         if (prev >= 0 && (c - prev) * ST_CH <= NB) {
             for (int cc = prev + 1; cc < c; ++cc) g.code[np++] = (unsigned char)(cc | (NP0 << 4));
             g.code[np++] = (unsigned char)(c | (NP0 << 4) | 0x80);
@@ -238,20 +240,37 @@ __device__ __forceinline__ void seg_geo(const ImgDesc &d, int local, int seg, in
         }
         prev = c;
     }
-    g.pieces = np;
+    return np;
 }
 
-// Thread 0: the block's next segment with a non-empty plan, from flat segment
-// t on in steps of the grid: its descriptor, index in its image and plan into
-// the slot; the segment's number (>= I.tiles: none left).
+// Warp 0: the block's next segment with a non-empty plan, from flat segment t
+// on in steps of the grid: its descriptor, index in its image and plan into
+// the slot (written by lane 0); the segment's number (>= I.tiles: none left).
+// Lane c reads the chunk mask of chunk c, so one segment costs one round trip
+// to memory.
 template <int R>
 __device__ __forceinline__ int next_segment(const Imgs &I, const StripArgs &sa, bool dense, int t, TileCache &tc,
                                             ImgDesc &d, int &local, SegGeo &g)
 {
+    const int lane = threadIdx.x & 31;
     for (; t < I.tiles; t += gridDim.x) {
-        find_tile_cached(I, sa.shape, t, tc, d, local);
-        seg_geo<R>(d, local, sa.seg, sa.s, dense, g);
+        if (lane == 0) {
+            find_tile_cached(I, sa.shape, t, tc, d, local);
+            seg_geo<R>(d, local, sa.seg, g);
+        }
+        __syncwarp();
+        const int nch = (min(g.ys + sa.seg, d.h) - g.ys + ST_CH - 1) / ST_CH;
+        unsigned need = nch >= 32 ? 0xffffffffu : (1u << nch) - 1u;
+        if (!dense && d.cmask) {
+            const int cw = (d.w + 31) / 32;
+            bool bit = false;
+            if (lane < nch) bit = (d.cmask[(size_t)(g.ys / ST_CH + lane) * cw + g.x0 / ST_TX] >> sa.s) & 1u;
+            need = __ballot_sync(0xffffffffu, bit);
+        }
+        if (lane == 0) g.pieces = seg_plan<R>(need, nch, g);
+        __syncwarp();
         if (g.pieces > 0) break;
+        __syncwarp();  // every lane has read g before lane 0 rewrites it
     }
     return t;
 }
@@ -281,9 +300,11 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
     const int G = gridDim.x, s = sa.s;
     float bmax = 0.0f;  // selection: max S^2 of this thread's pixels in the current segment
     if (blockIdx.x >= I.tiles) return;
-    if (tid == 0) {
-        tc_reset(tcache);
-        s_t[0] = next_segment<R>(I, sa, DENSE, blockIdx.x, tcache, sd[0], s_local[0], sg[0]);
+    if (tid == 0) tc_reset(tcache);
+    if (warp == 0) {
+        __syncwarp();
+        const int tt = next_segment<R>(I, sa, DENSE, blockIdx.x, tcache, sd[0], s_local[0], sg[0]);
+        if (lane == 0) s_t[0] = tt;
     }
     __syncthreads();
     int t = s_t[0];
@@ -324,8 +345,10 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
         __syncthreads();  // this piece's rows have landed; the previous chunk's column pass is done
         // the block's next segment: its slot held the previous segment, whose last
         // readers (the column pass above) are past this barrier
-        if (i == 0 && tid == 0)
-            s_t[cur ^ 1] = next_segment<R>(I, sa, DENSE, t + G, tcache, sd[cur ^ 1], s_local[cur ^ 1], sg[cur ^ 1]);
+        if (i == 0 && warp == 0) {
+            const int tt = next_segment<R>(I, sa, DENSE, t + G, tcache, sd[cur ^ 1], s_local[cur ^ 1], sg[cur ^ 1]);
+            if (lane == 0) s_t[cur ^ 1] = tt;
+        }
         if (pc.roll) {
             // keep buffer rows ST_CH .. ST_CH + 2R - 1 as rows 0 .. 2R - 1.
             // Thread (row r, columns c .. c + 3) moves rows k0 + r for k0 = 0,
