@@ -197,52 +197,55 @@ def test_bounded_wait_reports_timeout_and_context_survives():
 
 
 def test_trained_network_carries_the_scale_information():
-    """What training gains: on a held-out 4096^2 tree of the full-size workload's
-    kind (12 scales, both creases) the trained network's scale image agrees with
-    the plain selection more often than the untrained network's and than the
-    single most frequent training label, and the filter run from the network's
-    scales lands closer to the plain filter's output than the filter run from
-    that single scale everywhere.  (Against the plain method itself the network
+    """What training gains: trained as the benchmark trains it (10,000 seeded
+    256^2 crops of 4096^2 trees of the full-size workload's kind, 12 scales,
+    both creases, four epochs), the network's scale image of a held-out tree
+    agrees with the plain selection more often than the single most frequent
+    training label does, it is right on pixels where that label is wrong far
+    more often than the untrained network, and the filter run from its scales
+    lands closer to the plain filter's output than the filter run from that
+    single scale everywhere.  (Against the plain method itself the network
     gains time, not accuracy: see the benchmark's `learned` leg.)"""
     import torch
     from paper_1611_06906_gb300 import selector_train as ST
     sig = list(synth.log_sigmas(0.75, 12.0, 12))
     K, mode = len(sig), fd4.BOTH
-    crops, labels = ST.make_training_set(2048, sig, mode, kind="tree16", seed0=990000)
+    crops, labels = ST.make_training_set(10000, sig, mode, kind="tree16", seed0=990000)
     majority = int(torch.bincount(labels.flatten().long(), minlength=K).argmax())
     sel = fd4.Selector()
     sel.init(7)
     src = fd4.to_device(synth.tree16(991000))
-    plain_full, _ = fd4.select_scales(src, 4096, sig, fd4.params(mode=mode))
-    side = 768
-    y0 = (4096 - side) // 2
+    plain, _ = fd4.select_scales(src, 4096, sig, fd4.params(mode=mode))
+    minority = plain[:, :4096] != majority  # where the single most frequent scale is wrong
+
+    def agreement():
+        idx, _ = sel.predict(src, 4096, n_bins=K)
+        hit = idx[:, :4096] == plain[:, :4096]
+        return float(hit.float().mean()), float(hit[minority].float().mean()), idx
+
+    before, before_min, _ = agreement()
+    losses = ST.train(sel, crops, labels, K, epochs=4, batch=32, lr=2e-3)
+    del crops, labels
+    after, after_min, idx = agreement()
+    base = float((~minority).float().mean())
+    msg = dict(before=before, after=after, majority=base, before_minority=before_min, after_minority=after_min,
+               loss_first=losses[0], loss_last=float(np.mean(losses[-10:])))
+    assert np.mean(losses[-10:]) < 0.6 * losses[0], msg
+    assert after > base, msg
+    assert after_min > before_min + 0.05, msg
+    # the filter from the network's scales against the one from a single scale,
+    # on the central 768^2 window (scales of the whole image)
+    side, y0 = 768, (4096 - 768) // 2
     u = fd4.empty_image(side, side)
     u[:, :side] = src[y0:y0 + side, y0:y0 + side]
     p = torch.zeros_like(u, dtype=torch.uint8)
-    p[:, :side] = plain_full[y0:y0 + side, y0:y0 + side]  # labels with the whole image's Frangi c
-
-    minority = p[:, :side] != majority  # where the single most frequent scale is wrong
-
-    def agreement():
-        idx, _ = sel.predict(u, side, n_bins=K)
-        hit = idx[:, :side] == p[:, :side]
-        return float(hit.float().mean()), float(hit[minority].float().mean())
-
-    before, before_min = agreement()
-    losses = ST.train(sel, crops, labels, K, epochs=4, batch=32, lr=3e-3)
-    after, after_min = agreement()
-    base = float((~minority).float().mean())
-    msg = dict(before=before, after=after, majority=base, before_minority=before_min, after_minority=after_min,
-               loss_first=losses[0], loss_last=losses[-1])
-    assert np.mean(losses[-5:]) < 0.9 * losses[0], msg
-    # on the pixels a single scale gets wrong, the trained network is right far more often
-    assert after_min > before_min + 0.05 and after_min > 0.1, msg
-    # the filter from the network's scales against the one from a single scale
+    p[:, :side] = plain[y0:y0 + side, y0:y0 + side]
+    q = torch.zeros_like(p)
+    q[:, :side] = idx[y0:y0 + side, y0:y0 + side]
     T, M, n = 11.0 / 3.0, 2, 10
     prm = fd4.params(mode=mode)
     ref, _ = fd4.filter_image(u, side, sig, T, M, n, prm, sigma_idx=p)
-    idx, _ = sel.predict(u, side, n_bins=K)
-    o_net, _ = fd4.filter_image(u, side, sig, T, M, n, prm, sigma_idx=idx)
+    o_net, _ = fd4.filter_image(u, side, sig, T, M, n, prm, sigma_idx=q)
     o_one, _ = fd4.filter_image(u, side, sig, T, M, n, prm, sigma_idx=torch.full_like(p, majority))
     d_net = float((o_net[:, :side] - ref[:, :side]).abs().mean())
     d_one = float((o_one[:, :side] - ref[:, :side]).abs().mean())
