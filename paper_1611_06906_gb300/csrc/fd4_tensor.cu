@@ -74,11 +74,19 @@ __device__ __forceinline__ void st_wait0() { asm volatile("cp.async.wait_group 0
 template <int R>
 constexpr int st_sw() { return 36 + 2 * R; }  // staged input row stride: >= 32 + 2R, == 4 mod 8
 
-template <int R>
+// NS scales of one padded radius R per launch (the tensor build pairs equal
+// radii): NS row-pass buffers of three fields share one staged input.
+template <int R, int NS = 1>
 constexpr size_t st_smem_bytes()
 {
-    return sizeof(float) * ((size_t)2 * ST_CH * st_sw<R>() + (size_t)3 * (ST_CH + 2 * R) * ST_RS);
+    return sizeof(float) * ((size_t)2 * ST_CH * st_sw<R>() + (size_t)3 * NS * (ST_CH + 2 * R) * ST_RS);
 }
+
+// The taps of the NS scales of one launch.
+template <int R, int NS>
+struct StripTapsN {
+    StripTaps<R> t[NS];
+};
 
 // A segment is walked as a sequence of pieces, each the row pass of up to
 // ST_CH rows into the rolling buffer, listed by a plan (SegGeo::code).  A
@@ -248,7 +256,7 @@ __device__ __forceinline__ int seg_plan(unsigned need, int nch, SegGeo &g)
 // the slot (written by lane 0); the segment's number (>= I.tiles: none left).
 // Lane c reads the chunk mask of chunk c, so one segment costs one round trip
 // to memory.
-template <int R>
+template <int R, int NS>
 __device__ __forceinline__ int next_segment(const Imgs &I, const StripArgs &sa, bool dense, int t, TileCache &tc,
                                             ImgDesc &d, int &local, SegGeo &g)
 {
@@ -264,7 +272,8 @@ __device__ __forceinline__ int next_segment(const Imgs &I, const StripArgs &sa, 
         if (!dense && d.cmask) {
             const int cw = (d.w + 31) / 32;
             bool bit = false;
-            if (lane < nch) bit = (d.cmask[(size_t)(g.ys / ST_CH + lane) * cw + g.x0 / ST_TX] >> sa.s) & 1u;
+            if (lane < nch)
+                bit = (d.cmask[(size_t)(g.ys / ST_CH + lane) * cw + g.x0 / ST_TX] >> sa.s) & ((1u << NS) - 1u);
             need = __ballot_sync(0xffffffffu, bit);
         }
         if (lane == 0) g.pieces = seg_plan<R>(need, nch, g);
@@ -275,22 +284,26 @@ __device__ __forceinline__ int next_segment(const Imgs &I, const StripArgs &sa, 
     return t;
 }
 
-// Scale s (radius R) over every strip segment of the batch.
+// Scale s (radius R) over every strip segment of the batch, or the NS scales
+// s .. s + NS - 1 of one padded radius (tensor build only).
 // Tensor build (ST_TENSOR): idx holds each pixel's selected scale; only pixels
-// with idx == s are written (nfield), and the s == 0 launch also zeroes N where
-// idx lies outside the scale set.  Selection (ST_SELECT): every pixel's Hessian
+// with idx in s .. s + NS - 1 are written (nfield), and the s == 0 launch also
+// zeroes N where idx lies outside the scale set.  Selection (ST_SELECT): every pixel's Hessian
 // at scale s gives the vesselness factor and S^2 of plane s (vp, s2) and the
 // image's max S^2.  The next piece's rows (of this segment or of the block's
 // next one) are copied with cp.async while the current piece is computed.
-template <int R, int MODE>
-__global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripArgs sa)
+template <int R, int MODE, int NS>
+__global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTapsN<R, NS> tpn, StripArgs sa)
 {
     constexpr bool SEL = MODE == ST_SELECT, DENSE = MODE != ST_TENSOR;
+    static_assert(NS == 1 || !DENSE, "scales share a launch in the tensor build only");
     constexpr int NB = ST_CH + 2 * R, SW = st_sw<R>();
+    const StripTaps<R> &tp = tpn.t[0];
     extern __shared__ __align__(16) float stsm[];
-    float *trow = stsm + 2 * ST_CH * SW;  // 3 fields x NB rows x ST_RS; staged rows: two ST_CH x SW buffers
-    __shared__ unsigned short plist[ST_TX * ST_CH];
-    __shared__ int wtot[ST_NT / 32];
+    // staged rows: two ST_CH x SW buffers; then per scale 3 fields x NB rows x ST_RS
+    float *trow = stsm + 2 * ST_CH * SW;
+    __shared__ unsigned short plist[NS][ST_TX * ST_CH];
+    __shared__ int wtot[NS][ST_NT / 32];
     __shared__ ImgDesc sd[2];
     __shared__ int s_local[2];
     __shared__ SegGeo sg[2];
@@ -303,7 +316,7 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
     if (tid == 0) tc_reset(tcache);
     if (warp == 0) {
         __syncwarp();
-        const int tt = next_segment<R>(I, sa, DENSE, blockIdx.x, tcache, sd[0], s_local[0], sg[0]);
+        const int tt = next_segment<R, NS>(I, sa, DENSE, blockIdx.x, tcache, sd[0], s_local[0], sg[0]);
         if (lane == 0) s_t[0] = tt;
     }
     __syncthreads();
@@ -346,7 +359,8 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
         // the block's next segment: its slot held the previous segment, whose last
         // readers (the column pass above) are past this barrier
         if (i == 0 && warp == 0) {
-            const int tt = next_segment<R>(I, sa, DENSE, t + G, tcache, sd[cur ^ 1], s_local[cur ^ 1], sg[cur ^ 1]);
+            const int tt =
+                next_segment<R, NS>(I, sa, DENSE, t + G, tcache, sd[cur ^ 1], s_local[cur ^ 1], sg[cur ^ 1]);
             if (lane == 0) s_t[cur ^ 1] = tt;
         }
         if (pc.roll) {
@@ -359,7 +373,7 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
             for (int k0 = 0; k0 < 2 * R; k0 += ST_CH) {
                 if (k0 + r < 2 * R) {
 #pragma unroll
-                    for (int f = 0; f < 3; ++f) {
+                    for (int f = 0; f < 3 * NS; ++f) {
                         float *fb = trow + f * NB * ST_RS;
                         *reinterpret_cast<float4 *>(fb + (k0 + r) * ST_RS + c) =
                             *reinterpret_cast<const float4 *>(fb + (ST_CH + k0 + r) * ST_RS + c);
@@ -368,7 +382,9 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
             }
             __syncthreads();
         }
-        st_rows2<R>(tp, stsm + buf * ST_CH * SW, trow, pc.b0, pc.n);
+#pragma unroll
+        for (int ns = 0; ns < NS; ++ns)
+            st_rows2<R>(tpn.t[ns], stsm + buf * ST_CH * SW, trow + ns * 3 * NB * ST_RS, pc.b0, pc.n);
         __syncthreads();
 
         if (DENSE && pc.col) {
@@ -439,63 +455,79 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTaps<R> tp, StripA
             }
         }
         if (!DENSE && pc.col) {
-            // the chunk's pixels of this scale, grouped in plist
-            unsigned m[4];
-            int cnt = 0;
+            // the chunk's pixels of each scale, grouped in plist[ns]
+            unsigned m[NS][4];
+            int cnt[NS];
+#pragma unroll
+            for (int ns = 0; ns < NS; ++ns) cnt[ns] = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (s == 0 && ids[j] >= sa.K_total)
                     sd[cur].nfield[(size_t)(y0 + warp * 4 + j) * pitch + x0 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-                m[j] = __ballot_sync(0xffffffffu, ids[j] == s);
-                cnt += __popc(m[j]);
-            }
-            if (lane == 0) wtot[warp] = cnt;
-            __syncthreads();
-            // every warp sums the counts itself: its first list slot and the total
-            int first, total;
-            {
-                const int c = lane < warp ? wtot[lane] : 0, a = lane < ST_NT / 32 ? wtot[lane] : 0;
-                first = c;
-                total = a;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {  // every lane ends with the sums
-                    first += __shfl_xor_sync(0xffffffffu, first, o);
-                    total += __shfl_xor_sync(0xffffffffu, total, o);
+                for (int ns = 0; ns < NS; ++ns) {
+                    m[ns][j] = __ballot_sync(0xffffffffu, ids[j] == s + ns);
+                    cnt[ns] += __popc(m[ns][j]);
                 }
             }
-            {
+            if (lane == 0) {
+#pragma unroll
+                for (int ns = 0; ns < NS; ++ns) wtot[ns][warp] = cnt[ns];
+            }
+            __syncthreads();
+            int total[NS];
+#pragma unroll
+            for (int ns = 0; ns < NS; ++ns) {
+                // every warp sums the counts itself: its first list slot and the total
+                int first;
+                {
+                    const int c = lane < warp ? wtot[ns][lane] : 0, a = lane < ST_NT / 32 ? wtot[ns][lane] : 0;
+                    first = c;
+                    total[ns] = a;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {  // every lane ends with the sums
+                        first += __shfl_xor_sync(0xffffffffu, first, o);
+                        total[ns] += __shfl_xor_sync(0xffffffffu, total[ns], o);
+                    }
+                }
                 int pos = first;
                 const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    if ((m[j] >> lane) & 1u) plist[pos + __popc(m[j] & lt)] = (unsigned short)(((warp * 4 + j) << 5) | lane);
-                    pos += __popc(m[j]);
+                    if ((m[ns][j] >> lane) & 1u)
+                        plist[ns][pos + __popc(m[ns][j] & lt)] = (unsigned short)(((warp * 4 + j) << 5) | lane);
+                    pos += __popc(m[ns][j]);
                 }
             }
             __syncthreads();
             // column pass: output row y0 + py reads buffer rows py .. py + 2R
-            for (int e = tid; e < total; e += ST_NT) {
-                const int entry = plist[e];
-                const int px = entry & 31, py = entry >> 5;
-                const float *c0 = trow + py * ST_RS + px;   // smoothed along x
-                const float *c1 = c0 + NB * ST_RS;           // d/dx
-                const float *c2 = c1 + NB * ST_RS;           // d2/dx2
-                float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
-                {  // (sy, syy) and (sx, sxy) share their input: packed pairs
-                    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int k = 0; k <= 2 * R; ++k) {
-                        const float v0 = c0[k * ST_RS], v1 = c1[k * ST_RS], v2 = c2[k * ST_RS];
-                        a = __ffma2_rn(tp.q12[k], make_float2(v0, v0), a);
-                        b = __ffma2_rn(tp.q01[k], make_float2(v1, v1), b);
-                        sxx = fmaf(tp.w0[k], v2, sxx);
+            for (int ns = 0; ns < NS; ++ns) {
+                const StripTaps<R> &tq = tpn.t[ns];
+                const float *tr = trow + ns * 3 * NB * ST_RS;
+                for (int e = tid; e < total[ns]; e += ST_NT) {
+                    const int entry = plist[ns][e];
+                    const int px = entry & 31, py = entry >> 5;
+                    const float *c0 = tr + py * ST_RS + px;   // smoothed along x
+                    const float *c1 = c0 + NB * ST_RS;         // d/dx
+                    const float *c2 = c1 + NB * ST_RS;         // d2/dx2
+                    float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
+                    {  // (sy, syy) and (sx, sxy) share their input: packed pairs
+                        float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int k = 0; k <= 2 * R; ++k) {
+                            const float v0 = c0[k * ST_RS], v1 = c1[k * ST_RS], v2 = c2[k * ST_RS];
+                            a = __ffma2_rn(tq.q12[k], make_float2(v0, v0), a);
+                            b = __ffma2_rn(tq.q01[k], make_float2(v1, v1), b);
+                            sxx = fmaf(tq.w0[k], v2, sxx);
+                        }
+                        sy = a.x; syy = a.y; sx = b.x; sxy = b.y;
                     }
-                    sy = a.x; syy = a.y; sx = b.x; sxy = b.y;
+                    const float g2 = fmaf(sx, sx, sy * sy);
+                    const float g = sa.grad_sq ? g2 : sqrtf(g2);
+                    const float f = 1.0f / sqrtf(1.0f + g);
+                    sd[cur].nfield[(size_t)(y0 + py) * pitch + x0 + px] = make_float4(f * sxx, f * sxy, f * syy, 0.0f);
                 }
-                const float g2 = fmaf(sx, sx, sy * sy);
-                const float g = sa.grad_sq ? g2 : sqrtf(g2);
-                const float f = 1.0f / sqrtf(1.0f + g);
-                sd[cur].nfield[(size_t)(y0 + py) * pitch + x0 + px] = make_float4(f * sxx, f * sxy, f * syy, 0.0f);
             }
         }
         buf ^= 1;
@@ -550,29 +582,28 @@ __global__ void __launch_bounds__(256) k_chunk_masks(Imgs I, int K)
     }
 }
 
-template <int R, int MODE>
-int launch_strip_k(const Imgs &I, const StripTaps<R> &tp, const StripArgs &a, cudaStream_t st)
+template <int R, int MODE, int NS>
+int launch_strip_k(const Imgs &I, const StripTapsN<R, NS> &tp, const StripArgs &a, cudaStream_t st)
 {
     static int attr_dev = -1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
-    constexpr size_t smem = st_smem_bytes<R>();
+    constexpr size_t smem = st_smem_bytes<R, NS>();
     if (attr_dev != dev) {
-        if (cudaFuncSetAttribute(k_strip<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        if (cudaFuncSetAttribute(k_strip<R, MODE, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return 1;
         attr_dev = dev;
     }
-    const int grid = persistent_grid((const void *)k_strip<R, MODE>, ST_NT, smem, I.tiles);
-    k_strip<R, MODE><<<grid, ST_NT, smem, st>>>(I, tp, a);
+    const int grid = persistent_grid((const void *)k_strip<R, MODE, NS>, ST_NT, smem, I.tiles);
+    k_strip<R, MODE, NS><<<grid, ST_NT, smem, st>>>(I, tp, a);
     return cudaGetLastError() != cudaSuccess;
 }
 
-template <int R, int MODE>
-int launch_strip_scale(const HostBatch &B, const GaussTaps &g, const StripArgs &sa, cudaStream_t st)
+// The taps of one scale in the strip kernels' layout (radius R >= g.r).
+template <int R>
+void strip_taps(const GaussTaps &g, StripTaps<R> &tp)
 {
-    constexpr size_t smem = st_smem_bytes<R>();
-    StripTaps<R> tp;
     const float *src[3] = {g.w0, g.w1, g.w2};
     float *dst[3] = {tp.w0, tp.w1, tp.w2};
     float2 *pd[3] = {tp.p0, tp.p1, tp.p2};
@@ -588,11 +619,20 @@ int launch_strip_scale(const HostBatch &B, const GaussTaps &g, const StripArgs &
         tp.q12[i] = make_float2(tp.w1[i], tp.w2[i]);
         tp.q01[i] = make_float2(tp.w0[i], tp.w1[i]);
     }
+}
+
+// NS scales of padded radius R (taps g[0 .. NS-1]) in one launch.
+template <int R, int MODE, int NS>
+int launch_strip_scale(const HostBatch &B, const GaussTaps *g, const StripArgs &sa, cudaStream_t st)
+{
+    constexpr size_t smem = st_smem_bytes<R, NS>();
+    StripTapsN<R, NS> tp;
+    for (int k = 0; k < NS; ++k) strip_taps<R>(g[k], tp.t[k]);
     // Segment length: the one with the smaller estimated time, taken as the
     // rounds of the persistent grid times the rows a block passes per segment
     // (its rows, the 2R halo rows and one chunk for the segment's start, whose
     // staging is not overlapped).
-    const int cap = persistent_grid((const void *)k_strip<R, MODE>, ST_NT, smem, 1 << 30);
+    const int cap = persistent_grid((const void *)k_strip<R, MODE, NS>, ST_NT, smem, 1 << 30);
     const long long rounds_l = (B.tiles[SHAPE_SEG] + cap - 1) / cap;
     const long long rounds_s = (B.tiles[SHAPE_SEG_S] + cap - 1) / cap;
     const bool lng = rounds_l * (kSegRows + 2 * R + ST_CH) <= rounds_s * (kSegRowsShort + 2 * R + ST_CH);
@@ -601,17 +641,26 @@ int launch_strip_scale(const HostBatch &B, const GaussTaps &g, const StripArgs &
     a.seg = lng ? kSegRows : kSegRowsShort;
     Imgs I = B.I;
     I.tiles = B.tiles[a.shape];
-    return launch_strip_k<R, MODE>(I, tp, a, st);
+    return launch_strip_k<R, MODE, NS>(I, tp, a, st);
 }
+
+// Scales s, s + 1 of one padded radius share a launch in the tensor build
+// (one staging and one barrier sequence for both) up to this radius.
+constexpr int kMaxPairRadius = 16;
 
 template <int MODE>
 int launch_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p, cudaStream_t st)
 {
     if (B.I.list) return 1;  // the strips walk whole images, never a tile subset
-    for (int s = 0; s < n_sigma; ++s) {
-        GaussTaps g;
-        if (gauss_taps(h_sigmas[s], &g) != FD4_OK) return 1;
-        const int R = (g.r + 3) / 4 * 4;
+    for (int s = 0; s < n_sigma;) {
+        GaussTaps g[2];
+        if (gauss_taps(h_sigmas[s], &g[0]) != FD4_OK) return 1;
+        const int R = (g[0].r + 3) / 4 * 4;
+        int ns = 1;
+        if (MODE == ST_TENSOR && s + 1 < n_sigma && R <= kMaxPairRadius) {
+            if (gauss_taps(h_sigmas[s + 1], &g[1]) != FD4_OK) return 1;
+            if ((g[1].r + 3) / 4 * 4 == R) ns = 2;
+        }
         StripArgs sa;
         sa.s = s;
         sa.K_total = n_sigma;
@@ -621,22 +670,36 @@ int launch_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const 
         sa.inv2b2 = (float)(1.0 / (2.0 * (double)p.beta * p.beta));
         sa.inv_lam2 = (float)(1.0 / ((double)p.lambda * p.lambda));
         int rc = 1;
-        switch (R) {
-        case 4: rc = launch_strip_scale<4, MODE>(B, g, sa, st); break;
-        case 8: rc = launch_strip_scale<8, MODE>(B, g, sa, st); break;
-        case 12: rc = launch_strip_scale<12, MODE>(B, g, sa, st); break;
-        case 16: rc = launch_strip_scale<16, MODE>(B, g, sa, st); break;
-        case 20: rc = launch_strip_scale<20, MODE>(B, g, sa, st); break;
-        case 24: rc = launch_strip_scale<24, MODE>(B, g, sa, st); break;
-        case 28: rc = launch_strip_scale<28, MODE>(B, g, sa, st); break;
-        case 32: rc = launch_strip_scale<32, MODE>(B, g, sa, st); break;
-        case 36: rc = launch_strip_scale<36, MODE>(B, g, sa, st); break;
-        case 40: rc = launch_strip_scale<40, MODE>(B, g, sa, st); break;
-        case 44: rc = launch_strip_scale<44, MODE>(B, g, sa, st); break;
-        case 48: rc = launch_strip_scale<48, MODE>(B, g, sa, st); break;
-        default: rc = 1;
+        if constexpr (MODE == ST_TENSOR) {
+            if (ns == 2) {
+                switch (R) {
+                case 4: rc = launch_strip_scale<4, MODE, 2>(B, g, sa, st); break;
+                case 8: rc = launch_strip_scale<8, MODE, 2>(B, g, sa, st); break;
+                case 12: rc = launch_strip_scale<12, MODE, 2>(B, g, sa, st); break;
+                case 16: rc = launch_strip_scale<16, MODE, 2>(B, g, sa, st); break;
+                default: rc = 1;
+                }
+            }
+        }
+        if (ns == 1) {
+            switch (R) {
+            case 4: rc = launch_strip_scale<4, MODE, 1>(B, g, sa, st); break;
+            case 8: rc = launch_strip_scale<8, MODE, 1>(B, g, sa, st); break;
+            case 12: rc = launch_strip_scale<12, MODE, 1>(B, g, sa, st); break;
+            case 16: rc = launch_strip_scale<16, MODE, 1>(B, g, sa, st); break;
+            case 20: rc = launch_strip_scale<20, MODE, 1>(B, g, sa, st); break;
+            case 24: rc = launch_strip_scale<24, MODE, 1>(B, g, sa, st); break;
+            case 28: rc = launch_strip_scale<28, MODE, 1>(B, g, sa, st); break;
+            case 32: rc = launch_strip_scale<32, MODE, 1>(B, g, sa, st); break;
+            case 36: rc = launch_strip_scale<36, MODE, 1>(B, g, sa, st); break;
+            case 40: rc = launch_strip_scale<40, MODE, 1>(B, g, sa, st); break;
+            case 44: rc = launch_strip_scale<44, MODE, 1>(B, g, sa, st); break;
+            case 48: rc = launch_strip_scale<48, MODE, 1>(B, g, sa, st); break;
+            default: rc = 1;
+            }
         }
         if (rc) return 1;
+        s += ns;
     }
     return 0;
 }
@@ -646,9 +709,12 @@ int set_strip_smem()
 {
     const int b = (int)st_smem_bytes<R>();
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    return cudaFuncSetAttribute(k_strip<R, ST_TENSOR>, a, b) != cudaSuccess ||
-           cudaFuncSetAttribute(k_strip<R, ST_SELECT>, a, b) != cudaSuccess ||
-           cudaFuncSetAttribute(k_strip<R, ST_IFOD>, a, b) != cudaSuccess;
+    if constexpr (R <= kMaxPairRadius) {
+        if (cudaFuncSetAttribute(k_strip<R, ST_TENSOR, 2>, a, (int)st_smem_bytes<R, 2>()) != cudaSuccess) return 1;
+    }
+    return cudaFuncSetAttribute(k_strip<R, ST_TENSOR, 1>, a, b) != cudaSuccess ||
+           cudaFuncSetAttribute(k_strip<R, ST_SELECT, 1>, a, b) != cudaSuccess ||
+           cudaFuncSetAttribute(k_strip<R, ST_IFOD, 1>, a, b) != cudaSuccess;
 }
 
 }  // namespace
