@@ -277,8 +277,8 @@ __global__ void __launch_bounds__(t_quads<RY>() / NQ, RY == 64 ? 1 : 2)
                 const float4 tt = v[i];
                 cc[i] = tt.x;
                 ss[i] = tt.y;
-                pp[i] = 0.5f * (tt.z + tt.w);
-                qq[i] = 0.5f * (tt.z - tt.w);
+                pp[i] = 0.25f * (tt.z + tt.w);  // quarter-scaled: quad_T carries its terms doubled
+                qq[i] = 0.25f * (tt.z - tt.w);
             }
             k[qd].c = make_float4(cc[0], cc[1], cc[2], cc[3]);
             k[qd].s = make_float4(ss[0], ss[1], ss[2], ss[3]);

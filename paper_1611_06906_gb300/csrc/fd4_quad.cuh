@@ -16,7 +16,7 @@ struct StepTaus {
 };
 
 struct QuadCoef {
-    float4 c, s, p, q;  // per pixel of the quad: cos 2t, sin 2t, mean and half difference of mu
+    float4 c, s, p, q;  // per pixel of the quad: cos 2t, sin 2t, (mu1 + mu2) / 4, (mu1 - mu2) / 4
 };
 
 __device__ __forceinline__ void f4_to(const float4 v, float *d)
@@ -35,6 +35,10 @@ __device__ __forceinline__ void quad_ext(const float4 m, float (&v)[6])
 // T = M D M L u for the 4 pixels of one quad.  a, b, c: rows y-1, y, y+1 at
 // columns x-1 .. x+4.  BOUNDARY: apply the natural-boundary masks (bits 0-3:
 // pixel inside, 4-7: Lxx row exists, 8: Lyy row exists for this row).
+// The mixed derivative shares its column differences a - c between
+// neighbouring pixels, and the eigenframe quantities are carried at twice
+// their size (sh2 = hxx + hyy, dh2 = hxx - hyy, hxy2 = 2 hxy), which the
+// quarter-scaled diffusivity coefficients p, q bring back to scale.
 template <bool BOUNDARY>
 __device__ __forceinline__ void quad_T(const float (&a)[6], const float (&b)[6], const float (&c)[6],
                                        const QuadCoef &k, unsigned mask, float4 &Txx, float4 &Txy, float4 &Tyy)
@@ -45,11 +49,14 @@ __device__ __forceinline__ void quad_T(const float (&a)[6], const float (&b)[6],
     f4_to(k.s, ss);
     f4_to(k.p, pp);
     f4_to(k.q, qq);
+    float e[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) e[j] = a[j] - c[j];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         float hxx = fmaf(-2.0f, b[i + 1], b[i] + b[i + 2]);
         float hyy = fmaf(-2.0f, b[i + 1], a[i + 1] + c[i + 1]);
-        float hxy = 0.25f * ((a[i] + c[i + 2]) - (c[i] + a[i + 2]));
+        float hxy2 = 0.5f * (e[i] - e[i + 2]);                 // 2 hxy
         bool vx = true, vy = true, in = true;
         if (BOUNDARY) {
             in = (mask >> i) & 1u;
@@ -57,14 +64,14 @@ __device__ __forceinline__ void quad_T(const float (&a)[6], const float (&b)[6],
             vy = (mask >> 8) & 1u;
             hxx = vx ? hxx : 0.0f;
             hyy = vy ? hyy : 0.0f;
-            hxy = (vx && vy) ? hxy : 0.0f;
+            hxy2 = (vx && vy) ? hxy2 : 0.0f;
         }
-        const float sh = 0.5f * (hxx + hyy), dh = 0.5f * (hxx - hyy);
-        const float z = fmaf(cc[i], dh, ss[i] * hxy);          // eigenframe: h11 = sh + z, h22 = sh - z
-        const float v = fmaf(cc[i], hxy, -ss[i] * dh);         // h12
-        const float st = fmaf(pp[i], sh, qq[i] * z);           // (t11 + t22) / 2
-        const float dt = fmaf(qq[i], sh, pp[i] * z);           // (t11 - t22) / 2
-        const float t12 = pp[i] * v;
+        const float sh2 = hxx + hyy, dh2 = hxx - hyy;
+        const float z2 = fmaf(cc[i], dh2, ss[i] * hxy2);       // eigenframe: h11 = (sh2 + z2) / 2, h22 = (sh2 - z2) / 2
+        const float v2 = fmaf(cc[i], hxy2, -ss[i] * dh2);      // 2 h12
+        const float st = fmaf(pp[i], sh2, qq[i] * z2);         // (t11 + t22) / 2
+        const float dt = fmaf(qq[i], sh2, pp[i] * z2);         // (t11 - t22) / 2
+        const float t12 = pp[i] * v2;
         float txx = fmaf(cc[i], dt, fmaf(-ss[i], t12, st));
         float tyy = fmaf(2.0f, st, -txx);
         float txy = fmaf(ss[i], dt, cc[i] * t12);
@@ -119,7 +126,7 @@ __device__ __forceinline__ void quad_steps_n(float *su, float *sxy, float *syy, 
 #pragma unroll
         for (int qd = 0; qd < NQ; ++qd) {
             // u -= tau (Lxx' Txx + Lyy' Tyy + 2 Lxy' Txy)
-            float X[6], Zu[6], Zd[6], Yu[4], Yc[4], Yd[4], U[4];
+            float X[6], Zu[6], Zd[6], Yu[4], Yc[4], Yd[4], U[4], f[6];
             quad_ext(txx[qd], X);
             quad_ext(*reinterpret_cast<const float4 *>(sxy + off[qd] - SW), Zu);
             quad_ext(*reinterpret_cast<const float4 *>(sxy + off[qd] + SW), Zd);
@@ -127,11 +134,13 @@ __device__ __forceinline__ void quad_steps_n(float *su, float *sxy, float *syy, 
             f4_to(tyy[qd], Yc);
             f4_to(*reinterpret_cast<const float4 *>(syy + off[qd] + SW), Yd);
             f4_to(uo[qd], U);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) f[j] = Zu[j] - Zd[j];  // column differences shared by neighbours
             float r[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const float div = fmaf(-2.0f, X[i + 1], X[i] + X[i + 2]) + fmaf(-2.0f, Yc[i], Yu[i] + Yd[i]) +
-                                  0.5f * ((Zd[i + 2] + Zu[i]) - (Zu[i + 2] + Zd[i]));
+                const float div = fmaf(0.5f, f[i] - f[i + 2],
+                                       fmaf(-2.0f, X[i + 1], X[i] + X[i + 2]) + fmaf(-2.0f, Yc[i], Yu[i] + Yd[i]));
                 r[i] = fmaf(-tau, div, U[i]);
                 if (BOUNDARY && !((mask[qd] >> i) & 1u)) r[i] = U[i];
             }
@@ -139,19 +148,6 @@ __device__ __forceinline__ void quad_steps_n(float *su, float *sxy, float *syy, 
             *reinterpret_cast<float4 *>(su + off[qd]) = uo[qd];
         }
     }
-}
-
-// One quad per thread.
-template <bool BOUNDARY, int SW>
-__device__ __forceinline__ float4 quad_steps(float *su, float *sxy, float *syy, const float *stau, int nsteps,
-                                             int off, const QuadCoef &k, unsigned mask, float4 uo)
-{
-    const int o[1] = {off};
-    const QuadCoef kk[1] = {k};
-    const unsigned m[1] = {mask};
-    float4 u[1] = {uo};
-    quad_steps_n<BOUNDARY, SW, 1>(su, sxy, syy, stau, nsteps, o, kk, m, u);
-    return u[0];
 }
 
 }  // namespace fd4
