@@ -53,8 +53,8 @@ from paper_1611_06906_gb300.dist import max_over_ranks as _max_over_ranks, rank_
 # Entries are removed (the field is then null) whenever that kernel changes.
 FED_DRAM_B_PER_PX = {
     # k_fed_tma<2,2,64>: one launch over one 4096^2 image of the workload, 335.60 MB
-    # read + 53.20 MB written over 16.78 Mpixel (profiles/k_fed_tma_tree16_4096.md)
-    (2, 64, 2): 23.17,
+    # read + 53.39 MB written over 16.78 Mpixel (profiles/k_fed_tma_tree16_4096.md)
+    (2, 64, 2): 23.18,
 }
 METRIC = "Mpixel-steps/s, batched+learned vs plain GB300, at stated FP64-oracle error"
 UNIT = "Mpixel-steps/s"
