@@ -1,6 +1,7 @@
 // Internal declarations shared by the fd4 translation units (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -8,6 +9,13 @@
 #include "fd4.h"
 
 namespace fd4 {
+
+// cuTensorMapEncodeTiled, reached through the runtime's driver entry point
+// (null if the driver does not provide it).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn tensor_map_encoder();
 
 constexpr int kMaxRadius = 48;              // ceil(4 * FD4_MAX_SIGMA)
 constexpr int kMaxTaps = 2 * kMaxRadius + 1;

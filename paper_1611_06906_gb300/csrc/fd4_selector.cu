@@ -8,17 +8,21 @@
 // Activations are NHWC bf16 (16 channels for the input layer, 32 after);
 // weights bf16; accumulation FP32 in tensor memory.
 //
-// Convolution as implicit GEMM on the 5th-generation tensor cores: a block
-// owns 128 consecutive output pixels of one image row (the MMA's M = 128); it
-// stages the three input rows y - d, y, y + d (with a d-pixel margin) in shared
+// Convolution as implicit GEMM on the 5th-generation tensor cores: a tile is
+// 128 consecutive output pixels of one image row (the MMA's M = 128); the
+// three input rows y - d, y, y + d (with a d-pixel margin) sit in shared
 // memory as 16-byte channel chunks laid out pixel-contiguous, so the A operand
-// of tap (ky, kx) is the same buffer shifted by kx * d pixels -- a plain
-// K-major no-swizzle descriptor, no im2col copy.  B (the weights of all nine
-// taps) is staged once per block.  One thread issues 9 * CI/16 MMAs of
-// 128 x CO x 16, commits them to an mbarrier, and the four warps read the
-// FP32 accumulator back from their TMEM lanes for the epilogue.  The weight
-// gradient is a tensor-core product too, with the pixels as the reduction
-// dimension (k_sel_wgrad_tc).
+// of tap (ky, kx) is a row buffer shifted by kx * d pixels -- a plain K-major
+// no-swizzle descriptor, no im2col copy.  A block walks down one residue class
+// of the rows modulo d, so consecutive tiles share two input rows and each
+// tile copies one new row (cp.async, during the previous tile's MMAs).  B (the
+// weights of all nine taps) is staged once per block.  One thread issues
+// 9 * CI/16 MMAs of 128 x CO x 16, commits them to an mbarrier, and the four
+// warps read the FP32 accumulator back from their TMEM lanes for the epilogue
+// (bias + ReLU + bf16, or at inference the argmax bin and its probability).
+// The weight gradient is a tensor-core product too, with the pixels as the
+// reduction dimension (k_sel_wgrad_tc).
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -41,157 +45,351 @@ __device__ __forceinline__ uint64_t globaltimer()
     return t;
 }
 
-enum ConvMode { CONV_RELU_BF16 = 0, CONV_LOGITS_F32 = 1, CONV_MASK_BF16 = 2 };
+enum ConvMode { CONV_RELU_BF16 = 0, CONV_LOGITS_F32 = 1, CONV_MASK_BF16 = 2, CONV_PREDICT = 3 };
+
+// Activations (bf16) are stored row-planar with their own pitch `apitch` (a
+// multiple of 8 pixels, pixels w .. apitch - 1 zero): row y of image i holds
+// C / 8 chunk planes of apitch pixels x 8 channels (16 bytes), so that
+// channels 8j .. 8j + 7 of pixel x are at
+// ((i * h + y) * apitch * C / 8 + j * apitch + x) * 8.  A row's run of pixels
+// in one plane is contiguous: one tensor-map copy moves a window of an input
+// row in all its planes, and a warp's 16-byte stores of one plane are
+// contiguous.
+__host__ __device__ inline size_t act_off(long long aimg_stride, int img, int y, int apitch, int cj, int j, int x)
+{
+    return (((size_t)img * (size_t)aimg_stride + (size_t)y * apitch) * cj + (size_t)j * apitch + x) * 8;
+}
+__host__ __device__ inline int act_pitch(int w) { return (w + 7) / 8 * 8; }
 
 struct ConvArgs {
-    const __nv_bfloat16 *in;    // NHWC, CI channels
-    void *out;                  // NHWC, CO channels (bf16) or n_out floats per pixel (fp32)
+    const __nv_bfloat16 *in;    // row-planar, CI channels (input of layer 0: one stored plane, the rest zero)
+    void *out;                  // row-planar CO channels (bf16), or n_out floats per pixel (fp32 logits)
     const uint4 *wts;           // weights in tile layout: [tap][ci / 8][co] x 16 bytes
     const float *bias;          // CO floats, nullable
-    const __nv_bfloat16 *mask;  // CONV_MASK_BF16: NHWC, CO channels; output zeroed where mask <= 0
-    int n_img, w, h, pitch, d;
-    long long img_stride;       // pixels between consecutive images
-    int n_out;                  // CONV_LOGITS_F32: channels written per pixel
+    const __nv_bfloat16 *mask;  // CONV_MASK_BF16: row-planar, CO channels; output zeroed where mask <= 0
+    uint8_t *idx;               // CONV_PREDICT: argmax of the first n_out outputs per pixel
+    float *conf;                // CONV_PREDICT: its softmax probability (nullable)
+    int n_img, w, h, d;
+    int pitch;                  // logits / idx / conf: elements per row
+    int apitch;                 // activations: pixels per row (act_pitch(w))
+    long long img_stride;       // h * pitch
+    long long aimg_stride;      // h * apitch
+    int n_out;                  // CONV_LOGITS_F32 / CONV_PREDICT: outputs used per pixel
+    int in_cj;                  // chunk planes stored per input row (<= CI / 8; the missing ones read as zero)
+    int seg_rows;               // output rows of one residue class per work unit
     int *status;                // FD4_ERR_TIMEOUT if a wait gives up
-    int withhold_commit;        // self-test only: issue no MMA, so the wait runs out
+    int withhold_commit;        // self-test only: issue no MMA, so the waits run out
 };
 
-__host__ __device__ inline size_t conv_smem_bytes(int CI, int CO, int d)
+constexpr int kConvThreads = 192;  // warps 0-3: epilogue (TMEM lane quarters), 4: copies, 5: MMAs
+constexpr int kSlots = 5;          // input rows staged per block
+constexpr uint64_t kConvWaitNs = 1000000000ull;  // bounded waits: one second
+// A staged row holds pixels x0 - 8 .. x0 + 135 of each plane: 18 segments of
+// 8 pixels (128 bytes), one tensor-map copy.  Tap kx of dilation d reads
+// pixels from x0 + (kx - 1) d, at offset 8 + (kx - 1) d.
+constexpr int kSegPx = 8;
+constexpr int kWinPx = 144;
+static_assert(TM + 2 * kMaxDil <= kWinPx && kMaxDil <= kSegPx, "the window covers the tile and its margins");
+
+__host__ __device__ constexpr uint32_t conv_slot_bytes(int cj) { return (uint32_t)cj * kWinPx * 16u; }
+// weights | row ring (plus 128 bytes to align the base)
+__host__ __device__ constexpr size_t conv_smem_bytes(int CI, int CO)
 {
-    return (size_t)16 * (9 * (CI / 8) * CO + 3 * (CI / 8) * (TM + 2 * d));
+    return 128 + (size_t)16 * 9 * (CI / 8) * CO + (size_t)kSlots * conv_slot_bytes(CI / 8);
+}
+// TMEM columns: two accumulators of 3 CO columns, rounded up to a power of two
+__host__ __device__ constexpr uint32_t conv_tmem_cols(int CO) { return 6 * CO <= 128 ? 128u : 256u; }
+
+// Work units of a convolution: (image, 128-pixel column tile, residue class of
+// the rows modulo the dilation d, segment of seg rows of that class).
+__host__ __device__ inline long long conv_units(int n_img, int w, int h, int d, int seg)
+{
+    const int tiles_x = (w + TM - 1) / TM;
+    const int cls = (h + d - 1) / d;  // rows of the longest residue class
+    const int segs = (cls + seg - 1) / seg;
+    return (long long)n_img * tiles_x * d * segs;
 }
 
+struct ConvUnit {
+    int img, x0, rho, k0, k1;  // output class positions k0 .. k1 - 1, rows y = rho + k d
+};
+__device__ __forceinline__ bool conv_unit(const ConvArgs &a, long long u, int segs, int tiles_x, ConvUnit &c)
+{
+    const int seg = (int)(u % segs);
+    long long rest = u / segs;
+    c.rho = (int)(rest % a.d);
+    rest /= a.d;
+    c.x0 = (int)(rest % tiles_x) * TM;
+    c.img = (int)(rest / tiles_x);
+    c.k0 = seg * a.seg_rows;
+    const int kmax = c.rho < a.h ? (a.h - 1 - c.rho) / a.d + 1 : 0;
+    c.k1 = min(c.k0 + a.seg_rows, kmax);
+    return c.k0 < c.k1;
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[N])
+{
+    if constexpr (N == 32) {
+        tc::tmem_ld_x32(taddr, v);
+    } else {
+        tc::tmem_ld_x16(taddr, v);
+    }
+}
+
+// Implicit-GEMM 3 x 3 dilated convolution on the tensor cores, one input row
+// at a time, with warp roles.  A block walks units (one residue class of the
+// rows modulo d, a 128-pixel column tile, a segment of its rows); output rows
+// k0 .. k1 - 1 of a unit read input rows k0 - 1 .. k1 (class positions).  For
+// input row r the MMA warp computes, in one TMEM accumulator of 3 CO columns,
+//   D_r[p][ky CO + co] = sum_kx sum_ci X_r[p + (kx - 1) d][ci] W[ky][kx][co][ci]
+// as 3 kx x CI / 16 MMAs of 128 x 3 CO x 16: A is the staged row at a
+// (kx - 1) d pixel shift (a K-major no-swizzle operand: LBO = one chunk plane,
+// SBO = 8 pixels), B the weights of the three ky taps stacked along N.
+// Output row k is D_{k-1}[ky = 0] + D_k[ky = 1] + D_{k+1}[ky = 2]: the four
+// epilogue warps (a pixel per thread, its TMEM lane) carry the two partial
+// sums of the rows still open in registers.  The copy warp streams input rows
+// into a ring of kSlots buffers (one tensor-map copy per row, zero fill
+// outside the image); the MMA warp issues a row's MMAs as soon as its copy
+// and a free accumulator are there, into the accumulator the epilogue is not
+// reading.  Handoffs are mbarriers: full (copy landed), empty (MMAs of the
+// slot done), acc_full (accumulator written), acc_empty (epilogue has read
+// it).  Every wait is bounded (one second): on timeout the kernel records
+// FD4_ERR_TIMEOUT, the roles stop, the copies and MMAs in flight are waited
+// for (bounded), the TMEM is freed and the kernel returns.
 template <int CI, int CO, int MODE>
-__global__ void __launch_bounds__(CT) k_conv_tc(ConvArgs a)
+__global__ void __launch_bounds__(kConvThreads, 2) k_conv_tc(const __grid_constant__ CUtensorMap xmap, ConvArgs a)
 {
     constexpr int CJ = CI / 8;  // 16-byte channel chunks per pixel
-    extern __shared__ __align__(128) uint4 csm[];
-    __shared__ uint64_t mbar;
+    constexpr int NN = 3 * CO;  // MMA N: the three ky taps
+    constexpr uint32_t kCols = conv_tmem_cols(CO);
+    constexpr uint32_t slot_bytes = conv_slot_bytes(CJ);
+    extern __shared__ unsigned char conv_raw[];
+    __shared__ __align__(8) uint64_t full_bar[kSlots];
+    __shared__ __align__(8) uint64_t empty_bar[kSlots];
+    __shared__ __align__(8) uint64_t accf_bar[2];
+    __shared__ __align__(8) uint64_t acce_bar[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_flag;
-    const int P = TM + 2 * a.d;  // staged pixels per row
-    uint4 *Bs = csm;             // 9 * CJ * CO chunks
-    uint4 *As = csm + 9 * CJ * CO;
+    __shared__ volatile int abort_flag;
+    __shared__ float bias_s[CO];
+    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)conv_raw + 127) & ~(uintptr_t)127);
+    uint4 *Bs = reinterpret_cast<uint4 *>(base);        // [kx][ci / 8][ky][co] x 16 bytes
+    unsigned char *ring = base + 16 * 9 * CJ * CO;      // kSlots x CJ planes x kWinPx pixels x 16 bytes
+    const int d = a.d;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    for (int i = tid; i < 9 * CJ * CO; i += CT) Bs[i] = a.wts[i];
+    // weights [tap][ci / 8][co] -> [kx][ci / 8][ky][co]: the ky taps of one
+    // (kx, chunk) are N-contiguous
+    for (int i = tid; i < 9 * CJ * CO; i += kConvThreads) {
+        const int co = i % CO, j = (i / CO) % CJ, tap = i / (CO * CJ);
+        const int ky = tap / 3, kx = tap - 3 * (tap / 3);
+        Bs[((kx * CJ + j) * 3 + ky) * CO + co] = a.wts[i];
+    }
+    // planes the input does not store are zero in every slot (no copy writes them)
+    for (int s = 0; s < kSlots; ++s)
+        for (int i = a.in_cj * kWinPx + tid; i < CJ * kWinPx; i += kConvThreads)
+            reinterpret_cast<uint4 *>(ring + s * slot_bytes)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int c = tid; c < CO; c += kConvThreads) bias_s[c] = a.bias ? a.bias[c] : 0.0f;
     if (warp == 0) {
-        tc::tmem_alloc(&tmem_base, 32);
+        tc::tmem_alloc(&tmem_base, kCols);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(&mbar, 1);
+        for (int s = 0; s < kSlots; ++s) {
+            tc::mbar_init(&full_bar[s], 1);
+            tc::mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&accf_bar[b], 1);
+            tc::mbar_init(&acce_bar[b], 4);  // one arrival per epilogue warp
+        }
         abort_flag = 0;
+        tc::fence_mbar_init();
     }
+    tc::fence_proxy_async();  // the weights and zero planes, written by this proxy, are read by the MMAs
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(TM, CO);
     const int tiles_x = (a.w + TM - 1) / TM;
-    const long long total = (long long)a.n_img * a.h * tiles_x;
-    uint32_t phase = 0;
+    const int cls = (a.h + d - 1) / d;
+    const int segs = (cls + a.seg_rows - 1) / a.seg_rows;
+    const long long total = conv_units(a.n_img, a.w, a.h, d, a.seg_rows);
+    const uint32_t ring_s = tc::smem_u32(ring);
 
-    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-        const int tx = (int)(t % tiles_x);
-        const long long rr = t / tiles_x;
-        const int y = (int)(rr % a.h);
-        const int img = (int)(rr / a.h);
-        const int x0 = tx * TM;
-        const __nv_bfloat16 *in = a.in + (size_t)img * (size_t)a.img_stride * CI;
-        // A: rows y - d, y, y + d; pixels x0 - d .. x0 + TM - 1 + d; zero outside the image
-        for (int ky = 0; ky < 3; ++ky) {
-            const int gy = y + (ky - 1) * a.d;
-            const bool row_in = gy >= 0 && gy < a.h;
-            const __nv_bfloat16 *src = in + (size_t)(row_in ? gy : 0) * a.pitch * CI;
-            for (int e = tid; e < P * CJ; e += CT) {
-                const int j = e % CJ, p = e / CJ;  // CJ is a compile-time power of two
-                const int gx = x0 - a.d + p;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (row_in && gx >= 0 && gx < a.w) v = *reinterpret_cast<const uint4 *>(src + (size_t)gx * CI + 8 * j);
-                As[(ky * CJ + j) * P + p] = v;
-            }
-        }
-        tc::fence_proxy_async();
-        __syncthreads();
-        if (tid == 0 && !a.withhold_commit) {
-            tc::fence_after_sync();
-            const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs);
-            uint32_t acc = 0;
-#pragma unroll 1
-            for (int tap = 0; tap < 9; ++tap) {
-                const int ky = tap / 3, kx = tap - 3 * (tap / 3);
-#pragma unroll
-                for (int k = 0; k < CI / 16; ++k) {
-                    const uint32_t aaddr = a0 + (uint32_t)(((ky * CJ + 2 * k) * P + kx * a.d) * 16);
-                    const uint32_t baddr = b0 + (uint32_t)((tap * CJ + 2 * k) * CO * 16);
-                    tc::mma_bf16(tmem, tc::sdesc_kmajor(aaddr, (uint32_t)(P * 16), 128),
-                                 tc::sdesc_kmajor(baddr, (uint32_t)(CO * 16), 128), idesc, acc);
-                    acc = 1;
+    if (warp == 4) {
+        // ---- copy warp: input rows into the ring
+        if (lane == 0) {
+            uint32_t q = 0;  // rows of this block so far: slot q % kSlots, use q / kSlots
+            bool stop = false;
+            for (long long u = blockIdx.x; u < total && !stop; u += gridDim.x) {
+                ConvUnit c;
+                if (!conv_unit(a, u, segs, tiles_x, c)) continue;
+                for (int r = c.k0 - 1; r <= c.k1; ++r, ++q) {
+                    const uint32_t s = q % kSlots, n = q / kSlots;
+                    if (abort_flag || (n > 0 && !tc::mbar_wait_bounded(&empty_bar[s], (n - 1) & 1u, kConvWaitNs))) {
+                        abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    tc::mbar_expect_tx(&full_bar[s], (uint32_t)a.in_cj * kWinPx * 16u);
+                    tc::tma_load_5d(ring_s + s * slot_bytes, &xmap, 0, c.x0 / kSegPx - 1, 0, c.rho + r * d, c.img,
+                                    &full_bar[s]);
                 }
             }
-            tc::mma_commit(&mbar);
+            // every copy issued has landed before the block ends
+            for (uint32_t s = 0; s < kSlots && s < q; ++s)
+                tc::mbar_wait_bounded(&full_bar[s], ((q - 1 - s) / kSlots) & 1u, kConvWaitNs);
         }
-        // wait for the MMAs, at most one second
-        {
-            const uint64_t t0 = globaltimer();
-            while (!tc::mbar_try_wait(&mbar, phase)) {
-                if (globaltimer() - t0 > 1000000000ull) {
-                    atomicExch(&abort_flag, 1);
+    } else if (warp == 5) {
+        // ---- MMA warp
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(TM, NN);
+            const uint64_t adesc0 = tc::sdesc_kmajor(ring_s, (uint32_t)(kWinPx * 16), 128);
+            const uint64_t bdesc0 = tc::sdesc_kmajor(tc::smem_u32(Bs), (uint32_t)(NN * 16), 128);
+            uint32_t q = 0, committed = 0;
+            bool stop = false;
+            for (long long u = blockIdx.x; u < total && !stop; u += gridDim.x) {
+                ConvUnit c;
+                if (!conv_unit(a, u, segs, tiles_x, c)) continue;
+                for (int r = c.k0 - 1; r <= c.k1; ++r, ++q) {
+                    const uint32_t s = q % kSlots, n = q / kSlots, b = q & 1u, nb = q >> 1;
+                    if (abort_flag || !tc::mbar_wait_bounded(&full_bar[s], n & 1u, kConvWaitNs) ||
+                        (nb > 0 && !tc::mbar_wait_bounded(&acce_bar[b], (nb - 1) & 1u, kConvWaitNs))) {
+                        abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    if (a.withhold_commit) continue;
+                    tc::fence_after_sync();
+                    const uint32_t srow = s * (slot_bytes >> 4) + (uint32_t)(kSegPx - d);
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx) {
+#pragma unroll
+                        for (int kk = 0; kk < CI / 16; ++kk) {
+                            // descriptor start addresses advance in 16-byte units
+                            const uint64_t ad = adesc0 + (uint64_t)(srow + (uint32_t)(2 * kk * kWinPx + kx * d));
+                            const uint64_t bd = bdesc0 + (uint64_t)((kx * CJ + 2 * kk) * NN);
+                            tc::mma_bf16(tmem + b * NN, ad, bd, idesc, (kx | kk) != 0 ? 1u : 0u);
+                        }
+                    }
+                    tc::mma_commit(&empty_bar[s]);
+                    tc::mma_commit(&accf_bar[b]);
+                    ++committed;
+                }
+            }
+            // the MMAs issued are complete before the TMEM is freed
+            for (uint32_t b = 0; b < 2 && b < committed; ++b)
+                tc::mbar_wait_bounded(&accf_bar[b], ((committed - 1 - b) / 2) & 1u, kConvWaitNs);
+        }
+    } else {
+        // ---- epilogue warps: lane quarter `warp` of the accumulators
+        const int i = warp * 32 + lane;  // tile pixel = TMEM lane
+        uint32_t q = 0;
+        bool stop = false;
+        for (long long u = blockIdx.x; u < total && !stop; u += gridDim.x) {
+            ConvUnit c;
+            if (!conv_unit(a, u, segs, tiles_x, c)) continue;
+            float accA[CO], accB[CO];  // partial sums of output rows r - 1 and r
+#pragma unroll
+            for (int k = 0; k < CO; ++k) accA[k] = accB[k] = 0.0f;
+            const int gx = c.x0 + i;
+            for (int r = c.k0 - 1; r <= c.k1; ++r, ++q) {
+                const uint32_t b = q & 1u, nb = q >> 1;
+                if (abort_flag || !tc::mbar_wait_bounded(&accf_bar[b], nb & 1u, kConvWaitNs)) {
+                    abort_flag = 1;
+                    stop = true;
                     break;
                 }
-            }
-        }
-        phase ^= 1u;
-        tc::fence_after_sync();
-        __syncthreads();
-        if (abort_flag) break;
-
-        const int i = warp * 32 + lane;  // tile pixel = TMEM lane
-        const int gx = x0 + i;
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-        float v[CO];
-        if constexpr (CO == 32) {
-            tc::tmem_ld_x32(taddr, v);
-        } else {
-            tc::tmem_ld_x16(taddr, v);
-        }
-        if (gx < a.w) {
-            const size_t p = (size_t)img * (size_t)a.img_stride + (size_t)y * a.pitch + gx;
-            if (MODE == CONV_LOGITS_F32) {
-                float *o = reinterpret_cast<float *>(a.out) + p * a.n_out;
-                for (int c = 0; c < a.n_out; ++c) o[c] = v[c] + (a.bias ? a.bias[c] : 0.0f);
-            } else {
-                if (MODE == CONV_MASK_BF16) {
-                    const __nv_bfloat16 *m = a.mask + p * CO;
+                tc::fence_after_sync();
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + b * NN;
+                float v[CO], t[CO];
+                tmem_ld_cols<CO>(taddr + 2 * CO, v);  // ky = 2 closes output row r - 1
 #pragma unroll
-                    for (int c = 0; c < CO; ++c)
-                        if (!(__bfloat162float(m[c]) > 0.0f)) v[c] = 0.0f;
+                for (int k = 0; k < CO; ++k) v[k] += accA[k];
+                tmem_ld_cols<CO>(taddr + CO, t);      // ky = 1 adds to output row r
+#pragma unroll
+                for (int k = 0; k < CO; ++k) accA[k] = accB[k] + t[k];
+                tmem_ld_cols<CO>(taddr, t);           // ky = 0 opens output row r + 1
+#pragma unroll
+                for (int k = 0; k < CO; ++k) accB[k] = t[k];
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&acce_bar[b]))
+                                            : "memory");
+                if (r - 1 < c.k0) continue;
+                const int y = c.rho + (r - 1) * d;
+                if (MODE == CONV_LOGITS_F32 || MODE == CONV_PREDICT) {
+                    if (gx >= a.w) continue;
+                    const size_t p = (size_t)c.img * (size_t)a.img_stride + (size_t)y * a.pitch + gx;
+#pragma unroll
+                    for (int k = 0; k < CO; ++k) v[k] += bias_s[k];
+                    if (MODE == CONV_LOGITS_F32) {
+                        float *o = reinterpret_cast<float *>(a.out) + p * a.n_out;
+#pragma unroll
+                        for (int k = 0; k < CO; ++k)
+                            if (k < a.n_out) o[k] = v[k];
+                    } else {
+                        // argmax of the logits (ties to the smaller bin) and its softmax probability
+                        float m = -INFINITY;
+                        int arg = 0;
+#pragma unroll
+                        for (int k = 0; k < CO; ++k)
+                            if (k < a.n_out && v[k] > m) {
+                                m = v[k];
+                                arg = k;
+                            }
+                        float sum = 0.0f;
+#pragma unroll
+                        for (int k = 0; k < CO; ++k)
+                            if (k < a.n_out) sum += expf(v[k] - m);
+                        a.idx[p] = (uint8_t)arg;
+                        if (a.conf) a.conf[p] = 1.0f / sum;
+                    }
                 } else {
+                    if (gx >= a.apitch) continue;
+                    if (gx >= a.w) {  // the zero margin of the activation rows
 #pragma unroll
-                    for (int c = 0; c < CO; ++c) v[c] = fmaxf(v[c] + (a.bias ? a.bias[c] : 0.0f), 0.0f);
-                }
-                uint4 *o = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(a.out) + p * CO);
+                        for (int k = 0; k < CO; ++k) v[k] = 0.0f;
+                    } else if (MODE == CONV_MASK_BF16) {
 #pragma unroll
-                for (int q = 0; q < CO / 8; ++q) {
-                    uint4 pk;
-                    __nv_bfloat162 b0 = __floats2bfloat162_rn(v[8 * q + 0], v[8 * q + 1]);
-                    __nv_bfloat162 b1 = __floats2bfloat162_rn(v[8 * q + 2], v[8 * q + 3]);
-                    __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * q + 4], v[8 * q + 5]);
-                    __nv_bfloat162 b3 = __floats2bfloat162_rn(v[8 * q + 6], v[8 * q + 7]);
-                    pk.x = *reinterpret_cast<uint32_t *>(&b0);
-                    pk.y = *reinterpret_cast<uint32_t *>(&b1);
-                    pk.z = *reinterpret_cast<uint32_t *>(&b2);
-                    pk.w = *reinterpret_cast<uint32_t *>(&b3);
-                    o[q] = pk;
+                        for (int qq = 0; qq < CO / 8; ++qq) {
+                            const uint4 mk = *reinterpret_cast<const uint4 *>(
+                                a.mask + act_off(a.aimg_stride, c.img, y, a.apitch, CO / 8, qq, gx));
+                            const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const uint32_t bits = (mw[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+                                // bf16 > 0: bit patterns 0x0001 .. 0x7F80 (positive, up to +inf)
+                                if (bits - 1u >= 0x7F80u) v[8 * qq + e] = 0.0f;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < CO; ++k) v[k] = fmaxf(v[k] + bias_s[k], 0.0f);
+                    }
+                    __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(a.out);
+#pragma unroll
+                    for (int qq = 0; qq < CO / 8; ++qq) {
+                        uint4 pk;
+                        __nv_bfloat162 b0 = __floats2bfloat162_rn(v[8 * qq + 0], v[8 * qq + 1]);
+                        __nv_bfloat162 b1 = __floats2bfloat162_rn(v[8 * qq + 2], v[8 * qq + 3]);
+                        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * qq + 4], v[8 * qq + 5]);
+                        __nv_bfloat162 b3 = __floats2bfloat162_rn(v[8 * qq + 6], v[8 * qq + 7]);
+                        pk.x = *reinterpret_cast<uint32_t *>(&b0);
+                        pk.y = *reinterpret_cast<uint32_t *>(&b1);
+                        pk.z = *reinterpret_cast<uint32_t *>(&b2);
+                        pk.w = *reinterpret_cast<uint32_t *>(&b3);
+                        *reinterpret_cast<uint4 *>(ob + act_off(a.aimg_stride, c.img, y, a.apitch, CO / 8, qq, gx)) =
+                            pk;
+                    }
                 }
             }
         }
-        tc::fence_before_sync();
-        __syncthreads();  // TMEM is read before the next tile's MMAs overwrite it
     }
+    tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 32);
+    if (warp == 0) tc::tmem_dealloc(tmem, kCols);
     if (tid == 0 && abort_flag && a.status) atomicExch(a.status, FD4_ERR_TIMEOUT);
 }
 
@@ -287,35 +485,37 @@ __global__ void k_sel_cast(CastArgs a)
             a.bias[l * 32 + c] = c < co_r ? a.master[a.b_off[l] + c] : 0.0f;
 }
 
-// Image -> input activations: channel 0 = intensity, channels 1..15 = 0.
+// Image -> input activations of layer 0: one stored chunk plane (channel 0 =
+// intensity, channels 1..7 = 0; zero from pixel w to the activation pitch);
+// the layer reads its second plane (channels 8..15) as zero.
 __global__ void k_sel_prep(const float *img, __nv_bfloat16 *act, int n_img, int w, int h, int pitch,
-                           long long img_stride)
+                           long long img_stride, int apitch, long long aimg_stride)
 {
     // one block-stride loop over the rows of the stack, threads over columns
     for (int row = blockIdx.x; row < n_img * h; row += gridDim.x) {
-        const size_t base = (size_t)(row / h) * (size_t)img_stride + (size_t)(row % h) * pitch;
-        for (int x = threadIdx.x; x < pitch; x += blockDim.x) {
-            const size_t i = base + x;
-            const float v = x < w ? img[i] : 0.0f;
-            uint4 *o = reinterpret_cast<uint4 *>(act + i * 16);
-            __nv_bfloat162 b = __floats2bfloat162_rn(v, 0.0f);
-            o[0] = make_uint4(*reinterpret_cast<uint32_t *>(&b), 0u, 0u, 0u);
-            o[1] = make_uint4(0u, 0u, 0u, 0u);
+        const int i = row / h, y = row - (row / h) * h;
+        const size_t base = (size_t)i * (size_t)img_stride + (size_t)y * pitch;
+        for (int x = threadIdx.x; x < apitch; x += blockDim.x) {
+            __nv_bfloat162 b = __floats2bfloat162_rn(x < w ? img[base + x] : 0.0f, 0.0f);
+            *reinterpret_cast<uint4 *>(act + act_off(aimg_stride, i, y, apitch, 1, 0, x)) =
+                make_uint4(*reinterpret_cast<uint32_t *>(&b), 0u, 0u, 0u);
         }
     }
 }
 
 // Softmax cross-entropy over the n_bins logits of every pixel (n_bins floats
 // per pixel): mean loss added to *loss, gradient (p - onehot) / npx written as
-// bf16 (16 channels, those from n_bins on zero).
+// row-planar bf16 (16 channels, those from n_bins on zero; zero from pixel w
+// to the activation pitch).
 __global__ void __launch_bounds__(256) k_sel_softmax_ce(const float *logits, const uint8_t *labels,
                                                         __nv_bfloat16 *dz, int n_img, int w, int h, int pitch,
-                                                        long long img_stride, float inv_npx, float *loss, int n_bins)
+                                                        long long img_stride, int apitch, long long aimg_stride,
+                                                        float inv_npx, float *loss, int n_bins)
 {
     __shared__ float red[8];
     float lsum = 0.0f;
     for (int row = blockIdx.x; row < n_img * h; row += gridDim.x)
-    for (int x = threadIdx.x; x < pitch; x += blockDim.x) {
+    for (int x = threadIdx.x; x < apitch; x += blockDim.x) {
         const size_t i = (size_t)(row / h) * (size_t)img_stride + (size_t)(row % h) * pitch + x;
         float g[kMaxBins];
 #pragma unroll
@@ -337,15 +537,15 @@ __global__ void __launch_bounds__(256) k_sel_softmax_ce(const float *logits, con
             for (int c = 0; c < kMaxBins; ++c)
                 if (c < n_bins) g[c] = (g[c] / sum - (c == lab ? 1.0f : 0.0f)) * inv_npx;
         }
-        uint4 *o = reinterpret_cast<uint4 *>(dz + i * 16);
         uint32_t q[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             __nv_bfloat162 b = __floats2bfloat162_rn(g[2 * c], g[2 * c + 1]);
             q[c] = *reinterpret_cast<uint32_t *>(&b);
         }
-        o[0] = make_uint4(q[0], q[1], q[2], q[3]);
-        o[1] = make_uint4(q[4], q[5], q[6], q[7]);
+        const int im = row / h, y = row - (row / h) * h;
+        *reinterpret_cast<uint4 *>(dz + act_off(aimg_stride, im, y, apitch, 2, 0, x)) = make_uint4(q[0], q[1], q[2], q[3]);
+        *reinterpret_cast<uint4 *>(dz + act_off(aimg_stride, im, y, apitch, 2, 1, x)) = make_uint4(q[4], q[5], q[6], q[7]);
     }
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lsum;
@@ -383,8 +583,8 @@ __device__ __forceinline__ uint32_t wg_off(int row, int k)  // byte offset of el
 
 template <int CIP, int COP>
 __global__ void __launch_bounds__(CT, 1)
-    k_sel_wgrad_tc(const __nv_bfloat16 *X, const __nv_bfloat16 *dZ, int ci_r, int co_r, int n_img, int w, int h,
-                   int pitch, int d, long long img_stride, float *gW, float *gb, int *status)
+    k_sel_wgrad_tc(const __nv_bfloat16 *X, int x_cj, const __nv_bfloat16 *dZ, int ci_r, int co_r, int n_img, int w,
+                   int h, int apitch, int d, long long aimg_stride, float *gW, float *gb, int *status)
 {
     constexpr int NB = wg_rows<CIP>(), CJ = CIP / 8;
     constexpr int N0 = NB > 256 ? ((NB / 2 + 15) / 16) * 16 : NB;  // first chunk of B rows (MMA N <= 256)
@@ -430,17 +630,17 @@ __global__ void __launch_bounds__(CT, 1)
         const int y = (int)(rr % h);
         const int img = (int)(rr / h);
         const int x0 = tx * TM;
-        const size_t base = (size_t)img * (size_t)img_stride;
-        // X rows y - d, y, y + d; pixels x0 - d .. x0 + TM - 1 + d (zero outside the image)
+        // X rows y - d, y, y + d; pixels x0 - d .. x0 + TM - 1 + d (zero outside the
+        // image and in the chunk planes X does not store)
         for (int ky = 0; ky < 3; ++ky) {
             const int gy = y + (ky - 1) * d;
             const bool row_in = gy >= 0 && gy < h;
             for (int e = tid; e < P * CJ; e += CT) {
-                const int j = e % CJ, p = e / CJ;
+                const int j = e / P, p = e - (e / P) * P;  // consecutive threads read consecutive pixels
                 const int gx = x0 - d + p;
                 uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (row_in && gx >= 0 && gx < w)
-                    v = *reinterpret_cast<const uint4 *>(X + (base + (size_t)gy * pitch + gx) * CIP + 8 * j);
+                if (row_in && j < x_cj && gx >= 0 && gx < w)
+                    v = *reinterpret_cast<const uint4 *>(X + act_off(aimg_stride, img, gy, apitch, x_cj, j, gx));
                 *reinterpret_cast<uint4 *>(Xs + ((size_t)ky * P + p) * CIP + 8 * j) = v;
             }
         }
@@ -448,7 +648,8 @@ __global__ void __launch_bounds__(CT, 1)
         for (int e = tid; e < TM * (COP / 8); e += CT) {
             const int k = e % TM, g = e / TM;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (x0 + k < w) v = *reinterpret_cast<const uint4 *>(dZ + (base + (size_t)y * pitch + x0 + k) * COP + 8 * g);
+            if (x0 + k < w)
+                v = *reinterpret_cast<const uint4 *>(dZ + act_off(aimg_stride, img, y, apitch, COP / 8, g, x0 + k));
             const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int r = 0; r < 8; ++r)
@@ -553,29 +754,6 @@ __global__ void k_sel_adam(float *w, float *m, float *v, float *g, size_t n, flo
     }
 }
 
-// Inference read-out over a stack of n_img images: scale bin = argmax of the
-// n_bins logits (ties to the smaller bin), confidence = its softmax probability.
-__global__ void k_sel_predict(const float *logits, int n_img, int w, int h, int pitch, int n_bins, uint8_t *idx,
-                              float *conf)
-{
-    for (int row = blockIdx.x; row < n_img * h; row += gridDim.x)
-    for (int x = threadIdx.x; x < w; x += blockDim.x) {
-        const size_t i = (size_t)row * pitch + x;
-        const float *z = logits + i * n_bins;
-        int arg = 0;
-        float m = z[0];
-        for (int c = 1; c < n_bins; ++c)
-            if (z[c] > m) {
-                m = z[c];
-                arg = c;
-            }
-        float sum = 0.0f;
-        for (int c = 0; c < n_bins; ++c) sum += expf(z[c] - m);
-        idx[i] = (uint8_t)arg;
-        if (conf) conf[i] = 1.0f / sum;
-    }
-}
-
 // Tiles (32 x 64, the scale sweep's tiling) whose least confident pixel is
 // below thr go to the fallback list.
 __global__ void __launch_bounds__(256) k_sel_fallback_tiles(const float *conf, int w, int h, int pitch, float thr,
@@ -607,12 +785,12 @@ __global__ void __launch_bounds__(256) k_sel_fallback_tiles(const float *conf, i
 
 namespace {
 
-// Persistent grid of a kernel that allocates 32 TMEM columns per block.  The
-// runtime's occupancy query reports one block per SM for any kernel that uses
-// tcgen05.alloc, whatever its resources, so the blocks per SM are taken here
-// from registers and shared memory, and capped so that every resident block's
-// columns fit the SM's 512 (an allocation never waits on another block).
-int tmem_grid(const void *kernel, size_t dyn_smem, int tiles)
+// Persistent grid of a kernel that allocates `cols` TMEM columns per block.
+// The runtime's occupancy query reports one block per SM for any kernel that
+// uses tcgen05.alloc, whatever its resources, so the blocks per SM are taken
+// here from registers and shared memory, and capped so that every resident
+// block's columns fit the SM's 512 (an allocation never waits on another block).
+int tmem_grid(const void *kernel, size_t dyn_smem, int tiles, int cols, int threads = CT)
 {
     static int sms = 0, regs_sm = 0, smem_sm = 0, smem_reserved = 0;
     int dev = 0;
@@ -629,24 +807,45 @@ int tmem_grid(const void *kernel, size_t dyn_smem, int tiles)
     cudaFuncAttributes fa;
     int per_sm = 1;
     if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) {
-        const int warps = (CT + 31) / 32;
+        const int warps = (threads + 31) / 32;
         const int regs_block = warps * ((fa.numRegs * 32 + 255) / 256) * 256;
         const size_t smem_block = fa.sharedSizeBytes + dyn_smem + (size_t)smem_reserved;
         per_sm = regs_block > 0 ? regs_sm / regs_block : 1;
         if (smem_block > 0) per_sm = std::min<int>(per_sm, (int)((size_t)smem_sm / smem_block));
-        per_sm = std::min(per_sm, std::min(2048 / CT, 512 / 32));
+        per_sm = std::min(per_sm, std::min(2048 / threads, 512 / cols));
         if (per_sm < 1) per_sm = 1;
     }
     const long long g = (long long)per_sm * sms;
     return (int)(tiles < g ? (tiles > 0 ? tiles : 1) : g);
 }
 
+// Tensor map of a row-planar activation tensor in 8-pixel segments (16
+// elements of 8 bytes = 128 bytes of one chunk plane): dimensions {16,
+// apitch / 8 segments, cj stored chunk planes, h rows, n_img images}; box
+// {16, 18, cj, 1, 1}, a 144-pixel window of a row in every stored plane.
+// Segments outside the row and rows outside 0 .. h - 1 read as zero; the
+// pixels w .. apitch - 1 are zero in memory.
+int make_act_map(CUtensorMap *m, const void *act, int cj, int apitch, int h, long long aimg_stride, int n_img)
+{
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc || ((uintptr_t)act & 15u) || apitch % kSegPx) return 1;
+    const cuuint64_t dim[5] = {16, (cuuint64_t)apitch / kSegPx, (cuuint64_t)cj, (cuuint64_t)h, (cuuint64_t)n_img};
+    const cuuint64_t str[4] = {128, (cuuint64_t)apitch * 16, (cuuint64_t)apitch * cj * 16,
+                               (cuuint64_t)aimg_stride * cj * 16};
+    const cuuint32_t box[5] = {16, kWinPx / kSegPx, (cuuint32_t)cj, 1, 1};
+    const cuuint32_t one[5] = {1, 1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<void *>(act), dim, str, box, one,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS;
+}
+
 template <int CI, int CO, int MODE>
 int launch_conv(const ConvArgs &a, cudaStream_t st)
 {
-    const size_t smem = conv_smem_bytes(CI, CO, kMaxDil);
+    const size_t smem = conv_smem_bytes(CI, CO);
     static int attr_dev = -1;
     int dev = 0;
+    if (a.d < 1 || a.d > kMaxDil || a.in_cj < 1 || a.in_cj > CI / 8 || a.apitch != act_pitch(a.w)) return 1;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
     if (attr_dev != dev) {
         if (cudaFuncSetAttribute(k_conv_tc<CI, CO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -654,15 +853,24 @@ int launch_conv(const ConvArgs &a, cudaStream_t st)
             return 1;
         attr_dev = dev;
     }
+    CUtensorMap map;
+    if (make_act_map(&map, a.in, a.in_cj, a.apitch, a.h, a.aimg_stride, a.n_img)) return 1;
+    // Segment length: about four units per resident block (each unit reads
+    // two input rows more than it writes; long segments leave blocks idle),
+    // 4 .. 64 rows.
+    const int resident =
+        tmem_grid((const void *)k_conv_tc<CI, CO, MODE>, smem, 1 << 30, (int)conv_tmem_cols(CO), kConvThreads);
     const long long tiles = (long long)a.n_img * a.h * ((a.w + TM - 1) / TM);
-    const int grid = tmem_grid((const void *)k_conv_tc<CI, CO, MODE>, conv_smem_bytes(CI, CO, a.d),
-                               (int)(tiles < (1 << 30) ? tiles : (1 << 30)));
-    k_conv_tc<CI, CO, MODE><<<grid, CT, conv_smem_bytes(CI, CO, a.d), st>>>(a);
+    ConvArgs b = a;
+    b.seg_rows = (int)std::max<long long>(4, std::min<long long>(64, tiles / (4LL * resident)));
+    const long long units = conv_units(b.n_img, b.w, b.h, b.d, b.seg_rows);
+    const int grid = (int)std::min<long long>(units, resident);
+    k_conv_tc<CI, CO, MODE><<<grid, kConvThreads, smem, st>>>(map, b);
     return cudaGetLastError() != cudaSuccess;
 }
 
 struct SelBufs {
-    __nv_bfloat16 *act[kLayers];  // inputs of layers 0..3 (16 / 32 / 32 / 32 channels)
+    __nv_bfloat16 *act[kLayers];  // inputs of layers 0..3, row-planar (8 stored / 32 / 32 / 32 channels)
     float *logits;                // n_bins per pixel (room for kMaxBins)
     __nv_bfloat16 *dz16;          // gradient of the last layer's output (16 channels)
     __nv_bfloat16 *dz[2];         // 32-channel gradients (ping-pong)
@@ -670,16 +878,19 @@ struct SelBufs {
     size_t bytes;
 };
 
-// Workspace of the network.  Training keeps every layer's input for the
-// backward pass; inference (infer) needs the input of the current layer only,
-// so layers 1 and 3 share one buffer: [status | act0 (16 channels) | A | B |
-// logits], with act1 = act3 = A and act2 = B.
-SelBufs sel_bufs(char *ws, long long npx, bool infer = false)
+// Workspace of the network for a stack of n_img images (h rows; the
+// activations at act_pitch(w) pixels per row, the logits at `pitch`).
+// Training keeps every layer's input for the backward pass; inference (infer)
+// needs the input of the current layer only, so layers 1 and 3 share one
+// buffer: [status | act0 | A | B | logits], with act1 = act3 = A and act2 = B.
+SelBufs sel_bufs(char *ws, int n_img, int w, int h, int pitch, bool infer = false)
 {
     SelBufs b{};
+    const long long npx = (long long)n_img * h * act_pitch(w);  // activation pixels
+    const long long lpx = (long long)n_img * h * pitch;         // logit pixels
     size_t o = 256;  // header: status word
     b.status = (int *)ws;
-    const size_t per[kLayers] = {16, 32, 32, 32};
+    const size_t per[kLayers] = {8, 32, 32, 32};  // layer 0 stores one chunk plane of its 16 channels
     for (int l = 0; l < kLayers; ++l) {
         if (infer && l == 3) {
             b.act[3] = b.act[1];
@@ -689,7 +900,7 @@ SelBufs sel_bufs(char *ws, long long npx, bool infer = false)
         o += align_up((size_t)npx * per[l] * 2, 256);
     }
     b.logits = ws ? (float *)(ws + o) : nullptr;
-    o += align_up((size_t)npx * kMaxBins * 4, 256);
+    o += align_up((size_t)lpx * kMaxBins * 4, 256);
     if (infer) {
         b.bytes = o;
         return b;
@@ -754,21 +965,33 @@ int check_stack(const void *d, int n_img, int w, int h, int pitch)
 }
 
 // Forward pass of the network over a stack of n_img images (img_stride = h * pitch).
-int sel_forward(const SelPtrs &P, const float *imgs, int n_img, int w, int h, int pitch, int n_bins,
-                const SelBufs &B, cudaStream_t st)
+// Geometry fields of a convolution over a stack of n_img images.
+ConvArgs conv_geometry(int n_img, int w, int h, int pitch, int *status)
 {
-    const long long stride = (long long)h * pitch;
-    const int g = n_img * h < 8192 ? n_img * h : 8192;  // blocks stride over image rows
-    k_sel_prep<<<g, 256, 0, st>>>(imgs, B.act[0], n_img, w, h, pitch, stride);
     ConvArgs a{};
     a.n_img = n_img;
     a.w = w;
     a.h = h;
     a.pitch = pitch;
-    a.img_stride = stride;
-    a.status = B.status;
+    a.apitch = act_pitch(w);
+    a.img_stride = (long long)h * pitch;
+    a.aimg_stride = (long long)h * a.apitch;
+    a.status = status;
+    return a;
+}
+
+// With idx set, the last layer writes the prediction (argmax bin and its
+// probability) instead of the logits.
+int sel_forward(const SelPtrs &P, const float *imgs, int n_img, int w, int h, int pitch, int n_bins,
+                const SelBufs &B, cudaStream_t st, uint8_t *idx = nullptr, float *conf = nullptr)
+{
+    const ConvArgs g0 = conv_geometry(n_img, w, h, pitch, B.status);
+    const int g = n_img * h < 8192 ? n_img * h : 8192;  // blocks stride over image rows
+    k_sel_prep<<<g, 256, 0, st>>>(imgs, B.act[0], n_img, w, h, pitch, g0.img_stride, g0.apitch, g0.aimg_stride);
+    ConvArgs a = g0;
     for (int l = 0; l < kLayers; ++l) {
         a.in = B.act[l];
+        a.in_cj = l == 0 ? 1 : CI_P[l] / 8;
         a.wts = P.fwd[l];
         a.bias = P.bias + 32 * l;
         a.d = DIL[l];
@@ -780,6 +1003,12 @@ int sel_forward(const SelPtrs &P, const float *imgs, int n_img, int w, int h, in
         } else if (l < kLayers - 1) {
             a.out = B.act[l + 1];
             rc = launch_conv<32, 32, CONV_RELU_BF16>(a, st);
+        } else if (idx) {
+            a.out = nullptr;
+            a.idx = idx;
+            a.conf = conf;
+            a.n_out = n_bins;
+            rc = launch_conv<32, 16, CONV_PREDICT>(a, st);
         } else {
             a.out = B.logits;
             a.n_out = n_bins;
@@ -792,7 +1021,7 @@ int sel_forward(const SelPtrs &P, const float *imgs, int n_img, int w, int h, in
 
 template <int CIP, int COP>
 int launch_wgrad(const __nv_bfloat16 *X, const __nv_bfloat16 *dZ, int l, const SelPtrs &P, int n_img, int w, int h,
-                 int pitch, int *status, cudaStream_t st)
+                 int *status, cudaStream_t st)
 {
     const SelLayout L = sel_layout();
     static int attr_dev = -1;
@@ -808,9 +1037,10 @@ int launch_wgrad(const __nv_bfloat16 *X, const __nv_bfloat16 *dZ, int l, const S
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long tiles = (long long)n_img * h * ((w + TM - 1) / TM);
     const int grid = (int)(tiles < sms ? (tiles > 0 ? tiles : 1) : sms);  // one block (all of TMEM) per SM
-    k_sel_wgrad_tc<CIP, COP><<<grid, CT, wg_smem<CIP>(), st>>>(X, dZ, CI_R[l], CO_R[l], n_img, w, h, pitch, DIL[l],
-                                                               (long long)h * pitch, P.grad + L.w_off[l],
-                                                               P.grad + L.b_off[l], status);
+    const int apitch = act_pitch(w);
+    k_sel_wgrad_tc<CIP, COP><<<grid, CT, wg_smem<CIP>(), st>>>(X, l == 0 ? 1 : CIP / 8, dZ, CI_R[l], CO_R[l], n_img,
+                                                               w, h, apitch, DIL[l], (long long)h * apitch,
+                                                               P.grad + L.w_off[l], P.grad + L.b_off[l], status);
     return cudaGetLastError() != cudaSuccess;
 }
 
@@ -824,13 +1054,13 @@ extern "C" size_t fd4_selector_param_bytes(void) { return sel_layout().bytes; }
 extern "C" size_t fd4_selector_workspace_bytes(int n_img, int w, int h, int pitch)
 {
     if (n_img < 1 || w < 1 || h < 1 || pitch < w) return 0;
-    return sel_bufs(nullptr, (long long)n_img * h * pitch).bytes;
+    return sel_bufs(nullptr, n_img, w, h, pitch).bytes;
 }
 
 extern "C" size_t fd4_selector_infer_workspace_bytes(int n_img, int w, int h, int pitch)
 {
     if (n_img < 1 || w < 1 || h < 1 || pitch < w) return 0;
-    return sel_bufs(nullptr, (long long)n_img * h * pitch, true).bytes;
+    return sel_bufs(nullptr, n_img, w, h, pitch, true).bytes;
 }
 
 extern "C" int fd4_selector_set_weights(void *d_params, const float *h_w, fd4_stream_t stream)
@@ -895,7 +1125,7 @@ extern "C" int fd4_selector_forward(const void *d_params, const float *d_imgs, i
     const long long npx = (long long)n_img * h * pitch;
     if (!d_ws || ws_bytes < fd4_selector_infer_workspace_bytes(n_img, w, h, pitch)) return FD4_ERR_WS_TOO_SMALL;
     cudaStream_t st = (cudaStream_t)stream;
-    SelBufs B = sel_bufs((char *)d_ws, npx, true);
+    SelBufs B = sel_bufs((char *)d_ws, n_img, w, h, pitch, true);
     if (cudaMemsetAsync(B.status, 0, sizeof(int), st) != cudaSuccess) return FD4_ERR_CUDA;
     if (sel_forward(sel_ptrs((void *)d_params), d_imgs, n_img, w, h, pitch, n_bins, B, st)) return FD4_ERR_CUDA;
     if (cudaMemcpyAsync(d_logits, B.logits, sizeof(float) * n_bins * npx, cudaMemcpyDeviceToDevice, st) !=
@@ -911,27 +1141,20 @@ extern "C" int fd4_selector_grad(void *d_params, const float *d_imgs, const uint
     int rc;
     if (!d_params || !d_labels || !d_loss || !bins_ok(n_bins)) return FD4_ERR_BAD_ARG;
     if ((rc = check_stack(d_imgs, n_img, w, h, pitch)) != FD4_OK) return rc;
-    const long long npx = (long long)n_img * h * pitch;
     if (!d_ws || ws_bytes < fd4_selector_workspace_bytes(n_img, w, h, pitch)) return FD4_ERR_WS_TOO_SMALL;
     cudaStream_t st = (cudaStream_t)stream;
-    SelBufs B = sel_bufs((char *)d_ws, npx);
+    SelBufs B = sel_bufs((char *)d_ws, n_img, w, h, pitch);
     const SelPtrs P = sel_ptrs(d_params);
-    const long long stride = (long long)h * pitch;
     if (cudaMemsetAsync(B.status, 0, sizeof(int), st) != cudaSuccess) return FD4_ERR_CUDA;
     if (sel_forward(P, d_imgs, n_img, w, h, pitch, n_bins, B, st)) return FD4_ERR_CUDA;
+    ConvArgs a = conv_geometry(n_img, w, h, pitch, B.status);
     const int g = n_img * h < 8192 ? n_img * h : 8192;
-    k_sel_softmax_ce<<<g, 256, 0, st>>>(B.logits, d_labels, B.dz16, n_img, w, h, pitch, stride,
-                                        1.0f / (float)((long long)n_img * w * h), d_loss, n_bins);
-    ConvArgs a{};
-    a.n_img = n_img;
-    a.w = w;
-    a.h = h;
-    a.pitch = pitch;
-    a.img_stride = stride;
-    a.status = B.status;
+    k_sel_softmax_ce<<<g, 256, 0, st>>>(B.logits, d_labels, B.dz16, n_img, w, h, pitch, a.img_stride, a.apitch,
+                                        a.aimg_stride, 1.0f / (float)((long long)n_img * w * h), d_loss, n_bins);
     // layer 3 (last): weight gradient, then data gradient into dz[0] masked by act[3] > 0
-    if (launch_wgrad<32, 16>(B.act[3], B.dz16, 3, P, n_img, w, h, pitch, B.status, st)) return FD4_ERR_CUDA;
+    if (launch_wgrad<32, 16>(B.act[3], B.dz16, 3, P, n_img, w, h, B.status, st)) return FD4_ERR_CUDA;
     a.in = B.dz16;
+    a.in_cj = 2;
     a.out = B.dz[0];
     a.wts = P.dgr[3];
     a.bias = nullptr;
@@ -940,8 +1163,9 @@ extern "C" int fd4_selector_grad(void *d_params, const float *d_imgs, const uint
     if (launch_conv<16, 32, CONV_MASK_BF16>(a, st)) return FD4_ERR_CUDA;
     int cur = 0;
     for (int l = 2; l >= 1; --l) {
-        if (launch_wgrad<32, 32>(B.act[l], B.dz[cur], l, P, n_img, w, h, pitch, B.status, st)) return FD4_ERR_CUDA;
+        if (launch_wgrad<32, 32>(B.act[l], B.dz[cur], l, P, n_img, w, h, B.status, st)) return FD4_ERR_CUDA;
         a.in = B.dz[cur];
+        a.in_cj = 4;
         a.out = B.dz[cur ^ 1];
         a.wts = P.dgr[l];
         a.mask = B.act[l];
@@ -949,7 +1173,7 @@ extern "C" int fd4_selector_grad(void *d_params, const float *d_imgs, const uint
         if (launch_conv<32, 32, CONV_MASK_BF16>(a, st)) return FD4_ERR_CUDA;
         cur ^= 1;
     }
-    if (launch_wgrad<16, 32>(B.act[0], B.dz[cur], 0, P, n_img, w, h, pitch, B.status, st)) return FD4_ERR_CUDA;
+    if (launch_wgrad<16, 32>(B.act[0], B.dz[cur], 0, P, n_img, w, h, B.status, st)) return FD4_ERR_CUDA;
     return FD4_OK;
 }
 
@@ -975,12 +1199,11 @@ extern "C" int fd4_selector_predict(const void *d_params, const float *d_imgs, i
     if ((rc = check_stack(d_imgs, n_img, w, h, pitch)) != FD4_OK) return rc;
     if (!d_ws || ws_bytes < fd4_selector_infer_workspace_bytes(n_img, w, h, pitch)) return FD4_ERR_WS_TOO_SMALL;
     cudaStream_t st = (cudaStream_t)stream;
-    SelBufs B = sel_bufs((char *)d_ws, (long long)n_img * h * pitch, true);
+    SelBufs B = sel_bufs((char *)d_ws, n_img, w, h, pitch, true);
     if (cudaMemsetAsync(B.status, 0, sizeof(int), st) != cudaSuccess) return FD4_ERR_CUDA;
-    if (sel_forward(sel_ptrs((void *)d_params), d_imgs, n_img, w, h, pitch, n_bins, B, st)) return FD4_ERR_CUDA;
-    const int g = n_img * h < 8192 ? n_img * h : 8192;
-    k_sel_predict<<<g, 256, 0, st>>>(B.logits, n_img, w, h, pitch, n_bins, d_idx, d_conf);
-    return cudaGetLastError() == cudaSuccess ? FD4_OK : FD4_ERR_CUDA;
+    if (sel_forward(sel_ptrs((void *)d_params), d_imgs, n_img, w, h, pitch, n_bins, B, st, d_idx, d_conf))
+        return FD4_ERR_CUDA;
+    return FD4_OK;
 }
 
 extern "C" int fd4_selector_status(const void *d_ws, int *status, fd4_stream_t stream)
@@ -1070,20 +1293,15 @@ extern "C" int fd4_selftest_wait_timeout(void *d_ws, size_t ws_bytes, int *statu
     if (!d_ws || !status || ((uintptr_t)d_ws & 255u)) return FD4_ERR_BAD_ARG;
     if (ws_bytes < fd4_selector_workspace_bytes(1, w, h, pitch)) return FD4_ERR_WS_TOO_SMALL;
     cudaStream_t st = (cudaStream_t)stream;
-    SelBufs B = sel_bufs((char *)d_ws, (long long)h * pitch);
+    SelBufs B = sel_bufs((char *)d_ws, 1, w, h, pitch);
     if (cudaMemsetAsync(d_ws, 0, fd4_selector_workspace_bytes(1, w, h, pitch), st) != cudaSuccess)
         return FD4_ERR_CUDA;
-    ConvArgs a{};
+    ConvArgs a = conv_geometry(1, w, h, pitch, B.status);
     a.in = B.act[1];
+    a.in_cj = 4;
     a.out = B.act[2];
     a.wts = (const uint4 *)B.act[3];  // zeros; never multiplied
-    a.n_img = 1;
-    a.w = w;
-    a.h = h;
-    a.pitch = pitch;
     a.d = 1;
-    a.img_stride = (long long)h * pitch;
-    a.status = B.status;
     a.withhold_commit = 1;
     if (launch_conv<32, 32, CONV_RELU_BF16>(a, st)) return FD4_ERR_CUDA;
     return fd4_selector_status(d_ws, status, stream);

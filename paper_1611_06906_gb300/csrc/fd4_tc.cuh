@@ -91,6 +91,53 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity)
     return ok != 0;
 }
 
+// Make the mbarrier initialisations visible to the bulk-copy (async) proxy.
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Arrive on m (count 1) and expect `bytes` more transaction bytes in this phase.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *m, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of m, at most ns nanoseconds; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, uint32_t parity, uint64_t ns)
+{
+    if (mbar_try_wait(m, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(m, parity))
+        if (global_ns() - t0 > ns) return false;
+    return true;
+}
+
+// Tensor-map copy of one 4-D box into shared memory (byte count reported to m).
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void *map, int c0, int c1, int c2, int c3, uint64_t *m)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(m))
+        : "memory");
+}
+
+// Tensor-map copy of one 5-D box into shared memory (byte count reported to m).
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const void *map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t *m)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(m))
+        : "memory");
+}
+
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 // Make generic-proxy shared-memory writes visible to the tensor core (async proxy).

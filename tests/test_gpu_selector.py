@@ -124,6 +124,9 @@ def test_predict_is_the_argmax_and_status_is_clean():
     assert torch.equal(idx[:, :w], ref)
     c = conf[:, :w]
     assert float(c.min()) >= 1.0 / 8 - 1e-6 and float(c.max()) <= 1.0
+    # the confidence is the softmax probability of the chosen bin
+    pr = torch.softmax(logits[0, :, :w].double(), -1).max(-1).values
+    assert float((c.double() - pr).abs().max()) <= 1e-5
     # a stack of images in one call: the same indices image by image
     img2 = synth.vessel_tree(7201, w, h, depth=3, r0=3.0)
     stack = torch.stack([u, fd4.to_device(img2)])
@@ -132,6 +135,44 @@ def test_predict_is_the_argmax_and_status_is_clean():
         one, _ = sel.predict(im, w, n_bins=12)
         assert torch.equal(idx_s[k, :, :w], one[:, :w])
     assert int(idx_s[:, :, :w].max()) < 12
+
+
+def test_forward_on_a_large_stack_matches_oracle_windows():
+    """Two 1024 x 1536 images: long row walks per block (several segments of
+    each dilation's residue classes).  The oracle evaluates windows with the
+    receptive-field margin (15 pixels: dilations 1 + 2 + 4 + 8); a pixel is
+    compared where its whole receptive field lies in the window or outside
+    the image (zero there on both sides)."""
+    h, w, n_bins, R = 1024, 1536, 12, 15
+    imgs = [synth.vessel_tree(7300 + i, w, h, depth=4, r0=4.0) for i in range(2)]
+    params = _params(4)
+    sel = fd4.Selector()
+    sel.set_weights(_flat(params))
+    logits = sel.forward(_stack(imgs), w, n_bins=n_bins)
+    P = _head(_unflat(_flat(params)), n_bins)
+    wins = [(0, 0), (0, w - 48), (h - 48, 0), (h - 48, w - 48), (500, 700), (64 * 7 + 3, 128 * 5 - 20)]
+    agree, tot = 0, 0
+    for i, im in enumerate(imgs):
+        for y0, x0 in wins:
+            ya, yb = max(0, y0 - R), min(h, y0 + 48 + R)
+            xa, xb = max(0, x0 - R), min(w, x0 + 48 + R)
+            _, _, ref = SO.forward(im[ya:yb, xa:xb].astype(np.float64), P)
+            got = logits[i, ya:yb, xa:xb, :].cpu().numpy()
+            ys = np.arange(ya, yb)
+            xs = np.arange(xa, xb)
+            vy = ((ys - R >= ya) | (ya == 0)) & ((ys + R < yb) | (yb == h))
+            vx = ((xs - R >= xa) | (xa == 0)) & ((xs + R < xb) | (xb == w))
+            m = vy[:, None] & vx[None, :]
+            assert m.sum() >= 48 * 48
+            scale = np.abs(ref[m]).max() + 1.0
+            assert np.abs(got[m] - ref[m]).max() <= 2e-2 * scale, (i, y0, x0)
+            agree += int((got[m].argmax(-1) == ref[m].argmax(-1)).sum())
+            tot += int(m.sum())
+    assert agree / tot >= 0.97
+    # the fused read-out of the same stack: the argmax of these logits
+    import torch
+    idx, _ = sel.predict(_stack(imgs), w, n_bins=n_bins)
+    assert torch.equal(idx[:, :, :w], logits[:, :, :w].argmax(-1).to(torch.uint8))
 
 
 def test_training_reduces_the_loss():
