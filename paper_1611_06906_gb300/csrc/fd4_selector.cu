@@ -81,7 +81,13 @@ struct ConvArgs {
     int withhold_commit;        // self-test only: issue no MMA, so the waits run out
 };
 
-constexpr int kConvThreads = 192;  // warps 0-3: epilogue (TMEM lane quarters), 4: copies, 5: MMAs
+// Warps of a convolution block: the epilogue warps (a TMEM lane quarter and a
+// group of 16 output channels each: 8 for 32 outputs, 4 for 16), then the
+// copy warp and the MMA warps: one for 32 outputs (the epilogue is the longer
+// stage), two for 16 (even and odd input rows; issuing is the longer stage).
+__host__ __device__ constexpr int conv_epi_warps(int CO) { return CO == 32 ? 8 : 4; }
+__host__ __device__ constexpr int conv_mma_warps(int CO) { return CO == 32 ? 1 : 2; }
+__host__ __device__ constexpr int conv_threads(int CO) { return (conv_epi_warps(CO) + 1 + conv_mma_warps(CO)) * 32; }
 constexpr int kSlots = 5;          // input rows staged per block
 constexpr uint64_t kConvWaitNs = 1000000000ull;  // bounded waits: one second
 // A staged row holds pixels x0 - 8 .. x0 + 135 of each plane: 18 segments of
@@ -152,16 +158,18 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[N])
 // into a ring of kSlots buffers (one tensor-map copy per row, zero fill
 // outside the image); the MMA warp issues a row's MMAs as soon as its copy
 // and a free accumulator are there, into the accumulator the epilogue is not
-// reading.  Handoffs are mbarriers: full (copy landed), empty (MMAs of the
+// reading (with two MMA warps, one per accumulator, alternate rows).  Handoffs are mbarriers: full (copy landed), empty (MMAs of the
 // slot done), acc_full (accumulator written), acc_empty (epilogue has read
 // it).  Every wait is bounded (one second): on timeout the kernel records
 // FD4_ERR_TIMEOUT, the roles stop, the copies and MMAs in flight are waited
 // for (bounded), the TMEM is freed and the kernel returns.
 template <int CI, int CO, int MODE>
-__global__ void __launch_bounds__(kConvThreads, 2) k_conv_tc(const __grid_constant__ CUtensorMap xmap, ConvArgs a)
+__global__ void __launch_bounds__(conv_threads(CO), 2) k_conv_tc(const __grid_constant__ CUtensorMap xmap, ConvArgs a)
 {
     constexpr int CJ = CI / 8;  // 16-byte channel chunks per pixel
     constexpr int NN = 3 * CO;  // MMA N: the three ky taps
+    constexpr int NEPI = conv_epi_warps(CO);
+    constexpr int kThreads = conv_threads(CO);
     constexpr uint32_t kCols = conv_tmem_cols(CO);
     constexpr uint32_t slot_bytes = conv_slot_bytes(CJ);
     extern __shared__ unsigned char conv_raw[];
@@ -180,16 +188,18 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv_tc(const __grid_consta
 
     // weights [tap][ci / 8][co] -> [kx][ci / 8][ky][co]: the ky taps of one
     // (kx, chunk) are N-contiguous
-    for (int i = tid; i < 9 * CJ * CO; i += kConvThreads) {
+    for (int i = tid; i < 9 * CJ * CO; i += kThreads) {
         const int co = i % CO, j = (i / CO) % CJ, tap = i / (CO * CJ);
         const int ky = tap / 3, kx = tap - 3 * (tap / 3);
         Bs[((kx * CJ + j) * 3 + ky) * CO + co] = a.wts[i];
     }
     // planes the input does not store are zero in every slot (no copy writes them)
     for (int s = 0; s < kSlots; ++s)
-        for (int i = a.in_cj * kWinPx + tid; i < CJ * kWinPx; i += kConvThreads)
+        for (int i = a.in_cj * kWinPx + tid; i < CJ * kWinPx; i += kThreads)
             reinterpret_cast<uint4 *>(ring + s * slot_bytes)[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int c = tid; c < CO; c += kConvThreads) bias_s[c] = a.bias ? a.bias[c] : 0.0f;
+    // (the prediction masks the bins from n_out on with a bias of -inf)
+    for (int c = tid; c < CO; c += kThreads)
+        bias_s[c] = (MODE == CONV_PREDICT && c >= a.n_out) ? -INFINITY : (a.bias ? a.bias[c] : 0.0f);
     if (warp == 0) {
         tc::tmem_alloc(&tmem_base, kCols);
         tc::tmem_relinquish();
@@ -201,7 +211,7 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv_tc(const __grid_consta
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&accf_bar[b], 1);
-            tc::mbar_init(&acce_bar[b], 4);  // one arrival per epilogue warp
+            tc::mbar_init(&acce_bar[b], NEPI);  // one arrival per epilogue warp
         }
         abort_flag = 0;
         tc::fence_mbar_init();
@@ -217,7 +227,7 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv_tc(const __grid_consta
     const long long total = conv_units(a.n_img, a.w, a.h, d, a.seg_rows);
     const uint32_t ring_s = tc::smem_u32(ring);
 
-    if (warp == 4) {
+    if (warp == NEPI) {
         // ---- copy warp: input rows into the ring
         if (lane == 0) {
             uint32_t q = 0;  // rows of this block so far: slot q % kSlots, use q / kSlots
@@ -241,8 +251,12 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv_tc(const __grid_consta
             for (uint32_t s = 0; s < kSlots && s < q; ++s)
                 tc::mbar_wait_bounded(&full_bar[s], ((q - 1 - s) / kSlots) & 1u, kConvWaitNs);
         }
-    } else if (warp == 5) {
-        // ---- MMA warp
+    } else if (warp > NEPI) {
+        // ---- MMA warps: with two, the first takes the even rows (accumulator
+        // 0), the second the odd rows (accumulator 1); a row's MMAs are issued
+        // by one thread, in order
+        constexpr int NMMA = conv_mma_warps(CO);
+        const uint32_t mine = (uint32_t)(warp - NEPI - 1);
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16_f32(TM, NN);
             const uint64_t adesc0 = tc::sdesc_kmajor(ring_s, (uint32_t)(kWinPx * 16), 128);
@@ -254,6 +268,7 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv_tc(const __grid_consta
                 if (!conv_unit(a, u, segs, tiles_x, c)) continue;
                 for (int r = c.k0 - 1; r <= c.k1; ++r, ++q) {
                     const uint32_t s = q % kSlots, n = q / kSlots, b = q & 1u, nb = q >> 1;
+                    if (NMMA == 2 && b != mine) continue;
                     if (abort_flag || !tc::mbar_wait_bounded(&full_bar[s], n & 1u, kConvWaitNs) ||
                         (nb > 0 && !tc::mbar_wait_bounded(&acce_bar[b], (nb - 1) & 1u, kConvWaitNs))) {
                         abort_flag = 1;
@@ -278,21 +293,29 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv_tc(const __grid_consta
                     ++committed;
                 }
             }
-            // the MMAs issued are complete before the TMEM is freed
-            for (uint32_t b = 0; b < 2 && b < committed; ++b)
-                tc::mbar_wait_bounded(&accf_bar[b], ((committed - 1 - b) / 2) & 1u, kConvWaitNs);
+            // the MMAs issued are complete before the TMEM is freed: the last
+            // commit on each accumulator this warp feeds
+            if (NMMA == 2) {
+                if (committed > 0) tc::mbar_wait_bounded(&accf_bar[mine], (committed - 1) & 1u, kConvWaitNs);
+            } else {
+                for (uint32_t b = 0; b < 2 && b < committed; ++b)
+                    tc::mbar_wait_bounded(&accf_bar[b], ((committed - 1 - b) / 2) & 1u, kConvWaitNs);
+            }
         }
     } else {
-        // ---- epilogue warps: lane quarter `warp` of the accumulators
-        const int i = warp * 32 + lane;  // tile pixel = TMEM lane
+        // ---- epilogue warps: lane quarter warp % 4 of the accumulators,
+        // output channels 16 g .. 16 g + 15 with g = warp / 4 (the running sums
+        // stay in registers)
+        const int lq = warp & 3, g = warp >> 2;
+        const int i = lq * 32 + lane;  // tile pixel = TMEM lane
         uint32_t q = 0;
         bool stop = false;
         for (long long u = blockIdx.x; u < total && !stop; u += gridDim.x) {
             ConvUnit c;
             if (!conv_unit(a, u, segs, tiles_x, c)) continue;
-            float accA[CO], accB[CO];  // partial sums of output rows r - 1 and r
+            float accA[16], accB[16];  // partial sums of output rows r - 1 and r
 #pragma unroll
-            for (int k = 0; k < CO; ++k) accA[k] = accB[k] = 0.0f;
+            for (int k = 0; k < 16; ++k) accA[k] = accB[k] = 0.0f;
             const int gx = c.x0 + i;
             for (int r = c.k0 - 1; r <= c.k1; ++r, ++q) {
                 const uint32_t b = q & 1u, nb = q >> 1;
@@ -302,86 +325,108 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv_tc(const __grid_consta
                     break;
                 }
                 tc::fence_after_sync();
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + b * NN;
-                float v[CO], t[CO];
-                tmem_ld_cols<CO>(taddr + 2 * CO, v);  // ky = 2 closes output row r - 1
-#pragma unroll
-                for (int k = 0; k < CO; ++k) v[k] += accA[k];
-                tmem_ld_cols<CO>(taddr + CO, t);      // ky = 1 adds to output row r
-#pragma unroll
-                for (int k = 0; k < CO; ++k) accA[k] = accB[k] + t[k];
-                tmem_ld_cols<CO>(taddr, t);           // ky = 0 opens output row r + 1
-#pragma unroll
-                for (int k = 0; k < CO; ++k) accB[k] = t[k];
-                tc::fence_before_sync();
-                __syncwarp();
-                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&acce_bar[b]))
-                                            : "memory");
-                if (r - 1 < c.k0) continue;
+                const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + b * NN;
+                const bool emit = r - 1 >= c.k0;
                 const int y = c.rho + (r - 1) * d;
-                if (MODE == CONV_LOGITS_F32 || MODE == CONV_PREDICT) {
-                    if (gx >= a.w) continue;
-                    const size_t p = (size_t)c.img * (size_t)a.img_stride + (size_t)y * a.pitch + gx;
+                {
+                    // ky = 2 closes output row r - 1, ky = 1 adds to row r, ky = 0 opens row r + 1
+                    uint32_t r2[16], r1[16], r0[16];
+                    tc::tmem_ld_x16_async(taddr + 2 * CO + 16 * g, r2);
+                    tc::tmem_ld_x16_async(taddr + CO + 16 * g, r1);
+                    tc::tmem_ld_x16_async(taddr + 16 * g, r0);
+                    tc::tmem_wait_ld();
+                    // the accumulator is read: release it to the MMA warp
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0)
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&acce_bar[b]))
+                                     : "memory");
+                    float v[16];
 #pragma unroll
-                    for (int k = 0; k < CO; ++k) v[k] += bias_s[k];
-                    if (MODE == CONV_LOGITS_F32) {
-                        float *o = reinterpret_cast<float *>(a.out) + p * a.n_out;
-#pragma unroll
-                        for (int k = 0; k < CO; ++k)
-                            if (k < a.n_out) o[k] = v[k];
-                    } else {
-                        // argmax of the logits (ties to the smaller bin) and its softmax probability
-                        float m = -INFINITY;
-                        int arg = 0;
-#pragma unroll
-                        for (int k = 0; k < CO; ++k)
-                            if (k < a.n_out && v[k] > m) {
-                                m = v[k];
-                                arg = k;
-                            }
-                        float sum = 0.0f;
-#pragma unroll
-                        for (int k = 0; k < CO; ++k)
-                            if (k < a.n_out) sum += expf(v[k] - m);
-                        a.idx[p] = (uint8_t)arg;
-                        if (a.conf) a.conf[p] = 1.0f / sum;
+                    for (int k = 0; k < 16; ++k) {
+                        v[k] = __uint_as_float(r2[k]) + accA[k];
+                        accA[k] = accB[k] + __uint_as_float(r1[k]);
+                        accB[k] = __uint_as_float(r0[k]);
                     }
-                } else {
-                    if (gx >= a.apitch) continue;
-                    if (gx >= a.w) {  // the zero margin of the activation rows
+                    if (!emit) continue;
+                    // this pixel's 16 bytes in chunk plane j of output row y: row_px + j * apitch * 8
+                    const size_t row_px = act_off(a.aimg_stride, c.img, y, a.apitch, CO / 8, 0, gx);
+                    if constexpr (MODE == CONV_LOGITS_F32 || MODE == CONV_PREDICT) {
+                        static_assert(CO == 16, "the logits layer has 16 outputs");
+                        if (gx >= a.w) continue;
+                        const size_t p = (size_t)c.img * (size_t)a.img_stride + (size_t)y * a.pitch + gx;
 #pragma unroll
-                        for (int k = 0; k < CO; ++k) v[k] = 0.0f;
-                    } else if (MODE == CONV_MASK_BF16) {
+                        for (int k = 0; k < 16; ++k) v[k] += bias_s[k];
+                        if constexpr (MODE == CONV_LOGITS_F32) {
+                            float *o = reinterpret_cast<float *>(a.out) + p * a.n_out;
 #pragma unroll
-                        for (int qq = 0; qq < CO / 8; ++qq) {
-                            const uint4 mk = *reinterpret_cast<const uint4 *>(
-                                a.mask + act_off(a.aimg_stride, c.img, y, a.apitch, CO / 8, qq, gx));
-                            const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
+                            for (int k = 0; k < 16; ++k)
+                                if (k < a.n_out) o[k] = v[k];
+                        } else {
+                            // argmax of the first n_out logits (ties to the smaller bin; the
+                            // logits are finite, the masked bins -inf) as a pairwise tree, then
+                            // the softmax probability of the winner: 1 / sum_k exp(v_k - max)
+                            float m[16];
+                            int ix[16];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const uint32_t bits = (mw[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
-                                // bf16 > 0: bit patterns 0x0001 .. 0x7F80 (positive, up to +inf)
-                                if (bits - 1u >= 0x7F80u) v[8 * qq + e] = 0.0f;
+                            for (int k = 0; k < 16; ++k) {
+                                m[k] = v[k];
+                                ix[k] = k;
                             }
+#pragma unroll
+                            for (int st = 1; st < 16; st *= 2)
+#pragma unroll
+                                for (int k = 0; k < 16; k += 2 * st)
+                                    if (m[k + st] > m[k]) {  // the right half wins only when larger
+                                        m[k] = m[k + st];
+                                        ix[k] = ix[k + st];
+                                    }
+                            float e[16];
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) e[k] = __expf(v[k] - m[0]);  // exp(-inf) = 0
+#pragma unroll
+                            for (int st = 1; st < 16; st *= 2)
+#pragma unroll
+                                for (int k = 0; k < 16; k += 2 * st) e[k] += e[k + st];
+                            a.idx[p] = (uint8_t)ix[0];
+                            if (a.conf) a.conf[p] = __frcp_rn(e[0]);
                         }
                     } else {
+                        if (gx >= a.apitch) continue;
+                        if (gx >= a.w) {  // the zero margin of the activation rows
 #pragma unroll
-                        for (int k = 0; k < CO; ++k) v[k] = fmaxf(v[k] + bias_s[k], 0.0f);
-                    }
-                    __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(a.out);
+                            for (int k = 0; k < 16; ++k) v[k] = 0.0f;
+                        } else if (MODE == CONV_MASK_BF16) {
 #pragma unroll
-                    for (int qq = 0; qq < CO / 8; ++qq) {
-                        uint4 pk;
-                        __nv_bfloat162 b0 = __floats2bfloat162_rn(v[8 * qq + 0], v[8 * qq + 1]);
-                        __nv_bfloat162 b1 = __floats2bfloat162_rn(v[8 * qq + 2], v[8 * qq + 3]);
-                        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * qq + 4], v[8 * qq + 5]);
-                        __nv_bfloat162 b3 = __floats2bfloat162_rn(v[8 * qq + 6], v[8 * qq + 7]);
-                        pk.x = *reinterpret_cast<uint32_t *>(&b0);
-                        pk.y = *reinterpret_cast<uint32_t *>(&b1);
-                        pk.z = *reinterpret_cast<uint32_t *>(&b2);
-                        pk.w = *reinterpret_cast<uint32_t *>(&b3);
-                        *reinterpret_cast<uint4 *>(ob + act_off(a.aimg_stride, c.img, y, a.apitch, CO / 8, qq, gx)) =
-                            pk;
+                            for (int h2 = 0; h2 < 2; ++h2) {
+                                const uint4 mk = *reinterpret_cast<const uint4 *>(
+                                    a.mask + row_px + (size_t)(2 * g + h2) * a.apitch * 8);
+                                const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) {
+                                    const uint32_t bits = (mw[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+                                    // bf16 > 0: bit patterns 0x0001 .. 0x7F80 (positive, up to +inf)
+                                    if (bits - 1u >= 0x7F80u) v[8 * h2 + e] = 0.0f;
+                                }
+                            }
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) v[k] = fmaxf(v[k] + bias_s[16 * g + k], 0.0f);
+                        }
+                        __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(a.out);
+#pragma unroll
+                        for (int h2 = 0; h2 < 2; ++h2) {
+                            uint4 pk;
+                            __nv_bfloat162 b0 = __floats2bfloat162_rn(v[8 * h2 + 0], v[8 * h2 + 1]);
+                            __nv_bfloat162 b1 = __floats2bfloat162_rn(v[8 * h2 + 2], v[8 * h2 + 3]);
+                            __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * h2 + 4], v[8 * h2 + 5]);
+                            __nv_bfloat162 b3 = __floats2bfloat162_rn(v[8 * h2 + 6], v[8 * h2 + 7]);
+                            pk.x = *reinterpret_cast<uint32_t *>(&b0);
+                            pk.y = *reinterpret_cast<uint32_t *>(&b1);
+                            pk.z = *reinterpret_cast<uint32_t *>(&b2);
+                            pk.w = *reinterpret_cast<uint32_t *>(&b3);
+                            *reinterpret_cast<uint4 *>(ob + row_px + (size_t)(2 * g + h2) * a.apitch * 8) = pk;
+                        }
                     }
                 }
             }
@@ -859,13 +904,13 @@ int launch_conv(const ConvArgs &a, cudaStream_t st)
     // two input rows more than it writes; long segments leave blocks idle),
     // 4 .. 64 rows.
     const int resident =
-        tmem_grid((const void *)k_conv_tc<CI, CO, MODE>, smem, 1 << 30, (int)conv_tmem_cols(CO), kConvThreads);
+        tmem_grid((const void *)k_conv_tc<CI, CO, MODE>, smem, 1 << 30, (int)conv_tmem_cols(CO), conv_threads(CO));
     const long long tiles = (long long)a.n_img * a.h * ((a.w + TM - 1) / TM);
     ConvArgs b = a;
     b.seg_rows = (int)std::max<long long>(4, std::min<long long>(64, tiles / (4LL * resident)));
     const long long units = conv_units(b.n_img, b.w, b.h, b.d, b.seg_rows);
     const int grid = (int)std::min<long long>(units, resident);
-    k_conv_tc<CI, CO, MODE><<<grid, kConvThreads, smem, st>>>(map, b);
+    k_conv_tc<CI, CO, MODE><<<grid, conv_threads(CO), smem, st>>>(map, b);
     return cudaGetLastError() != cudaSuccess;
 }
 

@@ -107,12 +107,31 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// Wait for phase `parity` of m, at most ns nanoseconds; false if it gave up.
+// try_wait with a suspend-time hint: the thread sleeps until the phase
+// completes or about hint_ns nanoseconds pass, instead of spinning on issue
+// slots the working warps need.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *m, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(m)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of m, at most about ns nanoseconds (plus one
+// suspend period of 0.1 ms); false if it gave up.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, uint32_t parity, uint64_t ns)
 {
     if (mbar_try_wait(m, parity)) return true;
     const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(m, parity))
+    while (!mbar_try_wait_sleep(m, parity, 100000u))
         if (global_ns() - t0 > ns) return false;
     return true;
 }
@@ -161,6 +180,20 @@ __device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, float (&v)[32])
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes, without waiting:
+// the registers are valid after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld_x16_async(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, float (&v)[16])
 {
