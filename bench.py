@@ -262,6 +262,23 @@ def run_fd4(args, rank, world, local_rank):
     def max_over_ranks(ms):
         return _max_over_ranks(ms, dev)
 
+    if args.only_selector:  # profiling: the learned selector's prediction over the batch's stack only
+        if len({(b.h, b.pitch) for b in ims}) != 1:
+            raise SystemExit("--only-selector needs images of one size")
+        sel = fd4.Selector()
+        sel.init(1)  # the kernels' work does not depend on the weights
+        stack = torch.stack([b.u_in for b in ims])
+        idx = torch.zeros(stack.shape, dtype=torch.uint8, device=dev)
+        conf = torch.zeros(stack.shape, dtype=torch.float32, device=dev)
+        wss = fd4.Selector.workspace(len(ims), ims[0].w, ims[0].h, ims[0].pitch, dev, infer=True)
+        for _ in range(args.warmup):
+            sel.predict(stack, ims[0].w, n_bins=K, idx=idx, conf=conf, ws=wss)
+        ms = _timed(lambda: sel.predict(stack, ims[0].w, n_bins=K, idx=idx, conf=conf, ws=wss), args.steps,
+                    stream, torch) / args.steps
+        print(json.dumps({"only_selector": True, "images": len(ims), "ms_per_prediction": ms,
+                          "gpx_per_s": npx / (ms * 1e-3) / 1e9}))
+        return
+
     # batched path: one launch per stage across the batch, replayed as a CUDA graph
     lst = fd4.image_list([b.u_in for b in ims], [b.w for b in ims], [b.out for b in ims], [b.idx for b in ims])
     ws = fd4.batch_workspace(lst, K, dev)
@@ -825,6 +842,8 @@ def main():
     ap.add_argument("--sel-epochs", type=int, default=4, help="training epochs of the learned selector")
     ap.add_argument("--sel-threshold", type=float, default=0.5, help="fallback confidence threshold")
     ap.add_argument("--only-graph", action="store_true", help="replay the full graph only (profiling)")
+    ap.add_argument("--only-selector", action="store_true",
+                    help="time the learned selector's prediction over the batch only (profiling)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per FED launch from an ncu capture of the kernel the schedule runs "
                          "(default: the stored per-pixel figure of that schedule, else null)")
