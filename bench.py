@@ -676,6 +676,79 @@ def _crease_accuracy(fd4, creases, pairs, gt, sigma_d, mode, label):
     return res
 
 
+def learned_reselect(sel, ims, src, wss, ws, sig, T, M, n, mode, sched, K, stream, torch, fd4, reps):
+    """Scales re-selected before every cycle by the network (SURVEY NEXT-2 with
+    the learned selector): M times, the network's prediction on u^k over the
+    image stack (one launch per layer), then one FED cycle with those scales
+    (a one-cycle graph, scales given; the cycle's steps are those of T / M).
+    Compared with the plain re-selecting schedule (reselect_each_cycle) on the
+    same batch: its rate, and the distance between the two outputs.  src: the
+    input stack; wss, ws: the selector's and the batch's workspaces (reused)."""
+    dev = ims[0].u_in.device
+    nb, w = len(ims), ims[0].w
+    shape = (nb,) + tuple(ims[0].u_in.shape)
+    buf = [torch.empty(shape, dtype=torch.float32, device=dev) for _ in range(2)]
+    idx = torch.zeros(shape, dtype=torch.uint8, device=dev)
+    prm = fd4.params(mode=mode, **sched.as_params())
+
+    def lst(a, b):
+        return fd4.image_list([a[k] for k in range(nb)], [w] * nb, [b[k] for k in range(nb)],
+                              [idx[k] for k in range(nb)])
+
+    lists = [lst(src, buf[0]), lst(buf[0], buf[1]), lst(buf[1], buf[0])]
+    graphs = [fd4.Graph(l, sig, T / M, 1, n, prm, sigma_given=True, ws=ws) for l in lists]
+    net_ms = [0.0]
+
+    def step():
+        cur = src
+        for c in range(M):
+            sel.predict(cur, w, n_bins=K, idx=idx, ws=wss)
+            g = 0 if c == 0 else (1 if c % 2 else 2)
+            graphs[g].launch()
+            cur = buf[0] if g != 1 else buf[1]
+        return cur
+
+    out = step()
+    torch.cuda.synchronize()
+    ms = _timed(step, reps, stream, torch) / reps
+    net_ms = _timed(lambda: sel.predict(src, w, n_bins=K, idx=idx, ws=wss), reps, stream, torch) / reps
+    # the network's scale agreement with the plain selection on the same u^k, cycle by cycle
+    agree = []
+    cur = src
+    wsel = fd4.workspace(fd4.OP_SELECT_SCALES, ims[0].pitch, ims[0].h, K, dev)
+    idx_plain = torch.zeros(ims[0].u_in.shape, dtype=torch.uint8, device=dev)
+    for c in range(M):
+        sel.predict(cur, w, n_bins=K, idx=idx, ws=wss)
+        a = 0
+        for k in range(nb):
+            fd4.select_scales(cur[k], w, sig, fd4.params(mode=mode), ws=wsel, idx=idx_plain)
+            a += int((idx[k, :, :w] == idx_plain[:, :w]).sum())
+        agree.append(a / (nb * ims[0].npx))
+        g = 0 if c == 0 else (1 if c % 2 else 2)
+        graphs[g].launch()
+        cur = buf[0] if g != 1 else buf[1]
+    out = cur
+    torch.cuda.synchronize()
+    # the plain re-selecting schedule on the same inputs
+    outp = torch.empty(shape, dtype=torch.float32, device=dev)
+    idxp = torch.zeros(shape, dtype=torch.uint8, device=dev)
+    lp = fd4.image_list([src[k] for k in range(nb)], [w] * nb, [outp[k] for k in range(nb)],
+                        [idxp[k] for k in range(nb)])
+    gp = fd4.Graph(lp, sig, T, M, n, fd4.params(mode=mode, reselect_each_cycle=1, **sched.as_params()), ws=ws)
+    gp.launch()
+    torch.cuda.synchronize()
+    d = (out[:, :, :w] - outp[:, :, :w]).abs()
+    res = {"value": nb * ims[0].npx * M * n / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+           "network_ms_per_cycle": net_ms,
+           "path": "per cycle: the network's prediction on u^k (one launch per layer over the stack), then a "
+                   "one-cycle batched graph with those scales; M cycles",
+           "sigma_agreement_per_cycle": agree,
+           "vs_plain_reselect": {"max_abs": float(d.max()), "mean_abs": float(d.double().mean())}}
+    for g in graphs + [gp]:
+        g.close()
+    return res
+
+
 def learned_variant(args, ims, wl, sig, T, M, n, mode, sched, stream, torch, fd4):
     """The batched filter with the learned selector.  The network (n_bins = the
     workload's scales) is trained here with the library's own kernels on seeded
@@ -769,7 +842,26 @@ def learned_variant(args, ims, wl, sig, T, M, n, mode, sched, stream, torch, fd4
              "max_abs_diff_to_plain_filter": max(float((o[:, :b.w] - b.out[:, :b.w]).abs().max())
                                                  for o, b in zip(outs_l, ims))}
     g.close()
-    return {"value": net_out["value"], "ms_per_step": net_ms,
+    rs = None
+    if same and not args.no_reselect:
+        # a second network for re-selection before every cycle, trained on the
+        # images of every cycle of the plain re-selecting schedule
+        t0 = time.perf_counter()
+        crops, labels = ST.make_training_set(args.sel_crops, sig, mode, kind=kind, cycles=(T, M, n))
+        t_set_rs = time.perf_counter() - t0
+        sel_rs = fd4.Selector()
+        sel_rs.init(2)
+        t0 = time.perf_counter()
+        losses_rs = ST.train(sel_rs, crops, labels, K, epochs=args.sel_epochs, batch=32, lr=2e-3)
+        torch.cuda.synchronize()
+        train_rs = time.perf_counter() - t0
+        del crops, labels
+        rs = learned_reselect(sel_rs, ims, stack, wss, ws, sig, T, M, n, mode, sched, K, stream, torch, fd4, reps)
+        rs["train"] = {"crops": args.sel_crops, "source": kind + ", every cycle of the re-selecting schedule",
+                       "epochs": args.sel_epochs, "steps": len(losses_rs), "loss_first": losses_rs[0],
+                       "loss_last": float(np.mean(losses_rs[-10:])), "set_seconds": t_set_rs,
+                       "train_seconds": train_rs}
+    return {"value": net_out["value"], "ms_per_step": net_ms, "reselect": rs,
             "value_is": "network-only scale selection + the batched filter graph (an approximation of the "
                         "method: see its agreement and its distance from the plain filter and the oracle)",
             "bins": K, "network_only": net_out, "with_fallback": fallback, "_sel": sel,

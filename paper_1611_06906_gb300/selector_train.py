@@ -9,7 +9,9 @@ scale index the plain vesselness selection picks on the whole source image
 (so the labels see the same image-wide Frangi c as inference on full images).
 Sources: "fundus" -- the `batch64_fundus` generator at side 2048 (64 crops
 each); "tree16" -- the full-size workload's 4096^2 trees (256 crops each).
-The seeds (from 900000 on) are disjoint from the benchmark's images.
+The seeds (from 900000 on) are disjoint from the benchmark's images.  A
+network that re-selects the scales before every FED cycle is trained on the
+images of every cycle instead (`cycles`).
 """
 from __future__ import annotations
 
@@ -39,29 +41,42 @@ def source_images(n_sources: int, kind: str = "fundus", seed0: int = 900000, pro
         return pool.map(_render, args)
 
 
-def make_training_set(n_crops: int, sigmas, mode: int, kind: str = "fundus", seed0: int = 900000, device="cuda"):
-    """(crops (n, 256, 256) float32, labels (n, 256, 256) uint8) on the device."""
+def make_training_set(n_crops: int, sigmas, mode: int, kind: str = "fundus", seed0: int = 900000, device="cuda",
+                      cycles=None):
+    """(crops (n, 256, 256) float32, labels (n, 256, 256) uint8) on the device.
+
+    cycles = (T, M, n): the crops come from every cycle of the re-selecting
+    schedule instead of the source images alone: before cycle c the current
+    image u^c is labelled by the plain selection on it, then one FED cycle
+    (T / M, n steps) runs with those scales -- the (u^c, sigma*_c) pairs a
+    network that re-selects before every cycle sees."""
     import torch
     side = SOURCES[kind]
     per = (side // CROP) ** 2
-    n_src = -(-n_crops // per)
+    n_cyc = 1 if cycles is None else int(cycles[1])
+    n_src = -(-n_crops // (per * n_cyc))
     srcs = source_images(n_src, kind, seed0)
     crops = torch.empty((n_crops, CROP, CROP), dtype=torch.float32, device=device)
     labels = torch.empty((n_crops, CROP, CROP), dtype=torch.uint8, device=device)
     prm = fd4.params(mode=mode)
     ws = fd4.workspace(fd4.OP_SELECT_SCALES, side, side, len(sigmas), device)
+    wsf = fd4.workspace(fd4.OP_FILTER, side, side, len(sigmas), device) if cycles is not None else None
     k = 0
     for img in srcs:
         u = fd4.to_device(img, device)
-        idx, _ = fd4.select_scales(u, side, sigmas, prm, ws=ws)
-        for cy in range(0, side, CROP):
-            for cx in range(0, side, CROP):
-                if k == n_crops:
-                    break
-                crops[k] = u[cy:cy + CROP, cx:cx + CROP]
-                labels[k] = idx[cy:cy + CROP, cx:cx + CROP]
-                k += 1
-    return crops, labels
+        for c in range(n_cyc):
+            idx, _ = fd4.select_scales(u, side, sigmas, prm, ws=ws)
+            for cy in range(0, side, CROP):
+                for cx in range(0, side, CROP):
+                    if k == n_crops:
+                        break
+                    crops[k] = u[cy:cy + CROP, cx:cx + CROP]
+                    labels[k] = idx[cy:cy + CROP, cx:cx + CROP]
+                    k += 1
+            if cycles is not None and c + 1 < n_cyc:
+                T, M, n = cycles
+                u, _ = fd4.filter_image(u, side, sigmas, T / M, 1, n, prm, sigma_idx=idx, ws=wsf)
+    return crops[:k], labels[:k]
 
 
 def train(sel: "fd4.Selector", crops, labels, n_bins: int, epochs: int = 1, batch: int = 32, lr: float = 2e-3,
