@@ -296,14 +296,20 @@ template <int R, int MODE, int NS>
 __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTapsN<R, NS> tpn, StripArgs sa)
 {
     constexpr bool SEL = MODE == ST_SELECT, DENSE = MODE != ST_TENSOR;
+    // the pair of the smallest radius (its two scales cover most pixels of a
+    // noisy image) takes the dense column pass of both scales; at R = 8 and 12
+    // the pixel list is faster (measured: 191 / 214 against 251 / 261 us per
+    // 4096^2 launch), at R = 4 the dense pass (193 against 228 us)
+    constexpr bool PAIR = MODE == ST_TENSOR && NS == 2 && R <= 4;
     static_assert(NS == 1 || !DENSE, "scales share a launch in the tensor build only");
     constexpr int NB = ST_CH + 2 * R, SW = st_sw<R>();
     const StripTaps<R> &tp = tpn.t[0];
     extern __shared__ __align__(16) float stsm[];
     // staged rows: two ST_CH x SW buffers; then per scale 3 fields x NB rows x ST_RS
     float *trow = stsm + 2 * ST_CH * SW;
-    __shared__ unsigned short plist[NS][ST_TX * ST_CH];
-    __shared__ int wtot[NS][ST_NT / 32];
+    constexpr int NL = (DENSE || PAIR) ? 1 : NS;  // pixel lists: the sparse column pass only
+    __shared__ unsigned short plist[NL][ST_TX * ST_CH];
+    __shared__ int wtot[NL][ST_NT / 32];
     __shared__ ImgDesc sd[2];
     __shared__ int s_local[2];
     __shared__ SegGeo sg[2];
@@ -454,7 +460,72 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTapsN<R, NS> tpn, 
                 bmax = 0.0f;
             }
         }
-        if (!DENSE && pc.col) {
+        if (PAIR && pc.col) {
+            // dense column pass of both scales of the pair: column lane, rows
+            // 4 warp .. + 3, in packed
+            // pairs of output rows as the selection's dense pass; each output gets
+            // the products in increasing tap order, as the pixel-list pass below
+            float n5[4][5];  // (sx, sy, sxx, sxy, syy) at the pixel's own scale
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (s == 0 && ids[j] >= sa.K_total)
+                    sd[cur].nfield[(size_t)(y0 + warp * 4 + j) * pitch + x0 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int f = 0; f < 5; ++f) n5[j][f] = 0.0f;
+            }
+#pragma unroll
+            for (int ns = 0; ns < NS; ++ns) {
+                bool mine = false;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mine |= ids[j] == s + ns;
+                if (!__any_sync(0xffffffffu, mine)) continue;  // warp-uniform
+                const StripTaps<R> &tq = tpn.t[ns];
+                const float *c0 = trow + ns * 3 * NB * ST_RS + (warp * 4) * ST_RS + lane;  // smoothed along x
+                const float *c1 = c0 + NB * ST_RS;                                         // d/dx
+                const float *c2 = c1 + NB * ST_RS;                                         // d2/dx2
+                float2 ay[2], ayy[2], ax[2], axy[2], axx[2];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) ay[j] = ayy[j] = ax[j] = axy[j] = axx[j] = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int k = 0; k < 2 * R + 4; ++k) {
+                    const float v0 = c0[k * ST_RS], v1 = c1[k * ST_RS], v2 = c2[k * ST_RS];
+                    const float2 x0v = make_float2(v0, v0), x1v = make_float2(v1, v1), x2v = make_float2(v2, v2);
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int q = k - 2 * j;  // tap pair of output rows 2j, 2j + 1
+                        if (q >= 0 && q <= 2 * R + 1) {
+                            ay[j] = __ffma2_rn(tq.p1[q], x0v, ay[j]);
+                            ayy[j] = __ffma2_rn(tq.p2[q], x0v, ayy[j]);
+                            ax[j] = __ffma2_rn(tq.p0[q], x1v, ax[j]);
+                            axy[j] = __ffma2_rn(tq.p1[q], x1v, axy[j]);
+                            axx[j] = __ffma2_rn(tq.p0[q], x2v, axx[j]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (ids[j] != s + ns) continue;
+                    const int jp = j >> 1;
+                    const bool hi = j & 1;
+                    n5[j][0] = hi ? ax[jp].y : ax[jp].x;
+                    n5[j][1] = hi ? ay[jp].y : ay[jp].x;
+                    n5[j][2] = hi ? axx[jp].y : axx[jp].x;
+                    n5[j][3] = hi ? axy[jp].y : axy[jp].x;
+                    n5[j][4] = hi ? ayy[jp].y : ayy[jp].x;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (ids[j] < s || ids[j] >= s + NS) continue;  // (ids is -1 outside the image)
+                const float sx = n5[j][0], sy = n5[j][1];
+                const float g2 = fmaf(sx, sx, sy * sy);
+                const float g = sa.grad_sq ? g2 : sqrtf(g2);
+                const float f = 1.0f / sqrtf(1.0f + g);
+                sd[cur].nfield[(size_t)(y0 + warp * 4 + j) * pitch + x0 + lane] =
+                    make_float4(f * n5[j][2], f * n5[j][3], f * n5[j][4], 0.0f);
+            }
+        }
+        if constexpr (!DENSE && !PAIR) if (pc.col) {
             // the chunk's pixels of each scale, grouped in plist[ns]
             unsigned m[NS][4];
             int cnt[NS];

@@ -237,6 +237,30 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     assert float(conf[:, :140].min()) > 0.0
 
 
+def test_training_set_from_every_cycle():
+    """The re-selection network's training set: before cycle c the crops are
+    the current image u^c and the plain selection on it; u^{c+1} is one FED
+    cycle of T / M with those scales."""
+    import torch
+    from paper_1611_06906_gb300 import selector_train as ST
+    sig = [1.0, 2.0, 4.0]
+    M, n = 2, 8
+    T = M * n * (n + 1) * 0.05 / 3  # the largest stable time for n steps (tau_max 0.05)
+    crops, labels = ST.make_training_set(128, sig, fd4.VALLEY, kind="fundus", cycles=(T, M, n))
+    assert crops.shape[0] == 128  # one 2048^2 source, 64 crops per cycle
+    src = fd4.to_device(synth.fundus_like(900000, 2048))
+    prm = fd4.params(mode=fd4.VALLEY)
+    idx0, _ = fd4.select_scales(src, 2048, sig, prm)
+    u1, _ = fd4.filter_image(src, 2048, sig, T / M, 1, n, prm, sigma_idx=idx0)
+    idx1, _ = fd4.select_scales(u1, 2048, sig, prm)
+    for k, (u, ix) in enumerate(((src, idx0), (u1, idx1))):
+        for j in (0, 9, 63):
+            cy, cx = (j // 8) * 256, (j % 8) * 256
+            assert torch.equal(crops[64 * k + j], u[cy:cy + 256, cx:cx + 256])
+            assert torch.equal(labels[64 * k + j], ix[cy:cy + 256, cx:cx + 256])
+    assert not torch.equal(crops[0], crops[64])  # the cycle changed the image
+
+
 def test_trained_network_carries_the_scale_information():
     """What training gains: trained as the benchmark trains it (10,000 seeded
     256^2 crops of 4096^2 trees of the full-size workload's kind, 12 scales,
