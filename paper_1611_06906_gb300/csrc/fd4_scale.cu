@@ -332,21 +332,23 @@ __device__ __forceinline__ float pm_mu(float nu, float inv_lambda, int mode)
 // closed-form eigen-decomposition of N_rho and the Perona-Malik diffusivities
 // -> (cos 2t, sin 2t, mu1, mu2), e1 for nu1 >= nu2.  The G_rho radius r is a
 // template parameter (r = ceil(4 rho) <= 8).
-constexpr int FX = 32, FY = 64, FNT_T = 256;
+// Each 32 x 64 tile is finished as two halves of FH = 32 rows (the smaller
+// staging buffers let three blocks share an SM).
+constexpr int FX = 32, FY = 64, FH = 32, FNT_T = 256;
 
 template <int r>
 constexpr size_t finish_smem_bytes()
 {
-    return sizeof(float4) * ((size_t)2 * (FY + 2 * r) * (FX + 2 * r) + (size_t)(FY + 2 * r) * FX);
+    return sizeof(float4) * ((size_t)2 * (FH + 2 * r) * (FX + 2 * r) + (size_t)(FH + 2 * r) * FX);
 }
 
-// cp.async (16 bytes = one pixel of N) of a tile's N region with its mirrored halo.
+// cp.async (16 bytes = one pixel of N) of a half tile's N region with its mirrored halo.
 template <int r>
 __device__ __forceinline__ void finish_stage(const ImgDesc &d, int2 o, float4 *dst)
 {
-    constexpr int ROWS = FY + 2 * r, COLS = FX + 2 * r;
+    constexpr int ROWS = FH + 2 * r, COLS = FX + 2 * r;
     const int w = d.w, h = d.h, pitch = d.pitch, x0 = o.x, y0 = o.y;
-    if (x0 >= r && y0 >= r && x0 + FX + r <= w && y0 + FY + r <= h) {  // no mirrored index
+    if (x0 >= r && y0 >= r && x0 + FX + r <= w && y0 + FH + r <= h) {  // no mirrored index
         const float4 *base = d.nfield + (size_t)(y0 - r) * pitch + (x0 - r);
         for (int i = threadIdx.x; i < ROWS * COLS; i += FNT_T) {
             const int ry = i / COLS, rx = i - ry * COLS;
@@ -368,20 +370,20 @@ __device__ __forceinline__ void finish_stage(const ImgDesc &d, int2 o, float4 *d
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// The origin of a finish tile, computed once by the thread that looks it up.
-__device__ __forceinline__ int2 finish_origin(const ImgDesc &d, int local)
+// The origin of half hf of a finish tile, computed once by the thread that looks it up.
+__device__ __forceinline__ int2 finish_origin(const ImgDesc &d, int local, int hf)
 {
     const int tiles_x = (d.w + FX - 1) / FX;
     const int ty = local / tiles_x;
-    return make_int2((local - ty * tiles_x) * FX, ty * FY);
+    return make_int2((local - ty * tiles_x) * FX, ty * FY + hf * FH);
 }
 
-// The next tile's region is copied (cp.async, double buffer) while the current
-// tile is smoothed and decomposed.
+// The next half tile's region is copied (cp.async, double buffer) while the
+// current one is smoothed and decomposed.  Work unit u = half u % 2 of tile u / 2.
 template <int r>
 __global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, float lambda, int mode)
 {
-    constexpr int ROWS = FY + 2 * r, COLS = FX + 2 * r;
+    constexpr int ROWS = FH + 2 * r, COLS = FX + 2 * r;
     extern __shared__ __align__(16) float4 fsm4[];
     // two ROWS x COLS buffers: N with the mirrored halo; then ROWS x FX: smoothed along x
     float4 *srow = fsm4 + 2 * ROWS * COLS;
@@ -394,84 +396,88 @@ __global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, f
 #pragma unroll
     for (int k = 0; k <= 2 * r; ++k) wr[k] = taps.w0[k];
     const float inv_lambda = 1.0f / lambda;
-    const int ntiles = tile_count(I, SHAPE_SWEEP);
-    int t = blockIdx.x, cur = 0;
-    if (t >= ntiles) return;
+    const int nunits = 2 * tile_count(I, SHAPE_SWEEP);
+    int u = blockIdx.x, cur = 0;
+    if (u >= nunits) return;
     if (tid == 0) {
         tc_reset(tcache);
-        find_tile_cached(I, SHAPE_SWEEP, t, tcache, sdb[0], s_localb[0]);
-        sorg[0] = finish_origin(sdb[0], s_localb[0]);
+        find_tile_cached(I, SHAPE_SWEEP, u >> 1, tcache, sdb[0], s_localb[0]);
+        sorg[0] = finish_origin(sdb[0], s_localb[0], u & 1);
     }
     __syncthreads();
     finish_stage<r>(sdb[0], sorg[0], fsm4);
-    for (; t < ntiles; t += gridDim.x) {
-        const int tn = t + gridDim.x;
-        __syncthreads();  // every thread is done with the previous tile (its slot and buffer)
-        if (tid == 0 && tn < ntiles) {
-            find_tile_cached(I, SHAPE_SWEEP, tn, tcache, sdb[cur ^ 1], s_localb[cur ^ 1]);
-            sorg[cur ^ 1] = finish_origin(sdb[cur ^ 1], s_localb[cur ^ 1]);
+    for (; u < nunits; u += gridDim.x) {
+        const int un = u + gridDim.x;
+        __syncthreads();  // every thread is done with the previous unit (its slot and buffer)
+        if (tid == 0 && un < nunits) {
+            find_tile_cached(I, SHAPE_SWEEP, un >> 1, tcache, sdb[cur ^ 1], s_localb[cur ^ 1]);
+            sorg[cur ^ 1] = finish_origin(sdb[cur ^ 1], s_localb[cur ^ 1], un & 1);
         }
         __syncthreads();
-        if (tn < ntiles) finish_stage<r>(sdb[cur ^ 1], sorg[cur ^ 1], fsm4 + (cur ^ 1) * ROWS * COLS);
+        if (un < nunits) finish_stage<r>(sdb[cur ^ 1], sorg[cur ^ 1], fsm4 + (cur ^ 1) * ROWS * COLS);
         else asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 1;" ::: "memory");
-        __syncthreads();  // this tile's region has landed
+        __syncthreads();  // this unit's region has landed
         const ImgDesc &sd = sdb[cur];
         const float4 *sin_ = fsm4 + cur * ROWS * COLS;
         const int w = sd.w, h = sd.h, pitch = sd.pitch;
         const int x0 = sorg[cur].x, y0 = sorg[cur].y;
-        for (int i = tid; i < ROWS * FX; i += FNT_T) {
-            const int ry = i / FX, rx = i - ry * FX;
-            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (y0 < h) {  // (the lower half of a tile on the last rows may lie below the image)
+            for (int i = tid; i < ROWS * FX; i += FNT_T) {
+                const int ry = i / FX, rx = i - ry * FX;
+                float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k <= 2 * r; ++k) {
-                const float4 v = sin_[ry * COLS + rx + k];
-                a.x = fmaf(wr[k], v.x, a.x);
-                a.y = fmaf(wr[k], v.y, a.y);
-                a.z = fmaf(wr[k], v.z, a.z);
+                for (int k = 0; k <= 2 * r; ++k) {
+                    const float4 v = sin_[ry * COLS + rx + k];
+                    a.x = fmaf(wr[k], v.x, a.x);
+                    a.y = fmaf(wr[k], v.y, a.y);
+                    a.z = fmaf(wr[k], v.z, a.z);
+                }
+                srow[i] = a;
             }
-            srow[i] = a;
         }
         __syncthreads();
-        // column pass: thread = column tid % 32, rows 8 (tid / 32) .. + 7
-        const int tx = tid & (FX - 1), ty0 = (tid >> 5) * 8;
-        const int gx = x0 + tx;
-        float4 win[8 + 2 * r];
+        if (y0 < h) {
+            // column pass: thread = column tid % 32, rows 4 (tid / 32) .. + 3
+            const int tx = tid & (FX - 1), ty0 = (tid >> 5) * 4;
+            const int gx = x0 + tx;
+            float4 win[4 + 2 * r];
 #pragma unroll
-        for (int q = 0; q < 8 + 2 * r; ++q) win[q] = srow[(ty0 + q) * FX + tx];
+            for (int q = 0; q < 4 + 2 * r; ++q) win[q] = srow[(ty0 + q) * FX + tx];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int gy = y0 + ty0 + j;
-            float a = 0.f, b = 0.f, d = 0.f;
+            for (int j = 0; j < 4; ++j) {
+                const int gy = y0 + ty0 + j;
+                float a = 0.f, b = 0.f, d = 0.f;
 #pragma unroll
-            for (int k = 0; k <= 2 * r; ++k) {
-                a = fmaf(wr[k], win[j + k].x, a);
-                b = fmaf(wr[k], win[j + k].y, b);
-                d = fmaf(wr[k], win[j + k].z, d);
+                for (int k = 0; k <= 2 * r; ++k) {
+                    a = fmaf(wr[k], win[j + k].x, a);
+                    b = fmaf(wr[k], win[j + k].y, b);
+                    d = fmaf(wr[k], win[j + k].z, d);
+                }
+                if (gx >= w || gy >= h) continue;
+                const float m = 0.5f * (a + d), q = 0.5f * (a - d);
+                const float rr = hypotf(q, b);
+                const float det = det2_sym(a, b, d);
+                float nu1, nu2;
+                if (m > 0.0f) {
+                    nu1 = m + rr;
+                    nu2 = det / nu1;
+                } else if (m < 0.0f) {
+                    nu2 = m - rr;
+                    nu1 = det / nu2;
+                } else {
+                    nu1 = rr;
+                    nu2 = -rr;
+                }
+                float c2 = 1.0f, s2 = 0.0f;
+                if (rr > 0.0f) {
+                    const float inv_rr = 1.0f / rr;
+                    c2 = q * inv_rr;
+                    s2 = b * inv_rr;
+                }
+                sd.tensor[(size_t)gy * pitch + gx] =
+                    make_float4(c2, s2, pm_mu(nu1, inv_lambda, mode), pm_mu(nu2, inv_lambda, mode));
             }
-            if (gx >= w || gy >= h) continue;
-            const float m = 0.5f * (a + d), q = 0.5f * (a - d);
-            const float rr = hypotf(q, b);
-            const float det = det2_sym(a, b, d);
-            float nu1, nu2;
-            if (m > 0.0f) {
-                nu1 = m + rr;
-                nu2 = det / nu1;
-            } else if (m < 0.0f) {
-                nu2 = m - rr;
-                nu1 = det / nu2;
-            } else {
-                nu1 = rr;
-                nu2 = -rr;
-            }
-            float c2 = 1.0f, s2 = 0.0f;
-            if (rr > 0.0f) {
-                const float inv_rr = 1.0f / rr;
-                c2 = q * inv_rr;
-                s2 = b * inv_rr;
-            }
-            sd.tensor[(size_t)gy * pitch + gx] =
-                make_float4(c2, s2, pm_mu(nu1, inv_lambda, mode), pm_mu(nu2, inv_lambda, mode));
         }
         cur ^= 1;
     }
@@ -493,7 +499,7 @@ int launch_finish(const HostBatch &B, const RhoTaps &rt, const fd4_params &p, cu
     }
     Imgs I = B.I;
     I.tiles = B.tiles[SHAPE_SWEEP];
-    const int grid = persistent_grid((const void *)k_tensor_finish<r>, FNT_T, smem, I.tiles);
+    const int grid = persistent_grid((const void *)k_tensor_finish<r>, FNT_T, smem, 2 * I.tiles);
     k_tensor_finish<r><<<grid, FNT_T, smem, st>>>(I, rt, p.lambda, p.mode);
     return 0;
 }
