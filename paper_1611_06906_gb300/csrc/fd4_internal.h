@@ -95,7 +95,8 @@ struct ImgDesc {
     uint8_t *idx2;       // post-processed scale index before its copy into idx
     float *vmax;         // nullable (set when the scale image is post-processed)
     uint32_t *cmask;     // nullable: per 32 x 32 chunk of the scale image, bit s set where a
-                         // pixel selected scale s (an index outside the set counts as 0)
+                         // pixel selected scale s (an index outside the set counts as 0); then
+                         // per chunk 32 unit masks (chunk_units)
     unsigned *max_s2;    // max S^2 of the image (float bits)
     size_t plane;
     const void *maps;    // batches: this image's TMA tensor maps (u, FED plane, tensor) in device memory
@@ -264,7 +265,16 @@ inline HostBatch single_batch(const ImgDesc &d)
 
 // Chunk masks of the scale image: one word per 32 x 32 chunk, (h/32) rows of (w/32).
 inline size_t cmask_words(int w, int h) { return (size_t)((w + 31) / 32) * (size_t)((h + 31) / 32); }
-inline size_t cmask_bytes(int w, int h) { return align_up(4 * cmask_words(w, h), 256); }
+// Per chunk: the mask word and 32 unit masks (one byte per scale: bit u set
+// where columns 4u .. 4u + 3 of the chunk hold a pixel of the scale).
+inline size_t cmask_bytes(int w, int h) { return align_up(36 * cmask_words(w, h), 256); }
+#ifdef __CUDACC__
+// The unit masks of an image's chunks (after its mask words, counted on w).
+__device__ __forceinline__ uint8_t *chunk_units(const ImgDesc &d)
+{
+    return (uint8_t *)(d.cmask + (size_t)((d.w + 31) / 32) * ((d.h + 31) / 32));
+}
+#endif
 
 // Stage launchers over a batch (fd4_scale.cu, fd4_fed.cu); nonzero on a CUDA error.
 int launch_select_batch(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,

@@ -184,6 +184,45 @@ __device__ __forceinline__ void st_rows2(const StripTaps<R> &tp, const float *ti
     }
 }
 
+// The row pass of st_rows2 with warp w computing columns 4w .. 4w + 3 of every
+// row (lane = row), so that a unit no chunk reads (bit w of units clear) is
+// skipped by its whole warp.  Each output gets the same operations in the
+// same order as in st_rows2.
+template <int R>
+__device__ __forceinline__ void st_rows_units(const StripTaps<R> &tp, const float *tin, float *trow, int b0, int n,
+                                              unsigned units)
+{
+    constexpr int SW = st_sw<R>(), NB = ST_CH + 2 * R;
+    const int r = threadIdx.x & 31, xo = (threadIdx.x >> 5) * 4;
+    if (!((units >> (threadIdx.x >> 5)) & 1u) || r >= n) return;
+    const float *src = tin + r * SW + xo;
+    float2 a0[2], a1[2], a2[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) a0[j] = a1[j] = a2[j] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int m4 = 0; m4 < (2 * R + 4 + 3) / 4; ++m4) {
+        const float4 v = *reinterpret_cast<const float4 *>(src + 4 * m4);
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 x2 = make_float2(vv[e], vv[e]);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int i = 4 * m4 + e - 2 * j;
+                if (i >= 0 && i <= 2 * R + 1) {
+                    a0[j] = __ffma2_rn(tp.p0[i], x2, a0[j]);
+                    a1[j] = __ffma2_rn(tp.p1[i], x2, a1[j]);
+                    a2[j] = __ffma2_rn(tp.p2[i], x2, a2[j]);
+                }
+            }
+        }
+    }
+    float *d = trow + (b0 + r) * ST_RS + xo;
+    *reinterpret_cast<float4 *>(d) = make_float4(a0[0].x, a0[0].y, a0[1].x, a0[1].y);
+    *reinterpret_cast<float4 *>(d + NB * ST_RS) = make_float4(a1[0].x, a1[0].y, a1[1].x, a1[1].y);
+    *reinterpret_cast<float4 *>(d + 2 * NB * ST_RS) = make_float4(a2[0].x, a2[0].y, a2[1].x, a2[1].y);
+}
+
 // Per-launch scalars of the strip kernels.
 struct StripArgs {
     int s;          // scale index in the set
@@ -213,6 +252,9 @@ struct SegGeo {
     int x0, ys;    // first column and row
     int pieces;    // plan length (0: nothing of this segment is needed)
     unsigned char code[kMaxPlan];
+    // per chunk: the 4-column units of the row pass its pieces compute (bit u:
+    // columns 4u .. 4u + 3), the units the chunks that read those rows need
+    unsigned char uni[kSegRows / ST_CH];
 };
 
 // The plan of a segment.  Dense launches (selection, IFOD) and images without
@@ -269,13 +311,23 @@ __device__ __forceinline__ int next_segment(const Imgs &I, const StripArgs &sa, 
         __syncwarp();
         const int nch = (min(g.ys + sa.seg, d.h) - g.ys + ST_CH - 1) / ST_CH;
         unsigned need = nch >= 32 ? 0xffffffffu : (1u << nch) - 1u;
+        unsigned uu = 0xffu;  // lane c: units of chunk c's pieces
         if (!dense && d.cmask) {
             const int cw = (d.w + 31) / 32;
             bool bit = false;
-            if (lane < nch)
-                bit = (d.cmask[(size_t)(g.ys / ST_CH + lane) * cw + g.x0 / ST_TX] >> sa.s) & ((1u << NS) - 1u);
+            unsigned um = 0u;
+            if (lane < nch) {
+                const size_t ch = (size_t)(g.ys / ST_CH + lane) * cw + g.x0 / ST_TX;
+                bit = (d.cmask[ch] >> sa.s) & ((1u << NS) - 1u);
+                const uint8_t *up = chunk_units(d) + ch * FD4_MAX_SIGMAS + sa.s;
+                for (int k = 0; k < NS; ++k) um |= up[k];
+            }
             need = __ballot_sync(0xffffffffu, bit);
+            // the rows of chunk c's pieces are read by chunks c .. c + (NB - 1) / 32
+            uu = um;
+            for (int k = 1; k <= (ST_CH + 2 * R - 1) / ST_CH; ++k) uu |= __shfl_down_sync(0xffffffffu, um, k);
         }
+        if (lane < kSegRows / ST_CH) g.uni[lane] = (unsigned char)uu;
         if (lane == 0) g.pieces = seg_plan<R>(need, nch, g);
         __syncwarp();
         if (g.pieces > 0) break;
@@ -389,8 +441,16 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTapsN<R, NS> tpn, 
             __syncthreads();
         }
 #pragma unroll
-        for (int ns = 0; ns < NS; ++ns)
-            st_rows2<R>(tpn.t[ns], stsm + buf * ST_CH * SW, trow + ns * 3 * NB * ST_RS, pc.b0, pc.n);
+        for (int ns = 0; ns < NS; ++ns) {
+            // single-scale launches (R >= 16 here) compute only the units their
+            // chunks read (the pairs' units are nearly all read: the row-per-thread
+            // mapping measured faster there)
+            if constexpr (!DENSE && !PAIR && NS == 1)
+                st_rows_units<R>(tpn.t[ns], stsm + buf * ST_CH * SW, trow + ns * 3 * NB * ST_RS, pc.b0, pc.n,
+                                 sg[cur].uni[pc.chunk]);
+            else
+                st_rows2<R>(tpn.t[ns], stsm + buf * ST_CH * SW, trow + ns * 3 * NB * ST_RS, pc.b0, pc.n);
+        }
         __syncthreads();
 
         if (DENSE && pc.col) {
@@ -614,13 +674,17 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTapsN<R, NS> tpn, 
 
 // Chunk masks of the scale image for the tensor build: for each 32 x 32 chunk,
 // bit s set where one of its pixels selected scale s; an index outside the set
-// sets bit 0 (the scale-0 launch zeroes N there).  32 x 64 tiles (two chunks),
-// 256 threads: lane = column, warp w = rows 8w .. 8w + 7 of the tile.
+// sets bit 0 (the scale-0 launch zeroes N there).  Then per chunk and scale
+// the unit mask: bit u set where columns 4u .. 4u + 3 hold a pixel of the
+// scale (the strips compute the row pass only for the units some chunk reads).
+// 32 x 64 tiles (two chunks), 256 threads: lane = column, warp w = rows
+// 8w .. 8w + 7 of the tile.
 __global__ void __launch_bounds__(256) k_chunk_masks(Imgs I, int K)
 {
     __shared__ ImgDesc sd;
     __shared__ int s_local;
     __shared__ unsigned sm[2];
+    __shared__ unsigned su[2][FD4_MAX_SIGMAS];
     __shared__ TileCache tcache;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) tc_reset(tcache);
@@ -630,12 +694,13 @@ __global__ void __launch_bounds__(256) k_chunk_masks(Imgs I, int K)
             find_tile_cached(I, SHAPE_SWEEP, t, tcache, sd, s_local);
             sm[0] = sm[1] = 0u;
         }
+        if (tid < 2 * FD4_MAX_SIGMAS) su[tid / FD4_MAX_SIGMAS][tid % FD4_MAX_SIGMAS] = 0u;
         __syncthreads();
         const int w = sd.w, h = sd.h, pitch = sd.pitch;
         const int cw = (w + 31) / 32;
         const int x0 = (s_local % cw) * 32, y0 = (s_local / cw) * 64;
         const int x = x0 + lane;
-        unsigned m = 0u;
+        unsigned m = 0u, mk = 0u;  // all indices; the valid ones (for the unit masks)
         if (x < w) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -643,13 +708,30 @@ __global__ void __launch_bounds__(256) k_chunk_masks(Imgs I, int K)
                 if (y < h) {
                     const int v = sd.idx[(size_t)y * pitch + x];
                     m |= v < K ? 1u << v : 1u;
+                    if (v < K) mk |= 1u << v;
                 }
             }
         }
-        m = __reduce_or_sync(0xffffffffu, m);
-        if (lane == 0) atomicOr(&sm[warp >> 2], m);
+        const unsigned wm = __reduce_or_sync(0xffffffffu, m);
+        if (lane == 0) atomicOr(&sm[warp >> 2], wm);
+        // unit masks of the scales this warp's rows hold
+        for (int sc = 0; sc < K; ++sc) {
+            if (!((wm >> sc) & 1u)) continue;  // warp-uniform
+            unsigned b = __ballot_sync(0xffffffffu, (mk >> sc) & 1u);
+            b |= b >> 1;
+            b |= b >> 2;  // bit 4u: columns 4u .. 4u + 3
+            unsigned u8 = 0u;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) u8 |= ((b >> (4 * u)) & 1u) << u;
+            if (lane == 0) atomicOr(&su[warp >> 2][sc], u8);
+        }
         __syncthreads();
         if (tid < 2 && y0 + 32 * tid < h) sd.cmask[(size_t)(y0 / 32 + tid) * cw + x0 / 32] = sm[tid];
+        if (tid < 2 * K) {
+            const int c = tid / K, sc = tid - (tid / K) * K;
+            if (y0 + 32 * c < h)
+                chunk_units(sd)[((size_t)(y0 / 32 + c) * cw + x0 / 32) * FD4_MAX_SIGMAS + sc] = (uint8_t)su[c][sc];
+        }
     }
 }
 
