@@ -684,7 +684,7 @@ __global__ void __launch_bounds__(256) k_chunk_masks(Imgs I, int K)
     __shared__ ImgDesc sd;
     __shared__ int s_local;
     __shared__ unsigned sm[2];
-    __shared__ unsigned su[2][FD4_MAX_SIGMAS];
+    __shared__ unsigned su[2][8];  // per chunk and 4-column unit: the scales it holds
     __shared__ TileCache tcache;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) tc_reset(tcache);
@@ -694,7 +694,7 @@ __global__ void __launch_bounds__(256) k_chunk_masks(Imgs I, int K)
             find_tile_cached(I, SHAPE_SWEEP, t, tcache, sd, s_local);
             sm[0] = sm[1] = 0u;
         }
-        if (tid < 2 * FD4_MAX_SIGMAS) su[tid / FD4_MAX_SIGMAS][tid % FD4_MAX_SIGMAS] = 0u;
+        if (tid < 16) su[tid >> 3][tid & 7] = 0u;
         __syncthreads();
         const int w = sd.w, h = sd.h, pitch = sd.pitch;
         const int cw = (w + 31) / 32;
@@ -714,23 +714,19 @@ __global__ void __launch_bounds__(256) k_chunk_masks(Imgs I, int K)
         }
         const unsigned wm = __reduce_or_sync(0xffffffffu, m);
         if (lane == 0) atomicOr(&sm[warp >> 2], wm);
-        // unit masks of the scales this warp's rows hold
-        for (int sc = 0; sc < K; ++sc) {
-            if (!((wm >> sc) & 1u)) continue;  // warp-uniform
-            unsigned b = __ballot_sync(0xffffffffu, (mk >> sc) & 1u);
-            b |= b >> 1;
-            b |= b >> 2;  // bit 4u: columns 4u .. 4u + 3
-            unsigned u8 = 0u;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) u8 |= ((b >> (4 * u)) & 1u) << u;
-            if (lane == 0) atomicOr(&su[warp >> 2][sc], u8);
-        }
+        // the scales of each 4-column unit (lanes 4u .. 4u + 3)
+        mk |= __shfl_xor_sync(0xffffffffu, mk, 1);
+        mk |= __shfl_xor_sync(0xffffffffu, mk, 2);
+        if ((lane & 3) == 0 && mk) atomicOr(&su[warp >> 2][lane >> 2], mk);
         __syncthreads();
         if (tid < 2 && y0 + 32 * tid < h) sd.cmask[(size_t)(y0 / 32 + tid) * cw + x0 / 32] = sm[tid];
-        if (tid < 2 * K) {
+        if (tid < 2 * K) {  // unit mask of scale sc: bit u where unit u holds it
             const int c = tid / K, sc = tid - (tid / K) * K;
+            unsigned u8 = 0u;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) u8 |= ((su[c][u] >> sc) & 1u) << u;
             if (y0 + 32 * c < h)
-                chunk_units(sd)[((size_t)(y0 / 32 + c) * cw + x0 / 32) * FD4_MAX_SIGMAS + sc] = (uint8_t)su[c][sc];
+                chunk_units(sd)[((size_t)(y0 / 32 + c) * cw + x0 / 32) * FD4_MAX_SIGMAS + sc] = (uint8_t)u8;
         }
     }
 }
