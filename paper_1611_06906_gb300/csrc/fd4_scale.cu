@@ -324,7 +324,7 @@ __device__ __forceinline__ float pm_mu(float nu, float inv_lambda, int mode)
 {
     if ((mode == FD4_RIDGE && nu >= 0.0f) || (mode == FD4_VALLEY && nu <= 0.0f)) return 1.0f;
     const float q = nu * inv_lambda;
-    return 1.0f / fmaf(q, q, 1.0f);
+    return __fdividef(1.0f, fmaf(q, q, 1.0f));  // divisor >= 1: the fast reciprocal is within 2 ulp
 }
 
 // Tensor finish on 32 x 64 tiles (SHAPE_SWEEP), 256 threads: N_rho = G_rho * N
@@ -335,25 +335,31 @@ __device__ __forceinline__ float pm_mu(float nu, float inv_lambda, int mode)
 // Each 32 x 64 tile is finished as two halves of FH = 32 rows (the smaller
 // staging buffers let three blocks share an SM).
 constexpr int FX = 32, FY = 64, FH = 32, FNT_T = 256;
+// Row strides of the staged region and of the row-smoothed rows, in float4
+// pixels: odd, so that the 16-byte accesses of eight threads on eight
+// consecutive rows of one column fall in eight distinct bank groups.
+template <int r>
+constexpr int finish_cp() { return FX + 2 * r + 1; }
+constexpr int FSR = FX + 1;
 
 template <int r>
 constexpr size_t finish_smem_bytes()
 {
-    return sizeof(float4) * ((size_t)2 * (FH + 2 * r) * (FX + 2 * r) + (size_t)(FH + 2 * r) * FX);
+    return sizeof(float4) * ((size_t)2 * (FH + 2 * r) * finish_cp<r>() + (size_t)(FH + 2 * r) * FSR);
 }
 
 // cp.async (16 bytes = one pixel of N) of a half tile's N region with its mirrored halo.
 template <int r>
 __device__ __forceinline__ void finish_stage(const ImgDesc &d, int2 o, float4 *dst)
 {
-    constexpr int ROWS = FH + 2 * r, COLS = FX + 2 * r;
+    constexpr int ROWS = FH + 2 * r, COLS = FX + 2 * r, CP = finish_cp<r>();
     const int w = d.w, h = d.h, pitch = d.pitch, x0 = o.x, y0 = o.y;
     if (x0 >= r && y0 >= r && x0 + FX + r <= w && y0 + FH + r <= h) {  // no mirrored index
         const float4 *base = d.nfield + (size_t)(y0 - r) * pitch + (x0 - r);
         for (int i = threadIdx.x; i < ROWS * COLS; i += FNT_T) {
             const int ry = i / COLS, rx = i - ry * COLS;
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                             (unsigned)__cvta_generic_to_shared(dst + i)),
+                             (unsigned)__cvta_generic_to_shared(dst + ry * CP + rx)),
                          "l"(base + (size_t)ry * pitch + rx)
                          : "memory");
         }
@@ -362,7 +368,7 @@ __device__ __forceinline__ void finish_stage(const ImgDesc &d, int2 o, float4 *d
             const int ry = i / COLS, rx = i - ry * COLS;
             const float4 *src = d.nfield + (size_t)mirror(y0 - r + ry, h) * pitch + mirror(x0 - r + rx, w);
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                             (unsigned)__cvta_generic_to_shared(dst + i)),
+                             (unsigned)__cvta_generic_to_shared(dst + ry * CP + rx)),
                          "l"(src)
                          : "memory");
         }
@@ -383,10 +389,10 @@ __device__ __forceinline__ int2 finish_origin(const ImgDesc &d, int local, int h
 template <int r>
 __global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, float lambda, int mode)
 {
-    constexpr int ROWS = FH + 2 * r, COLS = FX + 2 * r;
+    constexpr int ROWS = FH + 2 * r, CP = finish_cp<r>();
     extern __shared__ __align__(16) float4 fsm4[];
-    // two ROWS x COLS buffers: N with the mirrored halo; then ROWS x FX: smoothed along x
-    float4 *srow = fsm4 + 2 * ROWS * COLS;
+    // two ROWS x CP buffers: N with the mirrored halo; then ROWS x FSR: smoothed along x
+    float4 *srow = fsm4 + 2 * ROWS * CP;
     __shared__ ImgDesc sdb[2];
     __shared__ int s_localb[2];
     __shared__ int2 sorg[2];
@@ -414,26 +420,38 @@ __global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, f
             sorg[cur ^ 1] = finish_origin(sdb[cur ^ 1], s_localb[cur ^ 1], un & 1);
         }
         __syncthreads();
-        if (un < nunits) finish_stage<r>(sdb[cur ^ 1], sorg[cur ^ 1], fsm4 + (cur ^ 1) * ROWS * COLS);
+        if (un < nunits) finish_stage<r>(sdb[cur ^ 1], sorg[cur ^ 1], fsm4 + (cur ^ 1) * ROWS * CP);
         else asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 1;" ::: "memory");
         __syncthreads();  // this unit's region has landed
         const ImgDesc &sd = sdb[cur];
-        const float4 *sin_ = fsm4 + cur * ROWS * COLS;
+        const float4 *sin_ = fsm4 + cur * ROWS * CP;
         const int w = sd.w, h = sd.h, pitch = sd.pitch;
         const int x0 = sorg[cur].x, y0 = sorg[cur].y;
         if (y0 < h) {  // (the lower half of a tile on the last rows may lie below the image)
-            for (int i = tid; i < ROWS * FX; i += FNT_T) {
-                const int ry = i / FX, rx = i - ry * FX;
-                float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+            // row pass: task e = row e % ROWS, columns 4 (e / ROWS) .. + 3 (one
+            // read of the 4 + 2r pixels they share); consecutive lanes take
+            // consecutive rows of one column group
+            for (int e = tid; e < ROWS * (FX / 4); e += FNT_T) {
+                const int g = e / ROWS, ry = e - g * ROWS;
+                const float4 *src = sin_ + ry * CP + 4 * g;
+                float3 v[4 + 2 * r];
 #pragma unroll
-                for (int k = 0; k <= 2 * r; ++k) {
-                    const float4 v = sin_[ry * COLS + rx + k];
-                    a.x = fmaf(wr[k], v.x, a.x);
-                    a.y = fmaf(wr[k], v.y, a.y);
-                    a.z = fmaf(wr[k], v.z, a.z);
+                for (int k = 0; k < 4 + 2 * r; ++k) {
+                    const float4 t4 = src[k];
+                    v[k] = make_float3(t4.x, t4.y, t4.z);
                 }
-                srow[i] = a;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k <= 2 * r; ++k) {
+                        a.x = fmaf(wr[k], v[j + k].x, a.x);
+                        a.y = fmaf(wr[k], v[j + k].y, a.y);
+                        a.z = fmaf(wr[k], v[j + k].z, a.z);
+                    }
+                    srow[ry * FSR + 4 * g + j] = a;
+                }
             }
         }
         __syncthreads();
@@ -443,7 +461,7 @@ __global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, f
             const int gx = x0 + tx;
             float4 win[4 + 2 * r];
 #pragma unroll
-            for (int q = 0; q < 4 + 2 * r; ++q) win[q] = srow[(ty0 + q) * FX + tx];
+            for (int q = 0; q < 4 + 2 * r; ++q) win[q] = srow[(ty0 + q) * FSR + tx];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int gy = y0 + ty0 + j;
@@ -456,24 +474,37 @@ __global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, f
                 }
                 if (gx >= w || gy >= h) continue;
                 const float m = 0.5f * (a + d), q = 0.5f * (a - d);
-                const float rr = hypotf(q, b);
                 const float det = det2_sym(a, b, d);
+                // rr = |(q, b)| and the rotation (cos 2t, sin 2t) = (q, b) / rr: by
+                // the fast reciprocal square root (within 2 ulp) where rr^2 is a
+                // normal number far from overflow, else by hypot and division
+                const float rr2 = fmaf(q, q, b * b);
+                float rr, c2 = 1.0f, s2 = 0.0f;
+                if (rr2 > 1e-30f && rr2 < 1e30f) {
+                    const float inv_rr = rsqrtf(rr2);
+                    rr = rr2 * inv_rr;
+                    c2 = q * inv_rr;
+                    s2 = b * inv_rr;
+                } else {
+                    rr = hypotf(q, b);
+                    if (rr > 0.0f) {
+                        const float inv_rr = 1.0f / rr;
+                        c2 = q * inv_rr;
+                        s2 = b * inv_rr;
+                    }
+                }
+                // the eigenvalue of smaller magnitude as det / (the larger one):
+                // a fast division unless the divisor is tiny
                 float nu1, nu2;
                 if (m > 0.0f) {
                     nu1 = m + rr;
-                    nu2 = det / nu1;
+                    nu2 = nu1 > 1e-30f ? __fdividef(det, nu1) : det / nu1;
                 } else if (m < 0.0f) {
                     nu2 = m - rr;
-                    nu1 = det / nu2;
+                    nu1 = nu2 < -1e-30f ? __fdividef(det, nu2) : det / nu2;
                 } else {
                     nu1 = rr;
                     nu2 = -rr;
-                }
-                float c2 = 1.0f, s2 = 0.0f;
-                if (rr > 0.0f) {
-                    const float inv_rr = 1.0f / rr;
-                    c2 = q * inv_rr;
-                    s2 = b * inv_rr;
                 }
                 sd.tensor[(size_t)gy * pitch + gx] =
                     make_float4(c2, s2, pm_mu(nu1, inv_lambda, mode), pm_mu(nu2, inv_lambda, mode));
