@@ -293,7 +293,10 @@ size_t fd4_batch_workspace_bytes(const fd4_image *h_imgs, int n_images, int n_si
  * one launch per stage covering all images: each stage kernel walks a flat
  * list of tiles spanning the batch.  Results are those of fd4_filter on each
  * image separately (identical arithmetic per pixel).  Errors as fd4_filter;
- * every image is validated before anything is enqueued.                      */
+ * every image is validated before anything is enqueued.  Without re-selection,
+ * a cycle whose FED steps end in the workspace's FED plane leaves the current
+ * image there and the next cycle starts from it, so d_out holds the result
+ * once the stream has passed the call, not between cycles.                  */
 int fd4_filter_batched(const fd4_image *h_imgs, int n_images, const float *h_sigmas, int n_sigma,
                        const fd4_params *params, double T, int M, int n_in, int sigma_given,
                        void *d_ws, size_t ws_bytes, fd4_stream_t stream);
@@ -348,8 +351,9 @@ typedef struct fd4_fed_schedule {
  * with each of the FD4_AUTOTUNE_CANDIDATES schedules -- 1 and 3 steps per
  * launch, and 2 and 4 steps per launch on regions of 64 or 32 rows with 1 or
  * 2 quads per thread (the halo depth is 2 pixels per step) -- with CUDA
- * events on `stream` (synchronising it), after one untimed cycle each.
- * *best receives the fastest; tried (nullable, FD4_AUTOTUNE_CANDIDATES
+ * events on `stream` (synchronising it), after one untimed cycle each; a
+ * cycle is timed as the batched filter runs it, without a copy of the result
+ * back into d_out.  *best receives the fastest; tried (nullable, FD4_AUTOTUNE_CANDIDATES
  * entries) every candidate with its time.  The schedule is copied into a
  * fd4_params by the caller.  The images' d_out buffers are overwritten.     */
 int fd4_autotune_batched(const fd4_image *h_imgs, int n_images, const float *h_sigmas, int n_sigma,

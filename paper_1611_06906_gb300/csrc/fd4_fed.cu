@@ -377,8 +377,17 @@ FedSched resolve_sched(const fd4_params &p)
     return s;
 }
 
+int launch_copy_back_batch(const HostBatch &B, cudaStream_t st)
+{
+    Imgs I = B.I;
+    I.tiles = B.tiles[SHAPE_SMALL];
+    const int grid = persistent_grid((const void *)k_copy_back, 256, 0, I.tiles);
+    k_copy_back<<<grid, 256, 0, st>>>(I);
+    return cudaGetLastError() != cudaSuccess;
+}
+
 int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundary, const FedSched &sch,
-                     cudaStream_t st)
+                     cudaStream_t st, int *end_parity)
 {
     const int periodic = boundary == FD4_BC_PERIODIC;
     int S = sch.steps;
@@ -411,12 +420,8 @@ int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundar
             parity ^= 1;
         }
     }
-    if (parity) {  // the last launch wrote the ping-pong plane
-        Imgs I = B.I;
-        I.tiles = B.tiles[SHAPE_SMALL];
-        const int grid = persistent_grid((const void *)k_copy_back, 256, 0, I.tiles);
-        k_copy_back<<<grid, 256, 0, st>>>(I);
-    }
+    if (end_parity) *end_parity = parity;
+    else if (parity && launch_copy_back_batch(B, st)) return 1;  // the last launch wrote the ping-pong plane
     return cudaGetLastError() != cudaSuccess;
 }
 

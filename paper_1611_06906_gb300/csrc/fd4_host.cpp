@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "fd4_internal.h"
@@ -472,14 +473,29 @@ static int enqueue_filter(const HostBatch &B, const float *h_sigmas, int n_sigma
                       (stages & FD4_STAGE_COPY);
     if (post && launch_postprocess_batch(B, h_sigmas, n_sigma, p, st)) return FD4_ERR_CUDA;
     const bool reselect = mafod && p.reselect_each_cycle && !sigma_given && (stages & FD4_STAGE_SELECT);
+    // A FED cycle of an odd number of launches ends in the FED plane.  Where
+    // the batch has the table with u and that plane exchanged, the next cycle
+    // runs on it (its tensor build reads the plane, its FED steps end in u), and
+    // the result is copied back at most once, after the last cycle.  Without
+    // re-selection the scale image, and with it the chunk masks, stay those of
+    // the first cycle.
+    const bool alternate = B.table_sw != nullptr && !reselect;
+    int view = 0;  // 1: the current image lies in the FED plane
     for (int k = 0; k < M; ++k) {
         if (k > 0 && reselect && launch_select_batch(current_view(B), h_sigmas, n_sigma, p, st))
             return FD4_ERR_CUDA;
         if (k > 0 && reselect && post && launch_postprocess_batch(B, h_sigmas, n_sigma, p, st))
             return FD4_ERR_CUDA;
-        if ((stages & FD4_STAGE_TENSOR) && launch_cycle_tensor(B, h_sigmas, n_sigma, p, st)) return FD4_ERR_CUDA;
-        if ((stages & FD4_STAGE_FED) && launch_fed_batch(B, tau, n, p.boundary, sch, st)) return FD4_ERR_CUDA;
+        HostBatch V = B;
+        if (view) V.I.table = B.table_sw;
+        V.cmask_fresh = k > 0 && !reselect;
+        if ((stages & FD4_STAGE_TENSOR) && launch_cycle_tensor(V, h_sigmas, n_sigma, p, st)) return FD4_ERR_CUDA;
+        int end = 0;
+        if ((stages & FD4_STAGE_FED) && launch_fed_batch(V, tau, n, p.boundary, sch, st, alternate ? &end : nullptr))
+            return FD4_ERR_CUDA;
+        view ^= end;
     }
+    if (view && launch_copy_back_batch(B, st)) return FD4_ERR_CUDA;
     return FD4_OK;
 }
 
@@ -543,10 +559,14 @@ extern "C" int fd4_filter(const float *d_in, float *d_out, int w, int h, int pit
 // Batches.  Workspace: [descriptor table | max S^2 words | per image:
 // sigma* plane, tensor plane, scratch (selection planes / N field / FED plane)].
 
+// Scratch of one image: the selection planes (vp, s2) over the whole of it; the
+// N field at its start and the FED plane right after the N field, so that the
+// current image may lie in the FED plane while a tensor build writes N.
 static size_t scratch_bytes(int h, int pitch, int n_sigma)
 {
     size_t sc = 2 * (size_t)n_sigma * plane_bytes(h, pitch, 4);
-    if (plane_bytes(h, pitch, 16) > sc) sc = plane_bytes(h, pitch, 16);
+    const size_t nt = plane_bytes(h, pitch, 16) + plane_bytes(h, pitch, 4);
+    if (nt > sc) sc = nt;
     return sc;
 }
 
@@ -558,9 +578,13 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
     size_t off = align_up(sizeof(ImgDesc) * (size_t)n, 256);
     const size_t tu_off = off;  // the same descriptors with in = u (re-selection)
     off += align_up(sizeof(ImgDesc) * (size_t)n, 256);
+    const size_t tsw_off = off;  // the descriptors with u and tmp exchanged (odd cycles)
+    off += align_up(sizeof(ImgDesc) * (size_t)n, 256);
     const size_t ms_off = off;
     off += align_up(sizeof(unsigned) * (size_t)n, 256);
     const size_t maps_off = off;  // TMA tensor maps of the FED kernel, one set per image
+    off += align_up(tma_maps_bytes() * (size_t)n, 256);
+    // then the same maps with u and tmp exchanged (the exchanged table's)
     off += align_up(tma_maps_bytes() * (size_t)n, 256);
     int t0[kShapes] = {};
     if (descs) descs->resize(n);
@@ -582,7 +606,7 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
         d = ImgDesc{};
         d.in = im.d_in;
         d.u = im.d_out;
-        d.tmp = (float *)(ws + o_sc);
+        d.tmp = (float *)(ws + o_sc + plane_bytes(im.h, im.pitch, 16));
         d.vp = (float *)(ws + o_sc);
         d.s2 = (float *)(ws + o_sc + (size_t)n_sigma * pb);
         d.nfield = (float4 *)(ws + o_sc);
@@ -616,7 +640,9 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
         B->max_s2 = (unsigned *)(ws + ms_off);
         B->n_max_s2 = two ? split : n;
         B->table_u = (const ImgDesc *)(ws + tu_off);
+        B->table_sw = (const ImgDesc *)(ws + tsw_off);
         B->has_cmask = true;
+        B->cmask_fresh = false;
     }
     if (B1 && two) {
         *B1 = *B;
@@ -626,6 +652,7 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
         B1->max_s2 = (unsigned *)(ws + ms_off) + split;
         B1->n_max_s2 = n - split;
         B1->table_u = (const ImgDesc *)(ws + tu_off) + split;
+        B1->table_sw = (const ImgDesc *)(ws + tsw_off) + split;
     }
     return off;
 }
@@ -680,9 +707,10 @@ static int batch_prepare(const fd4_image *imgs, int n_images, const float *h_sig
 
 // The device tables of a batch: the descriptors, the FED kernel's tensor maps
 // and, when the filter re-selects on the current image, the descriptors with
-// in = u (B.table_u).
+// in = u (B.table_u); otherwise the descriptors with u and the FED plane
+// exchanged (B.table_sw) with their own maps, which follow the batch's maps.
 static int put_tables(const std::vector<ImgDesc> &descs, int n, const HostBatch &B, void *d_ws, bool with_u,
-                      cudaStream_t st)
+                      bool with_sw, cudaStream_t st)
 {
     if (launch_put_descs(descs.data(), n, (ImgDesc *)d_ws, st)) return 1;
     if (n > 0 && launch_put_maps(descs.data(), n, (void *)descs[0].maps, st)) return 1;
@@ -690,6 +718,15 @@ static int put_tables(const std::vector<ImgDesc> &descs, int n, const HostBatch 
         std::vector<ImgDesc> du(descs);
         for (ImgDesc &d : du) d.in = d.u;
         if (launch_put_descs(du.data(), n, (ImgDesc *)B.table_u, st)) return 1;
+    } else if (with_sw && n > 0 && B.table_sw) {
+        std::vector<ImgDesc> dw(descs);
+        char *maps_sw = (char *)descs[0].maps + align_up(tma_maps_bytes() * (size_t)n, 256);
+        for (int i = 0; i < n; ++i) {
+            std::swap(dw[i].u, dw[i].tmp);
+            dw[i].maps = maps_sw + tma_maps_bytes() * (size_t)i;
+        }
+        if (launch_put_descs(dw.data(), n, (ImgDesc *)B.table_sw, st)) return 1;
+        if (launch_put_maps(dw.data(), n, (void *)maps_sw, st)) return 1;
     }
     return 0;
 }
@@ -712,7 +749,7 @@ static int enqueue_batch_two_streams(const fd4_image *imgs, int n_images, const 
     const bool post = sel && p.postprocess_scales;
     batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B0, split, &B1, post);
     const bool reselect = sel && p.reselect_each_cycle;
-    if (put_tables(descs, n_images, B0, d_ws, reselect, s0)) return FD4_ERR_CUDA;
+    if (put_tables(descs, n_images, B0, d_ws, reselect, false, s0)) return FD4_ERR_CUDA;
     const FedSched steps = resolve_sched(p);
     if (cudaEventRecord(ev_fork, s0) != cudaSuccess || cudaStreamWaitEvent(s1, ev_fork, 0) != cudaSuccess)
         return FD4_ERR_CUDA;
@@ -758,7 +795,10 @@ static int enqueue_batch(const fd4_image *imgs, int n_images, const float *h_sig
     const bool post = sel && p.postprocess_scales && (stages & FD4_STAGE_COPY);
     batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B, 0, nullptr, post);
     const bool reselect = sel && p.reselect_each_cycle;
-    if (put_tables(descs, n_images, B, d_ws, reselect, st)) return FD4_ERR_CUDA;
+    // the exchanged table serves cycles that end in the FED plane
+    const bool with_sw = !reselect && (stages & FD4_STAGE_FED);
+    if (!with_sw) B.table_sw = nullptr;
+    if (put_tables(descs, n_images, B, d_ws, reselect, with_sw, st)) return FD4_ERR_CUDA;
     return enqueue_filter(B, h_sigmas, n_sigma, p, tau, n, M, sigma_given, st, stages);
 }
 
@@ -910,9 +950,11 @@ extern "C" int fd4_autotune_batched(const fd4_image *h_imgs, int n_images, const
     for (int c = 0; c < FD4_AUTOTUNE_CANDIDATES && rc == FD4_OK; ++c) {
         const FedSched sch{cand[c][0], cand[c][1] ? cand[c][1] : kDefaultSched.rows,
                            cand[c][2] ? cand[c][2] : kDefaultSched.quads};
-        // one untimed cycle, then the timed one
-        if (launch_fed_batch(B, tau.data(), n, p.boundary, sch, st) || cudaEventRecord(e0, st) != cudaSuccess ||
-            launch_fed_batch(B, tau.data(), n, p.boundary, sch, st) || cudaEventRecord(e1, st) != cudaSuccess ||
+        // one untimed cycle, then the timed one, each without the copy back
+        // that the filter's alternating cycles do not make
+        int end = 0;
+        if (launch_fed_batch(B, tau.data(), n, p.boundary, sch, st, &end) || cudaEventRecord(e0, st) != cudaSuccess ||
+            launch_fed_batch(B, tau.data(), n, p.boundary, sch, st, &end) || cudaEventRecord(e1, st) != cudaSuccess ||
             cudaEventSynchronize(e1) != cudaSuccess) {
             rc = FD4_ERR_CUDA;
             break;

@@ -247,7 +247,10 @@ struct HostBatch {
     unsigned *max_s2;
     int n_max_s2;
     const ImgDesc *table_u;  // batches: the descriptor table with in = u (nullptr for single images)
+    const ImgDesc *table_sw; // batches: the descriptor table with u and the FED plane exchanged
+                             // (their TMA maps too); nullptr where the two cannot trade roles
     bool has_cmask;          // every descriptor has its chunk-mask plane (cmask)
+    bool cmask_fresh;        // the chunk masks already describe the current scale image
 };
 
 // One image: inline descriptor.
@@ -259,7 +262,9 @@ inline HostBatch single_batch(const ImgDesc &d)
     B.max_s2 = d.max_s2;
     B.n_max_s2 = 1;
     B.table_u = nullptr;
+    B.table_sw = nullptr;
     B.has_cmask = d.cmask != nullptr;
+    B.cmask_fresh = false;
     return B;
 }
 
@@ -307,9 +312,13 @@ struct FedSched {
 };
 constexpr FedSched kDefaultSched = {2, 64, 2};
 FedSched resolve_sched(const fd4_params &p);  // zero fields of p take the default
-// n FED steps on every image; the result ends in ImgDesc::u.
+// n FED steps on every image.  end_parity == nullptr: the result ends in
+// ImgDesc::u (copied back from the FED plane after an odd number of launches);
+// otherwise nothing is copied and *end_parity = 1 where it ends in ImgDesc::tmp.
 int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundary, const FedSched &sch,
-                     cudaStream_t st);
+                     cudaStream_t st, int *end_parity = nullptr);
+// Copies every image's FED plane (ImgDesc::tmp) into ImgDesc::u.
+int launch_copy_back_batch(const HostBatch &B, cudaStream_t st);
 int launch_select_tiles(const ImgDesc &d, const int *list, const int *count, const float *h_sigmas, int n_sigma,
                         const fd4_params &p, cudaStream_t st);
 // Sets the shared-memory attributes of every kernel (call before stream capture).

@@ -879,7 +879,7 @@ int prepare_tensor_kernels()
 int launch_tensor_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const fd4_params &p,
                          cudaStream_t st)
 {
-    if (B.has_cmask) {  // which chunks hold which scales: the strips skip the others
+    if (B.has_cmask && !B.cmask_fresh) {  // which chunks hold which scales: the strips skip the others
         Imgs I = B.I;
         I.tiles = B.tiles[SHAPE_SWEEP];
         const int grid = persistent_grid((const void *)k_chunk_masks, 256, 0, I.tiles);

@@ -103,11 +103,17 @@ def test_reselect_schedule_and_launch_count():
     fd4.filter_batched(b[3], SIGMAS, T, M, N, again)
     torch.cuda.synchronize()
     assert any(not torch.equal(x, y) for x, y in zip(a[2], b[2]))
-    # the graph holds (M - 1) more selections (K strip launches and the argmax
-    # each) and the copy of the descriptor table the re-selection reads
+    # the re-selecting graph holds (M - 1) more selections (K strip launches and
+    # the argmax each), the copy of the descriptor table the re-selection reads,
+    # the chunk masks of every cycle's scale image (the other builds them once)
+    # and a copy-back after every cycle of an odd launch count (the other
+    # alternates between u and the FED plane, with a table and its tensor maps
+    # for the exchanged pair, and copies back once at most)
     ga = fd4.Graph(a[3], SIGMAS, T, M, N, once)
     gb = fd4.Graph(b[3], SIGMAS, T, M, N, again)
-    assert gb.kernel_count() == ga.kernel_count() + (M - 1) * (len(SIGMAS) + 1) + 1
+    odd = -(-N // 2) % 2
+    copies = M * odd - (M * odd) % 2
+    assert gb.kernel_count() == ga.kernel_count() + (M - 1) * (len(SIGMAS) + 1) + 1 - 2 + (M - 1) + copies
     ga.close()
     gb.close()
 
