@@ -399,9 +399,10 @@ def run_fd4(args, rank, world, local_rank):
     ten_ms = _timed(g_ten.launch, args.steps, stream, torch) / args.steps
     fed_ms = _timed(g_fed.launch, args.steps, stream, torch) / args.steps
     # the FED kernel's own launches (events around each launch of the FED-only graph
-    # would split it; the graph's FED launches are all of one kernel, plus a copy-back
-    # launch per cycle when the launch count is odd)
-    fed_copy_backs = M * ((-(-n // S)) % 2) if S > 1 else M * (n % 2)
+    # would split it; the graph's FED launches are all of one kernel, plus one
+    # copy-back after the last cycle when the pass's launch count is odd: the cycles
+    # alternate between u and the FED plane)
+    fed_copy_backs = (M * ((-(-n // S)) if S > 1 else n)) % 2
 
     variants = {}
     crop_px_steps = None
@@ -469,7 +470,7 @@ def run_fd4(args, rank, world, local_rank):
         return
     peak, peak_kind = load_peaks()
     fed_bytes = 24 * npx * M * n  # algorithmic bytes of the FED steps of one pass
-    fed_kernel_ms = fed_ms  # includes the copy-back launches (memory copies of u, < 1 % of the stage)
+    fed_kernel_ms = fed_ms  # includes the copy-back launch, if any (one memory copy of u per pass)
     achieved = fed_bytes / (fed_kernel_ms * 1e-3) / 1e9
     key = (sched.steps_per_launch, sched.tile_rows, sched.quads_per_thread)
     traffic = args.traffic
