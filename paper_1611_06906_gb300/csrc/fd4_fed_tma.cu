@@ -271,19 +271,20 @@ __global__ void __launch_bounds__(t_quads<RY>() / NQ, RY == 64 ? 1 : 2)
             float4 v[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) v[i] = tq[i ^ tswz];
-            float cc[4], ss[4], pp[4], qq[4];
+            float mm[4], qc[4], qs[4], q2[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const float4 tt = v[i];
-                cc[i] = tt.x;
-                ss[i] = tt.y;
-                pp[i] = 0.25f * (tt.z + tt.w);  // quarter-scaled: quad_T carries its terms doubled
-                qq[i] = 0.25f * (tt.z - tt.w);
+                const float4 tt = v[i];  // (cos 2t, sin 2t, mu1, mu2)
+                const float qq = 0.25f * (tt.z - tt.w);
+                mm[i] = 0.5f * (tt.z + tt.w);
+                qc[i] = qq * tt.x;
+                qs[i] = qq * tt.y;
+                q2[i] = qs[i] + qs[i];
             }
-            k[qd].c = make_float4(cc[0], cc[1], cc[2], cc[3]);
-            k[qd].s = make_float4(ss[0], ss[1], ss[2], ss[3]);
-            k[qd].p = make_float4(pp[0], pp[1], pp[2], pp[3]);
-            k[qd].q = make_float4(qq[0], qq[1], qq[2], qq[3]);
+            k[qd].m = make_float4(mm[0], mm[1], mm[2], mm[3]);
+            k[qd].qc = make_float4(qc[0], qc[1], qc[2], qc[3]);
+            k[qd].qs = make_float4(qs[0], qs[1], qs[2], qs[3]);
+            k[qd].qs2 = make_float4(q2[0], q2[1], q2[2], q2[3]);
         }
         // Tile j + kAhead goes into box bj and plane (j + kAhead) % NU, once every
         // thread has read box bj (above) and is past tile j - 1, the last user of

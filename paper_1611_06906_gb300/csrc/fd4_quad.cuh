@@ -15,8 +15,11 @@ struct StepTaus {
     int n;
 };
 
+// Per pixel of the quad, from the tensor field (cos 2t, sin 2t, mu1, mu2):
+// m = mu3 = (mu1 + mu2) / 2, and with q = (mu1 - mu2) / 4: qc = q cos 2t,
+// qs = q sin 2t, qs2 = 2 qs.
 struct QuadCoef {
-    float4 c, s, p, q;  // per pixel of the quad: cos 2t, sin 2t, (mu1 + mu2) / 4, (mu1 - mu2) / 4
+    float4 m, qc, qs, qs2;
 };
 
 __device__ __forceinline__ void f4_to(const float4 v, float *d)
@@ -35,20 +38,25 @@ __device__ __forceinline__ void quad_ext(const float4 m, float (&v)[6])
 // T = M D M L u for the 4 pixels of one quad.  a, b, c: rows y-1, y, y+1 at
 // columns x-1 .. x+4.  BOUNDARY: apply the natural-boundary masks (bits 0-3:
 // pixel inside, 4-7: Lxx row exists, 8: Lyy row exists for this row).
-// The mixed derivative shares its column differences a - c between
-// neighbouring pixels, and the eigenframe quantities are carried at twice
-// their size (sh2 = hxx + hyy, dh2 = hxx - hyy, hxy2 = 2 hxy), which the
-// quarter-scaled diffusivity coefficients p, q bring back to scale.
+// D acts on the Hessian H through its eigentensors: with E1, E2 the projectors
+// on the eigenvectors, t11 = mu1 h11, t22 = mu2 h22 and t12 = mu3 h12 give
+//   T = mu3 H + (mu1 - mu2) / 2 (h11 E1 - h22 E2) = mu3 H + q (z I + tr H R),
+// where R = E1 - E2 = [[c, s], [s, -c]] (c = cos 2t, s = sin 2t),
+// z = R:H = c (hxx - hyy) + 2 s hxy and q = (mu1 - mu2) / 4.  So
+//   Txx = mu3 hxx + Z + qc tr H,  Tyy = mu3 hyy + Z - qc tr H,
+//   Txy = mu3 hxy + qs tr H,      Z = qc (hxx - hyy) + 2 qs hxy,
+// ten operations for T per pixel on three coefficients (and 2 qs).  The mixed
+// derivative shares its column differences a - c between neighbouring pixels.
 template <bool BOUNDARY>
 __device__ __forceinline__ void quad_T(const float (&a)[6], const float (&b)[6], const float (&c)[6],
                                        const QuadCoef &k, unsigned mask, float4 &Txx, float4 &Txy, float4 &Tyy)
 {
     float rxx[4], rxy[4], ryy[4];
-    float cc[4], ss[4], pp[4], qq[4];
-    f4_to(k.c, cc);
-    f4_to(k.s, ss);
-    f4_to(k.p, pp);
-    f4_to(k.q, qq);
+    float mm[4], qc[4], qs[4], q2[4];
+    f4_to(k.m, mm);
+    f4_to(k.qc, qc);
+    f4_to(k.qs, qs);
+    f4_to(k.qs2, q2);
     float e[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) e[j] = a[j] - c[j];
@@ -56,7 +64,7 @@ __device__ __forceinline__ void quad_T(const float (&a)[6], const float (&b)[6],
     for (int i = 0; i < 4; ++i) {
         float hxx = fmaf(-2.0f, b[i + 1], b[i] + b[i + 2]);
         float hyy = fmaf(-2.0f, b[i + 1], a[i + 1] + c[i + 1]);
-        float hxy2 = 0.5f * (e[i] - e[i + 2]);                 // 2 hxy
+        float hxy = 0.25f * (e[i] - e[i + 2]);
         bool vx = true, vy = true, in = true;
         if (BOUNDARY) {
             in = (mask >> i) & 1u;
@@ -64,17 +72,13 @@ __device__ __forceinline__ void quad_T(const float (&a)[6], const float (&b)[6],
             vy = (mask >> 8) & 1u;
             hxx = vx ? hxx : 0.0f;
             hyy = vy ? hyy : 0.0f;
-            hxy2 = (vx && vy) ? hxy2 : 0.0f;
+            hxy = (vx && vy) ? hxy : 0.0f;
         }
-        const float sh2 = hxx + hyy, dh2 = hxx - hyy;
-        const float z2 = fmaf(cc[i], dh2, ss[i] * hxy2);       // eigenframe: h11 = (sh2 + z2) / 2, h22 = (sh2 - z2) / 2
-        const float v2 = fmaf(cc[i], hxy2, -ss[i] * dh2);      // 2 h12
-        const float st = fmaf(pp[i], sh2, qq[i] * z2);         // (t11 + t22) / 2
-        const float dt = fmaf(qq[i], sh2, pp[i] * z2);         // (t11 - t22) / 2
-        const float t12 = pp[i] * v2;
-        float txx = fmaf(cc[i], dt, fmaf(-ss[i], t12, st));
-        float tyy = fmaf(2.0f, st, -txx);
-        float txy = fmaf(ss[i], dt, cc[i] * t12);
+        const float tr = hxx + hyy, dh = hxx - hyy;
+        const float Z = fmaf(qc[i], dh, q2[i] * hxy);  // q z
+        float txx = fmaf(mm[i], hxx, fmaf(qc[i], tr, Z));
+        float tyy = fmaf(mm[i], hyy, fmaf(-qc[i], tr, Z));
+        float txy = fmaf(mm[i], hxy, qs[i] * tr);
         if (BOUNDARY) {
             txx = (in && vx) ? txx : 0.0f;
             tyy = (in && vy) ? tyy : 0.0f;
