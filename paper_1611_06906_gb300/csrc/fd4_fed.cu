@@ -392,6 +392,8 @@ int launch_fed_batch(const HostBatch &B, const double *h_tau, int n, int boundar
     const int periodic = boundary == FD4_BC_PERIODIC;
     int S = sch.steps;
     if (S < 1 || S > 4) S = kDefaultSched.steps;
+    // the FED coefficient planes are read by the TMA kernel only
+    if (B.fed_soa && (periodic || S == 1 || S == 3)) return 1;
     int parity = 0;
     if (S == 1) {
         Imgs I = B.I;

@@ -47,17 +47,23 @@ template <int RY>
 constexpr int t_plane() { return (RY + 2) * TSW; }  // one zero ring row above and below
 template <int RY>
 constexpr unsigned t_ubytes() { return TR * RY * 4; }   // u box
-template <int RY>
-constexpr unsigned t_tbytes() { return TR * RY * 16; }  // tensor box (cos 2t, sin 2t, mu1, mu2)
+// tensor box: (cos 2t, sin 2t, mu1, mu2) per pixel, 16 B; or (SOA) the three
+// FED coefficient planes (mu3, q cos 2t, q sin 2t), 12 B
+template <int RY, bool SOA>
+constexpr unsigned t_tbytes() { return SOA ? TR * RY * 12 : TR * RY * 16; }
 // shared memory: tensor boxes x2 (1024-byte aligned) | u planes x3 | T_xy, T_yy
-template <int RY>
-constexpr size_t t_smem() { return 1024 + kAhead * t_tbytes<RY>() + sizeof(float) * (kAhead + 1 + 2) * t_plane<RY>(); }
+template <int RY, bool SOA>
+constexpr size_t t_smem()
+{
+    return 1024 + kAhead * t_tbytes<RY, SOA>() + sizeof(float) * (kAhead + 1 + 2) * t_plane<RY>();
+}
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded wait on a tile's copies
 
-// 2-D maps of the two u planes {w, h} and the 3-D map of the tensor field
-// {16, quads, h}; their boxes have the region's rows.
+// 2-D maps of the two u planes {w, h}, the 3-D map of the tensor field
+// {16, quads, h} and the 3-D map of the FED coefficient planes {w, h, 3}; their
+// boxes have the region's rows.
 struct TmaMaps {
-    CUtensorMap u, tmp, ten;
+    CUtensorMap u, tmp, ten, co;
 };
 // One image's maps for both region heights.
 struct TmaMapSet {
@@ -149,7 +155,7 @@ struct TileGeo {
 // Thread 0: the copies of the region of tile `local` of image d into u_dst (plane
 // row 1) and the tensor box; the tile's geometry into *g.  withhold (self-test
 // only): the barrier is armed for the bytes but no copy is issued.
-template <int S, int RY>
+template <int S, int RY, bool SOA>
 __device__ __forceinline__ void tma_issue(const ImgDesc &d, int local, const TmaMaps &one, bool from_table,
                                           int parity, float *u_dst, void *t_dst, uint64_t *mbar, TileGeo *g,
                                           int withhold)
@@ -167,15 +173,19 @@ __device__ __forceinline__ void tma_issue(const ImgDesc &d, int local, const Tma
         m = RY == 64 ? &set->r64 : &set->r32;
     }
     const CUtensorMap *mu = parity ? &m->tmp : &m->u;
+    const CUtensorMap *mt = SOA ? &m->co : &m->ten;
     if (from_table) {
         fence_tensormap_acquire(mu);
-        fence_tensormap_acquire(&m->ten);
+        fence_tensormap_acquire(mt);
     }
     fence_async_smem();
-    tma_expect(mbar, t_ubytes<RY>() + t_tbytes<RY>());
+    tma_expect(mbar, t_ubytes<RY>() + t_tbytes<RY, SOA>());
     if (withhold) return;
-    tma_load_2d(u_dst + TSW, mu, gx0, gy0, mbar);         // x: 4 gx0 bytes, a multiple of 16
-    tma_load_3d(t_dst, &m->ten, 0, gx0 >> 2, gy0, mbar);  // x: 0; the quad index may be -1
+    tma_load_2d(u_dst + TSW, mu, gx0, gy0, mbar);  // x: 4 gx0 bytes, a multiple of 16
+    if (SOA)
+        tma_load_3d(t_dst, mt, gx0, gy0, 0, mbar);  // x: 4 gx0 bytes, as above
+    else
+        tma_load_3d(t_dst, mt, 0, gx0 >> 2, gy0, mbar);  // x: 0; the quad index may be -1
 }
 
 // NQ quads per thread: 16 RY / NQ threads, thread (row ry, quad column q) owns
@@ -183,17 +193,18 @@ __device__ __forceinline__ void tma_issue(const ImgDesc &d, int local, const Tma
 // half the warps and each thread has two independent quads in flight.  A block
 // of 64-row regions takes one SM (217 KB of shared memory); two blocks of
 // 32-row regions share one.
-template <int S, int NQ, int RY>
+template <int S, int NQ, int RY, bool SOA>
 __global__ void __launch_bounds__(t_quads<RY>() / NQ, RY == 64 ? 1 : 2)
     k_fed_tma(Imgs I, StepTaus taus, int parity, const __grid_constant__ TmaMaps one, FedWait wt)
 {
     constexpr int H = 2 * S, TOX = TR - 2 * H, TOY = RY - 2 * H, SHAPE = tma_shape<S, RY>(), NU = kAhead + 1;
     constexpr int NT = t_quads<RY>() / NQ, TPLANE = t_plane<RY>();
-    constexpr unsigned TBYTES = t_tbytes<RY>();
+    constexpr unsigned TBYTES = t_tbytes<RY, SOA>();
     static_assert(TOX % 4 == 0 && H % 4 == 0 && TOY > 0, "whole quads in the exact interior");
     extern __shared__ unsigned char tma_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)tma_raw + 1023) & ~(uintptr_t)1023);
-    // tensor boxes: tile j of this block in box j % kAhead (RY rows x 64 pixels x 16 B each)
+    // tensor boxes: tile j of this block in box j % kAhead (RY rows x 64 pixels x 16 B,
+    // or SOA: 3 planes x RY rows x 64 pixels x 4 B)
     float *planes = reinterpret_cast<float *>(base + kAhead * TBYTES);  // u planes x NU | T_xy | T_yy
     float *sxy = planes + NU * TPLANE, *syy = planes + (NU + 1) * TPLANE;
     __shared__ uint64_t mbar[kAhead];     // tile j waits on mbar[j % kAhead]
@@ -231,8 +242,8 @@ __global__ void __launch_bounds__(t_quads<RY>() / NQ, RY == 64 ? 1 : 2)
             const int tj = blockIdx.x + j * G;
             if (tj >= ntiles) break;
             find_tile_cached(I, SHAPE, tj, tcache, sd[j], s_local[j]);
-            tma_issue<S, RY>(sd[j], s_local[j], one, from_table, parity, planes + j * TPLANE, base + j * TBYTES,
-                             &mbar[j], &sgeo[j], wt.withhold);
+            tma_issue<S, RY, SOA>(sd[j], s_local[j], one, from_table, parity, planes + j * TPLANE,
+                                  base + j * TBYTES, &mbar[j], &sgeo[j], wt.withhold);
         }
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += G, ++j) {
@@ -261,6 +272,17 @@ __global__ void __launch_bounds__(t_quads<RY>() / NQ, RY == 64 ? 1 : 2)
                     mask[qd] |= (x >= 1 && x <= w - 2 ? 1u : 0u) << (4 + i);
                 }
                 mask[qd] |= (gy >= 1 && gy <= h - 2 ? 1u : 0u) << 8;
+            }
+            if (SOA) {
+                // the three coefficient planes of the box, dense rows of 64
+                // floats: a quarter-warp reads 128 contiguous bytes of each
+                const float *tb = reinterpret_cast<const float *>(base + bj * TBYTES) + rowq[qd] * TR + 4 * q;
+                const float4 qs4 = *reinterpret_cast<const float4 *>(tb + 2 * RY * TR);
+                k[qd].m = *reinterpret_cast<const float4 *>(tb);
+                k[qd].qc = *reinterpret_cast<const float4 *>(tb + RY * TR);
+                k[qd].qs = qs4;
+                k[qd].qs2 = make_float4(qs4.x + qs4.x, qs4.y + qs4.y, qs4.z + qs4.z, qs4.w + qs4.w);
+                continue;
             }
             // The copy's 64-byte swizzle put pixel i of quad q in 16-byte slot
             // i ^ r of the quad, r = (q / 2) mod 4: the 8 lanes of a quarter-warp
@@ -294,8 +316,8 @@ __global__ void __launch_bounds__(t_quads<RY>() / NQ, RY == 64 ? 1 : 2)
             if (tid == 0 && ta < ntiles) {
                 const int ua = (j + kAhead) % NU;
                 find_tile_cached(I, SHAPE, ta, tcache, sd[ua], s_local[ua]);
-                tma_issue<S, RY>(sd[ua], s_local[ua], one, from_table, parity, planes + ua * TPLANE,
-                                 base + bj * TBYTES, &mbar[bj], &sgeo[ua], wt.withhold);
+                tma_issue<S, RY, SOA>(sd[ua], s_local[ua], one, from_table, parity, planes + ua * TPLANE,
+                                      base + bj * TBYTES, &mbar[bj], &sgeo[ua], wt.withhold);
             }
         };
         if (taus.n < 1) {
@@ -339,14 +361,14 @@ struct MapChunk {
 };
 __global__ void k_put_maps(const __grid_constant__ MapChunk c, TmaMapSet *table)
 {
-    const int i = blockIdx.x, j = threadIdx.x;  // set i of the chunk, 16-byte word j of 48
+    const int i = blockIdx.x, j = threadIdx.x;  // set i of the chunk, its 16-byte word j
     if (i < c.n && j < (int)(sizeof(TmaMapSet) / 16)) {
         reinterpret_cast<uint4 *>(&table[c.first + i])[j] = reinterpret_cast<const uint4 *>(&c.m[i])[j];
         asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
     }
 }
 
-// The three maps of one image for regions of `rows` rows (zero fill outside the image).
+// The four maps of one image for regions of `rows` rows (zero fill outside the image).
 int make_maps(const ImgDesc &d, int rows, TmaMaps *m)
 {
     EncodeTiledFn enc = tensor_map_encoder();
@@ -374,35 +396,53 @@ int make_maps(const ImgDesc &d, int rows, TmaMaps *m)
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return 1;
+    // FED coefficient planes: columns x rows x the three planes (they lie in the
+    // 16 B per pixel of the tensor plane)
+    const cuuint64_t dimc[3] = {(cuuint64_t)d.w, (cuuint64_t)d.h, 3};
+    const cuuint64_t strc[2] = {(cuuint64_t)d.pitch * 4, (cuuint64_t)fed_coef_plane(d.h, d.pitch) * 4};
+    const cuuint32_t boxc[3] = {TR, (cuuint32_t)rows, 3};
+    if (enc(&m->co, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)d.tensor, dimc, strc, boxc, one3,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return 1;
     return 0;
 }
 
 int make_map_set(const ImgDesc &d, TmaMapSet *m) { return make_maps(d, 64, &m->r64) || make_maps(d, 32, &m->r32); }
 
-template <int S, int NQ, int RY>
+template <int S, int NQ, int RY, bool SOA>
 int set_tma_smem()
 {
     static int attr_dev = -1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
     if (attr_dev != dev) {
-        if (cudaFuncSetAttribute(k_fed_tma<S, NQ, RY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)t_smem<RY>()) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_fed_tma<S, NQ, RY, SOA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)t_smem<RY, SOA>()) != cudaSuccess)
             return 1;
         attr_dev = dev;
     }
     return 0;
 }
 
-template <int S, int NQ, int RY>
+template <int S, int NQ, int RY, bool SOA>
 int launch_tma_k(const Imgs &I, const StepTaus &t, int parity, const TmaMaps &one, const FedWait &wt,
                  cudaStream_t st)
 {
-    if (set_tma_smem<S, NQ, RY>()) return 1;
+    if (set_tma_smem<S, NQ, RY, SOA>()) return 1;
     constexpr int NT = t_quads<RY>() / NQ;
-    const int grid = persistent_grid((const void *)k_fed_tma<S, NQ, RY>, NT, t_smem<RY>(), I.tiles);
-    k_fed_tma<S, NQ, RY><<<grid, NT, t_smem<RY>(), st>>>(I, t, parity, one, wt);
+    constexpr size_t smem = t_smem<RY, SOA>();
+    const int grid = persistent_grid((const void *)k_fed_tma<S, NQ, RY, SOA>, NT, smem, I.tiles);
+    k_fed_tma<S, NQ, RY, SOA><<<grid, NT, smem, st>>>(I, t, parity, one, wt);
     return cudaGetLastError() != cudaSuccess;
+}
+
+template <int S, int RY, bool SOA>
+int launch_tma_q(const Imgs &I, const StepTaus &t, int parity, const TmaMaps &one, const FedWait &wt, int quads,
+                 cudaStream_t st)
+{
+    return quads == 1 ? launch_tma_k<S, 1, RY, SOA>(I, t, parity, one, wt, st)
+                      : launch_tma_k<S, 2, RY, SOA>(I, t, parity, one, wt, st);
 }
 
 template <int S>
@@ -419,11 +459,11 @@ int launch_tma_sched(const HostBatch &B, const double *tau, int k, int parity, c
     memset(&set, 0, sizeof(set));
     if (!I.table && make_map_set(I.one, &set)) return 1;
     const TmaMaps &one = r32 ? set.r32 : set.r64;
-    if (r32)
-        return sch.quads == 1 ? launch_tma_k<S, 1, 32>(I, t, parity, one, wt, st)
-                              : launch_tma_k<S, 2, 32>(I, t, parity, one, wt, st);
-    return sch.quads == 1 ? launch_tma_k<S, 1, 64>(I, t, parity, one, wt, st)
-                          : launch_tma_k<S, 2, 64>(I, t, parity, one, wt, st);
+    if (B.fed_soa)
+        return r32 ? launch_tma_q<S, 32, true>(I, t, parity, one, wt, sch.quads, st)
+                   : launch_tma_q<S, 64, true>(I, t, parity, one, wt, sch.quads, st);
+    return r32 ? launch_tma_q<S, 32, false>(I, t, parity, one, wt, sch.quads, st)
+               : launch_tma_q<S, 64, false>(I, t, parity, one, wt, sch.quads, st);
 }
 
 }  // namespace
@@ -445,18 +485,21 @@ EncodeTiledFn tensor_map_encoder()
 
 size_t tma_maps_bytes() { return sizeof(TmaMapSet); }
 
-int prepare_tma_kernels()
+template <bool SOA>
+int prepare_tma_kernels_of()
 {
-    return set_tma_smem<2, 1, 64>() || set_tma_smem<4, 1, 64>() || set_tma_smem<2, 2, 64>() ||
-           set_tma_smem<4, 2, 64>() || set_tma_smem<2, 1, 32>() || set_tma_smem<4, 1, 32>() ||
-           set_tma_smem<2, 2, 32>() || set_tma_smem<4, 2, 32>();
+    return set_tma_smem<2, 1, 64, SOA>() || set_tma_smem<4, 1, 64, SOA>() || set_tma_smem<2, 2, 64, SOA>() ||
+           set_tma_smem<4, 2, 64, SOA>() || set_tma_smem<2, 1, 32, SOA>() || set_tma_smem<4, 1, 32, SOA>() ||
+           set_tma_smem<2, 2, 32, SOA>() || set_tma_smem<4, 2, 32, SOA>();
 }
+
+int prepare_tma_kernels() { return prepare_tma_kernels_of<false>() || prepare_tma_kernels_of<true>(); }
 
 // Writes the map sets of the n descriptors (their maps fields point into a
 // device table) with kernels on st.
 int launch_put_maps(const ImgDesc *h_descs, int n, void *d_table, cudaStream_t st)
 {
-    thread_local static MapChunk c;  // 12 KB: kept off the stack
+    thread_local static MapChunk c;  // 16 KB: kept off the stack
     for (int first = 0; first < n; first += kMapChunk) {
         c.first = first;
         c.n = n - first < kMapChunk ? n - first : kMapChunk;

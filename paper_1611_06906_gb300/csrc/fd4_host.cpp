@@ -499,6 +499,15 @@ static int enqueue_filter(const HostBatch &B, const float *h_sigmas, int n_sigma
     return FD4_OK;
 }
 
+// Whether the filter's FED schedule runs the TMA kernel (2 or 4 steps per
+// launch under the natural boundary): its tensor builds then write the FED
+// coefficient planes that kernel reads instead of the float4 tensor field.
+static bool fed_reads_coef(const fd4_params &p)
+{
+    const FedSched s = resolve_sched(p);
+    return (s.steps == 2 || s.steps == 4) && p.boundary == FD4_BC_NATURAL;
+}
+
 static int check_steps(const fd4_params &p)
 {
     return check_sched(p.fed_steps_per_launch, p.fed_tile_rows, p.fed_quads_per_thread);
@@ -551,8 +560,9 @@ extern "C" int fd4_filter(const float *d_in, float *d_out, int w, int h, int pit
     d.w = w;
     d.h = h;
     d.pitch = pitch;
-    return enqueue_filter(single_batch(d), h_sigmas, n_sigma, p, tau.data(), n, M, sigma_given,
-                          (cudaStream_t)stream);
+    HostBatch B = single_batch(d);
+    B.fed_soa = fed_reads_coef(p);
+    return enqueue_filter(B, h_sigmas, n_sigma, p, tau.data(), n, M, sigma_given, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -643,6 +653,7 @@ static size_t batch_layout(const fd4_image *imgs, int n, int n_sigma, std::vecto
         B->table_sw = (const ImgDesc *)(ws + tsw_off);
         B->has_cmask = true;
         B->cmask_fresh = false;
+        B->fed_soa = false;
     }
     if (B1 && two) {
         *B1 = *B;
@@ -748,6 +759,7 @@ static int enqueue_batch_two_streams(const fd4_image *imgs, int n_images, const 
     const bool sel = mafod && !sigma_given;
     const bool post = sel && p.postprocess_scales;
     batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B0, split, &B1, post);
+    B0.fed_soa = B1.fed_soa = fed_reads_coef(p);
     const bool reselect = sel && p.reselect_each_cycle;
     if (put_tables(descs, n_images, B0, d_ws, reselect, false, s0)) return FD4_ERR_CUDA;
     const FedSched steps = resolve_sched(p);
@@ -794,6 +806,7 @@ static int enqueue_batch(const fd4_image *imgs, int n_images, const float *h_sig
     const bool sel = p.model == FD4_MODEL_MAFOD && !sigma_given && (stages & FD4_STAGE_SELECT);
     const bool post = sel && p.postprocess_scales && (stages & FD4_STAGE_COPY);
     batch_layout(imgs, n_images, n_sigma, &descs, (char *)d_ws, &B, 0, nullptr, post);
+    B.fed_soa = fed_reads_coef(p);
     const bool reselect = sel && p.reselect_each_cycle;
     // the exchanged table serves cycles that end in the FED plane
     const bool with_sw = !reselect && (stages & FD4_STAGE_FED);
@@ -931,6 +944,7 @@ extern "C" int fd4_autotune_batched(const fd4_image *h_imgs, int n_images, const
     batch_layout(h_imgs, n_images, n_sigma, &descs, (char *)d_ws, &B);
     if (launch_put_descs(descs.data(), n_images, (ImgDesc *)d_ws, st)) return FD4_ERR_CUDA;
     if (n_images > 0 && launch_put_maps(descs.data(), n_images, (void *)descs[0].maps, st)) return FD4_ERR_CUDA;
+    B.fed_soa = false;
     if ((p.model == FD4_MODEL_MAFOD && launch_select_batch(B, h_sigmas, n_sigma, p, st)) ||
         launch_copy_in_batch(B, st) || launch_cycle_tensor(B, h_sigmas, n_sigma, p, st))
         return FD4_ERR_CUDA;
@@ -950,6 +964,16 @@ extern "C" int fd4_autotune_batched(const fd4_image *h_imgs, int n_images, const
     for (int c = 0; c < FD4_AUTOTUNE_CANDIDATES && rc == FD4_OK; ++c) {
         const FedSched sch{cand[c][0], cand[c][1] ? cand[c][1] : kDefaultSched.rows,
                            cand[c][2] ? cand[c][2] : kDefaultSched.quads};
+        // the tensor field in the form this candidate reads, as the filter builds it
+        fd4_params pc = p;
+        pc.fed_steps_per_launch = sch.steps;
+        if (fed_reads_coef(pc) != B.fed_soa) {
+            B.fed_soa = !B.fed_soa;
+            if (launch_cycle_tensor(B, h_sigmas, n_sigma, p, st)) {
+                rc = FD4_ERR_CUDA;
+                break;
+            }
+        }
         // one untimed cycle, then the timed one, each without the copy back
         // that the filter's alternating cycles do not make
         int end = 0;

@@ -251,7 +251,15 @@ struct HostBatch {
                              // (their TMA maps too); nullptr where the two cannot trade roles
     bool has_cmask;          // every descriptor has its chunk-mask plane (cmask)
     bool cmask_fresh;        // the chunk masks already describe the current scale image
+    bool fed_soa;            // ImgDesc::tensor holds the FED coefficient planes (fed_coef_plane)
+                             // instead of float4 (cos 2t, sin 2t, mu1, mu2) per pixel
 };
+
+// The FED coefficient planes of an image's tensor plane (16 B per pixel): three
+// float planes of h x pitch, mu3 = (mu1 + mu2) / 2, q cos 2t and q sin 2t with
+// q = (mu1 - mu2) / 4 -- what the TMA FED kernel reads (12 B per pixel).  A
+// filter builds them when its FED schedule runs that kernel.
+__host__ __device__ inline size_t fed_coef_plane(int h, int pitch) { return (size_t)h * pitch; }
 
 // One image: inline descriptor.
 inline HostBatch single_batch(const ImgDesc &d)
@@ -265,6 +273,7 @@ inline HostBatch single_batch(const ImgDesc &d)
     B.table_sw = nullptr;
     B.has_cmask = d.cmask != nullptr;
     B.cmask_fresh = false;
+    B.fed_soa = false;
     return B;
 }
 

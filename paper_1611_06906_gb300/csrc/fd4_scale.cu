@@ -387,7 +387,7 @@ __device__ __forceinline__ int2 finish_origin(const ImgDesc &d, int local, int h
 // The next half tile's region is copied (cp.async, double buffer) while the
 // current one is smoothed and decomposed.  Work unit u = half u % 2 of tile u / 2.
 template <int r>
-__global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, float lambda, int mode)
+__global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, float lambda, int mode, int soa)
 {
     constexpr int ROWS = FH + 2 * r, CP = finish_cp<r>();
     extern __shared__ __align__(16) float4 fsm4[];
@@ -506,8 +506,17 @@ __global__ void __launch_bounds__(FNT_T) k_tensor_finish(Imgs I, RhoTaps taps, f
                     nu1 = rr;
                     nu2 = -rr;
                 }
-                sd.tensor[(size_t)gy * pitch + gx] =
-                    make_float4(c2, s2, pm_mu(nu1, inv_lambda, mode), pm_mu(nu2, inv_lambda, mode));
+                const float mu1 = pm_mu(nu1, inv_lambda, mode), mu2 = pm_mu(nu2, inv_lambda, mode);
+                if (soa) {  // the FED coefficient planes
+                    float *tp = reinterpret_cast<float *>(sd.tensor) + (size_t)gy * pitch + gx;
+                    const size_t P = fed_coef_plane(h, pitch);
+                    const float qq = 0.25f * (mu1 - mu2);
+                    tp[0] = 0.5f * (mu1 + mu2);
+                    tp[P] = qq * c2;
+                    tp[2 * P] = qq * s2;
+                } else {
+                    sd.tensor[(size_t)gy * pitch + gx] = make_float4(c2, s2, mu1, mu2);
+                }
             }
         }
         cur ^= 1;
@@ -531,7 +540,7 @@ int launch_finish(const HostBatch &B, const RhoTaps &rt, const fd4_params &p, cu
     Imgs I = B.I;
     I.tiles = B.tiles[SHAPE_SWEEP];
     const int grid = persistent_grid((const void *)k_tensor_finish<r>, FNT_T, smem, 2 * I.tiles);
-    k_tensor_finish<r><<<grid, FNT_T, smem, st>>>(I, rt, p.lambda, p.mode);
+    k_tensor_finish<r><<<grid, FNT_T, smem, st>>>(I, rt, p.lambda, p.mode, B.fed_soa ? 1 : 0);
     return 0;
 }
 

@@ -234,6 +234,7 @@ struct StripArgs {
     int shape;      // SHAPE_SEG or SHAPE_SEG_S
     int seg;        // its rows
     float inv_lam2; // IFOD: 1 / lambda^2
+    int soa;        // IFOD: the FED coefficient planes (g, 0, 0) instead of (1, 0, g, g)
 };
 
 // What a strip launch computes (the kernels' MODE).
@@ -492,7 +493,15 @@ __global__ void __launch_bounds__(ST_NT) k_strip(Imgs I, StripTapsN<R, NS> tpn, 
                 if (!SEL) {  // IFOD: D = g I
                     const float f2 = fmaf(a, a, fmaf(2.0f * b, b, d * d));
                     const float g = 1.0f / fmaf(f2, sa.inv_lam2, 1.0f);
-                    sd[cur].tensor[(size_t)gy * pitch + gx] = make_float4(1.0f, 0.0f, g, g);
+                    if (sa.soa) {
+                        float *tp = reinterpret_cast<float *>(sd[cur].tensor) + (size_t)gy * pitch + gx;
+                        const size_t P = fed_coef_plane(h, pitch);
+                        tp[0] = g;  // mu3 = (g + g) / 2; q = 0
+                        tp[P] = 0.0f;
+                        tp[2 * P] = 0.0f;
+                    } else {
+                        sd[cur].tensor[(size_t)gy * pitch + gx] = make_float4(1.0f, 0.0f, g, g);
+                    }
                     continue;
                 }
                 // eigenvalues of H (sigma^(2 gamma) cancels in R_B and the sign
@@ -818,6 +827,7 @@ int launch_strips(const HostBatch &B, const float *h_sigmas, int n_sigma, const 
         sa.scale4 = (float)pow((double)h_sigmas[s], 4.0 * p.gamma);
         sa.inv2b2 = (float)(1.0 / (2.0 * (double)p.beta * p.beta));
         sa.inv_lam2 = (float)(1.0 / ((double)p.lambda * p.lambda));
+        sa.soa = B.fed_soa ? 1 : 0;
         int rc = 1;
         if constexpr (MODE == ST_TENSOR) {
             if (ns == 2) {
