@@ -52,10 +52,14 @@ from paper_1611_06906_gb300.dist import max_over_ranks as _max_over_ranks, rank_
 # (profiles/); the roofline's `traffic` scales it to the launch timed here.
 # Entries are removed (the field is then null) whenever that kernel changes.
 FED_DRAM_B_PER_PX = {
-    # k_fed_tma<2,2,64>: one launch over one 4096^2 image of the workload, 335.60 MB
-    # read + 53.39 MB written over 16.78 Mpixel (profiles/k_fed_tma_tree16_4096.md)
-    (2, 64, 2): 23.18,
+    # k_fed_tma<2,2,64,true>: one launch over one 4096^2 image of the workload, 268.53 MB
+    # read + 50.76 MB written over 16.78 Mpixel (profiles/k_fed_tma_tree16_4096.md)
+    (2, 64, 2): 19.03,
 }
+# Algorithmic bytes of one FED step per pixel: u read (4) and written (4), and
+# the three FED coefficient planes the filter's tensor build leaves for the
+# kernel (mu3, q cos 2t, q sin 2t: 12).
+FED_B_PER_PX_STEP = 20
 METRIC = "Mpixel-steps/s, batched+learned vs plain GB300, at stated FP64-oracle error"
 UNIT = "Mpixel-steps/s"
 
@@ -236,7 +240,8 @@ def fed_kernel_name(sch) -> str:
         return "k_fed_step"
     if s == 3:
         return "k_fed_fused<3>"
-    return "k_fed_tma<%d,%d,%d>" % (s, q or 2, r or 64)
+    # the filter's tensor builds leave the FED coefficient planes for this kernel (SOA)
+    return "k_fed_tma<%d,%d,%d,true>" % (s, q or 2, r or 64)
 
 
 def run_fd4(args, rank, world, local_rank):
@@ -469,7 +474,7 @@ def run_fd4(args, rank, world, local_rank):
     if rank != 0:
         return
     peak, peak_kind = load_peaks()
-    fed_bytes = 24 * npx * M * n  # algorithmic bytes of the FED steps of one pass
+    fed_bytes = FED_B_PER_PX_STEP * npx * M * n  # algorithmic bytes of the FED steps of one pass
     fed_kernel_ms = fed_ms  # includes the copy-back launch, if any (one memory copy of u per pass)
     achieved = fed_bytes / (fed_kernel_ms * 1e-3) / 1e9
     key = (sched.steps_per_launch, sched.tile_rows, sched.quads_per_thread)
@@ -479,7 +484,7 @@ def run_fd4(args, rank, world, local_rank):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "traffic_unit": "bytes per launch", "kernel": fed_kernel_name(sched),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind,
-            "bytes_per_px_step": 24, "steps_per_launch": S,
+            "bytes_per_px_step": FED_B_PER_PX_STEP, "steps_per_launch": S,
             "avg_launch_us": fed_kernel_ms * 1e3 / fed_launches, "copy_back_launches_per_pass": fed_copy_backs,
             "algorithmic_bytes_per_launch": fed_bytes / fed_launches}
     # the selection stage is FP32-FMA bound: its algorithmic FMAs per pass (row and
