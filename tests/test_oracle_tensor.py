@@ -8,7 +8,9 @@ Sec. 3.4 D_i = E M E^T).
   * on u = g x + q (y - y0)^2 / 2 the normalised Hessian at row y0 is exactly
     diag(0, q) / sqrt(1 + g) (gradient (g, 0), Hessian diag(0, q)), which fixes
     the eigenvector, both eigenvalues and the diffusivities in every mode;
-  * transposing the image maps (cos 2t, sin 2t) to (-cos 2t, sin 2t).
+  * transposing the image maps (cos 2t, sin 2t) to (-cos 2t, sin 2t);
+  * the closed form D_i H = mu3 H + q (z I + tr H R) that the FED kernel
+    evaluates equals the oracle's D_i on random symmetric H.
 """
 import math
 
@@ -104,3 +106,29 @@ def test_per_pixel_scale_is_respected(oracle):
     t_all, _ = oracle.build_tensor(img, one, sig, mode=oracle.VALLEY)
     t_single, _ = oracle.build_tensor(img, np.zeros_like(one), [2.0], mode=oracle.VALLEY)
     assert np.array_equal(t_all, t_single)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_D_action_closed_form_of_the_fed_step(oracle, seed):
+    """The FED kernel applies D_i to the Hessian without rotating into the
+    eigenframe: with mu3 = (mu1 + mu2) / 2, q = (mu1 - mu2) / 4, R = [[c, s], [s, -c]]
+    and z = R:H, D_i H = mu3 H + q (z I + tr H R), i.e. on the coefficients
+    (mu3, q c, q s) that its tensor build leaves:
+    Txx = mu3 hxx + Z + qc tr H, Tyy = mu3 hyy + Z - qc tr H, Txy = mu3 hxy + qs tr H,
+    Z = qc (hxx - hyy) + 2 qs hxy.  Checked against the oracle's 4 x 4 D_i on
+    random symmetric H, orientations and diffusivities (Sec. 3.4)."""
+    rng = np.random.default_rng(100 + seed)
+    for _ in range(50):
+        th = rng.uniform(-math.pi, math.pi)
+        mu1, mu2 = rng.uniform(0.0, 1.0, size=2)
+        hxx, hxy, hyy = rng.normal(size=3)
+        c, s = math.cos(2 * th), math.sin(2 * th)
+        D = oracle.tensor_matrix(c, s, mu1, mu2)
+        T = (D @ np.array([hxx, hxy, hxy, hyy])).reshape(2, 2)
+        mu3, q = 0.5 * (mu1 + mu2), 0.25 * (mu1 - mu2)
+        qc, qs = q * c, q * s
+        tr, Z = hxx + hyy, qc * (hxx - hyy) + 2.0 * qs * hxy
+        assert abs(T[0, 0] - (mu3 * hxx + Z + qc * tr)) < 1e-14
+        assert abs(T[1, 1] - (mu3 * hyy + Z - qc * tr)) < 1e-14
+        assert abs(T[0, 1] - (mu3 * hxy + qs * tr)) < 1e-14
+        assert abs(T[1, 0] - T[0, 1]) < 1e-14
