@@ -266,6 +266,11 @@ int fd4_fed_cycle_sched(float *d_u, int w, int h, int pitch, const float *d_tens
  * params->kappa) as in fd4_fed_taus; sigma* once on the input (unless
  * sigma_given, in which case d_sigma_idx is read); then M cycles of
  * fd4_build_tensor on the current image followed by one fd4_fed_cycle.
+ * Where the FED schedule runs the TMA kernel (2 or 4 steps per launch, the
+ * natural boundary), each cycle's tensor build leaves, in the workspace, the
+ * three coefficients that kernel reads -- (mu1 + mu2) / 2, q cos 2t and
+ * q sin 2t with q = (mu1 - mu2) / 4 -- instead of the float4 field: the same
+ * arithmetic, 12 instead of 16 bytes per pixel for the FED steps to read.
  * d_in is not modified; d_out receives the result (may equal d_in).
  * d_sigma_idx: nullable when !sigma_given (then kept in the workspace);
  * otherwise receives / supplies sigma*.                                     */
