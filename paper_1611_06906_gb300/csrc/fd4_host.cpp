@@ -566,8 +566,11 @@ extern "C" int fd4_filter(const float *d_in, float *d_out, int w, int h, int pit
 }
 
 // ---------------------------------------------------------------------------
-// Batches.  Workspace: [descriptor table | max S^2 words | per image:
-// sigma* plane, tensor plane, scratch (selection planes / N field / FED plane)].
+// Batches.  Workspace: [descriptor table | the table with in = u | the table
+// with u and the FED plane exchanged | max S^2 words | TMA maps | the exchanged
+// table's maps | per image: sigma* plane, tensor plane (float4 tensor field or
+// FED coefficient planes), chunk masks, scratch (selection planes / N field
+// and FED plane)].
 
 // Scratch of one image: the selection planes (vp, s2) over the whole of it; the
 // N field at its start and the FED plane right after the N field, so that the
