@@ -8,11 +8,16 @@
 // copies (cp.async.bulk.tensor) that one thread issues and an mbarrier counts
 // in bytes: the hardware generates the addresses, zero-fills what lies outside
 // the image, and the copies of the next two tiles overlap the current tile's
-// steps.  The u box lands dense (64 rows of 256 B); the tensor box (64 rows of
-// 16 quads of 64 B) lands with the copy's 64-byte swizzle, which places the
-// four pixels of quad q in the 16-byte slots i ^ ((q / 2) mod 4), so that the
-// 16-byte reads of a quarter-warp hit distinct banks while each value goes
-// straight to its pixel's register.  The issuing thread
+// steps.  The u box lands dense (64 rows of 256 B).  The tensor comes in one of
+// two forms (the kernel's SOA parameter).  Inside the filter, the tensor build
+// leaves the FED coefficient planes (mu3, q cos 2t, q sin 2t), whose box lands
+// as three dense planes: 12 B per pixel, read by each thread as one float4 per
+// plane and quad.  The float4 field (cos 2t, sin 2t, mu1, mu2) of fd4_fed_cycle
+// lands as 64 rows of 16 quads of 64 B with the copy's 64-byte swizzle, which
+// places the four pixels of quad q in the 16-byte slots i ^ ((q / 2) mod 4), so
+// that the 16-byte reads of a quarter-warp hit distinct banks while each value
+// goes straight to its pixel's register; the coefficients then follow per
+// tile.  The issuing thread
 // also records the tile's geometry in shared memory, so the other threads do
 // no per-tile integer division.  Per-thread 16-byte copies
 // (the cp.async kernels of fd4_fed.cu) reach about half of the HBM bandwidth on
